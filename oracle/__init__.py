@@ -1,0 +1,211 @@
+"""CPU oracle for exact k-bisimulation -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The product path (the CUDA library and
+its binding) never does, and the oracle shares no code with it.
+
+``bisim_oracle.cpp`` restates the definition of forward k-bisimulation
+(Section 2.5, with the chaining parameterization of Section 2.4.2) using exact
+signatures: sorted vectors of (edge label, neighbour block) pairs inside an
+ordered map, no hashing. ``apply_ops`` restates the update semantics of the
+incremental setting (Section 3.2: additions, deletions and modifications of
+vertices and edges) as a plain sequential edit of an edge list; by Theorem 2
+(Section 3.2.2) an incremental summary must equal the batch summary of the
+edited graph, so the oracle for an update batch is the batch oracle run on the
+result of ``apply_ops``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bisim_oracle.cpp")
+_LIB = os.path.join(_HERE, "libbisim_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+VARIANT_DEFINITION = 0
+VARIANT_DROP_EDGE_LABEL = 1
+VARIANT_DROP_SELF = 2
+VARIANT_REVERSE = 4
+VARIANT_MULTISET = 8
+VARIANT_OWN_LABEL = 16
+
+FIXPOINT = -1
+
+OP_EDGE_ADD = 0
+OP_EDGE_DEL = 1
+OP_VERTEX_ADD = 2
+OP_VERTEX_DEL = 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with the host C++ compiler."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            p = ctypes.c_void_p
+            i32, i64 = ctypes.c_int32, ctypes.c_int64
+            lib.oracle_refine.argtypes = [i32, p, p, p, i64, p, p, p, i32, i32, i32, p, p, p, p, i32]
+            lib.oracle_refine.restype = ctypes.c_int
+            lib.oracle_round.argtypes = [i32, p, p, p, i64, p, p, p, p, i32, p]
+            lib.oracle_round.restype = ctypes.c_int
+            lib.oracle_label_partition.argtypes = [i32, p, p, p, p]
+            lib.oracle_label_partition.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _i32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.int32)
+
+
+def refine(n, src, dst, elabel, vlabel, k, cap=10_000, alive=None, graph=None,
+           variant=VARIANT_DEFINITION, history=False):
+    """Exact partition after k rounds (k >= 0) or at the fixpoint (k = FIXPOINT).
+
+    Returns (P, rounds, executed[, history]) where P is int32 [n] of canonical
+    block ids (smallest vertex id of the block, -1 for dead vertices).
+    """
+    lib = _load()
+    src, dst, elabel, vlabel, graph = map(_i32, (src, dst, elabel, vlabel, graph))
+    alive = None if alive is None else np.ascontiguousarray(alive, dtype=np.uint8)
+    m = len(src)
+    P = np.empty(n, dtype=np.int32)
+    rounds = ctypes.c_int32(0)
+    executed = ctypes.c_int32(0)
+    rows = (k if k >= 0 else cap) + 1
+    hist = np.full((rows, n), -2, dtype=np.int32) if history else None
+    rc = lib.oracle_refine(n, _ptr(alive), _ptr(vlabel), _ptr(graph), m, _ptr(src), _ptr(dst),
+                           _ptr(elabel), k, cap, variant, _ptr(P), ctypes.byref(rounds),
+                           ctypes.byref(executed), _ptr(hist), rows if history else 0)
+    if rc != 0:
+        raise ValueError(f"oracle_refine rejected its input (code {rc})")
+    if history:
+        return P, rounds.value, executed.value, hist[: rounds.value + 1]
+    return P, rounds.value, executed.value
+
+
+def refine_round(n, src, dst, elabel, vlabel, P, alive=None, graph=None, variant=VARIANT_DEFINITION):
+    """One exact refinement round from partition P."""
+    lib = _load()
+    src, dst, elabel, vlabel, graph, P = map(_i32, (src, dst, elabel, vlabel, graph, P))
+    alive = None if alive is None else np.ascontiguousarray(alive, dtype=np.uint8)
+    out = np.empty(n, dtype=np.int32)
+    rc = lib.oracle_round(n, _ptr(alive), _ptr(vlabel), _ptr(graph), len(src), _ptr(src),
+                          _ptr(dst), _ptr(elabel), _ptr(P), variant, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_round rejected its input (code {rc})")
+    return out
+
+
+def label_partition(n, vlabel, alive=None, graph=None):
+    lib = _load()
+    vlabel, graph = _i32(vlabel), _i32(graph)
+    alive = None if alive is None else np.ascontiguousarray(alive, dtype=np.uint8)
+    out = np.empty(n, dtype=np.int32)
+    lib.oracle_label_partition(n, _ptr(alive), _ptr(vlabel), _ptr(graph), _ptr(out))
+    return out
+
+
+def refine_batched(b, k, cap=10_000):
+    """Each graph of a batched set refined on its own; ids are graph-local minima."""
+    vo, eo = b["vertex_offsets"], b["edge_offsets"]
+    out = np.empty(int(vo[-1]), dtype=np.int32)
+    for g in range(b["n_graphs"]):
+        v0, v1, e0, e1 = int(vo[g]), int(vo[g + 1]), int(eo[g]), int(eo[g + 1])
+        P, _, _ = refine(v1 - v0, b["src_local"][e0:e1], b["dst_local"][e0:e1],
+                         b["elabel"][e0:e1], b["vlabel"][v0:v1], k, cap)
+        out[v0:v1] = P
+    return out
+
+
+class UpdateRejected(ValueError):
+    """A batch that names an invalid vertex or operation; nothing was applied."""
+
+
+def apply_ops(state: dict, ops: np.ndarray) -> dict:
+    """Apply an update batch with sequential semantics; returns a new state.
+
+    state: dict(n, alive uint8[n], vlabel int32[n], src, dst, elabel int32[m]).
+    ops:   int32 [n_ops, 4] rows (kind, a, b, label):
+      EDGE_ADD (a -> b, label): both endpoints in range and alive, else the whole
+                                 batch is rejected.
+      EDGE_DEL (a -> b, label): removes one matching edge; a no-op if none exists.
+      VERTEX_ADD (a, label):     makes a alive with this label (relabels if alive).
+      VERTEX_DEL (a):            removes a and every edge incident to it.
+    Ids out of range or unknown kinds reject the whole batch.
+    """
+    n = int(state["n"])
+    alive = [bool(x) for x in state["alive"]]
+    vlabel = [int(x) for x in state["vlabel"]]
+    edges = list(zip((int(x) for x in state["src"]), (int(x) for x in state["dst"]),
+                     (int(x) for x in state["elabel"])))
+    # index: edge tuple -> list of live positions (a multiset)
+    where: dict = {}
+    for i, e in enumerate(edges):
+        where.setdefault(e, []).append(i)
+    live = [True] * len(edges)
+    incident: dict = {}
+    for i, (s, d, _) in enumerate(edges):
+        incident.setdefault(s, []).append(i)
+        if d != s:
+            incident.setdefault(d, []).append(i)
+    for row in np.asarray(ops, dtype=np.int64).reshape(-1, 4):
+        kind, a, b, lab = (int(x) for x in row)
+        if kind == OP_EDGE_ADD:
+            if not (0 <= a < n and 0 <= b < n) or not alive[a] or not alive[b]:
+                raise UpdateRejected(f"EDGE_ADD with invalid endpoint ({a}, {b})")
+            i = len(edges)
+            e = (a, b, lab)
+            edges.append(e)
+            live.append(True)
+            where.setdefault(e, []).append(i)
+            incident.setdefault(a, []).append(i)
+            if b != a:
+                incident.setdefault(b, []).append(i)
+        elif kind == OP_EDGE_DEL:
+            if not (0 <= a < n and 0 <= b < n):
+                raise UpdateRejected(f"EDGE_DEL with out-of-range endpoint ({a}, {b})")
+            lst = where.get((a, b, lab), [])
+            while lst and not live[lst[-1]]:
+                lst.pop()
+            if lst:
+                live[lst.pop()] = False
+        elif kind == OP_VERTEX_ADD:
+            if not (0 <= a < n):
+                raise UpdateRejected(f"VERTEX_ADD with out-of-range vertex {a}")
+            alive[a] = True
+            vlabel[a] = lab
+        elif kind == OP_VERTEX_DEL:
+            if not (0 <= a < n):
+                raise UpdateRejected(f"VERTEX_DEL with out-of-range vertex {a}")
+            alive[a] = False
+            for i in incident.get(a, []):
+                live[i] = False
+        else:
+            raise UpdateRejected(f"unknown op kind {kind}")
+    keep = [e for e, ok in zip(edges, live) if ok]
+    arr = np.array(keep, dtype=np.int32).reshape(-1, 3)
+    return dict(n=n, alive=np.array(alive, dtype=np.uint8), vlabel=np.array(vlabel, dtype=np.int32),
+                src=arr[:, 0].copy(), dst=arr[:, 1].copy(), elabel=arr[:, 2].copy())

@@ -1,0 +1,361 @@
+"""Pins for the CPU oracle: it is checked against things other than itself.
+
+* the paper's worked examples (tests/golden/, each with its citation);
+* closed forms that follow from the definition (Section 2.5);
+* brute force of the pairwise definition on tiny graphs (exhaustive and random);
+* the Paige-Tarjan coarsest stable partition for the fixpoint;
+* invariants: refinement, stability, permutation / edge-order / duplicate-edge
+  invariance, and the own-label form of the self term;
+* planted mistakes: every wrong variant of the oracle fails at least one pin.
+"""
+
+import itertools
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from refcheck import (brute_force, canonical, coarsest_stable, edges_to_arrays,
+                      parse_golden)
+
+
+def run(n, edges, vlabel, k, variant=0, cap=10_000, alive=None):
+    s, d, l = edges_to_arrays(edges)
+    P, rounds, _ = oracle.refine(n, s, d, l, np.array(vlabel, dtype=np.int32), k, cap,
+                                 alive=alive, variant=variant)
+    return P, rounds
+
+
+# --------------------------------------------------------------------------- worked examples
+
+@pytest.mark.parametrize("mode", ["T", "L"])
+def test_fig3_worked_example(mode):
+    g = parse_golden("fig3_worked_example.txt")
+    for (m, k), want in g["expect"].items():
+        if m != mode:
+            continue
+        P, _ = run(g["n"], g["edges"], g["vlabel"][mode], k)
+        assert P.tolist() == want.tolist()
+
+
+def test_fig1_schemex_reconstructed():
+    g = parse_golden("fig1_schemex_reconstructed.txt")
+    P, _ = run(g["n"], g["edges"], g["vlabel"]["t"], 1)
+    assert P.tolist() == g["expect"][("t", 1)].tolist()
+    assert P[0] == P[3]                       # v1 ~ v7 at time t
+    s, d, l = edges_to_arrays(g["edges"])
+    state = dict(n=g["n"], alive=np.ones(g["n"], np.uint8), vlabel=np.array(g["vlabel"]["t"], np.int32),
+                 src=s, dst=d, elabel=l)
+    st = oracle.apply_ops(state, np.array(g["ops"]["t1"], dtype=np.int32))
+    P1, _, _ = oracle.refine(st["n"], st["src"], st["dst"], st["elabel"], st["vlabel"], 1,
+                             alive=st["alive"])
+    assert P1.tolist() == g["expect"][("t1", 1)].tolist()
+    assert P1[0] != P1[3]                     # v1 and v7 separate after v8 becomes an Agent
+
+
+# --------------------------------------------------------------------------- closed forms
+
+def test_no_edges_keeps_label_partition():
+    vl = [3, 1, 3, 0, 1, 1, 7]
+    P0, _ = run(7, [], vl, 0)
+    assert P0.tolist() == [0, 1, 0, 3, 1, 1, 6]
+    for k in range(1, 5):
+        Pk, _ = run(7, [], vl, k)
+        assert Pk.tolist() == P0.tolist()
+    Pf, r = run(7, [], vl, oracle.FIXPOINT)
+    assert r == 0 and Pf.tolist() == P0.tolist()
+
+
+@pytest.mark.parametrize("m", [1, 2, 5, 13])
+def test_directed_path(m):
+    # v_0 -> v_1 -> ... -> v_m, one label everywhere. Vertex j lies m-j hops from
+    # the sink; after round i the vertices >= i hops away share block 0 and the
+    # others are singletons, so round i has min(i+1, m+1) blocks, fixpoint r = m.
+    edges = [(j, j + 1, 0) for j in range(m)]
+    vl = [0] * (m + 1)
+    for i in range(m + 3):
+        P, _ = run(m + 1, edges, vl, i)
+        want = [0 if (m - j) >= i else j for j in range(m + 1)]
+        assert P.tolist() == want
+        assert len(set(P.tolist())) == min(i + 1, m + 1)
+    P, r = run(m + 1, edges, vl, oracle.FIXPOINT)
+    assert r == m and P.tolist() == list(range(m + 1))
+
+
+@pytest.mark.parametrize("n", [1, 2, 7])
+def test_directed_cycle_is_one_block(n):
+    edges = [(j, (j + 1) % n, 4) for j in range(n)]
+    for k in range(4):
+        P, _ = run(n, edges, [2] * n, k)
+        assert P.tolist() == [0] * n
+
+
+def test_complete_digraph_is_one_block():
+    n = 6
+    edges = [(u, v, 1) for u in range(n) for v in range(n) if u != v]
+    P, r = run(n, edges, [5] * n, oracle.FIXPOINT)
+    assert P.tolist() == [0] * n and r == 0
+
+
+def test_out_star():
+    # hub 0 (label 0) -> leaves with labels 0/1; leaves are sinks, grouped by label;
+    # from k = 1 on the hub is a block of its own.
+    leaves = [0, 1, 1, 0, 1, 0, 0]
+    vl = [0] + leaves
+    edges = [(0, j + 1, 9) for j in range(len(leaves))]
+    P0, _ = run(len(vl), edges, vl, 0)
+    assert P0[0] == 0 and P0[1] == 0
+    first = {0: 1, 1: 2}
+    for k in (1, 2, 3):
+        P, _ = run(len(vl), edges, vl, k)
+        assert P[0] == 0
+        assert P[1:].tolist() == [first[x] for x in leaves]
+
+
+def test_label_to_neighbour_pairing_is_kept():
+    # v -a-> X, v -b-> Y, v' -a-> Y, v' -b-> X, X -c-> sink, Y -d-> sink.
+    # At k = 1 v ~ v' (X and Y share the label block); at k = 2 the definition
+    # separates them because (a, [X]) != (a, [Y]). Hashing only the neighbour
+    # ids without their edge labels would merge them.
+    v, vp, X, Y, z = 0, 1, 2, 3, 4
+    a, b, c, d = 0, 1, 2, 3
+    edges = [(v, X, a), (v, Y, b), (vp, Y, a), (vp, X, b), (X, z, c), (Y, z, d)]
+    vl = [0, 0, 0, 0, 0]
+    P1, _ = run(5, edges, vl, 1)
+    assert P1[v] == P1[vp]
+    P2, _ = run(5, edges, vl, 2)
+    assert P2[v] != P2[vp]
+
+
+# --------------------------------------------------------------------------- brute force
+
+def _check_against_brute(n, edges, vl, kmax, alive=None):
+    bf = brute_force(n, edges, vl, kmax, alive=alive)
+    for k in range(kmax + 1):
+        P, _ = run(n, edges, vl, k, alive=alive)
+        assert P.tolist() == bf[k].tolist(), (n, edges, vl, k)
+
+
+def test_brute_force_exhaustive_n3_one_label():
+    pairs = [(u, v) for u in range(3) for v in range(3)]
+    for mask in range(1 << len(pairs)):
+        edges = [(u, v, 0) for i, (u, v) in enumerate(pairs) if mask >> i & 1]
+        for vl in ([0, 0, 0], [0, 0, 1], [0, 1, 0], [1, 0, 0]):
+            _check_against_brute(3, edges, vl, 3)
+
+
+def test_brute_force_exhaustive_n2_two_labels():
+    cand = [(u, v, l) for u in range(2) for v in range(2) for l in range(2)]
+    for mask in range(1 << len(cand)):
+        edges = [e for i, e in enumerate(cand) if mask >> i & 1]
+        for vl in ([0, 0], [0, 1]):
+            _check_against_brute(2, edges, vl, 3)
+
+
+def test_brute_force_random_multigraphs():
+    rnd = random.Random(12493)
+    for _ in range(250):
+        n = rnd.randint(1, 11)
+        m = rnd.randint(0, 3 * n)
+        L = rnd.randint(1, 3)
+        edges = [(rnd.randrange(n), rnd.randrange(n), rnd.randrange(L)) for _ in range(m)]
+        edges += edges[: rnd.randint(0, len(edges))]          # duplicate some edges
+        vl = [rnd.choice([-1, 0, 1]) for _ in range(n)]
+        alive = [rnd.random() > 0.15 for _ in range(n)]
+        _check_against_brute(n, edges, vl, rnd.randint(0, 5), alive=np.array(alive, np.uint8))
+
+
+# --------------------------------------------------------------------------- fixpoint
+
+def test_fixpoint_equals_coarsest_stable_partition():
+    rnd = random.Random(7)
+    for _ in range(120):
+        n = rnd.randint(1, 16)
+        m = rnd.randint(0, 3 * n)
+        L = rnd.randint(1, 3)
+        edges = [(rnd.randrange(n), rnd.randrange(n), rnd.randrange(L)) for _ in range(m)]
+        vl = [rnd.randrange(2) for _ in range(n)]
+        P, r = run(n, edges, vl, oracle.FIXPOINT)
+        assert P.tolist() == coarsest_stable(n, edges, vl).tolist()
+        # r is the first round after which nothing changes
+        Pr, _ = run(n, edges, vl, r)
+        assert Pr.tolist() == P.tolist()
+        if r > 0:
+            Prm, _ = run(n, edges, vl, r - 1)
+            assert Prm.tolist() != P.tolist()
+
+
+# --------------------------------------------------------------------------- invariants
+
+def _rand_graph(seed, n=60, m=200, L=4, V=3):
+    rnd = np.random.default_rng(seed)
+    return (n, rnd.integers(0, n, m).astype(np.int32), rnd.integers(0, n, m).astype(np.int32),
+            rnd.integers(0, L, m).astype(np.int32), rnd.integers(0, V, n).astype(np.int32))
+
+
+def _refines(fine, coarse):
+    seen = {}
+    for f, c in zip(fine.tolist(), coarse.tolist()):
+        if seen.setdefault(f, c) != c:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_refinement_and_stability(seed):
+    n, s, d, l, vl = _rand_graph(seed)
+    P, r, ex, hist = oracle.refine(n, s, d, l, vl, oracle.FIXPOINT, history=True)
+    for i in range(1, len(hist)):
+        assert _refines(hist[i], hist[i - 1])
+        assert len(set(hist[i].tolist())) >= len(set(hist[i - 1].tolist()))
+    again = oracle.refine_round(n, s, d, l, vl, P)
+    assert again.tolist() == P.tolist()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_permutation_invariance(seed):
+    n, s, d, l, vl = _rand_graph(seed)
+    pi = np.random.default_rng(100 + seed).permutation(n).astype(np.int32)
+    for k in (0, 1, 2, 4):
+        P, _, _ = oracle.refine(n, s, d, l, vl, k)
+        vl2 = np.empty_like(vl)
+        vl2[pi] = vl
+        Q, _, _ = oracle.refine(n, pi[s], pi[d], l, vl2, k)
+        # the partition maps under pi: u ~ v  <=>  pi(u) ~ pi(v)
+        assert canonical(Q[pi]).tolist() == P.tolist()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_edge_order_and_duplicate_invariance(seed):
+    n, s, d, l, vl = _rand_graph(seed)
+    P, _, _ = oracle.refine(n, s, d, l, vl, 3)
+    order = np.random.default_rng(seed).permutation(len(s))
+    dup = np.random.default_rng(seed + 1).integers(0, len(s), 80)
+    s2 = np.concatenate([s[order], s[dup]])
+    d2 = np.concatenate([d[order], d[dup]])
+    l2 = np.concatenate([l[order], l[dup]])
+    Q, _, _ = oracle.refine(n, s2, d2, l2, vl, 3)
+    assert Q.tolist() == P.tolist()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_own_label_self_term_gives_same_partition(seed):
+    n, s, d, l, vl = _rand_graph(seed)
+    for k in (1, 2, 5, oracle.FIXPOINT):
+        P, r1, _ = oracle.refine(n, s, d, l, vl, k)
+        Q, r2, _ = oracle.refine(n, s, d, l, vl, k, variant=oracle.VARIANT_OWN_LABEL)
+        assert P.tolist() == Q.tolist() and r1 == r2
+
+
+def test_batched_graph_ids_keep_graphs_apart():
+    from paper_2111_12493_gb300 import graphgen
+    b = graphgen.batched_graphs(n_graphs=12, nmin=5, nmax=60, seed=9)
+    u = graphgen.batched_union(b)
+    P, _, _ = oracle.refine(u["n"], u["src"], u["dst"], u["elabel"], u["vlabel"], 3, graph=u["graph"])
+    local = oracle.refine_batched(b, 3)
+    off = np.repeat(b["vertex_offsets"][:-1], np.diff(b["vertex_offsets"]))
+    assert (P - off).tolist() == local.tolist()
+
+
+# --------------------------------------------------------------------------- planted mistakes
+
+PINS = []
+
+
+def _pin(f):
+    PINS.append(f)
+    return f
+
+
+@_pin
+def _pin_fig3(variant):
+    g = parse_golden("fig3_worked_example.txt")
+    for (mode, k), want in g["expect"].items():
+        P, _ = run(g["n"], g["edges"], g["vlabel"][mode], k, variant=variant)
+        if P.tolist() != want.tolist():
+            return False
+    return True
+
+
+@_pin
+def _pin_no_edges(variant):
+    vl = [3, 1, 3, 0, 1]
+    P, _ = run(5, [], vl, 2, variant=variant)
+    return P.tolist() == [0, 1, 0, 3, 1]
+
+
+@_pin
+def _pin_path(variant):
+    m = 6
+    edges = [(j, j + 1, 0) for j in range(m)]
+    for i in range(m + 1):
+        P, _ = run(m + 1, edges, [0] * (m + 1), i, variant=variant)
+        if P.tolist() != [0 if (m - j) >= i else j for j in range(m + 1)]:
+            return False
+    return True
+
+
+@_pin
+def _pin_pairing(variant):
+    edges = [(0, 2, 0), (0, 3, 1), (1, 3, 0), (1, 2, 1), (2, 4, 2), (3, 4, 3)]
+    P, _ = run(5, edges, [0] * 5, 2, variant=variant)
+    return P[0] != P[1]
+
+
+@_pin
+def _pin_brute(variant):
+    rnd = random.Random(5)
+    for _ in range(60):
+        n = rnd.randint(2, 8)
+        edges = [(rnd.randrange(n), rnd.randrange(n), rnd.randrange(2)) for _ in range(rnd.randint(1, 2 * n))]
+        edges += edges[:2]
+        vl = [rnd.randrange(2) for _ in range(n)]
+        bf = brute_force(n, edges, vl, 3)
+        for k in range(4):
+            P, _ = run(n, edges, vl, k, variant=variant)
+            if P.tolist() != bf[k].tolist():
+                return False
+    return True
+
+
+def test_definition_passes_every_pin():
+    for pin in PINS:
+        assert pin(oracle.VARIANT_DEFINITION), pin.__name__
+        assert pin(oracle.VARIANT_OWN_LABEL), pin.__name__
+
+
+@pytest.mark.parametrize("variant", [oracle.VARIANT_DROP_EDGE_LABEL, oracle.VARIANT_DROP_SELF,
+                                     oracle.VARIANT_REVERSE, oracle.VARIANT_MULTISET])
+def test_planted_mistake_is_caught(variant):
+    failed = [pin.__name__ for pin in PINS if not pin(variant)]
+    assert failed, f"variant {variant} passed every pin"
+
+
+# --------------------------------------------------------------------------- update semantics
+
+def test_apply_ops_sequential_semantics():
+    st = dict(n=4, alive=np.ones(4, np.uint8), vlabel=np.zeros(4, np.int32),
+              src=np.array([0, 0, 1], np.int32), dst=np.array([1, 1, 2], np.int32),
+              elabel=np.array([5, 5, 6], np.int32))
+    ops = np.array([[oracle.OP_EDGE_DEL, 0, 1, 5],     # removes one of the two parallel edges
+                    [oracle.OP_EDGE_DEL, 3, 2, 1],     # absent: no-op
+                    [oracle.OP_EDGE_ADD, 2, 3, 7],
+                    [oracle.OP_VERTEX_DEL, 1, 0, 0],   # drops 0->1 and 1->2
+                    [oracle.OP_VERTEX_ADD, 1, 0, 9]],  # back, with no edges and label 9
+                   dtype=np.int32)
+    out = oracle.apply_ops(st, ops)
+    assert out["alive"].tolist() == [1, 1, 1, 1]
+    assert out["vlabel"].tolist() == [0, 9, 0, 0]
+    assert sorted(zip(out["src"].tolist(), out["dst"].tolist(), out["elabel"].tolist())) == [(2, 3, 7)]
+
+
+def test_apply_ops_rejects_whole_batch():
+    st = dict(n=3, alive=np.array([1, 1, 0], np.uint8), vlabel=np.zeros(3, np.int32),
+              src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32), elabel=np.zeros(0, np.int32))
+    with pytest.raises(oracle.UpdateRejected):
+        oracle.apply_ops(st, np.array([[oracle.OP_EDGE_ADD, 0, 1, 0], [oracle.OP_EDGE_ADD, 0, 2, 0]], np.int32))
+    with pytest.raises(oracle.UpdateRejected):
+        oracle.apply_ops(st, np.array([[oracle.OP_EDGE_ADD, 0, 3, 0]], np.int32))
+    with pytest.raises(oracle.UpdateRejected):
+        oracle.apply_ops(st, np.array([[9, 0, 1, 0]], np.int32))
