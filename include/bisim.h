@@ -1,0 +1,221 @@
+/*
+ * bisim.h -- C-ABI of the GB300 k-bisimulation library (libbisim_gb300.so).
+ *
+ * The library computes the forward k-bisimulation partition of a directed,
+ * edge-labelled multigraph with one int32 label per vertex and one per edge:
+ * the equivalence of Section 2.5 of arXiv 2111.12493, refined round by round
+ * as in Algorithm 4 (Section 3.3.1, "Iterative Parallel Hash-Messaging"), with
+ * every hash match confirmed by an exact comparison of the full signatures so
+ * that the result is the exact partition and not a probabilistic one.
+ *
+ * Round i -> i+1 (Algorithm 4: SignalMessages, MergeMessages, Hash; the
+ * definition of Section 2.5; the chaining parameterization of Section 2.4.2):
+ *   S_i(v)     = { (l, P_i[w]) : (v, w, l) is an out-edge of v }   (a set)
+ *   P_{i+1}[v] = smallest u with (P_i[u], S_i(u)) == (P_i[v], S_i(v))
+ * P_0 groups vertices by label (the labelled variant of Section 2.5); with all
+ * labels equal it is the tautology start of the paper's worked example.
+ * Block ids are canonical: the smallest vertex id in the block (for batched
+ * graphs: the smallest graph-local id). Deleted vertices read -1.
+ *
+ * Conventions for every call:
+ *  - Vertex ids are int32 in [0, n); edge counts are int64.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Work is enqueued on it; calls that return scalars (rounds, block
+ *    counts) synchronise it before returning.
+ *  - Input arrays may live in device memory or in host memory (pinned host
+ *    memory is copied asynchronously, pageable memory synchronously). The
+ *    library copies every input into buffers it owns before the call returns
+ *    control of the stream; the caller keeps ownership of its arrays and may
+ *    reuse them once the stream has passed that point.
+ *  - Output arrays are caller-allocated (device or host memory).
+ *  - Errors are reported only by return code; no exception crosses the ABI.
+ *    After an error the context keeps its last good state, and
+ *    bisim_last_error() describes what went wrong.
+ *  - A context is not thread-safe: one caller at a time per context.
+ */
+#ifndef BISIM_GB300_H
+#define BISIM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bisim_ctx bisim_ctx;   /* opaque; owned by the library */
+
+typedef enum {
+    BISIM_OK = 0,
+    BISIM_EINVAL = 1,    /* invalid argument or malformed graph */
+    BISIM_ENOMEM = 2,    /* device allocation failed or the memory budget is exceeded */
+    BISIM_ECUDA = 3,     /* a CUDA call failed; see bisim_last_error() */
+    BISIM_ESTATE = 4,    /* call not valid in the context's current state */
+    BISIM_ETIMEOUT = 5,  /* a bounded device-side loop ran out of iterations */
+    BISIM_EADMIT = 6     /* request refused by admission control (serving) */
+} bisim_status;
+
+enum { BISIM_FIXPOINT = -1 };
+
+/* Update operations (Section 3.2, incremental summarization of evolving graphs:
+ * additions, deletions and modifications of vertices and edges). */
+enum {
+    BISIM_OP_EDGE_ADD = 0,    /* add edge (src -> dst, label); both endpoints must be live */
+    BISIM_OP_EDGE_DEL = 1,    /* remove one edge (src -> dst, label); a no-op if none exists */
+    BISIM_OP_VERTEX_ADD = 2,  /* make vertex src live with vertex label `label` (relabels a live one) */
+    BISIM_OP_VERTEX_DEL = 3   /* remove vertex src and every edge incident to it */
+};
+
+typedef struct {
+    int32_t kind;
+    int32_t src;
+    int32_t dst;
+    int32_t label;
+} bisim_op;
+
+typedef struct {
+    int32_t k_incremental;     /* rounds maintained by apply_updates (default 2) */
+    int32_t hash_bits;         /* signature hash width, 1..64 (default 64). Lower values force
+                                  collisions and exist to test the exact check; results are
+                                  identical at every width, only slower. */
+    int32_t small_max_degree;  /* out-degree <= this: one thread per vertex (default 32, max 32) */
+    int32_t mid_max_degree;    /* out-degree <= this: one CTA per vertex, keys staged in shared
+                                  memory (default 8192, max 8192); above it: hub path, many CTAs
+                                  per vertex with a global dedup table */
+    int32_t hub_chunk;         /* edges per CTA on the hub path (default 4096) */
+    int32_t reserved0;
+    int64_t mem_budget_bytes;  /* refuse (BISIM_ENOMEM) contexts whose device footprint would
+                                  exceed this; 0 = no limit */
+} bisim_options;
+
+typedef struct {
+    int32_t n_vertices;
+    int32_t n_graphs;
+    int64_t n_edges;
+    int32_t rounds;            /* result of the last bisim_iterate (k or the fixpoint round) */
+    int32_t rounds_executed;   /* refinement rounds computed by the last bisim_iterate */
+    int64_t num_blocks;        /* blocks of the current partition */
+    int64_t collision_levels;  /* extra exact-resolution passes taken after hash collisions */
+    int64_t device_bytes;      /* device memory held by the context */
+    int64_t n_small, n_mid, n_hub;  /* vertices per degree bucket */
+    int64_t updates_applied;   /* operations applied by apply_updates so far */
+    int64_t last_frontier;     /* vertices recomputed by the last apply_updates */
+} bisim_stats;
+
+/* Fills `opt` with the defaults listed above. */
+void bisim_default_options(bisim_options* opt);
+
+/*
+ * summarize_init -- create a context from an out-CSR graph (the initialization
+ * step of Algorithm 4: every vertex gets its initial id from its label).
+ *   n_vertices  number of vertices n >= 0
+ *   n_edges     number of edges m >= 0
+ *   row_ptr     int64[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
+ *   col         int32[m], edge targets in [0, n), row v holds the out-edges of v
+ *   edge_label  int32[m], any int32 values
+ *   vertex_label int32[n], any int32 values (-1 is an ordinary label)
+ *   alive       uint8[n] or NULL (all live); a dead vertex may not have edges
+ *   opt         options or NULL for defaults
+ * Returns BISIM_EINVAL for malformed input (nothing is allocated then).
+ * The partition starts at P_0; call bisim_iterate to refine it.
+ */
+bisim_status summarize_init(bisim_ctx** out, int32_t n_vertices, int64_t n_edges,
+                            const int64_t* row_ptr, const int32_t* col,
+                            const int32_t* edge_label, const int32_t* vertex_label,
+                            const uint8_t* alive, const bisim_options* opt, void* stream);
+
+/*
+ * summarize_init_coo -- as summarize_init, from an edge list: src/dst int32[m]
+ * in [0, n), edge_label int32[m]. The out-CSR is built on the device by a
+ * stable LSD radix sort on src.
+ */
+bisim_status summarize_init_coo(bisim_ctx** out, int32_t n_vertices, int64_t n_edges,
+                                const int32_t* src, const int32_t* dst,
+                                const int32_t* edge_label, const int32_t* vertex_label,
+                                const uint8_t* alive, const bisim_options* opt, void* stream);
+
+/*
+ * summarize_init_batched -- many independent graphs refined together as one
+ * disjoint union. vertex_offsets / edge_offsets are int64[n_graphs+1] prefix
+ * sums; src_local / dst_local are graph-local ids (0 <= id < n_g) of the edges
+ * of each graph, stored graph after graph; edge_label int32[total edges];
+ * vertex_label int32[total vertices]. No block ever crosses two graphs, and
+ * get_partition returns graph-local canonical ids. The result for every graph
+ * equals refining that graph alone.
+ */
+bisim_status summarize_init_batched(bisim_ctx** out, int32_t n_graphs,
+                                    const int64_t* vertex_offsets, const int64_t* edge_offsets,
+                                    const int32_t* src_local, const int32_t* dst_local,
+                                    const int32_t* edge_label, const int32_t* vertex_label,
+                                    const bisim_options* opt, void* stream);
+
+/*
+ * bisim_iterate -- reset to P_0 and refine (Algorithm 4's k signal phases).
+ *   k >= 0          run k rounds (k = 0 leaves the label partition)
+ *   k = BISIM_FIXPOINT  run until a round changes nothing, at most `cap` rounds
+ *   out_rounds      k, or the fixpoint round r (the first r with P_{r+1} = P_r;
+ *                   cap if the cap was hit first); may be NULL
+ *   out_num_blocks  number of blocks of the result; may be NULL
+ * A round whose block count equals the previous one proves the fixpoint (each
+ * round refines the previous partition), so later rounds are skipped; the
+ * result is the same partition. Synchronises `stream`.
+ */
+bisim_status bisim_iterate(bisim_ctx* ctx, int32_t k, int32_t cap, int32_t* out_rounds,
+                           int64_t* out_num_blocks, void* stream);
+
+/*
+ * apply_updates -- apply a batch of update operations (bisim_op[n_ops]) in
+ * array order and bring the partition up to date at k = opt.k_incremental
+ * rounds, recomputing only vertices within k reverse hops of a change. By
+ * Theorem 2 (Section 3.2.2) the result equals a batch run on the edited graph.
+ * A batch naming an out-of-range vertex, a dead endpoint of EDGE_ADD, or an
+ * unknown kind is rejected whole with BISIM_EINVAL and nothing changes.
+ * Synchronises `stream`.
+ */
+bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, void* stream);
+
+/*
+ * get_partition -- write the current canonical block ids to `block`
+ * (int32[n], or int32[total vertices] for batched contexts; -1 for dead
+ * vertices).
+ */
+bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream);
+
+/* Counters of the context (see bisim_stats). Synchronises nothing. */
+bisim_status bisim_get_stats(const bisim_ctx* ctx, bisim_stats* out);
+
+/* Free every device buffer of the context. NULL is accepted. */
+bisim_status summarize_destroy(bisim_ctx* ctx);
+
+/*
+ * Kernel timing (process-wide, off by default). When enabled, every kernel the
+ * library launches is bracketed by CUDA events on the stream it runs on, and
+ * its duration is accumulated per launch site together with the algorithmic
+ * bytes the launch had to move (per-unit figures x units processed). Enabling
+ * adds two event records per launch; the numbers are read back with
+ * bisim_profile_read, which synchronises the recorded events.
+ */
+typedef struct {
+    char name[40];           /* launch site, e.g. "sig_small_4", "verify" */
+    int64_t launches;
+    double total_ms;         /* summed event-timed durations */
+    double alg_bytes;        /* summed algorithmic bytes */
+    int64_t vertices;        /* vertices processed */
+    int64_t edges;           /* edges processed */
+} bisim_kernel_profile;
+
+void bisim_profile_enable(int32_t enable);
+void bisim_profile_reset(void);
+/* Copies up to `max` entries into `out` and returns how many sites exist. */
+int32_t bisim_profile_read(bisim_kernel_profile* out, int32_t max);
+/* Kernels launched by this library in this process so far (always counted). */
+int64_t bisim_launch_count(void);
+
+/* Description of the last error on ctx, or of the calling thread's last
+ * failed call when ctx is NULL. Never NULL. */
+const char* bisim_last_error(const bisim_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BISIM_GB300_H */

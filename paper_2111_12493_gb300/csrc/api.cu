@@ -1,0 +1,425 @@
+// C-ABI entry points (declared in include/bisim.h): argument checks, input
+// staging, context lifetime, and the round loop of bisim_iterate.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+#include "prof.cuh"
+
+namespace bisim {
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+void setup_pool(int device) {
+    static std::once_flag once[64];
+    if (device < 0 || device >= 64) return;
+    std::call_once(once[device], [device]() {
+        // Keep freed memory in the stream-ordered pool for this process, so that
+        // repeated contexts do not return to the driver for every allocation.
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+bool device_accessible(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device-resident view of a caller array: the array itself if the GPU can
+// read it, else a stream-ordered copy that the caller frees after use.
+cudaError_t stage(const void* p, size_t bytes, cudaStream_t s, const void** out, std::vector<void*>& temps) {
+    if (p == nullptr || bytes == 0 || device_accessible(p)) {
+        *out = p;
+        return cudaSuccess;
+    }
+    void* d = nullptr;
+    cudaError_t e = cudaMallocAsync(&d, bytes, s);
+    if (e) return e;
+    temps.push_back(d);
+    e = cudaMemcpyAsync(d, p, bytes, cudaMemcpyDefault, s);
+    *out = d;
+    return e;
+}
+
+void free_temps(std::vector<void*>& temps, cudaStream_t s) {
+    for (void* p : temps) cudaFreeAsync(p, s);
+    temps.clear();
+}
+
+void destroy_ctx(bisim_ctx* ctx) {
+    if (ctx == nullptr) return;
+    for (void* p : ctx->allocs) cudaFreeAsync(p, 0);
+    if (ctx->dstate) cudaFreeAsync(ctx->dstate, 0);
+    if (ctx->hstate) cudaFreeHost(ctx->hstate);
+    delete ctx;
+}
+
+bisim_options resolve_options(const bisim_options* in) {
+    bisim_options o;
+    bisim_default_options(&o);
+    if (in != nullptr) o = *in;
+    if (o.hash_bits <= 0 || o.hash_bits > 64) o.hash_bits = 64;
+    o.small_max_degree = std::min(std::max(o.small_max_degree, 0), 32);
+    o.mid_max_degree = std::min(std::max(o.mid_max_degree, 0), kMidMaxN);
+    if (o.hub_chunk <= 0) o.hub_chunk = 4096;
+    if (o.k_incremental < 0) o.k_incremental = 0;
+    return o;
+}
+
+bisim_status new_ctx(bisim_ctx** out, int32_t n, int64_t m, const bisim_options* opt, cudaStream_t s,
+                     bisim_ctx** made) {
+    if (out == nullptr) return set_error(nullptr, BISIM_EINVAL, "out pointer is NULL");
+    *out = nullptr;
+    if (n < 0 || m < 0) return set_error(nullptr, BISIM_EINVAL, "negative vertex or edge count");
+    bisim_ctx* ctx = new bisim_ctx();
+    ctx->n = n;
+    ctx->m = m;
+    ctx->opt = resolve_options(opt);
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e) { delete ctx; return cuda_error(nullptr, e, "cudaGetDevice"); }
+    setup_pool(ctx->device);
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&ctx->dstate), sizeof(DevState), s)) ||
+        (e = cudaHostAlloc(reinterpret_cast<void**>(&ctx->hstate), sizeof(DevState), cudaHostAllocDefault))) {
+        destroy_ctx(ctx);
+        return cuda_error(nullptr, e, "allocate context state");
+    }
+    cudaMemsetAsync(ctx->dstate, 0, sizeof(DevState), s);
+    std::memset(ctx->hstate, 0, sizeof(DevState));
+    *made = ctx;
+    return BISIM_OK;
+}
+
+bisim_status copy_vertex_arrays(bisim_ctx* ctx, const int32_t* vlabel, const uint8_t* alive, cudaStream_t s) {
+    const size_t nv = static_cast<size_t>(std::max(ctx->n, 1));
+    cudaError_t e;
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->vlabel), sizeof(int32_t) * nv, s))) return cuda_error(ctx, e, "alloc labels");
+    if (ctx->n > 0) cudaMemcpyAsync(ctx->vlabel, vlabel, sizeof(int32_t) * ctx->n, cudaMemcpyDefault, s);
+    if (alive != nullptr) {
+        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->alive), nv, s))) return cuda_error(ctx, e, "alloc alive");
+        if (ctx->n > 0) cudaMemcpyAsync(ctx->alive, alive, ctx->n, cudaMemcpyDefault, s);
+    }
+    if ((e = cudaGetLastError())) return cuda_error(ctx, e, "copy vertex arrays");
+    return BISIM_OK;
+}
+
+bisim_status finish_init(bisim_ctx* ctx, cudaStream_t s) {
+    bisim_status st;
+    if ((st = build_buckets(ctx, s)) != BISIM_OK) return st;
+    if ((st = alloc_refine_state(ctx, s)) != BISIM_OK) return st;
+    if (ctx->opt.mem_budget_bytes > 0 && ctx->device_bytes > ctx->opt.mem_budget_bytes)
+        return set_error(ctx, BISIM_ENOMEM, "context exceeds the memory budget");
+    if ((st = compute_p0(ctx, s)) != BISIM_OK) return st;
+    cudaMemcpyAsync(ctx->P[0], ctx->P0, sizeof(int32_t) * std::max(ctx->n, 1), cudaMemcpyDeviceToDevice, s);
+    ctx->cur = 0;
+    ctx->stats.n_vertices = ctx->n;
+    ctx->stats.n_edges = ctx->m;
+    ctx->stats.n_graphs = ctx->n_graphs;
+    ctx->stats.device_bytes = ctx->device_bytes;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e) return cuda_error(ctx, e, "initialise partition");
+    return BISIM_OK;
+}
+
+__global__ void k_globalize(const int64_t* __restrict__ voff, const int64_t* __restrict__ eoff, int32_t G,
+                            const int32_t* __restrict__ sl, const int32_t* __restrict__ dl, int64_t m,
+                            int32_t* __restrict__ src, int32_t* __restrict__ dst, unsigned* err) {
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        int lo = 0, hi = G - 1;   // graph g with eoff[g] <= e < eoff[g+1]
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (eoff[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const int64_t ng = voff[lo + 1] - voff[lo];
+        const int32_t a = sl[e], b = dl[e];
+        if (a < 0 || a >= ng || b < 0 || b >= ng) {
+            atomicOr(err, kErrBadInput);
+            src[e] = 0;
+            dst[e] = 0;
+        } else {
+            src[e] = static_cast<int32_t>(voff[lo] + a);
+            dst[e] = static_cast<int32_t>(voff[lo] + b);
+        }
+    }
+}
+
+__global__ void k_graph_ids(const int64_t* __restrict__ voff, int32_t G, int32_t n, int32_t* __restrict__ gid) {
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (voff[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    gid[v] = lo;
+}
+
+}  // namespace
+
+bisim_status set_error(bisim_ctx* ctx, bisim_status st, const std::string& msg) {
+    if (ctx != nullptr) ctx->err = msg;
+    g_last_error = msg;
+    return st;
+}
+
+bisim_status cuda_error(bisim_ctx* ctx, cudaError_t e, const char* what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return set_error(ctx, BISIM_ECUDA, msg);
+}
+
+cudaError_t ctx_alloc(bisim_ctx* ctx, void** p, size_t bytes, cudaStream_t s) {
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaSuccess) {
+        ctx->allocs.push_back(*p);
+        ctx->device_bytes += static_cast<int64_t>(bytes);
+    }
+    return e;
+}
+
+}  // namespace bisim
+
+using namespace bisim;
+
+extern "C" {
+
+void bisim_default_options(bisim_options* opt) {
+    if (opt == nullptr) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->k_incremental = 2;
+    opt->hash_bits = 64;
+    opt->small_max_degree = 32;
+    opt->mid_max_degree = kMidMaxN;
+    opt->hub_chunk = 4096;
+    opt->mem_budget_bytes = 0;
+}
+
+bisim_status summarize_init(bisim_ctx** out, int32_t n_vertices, int64_t n_edges, const int64_t* row_ptr,
+                            const int32_t* col, const int32_t* edge_label, const int32_t* vertex_label,
+                            const uint8_t* alive, const bisim_options* opt, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bisim_ctx* ctx = nullptr;
+    bisim_status st = new_ctx(out, n_vertices, n_edges, opt, s, &ctx);
+    if (st != BISIM_OK) return st;
+    if (row_ptr == nullptr || (n_vertices > 0 && vertex_label == nullptr) ||
+        (n_edges > 0 && (col == nullptr || edge_label == nullptr))) {
+        destroy_ctx(ctx);
+        return set_error(nullptr, BISIM_EINVAL, "a required array is NULL");
+    }
+    if ((st = copy_vertex_arrays(ctx, vertex_label, alive, s)) == BISIM_OK &&
+        (st = build_from_csr(ctx, row_ptr, col, edge_label, s)) == BISIM_OK &&
+        (st = finish_init(ctx, s)) == BISIM_OK) {
+        *out = ctx;
+        return BISIM_OK;
+    }
+    std::string msg = ctx->err;
+    destroy_ctx(ctx);
+    return set_error(nullptr, st, msg);
+}
+
+bisim_status summarize_init_coo(bisim_ctx** out, int32_t n_vertices, int64_t n_edges, const int32_t* src,
+                                const int32_t* dst, const int32_t* edge_label, const int32_t* vertex_label,
+                                const uint8_t* alive, const bisim_options* opt, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bisim_ctx* ctx = nullptr;
+    bisim_status st = new_ctx(out, n_vertices, n_edges, opt, s, &ctx);
+    if (st != BISIM_OK) return st;
+    if ((n_vertices > 0 && vertex_label == nullptr) ||
+        (n_edges > 0 && (src == nullptr || dst == nullptr || edge_label == nullptr))) {
+        destroy_ctx(ctx);
+        return set_error(nullptr, BISIM_EINVAL, "a required array is NULL");
+    }
+    std::vector<void*> temps;
+    const void *ds = nullptr, *dd = nullptr, *dl = nullptr;
+    cudaError_t e;
+    const size_t eb = sizeof(int32_t) * static_cast<size_t>(n_edges);
+    if ((st = copy_vertex_arrays(ctx, vertex_label, alive, s)) == BISIM_OK) {
+        if ((e = stage(src, eb, s, &ds, temps)) || (e = stage(dst, eb, s, &dd, temps)) ||
+            (e = stage(edge_label, eb, s, &dl, temps)))
+            st = cuda_error(ctx, e, "stage edge arrays");
+    }
+    if (st == BISIM_OK)
+        st = build_from_coo(ctx, static_cast<const int32_t*>(ds), static_cast<const int32_t*>(dd),
+                            static_cast<const int32_t*>(dl), s);
+    free_temps(temps, s);
+    if (st == BISIM_OK && (st = finish_init(ctx, s)) == BISIM_OK) {
+        *out = ctx;
+        return BISIM_OK;
+    }
+    std::string msg = ctx->err;
+    destroy_ctx(ctx);
+    return set_error(nullptr, st, msg);
+}
+
+bisim_status summarize_init_batched(bisim_ctx** out, int32_t n_graphs, const int64_t* vertex_offsets,
+                                    const int64_t* edge_offsets, const int32_t* src_local,
+                                    const int32_t* dst_local, const int32_t* edge_label,
+                                    const int32_t* vertex_label, const bisim_options* opt, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (out == nullptr) return set_error(nullptr, BISIM_EINVAL, "out pointer is NULL");
+    *out = nullptr;
+    if (n_graphs <= 0 || vertex_offsets == nullptr || edge_offsets == nullptr)
+        return set_error(nullptr, BISIM_EINVAL, "batched init needs n_graphs >= 1 and both offset arrays");
+    std::vector<int64_t> hv(n_graphs + 1), he(n_graphs + 1);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(hv.data(), vertex_offsets, sizeof(int64_t) * (n_graphs + 1), cudaMemcpyDefault, s)) ||
+        (e = cudaMemcpyAsync(he.data(), edge_offsets, sizeof(int64_t) * (n_graphs + 1), cudaMemcpyDefault, s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return cuda_error(nullptr, e, "read batch offsets");
+    if (hv[0] != 0 || he[0] != 0) return set_error(nullptr, BISIM_EINVAL, "offsets must start at 0");
+    for (int32_t g = 0; g < n_graphs; ++g)
+        if (hv[g + 1] < hv[g] || he[g + 1] < he[g]) return set_error(nullptr, BISIM_EINVAL, "offsets must be non-decreasing");
+    if (hv[n_graphs] > INT32_MAX) return set_error(nullptr, BISIM_EINVAL, "more than 2^31-1 vertices in total");
+    const int32_t n = static_cast<int32_t>(hv[n_graphs]);
+    const int64_t m = he[n_graphs];
+    bisim_ctx* ctx = nullptr;
+    bisim_status st = new_ctx(out, n, m, opt, s, &ctx);
+    if (st != BISIM_OK) return st;
+    ctx->n_graphs = n_graphs;
+    if ((n > 0 && vertex_label == nullptr) || (m > 0 && (src_local == nullptr || dst_local == nullptr || edge_label == nullptr))) {
+        destroy_ctx(ctx);
+        return set_error(nullptr, BISIM_EINVAL, "a required array is NULL");
+    }
+    std::vector<void*> temps;
+    const void *ds = nullptr, *dd = nullptr, *dl = nullptr;
+    const size_t eb = sizeof(int32_t) * static_cast<size_t>(m);
+    int32_t* gsrc = nullptr;
+    int32_t* gdst = nullptr;
+    int64_t* deoff = nullptr;
+    if ((st = copy_vertex_arrays(ctx, vertex_label, nullptr, s)) == BISIM_OK) {
+        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->voff), sizeof(int64_t) * (n_graphs + 1), s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->gid), sizeof(int32_t) * std::max(n, 1), s)) ||
+            (e = cudaMallocAsync(reinterpret_cast<void**>(&deoff), sizeof(int64_t) * (n_graphs + 1), s)) ||
+            (e = cudaMallocAsync(reinterpret_cast<void**>(&gsrc), std::max<size_t>(eb, 4), s)) ||
+            (e = cudaMallocAsync(reinterpret_cast<void**>(&gdst), std::max<size_t>(eb, 4), s)) ||
+            (e = stage(src_local, eb, s, &ds, temps)) || (e = stage(dst_local, eb, s, &dd, temps)) ||
+            (e = stage(edge_label, eb, s, &dl, temps)))
+            st = cuda_error(ctx, e, "stage batched arrays");
+    }
+    if (st == BISIM_OK) {
+        cudaMemcpyAsync(ctx->voff, hv.data(), sizeof(int64_t) * (n_graphs + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(deoff, he.data(), sizeof(int64_t) * (n_graphs + 1), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(&ctx->dstate->error, 0, sizeof(unsigned), s);
+        BISIM_SITE(site_g, "batch_graph_ids");
+        BISIM_SITE(site_e, "batch_globalize");
+        if (n > 0)
+            Launch(site_g, s, n, 0, 4.0 * n),
+            k_graph_ids<<<(n + 255) / 256, 256, 0, s>>>(ctx->voff, n_graphs, n, ctx->gid);
+        if (m > 0)
+            Launch(site_e, s, 0, m, 16.0 * m),
+            k_globalize<<<static_cast<unsigned>(std::min<int64_t>((m + 255) / 256, 1 << 16)), 256, 0, s>>>(
+                ctx->voff, deoff, n_graphs, static_cast<const int32_t*>(ds), static_cast<const int32_t*>(dd), m,
+                gsrc, gdst, &ctx->dstate->error);
+        cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s))) st = cuda_error(ctx, e, "globalize batched edges");
+        else if (ctx->hstate->error & kErrBadInput) st = set_error(ctx, BISIM_EINVAL, "a graph-local edge endpoint is out of range");
+    }
+    if (st == BISIM_OK)
+        st = build_from_coo(ctx, gsrc, gdst, static_cast<const int32_t*>(dl), s);
+    free_temps(temps, s);
+    if (deoff) cudaFreeAsync(deoff, s);
+    if (gsrc) cudaFreeAsync(gsrc, s);
+    if (gdst) cudaFreeAsync(gdst, s);
+    if (st == BISIM_OK && (st = finish_init(ctx, s)) == BISIM_OK) {
+        *out = ctx;
+        return BISIM_OK;
+    }
+    std::string msg = ctx->err;
+    destroy_ctx(ctx);
+    return set_error(nullptr, st, msg);
+}
+
+bisim_status bisim_iterate(bisim_ctx* ctx, int32_t k, int32_t cap, int32_t* out_rounds, int64_t* out_num_blocks,
+                           void* stream) {
+    if (ctx == nullptr) return set_error(nullptr, BISIM_EINVAL, "ctx is NULL");
+    if (k < BISIM_FIXPOINT) return set_error(ctx, BISIM_EINVAL, "k must be >= 0 or BISIM_FIXPOINT");
+    if (k == BISIM_FIXPOINT && cap < 0) return set_error(ctx, BISIM_EINVAL, "cap must be >= 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (ctx->n > 0)
+        cudaMemcpyAsync(ctx->P[0], ctx->P0, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToDevice, s);
+    ctx->cur = 0;
+    int64_t prev = ctx->last_blocks;
+    // ctx->last_blocks holds |P_0| after init; keep it for the next call
+    const int64_t p0_blocks = ctx->last_blocks;
+    const int32_t limit = (k == BISIM_FIXPOINT) ? cap : k;
+    int32_t rounds = limit, executed = 0;
+    for (int32_t i = 0; i < limit; ++i) {
+        int64_t blocks = 0;
+        bisim_status st = refine_round(ctx, s, &blocks);
+        if (st != BISIM_OK) return st;
+        ++executed;
+        if (blocks == prev) {   // P_{i+1} refines P_i with as many blocks: P_{i+1} = P_i
+            rounds = (k == BISIM_FIXPOINT) ? i : k;
+            break;
+        }
+        prev = blocks;
+    }
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "bisim_iterate");
+    ctx->last_blocks = p0_blocks;
+    ctx->stats.rounds = rounds;
+    ctx->stats.rounds_executed = executed;
+    ctx->stats.num_blocks = prev;
+    if (out_rounds) *out_rounds = rounds;
+    if (out_num_blocks) *out_num_blocks = prev;
+    return BISIM_OK;
+}
+
+bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, void* stream) {
+    (void)ops;
+    (void)n_ops;
+    (void)stream;
+    if (ctx == nullptr) return set_error(nullptr, BISIM_EINVAL, "ctx is NULL");
+    return set_error(ctx, BISIM_ESTATE, "apply_updates is not available in this build");
+}
+
+bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream) {
+    if (ctx == nullptr) return set_error(nullptr, BISIM_EINVAL, "ctx is NULL");
+    if (block == nullptr && ctx->n > 0) return set_error(ctx, BISIM_EINVAL, "output is NULL");
+    if (ctx->n == 0) return BISIM_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    const int32_t* src = ctx->P[ctx->cur];
+    if (ctx->gid != nullptr) {
+        int32_t* tmp = ctx->P[ctx->cur ^ 1];   // scratch: the other partition buffer
+        launch_local_ids(ctx, tmp, s);
+        src = tmp;
+    }
+    if ((e = cudaMemcpyAsync(block, src, sizeof(int32_t) * ctx->n, cudaMemcpyDefault, s)))
+        return cuda_error(ctx, e, "copy partition");
+    if (ctx->gid != nullptr) {
+        // the scratch buffer is the next round's output; make sure the copy is done first
+        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "copy partition");
+    }
+    return BISIM_OK;
+}
+
+bisim_status bisim_get_stats(const bisim_ctx* ctx, bisim_stats* out) {
+    if (ctx == nullptr || out == nullptr) return set_error(nullptr, BISIM_EINVAL, "NULL argument");
+    *out = ctx->stats;
+    return BISIM_OK;
+}
+
+bisim_status summarize_destroy(bisim_ctx* ctx) {
+    destroy_ctx(ctx);
+    return BISIM_OK;
+}
+
+const char* bisim_last_error(const bisim_ctx* ctx) {
+    if (ctx != nullptr) return ctx->err.empty() ? "no error" : ctx->err.c_str();
+    return g_last_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,242 @@
+// Internal declarations shared by the translation units of libbisim_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bisim.h"
+
+namespace bisim {
+
+// ----------------------------------------------------------------------------- constants
+
+constexpr int kSmallClasses = 4;          // thread-per-vertex classes: D = 4, 8, 16, 32
+constexpr int kMidClasses = 8;            // CTA-per-vertex classes: N = 64 .. 8192
+constexpr int kMidMaxN = 8192;            // largest CTA-path key count (64 KB of shared memory)
+constexpr int kClassHub = kSmallClasses + kMidClasses;   // 12
+constexpr int kNumClasses = kClassHub + 1;               // 13
+constexpr uint8_t kClassDead = 255;
+
+constexpr uint64_t kSaltKey = 0x243f6a8885a308d3ull;     // per-pair key -> m value
+constexpr uint64_t kSaltSig = 0x13198a2e03707344ull;     // own term of the signature hash
+constexpr uint64_t kSaltLabel = 0xa4093822299f31d0ull;   // label partition hash
+constexpr uint64_t kLevelStep = 0x9e3779b97f4a7c15ull;   // re-hash step of collision levels
+constexpr uint64_t kKey56 = 0x00ffffffffffffffull;
+
+// device error bits
+constexpr unsigned kErrTableFull = 1u;
+constexpr unsigned kErrHubFull = 2u;
+constexpr unsigned kErrBadInput = 4u;
+
+// ----------------------------------------------------------------------------- hashing
+
+// SplitMix64 output function (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014). A bijection on 64-bit words.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// The value stored for one (edge label, neighbour block) pair. mix64 is a
+// bijection, so a set of these values identifies the set of pairs exactly;
+// lists are kept sorted by this value, which gives every path the same
+// canonical order.
+__device__ __forceinline__ uint64_t pair_value(int32_t label, int32_t block) {
+    uint64_t key = (static_cast<uint64_t>(static_cast<uint32_t>(label)) << 32) |
+                   static_cast<uint32_t>(block);
+    return mix64(key ^ kSaltKey);
+}
+
+// Order-independent 64-bit hash of a signature (own block p, set S given by
+// its size c and the wrap-around sum of its pair values). Algorithm 4's Hash
+// is order independent too; the own block plays the role of its (self, id) tuple.
+__device__ __forceinline__ uint64_t sig_hash(int32_t p, uint32_t c, uint64_t sum) {
+    uint64_t h = mix64(((static_cast<uint64_t>(static_cast<uint32_t>(p)) << 32) | c) ^ kSaltSig);
+    return mix64(h + sum);
+}
+
+__device__ __forceinline__ uint64_t label_hash(int32_t g, int32_t label) {
+    uint64_t key = (static_cast<uint64_t>(static_cast<uint32_t>(g)) << 32) |
+                   static_cast<uint32_t>(label);
+    return mix64(key ^ kSaltLabel);
+}
+
+__device__ __forceinline__ uint64_t level_hash(uint64_t h0, uint32_t level, uint64_t hmask) {
+    uint64_t h = level == 0 ? h0 : mix64(h0 ^ (kLevelStep * level));
+    return h & hmask;
+}
+
+// ----------------------------------------------------------------------------- signature table
+
+// One slot of the open-addressing signature table. `key` holds the 8-bit epoch
+// in its top byte and the low 56 bits of the signature hash; a slot whose
+// epoch byte differs from the current one is free, so the table needs no
+// clearing between rounds. `minv` holds (~epoch32 << 32 | vertex); atomicMin
+// keeps the smallest vertex id of the current epoch and overrides stale ones.
+struct __align__(16) Slot {
+    unsigned long long key;
+    unsigned long long minv;
+};
+
+struct TableRef {
+    Slot* slots;
+    uint64_t mask;        // nslots - 1
+    uint64_t epoch8;      // 1..254, already shifted into bits 56..63
+    unsigned long long tag;  // (~epoch32) << 32
+    uint64_t hmask;       // hash width mask (tests only narrow it)
+};
+
+struct DevState {
+    unsigned long long blocks;      // vertices that are the minimum of their block
+    unsigned int unresolved;        // vertices pushed to the next collision level
+    unsigned int error;             // kErr* bits
+    unsigned long long aux;
+};
+
+// Insert `h` (already masked) for vertex v; returns the slot index or ~0u on overflow.
+__device__ __forceinline__ uint32_t table_insert(const TableRef& t, uint64_t h, int32_t v,
+                                                 unsigned* err) {
+    const unsigned long long want = t.epoch8 | (h & kKey56);
+    uint64_t pos = (h ^ (h >> 32)) & t.mask;
+    for (uint64_t probe = 0; probe <= t.mask; ++probe) {
+        unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&t.slots[pos].key);
+        while ((cur & ~kKey56) != t.epoch8) {          // stale: try to claim
+            unsigned long long prev = atomicCAS(&t.slots[pos].key, cur, want);
+            if (prev == cur) { cur = want; break; }
+            cur = prev;
+        }
+        if (cur == want) {
+            atomicMin(&t.slots[pos].minv, t.tag | static_cast<uint32_t>(v));
+            return static_cast<uint32_t>(pos);
+        }
+        pos = (pos + 1) & t.mask;
+    }
+    atomicOr(err, kErrTableFull);
+    return ~0u;
+}
+
+__device__ __forceinline__ int32_t table_rep(const Slot* slots, uint32_t pos) {
+    return static_cast<int32_t>(static_cast<uint32_t>(slots[pos].minv & 0xffffffffull));
+}
+
+// ----------------------------------------------------------------------------- hub tables
+
+// Per-hub dedup table of pair values (0 = empty; the pair value 0 is tracked by a flag).
+struct HubChunk {
+    int32_t hub;      // index into the hub list
+    int32_t vertex;
+    int64_t begin;    // edge range [begin, end)
+    int64_t end;
+};
+
+struct HubAcc {
+    unsigned long long sum;
+    unsigned int count;
+    unsigned int zero;
+};
+
+// ----------------------------------------------------------------------------- device buffer helper
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace bisim
+
+// ----------------------------------------------------------------------------- context
+
+struct bisim_ctx {
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t n_graphs = 1;
+    bisim_options opt{};
+    int device = 0;
+
+    // graph (out-CSR) -- owned
+    int64_t* row_ptr = nullptr;
+    int32_t* col = nullptr;
+    int32_t* elab = nullptr;
+    int32_t* vlabel = nullptr;
+    uint8_t* alive = nullptr;      // may be null: all live
+    int32_t* gid = nullptr;        // batched only
+    int64_t* voff = nullptr;       // batched only, [n_graphs+1]
+
+    // partition state
+    int32_t* P0 = nullptr;
+    int32_t* P[2] = {nullptr, nullptr};
+    int cur = 0;                   // P[cur] is the current partition
+    int32_t* cnt = nullptr;        // |S_v|
+    unsigned long long* skey = nullptr;   // sorted unique pair values, at row_ptr[v]
+    uint32_t* slot = nullptr;
+    bisim::Slot* table = nullptr;
+    uint64_t nslots = 0;
+    uint32_t epoch32 = 0;
+
+    // degree buckets
+    int32_t* class_list = nullptr;                 // vertices grouped by class
+    int64_t class_begin[bisim::kNumClasses + 1] = {};
+    int64_t class_edges[bisim::kNumClasses] = {};   // out-edges of the vertices of each class
+    int32_t* hub_list = nullptr;                   // = class_list + class_begin[kClassHub]
+    int64_t n_hub = 0;
+    int64_t* hub_toff = nullptr;                   // table offset per hub (in words)
+    uint32_t* hub_tmask = nullptr;                 // table size - 1 per hub
+    unsigned long long* hub_tab = nullptr;
+    int64_t hub_tab_words = 0;
+    bisim::HubChunk* chunks = nullptr;
+    int64_t n_chunks = 0;
+    bisim::HubAcc* hub_acc = nullptr;
+
+    // collision resolution
+    int32_t* ulist[2] = {nullptr, nullptr};
+    bisim::DevState* dstate = nullptr;
+    bisim::DevState* hstate = nullptr;   // pinned mirror
+
+    // bookkeeping
+    std::vector<void*> allocs;
+    int64_t device_bytes = 0;
+    bisim_stats stats{};
+    int64_t last_blocks = 0;
+    std::string err;
+};
+
+namespace bisim {
+
+// ----------------------------------------------------------------------------- host helpers (api.cu)
+
+bisim_status set_error(bisim_ctx* ctx, bisim_status st, const std::string& msg);
+bisim_status cuda_error(bisim_ctx* ctx, cudaError_t e, const char* what);
+cudaError_t ctx_alloc(bisim_ctx* ctx, void** p, size_t bytes, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- primitives (sort.cu)
+
+// Exclusive prefix sum of int64 values; `tmp` must hold scan_temp_words(n) words.
+size_t scan_temp_words(int64_t n);
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s);
+
+// Stable LSD radix sort of (u32 key, u64 value) pairs on the low `bits` key bits.
+// Buffers are ping-ponged; returns 0 if the result ended in (k0, v0), 1 if in (k1, v1).
+size_t radix_temp_words(int64_t m);
+int radix_sort_pairs(uint32_t* k0, uint64_t* v0, uint32_t* k1, uint64_t* v1, int64_t m, int bits,
+                     int64_t* tmp, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- graph build (graph.cu)
+
+bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* dst,
+                            const int32_t* elab, cudaStream_t s);
+bisim_status build_from_csr(bisim_ctx* ctx, const int64_t* row_ptr, const int32_t* col,
+                            const int32_t* elab, cudaStream_t s);
+bisim_status build_buckets(bisim_ctx* ctx, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- refinement (refine.cu)
+
+bisim_status compute_p0(bisim_ctx* ctx, cudaStream_t s);
+bisim_status refine_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks);
+bisim_status alloc_refine_state(bisim_ctx* ctx, cudaStream_t s);
+void launch_local_ids(const bisim_ctx* ctx, int32_t* out, cudaStream_t s);
+
+}  // namespace bisim

@@ -1,0 +1,34 @@
+// Launch accounting: a process-wide launch counter and optional event timing
+// per launch site (see bisim_profile_* in bisim.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace bisim {
+
+// Registers (once) and returns the index of a launch site.
+int prof_site(const char* name);
+
+// Brackets one kernel launch: counts it and, when profiling is enabled,
+// records events around it on stream `s`.
+class Launch {
+  public:
+    Launch(int site, cudaStream_t s, int64_t vertices, int64_t edges, double alg_bytes);
+    ~Launch();
+    Launch(const Launch&) = delete;
+    Launch& operator=(const Launch&) = delete;
+
+  private:
+    int site_;
+    cudaStream_t s_;
+    cudaEvent_t start_ = nullptr;
+    int64_t vertices_, edges_;
+    double bytes_;
+};
+
+}  // namespace bisim
+
+// Declares a function-local static site id and brackets the statement that follows.
+#define BISIM_SITE(var, name) static const int var = ::bisim::prof_site(name)

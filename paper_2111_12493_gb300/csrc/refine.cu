@@ -1,0 +1,639 @@
+// One refinement round of forward k-bisimulation (Algorithm 4, Section 3.3.1),
+// made exact.
+//
+// Per round i -> i+1 every live vertex v
+//   1. gathers the pairs (l, P_i[w]) of its out-edges (SignalMessages: a pull over
+//      the out-CSR instead of messages pushed along reversed edges),
+//   2. removes duplicates (MergeMessages) -- by sorting for small and mid
+//      degrees, by a per-hub hash set for hubs,
+//   3. hashes (P_i[v], set) order-independently (Hash, with the own block in the
+//      role of the paper's (self, old id) tuple),
+//   4. inserts the hash into an open-addressing table whose slots keep the
+//      smallest vertex id seen (FindAndMerge; canonical id = smallest member).
+// A verification pass then compares every vertex's full signature with that of
+// its block representative. Vertices whose signature differs (a hash
+// collision) move to the next "level", where only they are re-hashed with a
+// new salt; the group containing each level's smallest vertex is final, so
+// every level resolves at least one group per colliding hash and the loop ends
+// with the exact partition.
+#include <algorithm>
+
+#include "common.cuh"
+#include "prof.cuh"
+
+namespace bisim {
+
+namespace {
+
+constexpr int kMaxLevels = 1 << 16;
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+unsigned grid_for(int64_t n, int threads) {
+    return static_cast<unsigned>(std::max<int64_t>(1, cdiv(n, threads)));
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+// ----------------------------------------------------------------------------- views
+
+struct GraphView {
+    const int64_t* rp;
+    const int32_t* col;
+    const int32_t* elab;
+    const int32_t* P;        // P_i
+};
+
+struct HubView {
+    const int32_t* hub_list;   // ascending vertex ids
+    int64_t n_hub;
+    const int64_t* toff;
+    const uint32_t* tmask;
+    const unsigned long long* tab;
+    const HubAcc* acc;
+};
+
+__device__ __forceinline__ bool is_hub_degree(int64_t d, int small_max, int mid_max) {
+    return d > 0 && d > small_max && d > mid_max;
+}
+
+__device__ __forceinline__ int64_t hub_index(const HubView& H, int32_t v) {
+    int64_t lo = 0, hi = H.n_hub - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (H.hub_list[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool hub_contains(const HubView& H, int64_t h, unsigned long long mv) {
+    if (mv == 0ull) return H.acc[h].zero != 0u;
+    const unsigned long long* tab = H.tab + H.toff[h];
+    const uint32_t mask = H.tmask[h];
+    uint32_t pos = static_cast<uint32_t>(mv) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        unsigned long long cur = tab[pos];
+        if (cur == mv) return true;
+        if (cur == 0ull) return false;
+        pos = (pos + 1) & mask;
+    }
+    return false;
+}
+
+// Full signature of a vertex: (P_i[v], the set of its pair values).
+struct SigMode {
+    static constexpr const char* kVerifySite = "verify";
+    static constexpr double kVerifyBytesPerVertex = 20.0;   // slot 16 B read + P_{i+1} 4 B write
+    GraphView G;
+    const int32_t* cnt;
+    const unsigned long long* skey;
+    HubView H;
+    int small_max, mid_max;
+
+    __device__ uint64_t hash0(int32_t v) const {
+        const int32_t c = cnt[v];
+        const unsigned long long* l = skey + G.rp[v];
+        uint64_t sum = 0;
+        for (int32_t j = 0; j < c; ++j) sum += l[j];
+        return sig_hash(G.P[v], static_cast<uint32_t>(c), sum);
+    }
+
+    // Exact comparison. Non-hub lists are sorted by pair value, so equal sets
+    // are equal element by element; a hub's list is unordered, so the other
+    // list is looked up in the hub's dedup table instead.
+    __device__ bool equal(int32_t v, int32_t r) const {
+        if (G.P[v] != G.P[r]) return false;
+        const int32_t c = cnt[v];
+        if (c != cnt[r]) return false;
+        const int64_t bv = G.rp[v], br = G.rp[r];
+        const bool hv = is_hub_degree(G.rp[v + 1] - bv, small_max, mid_max);
+        const bool hr = is_hub_degree(G.rp[r + 1] - br, small_max, mid_max);
+        const unsigned long long* lv = skey + bv;
+        const unsigned long long* lr = skey + br;
+        if (!hv && !hr) {
+            for (int32_t j = 0; j < c; ++j)
+                if (lv[j] != lr[j]) return false;
+            return true;
+        }
+        const int64_t h = hub_index(H, hv ? v : r);
+        const unsigned long long* other = hv ? lr : lv;
+        for (int32_t j = 0; j < c; ++j)
+            if (!hub_contains(H, h, other[j])) return false;
+        return true;
+    }
+};
+
+// Label partition P_0: key (graph id, vertex label).
+struct LabelMode {
+    static constexpr const char* kVerifySite = "label_verify";
+    static constexpr double kVerifyBytesPerVertex = 20.0;
+    const int32_t* vlabel;
+    const int32_t* gid;   // may be null
+
+    __device__ uint64_t hash0(int32_t v) const { return label_hash(gid ? gid[v] : 0, vlabel[v]); }
+    __device__ bool equal(int32_t v, int32_t r) const {
+        return vlabel[v] == vlabel[r] && (gid == nullptr || gid[v] == gid[r]);
+    }
+};
+
+// ----------------------------------------------------------------------------- signature kernels
+
+template <int D>
+__device__ __forceinline__ void bitonic_regs(uint64_t (&s)[D]) {
+#pragma unroll
+    for (int k = 2; k <= D; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const uint64_t a = s[i], b = s[l];
+                    const bool sw = up ? (a > b) : (a < b);
+                    s[i] = sw ? b : a;
+                    s[l] = sw ? a : b;
+                }
+            }
+        }
+    }
+}
+
+// One thread per vertex of out-degree <= D: the pairs live in registers and
+// are sorted by a bitonic network.
+template <int D>
+__global__ void __launch_bounds__(128) k_sig_small(const int32_t* __restrict__ list, int64_t count,
+                                                   GraphView G, int32_t* __restrict__ cnt,
+                                                   unsigned long long* __restrict__ skey,
+                                                   uint32_t* __restrict__ slot, TableRef t,
+                                                   unsigned* err) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int32_t v = list[i];
+    const int64_t b = G.rp[v];
+    const int d = static_cast<int>(G.rp[v + 1] - b);
+    uint64_t s[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        if (j < d) {
+            const int32_t w = __ldcs(G.col + b + j);
+            const int32_t l = __ldcs(G.elab + b + j);
+            s[j] = pair_value(l, __ldg(G.P + w));
+        } else {
+            s[j] = ~0ull;
+        }
+    }
+    bitonic_regs<D>(s);
+    uint32_t u = 0;
+    uint64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        if (j < d && (j == 0 || s[j] != s[j - 1])) {
+            skey[b + u] = s[j];
+            sum += s[j];
+            ++u;
+        }
+    }
+    cnt[v] = static_cast<int32_t>(u);
+    const uint64_t h = sig_hash(G.P[v], u, sum) & t.hmask;
+    slot[v] = table_insert(t, h, v, err);
+}
+
+// One CTA of T threads per vertex of out-degree <= N: pairs staged in shared
+// memory, bitonic sort, then duplicate removal and compaction by a block scan.
+template <int N, int T>
+__global__ void __launch_bounds__(T) k_sig_mid(const int32_t* __restrict__ list, GraphView G,
+                                               int32_t* __restrict__ cnt,
+                                               unsigned long long* __restrict__ skey,
+                                               uint32_t* __restrict__ slot, TableRef t,
+                                               unsigned* err) {
+    extern __shared__ unsigned long long sm[];
+    __shared__ unsigned wc[T / 32];
+    __shared__ unsigned long long ws[T / 32];
+    constexpr int E = N / T;
+    static_assert(E >= 1 && N % T == 0, "tile shape");
+    const int32_t v = list[blockIdx.x];
+    const int64_t b = G.rp[v];
+    const int d = static_cast<int>(G.rp[v + 1] - b);
+    for (int j = threadIdx.x; j < N; j += T) {
+        if (j < d) {
+            const int32_t w = __ldcs(G.col + b + j);
+            const int32_t l = __ldcs(G.elab + b + j);
+            sm[j] = pair_value(l, __ldg(G.P + w));
+        } else {
+            sm[j] = ~0ull;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < N / 2; i += T) {
+                const int lo = 2 * i - (i & (j - 1));
+                const int hi = lo + j;
+                const bool up = (lo & k) == 0;
+                const unsigned long long a = sm[lo], c = sm[hi];
+                if ((a > c) == up) {
+                    sm[lo] = c;
+                    sm[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // each thread owns E consecutive sorted positions
+    const int base = threadIdx.x * E;
+    unsigned myc = 0;
+    unsigned long long mys = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int j = base + e;
+        if (j < d && (j == 0 || sm[j] != sm[j - 1])) {
+            ++myc;
+            mys += sm[j];
+        }
+    }
+    // block-wide exclusive scan of myc and reduction of mys
+    unsigned inc = myc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane_id() >= static_cast<unsigned>(o)) inc += y;
+    }
+    unsigned long long wsum = mys;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    const int warp = threadIdx.x >> 5;
+    if (lane_id() == 31) wc[warp] = inc;
+    if (lane_id() == 0) ws[warp] = wsum;
+    __syncthreads();
+    unsigned before = 0, total = 0;
+    unsigned long long tsum = 0;
+#pragma unroll
+    for (int w = 0; w < T / 32; ++w) {
+        if (w < warp) before += wc[w];
+        total += wc[w];
+        tsum += ws[w];
+    }
+    unsigned pos = before + inc - myc;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int j = base + e;
+        if (j < d && (j == 0 || sm[j] != sm[j - 1])) skey[b + pos++] = sm[j];
+    }
+    if (threadIdx.x == 0) {
+        cnt[v] = static_cast<int32_t>(total);
+        const uint64_t h = sig_hash(G.P[v], total, tsum) & t.hmask;
+        slot[v] = table_insert(t, h, v, err);
+    }
+}
+
+// Hub path, phase 1: every CTA dedups one chunk of a hub's edges into the hub's
+// global hash set; first inserters append their value to the hub's list and
+// add it to the hub's order-independent sum.
+__global__ void __launch_bounds__(256) k_hub_insert(const HubChunk* __restrict__ chunks, GraphView G,
+                                                    const int64_t* __restrict__ toff,
+                                                    const uint32_t* __restrict__ tmask,
+                                                    unsigned long long* __restrict__ tab_all,
+                                                    HubAcc* __restrict__ acc,
+                                                    unsigned long long* __restrict__ skey,
+                                                    unsigned* err) {
+    __shared__ unsigned long long red[8];
+    const HubChunk c = chunks[blockIdx.x];
+    unsigned long long* tab = tab_all + toff[c.hub];
+    const uint32_t mask = tmask[c.hub];
+    const int64_t row = G.rp[c.vertex];
+    unsigned long long lsum = 0;
+    for (int64_t e0 = c.begin; e0 < c.end; e0 += blockDim.x) {
+        const int64_t e = e0 + threadIdx.x;
+        bool fresh = false;
+        unsigned long long mv = 0;
+        if (e < c.end) {
+            const int32_t w = __ldcs(G.col + e);
+            const int32_t l = __ldcs(G.elab + e);
+            mv = pair_value(l, __ldg(G.P + w));
+            if (mv == 0ull) {
+                fresh = atomicOr(&acc[c.hub].zero, 1u) == 0u;
+            } else {
+                uint32_t pos = static_cast<uint32_t>(mv) & mask;
+                uint32_t probe = 0;
+                for (; probe <= mask; ++probe) {
+                    unsigned long long cur = tab[pos];
+                    if (cur == mv) break;
+                    if (cur == 0ull) {
+                        unsigned long long prev = atomicCAS(&tab[pos], 0ull, mv);
+                        if (prev == 0ull) { fresh = true; break; }
+                        if (prev == mv) break;
+                    }
+                    pos = (pos + 1) & mask;
+                }
+                if (probe > mask) atomicOr(err, kErrHubFull);
+            }
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, fresh);
+        if (ball) {
+            const int leader = __ffs(ball) - 1;
+            unsigned base = 0;
+            if (static_cast<int>(lane_id()) == leader) base = atomicAdd(&acc[c.hub].count, __popc(ball));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (fresh) {
+                skey[row + base + __popc(ball & lanemask_lt())] = mv;
+                lsum += mv;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane_id() == 0) red[threadIdx.x >> 5] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += red[w];
+        atomicAdd(&acc[c.hub].sum, s);
+    }
+}
+
+// Hub path, phase 2: one thread per hub finishes its signature and inserts it.
+__global__ void k_hub_finalize(const int32_t* __restrict__ hubs, int64_t nh, GraphView G,
+                               const HubAcc* __restrict__ acc, int32_t* __restrict__ cnt,
+                               uint32_t* __restrict__ slot, TableRef t, unsigned* err) {
+    const int64_t h = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (h >= nh) return;
+    const int32_t v = hubs[h];
+    const unsigned c = acc[h].count;
+    cnt[v] = static_cast<int32_t>(c);
+    const uint64_t hv = sig_hash(G.P[v], c, acc[h].sum) & t.hmask;
+    slot[v] = table_insert(t, hv, v, err);
+}
+
+// ----------------------------------------------------------------------------- resolution
+
+// Insert level-`level` hashes for every live vertex (list == null) or for the
+// listed ones.
+template <class Mode>
+__global__ void k_resolve_insert(const int32_t* __restrict__ list, int64_t count,
+                                 const uint8_t* __restrict__ alive, Mode M, uint32_t level,
+                                 uint32_t* __restrict__ slot, TableRef t, unsigned* err) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int32_t v = list ? list[i] : static_cast<int32_t>(i);
+    if (!list && alive && !alive[v]) return;
+    const uint64_t h = level_hash(M.hash0(v), level, t.hmask);
+    slot[v] = table_insert(t, h, v, err);
+}
+
+// Confirm each vertex against its slot's smallest vertex. Equal: that vertex is
+// its block id. Different: queue it for the next level.
+template <class Mode>
+__global__ void k_resolve_verify(const int32_t* __restrict__ list, int64_t count,
+                                 const uint8_t* __restrict__ alive, Mode M,
+                                 const uint32_t* __restrict__ slot, const Slot* __restrict__ slots,
+                                 int32_t* __restrict__ Pout, int32_t* __restrict__ next,
+                                 DevState* st, int32_t n_total) {
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x;
+    const int64_t i = i0 + threadIdx.x;
+    bool is_block = false, push = false;
+    int32_t v = -1;
+    if (i < count) {
+        v = list ? list[i] : static_cast<int32_t>(i);
+        if (!list && alive && !alive[v]) {
+            Pout[v] = -1;
+        } else {
+            const uint32_t sv = slot[v];
+            const int32_t r = sv == ~0u ? -1 : table_rep(slots, sv);
+            if (r < 0 || r >= n_total) {          // failed insert: reported through st->error
+                atomicOr(&st->error, kErrTableFull);
+                Pout[v] = -1;
+            } else if (r == v) {
+                Pout[v] = v;
+                is_block = true;
+            } else if (M.equal(v, r)) {
+                Pout[v] = r;
+            } else {
+                push = true;
+            }
+        }
+    }
+    const unsigned bb = __ballot_sync(0xffffffffu, is_block);
+    if (bb && lane_id() == static_cast<unsigned>(__ffs(bb) - 1))
+        atomicAdd(&st->blocks, static_cast<unsigned long long>(__popc(bb)));
+    const unsigned pb = __ballot_sync(0xffffffffu, push);
+    if (pb) {
+        const int leader = __ffs(pb) - 1;
+        unsigned base = 0;
+        if (static_cast<int>(lane_id()) == leader) base = atomicAdd(&st->unresolved, __popc(pb));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (push) next[base + __popc(pb & lanemask_lt())] = v;
+    }
+}
+
+__global__ void k_local_ids(const int32_t* __restrict__ P, const int32_t* __restrict__ gid,
+                            const int64_t* __restrict__ voff, int32_t n, int32_t* __restrict__ out) {
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t p = P[v];
+    out[v] = p < 0 ? -1 : static_cast<int32_t>(p - voff[gid[v]]);
+}
+
+// ----------------------------------------------------------------------------- host side
+
+TableRef next_epoch(bisim_ctx* ctx, cudaStream_t s) {
+    ctx->epoch32 += 1;
+    const uint32_t e8 = ((ctx->epoch32 - 1) % 254u) + 1u;
+    if (ctx->epoch32 > 1 && e8 == 1)   // the 8-bit tag wrapped: start from a blank table
+        cudaMemsetAsync(ctx->table, 0xff, sizeof(Slot) * ctx->nslots, s);
+    TableRef t;
+    t.slots = ctx->table;
+    t.mask = ctx->nslots - 1;
+    t.epoch8 = static_cast<uint64_t>(e8) << 56;
+    t.tag = static_cast<unsigned long long>(~ctx->epoch32) << 32;
+    const int hb = ctx->opt.hash_bits;
+    t.hmask = hb >= 64 ? ~0ull : ((1ull << hb) - 1ull);
+    return t;
+}
+
+template <class Mode>
+bisim_status resolve(bisim_ctx* ctx, Mode M, int32_t* Pout, cudaStream_t s, int64_t* blocks) {
+    const int32_t n = ctx->n;
+    cudaError_t e;
+    cudaMemsetAsync(ctx->dstate, 0, sizeof(DevState), s);
+    if (n > 0) {
+        BISIM_SITE(site, Mode::kVerifySite);
+        Launch L(site, s, n, 0, Mode::kVerifyBytesPerVertex * n);
+        k_resolve_verify<Mode><<<grid_for(n, 256), 256, 0, s>>>(nullptr, n, ctx->alive, M, ctx->slot,
+                                                                ctx->table, Pout, ctx->ulist[0], ctx->dstate, n);
+    }
+    cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "verify signatures");
+    int which = 0;
+    uint32_t level = 0;
+    while (ctx->hstate->error == 0 && ctx->hstate->unresolved > 0) {
+        if (++level > static_cast<uint32_t>(kMaxLevels))
+            return set_error(ctx, BISIM_ETIMEOUT, "hash collision resolution did not converge");
+        const int64_t cu = ctx->hstate->unresolved;
+        TableRef t = next_epoch(ctx, s);
+        cudaMemsetAsync(&ctx->dstate->unresolved, 0, sizeof(unsigned), s);
+        BISIM_SITE(site_i, "collision_insert");
+        BISIM_SITE(site_v, "collision_verify");
+        {
+            Launch L(site_i, s, cu, 0, 0.0);
+            k_resolve_insert<Mode><<<grid_for(cu, 256), 256, 0, s>>>(ctx->ulist[which], cu, ctx->alive, M, level,
+                                                                      ctx->slot, t, &ctx->dstate->error);
+        }
+        {
+            Launch L(site_v, s, cu, 0, 0.0);
+            k_resolve_verify<Mode><<<grid_for(cu, 256), 256, 0, s>>>(ctx->ulist[which], cu, ctx->alive, M, ctx->slot,
+                                                                      ctx->table, Pout, ctx->ulist[which ^ 1],
+                                                                      ctx->dstate, n);
+        }
+        cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "resolve hash collisions");
+        which ^= 1;
+        ctx->stats.collision_levels += 1;
+    }
+    if (ctx->hstate->error & kErrTableFull) return set_error(ctx, BISIM_ETIMEOUT, "signature table probe limit reached");
+    if (ctx->hstate->error & kErrHubFull) return set_error(ctx, BISIM_ETIMEOUT, "hub dedup table probe limit reached");
+    if (ctx->hstate->error) return set_error(ctx, BISIM_EINVAL, "device reported invalid input");
+    *blocks = static_cast<int64_t>(ctx->hstate->blocks);
+    return BISIM_OK;
+}
+
+// Algorithmic bytes of the signature kernels: per edge col 4 + label 4 + the
+// gathered P_i[w] 4; per vertex row_ptr 4 + P_i[v] 4 + one 16-byte table slot.
+constexpr double kSigBytesPerEdge = 12.0;
+constexpr double kSigBytesPerVertex = 24.0;
+
+constexpr int mid_class_of(int N) {
+    return N == 64 ? 0 : N == 128 ? 1 : N == 256 ? 2 : N == 512 ? 3 : N == 1024 ? 4 : N == 2048 ? 5 : N == 4096 ? 6 : 7;
+}
+
+template <int N>
+void launch_mid(bisim_ctx* ctx, const int32_t* list, int64_t count, GraphView G, TableRef t, cudaStream_t s) {
+    constexpr int T = N / 2 < 512 ? N / 2 : 512;
+    const size_t smem = sizeof(unsigned long long) * N;
+    static bool attr_set = false;   // per process; the attribute belongs to the function
+    if (!attr_set && smem > 48 * 1024) {
+        cudaFuncSetAttribute(k_sig_mid<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        attr_set = true;
+    }
+    static const int site = prof_site(N == 64 ? "sig_mid_64" : N == 128 ? "sig_mid_128" : N == 256 ? "sig_mid_256"
+                                      : N == 512 ? "sig_mid_512" : N == 1024 ? "sig_mid_1024" : N == 2048 ? "sig_mid_2048"
+                                      : N == 4096 ? "sig_mid_4096" : "sig_mid_8192");
+    const int64_t edges = ctx->class_edges[kSmallClasses + mid_class_of(N)];
+    Launch L(site, s, count, edges, kSigBytesPerEdge * edges + kSigBytesPerVertex * count);
+    k_sig_mid<N, T><<<static_cast<unsigned>(count), T, smem, s>>>(list, G, ctx->cnt, ctx->skey, ctx->slot, t,
+                                                                  &ctx->dstate->error);
+}
+
+}  // namespace
+
+bisim_status alloc_refine_state(bisim_ctx* ctx, cudaStream_t s) {
+    const int32_t n = ctx->n;
+    const int64_t m = ctx->m;
+    cudaError_t e;
+    const size_t nv = static_cast<size_t>(std::max(n, 1));
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->P0), sizeof(int32_t) * nv, s))) return cuda_error(ctx, e, "alloc P0");
+    for (int i = 0; i < 2; ++i)
+        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->P[i]), sizeof(int32_t) * nv, s))) return cuda_error(ctx, e, "alloc P");
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->cnt), sizeof(int32_t) * nv, s))) return cuda_error(ctx, e, "alloc cnt");
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->slot), sizeof(uint32_t) * nv, s))) return cuda_error(ctx, e, "alloc slot");
+    for (int i = 0; i < 2; ++i)
+        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ulist[i]), sizeof(int32_t) * nv, s))) return cuda_error(ctx, e, "alloc unresolved list");
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->skey), sizeof(unsigned long long) * std::max<int64_t>(m, 1), s))) return cuda_error(ctx, e, "alloc signature lists");
+    uint64_t ns = 1024;
+    while (ns < 2ull * static_cast<uint64_t>(n)) ns <<= 1;
+    ctx->nslots = ns;
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->table), sizeof(Slot) * ns, s))) return cuda_error(ctx, e, "alloc signature table");
+    cudaMemsetAsync(ctx->table, 0xff, sizeof(Slot) * ns, s);
+    if (ctx->hub_tab) cudaMemsetAsync(ctx->hub_tab, 0, sizeof(unsigned long long) * ctx->hub_tab_words, s);
+    if ((e = cudaGetLastError())) return cuda_error(ctx, e, "init refine state");
+    return BISIM_OK;
+}
+
+bisim_status compute_p0(bisim_ctx* ctx, cudaStream_t s) {
+    TableRef t = next_epoch(ctx, s);
+    LabelMode M{ctx->vlabel, ctx->gid};
+    if (ctx->n > 0) {
+        BISIM_SITE(site, "label_insert");
+        Launch L(site, s, ctx->n, 0, 20.0 * ctx->n);   // label 4 B + one 16-byte table slot
+        k_resolve_insert<LabelMode><<<grid_for(ctx->n, 256), 256, 0, s>>>(nullptr, ctx->n, ctx->alive, M, 0u,
+                                                                          ctx->slot, t, &ctx->dstate->error);
+    }
+    int64_t blocks = 0;
+    bisim_status st = resolve(ctx, M, ctx->P0, s, &blocks);
+    if (st != BISIM_OK) return st;
+    ctx->last_blocks = blocks;
+    ctx->stats.num_blocks = blocks;
+    return BISIM_OK;
+}
+
+bisim_status refine_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
+    const int32_t* P = ctx->P[ctx->cur];
+    int32_t* Pn = ctx->P[ctx->cur ^ 1];
+    GraphView G{ctx->row_ptr, ctx->col, ctx->elab, P};
+    TableRef t = next_epoch(ctx, s);
+    if (ctx->n_hub > 0) {
+        cudaMemsetAsync(ctx->hub_tab, 0, sizeof(unsigned long long) * ctx->hub_tab_words, s);
+        cudaMemsetAsync(ctx->hub_acc, 0, sizeof(HubAcc) * ctx->n_hub, s);
+    }
+    const int64_t* cb = ctx->class_begin;
+    unsigned* err = &ctx->dstate->error;
+    static const int small_site[kSmallClasses] = {prof_site("sig_small_4"), prof_site("sig_small_8"),
+                                                   prof_site("sig_small_16"), prof_site("sig_small_32")};
+    auto small = [&](int c, auto kern) {
+        const int64_t cnt = cb[c + 1] - cb[c];
+        if (cnt > 0) {
+            const int64_t edges = ctx->class_edges[c];
+            Launch L(small_site[c], s, cnt, edges, kSigBytesPerEdge * edges + kSigBytesPerVertex * cnt);
+            kern<<<grid_for(cnt, 128), 128, 0, s>>>(ctx->class_list + cb[c], cnt, G, ctx->cnt, ctx->skey,
+                                                   ctx->slot, t, err);
+        }
+    };
+    small(0, k_sig_small<4>);
+    small(1, k_sig_small<8>);
+    small(2, k_sig_small<16>);
+    small(3, k_sig_small<32>);
+    auto mid = [&](int c) { return std::make_pair(ctx->class_list + cb[kSmallClasses + c], cb[kSmallClasses + c + 1] - cb[kSmallClasses + c]); };
+    { auto [l, c] = mid(0); if (c > 0) launch_mid<64>(ctx, l, c, G, t, s); }
+    { auto [l, c] = mid(1); if (c > 0) launch_mid<128>(ctx, l, c, G, t, s); }
+    { auto [l, c] = mid(2); if (c > 0) launch_mid<256>(ctx, l, c, G, t, s); }
+    { auto [l, c] = mid(3); if (c > 0) launch_mid<512>(ctx, l, c, G, t, s); }
+    { auto [l, c] = mid(4); if (c > 0) launch_mid<1024>(ctx, l, c, G, t, s); }
+    { auto [l, c] = mid(5); if (c > 0) launch_mid<2048>(ctx, l, c, G, t, s); }
+    { auto [l, c] = mid(6); if (c > 0) launch_mid<4096>(ctx, l, c, G, t, s); }
+    { auto [l, c] = mid(7); if (c > 0) launch_mid<8192>(ctx, l, c, G, t, s); }
+    if (ctx->n_chunks > 0) {
+        BISIM_SITE(site_hi, "hub_insert");
+        BISIM_SITE(site_hf, "hub_finalize");
+        const int64_t hub_edges = ctx->class_edges[kClassHub];
+        {
+            Launch L1(site_hi, s, 0, hub_edges, kSigBytesPerEdge * hub_edges);
+            k_hub_insert<<<static_cast<unsigned>(ctx->n_chunks), 256, 0, s>>>(ctx->chunks, G, ctx->hub_toff, ctx->hub_tmask,
+                                                                             ctx->hub_tab, ctx->hub_acc, ctx->skey, err);
+        }
+        Launch L2(site_hf, s, ctx->n_hub, 0, kSigBytesPerVertex * ctx->n_hub);
+        k_hub_finalize<<<grid_for(ctx->n_hub, 128), 128, 0, s>>>(ctx->hub_list, ctx->n_hub, G, ctx->hub_acc,
+                                                                ctx->cnt, ctx->slot, t, err);
+    }
+    cudaError_t e;
+    if ((e = cudaGetLastError())) return cuda_error(ctx, e, "launch signature kernels");
+    SigMode M;
+    M.G = G;
+    M.cnt = ctx->cnt;
+    M.skey = ctx->skey;
+    M.H = HubView{ctx->hub_list, ctx->n_hub, ctx->hub_toff, ctx->hub_tmask, ctx->hub_tab, ctx->hub_acc};
+    M.small_max = ctx->opt.small_max_degree;
+    M.mid_max = ctx->opt.mid_max_degree;
+    bisim_status st = resolve(ctx, M, Pn, s, out_blocks);
+    if (st != BISIM_OK) return st;
+    ctx->cur ^= 1;
+    return BISIM_OK;
+}
+
+void launch_local_ids(const bisim_ctx* ctx, int32_t* out, cudaStream_t s) {
+    BISIM_SITE(site, "local_ids");
+    Launch L(site, s, ctx->n, 0, 8.0 * ctx->n);
+    if (ctx->n > 0)
+        k_local_ids<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->P[ctx->cur], ctx->gid, ctx->voff, ctx->n, out);
+}
+
+}  // namespace bisim

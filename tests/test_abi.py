@@ -1,0 +1,56 @@
+"""The C-ABI library loads without a GPU and exports every entry point of include/bisim.h."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bisim.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^(?:bisim_status|void|const char\*)\s+(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("summarize_init", "summarize_init_coo", "summarize_init_batched", "bisim_iterate",
+                     "apply_updates", "get_partition", "summarize_destroy", "bisim_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2111_12493_gb300 import build
+    try:
+        path = build.build()
+    except RuntimeError as e:  # no CUDA toolkit on this machine
+        pytest.skip(str(e))
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_options_without_gpu():
+    from paper_2111_12493_gb300 import build
+    try:
+        path = build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    lib = ctypes.CDLL(path)
+
+    class Options(ctypes.Structure):
+        _fields_ = [("k_incremental", ctypes.c_int32), ("hash_bits", ctypes.c_int32),
+                    ("small_max_degree", ctypes.c_int32), ("mid_max_degree", ctypes.c_int32),
+                    ("hub_chunk", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                    ("mem_budget_bytes", ctypes.c_int64)]
+
+    o = Options()
+    lib.bisim_default_options(ctypes.byref(o))
+    assert (o.k_incremental, o.hash_bits, o.small_max_degree, o.mid_max_degree) == (2, 64, 32, 8192)
+    lib.bisim_last_error.restype = ctypes.c_char_p
+    assert lib.bisim_last_error(None) is not None
