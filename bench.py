@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Throughput of exact k-bisimulation refinement on one GB300.
+
+Workload: the power-law graph with 10M vertices and 100M edges (out-degree
+exponent 2.1 capped at 1M, targets preferential by in-degree, 1000 Zipf edge
+labels, 200 Zipf vertex labels, 10% untyped), refined to the fixpoint with a
+cap of 10 rounds. One step is one pass of the whole path over that graph:
+summarize_init_coo (CSR build by radix sort, label partition), bisim_iterate
+(refinement rounds until the block count stops changing, at most 10) and
+get_partition, through the C-ABI.
+
+  value  = edges x rounds executed / step time, COO already resident in HBM
+  e2e    = the same metric with the COO and labels in pinned host memory and
+           the partition copied back to pinned host memory inside the timed region
+  roofline = the kernel with the largest event-timed share of the timed steps:
+           its algorithmic bytes / its summed launch time, against the measured
+           HBM copy bandwidth
+
+--impl reference times the CPU oracle (exact signatures in an ordered map)
+on a bounded sample of the same workload. --gpus N > 1 runs N independent
+replicas (the refinement of one graph has no sharded form here), one per rank.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "k-bisim edge-iterations/sec (1 GB300, bit-exact); update-batch p50/p99 latency"
+UNIT = "edge-iterations/s"
+WORKLOAD = dict(n=10_000_000, m=100_000_000, exponent=2.1, dmax=1_000_000, n_elabels=1000, n_vlabels=200,
+                untyped=0.1, k="fixpoint", cap=10, seed=2)
+# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel from one ncu capture; None until captured for the current kernel.
+NCU_TRAFFIC_BYTES = {}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (smoke runs only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_graph(scale):
+    from paper_2111_12493_gb300 import graphgen
+    n = max(1000, int(WORKLOAD["n"] * scale))
+    m = max(10_000, int(WORKLOAD["m"] * scale))
+    return graphgen.powerlaw_graph(n=n, m=m, exponent=WORKLOAD["exponent"], dmax=min(WORKLOAD["dmax"], m // 10),
+                                   n_elabels=WORKLOAD["n_elabels"], n_vlabels=WORKLOAD["n_vlabels"],
+                                   untyped_frac=WORKLOAD["untyped"], seed=WORKLOAD["seed"])
+
+
+def config_dict(n, m, g=None, extra=None):
+    d = {"workload": f"power-law digraph {n:,} vertices / {m:,} edges, out-degree exponent 2.1 (max 1M), "
+                     f"copy-model targets, 1000 Zipf(1.1) edge labels, 200 Zipf(1.0) vertex labels + 10% untyped; "
+                     f"refine to the fixpoint, cap 10 rounds",
+         "n_vertices": int(n), "n_edges": int(m), "k": "fixpoint", "cap": 10,
+         "l2": "inputs larger than L2 (COO 1.2 GB, CSR 0.8 GB)"}
+    if g is not None:
+        d["max_out_degree"] = int(np.bincount(g["src"], minlength=g["n"]).max())
+        d["max_in_degree"] = int(np.bincount(g["dst"], minlength=g["n"]).max())
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ----------------------------------------------------------------------------- distributed plumbing
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, x):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2111_12493_gb300 import bisim
+
+    g = workload_graph(args.scale)
+    n, m = g["n"], len(g["src"])
+    dev = torch.device("cuda", local)
+    d_src, d_dst, d_lab, d_vl = (torch.from_numpy(g[k]).to(dev) for k in ("src", "dst", "elabel", "vlabel"))
+    d_out = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(src, dst, lab, vl, out):
+        ctx = bisim.summarize_init_coo(n, src, dst, lab, vl)
+        rounds, blocks = bisim.bisim_iterate(ctx, bisim.FIXPOINT, WORKLOAD["cap"])
+        bisim.get_partition(ctx, out=out)
+        executed = bisim.bisim_get_stats(ctx)["rounds_executed"]
+        bisim.summarize_destroy(ctx)
+        return rounds, blocks, executed
+
+    for _ in range(args.warmup):
+        rounds, blocks, executed = step(d_src, d_dst, d_lab, d_vl, d_out)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, inputs resident in HBM
+    clocks = ClockSampler(local)
+    bisim.bisim_profile_reset()
+    bisim.bisim_profile_enable(True)
+    launches0 = bisim.bisim_launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    edge_iters = 0
+    for _ in range(args.steps):
+        rounds, blocks, executed = step(d_src, d_dst, d_lab, d_vl, d_out)
+        edge_iters += m * executed
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clock_info = clocks.stop()
+    launches = bisim.bisim_launch_count() - launches0
+    bisim.bisim_profile_enable(False)
+    prof = bisim.bisim_profile_read()
+    t_ms = max_over_ranks(world, ev0.elapsed_time(ev1))
+    total_edge_iters = sum_over_ranks(world, edge_iters)
+    value = total_edge_iters / (t_ms / 1e3)
+
+    # iterate-only throughput (CSR already built), one more untimed-for-value run
+    ctx = bisim.summarize_init_coo(n, d_src, d_dst, d_lab, d_vl)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r2, _ = bisim.bisim_iterate(ctx, bisim.FIXPOINT, WORKLOAD["cap"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    it_exec = bisim.bisim_get_stats(ctx)["rounds_executed"]
+    iterate_only = m * it_exec / (e0.elapsed_time(e1) / 1e3)
+    stats = bisim.bisim_get_stats(ctx)
+    bisim.summarize_destroy(ctx)
+
+    # sanity of the result that was timed: canonical ids (block id = its smallest member)
+    P = d_out.cpu().numpy()
+    assert (P >= 0).all() and (P <= np.arange(n)).all() and (P[P] == P).all(), "non-canonical partition"
+    assert len(np.unique(P)) == blocks
+
+    # end to end through the C-ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_src, h_dst, h_lab, h_vl = (torch.from_numpy(g[k]).pin_memory() for k in ("src", "dst", "elabel", "vlabel"))
+        h_out = torch.empty(n, dtype=torch.int32).pin_memory()
+        step(h_src, h_dst, h_lab, h_vl, h_out)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        ei = 0
+        for _ in range(args.steps):
+            _, _, ex = step(h_src, h_dst, h_lab, h_vl, h_out)
+            torch.cuda.synchronize()           # the partition is in host memory now
+            ei += m * ex
+        f1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        e_ms = max_over_ranks(world, max(f0.elapsed_time(f1), wall * 1e3))
+        assert np.array_equal(h_out.numpy(), P), "host-buffer run differs from the device run"
+        e2e = {"value": sum_over_ranks(world, ei) / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(4 * (3 * m + n)), "d2h_bytes_per_step": int(4 * n)}
+
+    # roofline of the dominant kernel (largest event-timed share of the timed steps)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    total_kernel_ms = sum(p["total_ms"] for p in prof)
+    top = max(prof, key=lambda p: p["total_ms"]) if prof else None
+    roofline = None
+    kernels = None
+    if top and top["total_ms"] > 0:
+        achieved = top["alg_bytes"] / (top["total_ms"] / 1e3) / 1e9
+        traffic = NCU_TRAFFIC_BYTES.get(top["name"])
+        roofline = {"bound": "hbm", "kernel": top["name"], "achieved": round(achieved, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                    "traffic": traffic, "alg_bytes_per_launch": top["alg_bytes"] / max(1, top["launches"]),
+                    "avg_launch_ms": top["total_ms"] / max(1, top["launches"]),
+                    "share_of_kernel_time": round(top["total_ms"] / total_kernel_ms, 4)}
+        kernels = sorted(({"name": p["name"], "launches": p["launches"], "ms": round(p["total_ms"], 3),
+                           "share": round(p["total_ms"] / total_kernel_ms, 4),
+                           "GB/s": round(p["alg_bytes"] / (p["total_ms"] / 1e3) / 1e9, 1) if p["total_ms"] else None}
+                          for p in prof if p["launches"]), key=lambda x: -x["ms"])[:12]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.scale)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32 ids, u64 hashes (integer only)",
+            "data": "synthetic (seeded generator; stands in for the paper's BSBM/DyLDO graphs)",
+            "config": config_dict(n, m, g, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                      "rounds": int(rounds), "rounds_executed": int(executed),
+                                      "blocks": int(blocks)}),
+            "iterate_only": {"value": iterate_only, "unit": UNIT, "rounds_executed": int(it_exec)},
+            "e2e": e2e, "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu,
+            "gpu_launches": int(launches), "clocks": clock_info,
+            "buckets": {"small": stats["n_small"], "mid": stats["n_mid"], "hub": stats["n_hub"]},
+            "collision_levels": stats["collision_levels"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- oracle on the host cores
+
+def cpu_sample_graph(scale):
+    from paper_2111_12493_gb300 import graphgen
+    # a quarter-size instance of the same generator: one oracle round takes ~10 s
+    n = max(1000, int(2_500_000 * scale))
+    m = max(10_000, int(25_000_000 * scale))
+    return graphgen.powerlaw_graph(n=n, m=m, exponent=WORKLOAD["exponent"], dmax=min(WORKLOAD["dmax"], m // 10),
+                                   n_elabels=WORKLOAD["n_elabels"], n_vlabels=WORKLOAD["n_vlabels"],
+                                   untyped_frac=WORKLOAD["untyped"], seed=WORKLOAD["seed"])
+
+
+def time_oracle_round(g):
+    import oracle
+    P0 = oracle.label_partition(g["n"], g["vlabel"])
+    t0 = time.perf_counter()
+    oracle.refine_round(g["n"], g["src"], g["dst"], g["elabel"], g["vlabel"], P0)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(scale):
+    g = cpu_sample_graph(scale)
+    dt = time_oracle_round(g)
+    m = len(g["src"])
+    return {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one exact refinement round P_0 -> P_1 of the same generator at quarter size "
+                      f"({g['n']:,} vertices / {m:,} edges), single-threaded C++ oracle, {dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    g = cpu_sample_graph(args.scale)
+    m = len(g["src"])
+    for _ in range(args.warmup):
+        time_oracle_round(g)
+    t = [time_oracle_round(g) for _ in range(args.steps)]
+    total = sum(t)
+    value = m * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32 ids (exact signatures, no hashing)", "data": "synthetic",
+            "config": config_dict(max(1000, int(WORKLOAD["n"] * args.scale)), max(10_000, int(WORKLOAD["m"] * args.scale)),
+                                  extra={"parallelism": "single CPU thread",
+                                         "note": "oracle timed on a bounded sample of the workload"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one exact refinement round per step on the quarter-size instance "
+                                       f"({g['n']:,} vertices / {m:,} edges)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

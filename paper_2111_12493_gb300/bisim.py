@@ -47,6 +47,11 @@ class Stats(ctypes.Structure):
                 ("last_frontier", ctypes.c_int64)]
 
 
+class KernelProfile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("alg_bytes", ctypes.c_double), ("vertices", ctypes.c_int64), ("edges", ctypes.c_int64)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing; build it with paper_2111_12493_gb300.build.build()")
@@ -64,6 +69,10 @@ def _load():
         "bisim_get_stats": (ctypes.c_int, [p, ctypes.POINTER(Stats)]),
         "summarize_destroy": (ctypes.c_int, [p]),
         "bisim_last_error": (ctypes.c_char_p, [p]),
+        "bisim_profile_enable": (None, [i32]),
+        "bisim_profile_reset": (None, []),
+        "bisim_profile_read": (i32, [ctypes.POINTER(KernelProfile), i32]),
+        "bisim_launch_count": (i64, []),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -217,3 +226,24 @@ def summarize_destroy(ctx: Context):
 def bisim_last_error(ctx: Context | None = None) -> str:
     msg = _lib.bisim_last_error(ctx.ptr if ctx is not None else None)
     return msg.decode() if msg else ""
+
+
+def bisim_profile_enable(enable: bool = True):
+    _lib.bisim_profile_enable(1 if enable else 0)
+
+
+def bisim_profile_reset():
+    _lib.bisim_profile_reset()
+
+
+def bisim_profile_read() -> list:
+    """Per launch site: name, launches, total_ms, alg_bytes, vertices, edges."""
+    n = _lib.bisim_profile_read(None, 0)
+    arr = (KernelProfile * max(n, 1))()
+    n = _lib.bisim_profile_read(arr, n)
+    return [dict(name=a.name.decode(), launches=a.launches, total_ms=a.total_ms, alg_bytes=a.alg_bytes,
+                 vertices=a.vertices, edges=a.edges) for a in arr[:n]]
+
+
+def bisim_launch_count() -> int:
+    return int(_lib.bisim_launch_count())
