@@ -180,6 +180,39 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
  */
 bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream);
 
+/*
+ * bisim_refine_round_noalloc -- one refinement round (block_in -> block_out)
+ * that allocates no memory at all. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory, such as a
+ * plugin running inside another runtime that owns the whole device heap (a
+ * database's user-defined function, a custom operator of an inference
+ * server), or a latency-critical loop that reserves every buffer up front
+ * because an allocation may synchronise the device or fail under
+ * fragmentation.
+ *   row_ptr, col, edge_label  a device-resident out-CSR as in summarize_init
+ *                             (every vertex live)
+ *   block_in   int32[n] device array: any labelling of the vertices -- the raw
+ *              vertex labels for the first round, then the previous output
+ *   block_out  int32[n] device array, distinct from block_in: the canonical
+ *              ids (smallest vertex of each block) of the partition that keeps
+ *              u and v together iff block_in[u] = block_in[v] and their sets of
+ *              (edge label, block_in of target) pairs are equal
+ *   out_num_blocks  number of blocks of block_out; may be NULL
+ * Limits: at most 65536 vertices, 1048576 edges and out-degree 8192; larger
+ * graphs, host pointers or block_in == block_out return BISIM_EINVAL and
+ * touch nothing. All scratch lives in one fixed array of about 11.3 MB inside
+ * the library, which every GPU that loads the library holds until the process
+ * exits. The first call on a device looks up that array's device address
+ * (once per device); make that first call before any stream capture. Every
+ * call shares the array and clears what it needs at its start, so calls that
+ * overlap on the GPU -- from two threads or two streams at once -- race and
+ * must be serialised by the caller. Synchronises `stream`.
+ */
+bisim_status bisim_refine_round_noalloc(int32_t n_vertices, int64_t n_edges, const int64_t* row_ptr,
+                                        const int32_t* col, const int32_t* edge_label,
+                                        const int32_t* block_in, int32_t* block_out,
+                                        int64_t* out_num_blocks, void* stream);
+
 /* Counters of the context (see bisim_stats). Synchronises nothing. */
 bisim_status bisim_get_stats(const bisim_ctx* ctx, bisim_stats* out);
 

@@ -73,6 +73,7 @@ def _load():
         "bisim_profile_reset": (None, []),
         "bisim_profile_read": (i32, [ctypes.POINTER(KernelProfile), i32]),
         "bisim_launch_count": (i64, []),
+        "bisim_refine_round_noalloc": (ctypes.c_int, [i32, i64, p, p, p, p, p, ctypes.POINTER(i64), p]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -247,3 +248,22 @@ def bisim_profile_read() -> list:
 
 def bisim_launch_count() -> int:
     return int(_lib.bisim_launch_count())
+
+
+def bisim_refine_round_noalloc(n_vertices, row_ptr, col, edge_label, block_in, block_out, stream=None) -> int:
+    """One refinement round into caller-provided block_out without any allocation.
+
+    For callers that may not allocate device memory (a plugin inside another
+    runtime that owns the device heap, a loop that reserves all buffers up
+    front); scratch comes from a fixed array inside the library. All tensors
+    must be on the device; returns the number of blocks of block_out.
+    """
+    blocks = ctypes.c_int64()
+    m = col.numel()
+    rc = _lib.bisim_refine_round_noalloc(n_vertices, m, _ptr(row_ptr, torch.int64, "row_ptr", n_vertices + 1),
+                                         _ptr(col, torch.int32, "col"), _ptr(edge_label, torch.int32, "edge_label", m),
+                                         _ptr(block_in, torch.int32, "block_in", n_vertices),
+                                         _ptr(block_out, torch.int32, "block_out", n_vertices),
+                                         ctypes.byref(blocks), _stream(stream))
+    _check(rc)
+    return blocks.value
