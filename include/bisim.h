@@ -200,7 +200,7 @@ bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream);
  *   out_num_blocks  number of blocks of block_out; may be NULL
  * Limits: at most 65536 vertices, 1048576 edges and out-degree 8192; larger
  * graphs, host pointers or block_in == block_out return BISIM_EINVAL and
- * touch nothing. All scratch lives in one fixed array of about 11.3 MB inside
+ * touch nothing. All scratch lives in one fixed array of about 11.5 MB inside
  * the library, which every GPU that loads the library holds until the process
  * exits. The first call on a device looks up that array's device address
  * (once per device); make that first call before any stream capture. Every

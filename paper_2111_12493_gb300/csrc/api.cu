@@ -74,6 +74,7 @@ bisim_options resolve_options(const bisim_options* in) {
     o.small_max_degree = std::min(std::max(o.small_max_degree, 0), 32);
     o.mid_max_degree = std::min(std::max(o.mid_max_degree, 0), kMidMaxN);
     if (o.hub_chunk <= 0) o.hub_chunk = 4096;
+    o.hub_chunk = std::min(std::max(o.hub_chunk, 256), kHubChunkMax);
     if (o.k_incremental < 0) o.k_incremental = 0;
     return o;
 }

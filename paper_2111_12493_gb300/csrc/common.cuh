@@ -16,6 +16,7 @@ namespace bisim {
 constexpr int kSmallClasses = 4;          // thread-per-vertex classes: D = 4, 8, 16, 32
 constexpr int kMidClasses = 8;            // CTA-per-vertex classes: N = 64 .. 8192
 constexpr int kMidMaxN = 8192;            // largest CTA-path key count (64 KB of shared memory)
+constexpr int kHubChunkMax = 4096;        // hub-path edges per CTA (staged in shared memory)
 constexpr int kClassHub = kSmallClasses + kMidClasses;   // 12
 constexpr int kNumClasses = kClassHub + 1;               // 13
 constexpr uint8_t kClassDead = 255;
@@ -95,6 +96,8 @@ struct DevState {
     unsigned int unresolved;        // vertices pushed to the next collision level
     unsigned int error;             // kErr* bits
     unsigned long long aux;
+    unsigned int deferred;          // vertices whose set comparison is left to k_verify_deferred
+    unsigned int pad;
 };
 
 // Insert `h` (already masked) for vertex v; returns the slot index or ~0u on overflow.
@@ -110,7 +113,12 @@ __device__ __forceinline__ uint32_t table_insert(const TableRef& t, uint64_t h, 
             cur = prev;
         }
         if (cur == want) {
-            atomicMin(&t.slots[pos].minv, t.tag | static_cast<uint32_t>(v));
+            // Popular signatures (and labels) are inserted by many vertices; a
+            // plain read first skips the atomic whenever a smaller vertex of
+            // this epoch is already recorded.
+            const unsigned long long mine = t.tag | static_cast<uint32_t>(v);
+            const unsigned long long seen = *reinterpret_cast<volatile unsigned long long*>(&t.slots[pos].minv);
+            if (mine < seen) atomicMin(&t.slots[pos].minv, mine);
             return static_cast<uint32_t>(pos);
         }
         pos = (pos + 1) & t.mask;
@@ -193,6 +201,7 @@ struct bisim_ctx {
 
     // collision resolution
     int32_t* ulist[2] = {nullptr, nullptr};
+    int32_t* dlist = nullptr;      // vertices whose verification needs a set comparison
     bisim::DevState* dstate = nullptr;
     bisim::DevState* hstate = nullptr;   // pinned mirror
 

@@ -28,13 +28,22 @@ __global__ void k_validate_coo(const int32_t* __restrict__ src, const int32_t* _
 __global__ void k_pack_coo(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                            const int32_t* __restrict__ elab, int64_t m, uint32_t* __restrict__ keys,
                            uint64_t* __restrict__ vals, int32_t* __restrict__ deg) {
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        int32_t s = src[e];
-        keys[e] = static_cast<uint32_t>(s);
-        vals[e] = (static_cast<uint64_t>(static_cast<uint32_t>(elab[e])) << 32) |
-                  static_cast<uint32_t>(dst[e]);
-        atomicAdd(&deg[s], 1);
+    // trip count is uniform across the warp so the match below sees every lane
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t e0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; e0 < m; e0 += stride) {
+        const int64_t e = e0 + threadIdx.x;
+        const bool valid = e < m;
+        int32_t s = -1;
+        if (valid) {
+            s = src[e];
+            keys[e] = static_cast<uint32_t>(s);
+            vals[e] = (static_cast<uint64_t>(static_cast<uint32_t>(elab[e])) << 32) |
+                      static_cast<uint32_t>(dst[e]);
+        }
+        // one atomic per distinct source in the warp (edge lists are often grouped by source)
+        const unsigned peers = __match_any_sync(0xffffffffu, s);
+        if (valid && (threadIdx.x & 31) == static_cast<unsigned>(__ffs(peers) - 1))
+            atomicAdd(&deg[s], __popc(peers));
     }
 }
 
@@ -118,13 +127,24 @@ __global__ void k_class_edges(const uint32_t* __restrict__ sorted_cls, const uin
     if (threadIdx.x < kNumClasses) acc[threadIdx.x] = 0;
     __syncthreads();
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    uint32_t c = kNumClasses;
+    unsigned long long d = 0;
     if (i < n) {
-        const uint32_t c = sorted_cls[i];
+        c = min(sorted_cls[i], static_cast<uint32_t>(kNumClasses));
         if (c < kNumClasses) {
             const int64_t v = static_cast<int64_t>(sorted_v[i]);
-            atomicAdd(&acc[c], static_cast<unsigned long long>(rp[v + 1] - rp[v]));
+            d = static_cast<unsigned long long>(rp[v + 1] - rp[v]);
         }
     }
+    // classes are sorted, so a warp holds one or two of them: reduce per class first
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    unsigned long long tot = d;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_down_sync(0xffffffffu, tot, o);
+        const int src = static_cast<int>(threadIdx.x & 31) + o;
+        if (src < 32 && ((peers >> src) & 1u)) tot += y;
+    }
+    if (c < kNumClasses && (threadIdx.x & 31) == static_cast<unsigned>(__ffs(peers) - 1)) atomicAdd(&acc[c], tot);
     __syncthreads();
     if (threadIdx.x < kNumClasses && acc[threadIdx.x]) atomicAdd(&out[threadIdx.x], acc[threadIdx.x]);
 }

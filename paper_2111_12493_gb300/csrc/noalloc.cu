@@ -36,8 +36,9 @@ constexpr size_t kOffCnt = kOffSlot + align256(sizeof(uint32_t) * kNoAllocMaxVer
 constexpr size_t kOffList = kOffCnt + align256(sizeof(int32_t) * kNoAllocMaxVertices);
 constexpr size_t kOffU0 = kOffList + align256(sizeof(int32_t) * kNoAllocMaxVertices);
 constexpr size_t kOffU1 = kOffU0 + align256(sizeof(int32_t) * kNoAllocMaxVertices);
-constexpr size_t kOffState = kOffU1 + align256(sizeof(int32_t) * kNoAllocMaxVertices);
-constexpr size_t kNoAllocBytes = kOffState + align256(sizeof(DevState));   // about 11.3 MB
+constexpr size_t kOffDefer = kOffU1 + align256(sizeof(int32_t) * kNoAllocMaxVertices);
+constexpr size_t kOffState = kOffDefer + align256(sizeof(int32_t) * kNoAllocMaxVertices);
+constexpr size_t kNoAllocBytes = kOffState + align256(sizeof(DevState));   // about 11.5 MB
 
 // The fixed scratch. In host code this name is only a stand-in for the
 // symbol; its device address comes from cudaGetSymbolAddress below.
@@ -180,6 +181,7 @@ extern "C" bisim_status bisim_refine_round_noalloc(int32_t n_vertices, int64_t n
     tc.epoch32 = 0;
     tc.ulist[0] = reinterpret_cast<int32_t*>(base + kOffU0);
     tc.ulist[1] = reinterpret_cast<int32_t*>(base + kOffU1);
+    tc.dlist = reinterpret_cast<int32_t*>(base + kOffDefer);
     tc.dstate = dstate;
     tc.hstate = &host_state;
     tc.class_list = list;

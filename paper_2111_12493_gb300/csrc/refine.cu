@@ -53,10 +53,6 @@ struct HubView {
     const HubAcc* acc;
 };
 
-__device__ __forceinline__ bool is_hub_degree(int64_t d, int small_max, int mid_max) {
-    return d > 0 && d > small_max && d > mid_max;
-}
-
 __device__ __forceinline__ int64_t hub_index(const HubView& H, int32_t v) {
     int64_t lo = 0, hi = H.n_hub - 1;
     while (lo < hi) {
@@ -98,28 +94,34 @@ struct SigMode {
         return sig_hash(G.P[v], static_cast<uint32_t>(c), sum);
     }
 
-    // Exact comparison. Non-hub lists are sorted by pair value, so equal sets
-    // are equal element by element; a hub's list is unordered, so the other
-    // list is looked up in the hub's dedup table instead.
-    __device__ bool equal(int32_t v, int32_t r) const {
-        if (G.P[v] != G.P[r]) return false;
+    static constexpr bool kDefers = true;
+
+    // Exact comparison: 1 equal, 0 different, 2 left to the set comparison of
+    // k_verify_deferred. Lists of vertices on the thread-per-vertex path are
+    // sorted by pair value, so two of them are equal sets iff they are equal
+    // element by element; every other list is in arrival order.
+    __device__ int compare(int32_t v, int32_t r) const {
+        if (G.P[v] != G.P[r]) return 0;
         const int32_t c = cnt[v];
-        if (c != cnt[r]) return false;
+        if (c != cnt[r]) return 0;
         const int64_t bv = G.rp[v], br = G.rp[r];
-        const bool hv = is_hub_degree(G.rp[v + 1] - bv, small_max, mid_max);
-        const bool hr = is_hub_degree(G.rp[r + 1] - br, small_max, mid_max);
+        const int64_t dv = G.rp[v + 1] - bv, dr = G.rp[r + 1] - br;
+        const bool sorted = (dv == 0 || dv <= small_max) && (dr == 0 || dr <= small_max);
+        if (!sorted) return 2;
         const unsigned long long* lv = skey + bv;
         const unsigned long long* lr = skey + br;
-        if (!hv && !hr) {
-            for (int32_t j = 0; j < c; ++j)
-                if (lv[j] != lr[j]) return false;
-            return true;
+        {
+            // independent loads, four pairs per step, no early exit inside a step
+            int32_t j = 0;
+            for (; j + 4 <= c; j += 4) {
+                const unsigned long long a0 = lv[j], a1 = lv[j + 1], a2 = lv[j + 2], a3 = lv[j + 3];
+                const unsigned long long b0 = lr[j], b1 = lr[j + 1], b2 = lr[j + 2], b3 = lr[j + 3];
+                if (((a0 ^ b0) | (a1 ^ b1) | (a2 ^ b2) | (a3 ^ b3)) != 0ull) return 0;
+            }
+            for (; j < c; ++j)
+                if (lv[j] != lr[j]) return 0;
+            return 1;
         }
-        const int64_t h = hub_index(H, hv ? v : r);
-        const unsigned long long* other = hv ? lr : lv;
-        for (int32_t j = 0; j < c; ++j)
-            if (!hub_contains(H, h, other[j])) return false;
-        return true;
     }
 };
 
@@ -130,9 +132,10 @@ struct LabelMode {
     const int32_t* vlabel;
     const int32_t* gid;   // may be null
 
+    static constexpr bool kDefers = false;
     __device__ uint64_t hash0(int32_t v) const { return label_hash(gid ? gid[v] : 0, vlabel[v]); }
-    __device__ bool equal(int32_t v, int32_t r) const {
-        return vlabel[v] == vlabel[r] && (gid == nullptr || gid[v] == gid[r]);
+    __device__ int compare(int32_t v, int32_t r) const {
+        return vlabel[v] == vlabel[r] && (gid == nullptr || gid[v] == gid[r]) ? 1 : 0;
     }
 };
 
@@ -199,88 +202,143 @@ __global__ void __launch_bounds__(128) k_sig_small(const int32_t* __restrict__ l
     slot[v] = table_insert(t, h, v, err);
 }
 
-// One CTA of T threads per vertex of out-degree <= N: pairs staged in shared
-// memory, bitonic sort, then duplicate removal and compaction by a block scan.
+// Inserts pair value mv into a shared-memory open-addressing set (0 = empty;
+// the value 0 itself is tracked by *zero). Returns true for the first inserter.
+__device__ __forceinline__ bool smem_set_insert(unsigned long long* tab, uint32_t mask, unsigned* zero,
+                                                unsigned long long mv) {
+    if (mv == 0ull) return atomicExch(zero, 1u) == 0u;
+    uint32_t pos = static_cast<uint32_t>(mv) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long cur = tab[pos];
+        if (cur == mv) return false;
+        if (cur == 0ull) {
+            const unsigned long long prev = atomicCAS(&tab[pos], 0ull, mv);
+            if (prev == 0ull) return true;
+            if (prev == mv) return false;
+        }
+        pos = (pos + 1) & mask;
+    }
+    return false;   // unreachable: the set has twice as many slots as keys
+}
+
+__device__ __forceinline__ bool smem_set_contains(const unsigned long long* tab, uint32_t mask, unsigned zero,
+                                                  unsigned long long mv) {
+    if (mv == 0ull) return zero != 0u;
+    uint32_t pos = static_cast<uint32_t>(mv) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long cur = tab[pos];
+        if (cur == mv) return true;
+        if (cur == 0ull) return false;
+        pos = (pos + 1) & mask;
+    }
+    return false;
+}
+
+// One warp per vertex of out-degree <= N (N <= 256), eight vertices per CTA:
+// duplicates are removed with a hash set in the warp's slice of shared memory
+// (2N slots), so the cost is linear in the degree and needs no CTA barrier.
+// The unique values are written in arrival order (the list is a set; it is
+// compared as a set by the verification pass).
+template <int N>
+__global__ void __launch_bounds__(256) k_sig_warp(const int32_t* __restrict__ list, int64_t count, GraphView G,
+                                                  int32_t* __restrict__ cnt,
+                                                  unsigned long long* __restrict__ skey,
+                                                  uint32_t* __restrict__ slot, TableRef t, unsigned* err) {
+    constexpr int S = 2 * N;
+    __shared__ unsigned long long sm_all[8 * S];
+    __shared__ unsigned zero_all[8];
+    const int warp = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    unsigned long long* tab = sm_all + warp * S;
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * 8 + warp;
+    if (i >= count) return;                      // whole warp leaves together
+#pragma unroll
+    for (int j = static_cast<int>(lane); j < S; j += 32) tab[j] = 0ull;
+    if (lane == 0) zero_all[warp] = 0u;
+    __syncwarp();
+    const int32_t v = list[i];
+    const int64_t b = G.rp[v];
+    const int d = static_cast<int>(G.rp[v + 1] - b);
+    unsigned out = 0;
+    unsigned long long mys = 0;
+    for (int j0 = 0; j0 < d; j0 += 32) {
+        const int j = j0 + static_cast<int>(lane);
+        bool fresh = false;
+        unsigned long long mv = 0;
+        if (j < d) {
+            const int32_t w = __ldcs(G.col + b + j);
+            const int32_t l = __ldcs(G.elab + b + j);
+            mv = pair_value(l, __ldg(G.P + w));
+            fresh = smem_set_insert(tab, S - 1, &zero_all[warp], mv);
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, fresh);
+        if (fresh) {
+            skey[b + out + __popc(ball & lanemask_lt())] = mv;
+            mys += mv;
+        }
+        out += __popc(ball);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mys += __shfl_xor_sync(0xffffffffu, mys, o);
+    if (lane == 0) {
+        cnt[v] = static_cast<int32_t>(out);
+        const uint64_t h = sig_hash(G.P[v], out, mys) & t.hmask;
+        slot[v] = table_insert(t, h, v, err);
+    }
+}
+
+// One CTA of T threads per vertex of out-degree <= N: hash-set dedup in a
+// shared-memory table of 2N slots, block-wide compaction of the unique values.
 template <int N, int T>
 __global__ void __launch_bounds__(T) k_sig_mid(const int32_t* __restrict__ list, GraphView G,
                                                int32_t* __restrict__ cnt,
                                                unsigned long long* __restrict__ skey,
                                                uint32_t* __restrict__ slot, TableRef t,
                                                unsigned* err) {
-    extern __shared__ unsigned long long sm[];
-    __shared__ unsigned wc[T / 32];
+    extern __shared__ unsigned long long tab[];   // 2N slots
     __shared__ unsigned long long ws[T / 32];
-    constexpr int E = N / T;
-    static_assert(E >= 1 && N % T == 0, "tile shape");
+    __shared__ unsigned n_out, zero;
+    constexpr uint32_t mask = 2 * N - 1;
     const int32_t v = list[blockIdx.x];
     const int64_t b = G.rp[v];
     const int d = static_cast<int>(G.rp[v + 1] - b);
-    for (int j = threadIdx.x; j < N; j += T) {
+    for (int j = threadIdx.x; j < 2 * N; j += T) tab[j] = 0ull;
+    if (threadIdx.x == 0) {
+        n_out = 0;
+        zero = 0;
+    }
+    __syncthreads();
+    unsigned long long mys = 0;
+    for (int j0 = 0; j0 < d; j0 += T) {
+        const int j = j0 + static_cast<int>(threadIdx.x);
+        bool fresh = false;
+        unsigned long long mv = 0;
         if (j < d) {
             const int32_t w = __ldcs(G.col + b + j);
             const int32_t l = __ldcs(G.elab + b + j);
-            sm[j] = pair_value(l, __ldg(G.P + w));
-        } else {
-            sm[j] = ~0ull;
+            mv = pair_value(l, __ldg(G.P + w));
+            fresh = smem_set_insert(tab, mask, &zero, mv);
         }
-    }
-    __syncthreads();
-    for (int k = 2; k <= N; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < N / 2; i += T) {
-                const int lo = 2 * i - (i & (j - 1));
-                const int hi = lo + j;
-                const bool up = (lo & k) == 0;
-                const unsigned long long a = sm[lo], c = sm[hi];
-                if ((a > c) == up) {
-                    sm[lo] = c;
-                    sm[hi] = a;
-                }
+        const unsigned ball = __ballot_sync(0xffffffffu, fresh);
+        if (ball) {
+            const int leader = __ffs(ball) - 1;
+            unsigned base = 0;
+            if (static_cast<int>(lane_id()) == leader) base = atomicAdd(&n_out, __popc(ball));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (fresh) {
+                skey[b + base + __popc(ball & lanemask_lt())] = mv;
+                mys += mv;
             }
-            __syncthreads();
         }
     }
-    // each thread owns E consecutive sorted positions
-    const int base = threadIdx.x * E;
-    unsigned myc = 0;
-    unsigned long long mys = 0;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int j = base + e;
-        if (j < d && (j == 0 || sm[j] != sm[j - 1])) {
-            ++myc;
-            mys += sm[j];
-        }
-    }
-    // block-wide exclusive scan of myc and reduction of mys
-    unsigned inc = myc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane_id() >= static_cast<unsigned>(o)) inc += y;
-    }
-    unsigned long long wsum = mys;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-    const int warp = threadIdx.x >> 5;
-    if (lane_id() == 31) wc[warp] = inc;
-    if (lane_id() == 0) ws[warp] = wsum;
+    for (int o = 16; o > 0; o >>= 1) mys += __shfl_xor_sync(0xffffffffu, mys, o);
+    if (lane_id() == 0) ws[threadIdx.x >> 5] = mys;
     __syncthreads();
-    unsigned before = 0, total = 0;
-    unsigned long long tsum = 0;
-#pragma unroll
-    for (int w = 0; w < T / 32; ++w) {
-        if (w < warp) before += wc[w];
-        total += wc[w];
-        tsum += ws[w];
-    }
-    unsigned pos = before + inc - myc;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int j = base + e;
-        if (j < d && (j == 0 || sm[j] != sm[j - 1])) skey[b + pos++] = sm[j];
-    }
     if (threadIdx.x == 0) {
+        unsigned long long tsum = 0;
+        for (int w = 0; w < T / 32; ++w) tsum += ws[w];
+        const unsigned total = n_out;
         cnt[v] = static_cast<int32_t>(total);
         const uint64_t h = sig_hash(G.P[v], total, tsum) & t.hmask;
         slot[v] = table_insert(t, h, v, err);
@@ -388,10 +446,10 @@ __global__ void k_resolve_verify(const int32_t* __restrict__ list, int64_t count
                                  const uint8_t* __restrict__ alive, Mode M,
                                  const uint32_t* __restrict__ slot, const Slot* __restrict__ slots,
                                  int32_t* __restrict__ Pout, int32_t* __restrict__ next,
-                                 DevState* st, int32_t n_total) {
+                                 int32_t* __restrict__ deferred, DevState* st, int32_t n_total) {
     const int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x;
     const int64_t i = i0 + threadIdx.x;
-    bool is_block = false, push = false;
+    bool is_block = false, push = false, defer = false;
     int32_t v = -1;
     if (i < count) {
         v = list ? list[i] : static_cast<int32_t>(i);
@@ -406,10 +464,11 @@ __global__ void k_resolve_verify(const int32_t* __restrict__ list, int64_t count
             } else if (r == v) {
                 Pout[v] = v;
                 is_block = true;
-            } else if (M.equal(v, r)) {
-                Pout[v] = r;
             } else {
-                push = true;
+                const int eq = M.compare(v, r);
+                if (eq == 1) Pout[v] = r;
+                else if (eq == 0) push = true;
+                else defer = true;
             }
         }
     }
@@ -423,6 +482,64 @@ __global__ void k_resolve_verify(const int32_t* __restrict__ list, int64_t count
         if (static_cast<int>(lane_id()) == leader) base = atomicAdd(&st->unresolved, __popc(pb));
         base = __shfl_sync(0xffffffffu, base, leader);
         if (push) next[base + __popc(pb & lanemask_lt())] = v;
+    }
+    const unsigned db = __ballot_sync(0xffffffffu, defer);
+    if (db) {
+        const int leader = __ffs(db) - 1;
+        unsigned base = 0;
+        if (static_cast<int>(lane_id()) == leader) base = atomicAdd(&st->deferred, __popc(db));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (defer) deferred[base + __popc(db & lanemask_lt())] = v;
+    }
+}
+
+constexpr int kDeferThreads = 256;
+constexpr int kDeferGrid = 304;                        // two waves of one CTA per SM
+constexpr int kDeferSetSlots = 2 * kMidMaxN;           // shared-memory set for lists up to 8192
+constexpr size_t kDeferSmem = sizeof(unsigned long long) * kDeferSetSlots;
+
+// Set comparison for the vertices deferred by k_resolve_verify: equal sizes
+// were already checked, so S_v == S_r iff every value of S_v is in S_r. Lists
+// up to 8192 values go through a shared-memory set of S_r; longer lists belong
+// to hubs (a list is never longer than the degree), whose dedup table is probed.
+// A persistent grid reads the deferred count on the device, so no host
+// round trip is needed between the two passes.
+__global__ void __launch_bounds__(kDeferThreads) k_verify_deferred(const int32_t* __restrict__ deferred,
+                                                                   SigMode M, const uint32_t* __restrict__ slot,
+                                                                   const Slot* __restrict__ slots,
+                                                                   int32_t* __restrict__ Pout,
+                                                                   int32_t* __restrict__ next, DevState* st) {
+    extern __shared__ unsigned long long tab[];
+    __shared__ unsigned zero;
+    const unsigned count = *reinterpret_cast<volatile unsigned*>(&st->deferred);
+    for (unsigned i = blockIdx.x; i < count; i += gridDim.x) {
+        const int32_t v = deferred[i];
+        const int32_t r = table_rep(slots, slot[v]);
+        const int32_t c = M.cnt[v];
+        const unsigned long long* lv = M.skey + M.G.rp[v];
+        const unsigned long long* lr = M.skey + M.G.rp[r];
+        bool miss = false;
+        if (c > kMidMaxN) {
+            const int64_t h = hub_index(M.H, v);
+            for (int32_t j = threadIdx.x; j < c && !miss; j += kDeferThreads)
+                miss = !hub_contains(M.H, h, lr[j]);
+        } else {
+            uint32_t size = 64;
+            while (size < 2u * static_cast<uint32_t>(c)) size <<= 1;
+            for (uint32_t j = threadIdx.x; j < size; j += kDeferThreads) tab[j] = 0ull;
+            if (threadIdx.x == 0) zero = 0u;
+            __syncthreads();
+            for (int32_t j = threadIdx.x; j < c; j += kDeferThreads) smem_set_insert(tab, size - 1, &zero, lr[j]);
+            __syncthreads();
+            for (int32_t j = threadIdx.x; j < c && !miss; j += kDeferThreads)
+                miss = !smem_set_contains(tab, size - 1, zero, lv[j]);
+        }
+        const int any = __syncthreads_or(miss ? 1 : 0);
+        if (threadIdx.x == 0) {
+            if (!any) Pout[v] = r;
+            else next[atomicAdd(&st->unresolved, 1u)] = v;
+        }
+        __syncthreads();
     }
 }
 
@@ -452,6 +569,22 @@ TableRef next_epoch(bisim_ctx* ctx, cudaStream_t s) {
 }
 
 template <class Mode>
+void launch_deferred(bisim_ctx* ctx, const Mode& M, int32_t* Pout, int32_t* next, cudaStream_t s) {
+    if constexpr (Mode::kDefers) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_verify_deferred, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kDeferSmem));
+            attr_set = true;
+        }
+        BISIM_SITE(site, "verify_deferred");
+        Launch L(site, s, 0, 0, 0.0);
+        k_verify_deferred<<<kDeferGrid, kDeferThreads, kDeferSmem, s>>>(ctx->dlist, M, ctx->slot, ctx->table, Pout,
+                                                                         next, ctx->dstate);
+    }
+}
+
+template <class Mode>
 bisim_status resolve(bisim_ctx* ctx, Mode M, int32_t* Pout, cudaStream_t s, int64_t* blocks) {
     const int32_t n = ctx->n;
     cudaError_t e;
@@ -460,8 +593,10 @@ bisim_status resolve(bisim_ctx* ctx, Mode M, int32_t* Pout, cudaStream_t s, int6
         BISIM_SITE(site, Mode::kVerifySite);
         Launch L(site, s, n, 0, Mode::kVerifyBytesPerVertex * n);
         k_resolve_verify<Mode><<<grid_for(n, 256), 256, 0, s>>>(nullptr, n, ctx->alive, M, ctx->slot,
-                                                                ctx->table, Pout, ctx->ulist[0], ctx->dstate, n);
+                                                                ctx->table, Pout, ctx->ulist[0], ctx->dlist,
+                                                                ctx->dstate, n);
     }
+    if (n > 0) launch_deferred(ctx, M, Pout, ctx->ulist[0], s);
     cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "verify signatures");
     int which = 0;
@@ -472,6 +607,7 @@ bisim_status resolve(bisim_ctx* ctx, Mode M, int32_t* Pout, cudaStream_t s, int6
         const int64_t cu = ctx->hstate->unresolved;
         TableRef t = next_epoch(ctx, s);
         cudaMemsetAsync(&ctx->dstate->unresolved, 0, sizeof(unsigned), s);
+        cudaMemsetAsync(&ctx->dstate->deferred, 0, sizeof(unsigned), s);
         BISIM_SITE(site_i, "collision_insert");
         BISIM_SITE(site_v, "collision_verify");
         {
@@ -483,8 +619,9 @@ bisim_status resolve(bisim_ctx* ctx, Mode M, int32_t* Pout, cudaStream_t s, int6
             Launch L(site_v, s, cu, 0, 0.0);
             k_resolve_verify<Mode><<<grid_for(cu, 256), 256, 0, s>>>(ctx->ulist[which], cu, ctx->alive, M, ctx->slot,
                                                                       ctx->table, Pout, ctx->ulist[which ^ 1],
-                                                                      ctx->dstate, n);
+                                                                      ctx->dlist, ctx->dstate, n);
         }
+        launch_deferred(ctx, M, Pout, ctx->ulist[which ^ 1], s);
         cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "resolve hash collisions");
         which ^= 1;
@@ -507,9 +644,25 @@ constexpr int mid_class_of(int N) {
 }
 
 template <int N>
+void launch_cta_mid(bisim_ctx* ctx, const int32_t* list, int64_t count, GraphView G, TableRef t, cudaStream_t s);
+
+template <int N>
 void launch_mid(bisim_ctx* ctx, const int32_t* list, int64_t count, GraphView G, TableRef t, cudaStream_t s) {
-    constexpr int T = N / 2 < 512 ? N / 2 : 512;
-    const size_t smem = sizeof(unsigned long long) * N;
+    if constexpr (N <= 256) {
+        static const int site = prof_site(N == 64 ? "sig_warp_64" : N == 128 ? "sig_warp_128" : "sig_warp_256");
+        const int64_t edges = ctx->class_edges[kSmallClasses + mid_class_of(N)];
+        Launch L(site, s, count, edges, kSigBytesPerEdge * edges + kSigBytesPerVertex * count);
+        k_sig_warp<N><<<grid_for(count, 8), 256, 0, s>>>(list, count, G, ctx->cnt, ctx->skey, ctx->slot, t,
+                                                         &ctx->dstate->error);
+    } else {
+        launch_cta_mid<N>(ctx, list, count, G, t, s);
+    }
+}
+
+template <int N>
+void launch_cta_mid(bisim_ctx* ctx, const int32_t* list, int64_t count, GraphView G, TableRef t, cudaStream_t s) {
+    constexpr int T = N <= 1024 ? 256 : 512;
+    const size_t smem = sizeof(unsigned long long) * 2 * N;
     static bool attr_set = false;   // per process; the attribute belongs to the function
     if (!attr_set && smem > 48 * 1024) {
         cudaFuncSetAttribute(k_sig_mid<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -538,6 +691,7 @@ bisim_status alloc_refine_state(bisim_ctx* ctx, cudaStream_t s) {
     if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->slot), sizeof(uint32_t) * nv, s))) return cuda_error(ctx, e, "alloc slot");
     for (int i = 0; i < 2; ++i)
         if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ulist[i]), sizeof(int32_t) * nv, s))) return cuda_error(ctx, e, "alloc unresolved list");
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dlist), sizeof(int32_t) * nv, s))) return cuda_error(ctx, e, "alloc deferred list");
     if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->skey), sizeof(unsigned long long) * std::max<int64_t>(m, 1), s))) return cuda_error(ctx, e, "alloc signature lists");
     uint64_t ns = 1024;
     while (ns < 2ull * static_cast<uint64_t>(n)) ns <<= 1;
