@@ -56,6 +56,13 @@ typedef enum {
 
 enum { BISIM_FIXPOINT = -1 };
 
+/* Option flags. BISIM_FLAG_L2_PIN: mark the current partition as persisting in
+ * L2 during bisim_iterate (an access-policy window on the caller's stream for
+ * the duration of the call, removed with the persisting lines reset before
+ * returning). Off by default: on the 10M-vertex power-law graph the set-aside
+ * slowed the rest of the round more than it sped up the gathers. */
+enum { BISIM_FLAG_L2_PIN = 1 };
+
 /* Update operations (Section 3.2, incremental summarization of evolving graphs:
  * additions, deletions and modifications of vertices and edges). */
 enum {
@@ -81,8 +88,8 @@ typedef struct {
     int32_t mid_max_degree;    /* out-degree <= this: one CTA per vertex, keys staged in shared
                                   memory (default 8192, max 8192); above it: hub path, many CTAs
                                   per vertex with a global dedup table */
-    int32_t hub_chunk;         /* edges per CTA on the hub path (default 4096) */
-    int32_t reserved0;
+    int32_t hub_chunk;         /* edges per CTA on the hub path (default 4096, 256..4096) */
+    int32_t flags;             /* BISIM_FLAG_* bits (default 0) */
     int64_t mem_budget_bytes;  /* refuse (BISIM_ENOMEM) contexts whose device footprint would
                                   exceed this; 0 = no limit */
 } bisim_options;
@@ -200,7 +207,7 @@ bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream);
  *   out_num_blocks  number of blocks of block_out; may be NULL
  * Limits: at most 65536 vertices, 1048576 edges and out-degree 8192; larger
  * graphs, host pointers or block_in == block_out return BISIM_EINVAL and
- * touch nothing. All scratch lives in one fixed array of about 11.5 MB inside
+ * touch nothing. All scratch lives in one fixed array of about 10.5 MB inside
  * the library, which every GPU that loads the library holds until the process
  * exits. The first call on a device looks up that array's device address
  * (once per device); make that first call before any stream capture. Every

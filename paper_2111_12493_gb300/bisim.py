@@ -34,7 +34,7 @@ class BisimError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("k_incremental", ctypes.c_int32), ("hash_bits", ctypes.c_int32),
                 ("small_max_degree", ctypes.c_int32), ("mid_max_degree", ctypes.c_int32),
-                ("hub_chunk", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("hub_chunk", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("mem_budget_bytes", ctypes.c_int64)]
 
 

@@ -360,7 +360,10 @@ bisim_status bisim_iterate(bisim_ctx* ctx, int32_t k, int32_t cap, int32_t* out_
     for (int32_t i = 0; i < limit; ++i) {
         int64_t blocks = 0;
         bisim_status st = refine_round(ctx, s, &blocks);
-        if (st != BISIM_OK) return st;
+        if (st != BISIM_OK) {
+            unpin_partition(ctx, s);
+            return st;
+        }
         ++executed;
         if (blocks == prev) {   // P_{i+1} refines P_i with as many blocks: P_{i+1} = P_i
             rounds = (k == BISIM_FIXPOINT) ? i : k;
@@ -368,6 +371,7 @@ bisim_status bisim_iterate(bisim_ctx* ctx, int32_t k, int32_t cap, int32_t* out_
         }
         prev = blocks;
     }
+    unpin_partition(ctx, s);
     if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "bisim_iterate");
     ctx->last_blocks = p0_blocks;
     ctx->stats.rounds = rounds;

@@ -25,7 +25,6 @@ constexpr uint64_t kSaltKey = 0x243f6a8885a308d3ull;     // per-pair key -> m va
 constexpr uint64_t kSaltSig = 0x13198a2e03707344ull;     // own term of the signature hash
 constexpr uint64_t kSaltLabel = 0xa4093822299f31d0ull;   // label partition hash
 constexpr uint64_t kLevelStep = 0x9e3779b97f4a7c15ull;   // re-hash step of collision levels
-constexpr uint64_t kKey56 = 0x00ffffffffffffffull;
 
 // device error bits
 constexpr unsigned kErrTableFull = 1u;
@@ -73,21 +72,25 @@ __device__ __forceinline__ uint64_t level_hash(uint64_t h0, uint32_t level, uint
 
 // ----------------------------------------------------------------------------- signature table
 
-// One slot of the open-addressing signature table. `key` holds the 8-bit epoch
-// in its top byte and the low 56 bits of the signature hash; a slot whose
-// epoch byte differs from the current one is free, so the table needs no
-// clearing between rounds. `minv` holds (~epoch32 << 32 | vertex); atomicMin
-// keeps the smallest vertex id of the current epoch and overrides stale ones.
-struct __align__(16) Slot {
-    unsigned long long key;
-    unsigned long long minv;
+// One 8-byte slot of the open-addressing signature table:
+//   bits 63..36  fingerprint: the top 28 bits of the signature hash
+//   bits 35..32  epoch 1..15; a slot whose epoch is not the current one is free,
+//                so the table needs clearing only when the epoch wraps
+//   bits 31..0   the smallest vertex inserted with this fingerprint this epoch
+// Two different signatures that meet in one slot with equal fingerprints are
+// merged here and split again by the exact verification pass.
+struct __align__(8) Slot {
+    unsigned long long w;
 };
+
+constexpr unsigned long long kSlotEpochMask = 0xf00000000ull;
+constexpr unsigned long long kSlotKeyMask = ~0xffffffffull;     // fingerprint | epoch
+constexpr uint32_t kEpochCycle = 15;
 
 struct TableRef {
     Slot* slots;
     uint64_t mask;        // nslots - 1
-    uint64_t epoch8;      // 1..254, already shifted into bits 56..63
-    unsigned long long tag;  // (~epoch32) << 32
+    uint64_t epoch;       // 1..15, already shifted into bits 32..35
     uint64_t hmask;       // hash width mask (tests only narrow it)
 };
 
@@ -103,23 +106,29 @@ struct DevState {
 // Insert `h` (already masked) for vertex v; returns the slot index or ~0u on overflow.
 __device__ __forceinline__ uint32_t table_insert(const TableRef& t, uint64_t h, int32_t v,
                                                  unsigned* err) {
-    const unsigned long long want = t.epoch8 | (h & kKey56);
-    uint64_t pos = (h ^ (h >> 32)) & t.mask;
+    const unsigned long long tag = (h & ~0xfffffffffull) | t.epoch;
+    const unsigned long long want = tag | static_cast<uint32_t>(v);
+    uint64_t pos = h & t.mask;
     for (uint64_t probe = 0; probe <= t.mask; ++probe) {
-        unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&t.slots[pos].key);
-        while ((cur & ~kKey56) != t.epoch8) {          // stale: try to claim
-            unsigned long long prev = atomicCAS(&t.slots[pos].key, cur, want);
-            if (prev == cur) { cur = want; break; }
-            cur = prev;
-        }
-        if (cur == want) {
-            // Popular signatures (and labels) are inserted by many vertices; a
-            // plain read first skips the atomic whenever a smaller vertex of
-            // this epoch is already recorded.
-            const unsigned long long mine = t.tag | static_cast<uint32_t>(v);
-            const unsigned long long seen = *reinterpret_cast<volatile unsigned long long*>(&t.slots[pos].minv);
-            if (mine < seen) atomicMin(&t.slots[pos].minv, mine);
-            return static_cast<uint32_t>(pos);
+        unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&t.slots[pos].w);
+        for (;;) {
+            if ((cur & kSlotEpochMask) != t.epoch) {            // free in this epoch: claim it
+                const unsigned long long prev = atomicCAS(&t.slots[pos].w, cur, want);
+                if (prev == cur) return static_cast<uint32_t>(pos);
+                cur = prev;
+                continue;
+            }
+            if ((cur & kSlotKeyMask) == tag) {                  // same fingerprint: keep the smaller vertex
+                // popular signatures are inserted by many vertices; the plain
+                // read above skips the atomic when a smaller one is recorded
+                while (static_cast<uint32_t>(v) < static_cast<uint32_t>(cur)) {
+                    const unsigned long long prev = atomicCAS(&t.slots[pos].w, cur, want);
+                    if (prev == cur) break;
+                    cur = prev;
+                }
+                return static_cast<uint32_t>(pos);
+            }
+            break;                                               // another signature: probe on
         }
         pos = (pos + 1) & t.mask;
     }
@@ -128,7 +137,7 @@ __device__ __forceinline__ uint32_t table_insert(const TableRef& t, uint64_t h, 
 }
 
 __device__ __forceinline__ int32_t table_rep(const Slot* slots, uint32_t pos) {
-    return static_cast<int32_t>(static_cast<uint32_t>(slots[pos].minv & 0xffffffffull));
+    return static_cast<int32_t>(static_cast<uint32_t>(slots[pos].w));
 }
 
 // ----------------------------------------------------------------------------- hub tables
@@ -246,6 +255,7 @@ bisim_status build_buckets(bisim_ctx* ctx, cudaStream_t s);
 bisim_status compute_p0(bisim_ctx* ctx, cudaStream_t s);
 bisim_status refine_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks);
 bisim_status alloc_refine_state(bisim_ctx* ctx, cudaStream_t s);
+void unpin_partition(bisim_ctx* ctx, cudaStream_t s);
 void launch_local_ids(const bisim_ctx* ctx, int32_t* out, cudaStream_t s);
 
 }  // namespace bisim

@@ -38,7 +38,7 @@ constexpr size_t kOffU0 = kOffList + align256(sizeof(int32_t) * kNoAllocMaxVerti
 constexpr size_t kOffU1 = kOffU0 + align256(sizeof(int32_t) * kNoAllocMaxVertices);
 constexpr size_t kOffDefer = kOffU1 + align256(sizeof(int32_t) * kNoAllocMaxVertices);
 constexpr size_t kOffState = kOffDefer + align256(sizeof(int32_t) * kNoAllocMaxVertices);
-constexpr size_t kNoAllocBytes = kOffState + align256(sizeof(DevState));   // about 11.5 MB
+constexpr size_t kNoAllocBytes = kOffState + align256(sizeof(DevState));   // about 10.5 MB
 
 // The fixed scratch. In host code this name is only a stand-in for the
 // symbol; its device address comes from cudaGetSymbolAddress below.
@@ -141,7 +141,7 @@ extern "C" bisim_status bisim_refine_round_noalloc(int32_t n_vertices, int64_t n
     std::memset(&host_state, 0, sizeof(host_state));
     DevState* dstate = reinterpret_cast<DevState*>(base + kOffState);
     int32_t* list = reinterpret_cast<int32_t*>(base + kOffList);
-    cudaMemsetAsync(base + kOffTable, 0xff, sizeof(Slot) * nslots, s);
+    cudaMemsetAsync(base + kOffTable, 0, sizeof(Slot) * nslots, s);
     cudaMemsetAsync(dstate, 0, sizeof(DevState), s);
     {
         BISIM_SITE(site, "noalloc_prepare");

@@ -17,6 +17,7 @@
 // every level resolves at least one group per colliding hash and the loop ends
 // with the exact partition.
 #include <algorithm>
+#include <cstring>
 
 #include "common.cuh"
 #include "prof.cuh"
@@ -555,14 +556,13 @@ __global__ void k_local_ids(const int32_t* __restrict__ P, const int32_t* __rest
 
 TableRef next_epoch(bisim_ctx* ctx, cudaStream_t s) {
     ctx->epoch32 += 1;
-    const uint32_t e8 = ((ctx->epoch32 - 1) % 254u) + 1u;
-    if (ctx->epoch32 > 1 && e8 == 1)   // the 8-bit tag wrapped: start from a blank table
-        cudaMemsetAsync(ctx->table, 0xff, sizeof(Slot) * ctx->nslots, s);
+    const uint32_t e = ((ctx->epoch32 - 1) % kEpochCycle) + 1u;
+    if (ctx->epoch32 > 1 && e == 1)   // the epoch wrapped: start from a blank table
+        cudaMemsetAsync(ctx->table, 0, sizeof(Slot) * ctx->nslots, s);
     TableRef t;
     t.slots = ctx->table;
     t.mask = ctx->nslots - 1;
-    t.epoch8 = static_cast<uint64_t>(e8) << 56;
-    t.tag = static_cast<unsigned long long>(~ctx->epoch32) << 32;
+    t.epoch = static_cast<uint64_t>(e) << 32;
     const int hb = ctx->opt.hash_bits;
     t.hmask = hb >= 64 ? ~0ull : ((1ull << hb) - 1ull);
     return t;
@@ -679,6 +679,47 @@ void launch_cta_mid(bisim_ctx* ctx, const int32_t* list, int64_t count, GraphVie
 
 }  // namespace
 
+// The gathers of a round read P_i at random (one 4-byte id per edge); P_i is
+// small enough to stay in L2, so it is marked persisting there while the
+// round's tables and edge streams pass through. The persisting set-aside is a
+// limit of this process's context and disappears with it.
+void pin_partition_in_l2(bisim_ctx* ctx, const int32_t* P, cudaStream_t s) {
+    if (!(ctx->opt.flags & BISIM_FLAG_L2_PIN)) return;
+    static int max_persist[64] = {};
+    static int max_window[64] = {};
+    const int dev = ctx->device;
+    if (dev < 0 || dev >= 64) return;
+    if (max_persist[dev] == 0) {
+        int mp = 0, mw = 0;
+        cudaDeviceGetAttribute(&mp, cudaDevAttrMaxPersistingL2CacheSize, dev);
+        cudaDeviceGetAttribute(&mw, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+        max_persist[dev] = mp > 0 ? mp : -1;
+        max_window[dev] = mw;
+        if (mp > 0) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, static_cast<size_t>(mp));
+    }
+    if (max_persist[dev] <= 0 || max_window[dev] <= 0) return;
+    const size_t bytes = std::min(sizeof(int32_t) * static_cast<size_t>(ctx->n), static_cast<size_t>(max_window[dev]));
+    cudaStreamAttrValue attr;
+    std::memset(&attr, 0, sizeof(attr));
+    attr.accessPolicyWindow.base_ptr = const_cast<int32_t*>(P);
+    attr.accessPolicyWindow.num_bytes = bytes;
+    attr.accessPolicyWindow.hitRatio = std::min(1.0f, static_cast<float>(max_persist[dev]) / static_cast<float>(bytes));
+    attr.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
+    cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &attr);
+    cudaGetLastError();   // a stream that takes no window (the legacy stream) simply runs without it
+}
+
+void unpin_partition(bisim_ctx* ctx, cudaStream_t s) {
+    if (!(ctx->opt.flags & BISIM_FLAG_L2_PIN)) return;
+    cudaStreamAttrValue attr;
+    std::memset(&attr, 0, sizeof(attr));
+    attr.accessPolicyWindow.num_bytes = 0;
+    cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &attr);
+    cudaCtxResetPersistingL2Cache();
+    cudaGetLastError();
+}
+
 bisim_status alloc_refine_state(bisim_ctx* ctx, cudaStream_t s) {
     const int32_t n = ctx->n;
     const int64_t m = ctx->m;
@@ -693,11 +734,12 @@ bisim_status alloc_refine_state(bisim_ctx* ctx, cudaStream_t s) {
         if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ulist[i]), sizeof(int32_t) * nv, s))) return cuda_error(ctx, e, "alloc unresolved list");
     if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dlist), sizeof(int32_t) * nv, s))) return cuda_error(ctx, e, "alloc deferred list");
     if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->skey), sizeof(unsigned long long) * std::max<int64_t>(m, 1), s))) return cuda_error(ctx, e, "alloc signature lists");
+    // load factor at most 0.6: 8 bytes per slot keeps the table near L2 size
     uint64_t ns = 1024;
-    while (ns < 2ull * static_cast<uint64_t>(n)) ns <<= 1;
+    while (static_cast<double>(ns) * 0.6 < static_cast<double>(n)) ns <<= 1;
     ctx->nslots = ns;
     if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->table), sizeof(Slot) * ns, s))) return cuda_error(ctx, e, "alloc signature table");
-    cudaMemsetAsync(ctx->table, 0xff, sizeof(Slot) * ns, s);
+    cudaMemsetAsync(ctx->table, 0, sizeof(Slot) * ns, s);
     if (ctx->hub_tab) cudaMemsetAsync(ctx->hub_tab, 0, sizeof(unsigned long long) * ctx->hub_tab_words, s);
     if ((e = cudaGetLastError())) return cuda_error(ctx, e, "init refine state");
     return BISIM_OK;
@@ -724,6 +766,7 @@ bisim_status refine_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     const int32_t* P = ctx->P[ctx->cur];
     int32_t* Pn = ctx->P[ctx->cur ^ 1];
     GraphView G{ctx->row_ptr, ctx->col, ctx->elab, P};
+    pin_partition_in_l2(ctx, P, s);
     TableRef t = next_epoch(ctx, s);
     if (ctx->n_hub > 0) {
         cudaMemsetAsync(ctx->hub_tab, 0, sizeof(unsigned long long) * ctx->hub_tab_words, s);
