@@ -190,6 +190,64 @@ cudaError_t ctx_alloc(bisim_ctx* ctx, void** p, size_t bytes, cudaStream_t s) {
     return e;
 }
 
+// Rebuilds what depends on the CSR after an update batch changed it: degree
+// buckets, signature-list capacity and the label partition.
+bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s) {
+    if (!ctx->buckets_dirty) return BISIM_OK;
+    cudaError_t e;
+    bisim_status st;
+    if (ctx->m > ctx->skey_cap) {
+        ctx_free(ctx, ctx->skey, sizeof(unsigned long long) * ctx->skey_cap, s);
+        ctx->skey = nullptr;
+        const int64_t cap = ctx->m + ctx->m / 4 + 1024;
+        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->skey), sizeof(unsigned long long) * cap, s)))
+            return cuda_error(ctx, e, "grow signature lists");
+        ctx->skey_cap = cap;
+    }
+    if ((st = build_buckets(ctx, s)) != BISIM_OK) return st;
+    if ((st = compute_p0(ctx, s)) != BISIM_OK) return st;
+    ctx->buckets_dirty = false;
+    ctx->stats.device_bytes = ctx->device_bytes;
+    return BISIM_OK;
+}
+
+// Resets to P_0 and refines: k rounds, or to the fixpoint (k = BISIM_FIXPOINT)
+// with at most `cap` rounds. Equal block counts in two consecutive rounds prove
+// the fixpoint, since every round refines the previous partition.
+bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
+                        int32_t* out_executed, int64_t* out_blocks) {
+    cudaError_t e;
+    if (ctx->n > 0) cudaMemcpyAsync(ctx->P[0], ctx->P0, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToDevice, s);
+    ctx->cur = 0;
+    int64_t prev = ctx->last_blocks;   // |P_0|
+    const int32_t limit = (k == BISIM_FIXPOINT) ? cap : k;
+    int32_t rounds = limit, executed = 0;
+    for (int32_t i = 0; i < limit; ++i) {
+        int64_t blocks = 0;
+        bisim_status st = refine_round(ctx, s, &blocks);
+        if (st != BISIM_OK) {
+            unpin_partition(ctx, s);
+            return st;
+        }
+        ++executed;
+        if (blocks == prev) {   // P_{i+1} refines P_i with as many blocks: P_{i+1} = P_i
+            rounds = (k == BISIM_FIXPOINT) ? i : k;
+            break;
+        }
+        prev = blocks;
+    }
+    unpin_partition(ctx, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "refinement rounds");
+    ctx->cur_k = rounds;
+    ctx->stats.rounds = rounds;
+    ctx->stats.rounds_executed = executed;
+    ctx->stats.num_blocks = prev;
+    *out_rounds = rounds;
+    *out_executed = executed;
+    *out_blocks = prev;
+    return BISIM_OK;
+}
+
 }  // namespace bisim
 
 using namespace bisim;
@@ -348,46 +406,49 @@ bisim_status bisim_iterate(bisim_ctx* ctx, int32_t k, int32_t cap, int32_t* out_
     if (k < BISIM_FIXPOINT) return set_error(ctx, BISIM_EINVAL, "k must be >= 0 or BISIM_FIXPOINT");
     if (k == BISIM_FIXPOINT && cap < 0) return set_error(ctx, BISIM_EINVAL, "cap must be >= 0");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    if (ctx->n > 0)
-        cudaMemcpyAsync(ctx->P[0], ctx->P0, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToDevice, s);
-    ctx->cur = 0;
-    int64_t prev = ctx->last_blocks;
-    // ctx->last_blocks holds |P_0| after init; keep it for the next call
-    const int64_t p0_blocks = ctx->last_blocks;
-    const int32_t limit = (k == BISIM_FIXPOINT) ? cap : k;
-    int32_t rounds = limit, executed = 0;
-    for (int32_t i = 0; i < limit; ++i) {
-        int64_t blocks = 0;
-        bisim_status st = refine_round(ctx, s, &blocks);
-        if (st != BISIM_OK) {
-            unpin_partition(ctx, s);
-            return st;
-        }
-        ++executed;
-        if (blocks == prev) {   // P_{i+1} refines P_i with as many blocks: P_{i+1} = P_i
-            rounds = (k == BISIM_FIXPOINT) ? i : k;
-            break;
-        }
-        prev = blocks;
-    }
-    unpin_partition(ctx, s);
-    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "bisim_iterate");
-    ctx->last_blocks = p0_blocks;
-    ctx->stats.rounds = rounds;
-    ctx->stats.rounds_executed = executed;
-    ctx->stats.num_blocks = prev;
+    bisim_status st;
+    if ((st = refresh_after_edit(ctx, s)) != BISIM_OK) return st;
+    int32_t rounds = 0, executed = 0;
+    int64_t blocks = 0;
+    if ((st = run_rounds(ctx, k, cap, s, &rounds, &executed, &blocks)) != BISIM_OK) return st;
     if (out_rounds) *out_rounds = rounds;
-    if (out_num_blocks) *out_num_blocks = prev;
+    if (out_num_blocks) *out_num_blocks = blocks;
     return BISIM_OK;
 }
 
 bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, void* stream) {
-    (void)ops;
-    (void)n_ops;
-    (void)stream;
     if (ctx == nullptr) return set_error(nullptr, BISIM_EINVAL, "ctx is NULL");
-    return set_error(ctx, BISIM_ESTATE, "apply_updates is not available in this build");
+    if (n_ops < 0 || (n_ops > 0 && ops == nullptr)) return set_error(ctx, BISIM_EINVAL, "invalid op array");
+    if (ctx->gid != nullptr) return set_error(ctx, BISIM_ESTATE, "apply_updates is not supported on batched contexts");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    bisim_status st = BISIM_OK;
+    if (n_ops > 0) {
+        std::vector<void*> temps;
+        const void* d_ops = nullptr;
+        if ((e = stage(ops, sizeof(bisim_op) * static_cast<size_t>(n_ops), s, &d_ops, temps)))
+            return cuda_error(ctx, e, "stage update batch");
+        uint8_t* flags = nullptr;
+        const size_t fb = 3 * static_cast<size_t>(ctx->n + 1);
+        if ((e = cudaMallocAsync(reinterpret_cast<void**>(&flags), fb, s))) {
+            free_temps(temps, s);
+            return cuda_error(ctx, e, "alloc update flags");
+        }
+        cudaMemsetAsync(flags, 0, fb, s);
+        st = apply_ops_to_graph(ctx, static_cast<const bisim_op*>(d_ops), n_ops, flags, flags + (ctx->n + 1),
+                                flags + 2 * (ctx->n + 1), s);
+        cudaFreeAsync(flags, s);
+        free_temps(temps, s);
+        if (st != BISIM_OK) return st;
+        ctx->buckets_dirty = true;
+    }
+    // bring the partition up to date at k_incremental rounds
+    if ((st = refresh_after_edit(ctx, s)) != BISIM_OK) return st;
+    int32_t rounds = 0, executed = 0;
+    int64_t blocks = 0;
+    if ((st = run_rounds(ctx, ctx->opt.k_incremental, 0, s, &rounds, &executed, &blocks)) != BISIM_OK) return st;
+    ctx->stats.last_frontier = ctx->n;
+    return BISIM_OK;
 }
 
 bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream) {

@@ -214,6 +214,13 @@ struct bisim_ctx {
     bisim::DevState* dstate = nullptr;
     bisim::DevState* hstate = nullptr;   // pinned mirror
 
+    // updates
+    int32_t* esrc = nullptr;       // source vertex of every CSR edge (kept once updates start)
+    int64_t esrc_cap = 0;
+    int64_t skey_cap = 0;          // capacity of skey in values
+    bool buckets_dirty = false;    // degree buckets no longer match the CSR
+    int32_t cur_k = 0;             // rounds of the current partition
+
     // bookkeeping
     std::vector<void*> allocs;
     int64_t device_bytes = 0;
@@ -257,5 +264,18 @@ bisim_status refine_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks);
 bisim_status alloc_refine_state(bisim_ctx* ctx, cudaStream_t s);
 void unpin_partition(bisim_ctx* ctx, cudaStream_t s);
 void launch_local_ids(const bisim_ctx* ctx, int32_t* out, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- updates (update.cu)
+
+void ctx_free(bisim_ctx* ctx, void* p, size_t bytes, cudaStream_t s);
+bisim_status ensure_edge_sources(bisim_ctx* ctx, cudaStream_t s);
+bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, uint8_t* vchanged,
+                                uint8_t* rowchg, uint8_t* killed, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- rounds (api.cu)
+
+bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
+                        int32_t* out_executed, int64_t* out_blocks);
+bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s);
 
 }  // namespace bisim

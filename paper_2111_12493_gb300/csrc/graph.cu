@@ -249,6 +249,22 @@ bisim_status build_from_csr(bisim_ctx* ctx, const int64_t* row_ptr, const int32_
 bisim_status build_buckets(bisim_ctx* ctx, cudaStream_t s) {
     const int32_t n = ctx->n;
     cudaError_t e;
+    // a rebuild after the graph changed: release the previous layout
+    ctx_free(ctx, ctx->class_list, sizeof(int32_t) * std::max(n, 1), s);
+    ctx_free(ctx, ctx->chunks, sizeof(HubChunk) * ctx->n_chunks, s);
+    ctx_free(ctx, ctx->hub_toff, sizeof(int64_t) * ctx->n_hub, s);
+    ctx_free(ctx, ctx->hub_tmask, sizeof(uint32_t) * ctx->n_hub, s);
+    ctx_free(ctx, ctx->hub_tab, sizeof(unsigned long long) * ctx->hub_tab_words, s);
+    ctx_free(ctx, ctx->hub_acc, sizeof(HubAcc) * ctx->n_hub, s);
+    ctx->class_list = nullptr;
+    ctx->chunks = nullptr;
+    ctx->hub_toff = nullptr;
+    ctx->hub_tmask = nullptr;
+    ctx->hub_tab = nullptr;
+    ctx->hub_acc = nullptr;
+    ctx->n_chunks = 0;
+    ctx->n_hub = 0;
+    ctx->hub_tab_words = 0;
     if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->class_list), sizeof(int32_t) * std::max(n, 1), s))) return cuda_error(ctx, e, "alloc class list");
     const size_t tmp_words = radix_temp_words(n);
     char* scratch = nullptr;
@@ -333,6 +349,7 @@ bisim_status build_buckets(bisim_ctx* ctx, cudaStream_t s) {
         cudaMemcpyAsync(ctx->chunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(ctx->hub_toff, toff.data(), sizeof(int64_t) * ctx->n_hub, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(ctx->hub_tmask, tmask.data(), sizeof(uint32_t) * ctx->n_hub, cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(ctx->hub_tab, 0, sizeof(unsigned long long) * words, s);
         if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "upload hub layout");
     }
     if ((e = cudaGetLastError())) return cuda_error(ctx, e, "build buckets");

@@ -1,0 +1,608 @@
+// Update batches on the device (Section 3.2: additions, deletions and
+// modifications of vertices and edges in an evolving graph).
+//
+// A batch is a list of operations with sequential semantics. It is applied in
+// parallel and exactly:
+//   * vertex operations are grouped by vertex (stable radix sort), which gives
+//     every vertex its final state and lets each EDGE_ADD check that both
+//     endpoints are live at its own position in the batch;
+//   * edge operations are grouped by edge key (u, w, l); for one key the
+//     multiplicity after the batch is a fold over its operations in order
+//     (ADD +1, DEL -1 floored at 0), started after the last deletion of u or w
+//     (which removes every edge of the vertex at that moment);
+//   * the out-CSR is rewritten once: initial edges incident to a deleted vertex
+//     and the first r occurrences of a key that lost r copies are dropped, and
+//     the added copies are appended to their rows.
+// A batch that names an out-of-range vertex, an unknown kind, or an EDGE_ADD
+// with an endpoint that is dead at that point is rejected before anything
+// changes.
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+#include "prof.cuh"
+
+namespace bisim {
+
+namespace {
+
+constexpr uint64_t kSaltEdgeKey = 0x452821e638d01377ull;
+constexpr unsigned kErrBadOp = 8u;
+constexpr unsigned kErrDeadEndpoint = 16u;
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+unsigned grid_for(int64_t n, int threads) {
+    return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(cdiv(n, threads), 1 << 20)));
+}
+
+__device__ __forceinline__ uint64_t edge_key_hash(int32_t u, int32_t w, int32_t l) {
+    const uint64_t uw = (static_cast<uint64_t>(static_cast<uint32_t>(u)) << 32) | static_cast<uint32_t>(w);
+    return mix64(uw ^ mix64(static_cast<uint64_t>(static_cast<uint32_t>(l)) ^ kSaltEdgeKey));
+}
+
+// ----------------------------------------------------------------------------- checks and grouping
+
+__global__ void k_ops_check(const bisim_op* __restrict__ ops, int64_t nops, int32_t n, DevState* st,
+                            uint32_t* __restrict__ vkey, uint64_t* __restrict__ vval) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nops;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const bisim_op o = ops[i];
+        bool ok = o.kind >= BISIM_OP_EDGE_ADD && o.kind <= BISIM_OP_VERTEX_DEL && o.src >= 0 && o.src < n;
+        const bool edge = o.kind == BISIM_OP_EDGE_ADD || o.kind == BISIM_OP_EDGE_DEL;
+        if (edge) ok = ok && o.dst >= 0 && o.dst < n;
+        if (!ok) atomicOr(&st->error, kErrBadOp);
+        // vertex operations sort by vertex; edge operations go last, in batch order
+        vkey[i] = (ok && !edge) ? static_cast<uint32_t>(o.src) : 0xffffffffu;
+        vval[i] = static_cast<uint64_t>(i);
+        if (ok && !edge) atomicAdd(&st->aux, 1ull);
+    }
+}
+
+struct VertexOps {
+    const uint32_t* key;     // sorted vertex of each vertex operation, [0, nv)
+    const uint64_t* pos;     // its position in the batch (ascending within a vertex)
+    int64_t nv;
+    const bisim_op* ops;
+    const uint8_t* alive0;   // state before the batch (null: all live)
+};
+
+__device__ __forceinline__ int64_t lower_bound_u32(const uint32_t* a, int64_t n, uint32_t x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Is vertex x live just before position p of the batch?
+__device__ bool alive_before(const VertexOps& V, int32_t x, uint64_t p) {
+    const int64_t lo = lower_bound_u32(V.key, V.nv, static_cast<uint32_t>(x));
+    int64_t hi = lo;
+    while (hi < V.nv && V.key[hi] == static_cast<uint32_t>(x) && V.pos[hi] < p) ++hi;
+    if (hi == lo) return V.alive0 == nullptr || V.alive0[x] != 0;
+    return V.ops[V.pos[hi - 1]].kind == BISIM_OP_VERTEX_ADD;
+}
+
+// Position of the last deletion of x in the batch, or -1.
+__device__ int64_t last_kill(const VertexOps& V, int32_t x) {
+    const int64_t lo = lower_bound_u32(V.key, V.nv, static_cast<uint32_t>(x));
+    int64_t last = -1;
+    for (int64_t i = lo; i < V.nv && V.key[i] == static_cast<uint32_t>(x); ++i)
+        if (V.ops[V.pos[i]].kind == BISIM_OP_VERTEX_DEL) last = static_cast<int64_t>(V.pos[i]);
+    return last;
+}
+
+// Final state of every vertex named by a vertex operation.
+__global__ void k_vertex_final(VertexOps V, uint8_t* __restrict__ alive, int32_t* __restrict__ vlabel,
+                               uint8_t* __restrict__ killed, uint8_t* __restrict__ vchanged) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < V.nv;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t x = V.key[i];
+        if (V.ops[V.pos[i]].kind == BISIM_OP_VERTEX_DEL) killed[x] = 1;
+        if (i + 1 < V.nv && V.key[i + 1] == x) continue;   // the last operation on x decides
+        const bisim_op o = V.ops[V.pos[i]];
+        const uint8_t was = alive[x];
+        const int32_t lab = vlabel[x];
+        if (o.kind == BISIM_OP_VERTEX_ADD) {
+            alive[x] = 1;
+            vlabel[x] = o.label;
+            if (!was || lab != o.label) vchanged[x] = 1;
+        } else {
+            alive[x] = 0;
+            if (was) vchanged[x] = 1;
+        }
+    }
+}
+
+// Every EDGE_ADD needs both endpoints live at its position; also emits the
+// edge-key hash of every edge operation for grouping.
+__global__ void k_edge_ops(VertexOps V, const uint64_t* __restrict__ epos, int64_t ne,
+                           uint32_t* __restrict__ klo, uint32_t* __restrict__ khi, uint64_t* __restrict__ kval,
+                           DevState* st) {
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < ne;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t p = epos[j];
+        const bisim_op o = V.ops[p];
+        if (o.kind == BISIM_OP_EDGE_ADD && (!alive_before(V, o.src, p) || !alive_before(V, o.dst, p)))
+            atomicOr(&st->error, kErrDeadEndpoint);
+        const uint64_t h = edge_key_hash(o.src, o.dst, o.label);
+        klo[j] = static_cast<uint32_t>(h);
+        khi[j] = static_cast<uint32_t>(h >> 32);
+        kval[j] = p;
+    }
+}
+
+// Key-hash halves of edge operations given in some order of positions.
+__global__ void k_key_halves(const bisim_op* __restrict__ ops, const uint64_t* __restrict__ pos, int64_t ne,
+                             uint32_t* __restrict__ lo, uint32_t* __restrict__ hi) {
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < ne;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const bisim_op o = ops[pos[j]];
+        const uint64_t h = edge_key_hash(o.src, o.dst, o.label);
+        if (lo) lo[j] = static_cast<uint32_t>(h);
+        if (hi) hi[j] = static_cast<uint32_t>(h >> 32);
+    }
+}
+
+struct RemoveRec {
+    int32_t u, w, l, count;
+};
+struct AddRec {
+    int32_t u, w, l, pad;
+};
+
+// One CTA per run of equal key hashes (normally one key): count the key's
+// current copies in row u, fold the key's operations, and emit the net change.
+__global__ void __launch_bounds__(128) k_fold_keys(VertexOps V, const uint32_t* __restrict__ khi,
+                                                   const uint32_t* __restrict__ klo,
+                                                   const uint64_t* __restrict__ kpos, int64_t ne,
+                                                   const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                   const int32_t* __restrict__ elab,
+                                                   const uint8_t* __restrict__ killed,
+                                                   RemoveRec* __restrict__ rem, AddRec* __restrict__ add,
+                                                   unsigned long long* __restrict__ counters,
+                                                   uint8_t* __restrict__ rowchg) {
+    __shared__ int red[4];
+    for (int64_t i = blockIdx.x; i < ne; i += gridDim.x) {
+        const bool head = i == 0 || khi[i] != khi[i - 1] || klo[i] != klo[i - 1];
+        if (!head) continue;                                    // uniform across the CTA
+        int64_t end = i + 1;
+        while (end < ne && khi[end] == khi[i] && klo[end] == klo[i]) ++end;
+        // distinct full keys inside the run, in order of first appearance
+        for (int64_t a = i; a < end; ++a) {
+            const bisim_op oa = V.ops[kpos[a]];
+            bool first = true;
+            for (int64_t b = i; b < a; ++b) {
+                const bisim_op ob = V.ops[kpos[b]];
+                if (ob.src == oa.src && ob.dst == oa.dst && ob.label == oa.label) { first = false; break; }
+            }
+            if (!first) continue;
+            const int32_t u = oa.src, w = oa.dst, l = oa.label;
+            const bool dropped = killed[u] || killed[w];          // initial copies go with the deletion
+            int c0 = 0;
+            if (!dropped) {
+                int mine = 0;
+                for (int64_t e = rp[u] + threadIdx.x; e < rp[u + 1]; e += blockDim.x)
+                    mine += (col[e] == w && elab[e] == l) ? 1 : 0;
+                for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+                if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mine;
+                __syncthreads();
+                c0 = red[0] + red[1] + red[2] + red[3];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                const int64_t lk = max(last_kill(V, u), last_kill(V, w));
+                int c = dropped ? 0 : c0;
+                for (int64_t b = a; b < end; ++b) {
+                    const uint64_t p = kpos[b];
+                    const bisim_op ob = V.ops[p];
+                    if (ob.src != u || ob.dst != w || ob.label != l) continue;
+                    if (static_cast<int64_t>(p) < lk) continue;     // before the last deletion: no effect
+                    if (ob.kind == BISIM_OP_EDGE_ADD) ++c;
+                    else if (c > 0) --c;
+                }
+                const int adds = dropped ? c : max(c - c0, 0);
+                const int removes = dropped ? 0 : max(c0 - c, 0);
+                if (removes > 0) {
+                    const unsigned long long r = atomicAdd(&counters[0], 1ull);
+                    rem[r] = RemoveRec{u, w, l, removes};
+                }
+                if (adds > 0) {
+                    const unsigned long long base = atomicAdd(&counters[1], static_cast<unsigned long long>(adds));
+                    for (int q = 0; q < adds; ++q) add[base + q] = AddRec{u, w, l, 0};
+                }
+                if (adds > 0 || removes > 0) rowchg[u] = 1;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Marks the first `count` copies of (w, l) in row u (row order) as dropped.
+__global__ void __launch_bounds__(128) k_mark_removals(const RemoveRec* __restrict__ rem, int64_t nrem,
+                                                       const int64_t* __restrict__ rp,
+                                                       const int32_t* __restrict__ col,
+                                                       const int32_t* __restrict__ elab,
+                                                       uint8_t* __restrict__ drop) {
+    __shared__ int wsum[4];
+    __shared__ int running;
+    for (int64_t r = blockIdx.x; r < nrem; r += gridDim.x) {
+        const RemoveRec R = rem[r];
+        if (threadIdx.x == 0) running = 0;
+        __syncthreads();
+        for (int64_t e0 = rp[R.u]; e0 < rp[R.u + 1]; e0 += blockDim.x) {
+            const int64_t e = e0 + threadIdx.x;
+            const int hit = (e < rp[R.u + 1] && col[e] == R.w && elab[e] == R.l) ? 1 : 0;
+            const unsigned ball = __ballot_sync(0xffffffffu, hit);
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            if (lane == 0) wsum[warp] = __popc(ball);
+            __syncthreads();
+            int before = running;
+            for (int q = 0; q < warp; ++q) before += wsum[q];
+            const int rank = before + __popc(ball & ((1u << lane) - 1u));
+            if (hit && rank < R.count) drop[e] = 1;
+            __syncthreads();
+            if (threadIdx.x == 0) running += wsum[0] + wsum[1] + wsum[2] + wsum[3];
+            __syncthreads();
+            if (running >= R.count) break;
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------- CSR rewrite
+
+__global__ void k_count_kept(const int32_t* __restrict__ esrc, const int32_t* __restrict__ col, int64_t m,
+                             const uint8_t* __restrict__ killed, const uint8_t* __restrict__ drop,
+                             int32_t* __restrict__ kept, uint8_t* __restrict__ rowdirty,
+                             uint8_t* __restrict__ rowchg) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t e0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; e0 < m; e0 += stride) {
+        const int64_t e = e0 + threadIdx.x;
+        int32_t u = -1;
+        bool keep = false;
+        if (e < m) {
+            u = esrc[e];
+            keep = !(killed[u] || killed[col[e]] || drop[e]);
+            if (!keep) {
+                rowdirty[u] = 1;
+                rowchg[u] = 1;
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, u);
+        const unsigned keepers = __ballot_sync(0xffffffffu, keep) & peers;
+        if (e < m && (threadIdx.x & 31) == static_cast<unsigned>(__ffs(peers) - 1) && keepers)
+            atomicAdd(&kept[u], __popc(keepers));
+    }
+}
+
+__global__ void k_count_adds(const AddRec* __restrict__ add, int64_t nadd, int32_t* __restrict__ addcnt) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nadd;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        atomicAdd(&addcnt[add[i].u], 1);
+}
+
+__global__ void k_new_degree(const int32_t* __restrict__ kept, const int32_t* __restrict__ addcnt, int32_t n,
+                             int64_t* __restrict__ deg) {
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v < n) deg[v] = static_cast<int64_t>(kept[v]) + addcnt[v];
+    if (v == n) deg[v] = 0;
+}
+
+// Rows without a dropped edge: every edge moves by the row's offset change.
+__global__ void k_copy_clean(const int32_t* __restrict__ esrc, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ elab, int64_t m, const int64_t* __restrict__ rp,
+                             const int64_t* __restrict__ nrp, const uint8_t* __restrict__ rowdirty,
+                             int32_t* __restrict__ ncol, int32_t* __restrict__ nelab, int32_t* __restrict__ nsrc) {
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t u = esrc[e];
+        if (rowdirty[u]) continue;
+        const int64_t p = nrp[u] + (e - rp[u]);
+        ncol[p] = col[e];
+        nelab[p] = elab[e];
+        nsrc[p] = u;
+    }
+}
+
+// Rows with dropped edges: one CTA compacts the row, keeping row order.
+__global__ void __launch_bounds__(128) k_copy_dirty(const int32_t* __restrict__ rows, int64_t nrows,
+                                                    const int32_t* __restrict__ col, const int32_t* __restrict__ elab,
+                                                    const int64_t* __restrict__ rp, const int64_t* __restrict__ nrp,
+                                                    const uint8_t* __restrict__ killed,
+                                                    const uint8_t* __restrict__ drop, int32_t* __restrict__ ncol,
+                                                    int32_t* __restrict__ nelab, int32_t* __restrict__ nsrc) {
+    __shared__ int wsum[4];
+    __shared__ int running;
+    for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int32_t u = rows[r];
+        if (threadIdx.x == 0) running = 0;
+        __syncthreads();
+        const bool uk = killed[u] != 0;
+        for (int64_t e0 = rp[u]; e0 < rp[u + 1]; e0 += blockDim.x) {
+            const int64_t e = e0 + threadIdx.x;
+            const int keep = (e < rp[u + 1] && !uk && !killed[col[e]] && !drop[e]) ? 1 : 0;
+            const unsigned ball = __ballot_sync(0xffffffffu, keep);
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            if (lane == 0) wsum[warp] = __popc(ball);
+            __syncthreads();
+            int before = running;
+            for (int q = 0; q < warp; ++q) before += wsum[q];
+            if (keep) {
+                const int64_t p = nrp[u] + before + __popc(ball & ((1u << lane) - 1u));
+                ncol[p] = col[e];
+                nelab[p] = elab[e];
+                nsrc[p] = u;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) running += wsum[0] + wsum[1] + wsum[2] + wsum[3];
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void k_rows_flagged(const uint8_t* __restrict__ flag, int32_t n, int32_t* __restrict__ out,
+                               unsigned long long* __restrict__ count) {
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const bool f = v < n && flag[v];
+    const unsigned ball = __ballot_sync(0xffffffffu, f);
+    if (!ball) return;
+    const int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == __ffs(ball) - 1) base = atomicAdd(count, static_cast<unsigned long long>(__popc(ball)));
+    base = __shfl_sync(0xffffffffu, base, __ffs(ball) - 1);
+    if (f) out[base + __popc(ball & ((1u << lane) - 1u))] = static_cast<int32_t>(v);
+}
+
+// Appended copies: one thread per record; records of a row are counted in order.
+__global__ void k_place_adds(const AddRec* __restrict__ add, int64_t nadd, const int64_t* __restrict__ nrp,
+                             const int32_t* __restrict__ kept, int32_t* __restrict__ cursor,
+                             int32_t* __restrict__ ncol, int32_t* __restrict__ nelab, int32_t* __restrict__ nsrc) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nadd;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const AddRec a = add[i];
+        const int slot = atomicAdd(&cursor[a.u], 1);
+        const int64_t p = nrp[a.u] + kept[a.u] + slot;
+        ncol[p] = a.w;
+        nelab[p] = a.l;
+        nsrc[p] = a.u;
+    }
+}
+
+__global__ void k_fill_src(const int64_t* __restrict__ rp, int32_t n, int32_t* __restrict__ esrc) {
+    // one warp per vertex
+    const int64_t v = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (v >= n) return;
+    for (int64_t e = rp[v] + (threadIdx.x & 31); e < rp[v + 1]; e += 32) esrc[e] = static_cast<int32_t>(v);
+}
+
+}  // namespace
+
+// Frees one buffer owned by ctx (stream-ordered).
+void ctx_free(bisim_ctx* ctx, void* p, size_t bytes, cudaStream_t s) {
+    if (p == nullptr) return;
+    auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+    if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+    ctx->device_bytes -= static_cast<int64_t>(bytes);
+    cudaFreeAsync(p, s);
+}
+
+// Per-edge source array for the current CSR (needed to rewrite it edge-parallel).
+bisim_status ensure_edge_sources(bisim_ctx* ctx, cudaStream_t s) {
+    if (ctx->esrc != nullptr) return BISIM_OK;
+    cudaError_t e;
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->esrc), sizeof(int32_t) * std::max<int64_t>(ctx->m, 1), s)))
+        return cuda_error(ctx, e, "alloc edge sources");
+    ctx->esrc_cap = std::max<int64_t>(ctx->m, 1);
+    if (ctx->n > 0) {
+        BISIM_SITE(site, "edge_sources");
+        Launch L(site, s, ctx->n, ctx->m, 8.0 * ctx->n + 4.0 * ctx->m);
+        k_fill_src<<<grid_for(static_cast<int64_t>(ctx->n) * 32, 256), 256, 0, s>>>(ctx->row_ptr, ctx->n, ctx->esrc);
+    }
+    if (!ctx->alive) {
+        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->alive), std::max(ctx->n, 1), s)))
+            return cuda_error(ctx, e, "alloc alive");
+        cudaMemsetAsync(ctx->alive, 1, std::max(ctx->n, 1), s);
+    }
+    return BISIM_OK;
+}
+
+bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, uint8_t* vchanged,
+                                uint8_t* rowchg, uint8_t* killed, cudaStream_t s) {
+    const int32_t n = ctx->n;
+    const int64_t m = ctx->m;
+    cudaError_t e;
+    bisim_status st;
+    if ((st = ensure_edge_sources(ctx, s)) != BISIM_OK) return st;
+
+    // scratch for the batch
+    const size_t tmpw = std::max(radix_temp_words(std::max<int64_t>(nops, 1)), scan_temp_words(n + 1));
+    const size_t nb = static_cast<size_t>(std::max<int64_t>(nops, 1));
+    size_t bytes = 0;
+    auto need = [&](size_t b) { bytes += (b + 255) & ~size_t(255); };
+    need(4 * nb); need(4 * nb); need(8 * nb); need(8 * nb);          // vertex-op keys / values (x2)
+    need(4 * nb); need(4 * nb); need(4 * nb); need(4 * nb);          // edge key halves (x2 each)
+    need(8 * nb); need(8 * nb); need(8 * nb); need(8 * nb);          // edge positions (x4)
+    need(sizeof(RemoveRec) * nb); need(sizeof(AddRec) * nb);
+    need(8 * 4);
+    need(8 * tmpw);
+    need(std::max<int64_t>(m, 1));                                    // drop flags
+    need(4 * (n + 1)); need(4 * (n + 1)); need(4 * (n + 1));          // kept, addcnt, cursor
+    need(1 * (n + 1));                                                // rowdirty
+    need(4 * (n + 1));                                                // dirty row list
+    need(8 * (n + 1));                                                // new degree
+    char* scratch = nullptr;
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s))) return cuda_error(ctx, e, "alloc update scratch");
+    char* base = scratch;
+    auto carve = [&](size_t b) { char* p = scratch; scratch += (b + 255) & ~size_t(255); return p; };
+    uint32_t* vk0 = reinterpret_cast<uint32_t*>(carve(4 * nb));
+    uint32_t* vk1 = reinterpret_cast<uint32_t*>(carve(4 * nb));
+    uint64_t* vv0 = reinterpret_cast<uint64_t*>(carve(8 * nb));
+    uint64_t* vv1 = reinterpret_cast<uint64_t*>(carve(8 * nb));
+    uint32_t* klo0 = reinterpret_cast<uint32_t*>(carve(4 * nb));
+    uint32_t* klo1 = reinterpret_cast<uint32_t*>(carve(4 * nb));
+    uint32_t* khi0 = reinterpret_cast<uint32_t*>(carve(4 * nb));
+    uint32_t* khi1 = reinterpret_cast<uint32_t*>(carve(4 * nb));
+    uint64_t* kp0 = reinterpret_cast<uint64_t*>(carve(8 * nb));
+    uint64_t* kp1 = reinterpret_cast<uint64_t*>(carve(8 * nb));
+    uint64_t* kp2 = reinterpret_cast<uint64_t*>(carve(8 * nb));
+    uint64_t* kp3 = reinterpret_cast<uint64_t*>(carve(8 * nb));
+    RemoveRec* rem = reinterpret_cast<RemoveRec*>(carve(sizeof(RemoveRec) * nb));
+    AddRec* add = reinterpret_cast<AddRec*>(carve(sizeof(AddRec) * nb));
+    unsigned long long* counters = reinterpret_cast<unsigned long long*>(carve(8 * 4));
+    int64_t* tmp = reinterpret_cast<int64_t*>(carve(8 * tmpw));
+    uint8_t* drop = reinterpret_cast<uint8_t*>(carve(std::max<int64_t>(m, 1)));
+    int32_t* kept = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
+    int32_t* addcnt = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
+    int32_t* cursor = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
+    uint8_t* rowdirty = reinterpret_cast<uint8_t*>(carve(n + 1));
+    int32_t* dirty_rows = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
+    int64_t* ndeg = reinterpret_cast<int64_t*>(carve(8 * (n + 1)));
+    auto fail = [&](bisim_status code, const char* msg) {
+        cudaFreeAsync(base, s);
+        return set_error(ctx, code, msg);
+    };
+
+    BISIM_SITE(site_ops, "update_ops");
+    // 1. check kinds and ranges; group vertex operations by vertex
+    cudaMemsetAsync(ctx->dstate, 0, sizeof(DevState), s);
+    {
+        Launch L(site_ops, s, 0, 0, 16.0 * nops);
+        k_ops_check<<<grid_for(nops, 256), 256, 0, s>>>(d_ops, nops, n, ctx->dstate, vk0, vv0);
+    }
+    int which = radix_sort_pairs(vk0, vv0, vk1, vv1, nops, 32, tmp, s);
+    const uint32_t* vkey = which ? vk1 : vk0;
+    const uint64_t* vpos = which ? vv1 : vv0;
+    cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); return cuda_error(ctx, e, "check update batch"); }
+    if (ctx->hstate->error & kErrBadOp) return fail(BISIM_EINVAL, "update batch names an out-of-range vertex or an unknown kind");
+    const int64_t nv = static_cast<int64_t>(ctx->hstate->aux);
+    const int64_t ne = nops - nv;
+    VertexOps V{vkey, vpos, nv, d_ops, ctx->alive};
+
+    // 2. EDGE_ADD liveness and edge-key hashes, then group edge operations by key
+    if (ne > 0) {
+        Launch L(site_ops, s, 0, 0, 24.0 * ne);
+        k_edge_ops<<<grid_for(ne, 256), 256, 0, s>>>(V, vpos + nv, ne, klo0, khi0, kp0, ctx->dstate);
+    }
+    cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); return cuda_error(ctx, e, "check edge operations"); }
+    if (ctx->hstate->error & kErrDeadEndpoint) return fail(BISIM_EINVAL, "EDGE_ADD with an endpoint that is dead at that point of the batch");
+
+    // ---- from here on the batch is valid and the graph changes ----
+    // stable LSD sort of the edge operations by key hash: low half, then high
+    // half; operations of one key stay in batch order
+    const uint32_t *skhi = khi0, *sklo = klo0;
+    const uint64_t* skp = kp0;
+    if (ne > 0) {
+        const int wa = radix_sort_pairs(klo0, kp0, klo1, kp1, ne, 32, tmp, s);
+        const uint64_t* posA = wa ? kp1 : kp0;
+        k_key_halves<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, posA, ne, nullptr, khi0);
+        cudaMemcpyAsync(kp2, posA, 8 * ne, cudaMemcpyDeviceToDevice, s);
+        const int wb = radix_sort_pairs(khi0, kp2, khi1, kp3, ne, 32, tmp, s);
+        skhi = wb ? khi1 : khi0;
+        skp = wb ? kp3 : kp2;
+        k_key_halves<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, skp, ne, klo0, nullptr);
+        sklo = klo0;
+    }
+    cudaMemsetAsync(killed, 0, n + 1, s);
+    cudaMemsetAsync(counters, 0, 8 * 4, s);
+    if (nv > 0) {
+        Launch L(site_ops, s, 0, 0, 16.0 * nv);
+        k_vertex_final<<<grid_for(nv, 256), 256, 0, s>>>(V, ctx->alive, ctx->vlabel, killed, vchanged);
+    }
+    if (ne > 0) {
+        Launch L(site_ops, s, 0, 0, 32.0 * ne);
+        k_fold_keys<<<grid_for(ne, 1), 128, 0, s>>>(V, skhi, sklo, skp, ne, ctx->row_ptr, ctx->col, ctx->elab, killed,
+                                                   rem, add, counters, rowchg);
+    }
+    unsigned long long hc[2] = {0, 0};
+    cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); return cuda_error(ctx, e, "fold edge operations"); }
+    const int64_t nrem = static_cast<int64_t>(hc[0]);
+    const int64_t nadd = static_cast<int64_t>(hc[1]);
+
+    // 3. rewrite the CSR
+    BISIM_SITE(site_csr, "update_csr");
+    cudaMemsetAsync(drop, 0, std::max<int64_t>(m, 1), s);
+    cudaMemsetAsync(kept, 0, 4 * (n + 1), s);
+    cudaMemsetAsync(addcnt, 0, 4 * (n + 1), s);
+    cudaMemsetAsync(cursor, 0, 4 * (n + 1), s);
+    cudaMemsetAsync(rowdirty, 0, n + 1, s);
+    if (nrem > 0) {
+        Launch L(site_csr, s, 0, 0, 16.0 * nrem);
+        k_mark_removals<<<grid_for(nrem, 1), 128, 0, s>>>(rem, nrem, ctx->row_ptr, ctx->col, ctx->elab, drop);
+    }
+    if (m > 0) {
+        Launch L(site_csr, s, 0, m, 9.0 * m);
+        k_count_kept<<<grid_for(m, 256), 256, 0, s>>>(ctx->esrc, ctx->col, m, killed, drop, kept, rowdirty, rowchg);
+    }
+    if (nadd > 0) {
+        Launch L(site_csr, s, 0, 0, 16.0 * nadd);
+        k_count_adds<<<grid_for(nadd, 256), 256, 0, s>>>(add, nadd, addcnt);
+    }
+    {
+        Launch L(site_csr, s, n, 0, 16.0 * n);
+        k_new_degree<<<grid_for(n + 1, 256), 256, 0, s>>>(kept, addcnt, n, ndeg);
+    }
+    int64_t* nrp = nullptr;
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&nrp), sizeof(int64_t) * (n + 1), s))) {
+        cudaFreeAsync(base, s);
+        return cuda_error(ctx, e, "alloc row_ptr");
+    }
+    exclusive_scan_i64(ndeg, nrp, n + 1, tmp, s);
+    int64_t new_m = 0;
+    cudaMemcpyAsync(&new_m, nrp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    unsigned long long ndirty = 0;
+    cudaMemsetAsync(counters + 2, 0, 8, s);
+    if (n > 0) {
+        Launch L(site_csr, s, n, 0, 5.0 * n);
+        k_rows_flagged<<<grid_for(n, 256), 256, 0, s>>>(rowdirty, n, dirty_rows, counters + 2);
+    }
+    cudaMemcpyAsync(&ndirty, counters + 2, 8, cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); cudaFreeAsync(nrp, s); return cuda_error(ctx, e, "size new CSR"); }
+    int32_t *ncol = nullptr, *nelab = nullptr, *nsrc = nullptr;
+    const size_t cap = static_cast<size_t>(std::max<int64_t>(new_m, 1));
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&ncol), 4 * cap, s)) ||
+        (e = cudaMallocAsync(reinterpret_cast<void**>(&nelab), 4 * cap, s)) ||
+        (e = cudaMallocAsync(reinterpret_cast<void**>(&nsrc), 4 * cap, s))) {
+        cudaFreeAsync(base, s);
+        return cuda_error(ctx, e, "alloc new CSR");
+    }
+    if (m > 0) {
+        Launch L(site_csr, s, 0, m, 24.0 * m);
+        k_copy_clean<<<grid_for(m, 256), 256, 0, s>>>(ctx->esrc, ctx->col, ctx->elab, m, ctx->row_ptr, nrp, rowdirty,
+                                                     ncol, nelab, nsrc);
+    }
+    if (ndirty > 0) {
+        Launch L(site_csr, s, static_cast<int64_t>(ndirty), 0, 0.0);
+        k_copy_dirty<<<grid_for(static_cast<int64_t>(ndirty), 1), 128, 0, s>>>(dirty_rows, static_cast<int64_t>(ndirty),
+                                                                               ctx->col, ctx->elab, ctx->row_ptr, nrp,
+                                                                               killed, drop, ncol, nelab, nsrc);
+    }
+    if (nadd > 0) {
+        Launch L(site_csr, s, 0, nadd, 24.0 * nadd);
+        k_place_adds<<<grid_for(nadd, 256), 256, 0, s>>>(add, nadd, nrp, kept, cursor, ncol, nelab, nsrc);
+    }
+    // swap in the new CSR
+    ctx_free(ctx, ctx->col, 4 * static_cast<size_t>(std::max<int64_t>(m, 1)), s);
+    ctx_free(ctx, ctx->elab, 4 * static_cast<size_t>(std::max<int64_t>(m, 1)), s);
+    ctx_free(ctx, ctx->esrc, 4 * static_cast<size_t>(ctx->esrc_cap), s);
+    ctx->col = ncol;
+    ctx->elab = nelab;
+    ctx->esrc = nsrc;
+    ctx->esrc_cap = static_cast<int64_t>(cap);
+    for (void* p : {static_cast<void*>(ncol), static_cast<void*>(nelab), static_cast<void*>(nsrc)}) ctx->allocs.push_back(p);
+    ctx->device_bytes += 12 * static_cast<int64_t>(cap);
+    cudaMemcpyAsync(ctx->row_ptr, nrp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s);
+    cudaFreeAsync(nrp, s);
+    cudaFreeAsync(base, s);
+    ctx->m = new_m;
+    ctx->stats.n_edges = new_m;
+    ctx->stats.updates_applied += nops;
+    if ((e = cudaGetLastError())) return cuda_error(ctx, e, "apply update batch");
+    return BISIM_OK;
+}
+
+}  // namespace bisim

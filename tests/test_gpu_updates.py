@@ -1,0 +1,183 @@
+"""apply_updates against the oracle: after every batch the maintained
+partition must equal a batch refinement of the edited graph (Theorem 2 and
+its corollary, Section 3.2.2), and invalid batches must change nothing."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_12493_gb300 import graphgen
+from refcheck import edges_to_arrays, parse_golden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2111_12493_gb300 import bisim
+    return bisim
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def random_batch(rng, state, size, n_elabels=4, n_vlabels=3, p_bad=0.0):
+    """Ops drawn against the evolving state so that most are meaningful."""
+    n = state["n"]
+    alive = state["alive"].astype(bool).copy()
+    edges = list(zip(state["src"].tolist(), state["dst"].tolist(), state["elabel"].tolist()))
+    ops = []
+    for _ in range(size):
+        r = rng.random()
+        live = np.flatnonzero(alive)
+        if r < 0.45 and len(live):
+            u, w = rng.choice(live), rng.choice(live)
+            ops.append((0, u, w, rng.integers(n_elabels)))
+            edges.append((u, w, ops[-1][3]))
+        elif r < 0.70 and edges:
+            e = edges[rng.integers(len(edges))]
+            ops.append((1, *e))                           # may already be gone: a no-op then
+        elif r < 0.78:
+            ops.append((1, rng.integers(n), rng.integers(n), rng.integers(n_elabels)))   # mostly absent
+        elif r < 0.86:
+            v = rng.integers(n)
+            ops.append((3, v, 0, 0))
+            alive[v] = False
+            edges = [e for e in edges if e[0] != v and e[1] != v]
+        else:
+            v = rng.integers(n)
+            ops.append((2, v, 0, rng.integers(n_vlabels)))
+            alive[v] = True
+    return np.array(ops, dtype=np.int32).reshape(-1, 4)
+
+
+def check_partition(B, ctx, state, k):
+    got = B.get_partition(ctx).cpu().numpy()
+    want, _, _ = oracle.refine(state["n"], state["src"], state["dst"], state["elabel"], state["vlabel"], k,
+                               alive=state["alive"])
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, f"{bad.size} differ; first {bad[:5]}: got {got[bad[:5]]} want {want[bad[:5]]}"
+
+
+@pytest.mark.parametrize("seed,k", [(0, 2), (1, 1), (2, 3), (3, 0)])
+def test_random_batches_match_batch_refinement(B, seed, k):
+    rng = np.random.default_rng(seed)
+    g = graphgen.uniform_graph(n=300, m=900, n_elabels=4, n_vlabels=3, seed=40 + seed)
+    state = dict(n=g["n"], alive=np.ones(g["n"], np.uint8), vlabel=g["vlabel"].copy(), src=g["src"],
+                 dst=g["dst"], elabel=g["elabel"])
+    opt = B.default_options(k_incremental=k)
+    ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]),
+                               options=opt)
+    for step in range(12):
+        ops = random_batch(rng, state, int(rng.integers(1, 60)))
+        try:
+            new_state = oracle.apply_ops(state, ops)
+        except oracle.UpdateRejected:
+            with pytest.raises(B.BisimError):
+                B.apply_updates(ctx, _dev(ops))
+            continue
+        B.apply_updates(ctx, _dev(ops))
+        state = new_state
+        check_partition(B, ctx, state, k)
+    B.summarize_destroy(ctx)
+
+
+def test_powerlaw_batches_with_hubs(B):
+    rng = np.random.default_rng(7)
+    g = graphgen.powerlaw_graph(n=5000, m=60_000, dmax=12_000, n_elabels=6, n_vlabels=4, seed=77)
+    state = dict(n=g["n"], alive=np.ones(g["n"], np.uint8), vlabel=g["vlabel"].copy(), src=g["src"],
+                 dst=g["dst"], elabel=g["elabel"])
+    ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]),
+                               options=B.default_options(k_incremental=2, mid_max_degree=1024))
+    for step in range(4):
+        ops = random_batch(rng, state, 300, n_elabels=6, n_vlabels=4)
+        try:
+            state2 = oracle.apply_ops(state, ops)
+        except oracle.UpdateRejected:
+            continue
+        B.apply_updates(ctx, _dev(ops))
+        state = state2
+        check_partition(B, ctx, state, 2)
+    B.summarize_destroy(ctx)
+
+
+def test_sequential_semantics_edge_cases(B):
+    # add then delete, delete absent, delete+re-add of a vertex with edges around it
+    n = 6
+    src = np.array([0, 0, 1, 2], np.int32)
+    dst = np.array([1, 1, 2, 3], np.int32)
+    lab = np.array([5, 5, 6, 7], np.int32)
+    vl = np.zeros(n, np.int32)
+    state = dict(n=n, alive=np.ones(n, np.uint8), vlabel=vl.copy(), src=src, dst=dst, elabel=lab)
+    ctx = B.summarize_init_coo(n, _dev(src), _dev(dst), _dev(lab), _dev(vl), options=B.default_options(k_incremental=2))
+    batches = [
+        [[0, 4, 5, 1], [1, 4, 5, 1]],                          # add then delete: nothing
+        [[1, 0, 1, 5]],                                        # one of two parallel copies
+        [[1, 3, 0, 9]],                                        # absent: no-op
+        [[3, 2, 0, 0], [2, 2, 0, 4], [0, 1, 2, 6], [0, 2, 3, 1]],   # kill 2, re-add, new edges
+        [[0, 5, 5, 2], [0, 5, 5, 2], [1, 5, 5, 2]],            # self-loop copies
+        [[2, 0, 0, 9]],                                        # relabel a live vertex
+    ]
+    for ops in batches:
+        ops = np.array(ops, np.int32)
+        state = oracle.apply_ops(state, ops)
+        B.apply_updates(ctx, _dev(ops))
+        check_partition(B, ctx, state, 2)
+    B.summarize_destroy(ctx)
+
+
+def test_rejected_batch_changes_nothing(B):
+    g = graphgen.uniform_graph(n=200, m=700, seed=5)
+    state = dict(n=g["n"], alive=np.ones(g["n"], np.uint8), vlabel=g["vlabel"].copy(), src=g["src"],
+                 dst=g["dst"], elabel=g["elabel"])
+    ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]))
+    B.apply_updates(ctx, _dev(np.array([[3, 7, 0, 0]], np.int32)))         # delete vertex 7
+    state = oracle.apply_ops(state, np.array([[3, 7, 0, 0]], np.int32))
+    before = B.get_partition(ctx).cpu().numpy()
+    for bad in ([[0, 1, 7, 0]],                                          # edge to a dead vertex
+                [[0, 1, 2, 0], [9, 0, 0, 0]],                            # unknown kind
+                [[0, 1, 200, 0]],                                        # out of range
+                [[2, 7, 0, 1], [3, 7, 0, 0], [0, 7, 1, 0]]):             # dead again at its position
+        with pytest.raises(B.BisimError) as ei:
+            B.apply_updates(ctx, _dev(np.array(bad, np.int32)))
+        assert ei.value.status == 1
+        assert np.array_equal(B.get_partition(ctx).cpu().numpy(), before)
+    # still consistent after the rejections
+    ops = np.array([[0, 1, 2, 0], [2, 7, 0, 2], [0, 7, 1, 3]], np.int32)
+    state = oracle.apply_ops(state, ops)
+    B.apply_updates(ctx, _dev(ops))
+    check_partition(B, ctx, state, 2)
+    B.summarize_destroy(ctx)
+
+
+def test_fig1_relabel_as_update(B):
+    gf = parse_golden("fig1_schemex_reconstructed.txt")
+    s, d, l = edges_to_arrays(gf["edges"])
+    vl = np.array(gf["vlabel"]["t"], np.int32)
+    ctx = B.summarize_init_coo(gf["n"], _dev(s), _dev(d), _dev(l), _dev(vl), options=B.default_options(k_incremental=1))
+    B.apply_updates(ctx, _dev(np.zeros((0, 4), np.int32)))
+    assert B.get_partition(ctx).cpu().tolist() == gf["expect"][("t", 1)].tolist()
+    B.apply_updates(ctx, _dev(np.array(gf["ops"]["t1"], np.int32)))
+    assert B.get_partition(ctx).cpu().tolist() == gf["expect"][("t1", 1)].tolist()
+    B.summarize_destroy(ctx)
+
+
+def test_iterate_after_updates_uses_the_edited_graph(B):
+    rng = np.random.default_rng(11)
+    g = graphgen.uniform_graph(n=400, m=1600, seed=12)
+    state = dict(n=g["n"], alive=np.ones(g["n"], np.uint8), vlabel=g["vlabel"].copy(), src=g["src"],
+                 dst=g["dst"], elabel=g["elabel"])
+    ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]))
+    ops = random_batch(rng, state, 80)
+    state = oracle.apply_ops(state, ops)
+    B.apply_updates(ctx, _dev(ops))
+    r, _ = B.bisim_iterate(ctx, oracle.FIXPOINT, 50)
+    want, wr, _ = oracle.refine(state["n"], state["src"], state["dst"], state["elabel"], state["vlabel"],
+                                oracle.FIXPOINT, 50, alive=state["alive"])
+    assert r == wr and np.array_equal(B.get_partition(ctx).cpu().numpy(), want)
+    B.summarize_destroy(ctx)
