@@ -63,6 +63,11 @@ enum { BISIM_FIXPOINT = -1 };
  * slowed the rest of the round more than it sped up the gathers. */
 enum { BISIM_FLAG_L2_PIN = 1 };
 
+/* BISIM_FLAG_FULL_RECOMPUTE: apply_updates recomputes all k_incremental
+ * rounds of the edited graph from scratch instead of maintaining the
+ * partition incrementally (same result; the reference point for latency). */
+enum { BISIM_FLAG_FULL_RECOMPUTE = 2 };
+
 /* Update operations (Section 3.2, incremental summarization of evolving graphs:
  * additions, deletions and modifications of vertices and edges). */
 enum {

@@ -435,14 +435,26 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
             return cuda_error(ctx, e, "alloc update flags");
         }
         cudaMemsetAsync(flags, 0, fb, s);
-        st = apply_ops_to_graph(ctx, static_cast<const bisim_op*>(d_ops), n_ops, flags, flags + (ctx->n + 1),
+        uint8_t* vchanged = flags;
+        uint8_t* rowchg = flags + (ctx->n + 1);
+        st = apply_ops_to_graph(ctx, static_cast<const bisim_op*>(d_ops), n_ops, vchanged, rowchg,
                                 flags + 2 * (ctx->n + 1), s);
-        cudaFreeAsync(flags, s);
         free_temps(temps, s);
+        if (st == BISIM_OK) {
+            ctx->buckets_dirty = true;
+            if (!(ctx->opt.flags & BISIM_FLAG_FULL_RECOMPUTE) && ctx->inc_k == ctx->opt.k_incremental)
+                st = inc_update(ctx, vchanged, rowchg, s);
+        }
+        cudaFreeAsync(flags, s);
         if (st != BISIM_OK) return st;
-        ctx->buckets_dirty = true;
+        if (!(ctx->opt.flags & BISIM_FLAG_FULL_RECOMPUTE) && ctx->inc_k == ctx->opt.k_incremental) return BISIM_OK;
     }
-    // bring the partition up to date at k_incremental rounds
+    if (!(ctx->opt.flags & BISIM_FLAG_FULL_RECOMPUTE)) {
+        // first batch (or k changed): build the incremental state of the current graph
+        if (ctx->inc_k != ctx->opt.k_incremental) return inc_build(ctx, s);
+        return write_current(ctx, s);
+    }
+    // full recompute at k_incremental rounds
     if ((st = refresh_after_edit(ctx, s)) != BISIM_OK) return st;
     int32_t rounds = 0, executed = 0;
     int64_t blocks = 0;

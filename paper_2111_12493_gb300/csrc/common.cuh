@@ -16,7 +16,8 @@ namespace bisim {
 constexpr int kSmallClasses = 4;          // thread-per-vertex classes: D = 4, 8, 16, 32
 constexpr int kMidClasses = 8;            // CTA-per-vertex classes: N = 64 .. 8192
 constexpr int kMidMaxN = 8192;            // largest CTA-path key count (64 KB of shared memory)
-constexpr int kHubChunkMax = 4096;        // hub-path edges per CTA (staged in shared memory)
+constexpr int kHubChunkMax = 4096;        // hub-path edges per CTA
+constexpr int kMaxIncLevels = 16;         // largest k_incremental
 constexpr int kClassHub = kSmallClasses + kMidClasses;   // 12
 constexpr int kNumClasses = kClassHub + 1;               // 13
 constexpr uint8_t kClassDead = 255;
@@ -156,6 +157,23 @@ struct HubAcc {
     unsigned int zero;
 };
 
+// Degree buckets of a set of vertices: vertices grouped by class (see
+// kNumClasses) plus the hub-path layout for the vertices of the hub class.
+struct Buckets {
+    const int32_t* class_list = nullptr;
+    int64_t begin[kNumClasses + 1] = {};
+    int64_t edges[kNumClasses] = {};
+    const int32_t* hub_list = nullptr;
+    int64_t n_hub = 0;
+    const HubChunk* chunks = nullptr;
+    int64_t n_chunks = 0;
+    const int64_t* toff = nullptr;
+    const uint32_t* tmask = nullptr;
+    unsigned long long* tab = nullptr;
+    int64_t tab_words = 0;
+    HubAcc* acc = nullptr;
+};
+
 // ----------------------------------------------------------------------------- device buffer helper
 
 struct Buf {
@@ -221,6 +239,21 @@ struct bisim_ctx {
     bool buckets_dirty = false;    // degree buckets no longer match the CSR
     int32_t cur_k = 0;             // rounds of the current partition
 
+    // incremental maintenance (apply_updates): per level j = 0..inc_k, block ids
+    // per vertex, |S| per vertex, block records and a hash index key -> block
+    int32_t inc_k = -1;            // levels built (-1: no incremental state)
+    int32_t* lid[bisim::kMaxIncLevels + 1] = {};
+    int32_t* lcnt[bisim::kMaxIncLevels + 1] = {};
+    unsigned long long* bkey[bisim::kMaxIncLevels + 1] = {};
+    int32_t* bcnt[bisim::kMaxIncLevels + 1] = {};
+    int32_t* bmin[bisim::kMaxIncLevels + 1] = {};
+    unsigned long long* ikey[bisim::kMaxIncLevels + 1] = {};
+    int32_t* ibid[bisim::kMaxIncLevels + 1] = {};
+    int64_t bnext[bisim::kMaxIncLevels + 1] = {};   // next unused block id
+    int64_t itomb[bisim::kMaxIncLevels + 1] = {};   // tombstones in the index
+    int64_t bcap = 0;              // block records per level
+    uint64_t isize = 0;            // index slots per level (power of two)
+
     // bookkeeping
     std::vector<void*> allocs;
     int64_t device_bytes = 0;
@@ -261,6 +294,16 @@ bisim_status build_buckets(bisim_ctx* ctx, cudaStream_t s);
 
 bisim_status compute_p0(bisim_ctx* ctx, cudaStream_t s);
 bisim_status refine_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks);
+// One signature round over the vertices of `B` (all of them, or the `vcount`
+// listed in `vlist` for verification): Pout[v] = smallest listed vertex with
+// v's exact signature over the labelling Pin; hout[v] (nullable) receives the
+// signature hash that was inserted.
+bisim_status signature_round(bisim_ctx* ctx, const Buckets& B, const int32_t* Pin, int32_t* Pout,
+                             const int32_t* vlist, int64_t vcount, unsigned long long* hout, cudaStream_t s,
+                             int64_t* out_blocks);
+Buckets ctx_buckets(const bisim_ctx* ctx);
+// Groups the listed vertices by label: Pout[v] = smallest listed vertex with v's label.
+bisim_status label_group(bisim_ctx* ctx, const int32_t* vlist, int64_t vcount, int32_t* Pout, cudaStream_t s);
 bisim_status alloc_refine_state(bisim_ctx* ctx, cudaStream_t s);
 void unpin_partition(bisim_ctx* ctx, cudaStream_t s);
 void launch_local_ids(const bisim_ctx* ctx, int32_t* out, cudaStream_t s);
@@ -277,5 +320,12 @@ bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
 bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
                         int32_t* out_executed, int64_t* out_blocks);
 bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- incremental levels (inc.cu)
+
+bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s);
+bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* rowchg, cudaStream_t s);
+void inc_release(bisim_ctx* ctx, cudaStream_t s);
+bisim_status write_current(bisim_ctx* ctx, cudaStream_t s);
 
 }  // namespace bisim

@@ -1,0 +1,968 @@
+// Incremental maintenance of the k-bisimulation partition under update
+// batches (Section 3.2; Theorem 2 states that the incremental summary equals
+// the batch summary of the edited graph, which is what this code keeps).
+//
+// For every level j = 0..k the state holds, per vertex, the id of its level-j
+// block, and per block its signature hash, member count and smallest member;
+// a hash index maps signature hashes to block ids. Block ids are stable names:
+// a block keeps its id while its membership is unchanged, so a change only
+// travels to the vertices whose own level-j block really changed.
+//
+// A batch touches, at level j, the frontier F_j: vertices whose label or
+// liveness changed (j = 0), or whose out-edge multiset changed, whose level
+// j-1 block changed, or that have an out-edge into such a vertex (j >= 1; the
+// cascade of the paper's incremental complexity analysis). For F_j:
+//   1. its vertices leave their old blocks (block minima that left are
+//      recomputed over the remaining members);
+//   2. it is grouped exactly among itself with the batch round machinery
+//      (signatures over the level j-1 block ids);
+//   3. each group is compared exactly with the live blocks of equal hash (a
+//      block's smallest member stands for it) and joins one on equality;
+//   4. otherwise a group that has exactly the members of one old block keeps
+//      that block's id, and any other group gets a new id.
+// The output partition names each level-k block by its smallest member.
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "prof.cuh"
+
+namespace bisim {
+
+namespace {
+
+constexpr unsigned long long kIdxEmpty = 0ull;
+constexpr unsigned long long kIdxTomb = 1ull;
+constexpr int32_t kUndecided = -2;
+constexpr int32_t kNew = -3;
+constexpr int kCmpThreads = 256;
+constexpr int kCmpSmallSlots = 4096;     // shared-memory set for lists up to 2048 values
+constexpr int kCmpLargeSlots = 16384;    // ... up to 8192 values
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+unsigned grid_for(int64_t n, int threads) {
+    return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(cdiv(n, threads), 1 << 20)));
+}
+
+__device__ __forceinline__ unsigned long long index_key(uint64_t h) { return h < 2 ? h + 2 : h; }
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Per-level device view.
+struct Level {
+    int32_t* lid;                 // block id per vertex (-1 dead)
+    int32_t* lcnt;                // |S| per vertex (levels >= 1)
+    unsigned long long* bkey;     // per block: signature index key
+    int32_t* bcnt;                // per block: members
+    int32_t* bmin;                // per block: smallest member
+    unsigned long long* ikey;     // index slots: key (0 empty, 1 tombstone)
+    int32_t* ibid;                // index slots: block id
+    uint64_t imask;
+};
+
+// Per-batch scratch shared by the levels.
+struct Work {
+    int32_t* old;                 // [n] previous block id of frontier vertices
+    int32_t* grp;                 // [n] frontier group (smallest frontier vertex with the same signature)
+    unsigned long long* h;        // [n] signature hash of frontier vertices
+    int32_t* gsize;               // [n] per group representative
+    int32_t* gomin;               // [n]
+    int32_t* gomax;               // [n]
+    int32_t* decision;            // [n] block chosen for a group representative
+    int64_t* resume;              // [n] next index slot to probe
+    uint32_t* cntF;               // [bcap] frontier members per old block
+    uint32_t* touched;            // [bcap]
+    uint32_t* dirty;              // [bcap]
+    int32_t* tlist;               // [bcap]
+    int32_t* dlist;               // [bcap]
+    int32_t* cand;                // [n] representatives with a candidate block
+    int32_t* candb;               // [n] the candidate block
+    unsigned long long* counters; // [8]
+    int32_t* F;                   // [n] frontier
+    int32_t* FL;                  // [n] live frontier
+    uint8_t* inF;                 // [n]
+    uint8_t* changed;             // [n]
+    uint8_t* next;                // [n]
+    int32_t n;
+    int64_t bcap;
+    unsigned* err;                // self-check bits: an index out of range was skipped
+};
+
+constexpr unsigned kChkGroup = 1u, kChkProbe = 2u, kChkMin = 4u, kChkCompare = 8u, kChkAssign = 16u,
+                   kChkOutput = 32u, kChkSettle = 64u;
+
+// ----------------------------------------------------------------------------- frontier
+
+__global__ void k_compact(const uint8_t* __restrict__ flag, const uint8_t* __restrict__ alive, int32_t n,
+                          int live_only, int32_t* __restrict__ out, unsigned long long* __restrict__ count) {
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const bool f = v < n && (flag == nullptr || flag[v]) && (!live_only || alive[v]);
+    const unsigned ball = __ballot_sync(0xffffffffu, f);
+    if (!ball) return;
+    const int leader = __ffs(ball) - 1;
+    unsigned long long base = 0;
+    if (static_cast<int>(lane_id()) == leader) base = atomicAdd(count, static_cast<unsigned long long>(__popc(ball)));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (f) out[base + __popc(ball & ((1u << lane_id()) - 1u))] = static_cast<int32_t>(v);
+}
+
+// mark[src] for every edge into a vertex whose previous-level block changed
+__global__ void k_in_neighbours(const int32_t* __restrict__ esrc, const int32_t* __restrict__ col, int64_t m,
+                                const uint8_t* __restrict__ changed, uint8_t* __restrict__ mark) {
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        if (changed[col[e]]) mark[esrc[e]] = 1;
+}
+
+__global__ void k_or_into(uint8_t* __restrict__ a, const uint8_t* __restrict__ b, const uint8_t* __restrict__ c,
+                          int32_t n) {
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v < n) a[v] = static_cast<uint8_t>(a[v] | b[v] | (c ? c[v] : 0));
+}
+
+__global__ void k_set_flags(const int32_t* __restrict__ list, int64_t count, uint8_t* __restrict__ flag, uint8_t v) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < count) flag[list[i]] = v;
+}
+
+// ----------------------------------------------------------------------------- frontier degree buckets
+
+__global__ void k_list_classify(const int32_t* __restrict__ list, int64_t count, const int64_t* __restrict__ rp,
+                                int small_max, int mid_max, uint32_t* __restrict__ keys, uint64_t* __restrict__ vals) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int32_t v = list[i];
+    const int64_t d = rp[v + 1] - rp[v];
+    uint32_t c;
+    if (d <= small_max || d == 0) {
+        c = d <= 4 ? 0u : d <= 8 ? 1u : d <= 16 ? 2u : 3u;
+    } else if (d <= mid_max) {
+        int lg = 64 - __clzll(static_cast<unsigned long long>(d - 1));
+        lg = lg < 6 ? 6 : lg;
+        c = static_cast<uint32_t>(kSmallClasses + (lg - 6));
+    } else {
+        c = kClassHub;
+    }
+    keys[i] = c;
+    vals[i] = static_cast<uint64_t>(v);
+}
+
+__global__ void k_list_bounds(const uint32_t* __restrict__ cls, const uint64_t* __restrict__ vals, int64_t count,
+                              const int64_t* __restrict__ rp, int64_t* __restrict__ begin,
+                              unsigned long long* __restrict__ edges, int32_t* __restrict__ out) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int c = static_cast<int>(cls[i]);
+    const int p = i == 0 ? -1 : static_cast<int>(cls[i - 1]);
+    for (int q = p + 1; q <= c; ++q) begin[q] = i;
+    const int32_t v = static_cast<int32_t>(vals[i]);
+    out[i] = v;
+    atomicAdd(&edges[c], static_cast<unsigned long long>(rp[v + 1] - rp[v]));
+}
+
+// ----------------------------------------------------------------------------- level passes
+
+// 1. frontier vertices leave their old blocks
+__global__ void k_remove(const int32_t* __restrict__ F, int64_t f, Level L, Work W) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= f) return;
+    const int32_t v = F[i];
+    const int32_t b = L.lid[v];
+    W.old[v] = b;
+    if (b < 0) return;
+    atomicSub(&L.bcnt[b], 1);
+    atomicAdd(&W.cntF[b], 1u);
+    if (atomicExch(&W.touched[b], 1u) == 0u) W.tlist[atomicAdd(&W.counters[0], 1ull)] = b;
+    if (L.bmin[b] == v && atomicExch(&W.dirty[b], 1u) == 0u) W.dlist[atomicAdd(&W.counters[1], 1ull)] = b;
+}
+
+__global__ void k_dirty_reset(const int32_t* __restrict__ dlist, int64_t nd, Level L) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < nd) L.bmin[dlist[i]] = INT_MAX;
+}
+
+// smallest remaining member of every block whose minimum left
+__global__ void k_rescan(int32_t n, const uint8_t* __restrict__ alive, Level L, Work W) {
+    const int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (u >= n || !alive[u] || W.inF[u]) return;
+    const int32_t b = L.lid[u];
+    if (b >= 0 && W.dirty[b]) atomicMin(&L.bmin[b], static_cast<int32_t>(u));
+}
+
+// group statistics of the live frontier
+__global__ void k_group_init(const int32_t* __restrict__ FL, int64_t fl, Work W) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= fl) return;
+    const int32_t v = FL[i];
+    if (W.grp[v] != v) return;
+    W.gsize[v] = 0;
+    W.gomin[v] = INT_MAX;
+    W.gomax[v] = INT_MIN;
+    W.decision[v] = kUndecided;
+    W.resume[v] = -1;
+}
+
+__global__ void k_group_stats(const int32_t* __restrict__ FL, int64_t fl, Work W) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= fl) return;
+    const int32_t v = FL[i];
+    const int32_t g = W.grp[v];
+    if (g < 0 || g >= W.n) {
+        atomicOr(W.err, kChkGroup);
+        return;
+    }
+    atomicAdd(&W.gsize[g], 1);
+    atomicMin(&W.gomin[g], W.old[v]);
+    atomicMax(&W.gomax[g], W.old[v]);
+}
+
+// 3a. probe the index for the next live block with the representative's key.
+// Level 0 compares labels right here; deeper levels queue a candidate.
+__global__ void k_probe(const int32_t* __restrict__ FL, int64_t fl, Level L, Work W, int level,
+                        const int32_t* __restrict__ vlabel, uint64_t hmask) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= fl) return;
+    const int32_t g = FL[i];
+    if (W.grp[g] != g || W.decision[g] != kUndecided) return;
+    const unsigned long long key = index_key(W.h[g]);
+    uint64_t pos = W.resume[g] >= 0 ? static_cast<uint64_t>(W.resume[g]) : (key & L.imask);
+    for (uint64_t probe = 0; probe <= L.imask; ++probe) {
+        const unsigned long long k = L.ikey[pos];
+        if (k == kIdxEmpty) {
+            W.decision[g] = kNew;
+            return;
+        }
+        if (k == key) {
+            const int32_t b = L.ibid[pos];
+            if (b < 0 || b >= W.bcap) {
+                atomicOr(W.err, kChkProbe);
+                W.decision[g] = kNew;
+                return;
+            }
+            if (L.bcnt[b] > 0) {
+                const int32_t r = L.bmin[b];
+                if (r < 0 || r >= W.n) {
+                    atomicOr(W.err, kChkMin);
+                    W.decision[g] = kNew;
+                    return;
+                }
+                if (level == 0) {
+                    if (vlabel[r] == vlabel[g]) {
+                        W.decision[g] = b;
+                        return;
+                    }
+                } else {
+                    W.resume[g] = static_cast<int64_t>((pos + 1) & L.imask);
+                    const unsigned long long c = atomicAdd(&W.counters[2], 1ull);
+                    W.cand[c] = g;
+                    W.candb[c] = b;
+                    return;
+                }
+            }
+        }
+        pos = (pos + 1) & L.imask;
+    }
+    W.decision[g] = kNew;
+    (void)hmask;
+}
+
+// Inserts value mv into a shared-memory set (0 = empty; value 0 flagged in *zero).
+__device__ __forceinline__ void cset_insert(unsigned long long* tab, uint32_t mask, unsigned* zero,
+                                            unsigned long long mv) {
+    if (mv == 0ull) { *zero = 1u; return; }
+    uint32_t pos = static_cast<uint32_t>(mv) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long prev = atomicCAS(&tab[pos], 0ull, mv);
+        if (prev == 0ull || prev == mv) return;
+        pos = (pos + 1) & mask;
+    }
+}
+
+__device__ __forceinline__ bool cset_has(const unsigned long long* tab, uint32_t mask, unsigned zero,
+                                         unsigned long long mv) {
+    if (mv == 0ull) return zero != 0u;
+    uint32_t pos = static_cast<uint32_t>(mv) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long cur = tab[pos];
+        if (cur == mv) return true;
+        if (cur == 0ull) return false;
+        pos = (pos + 1) & mask;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint64_t pair_value_dev(int32_t label, int32_t block) { return pair_value(label, block); }
+
+// 3b. exact comparison of a representative g with a candidate block's
+// smallest member r: same previous-level block, same set size, and every pair
+// of r is in g's set. Lists up to SLOTS/2 values use a shared-memory set; the
+// list of a hub representative (above 8192 values) is looked up in its
+// dedup table. One CTA per candidate.
+template <int SLOTS>
+__global__ void __launch_bounds__(kCmpThreads) k_compare(int64_t ncand, Level L, Level Lprev, Work W,
+                                                         const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                         const int32_t* __restrict__ elab,
+                                                         const int32_t* __restrict__ cnt,
+                                                         const unsigned long long* __restrict__ skey,
+                                                         const int32_t* __restrict__ hub_list, int64_t n_hub,
+                                                         const int64_t* __restrict__ toff,
+                                                         const uint32_t* __restrict__ tmask,
+                                                         const unsigned long long* __restrict__ tab_all,
+                                                         const HubAcc* __restrict__ acc, int lo_c, int hi_c) {
+    extern __shared__ unsigned long long tab[];
+    __shared__ unsigned zero;
+    for (int64_t i = blockIdx.x; i < ncand; i += gridDim.x) {
+        const int32_t g = W.cand[i];
+        const int32_t b = W.candb[i];
+        const int32_t c = cnt[g];
+        if (c < lo_c || c > hi_c) continue;                    // uniform: handled by another launch
+        const int32_t r = L.bmin[b];
+        if (r < 0 || r >= W.n || g < 0 || g >= W.n) {
+            if (threadIdx.x == 0) atomicOr(W.err, kChkCompare);
+            continue;
+        }
+        bool same = Lprev.lid[g] == Lprev.lid[r] && L.lcnt[r] == c;
+        if (same) {
+            bool miss = false;
+            if (SLOTS > 0) {
+                uint32_t size = 64;
+                while (size < 2u * static_cast<uint32_t>(c)) size <<= 1;
+                for (uint32_t j = threadIdx.x; j < size; j += kCmpThreads) tab[j] = 0ull;
+                if (threadIdx.x == 0) zero = 0u;
+                __syncthreads();
+                const unsigned long long* lg = skey + rp[g];
+                for (int32_t j = threadIdx.x; j < c; j += kCmpThreads) cset_insert(tab, size - 1, &zero, lg[j]);
+                __syncthreads();
+                for (int64_t e = rp[r] + threadIdx.x; e < rp[r + 1] && !miss; e += kCmpThreads)
+                    miss = !cset_has(tab, size - 1, zero, pair_value_dev(elab[e], Lprev.lid[col[e]]));
+            } else {
+                // hub representative: its dedup table from the frontier's hub path
+                int64_t lo = 0, hi = n_hub - 1;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (hub_list[mid] < g) lo = mid + 1; else hi = mid;
+                }
+                const unsigned long long* ht = tab_all + toff[lo];
+                const uint32_t mask = tmask[lo];
+                for (int64_t e = rp[r] + threadIdx.x; e < rp[r + 1] && !miss; e += kCmpThreads) {
+                    const unsigned long long mv = pair_value_dev(elab[e], Lprev.lid[col[e]]);
+                    bool found = false;
+                    if (mv == 0ull) {
+                        found = acc[lo].zero != 0u;
+                    } else {
+                        uint32_t pos = static_cast<uint32_t>(mv) & mask;
+                        for (uint32_t probe = 0; probe <= mask; ++probe) {
+                            const unsigned long long cur = ht[pos];
+                            if (cur == mv) { found = true; break; }
+                            if (cur == 0ull) break;
+                            pos = (pos + 1) & mask;
+                        }
+                    }
+                    miss = !found;
+                }
+            }
+            same = !__syncthreads_or(miss ? 1 : 0);
+        }
+        if (threadIdx.x == 0 && same) W.decision[g] = b;
+        __syncthreads();
+    }
+}
+
+// 4. groups without a live match: keep the old id if the membership is that
+// of one old block, else take a fresh id. Also (re)keys the index.
+__global__ void k_settle(const int32_t* __restrict__ FL, int64_t fl, Level L, Work W, int64_t* __restrict__ bnext,
+                         int64_t bcap, unsigned long long* __restrict__ counters) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= fl) return;
+    const int32_t g = FL[i];
+    if (W.grp[g] != g) return;
+    if (W.decision[g] >= 0) return;                        // joined a live block
+    const unsigned long long key = index_key(W.h[g]);
+    const int32_t ob = W.gomin[g];
+    if (ob >= W.bcap) {
+        atomicOr(W.err, kChkSettle);
+        return;
+    }
+    int32_t b;
+    if (ob >= 0 && ob == W.gomax[g] && L.bcnt[ob] == 0 && static_cast<int32_t>(W.cntF[ob]) == W.gsize[g]) {
+        b = ob;                                            // same members as before: keep the name
+        if (L.bkey[b] != key) {
+            // drop the old index entry of b, then insert the new key below
+            const unsigned long long okey = L.bkey[b];
+            uint64_t pos = okey & L.imask;
+            for (uint64_t probe = 0; probe <= L.imask; ++probe) {
+                if (L.ikey[pos] == kIdxEmpty) break;
+                if (L.ikey[pos] == okey && L.ibid[pos] == b) {
+                    L.ikey[pos] = kIdxTomb;
+                    atomicAdd(&counters[3], 1ull);
+                    break;
+                }
+                pos = (pos + 1) & L.imask;
+            }
+        } else {
+            W.decision[g] = b;
+            L.bmin[b] = INT_MAX;
+            return;
+        }
+    } else {
+        const long long nb = atomicAdd(reinterpret_cast<unsigned long long*>(bnext), 1ull);
+        if (nb >= bcap) {
+            atomicOr(reinterpret_cast<unsigned*>(&counters[4]), 1u);   // out of block ids: rebuild
+            W.decision[g] = kNew;
+            return;
+        }
+        b = static_cast<int32_t>(nb);
+        L.bcnt[b] = 0;
+    }
+    L.bkey[b] = key;
+    L.bmin[b] = INT_MAX;
+    W.decision[g] = b;
+    uint64_t pos = key & L.imask;
+    for (uint64_t probe = 0; probe <= L.imask; ++probe) {
+        unsigned long long cur = L.ikey[pos];
+        if (cur == kIdxEmpty || cur == kIdxTomb) {
+            const unsigned long long prev = atomicCAS(&L.ikey[pos], cur, key);
+            if (prev == cur) {
+                L.ibid[pos] = b;
+                if (cur == kIdxTomb) atomicAdd(&counters[5], 1ull);   // a tombstone reused
+                return;
+            }
+            continue;                                       // lost the slot: look at it again
+        }
+        pos = (pos + 1) & L.imask;
+    }
+    atomicOr(reinterpret_cast<unsigned*>(&counters[4]), 2u);   // index full
+}
+
+// 5. frontier vertices take their blocks
+__global__ void k_assign(const int32_t* __restrict__ F, int64_t f, const uint8_t* __restrict__ alive, Level L,
+                         Work W, const int32_t* __restrict__ cnt_now, int level) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= f) return;
+    const int32_t v = F[i];
+    const int32_t o = W.old[v];
+    if (alive[v]) {
+        const int32_t g = W.grp[v];
+        if (g < 0 || g >= W.n) {
+            atomicOr(W.err, kChkAssign);
+            return;
+        }
+        const int32_t b = W.decision[g];
+        if (b < 0 || b >= W.bcap) {                        // ids ran out: the host rebuilds the state
+            if (b != kNew) atomicOr(W.err, kChkAssign);
+            return;
+        }
+        L.lid[v] = b;
+        atomicAdd(&L.bcnt[b], 1);
+        atomicMin(&L.bmin[b], v);
+        if (level > 0) L.lcnt[v] = cnt_now[v];
+        W.changed[v] = b != o;
+    } else {
+        L.lid[v] = -1;
+        W.changed[v] = o != -1;
+    }
+}
+
+// blocks left without members lose their index entry; per-block flags reset
+__global__ void k_retire(const int32_t* __restrict__ tlist, int64_t nt, Level L, Work W,
+                         unsigned long long* __restrict__ counters) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    const int32_t b = tlist[i];
+    W.touched[b] = 0u;
+    W.dirty[b] = 0u;
+    W.cntF[b] = 0u;
+    if (L.bcnt[b] != 0) return;
+    const unsigned long long key = L.bkey[b];
+    uint64_t pos = key & L.imask;
+    for (uint64_t probe = 0; probe <= L.imask; ++probe) {
+        const unsigned long long k = L.ikey[pos];
+        if (k == kIdxEmpty) return;
+        if (k == key && L.ibid[pos] == b) {
+            L.ikey[pos] = kIdxTomb;
+            atomicAdd(&counters[3], 1ull);
+            return;
+        }
+        pos = (pos + 1) & L.imask;
+    }
+}
+
+__global__ void k_label_keys(const int32_t* __restrict__ FL, int64_t fl, const int32_t* __restrict__ vlabel,
+                             unsigned long long* __restrict__ h, uint64_t hmask) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < fl) {
+        const int32_t v = FL[i];
+        h[v] = label_hash(0, vlabel[v]) & hmask;
+    }
+}
+
+__global__ void k_output(int32_t n, const uint8_t* __restrict__ alive, const int32_t* __restrict__ lid,
+                         const int32_t* __restrict__ bmin, int64_t bcap, int32_t* __restrict__ P, unsigned* err) {
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t b = alive[v] ? lid[v] : -1;
+    if (alive[v] && (b < 0 || b >= bcap)) {
+        atomicOr(err, kChkOutput);
+        P[v] = -1;
+        return;
+    }
+    P[v] = alive[v] ? bmin[b] : -1;
+}
+
+// ----------------------------------------------------------------------------- host side
+
+Level level_view(const bisim_ctx* ctx, int j) {
+    return Level{ctx->lid[j], ctx->lcnt[j], ctx->bkey[j], ctx->bcnt[j], ctx->bmin[j], ctx->ikey[j], ctx->ibid[j],
+                 ctx->isize - 1};
+}
+
+// Scratch that lives for one batch.
+struct Scratch {
+    char* base = nullptr;
+    Work W{};
+    int64_t* dbnext = nullptr;
+    uint32_t* ck0 = nullptr;
+    uint32_t* ck1 = nullptr;
+    uint64_t* cv0 = nullptr;
+    uint64_t* cv1 = nullptr;
+    int64_t* ctmp = nullptr;
+    int32_t* blist = nullptr;
+    int64_t* dbegin = nullptr;
+    unsigned long long* dedges = nullptr;
+};
+
+cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
+    const size_t n = static_cast<size_t>(std::max(ctx->n, 1));
+    const size_t bc = static_cast<size_t>(ctx->bcap);
+    const size_t tw = radix_temp_words(static_cast<int64_t>(n));
+    size_t bytes = 0;
+    auto need = [&](size_t b) { bytes += (b + 255) & ~size_t(255); };
+    need(4 * n); need(4 * n); need(8 * n); need(4 * n); need(4 * n); need(4 * n); need(4 * n); need(8 * n);
+    need(4 * bc); need(4 * bc); need(4 * bc); need(4 * bc); need(4 * bc);
+    need(4 * n); need(4 * n); need(8 * 8); need(4 * n); need(4 * n); need(n); need(n); need(n);
+    need(8 * 2); need(32);
+    need(4 * n); need(4 * n); need(8 * n); need(8 * n); need(8 * tw); need(4 * n);
+    need(8 * (kNumClasses + 1)); need(8 * kNumClasses);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&S.base), bytes, s);
+    if (e) return e;
+    char* p = S.base;
+    auto carve = [&](size_t b) { char* q = p; p += (b + 255) & ~size_t(255); return q; };
+    Work& W = S.W;
+    W.old = reinterpret_cast<int32_t*>(carve(4 * n));
+    W.grp = reinterpret_cast<int32_t*>(carve(4 * n));
+    W.h = reinterpret_cast<unsigned long long*>(carve(8 * n));
+    W.gsize = reinterpret_cast<int32_t*>(carve(4 * n));
+    W.gomin = reinterpret_cast<int32_t*>(carve(4 * n));
+    W.gomax = reinterpret_cast<int32_t*>(carve(4 * n));
+    W.decision = reinterpret_cast<int32_t*>(carve(4 * n));
+    W.resume = reinterpret_cast<int64_t*>(carve(8 * n));
+    W.cntF = reinterpret_cast<uint32_t*>(carve(4 * bc));
+    W.touched = reinterpret_cast<uint32_t*>(carve(4 * bc));
+    W.dirty = reinterpret_cast<uint32_t*>(carve(4 * bc));
+    W.tlist = reinterpret_cast<int32_t*>(carve(4 * bc));
+    W.dlist = reinterpret_cast<int32_t*>(carve(4 * bc));
+    W.cand = reinterpret_cast<int32_t*>(carve(4 * n));
+    W.candb = reinterpret_cast<int32_t*>(carve(4 * n));
+    W.counters = reinterpret_cast<unsigned long long*>(carve(8 * 8));
+    W.F = reinterpret_cast<int32_t*>(carve(4 * n));
+    W.FL = reinterpret_cast<int32_t*>(carve(4 * n));
+    W.inF = reinterpret_cast<uint8_t*>(carve(n));
+    W.changed = reinterpret_cast<uint8_t*>(carve(n));
+    W.next = reinterpret_cast<uint8_t*>(carve(n));
+    S.dbnext = reinterpret_cast<int64_t*>(carve(8 * 2));
+    W.err = reinterpret_cast<unsigned*>(carve(32));
+    W.n = ctx->n;
+    W.bcap = ctx->bcap;
+    cudaMemsetAsync(W.err, 0, 32, s);
+    S.ck0 = reinterpret_cast<uint32_t*>(carve(4 * n));
+    S.ck1 = reinterpret_cast<uint32_t*>(carve(4 * n));
+    S.cv0 = reinterpret_cast<uint64_t*>(carve(8 * n));
+    S.cv1 = reinterpret_cast<uint64_t*>(carve(8 * n));
+    S.ctmp = reinterpret_cast<int64_t*>(carve(8 * tw));
+    S.blist = reinterpret_cast<int32_t*>(carve(4 * n));
+    S.dbegin = reinterpret_cast<int64_t*>(carve(8 * (kNumClasses + 1)));
+    S.dedges = reinterpret_cast<unsigned long long*>(carve(8 * kNumClasses));
+    // per-block flags start (and are kept) at zero
+    cudaMemsetAsync(W.cntF, 0, 4 * bc, s);
+    cudaMemsetAsync(W.touched, 0, 4 * bc, s);
+    cudaMemsetAsync(W.dirty, 0, 4 * bc, s);
+    cudaMemsetAsync(W.changed, 0, n, s);
+    cudaMemsetAsync(W.inF, 0, n, s);                       // pool memory is recycled: start clean
+    return cudaSuccess;
+}
+
+// Degree buckets of the live frontier (and a hub layout for its hubs).
+struct ListBuckets {
+    Buckets B;
+    void* hubmem = nullptr;
+};
+
+bisim_status list_buckets(bisim_ctx* ctx, const int32_t* list, int64_t count, Scratch& S, ListBuckets& out,
+                          cudaStream_t s) {
+    Buckets& B = out.B;
+    cudaError_t e;
+    int64_t begin[kNumClasses + 1];
+    unsigned long long edges[kNumClasses];
+    for (int c = 0; c <= kNumClasses; ++c) begin[c] = count;
+    cudaMemcpyAsync(S.dbegin, begin, sizeof(begin), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(S.dedges, 0, sizeof(edges), s);
+    if (count > 0) {
+        BISIM_SITE(site, "inc_buckets");
+        Launch L(site, s, count, 0, 24.0 * count);
+        k_list_classify<<<grid_for(count, 256), 256, 0, s>>>(list, count, ctx->row_ptr, ctx->opt.small_max_degree,
+                                                            ctx->opt.mid_max_degree, S.ck0, S.cv0);
+        const int w = radix_sort_pairs(S.ck0, S.cv0, S.ck1, S.cv1, count, 8, S.ctmp, s);
+        k_list_bounds<<<grid_for(count, 256), 256, 0, s>>>(w ? S.ck1 : S.ck0, w ? S.cv1 : S.cv0, count,
+                                                          ctx->row_ptr, S.dbegin, S.dedges, S.blist);
+    }
+    cudaMemcpyAsync(begin, S.dbegin, sizeof(begin), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(edges, S.dedges, sizeof(edges), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "bucket frontier");
+    for (int c = kNumClasses - 1; c >= 0; --c) begin[c] = std::min(begin[c], begin[c + 1]);
+    B.class_list = S.blist;
+    for (int c = 0; c <= kNumClasses; ++c) B.begin[c] = begin[c];
+    for (int c = 0; c < kNumClasses; ++c) B.edges[c] = static_cast<int64_t>(edges[c]);
+    B.hub_list = S.blist + begin[kClassHub];
+    B.n_hub = begin[kClassHub + 1] - begin[kClassHub];
+    if (B.n_hub == 0) return BISIM_OK;
+    // hub layout on the host: few vertices
+    std::vector<int32_t> hubs(B.n_hub);
+    cudaMemcpyAsync(hubs.data(), B.hub_list, sizeof(int32_t) * B.n_hub, cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "read frontier hubs");
+    std::vector<int64_t> rb(B.n_hub), re(B.n_hub);
+    for (int64_t h = 0; h < B.n_hub; ++h) {
+        cudaMemcpyAsync(&rb[h], ctx->row_ptr + hubs[h], sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&re[h], ctx->row_ptr + hubs[h] + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    }
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "read frontier hub rows");
+    std::vector<HubChunk> chunks;
+    std::vector<int64_t> toff(B.n_hub);
+    std::vector<uint32_t> tmask(B.n_hub);
+    int64_t words = 0;
+    const int64_t csz = ctx->opt.hub_chunk;
+    for (int64_t h = 0; h < B.n_hub; ++h) {
+        uint64_t sz = 64;
+        while (sz < static_cast<uint64_t>(2 * (re[h] - rb[h]))) sz <<= 1;
+        toff[h] = words;
+        tmask[h] = static_cast<uint32_t>(sz - 1);
+        words += static_cast<int64_t>(sz);
+        for (int64_t b = rb[h]; b < re[h]; b += csz)
+            chunks.push_back(HubChunk{static_cast<int32_t>(h), hubs[h], b, std::min(re[h], b + csz)});
+    }
+    const size_t bytes = sizeof(HubChunk) * chunks.size() + 256 + sizeof(int64_t) * B.n_hub + 256 +
+                         sizeof(uint32_t) * B.n_hub + 256 + sizeof(unsigned long long) * words + 256 +
+                         sizeof(HubAcc) * B.n_hub + 256;
+    char* p = nullptr;
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&p), bytes, s))) return cuda_error(ctx, e, "alloc frontier hubs");
+    out.hubmem = p;
+    auto carve = [&](size_t b) { char* q = p; p += (b + 255) & ~size_t(255); return q; };
+    HubChunk* dchunks = reinterpret_cast<HubChunk*>(carve(sizeof(HubChunk) * chunks.size()));
+    int64_t* dtoff = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * B.n_hub));
+    uint32_t* dtmask = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * B.n_hub));
+    unsigned long long* dtab = reinterpret_cast<unsigned long long*>(carve(sizeof(unsigned long long) * words));
+    HubAcc* dacc = reinterpret_cast<HubAcc*>(carve(sizeof(HubAcc) * B.n_hub));
+    cudaMemcpyAsync(dchunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dtoff, toff.data(), sizeof(int64_t) * B.n_hub, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dtmask, tmask.data(), sizeof(uint32_t) * B.n_hub, cudaMemcpyHostToDevice, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "upload frontier hubs");
+    B.chunks = dchunks;
+    B.n_chunks = static_cast<int64_t>(chunks.size());
+    B.toff = dtoff;
+    B.tmask = dtmask;
+    B.tab = dtab;
+    B.tab_words = words;
+    B.acc = dacc;
+    return BISIM_OK;
+}
+
+bisim_status ensure_skey(bisim_ctx* ctx, cudaStream_t s) {
+    if (ctx->m <= ctx->skey_cap) return BISIM_OK;
+    ctx_free(ctx, ctx->skey, sizeof(unsigned long long) * ctx->skey_cap, s);
+    ctx->skey = nullptr;
+    const int64_t cap = ctx->m + ctx->m / 4 + 1024;
+    cudaError_t e;
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->skey), sizeof(unsigned long long) * cap, s)))
+        return cuda_error(ctx, e, "grow signature lists");
+    ctx->skey_cap = cap;
+    return BISIM_OK;
+}
+
+// One level: frontier F (f vertices, live or dead) with live part FL (fl).
+bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t f, int64_t fl, bool all_static,
+                        int64_t* rebuild, cudaStream_t s) {
+    Work& W = S.W;
+    Level L = level_view(ctx, j);
+    const int32_t n = ctx->n;
+    cudaError_t e;
+    bisim_status st;
+    BISIM_SITE(site, "inc_level");
+    cudaMemsetAsync(W.counters, 0, 8 * 8, s);
+    if (f > 0) {
+        Launch Lk(site, s, f, 0, 16.0 * f);
+        k_set_flags<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, W.inF, 1);
+        k_remove<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, L, W);
+    }
+    unsigned long long hc[8];
+    cudaMemcpyAsync(hc, W.counters, sizeof(hc), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "leave old blocks");
+    const int64_t ntouched = static_cast<int64_t>(hc[0]);
+    const int64_t ndirty = static_cast<int64_t>(hc[1]);
+    if (ndirty > 0) {
+        Launch Lk(site, s, n, 0, 8.0 * n);
+        k_dirty_reset<<<grid_for(ndirty, 256), 256, 0, s>>>(W.dlist, ndirty, L);
+        k_rescan<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->alive, L, W);
+    }
+    // 2. exact groups within the live frontier
+    ListBuckets LB;
+    if (fl > 0) {
+        if (j == 0) {
+            if ((st = label_group(ctx, W.FL, fl, W.grp, s)) != BISIM_OK) return st;
+            Launch Lk(site, s, fl, 0, 12.0 * fl);
+            k_label_keys<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, ctx->vlabel, W.h,
+                                                          ctx->opt.hash_bits >= 64 ? ~0ull : ((1ull << ctx->opt.hash_bits) - 1));
+        } else {
+            Buckets B;
+            if (all_static) {
+                B = ctx_buckets(ctx);
+            } else {
+                if ((st = list_buckets(ctx, W.FL, fl, S, LB, s)) != BISIM_OK) return st;
+                B = LB.B;
+            }
+            int64_t blocks = 0;
+            st = signature_round(ctx, B, ctx->lid[j - 1], W.grp, all_static ? nullptr : W.FL, all_static ? 0 : fl,
+                                 W.h, s, &blocks);
+            if (st != BISIM_OK) {
+                if (LB.hubmem) cudaFreeAsync(LB.hubmem, s);
+                return st;
+            }
+        }
+        Launch Lk(site, s, fl, 0, 24.0 * fl);
+        k_group_init<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, W);
+        k_group_stats<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, W);
+    }
+    // 3. match live blocks
+    const uint64_t hmask = ctx->opt.hash_bits >= 64 ? ~0ull : ((1ull << ctx->opt.hash_bits) - 1);
+    for (int iter = 0; fl > 0; ++iter) {
+        if (iter > 1 << 16) return set_error(ctx, BISIM_ETIMEOUT, "incremental block matching did not converge");
+        cudaMemsetAsync(&W.counters[2], 0, 8, s);
+        {
+            Launch Lk(site, s, fl, 0, 32.0 * fl);
+            k_probe<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, L, W, j, ctx->vlabel, hmask);
+        }
+        unsigned long long ncand = 0;
+        cudaMemcpyAsync(&ncand, &W.counters[2], 8, cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "probe blocks");
+        if (ncand == 0 || j == 0) break;
+        Level Lp = level_view(ctx, j - 1);
+        const Buckets& B = LB.B;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_compare<kCmpLargeSlots>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(sizeof(unsigned long long) * kCmpLargeSlots));
+            attr = true;
+        }
+        const unsigned grid = static_cast<unsigned>(std::min<unsigned long long>(ncand, 4096));
+        Launch Lk(site, s, static_cast<int64_t>(ncand), 0, 0.0);
+        k_compare<kCmpSmallSlots><<<grid, kCmpThreads, sizeof(unsigned long long) * kCmpSmallSlots, s>>>(
+            static_cast<int64_t>(ncand), L, Lp, W, ctx->row_ptr, ctx->col, ctx->elab, ctx->cnt, ctx->skey,
+            B.hub_list, B.n_hub, B.toff, B.tmask, B.tab, B.acc, 0, kCmpSmallSlots / 2);
+        k_compare<kCmpLargeSlots><<<grid, kCmpThreads, sizeof(unsigned long long) * kCmpLargeSlots, s>>>(
+            static_cast<int64_t>(ncand), L, Lp, W, ctx->row_ptr, ctx->col, ctx->elab, ctx->cnt, ctx->skey,
+            B.hub_list, B.n_hub, B.toff, B.tmask, B.tab, B.acc, kCmpSmallSlots / 2 + 1, kCmpLargeSlots / 2);
+        if (B.n_hub > 0)
+            k_compare<0><<<grid, kCmpThreads, 0, s>>>(static_cast<int64_t>(ncand), L, Lp, W, ctx->row_ptr, ctx->col,
+                                                      ctx->elab, ctx->cnt, ctx->skey, B.hub_list, B.n_hub, B.toff,
+                                                      B.tmask, B.tab, B.acc, kCmpLargeSlots / 2 + 1, INT_MAX);
+    }
+    if (LB.hubmem) cudaFreeAsync(LB.hubmem, s);
+    // 4. keep or create ids; 5. assign; retire empty blocks
+    cudaMemcpyAsync(S.dbnext, &ctx->bnext[j], sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (fl > 0) {
+        Launch Lk(site, s, fl, 0, 24.0 * fl);
+        k_settle<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, L, W, S.dbnext, ctx->bcap, W.counters);
+    }
+    if (f > 0) {
+        Launch Lk(site, s, f, 0, 24.0 * f);
+        k_assign<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, ctx->alive, L, W, ctx->cnt, j);
+        k_set_flags<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, W.inF, 0);
+    }
+    if (ntouched > 0) {
+        Launch Lk(site, s, ntouched, 0, 16.0 * ntouched);
+        k_retire<<<grid_for(ntouched, 256), 256, 0, s>>>(W.tlist, ntouched, L, W, W.counters);
+    }
+    cudaMemcpyAsync(&ctx->bnext[j], S.dbnext, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(hc, W.counters, sizeof(hc), cudaMemcpyDeviceToHost, s);
+    unsigned chk = 0;
+    cudaMemcpyAsync(&chk, W.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "settle blocks");
+    if (chk) {
+        char msg[96];
+        std::snprintf(msg, sizeof(msg), "incremental level %d self-check failed (bits 0x%x)", j, chk);
+        return set_error(ctx, BISIM_EINVAL, msg);
+    }
+    ctx->itomb[j] += static_cast<int64_t>(hc[3]) - static_cast<int64_t>(hc[5]);
+    *rebuild = static_cast<int64_t>(hc[4]);
+    if (ctx->bnext[j] > ctx->bcap) ctx->bnext[j] = ctx->bcap;
+    return BISIM_OK;
+}
+
+// Builds the frontier list(s) from W.next (or all live vertices when flags == null).
+bisim_status make_frontier(bisim_ctx* ctx, Scratch& S, const uint8_t* flags, int64_t* f, int64_t* fl,
+                           cudaStream_t s) {
+    Work& W = S.W;
+    const int32_t n = ctx->n;
+    cudaError_t e;
+    cudaMemsetAsync(&W.counters[6], 0, 16, s);
+    if (n > 0) {
+        k_compact<<<grid_for(n, 256), 256, 0, s>>>(flags, ctx->alive, n, 0, W.F, &W.counters[6]);
+        k_compact<<<grid_for(n, 256), 256, 0, s>>>(flags, ctx->alive, n, 1, W.FL, &W.counters[7]);
+    }
+    unsigned long long c[2] = {0, 0};
+    cudaMemcpyAsync(c, &W.counters[6], sizeof(c), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "compact frontier");
+    *f = static_cast<int64_t>(c[0]);
+    *fl = static_cast<int64_t>(c[1]);
+    return BISIM_OK;
+}
+
+bisim_status write_output(bisim_ctx* ctx, cudaStream_t s) {
+    const int k = ctx->inc_k;
+    if (ctx->n > 0) {
+        BISIM_SITE(site, "inc_output");
+        Launch L(site, s, ctx->n, 0, 13.0 * ctx->n);
+        cudaMemsetAsync(&ctx->dstate->error, 0, sizeof(unsigned), s);
+        k_output<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, ctx->alive, ctx->lid[k], ctx->bmin[k], ctx->bcap,
+                                                      ctx->P[0], &ctx->dstate->error);
+        cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e) return cuda_error(ctx, e, "write partition");
+        if (ctx->hstate->error) return set_error(ctx, BISIM_EINVAL, "incremental state inconsistent at output");
+    }
+    ctx->cur = 0;
+    ctx->cur_k = k;
+    return BISIM_OK;
+}
+
+}  // namespace
+
+void inc_release(bisim_ctx* ctx, cudaStream_t s) {
+    const size_t n = static_cast<size_t>(std::max(ctx->n, 1));
+    for (int j = 0; j <= kMaxIncLevels; ++j) {
+        ctx_free(ctx, ctx->lid[j], 4 * n, s);
+        ctx_free(ctx, ctx->lcnt[j], 4 * n, s);
+        ctx_free(ctx, ctx->bkey[j], 8 * static_cast<size_t>(ctx->bcap), s);
+        ctx_free(ctx, ctx->bcnt[j], 4 * static_cast<size_t>(ctx->bcap), s);
+        ctx_free(ctx, ctx->bmin[j], 4 * static_cast<size_t>(ctx->bcap), s);
+        ctx_free(ctx, ctx->ikey[j], 8 * ctx->isize, s);
+        ctx_free(ctx, ctx->ibid[j], 4 * ctx->isize, s);
+        ctx->lid[j] = ctx->lcnt[j] = ctx->bcnt[j] = ctx->bmin[j] = ctx->ibid[j] = nullptr;
+        ctx->bkey[j] = ctx->ikey[j] = nullptr;
+        ctx->bnext[j] = ctx->itomb[j] = 0;
+    }
+    ctx->inc_k = -1;
+}
+
+// Full build of the incremental state: every live vertex is the frontier of
+// an empty state at every level.
+bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s) {
+    const int K = ctx->opt.k_incremental;
+    if (K > kMaxIncLevels) return set_error(ctx, BISIM_EINVAL, "k_incremental exceeds 16");
+    inc_release(ctx, s);
+    bisim_status st;
+    if ((st = ensure_edge_sources(ctx, s)) != BISIM_OK) return st;
+    if ((st = refresh_after_edit(ctx, s)) != BISIM_OK) return st;
+    if ((st = ensure_skey(ctx, s)) != BISIM_OK) return st;
+    const size_t n = static_cast<size_t>(std::max(ctx->n, 1));
+    ctx->bcap = 2 * static_cast<int64_t>(n) + 1024;
+    uint64_t is = 1024;
+    while (is < 3ull * n) is <<= 1;
+    ctx->isize = is;
+    cudaError_t e;
+    for (int j = 0; j <= K; ++j) {
+        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->lid[j]), 4 * n, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->lcnt[j]), 4 * n, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bkey[j]), 8 * static_cast<size_t>(ctx->bcap), s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bcnt[j]), 4 * static_cast<size_t>(ctx->bcap), s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bmin[j]), 4 * static_cast<size_t>(ctx->bcap), s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ikey[j]), 8 * is, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ibid[j]), 4 * is, s)))
+            return cuda_error(ctx, e, "alloc incremental state");
+        cudaMemsetAsync(ctx->lid[j], 0xff, 4 * n, s);        // -1: no block yet
+        cudaMemsetAsync(ctx->lcnt[j], 0, 4 * n, s);
+        cudaMemsetAsync(ctx->bcnt[j], 0, 4 * static_cast<size_t>(ctx->bcap), s);
+        cudaMemsetAsync(ctx->ikey[j], 0, 8 * is, s);
+    }
+    ctx->inc_k = K;
+    Scratch S;
+    if ((e = alloc_scratch(ctx, S, s))) return cuda_error(ctx, e, "alloc incremental scratch");
+    int64_t f = 0, fl = 0, rebuild = 0;
+    st = make_frontier(ctx, S, nullptr, &f, &fl, s);
+    for (int j = 0; st == BISIM_OK && j <= K; ++j) st = level_pass(ctx, j, S, f, fl, true, &rebuild, s);
+    if (st == BISIM_OK && rebuild) st = set_error(ctx, BISIM_ENOMEM, "incremental state overflow during build");
+    if (st == BISIM_OK) st = write_output(ctx, s);
+    cudaFreeAsync(S.base, s);
+    if (st != BISIM_OK) {
+        inc_release(ctx, s);
+        return st;
+    }
+    ctx->stats.last_frontier = fl;
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e2) return cuda_error(ctx, e2, "build incremental state");
+    return BISIM_OK;
+}
+
+bisim_status write_current(bisim_ctx* ctx, cudaStream_t s) {
+    bisim_status st = write_output(ctx, s);
+    if (st != BISIM_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(s);
+    return e ? cuda_error(ctx, e, "write partition") : BISIM_OK;
+}
+
+bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* rowchg, cudaStream_t s) {
+    bisim_status st;
+    if ((st = ensure_skey(ctx, s)) != BISIM_OK) return st;
+    const int K = ctx->inc_k;
+    const int32_t n = ctx->n;
+    cudaError_t e;
+    Scratch S;
+    if ((e = alloc_scratch(ctx, S, s))) return cuda_error(ctx, e, "alloc incremental scratch");
+    Work& W = S.W;
+    int64_t f = 0, fl = 0, total = 0, rebuild = 0;
+    st = make_frontier(ctx, S, vchanged, &f, &fl, s);
+    for (int j = 0; st == BISIM_OK && j <= K; ++j) {
+        if (j > 0) {
+            // F_j: block changed one level down, out-edges changed, or an out-edge into a changed vertex
+            cudaMemsetAsync(W.next, 0, n, s);
+            if (ctx->m > 0) {
+                BISIM_SITE(site, "inc_in_neighbours");
+                Launch L(site, s, 0, ctx->m, 8.0 * ctx->m);
+                k_in_neighbours<<<grid_for(ctx->m, 256), 256, 0, s>>>(ctx->esrc, ctx->col, ctx->m, W.changed, W.next);
+            }
+            k_or_into<<<grid_for(n, 256), 256, 0, s>>>(W.next, W.changed, rowchg, n);
+            st = make_frontier(ctx, S, W.next, &f, &fl, s);
+            if (st != BISIM_OK) break;
+            cudaMemsetAsync(W.changed, 0, n, s);
+        } else {
+            cudaMemsetAsync(W.changed, 0, n, s);
+        }
+        total += fl;
+        st = level_pass(ctx, j, S, f, fl, false, &rebuild, s);
+        if (st == BISIM_OK && rebuild) break;
+    }
+    cudaFreeAsync(S.base, s);
+    if (st != BISIM_OK) return st;
+    // out of block ids or index slots: start over from the current graph
+    bool full = rebuild != 0;
+    for (int j = 0; j <= K; ++j)
+        if (ctx->bnext[j] + n >= ctx->bcap || static_cast<uint64_t>(ctx->bnext[j] + ctx->itomb[j]) * 10 > ctx->isize * 7)
+            full = true;
+    if (full) return inc_build(ctx, s);
+    ctx->stats.last_frontier = total;
+    if ((st = write_output(ctx, s)) != BISIM_OK) return st;
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "incremental update");
+    return BISIM_OK;
+}
+
+}  // namespace bisim

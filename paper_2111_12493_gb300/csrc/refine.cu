@@ -18,6 +18,7 @@
 // with the exact partition.
 #include <algorithm>
 #include <cstring>
+#include <tuple>
 
 #include "common.cuh"
 #include "prof.cuh"
@@ -43,6 +44,7 @@ struct GraphView {
     const int32_t* col;
     const int32_t* elab;
     const int32_t* P;        // P_i
+    unsigned long long* hout;   // nullable: receives each vertex's signature hash
 };
 
 struct HubView {
@@ -200,6 +202,7 @@ __global__ void __launch_bounds__(128) k_sig_small(const int32_t* __restrict__ l
     }
     cnt[v] = static_cast<int32_t>(u);
     const uint64_t h = sig_hash(G.P[v], u, sum) & t.hmask;
+    if (G.hout) G.hout[v] = h;
     slot[v] = table_insert(t, h, v, err);
 }
 
@@ -284,6 +287,7 @@ __global__ void __launch_bounds__(256) k_sig_warp(const int32_t* __restrict__ li
     if (lane == 0) {
         cnt[v] = static_cast<int32_t>(out);
         const uint64_t h = sig_hash(G.P[v], out, mys) & t.hmask;
+        if (G.hout) G.hout[v] = h;
         slot[v] = table_insert(t, h, v, err);
     }
 }
@@ -342,6 +346,7 @@ __global__ void __launch_bounds__(T) k_sig_mid(const int32_t* __restrict__ list,
         const unsigned total = n_out;
         cnt[v] = static_cast<int32_t>(total);
         const uint64_t h = sig_hash(G.P[v], total, tsum) & t.hmask;
+        if (G.hout) G.hout[v] = h;
         slot[v] = table_insert(t, h, v, err);
     }
 }
@@ -421,6 +426,7 @@ __global__ void k_hub_finalize(const int32_t* __restrict__ hubs, int64_t nh, Gra
     const unsigned c = acc[h].count;
     cnt[v] = static_cast<int32_t>(c);
     const uint64_t hv = sig_hash(G.P[v], c, acc[h].sum) & t.hmask;
+    if (G.hout) G.hout[v] = hv;
     slot[v] = table_insert(t, hv, v, err);
 }
 
@@ -585,18 +591,20 @@ void launch_deferred(bisim_ctx* ctx, const Mode& M, int32_t* Pout, int32_t* next
 }
 
 template <class Mode>
-bisim_status resolve(bisim_ctx* ctx, Mode M, int32_t* Pout, cudaStream_t s, int64_t* blocks) {
+bisim_status resolve(bisim_ctx* ctx, Mode M, int32_t* Pout, const int32_t* vlist, int64_t vcount, cudaStream_t s,
+                     int64_t* blocks) {
     const int32_t n = ctx->n;
+    const int64_t nv = vlist ? vcount : n;
     cudaError_t e;
     cudaMemsetAsync(ctx->dstate, 0, sizeof(DevState), s);
-    if (n > 0) {
+    if (nv > 0) {
         BISIM_SITE(site, Mode::kVerifySite);
-        Launch L(site, s, n, 0, Mode::kVerifyBytesPerVertex * n);
-        k_resolve_verify<Mode><<<grid_for(n, 256), 256, 0, s>>>(nullptr, n, ctx->alive, M, ctx->slot,
-                                                                ctx->table, Pout, ctx->ulist[0], ctx->dlist,
-                                                                ctx->dstate, n);
+        Launch L(site, s, nv, 0, Mode::kVerifyBytesPerVertex * nv);
+        k_resolve_verify<Mode><<<grid_for(nv, 256), 256, 0, s>>>(vlist, nv, ctx->alive, M, ctx->slot,
+                                                                 ctx->table, Pout, ctx->ulist[0], ctx->dlist,
+                                                                 ctx->dstate, n);
     }
-    if (n > 0) launch_deferred(ctx, M, Pout, ctx->ulist[0], s);
+    if (nv > 0) launch_deferred(ctx, M, Pout, ctx->ulist[0], s);
     cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "verify signatures");
     int which = 0;
@@ -639,28 +647,27 @@ bisim_status resolve(bisim_ctx* ctx, Mode M, int32_t* Pout, cudaStream_t s, int6
 constexpr double kSigBytesPerEdge = 12.0;
 constexpr double kSigBytesPerVertex = 24.0;
 
-constexpr int mid_class_of(int N) {
-    return N == 64 ? 0 : N == 128 ? 1 : N == 256 ? 2 : N == 512 ? 3 : N == 1024 ? 4 : N == 2048 ? 5 : N == 4096 ? 6 : 7;
-}
 
 template <int N>
-void launch_cta_mid(bisim_ctx* ctx, const int32_t* list, int64_t count, GraphView G, TableRef t, cudaStream_t s);
+void launch_cta_mid(bisim_ctx* ctx, const int32_t* list, int64_t count, int64_t edges, GraphView G, TableRef t,
+                    cudaStream_t s);
 
 template <int N>
-void launch_mid(bisim_ctx* ctx, const int32_t* list, int64_t count, GraphView G, TableRef t, cudaStream_t s) {
+void launch_mid(bisim_ctx* ctx, const int32_t* list, int64_t count, int64_t edges, GraphView G, TableRef t,
+                cudaStream_t s) {
     if constexpr (N <= 256) {
         static const int site = prof_site(N == 64 ? "sig_warp_64" : N == 128 ? "sig_warp_128" : "sig_warp_256");
-        const int64_t edges = ctx->class_edges[kSmallClasses + mid_class_of(N)];
         Launch L(site, s, count, edges, kSigBytesPerEdge * edges + kSigBytesPerVertex * count);
         k_sig_warp<N><<<grid_for(count, 8), 256, 0, s>>>(list, count, G, ctx->cnt, ctx->skey, ctx->slot, t,
                                                          &ctx->dstate->error);
     } else {
-        launch_cta_mid<N>(ctx, list, count, G, t, s);
+        launch_cta_mid<N>(ctx, list, count, edges, G, t, s);
     }
 }
 
 template <int N>
-void launch_cta_mid(bisim_ctx* ctx, const int32_t* list, int64_t count, GraphView G, TableRef t, cudaStream_t s) {
+void launch_cta_mid(bisim_ctx* ctx, const int32_t* list, int64_t count, int64_t edges, GraphView G, TableRef t,
+                    cudaStream_t s) {
     constexpr int T = N <= 1024 ? 256 : 512;
     const size_t smem = sizeof(unsigned long long) * 2 * N;
     static bool attr_set = false;   // per process; the attribute belongs to the function
@@ -671,7 +678,6 @@ void launch_cta_mid(bisim_ctx* ctx, const int32_t* list, int64_t count, GraphVie
     static const int site = prof_site(N == 64 ? "sig_mid_64" : N == 128 ? "sig_mid_128" : N == 256 ? "sig_mid_256"
                                       : N == 512 ? "sig_mid_512" : N == 1024 ? "sig_mid_1024" : N == 2048 ? "sig_mid_2048"
                                       : N == 4096 ? "sig_mid_4096" : "sig_mid_8192");
-    const int64_t edges = ctx->class_edges[kSmallClasses + mid_class_of(N)];
     Launch L(site, s, count, edges, kSigBytesPerEdge * edges + kSigBytesPerVertex * count);
     k_sig_mid<N, T><<<static_cast<unsigned>(count), T, smem, s>>>(list, G, ctx->cnt, ctx->skey, ctx->slot, t,
                                                                   &ctx->dstate->error);
@@ -756,33 +762,49 @@ bisim_status compute_p0(bisim_ctx* ctx, cudaStream_t s) {
                                                                           ctx->slot, t, &ctx->dstate->error);
     }
     int64_t blocks = 0;
-    bisim_status st = resolve(ctx, M, ctx->P0, s, &blocks);
+    bisim_status st = resolve(ctx, M, ctx->P0, nullptr, 0, s, &blocks);
     if (st != BISIM_OK) return st;
     ctx->last_blocks = blocks;
     ctx->stats.num_blocks = blocks;
     return BISIM_OK;
 }
 
-bisim_status refine_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
-    const int32_t* P = ctx->P[ctx->cur];
-    int32_t* Pn = ctx->P[ctx->cur ^ 1];
-    GraphView G{ctx->row_ptr, ctx->col, ctx->elab, P};
-    pin_partition_in_l2(ctx, P, s);
+Buckets ctx_buckets(const bisim_ctx* ctx) {
+    Buckets B;
+    B.class_list = ctx->class_list;
+    for (int c = 0; c <= kNumClasses; ++c) B.begin[c] = ctx->class_begin[c];
+    for (int c = 0; c < kNumClasses; ++c) B.edges[c] = ctx->class_edges[c];
+    B.hub_list = ctx->hub_list;
+    B.n_hub = ctx->n_hub;
+    B.chunks = ctx->chunks;
+    B.n_chunks = ctx->n_chunks;
+    B.toff = ctx->hub_toff;
+    B.tmask = ctx->hub_tmask;
+    B.tab = ctx->hub_tab;
+    B.tab_words = ctx->hub_tab_words;
+    B.acc = ctx->hub_acc;
+    return B;
+}
+
+bisim_status signature_round(bisim_ctx* ctx, const Buckets& B, const int32_t* Pin, int32_t* Pout,
+                             const int32_t* vlist, int64_t vcount, unsigned long long* hout, cudaStream_t s,
+                             int64_t* out_blocks) {
+    GraphView G{ctx->row_ptr, ctx->col, ctx->elab, Pin, hout};
     TableRef t = next_epoch(ctx, s);
-    if (ctx->n_hub > 0) {
-        cudaMemsetAsync(ctx->hub_tab, 0, sizeof(unsigned long long) * ctx->hub_tab_words, s);
-        cudaMemsetAsync(ctx->hub_acc, 0, sizeof(HubAcc) * ctx->n_hub, s);
+    if (B.n_hub > 0) {
+        cudaMemsetAsync(B.tab, 0, sizeof(unsigned long long) * B.tab_words, s);
+        cudaMemsetAsync(B.acc, 0, sizeof(HubAcc) * B.n_hub, s);
     }
-    const int64_t* cb = ctx->class_begin;
+    const int64_t* cb = B.begin;
     unsigned* err = &ctx->dstate->error;
     static const int small_site[kSmallClasses] = {prof_site("sig_small_4"), prof_site("sig_small_8"),
                                                    prof_site("sig_small_16"), prof_site("sig_small_32")};
     auto small = [&](int c, auto kern) {
         const int64_t cnt = cb[c + 1] - cb[c];
         if (cnt > 0) {
-            const int64_t edges = ctx->class_edges[c];
+            const int64_t edges = B.edges[c];
             Launch L(small_site[c], s, cnt, edges, kSigBytesPerEdge * edges + kSigBytesPerVertex * cnt);
-            kern<<<grid_for(cnt, 128), 128, 0, s>>>(ctx->class_list + cb[c], cnt, G, ctx->cnt, ctx->skey,
+            kern<<<grid_for(cnt, 128), 128, 0, s>>>(B.class_list + cb[c], cnt, G, ctx->cnt, ctx->skey,
                                                    ctx->slot, t, err);
         }
     };
@@ -790,27 +812,30 @@ bisim_status refine_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     small(1, k_sig_small<8>);
     small(2, k_sig_small<16>);
     small(3, k_sig_small<32>);
-    auto mid = [&](int c) { return std::make_pair(ctx->class_list + cb[kSmallClasses + c], cb[kSmallClasses + c + 1] - cb[kSmallClasses + c]); };
-    { auto [l, c] = mid(0); if (c > 0) launch_mid<64>(ctx, l, c, G, t, s); }
-    { auto [l, c] = mid(1); if (c > 0) launch_mid<128>(ctx, l, c, G, t, s); }
-    { auto [l, c] = mid(2); if (c > 0) launch_mid<256>(ctx, l, c, G, t, s); }
-    { auto [l, c] = mid(3); if (c > 0) launch_mid<512>(ctx, l, c, G, t, s); }
-    { auto [l, c] = mid(4); if (c > 0) launch_mid<1024>(ctx, l, c, G, t, s); }
-    { auto [l, c] = mid(5); if (c > 0) launch_mid<2048>(ctx, l, c, G, t, s); }
-    { auto [l, c] = mid(6); if (c > 0) launch_mid<4096>(ctx, l, c, G, t, s); }
-    { auto [l, c] = mid(7); if (c > 0) launch_mid<8192>(ctx, l, c, G, t, s); }
-    if (ctx->n_chunks > 0) {
+    auto mid = [&](int c) {
+        const int k = kSmallClasses + c;
+        return std::make_tuple(B.class_list + cb[k], cb[k + 1] - cb[k], B.edges[k]);
+    };
+    { auto [l, c, e] = mid(0); if (c > 0) launch_mid<64>(ctx, l, c, e, G, t, s); }
+    { auto [l, c, e] = mid(1); if (c > 0) launch_mid<128>(ctx, l, c, e, G, t, s); }
+    { auto [l, c, e] = mid(2); if (c > 0) launch_mid<256>(ctx, l, c, e, G, t, s); }
+    { auto [l, c, e] = mid(3); if (c > 0) launch_mid<512>(ctx, l, c, e, G, t, s); }
+    { auto [l, c, e] = mid(4); if (c > 0) launch_mid<1024>(ctx, l, c, e, G, t, s); }
+    { auto [l, c, e] = mid(5); if (c > 0) launch_mid<2048>(ctx, l, c, e, G, t, s); }
+    { auto [l, c, e] = mid(6); if (c > 0) launch_mid<4096>(ctx, l, c, e, G, t, s); }
+    { auto [l, c, e] = mid(7); if (c > 0) launch_mid<8192>(ctx, l, c, e, G, t, s); }
+    if (B.n_chunks > 0) {
         BISIM_SITE(site_hi, "hub_insert");
         BISIM_SITE(site_hf, "hub_finalize");
-        const int64_t hub_edges = ctx->class_edges[kClassHub];
+        const int64_t hub_edges = B.edges[kClassHub];
         {
             Launch L1(site_hi, s, 0, hub_edges, kSigBytesPerEdge * hub_edges);
-            k_hub_insert<<<static_cast<unsigned>(ctx->n_chunks), 256, 0, s>>>(ctx->chunks, G, ctx->hub_toff, ctx->hub_tmask,
-                                                                             ctx->hub_tab, ctx->hub_acc, ctx->skey, err);
+            k_hub_insert<<<static_cast<unsigned>(B.n_chunks), 256, 0, s>>>(B.chunks, G, B.toff, B.tmask, B.tab, B.acc,
+                                                                          ctx->skey, err);
         }
-        Launch L2(site_hf, s, ctx->n_hub, 0, kSigBytesPerVertex * ctx->n_hub);
-        k_hub_finalize<<<grid_for(ctx->n_hub, 128), 128, 0, s>>>(ctx->hub_list, ctx->n_hub, G, ctx->hub_acc,
-                                                                ctx->cnt, ctx->slot, t, err);
+        Launch L2(site_hf, s, B.n_hub, 0, kSigBytesPerVertex * B.n_hub);
+        k_hub_finalize<<<grid_for(B.n_hub, 128), 128, 0, s>>>(B.hub_list, B.n_hub, G, B.acc, ctx->cnt, ctx->slot, t,
+                                                             err);
     }
     cudaError_t e;
     if ((e = cudaGetLastError())) return cuda_error(ctx, e, "launch signature kernels");
@@ -818,10 +843,30 @@ bisim_status refine_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     M.G = G;
     M.cnt = ctx->cnt;
     M.skey = ctx->skey;
-    M.H = HubView{ctx->hub_list, ctx->n_hub, ctx->hub_toff, ctx->hub_tmask, ctx->hub_tab, ctx->hub_acc};
+    M.H = HubView{B.hub_list, B.n_hub, B.toff, B.tmask, B.tab, B.acc};
     M.small_max = ctx->opt.small_max_degree;
     M.mid_max = ctx->opt.mid_max_degree;
-    bisim_status st = resolve(ctx, M, Pn, s, out_blocks);
+    return resolve(ctx, M, Pout, vlist, vcount, s, out_blocks);
+}
+
+bisim_status label_group(bisim_ctx* ctx, const int32_t* vlist, int64_t vcount, int32_t* Pout, cudaStream_t s) {
+    TableRef t = next_epoch(ctx, s);
+    LabelMode M{ctx->vlabel, ctx->gid};
+    if (vcount > 0) {
+        BISIM_SITE(site, "label_insert");
+        Launch L(site, s, vcount, 0, 20.0 * vcount);
+        k_resolve_insert<LabelMode><<<grid_for(vcount, 256), 256, 0, s>>>(vlist, vcount, ctx->alive, M, 0u, ctx->slot,
+                                                                          t, &ctx->dstate->error);
+    }
+    int64_t blocks = 0;
+    return resolve(ctx, M, Pout, vlist, vcount, s, &blocks);
+}
+
+bisim_status refine_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
+    const int32_t* P = ctx->P[ctx->cur];
+    pin_partition_in_l2(ctx, P, s);
+    bisim_status st = signature_round(ctx, ctx_buckets(ctx), P, ctx->P[ctx->cur ^ 1], nullptr, 0, nullptr, s,
+                                      out_blocks);
     if (st != BISIM_OK) return st;
     ctx->cur ^= 1;
     return BISIM_OK;

@@ -181,3 +181,49 @@ def test_iterate_after_updates_uses_the_edited_graph(B):
                                 oracle.FIXPOINT, 50, alive=state["alive"])
     assert r == wr and np.array_equal(B.get_partition(ctx).cpu().numpy(), want)
     B.summarize_destroy(ctx)
+
+
+@pytest.mark.parametrize("opts", [dict(hash_bits=6), dict(small_max_degree=0, mid_max_degree=64, hub_chunk=256),
+                                  dict(flags=2)])
+def test_update_paths_and_forced_collisions(B, opts):
+    """Incremental maintenance with forced hash collisions, with every vertex on
+    the shared-memory / hub paths, and the full-recompute flag: all exact."""
+    rng = np.random.default_rng(99)
+    g = graphgen.powerlaw_graph(n=2000, m=16_000, dmax=1500, n_elabels=5, n_vlabels=3, seed=98)
+    state = dict(n=g["n"], alive=np.ones(g["n"], np.uint8), vlabel=g["vlabel"].copy(), src=g["src"],
+                 dst=g["dst"], elabel=g["elabel"])
+    ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]),
+                               options=B.default_options(k_incremental=2, **opts))
+    B.apply_updates(ctx, _dev(np.zeros((0, 4), np.int32)))
+    check_partition(B, ctx, state, 2)
+    for step in range(5):
+        ops = random_batch(rng, state, int(rng.integers(5, 120)), n_elabels=5, n_vlabels=3)
+        try:
+            state2 = oracle.apply_ops(state, ops)
+        except oracle.UpdateRejected:
+            continue
+        B.apply_updates(ctx, _dev(ops))
+        state = state2
+        check_partition(B, ctx, state, 2)
+    B.summarize_destroy(ctx)
+
+
+def test_many_small_batches_long_run(B):
+    """A longer stream of small batches (the serving pattern), every result checked."""
+    rng = np.random.default_rng(5150)
+    g = graphgen.powerlaw_graph(n=3000, m=24_000, dmax=2000, n_elabels=4, n_vlabels=3, seed=51)
+    state = dict(n=g["n"], alive=np.ones(g["n"], np.uint8), vlabel=g["vlabel"].copy(), src=g["src"],
+                 dst=g["dst"], elabel=g["elabel"])
+    ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]),
+                               options=B.default_options(k_incremental=2))
+    for step in range(40):
+        ops = random_batch(rng, state, int(rng.integers(1, 12)), n_elabels=4, n_vlabels=3)
+        try:
+            state2 = oracle.apply_ops(state, ops)
+        except oracle.UpdateRejected:
+            continue
+        B.apply_updates(ctx, _dev(ops))
+        state = state2
+        check_partition(B, ctx, state, 2)
+    assert B.bisim_get_stats(ctx)["last_frontier"] < state["n"]
+    B.summarize_destroy(ctx)
