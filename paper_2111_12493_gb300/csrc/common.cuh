@@ -251,6 +251,7 @@ struct bisim_ctx {
     int32_t* ibid[bisim::kMaxIncLevels + 1] = {};
     int64_t bnext[bisim::kMaxIncLevels + 1] = {};   // next unused block id
     int64_t itomb[bisim::kMaxIncLevels + 1] = {};   // tombstones in the index
+    void* inc_ws = nullptr;        // per-batch work buffers of the incremental path (kept between batches)
     int64_t bcap = 0;              // block records per level
     uint64_t isize = 0;            // index slots per level (power of two)
 

@@ -162,6 +162,15 @@ __global__ void k_list_bounds(const uint32_t* __restrict__ cls, const uint64_t* 
     atomicAdd(&edges[c], static_cast<unsigned long long>(rp[v + 1] - rp[v]));
 }
 
+__global__ void k_row_bounds(const int32_t* __restrict__ list, int64_t count, const int64_t* __restrict__ rp,
+                             int64_t* __restrict__ out) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < count) {
+        out[2 * i] = rp[list[i]];
+        out[2 * i + 1] = rp[list[i] + 1];
+    }
+}
+
 // ----------------------------------------------------------------------------- level passes
 
 // 1. frontier vertices leave their old blocks
@@ -627,16 +636,20 @@ bisim_status list_buckets(bisim_ctx* ctx, const int32_t* list, int64_t count, Sc
     B.hub_list = S.blist + begin[kClassHub];
     B.n_hub = begin[kClassHub + 1] - begin[kClassHub];
     if (B.n_hub == 0) return BISIM_OK;
-    // hub layout on the host: few vertices
+    // hub layout on the host: few vertices, their row bounds gathered in one copy
     std::vector<int32_t> hubs(B.n_hub);
+    std::vector<int64_t> bounds(2 * B.n_hub);
+    // the two sort value buffers are free again and adjacent: 16 bytes x n >= 2 x 8 bytes x hubs
+    int64_t* dbounds = reinterpret_cast<int64_t*>(S.cv0);
+    k_row_bounds<<<grid_for(B.n_hub, 256), 256, 0, s>>>(B.hub_list, B.n_hub, ctx->row_ptr, dbounds);
     cudaMemcpyAsync(hubs.data(), B.hub_list, sizeof(int32_t) * B.n_hub, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(bounds.data(), dbounds, sizeof(int64_t) * 2 * B.n_hub, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "read frontier hubs");
     std::vector<int64_t> rb(B.n_hub), re(B.n_hub);
     for (int64_t h = 0; h < B.n_hub; ++h) {
-        cudaMemcpyAsync(&rb[h], ctx->row_ptr + hubs[h], sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&re[h], ctx->row_ptr + hubs[h] + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        rb[h] = bounds[2 * h];
+        re[h] = bounds[2 * h + 1];
     }
-    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "read frontier hub rows");
     std::vector<HubChunk> chunks;
     std::vector<int64_t> toff(B.n_hub);
     std::vector<uint32_t> tmask(B.n_hub);
@@ -849,6 +862,12 @@ bisim_status write_output(bisim_ctx* ctx, cudaStream_t s) {
 
 void inc_release(bisim_ctx* ctx, cudaStream_t s) {
     const size_t n = static_cast<size_t>(std::max(ctx->n, 1));
+    if (ctx->inc_ws != nullptr) {
+        Scratch* S = static_cast<Scratch*>(ctx->inc_ws);
+        cudaFreeAsync(S->base, s);
+        delete S;
+        ctx->inc_ws = nullptr;
+    }
     for (int j = 0; j <= kMaxIncLevels; ++j) {
         ctx_free(ctx, ctx->lid[j], 4 * n, s);
         ctx_free(ctx, ctx->lcnt[j], 4 * n, s);
@@ -895,14 +914,19 @@ bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s) {
         cudaMemsetAsync(ctx->ikey[j], 0, 8 * is, s);
     }
     ctx->inc_k = K;
-    Scratch S;
-    if ((e = alloc_scratch(ctx, S, s))) return cuda_error(ctx, e, "alloc incremental scratch");
+    Scratch* Sp = new Scratch();
+    if ((e = alloc_scratch(ctx, *Sp, s))) {
+        delete Sp;
+        inc_release(ctx, s);
+        return cuda_error(ctx, e, "alloc incremental scratch");
+    }
+    ctx->inc_ws = Sp;
+    Scratch& S = *Sp;
     int64_t f = 0, fl = 0, rebuild = 0;
     st = make_frontier(ctx, S, nullptr, &f, &fl, s);
     for (int j = 0; st == BISIM_OK && j <= K; ++j) st = level_pass(ctx, j, S, f, fl, true, &rebuild, s);
     if (st == BISIM_OK && rebuild) st = set_error(ctx, BISIM_ENOMEM, "incremental state overflow during build");
     if (st == BISIM_OK) st = write_output(ctx, s);
-    cudaFreeAsync(S.base, s);
     if (st != BISIM_OK) {
         inc_release(ctx, s);
         return st;
@@ -926,8 +950,7 @@ bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* 
     const int K = ctx->inc_k;
     const int32_t n = ctx->n;
     cudaError_t e;
-    Scratch S;
-    if ((e = alloc_scratch(ctx, S, s))) return cuda_error(ctx, e, "alloc incremental scratch");
+    Scratch& S = *static_cast<Scratch*>(ctx->inc_ws);
     Work& W = S.W;
     int64_t f = 0, fl = 0, total = 0, rebuild = 0;
     st = make_frontier(ctx, S, vchanged, &f, &fl, s);
@@ -951,8 +974,10 @@ bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* 
         st = level_pass(ctx, j, S, f, fl, false, &rebuild, s);
         if (st == BISIM_OK && rebuild) break;
     }
-    cudaFreeAsync(S.base, s);
-    if (st != BISIM_OK) return st;
+    if (st != BISIM_OK) {
+        inc_release(ctx, s);      // the state may be half-updated: the next batch rebuilds it
+        return st;
+    }
     // out of block ids or index slots: start over from the current graph
     bool full = rebuild != 0;
     for (int j = 0; j <= K; ++j)

@@ -145,118 +145,127 @@ __global__ void k_key_halves(const bisim_op* __restrict__ ops, const uint64_t* _
     }
 }
 
-struct RemoveRec {
-    int32_t u, w, l, count;
-};
 struct AddRec {
     int32_t u, w, l, pad;
 };
 
-// One CTA per run of equal key hashes (normally one key): count the key's
-// current copies in row u, fold the key's operations, and emit the net change.
-__global__ void __launch_bounds__(128) k_fold_keys(VertexOps V, const uint32_t* __restrict__ khi,
-                                                   const uint32_t* __restrict__ klo,
-                                                   const uint64_t* __restrict__ kpos, int64_t ne,
-                                                   const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                   const int32_t* __restrict__ elab,
-                                                   const uint8_t* __restrict__ killed,
-                                                   RemoveRec* __restrict__ rem, AddRec* __restrict__ add,
-                                                   unsigned long long* __restrict__ counters,
-                                                   uint8_t* __restrict__ rowchg) {
-    __shared__ int red[4];
-    for (int64_t i = blockIdx.x; i < ne; i += gridDim.x) {
-        const bool head = i == 0 || khi[i] != khi[i - 1] || klo[i] != klo[i - 1];
-        if (!head) continue;                                    // uniform across the CTA
-        int64_t end = i + 1;
-        while (end < ne && khi[end] == khi[i] && klo[end] == klo[i]) ++end;
-        // distinct full keys inside the run, in order of first appearance
-        for (int64_t a = i; a < end; ++a) {
-            const bisim_op oa = V.ops[kpos[a]];
-            bool first = true;
-            for (int64_t b = i; b < a; ++b) {
-                const bisim_op ob = V.ops[kpos[b]];
-                if (ob.src == oa.src && ob.dst == oa.dst && ob.label == oa.label) { first = false; break; }
-            }
-            if (!first) continue;
-            const int32_t u = oa.src, w = oa.dst, l = oa.label;
-            const bool dropped = killed[u] || killed[w];          // initial copies go with the deletion
-            int c0 = 0;
-            if (!dropped) {
-                int mine = 0;
-                for (int64_t e = rp[u] + threadIdx.x; e < rp[u + 1]; e += blockDim.x)
-                    mine += (col[e] == w && elab[e] == l) ? 1 : 0;
-                for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-                if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mine;
-                __syncthreads();
-                c0 = red[0] + red[1] + red[2] + red[3];
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) {
-                const int64_t lk = max(last_kill(V, u), last_kill(V, w));
-                int c = dropped ? 0 : c0;
-                for (int64_t b = a; b < end; ++b) {
-                    const uint64_t p = kpos[b];
-                    const bisim_op ob = V.ops[p];
-                    if (ob.src != u || ob.dst != w || ob.label != l) continue;
-                    if (static_cast<int64_t>(p) < lk) continue;     // before the last deletion: no effect
-                    if (ob.kind == BISIM_OP_EDGE_ADD) ++c;
-                    else if (c > 0) --c;
-                }
-                const int adds = dropped ? c : max(c - c0, 0);
-                const int removes = dropped ? 0 : max(c0 - c, 0);
-                if (removes > 0) {
-                    const unsigned long long r = atomicAdd(&counters[0], 1ull);
-                    rem[r] = RemoveRec{u, w, l, removes};
-                }
-                if (adds > 0) {
-                    const unsigned long long base = atomicAdd(&counters[1], static_cast<unsigned long long>(adds));
-                    for (int q = 0; q < adds; ++q) add[base + q] = AddRec{u, w, l, 0};
-                }
-                if (adds > 0 || removes > 0) rowchg[u] = 1;
-            }
-            __syncthreads();
+// A small open-addressing table of the batch's distinct edge keys (u, w, l):
+// per key the copies present before the batch (c0), the copies to remove and
+// the copies already marked for removal.
+struct KeyTable {
+    int32_t* u;
+    int32_t* w;
+    int32_t* l;
+    int32_t* used;
+    int32_t* c0;
+    int32_t* rem;
+    int32_t* taken;
+    uint32_t mask;
+};
+
+__device__ __forceinline__ uint32_t key_home(int32_t u, int32_t w, int32_t l, uint32_t mask) {
+    return static_cast<uint32_t>(edge_key_hash(u, w, l)) & mask;
+}
+
+__device__ int64_t key_insert(const KeyTable& T, int32_t u, int32_t w, int32_t l) {
+    uint32_t pos = key_home(u, w, l, T.mask);
+    for (uint32_t probe = 0; probe <= T.mask; ++probe) {
+        if (atomicCAS(&T.used[pos], 0, 1) == 0) {
+            T.u[pos] = u;
+            T.w[pos] = w;
+            T.l[pos] = l;
+            return pos;
         }
+        pos = (pos + 1) & T.mask;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int64_t key_find(const KeyTable& T, int32_t u, int32_t w, int32_t l) {
+    uint32_t pos = key_home(u, w, l, T.mask);
+    for (uint32_t probe = 0; probe <= T.mask; ++probe) {
+        if (!T.used[pos]) return -1;
+        if (T.u[pos] == u && T.w[pos] == w && T.l[pos] == l) return pos;
+        pos = (pos + 1) & T.mask;
+    }
+    return -1;
+}
+
+// Every distinct key of the batch's edge operations enters the table once.
+__global__ void k_keys_insert(const bisim_op* __restrict__ ops, const uint32_t* __restrict__ khi,
+                              const uint32_t* __restrict__ klo, const uint64_t* __restrict__ kpos, int64_t ne,
+                              KeyTable T, int64_t* __restrict__ keyslot, unsigned* err) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < ne;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const bisim_op o = ops[kpos[i]];
+        // first appearance of this full key within its run of equal hashes
+        bool first = true;
+        for (int64_t b = i - 1; b >= 0 && khi[b] == khi[i] && klo[b] == klo[i]; --b) {
+            const bisim_op ob = ops[kpos[b]];
+            if (ob.src == o.src && ob.dst == o.dst && ob.label == o.label) { first = false; break; }
+        }
+        if (!first) { keyslot[i] = -1; continue; }
+        const int64_t slot = key_insert(T, o.src, o.dst, o.label);
+        if (slot < 0) atomicOr(err, 32u);
+        keyslot[i] = slot;
     }
 }
 
-// Marks the first `count` copies of (w, l) in row u (row order) as dropped.
-__global__ void __launch_bounds__(128) k_mark_removals(const RemoveRec* __restrict__ rem, int64_t nrem,
-                                                       const int64_t* __restrict__ rp,
-                                                       const int32_t* __restrict__ col,
-                                                       const int32_t* __restrict__ elab,
-                                                       uint8_t* __restrict__ drop) {
-    __shared__ int wsum[4];
-    __shared__ int running;
-    for (int64_t r = blockIdx.x; r < nrem; r += gridDim.x) {
-        const RemoveRec R = rem[r];
-        if (threadIdx.x == 0) running = 0;
-        __syncthreads();
-        for (int64_t e0 = rp[R.u]; e0 < rp[R.u + 1]; e0 += blockDim.x) {
-            const int64_t e = e0 + threadIdx.x;
-            const int hit = (e < rp[R.u + 1] && col[e] == R.w && elab[e] == R.l) ? 1 : 0;
-            const unsigned ball = __ballot_sync(0xffffffffu, hit);
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            if (lane == 0) wsum[warp] = __popc(ball);
-            __syncthreads();
-            int before = running;
-            for (int q = 0; q < warp; ++q) before += wsum[q];
-            const int rank = before + __popc(ball & ((1u << lane) - 1u));
-            if (hit && rank < R.count) drop[e] = 1;
-            __syncthreads();
-            if (threadIdx.x == 0) running += wsum[0] + wsum[1] + wsum[2] + wsum[3];
-            __syncthreads();
-            if (running >= R.count) break;
+// Copies of every batch key present before the batch (one pass over the edges).
+__global__ void k_keys_count(const int32_t* __restrict__ esrc, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ elab, int64_t m, KeyTable T) {
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t k = key_find(T, esrc[e], col[e], elab[e]);
+        if (k >= 0) atomicAdd(&T.c0[k], 1);
+    }
+}
+
+// One thread per distinct key: fold its operations in batch order, starting
+// after the last deletion of an endpoint, and record the net change.
+__global__ void k_fold_keys(VertexOps V, const uint32_t* __restrict__ khi, const uint32_t* __restrict__ klo,
+                            const uint64_t* __restrict__ kpos, int64_t ne, const int64_t* __restrict__ keyslot,
+                            KeyTable T, const uint8_t* __restrict__ killed, AddRec* __restrict__ add,
+                            unsigned long long* __restrict__ counters, uint8_t* __restrict__ rowchg) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < ne;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t slot = keyslot[i];
+        if (slot < 0) continue;                                // not the first appearance of its key
+        const bisim_op oa = V.ops[kpos[i]];
+        const int32_t u = oa.src, w = oa.dst, l = oa.label;
+        const bool dropped = killed[u] || killed[w];           // initial copies go with the deletion
+        const int c0 = dropped ? 0 : T.c0[slot];
+        const int64_t lk = max(last_kill(V, u), last_kill(V, w));
+        int c = c0;
+        int64_t end = i;
+        while (end < ne && khi[end] == khi[i] && klo[end] == klo[i]) ++end;
+        for (int64_t b = i; b < end; ++b) {
+            const uint64_t p = kpos[b];
+            const bisim_op ob = V.ops[p];
+            if (ob.src != u || ob.dst != w || ob.label != l) continue;
+            if (static_cast<int64_t>(p) < lk) continue;         // before the last deletion: no effect
+            if (ob.kind == BISIM_OP_EDGE_ADD) ++c;
+            else if (c > 0) --c;
         }
-        __syncthreads();
+        const int adds = dropped ? c : max(c - c0, 0);
+        const int removes = dropped ? 0 : max(c0 - c, 0);
+        T.rem[slot] = removes;
+        if (adds > 0) {
+            const unsigned long long base = atomicAdd(&counters[1], static_cast<unsigned long long>(adds));
+            for (int q = 0; q < adds; ++q) add[base + q] = AddRec{u, w, l, 0};
+        }
+        if (adds > 0 || removes > 0) rowchg[u] = 1;
     }
 }
 
 // ----------------------------------------------------------------------------- CSR rewrite
 
-__global__ void k_count_kept(const int32_t* __restrict__ esrc, const int32_t* __restrict__ col, int64_t m,
-                             const uint8_t* __restrict__ killed, const uint8_t* __restrict__ drop,
-                             int32_t* __restrict__ kept, uint8_t* __restrict__ rowdirty,
-                             uint8_t* __restrict__ rowchg) {
+// Which edges survive the batch: not incident to a deleted vertex, and not one
+// of the copies a key loses (any copies of one key are interchangeable).
+__global__ void k_count_kept(const int32_t* __restrict__ esrc, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ elab, int64_t m, const uint8_t* __restrict__ killed,
+                             KeyTable T, int use_table, uint8_t* __restrict__ keepf, int32_t* __restrict__ kept,
+                             uint8_t* __restrict__ rowdirty, uint8_t* __restrict__ rowchg) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t e0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; e0 < m; e0 += stride) {
         const int64_t e = e0 + threadIdx.x;
@@ -264,7 +273,13 @@ __global__ void k_count_kept(const int32_t* __restrict__ esrc, const int32_t* __
         bool keep = false;
         if (e < m) {
             u = esrc[e];
-            keep = !(killed[u] || killed[col[e]] || drop[e]);
+            const int32_t w = col[e];
+            keep = !(killed[u] || killed[w]);
+            if (keep && use_table) {
+                const int64_t k = key_find(T, u, w, elab[e]);
+                if (k >= 0 && T.rem[k] > 0 && atomicAdd(&T.taken[k], 1) < T.rem[k]) keep = false;
+            }
+            keepf[e] = keep ? 1 : 0;
             if (!keep) {
                 rowdirty[u] = 1;
                 rowchg[u] = 1;
@@ -290,69 +305,44 @@ __global__ void k_new_degree(const int32_t* __restrict__ kept, const int32_t* __
     if (v == n) deg[v] = 0;
 }
 
-// Rows without a dropped edge: every edge moves by the row's offset change.
-__global__ void k_copy_clean(const int32_t* __restrict__ esrc, const int32_t* __restrict__ col,
-                             const int32_t* __restrict__ elab, int64_t m, const int64_t* __restrict__ rp,
-                             const int64_t* __restrict__ nrp, const uint8_t* __restrict__ rowdirty,
-                             int32_t* __restrict__ ncol, int32_t* __restrict__ nelab, int32_t* __restrict__ nsrc) {
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int32_t u = esrc[e];
-        if (rowdirty[u]) continue;
-        const int64_t p = nrp[u] + (e - rp[u]);
-        ncol[p] = col[e];
-        nelab[p] = elab[e];
-        nsrc[p] = u;
-    }
-}
-
-// Rows with dropped edges: one CTA compacts the row, keeping row order.
-__global__ void __launch_bounds__(128) k_copy_dirty(const int32_t* __restrict__ rows, int64_t nrows,
-                                                    const int32_t* __restrict__ col, const int32_t* __restrict__ elab,
-                                                    const int64_t* __restrict__ rp, const int64_t* __restrict__ nrp,
-                                                    const uint8_t* __restrict__ killed,
-                                                    const uint8_t* __restrict__ drop, int32_t* __restrict__ ncol,
-                                                    int32_t* __restrict__ nelab, int32_t* __restrict__ nsrc) {
-    __shared__ int wsum[4];
-    __shared__ int running;
-    for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
-        const int32_t u = rows[r];
-        if (threadIdx.x == 0) running = 0;
-        __syncthreads();
-        const bool uk = killed[u] != 0;
-        for (int64_t e0 = rp[u]; e0 < rp[u + 1]; e0 += blockDim.x) {
-            const int64_t e = e0 + threadIdx.x;
-            const int keep = (e < rp[u + 1] && !uk && !killed[col[e]] && !drop[e]) ? 1 : 0;
-            const unsigned ball = __ballot_sync(0xffffffffu, keep);
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            if (lane == 0) wsum[warp] = __popc(ball);
-            __syncthreads();
-            int before = running;
-            for (int q = 0; q < warp; ++q) before += wsum[q];
-            if (keep) {
-                const int64_t p = nrp[u] + before + __popc(ball & ((1u << lane) - 1u));
-                ncol[p] = col[e];
-                nelab[p] = elab[e];
-                nsrc[p] = u;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) running += wsum[0] + wsum[1] + wsum[2] + wsum[3];
-            __syncthreads();
+// Kept edges move to the new CSR: rows without a dropped edge keep their order
+// (offset shift); rows with drops take places from a per-row cursor, a warp
+// reserving its share with one atomic (row order inside a row is irrelevant).
+__global__ void k_copy_kept(const int32_t* __restrict__ esrc, const int32_t* __restrict__ col,
+                            const int32_t* __restrict__ elab, int64_t m, const int64_t* __restrict__ rp,
+                            const int64_t* __restrict__ nrp, const uint8_t* __restrict__ rowdirty,
+                            const uint8_t* __restrict__ keepf, int32_t* __restrict__ dcursor,
+                            int32_t* __restrict__ ncol, int32_t* __restrict__ nelab, int32_t* __restrict__ nsrc) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t e0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; e0 < m; e0 += stride) {
+        const int64_t e = e0 + threadIdx.x;
+        int32_t u = -1;
+        bool keep = false, dirty = false;
+        if (e < m) {
+            u = esrc[e];
+            keep = keepf[e] != 0;
+            dirty = rowdirty[u] != 0;
+        }
+        const bool via_cursor = keep && dirty;
+        const int lane = static_cast<int>(threadIdx.x & 31);
+        const unsigned peers = __match_any_sync(0xffffffffu, via_cursor ? u : -1);
+        const unsigned takers = __ballot_sync(0xffffffffu, via_cursor) & peers;
+        const int leader = via_cursor ? __ffs(takers) - 1 : lane;
+        int base = 0;
+        if (via_cursor && lane == leader) base = atomicAdd(&dcursor[u], __popc(takers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        int64_t p = -1;
+        if (via_cursor) {
+            p = nrp[u] + base + __popc(takers & ((1u << lane) - 1u));
+        } else if (keep) {
+            p = nrp[u] + (e - rp[u]);
+        }
+        if (p >= 0) {
+            ncol[p] = col[e];
+            nelab[p] = elab[e];
+            nsrc[p] = u;
         }
     }
-}
-
-__global__ void k_rows_flagged(const uint8_t* __restrict__ flag, int32_t n, int32_t* __restrict__ out,
-                               unsigned long long* __restrict__ count) {
-    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const bool f = v < n && flag[v];
-    const unsigned ball = __ballot_sync(0xffffffffu, f);
-    if (!ball) return;
-    const int lane = threadIdx.x & 31;
-    unsigned long long base = 0;
-    if (lane == __ffs(ball) - 1) base = atomicAdd(count, static_cast<unsigned long long>(__popc(ball)));
-    base = __shfl_sync(0xffffffffu, base, __ffs(ball) - 1);
-    if (f) out[base + __popc(ball & ((1u << lane) - 1u))] = static_cast<int32_t>(v);
 }
 
 // Appended copies: one thread per record; records of a row are counted in order.
@@ -424,13 +414,16 @@ bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
     need(4 * nb); need(4 * nb); need(8 * nb); need(8 * nb);          // vertex-op keys / values (x2)
     need(4 * nb); need(4 * nb); need(4 * nb); need(4 * nb);          // edge key halves (x2 each)
     need(8 * nb); need(8 * nb); need(8 * nb); need(8 * nb);          // edge positions (x4)
-    need(sizeof(RemoveRec) * nb); need(sizeof(AddRec) * nb);
+    uint32_t tsize = 64;
+    while (tsize < 2u * static_cast<uint32_t>(std::min<int64_t>(nops, 1 << 30))) tsize <<= 1;
+    need(sizeof(AddRec) * nb); need(8 * nb);                          // additions, key slots
+    for (int q = 0; q < 7; ++q) need(4 * static_cast<size_t>(tsize)); // key table
     need(8 * 4);
     need(8 * tmpw);
-    need(std::max<int64_t>(m, 1));                                    // drop flags
+    need(std::max<int64_t>(m, 1));                                    // keep flags
     need(4 * (n + 1)); need(4 * (n + 1)); need(4 * (n + 1));          // kept, addcnt, cursor
+    need(4 * (n + 1));                                                // dirty-row cursor
     need(1 * (n + 1));                                                // rowdirty
-    need(4 * (n + 1));                                                // dirty row list
     need(8 * (n + 1));                                                // new degree
     char* scratch = nullptr;
     if ((e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s))) return cuda_error(ctx, e, "alloc update scratch");
@@ -448,16 +441,27 @@ bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
     uint64_t* kp1 = reinterpret_cast<uint64_t*>(carve(8 * nb));
     uint64_t* kp2 = reinterpret_cast<uint64_t*>(carve(8 * nb));
     uint64_t* kp3 = reinterpret_cast<uint64_t*>(carve(8 * nb));
-    RemoveRec* rem = reinterpret_cast<RemoveRec*>(carve(sizeof(RemoveRec) * nb));
     AddRec* add = reinterpret_cast<AddRec*>(carve(sizeof(AddRec) * nb));
+    int64_t* keyslot = reinterpret_cast<int64_t*>(carve(8 * nb));
+    KeyTable T;
+    int32_t* tab_arrays[7];
+    for (int q = 0; q < 7; ++q) tab_arrays[q] = reinterpret_cast<int32_t*>(carve(4 * static_cast<size_t>(tsize)));
+    T.u = tab_arrays[0];
+    T.w = tab_arrays[1];
+    T.l = tab_arrays[2];
+    T.used = tab_arrays[3];
+    T.c0 = tab_arrays[4];
+    T.rem = tab_arrays[5];
+    T.taken = tab_arrays[6];
+    T.mask = tsize - 1;
     unsigned long long* counters = reinterpret_cast<unsigned long long*>(carve(8 * 4));
     int64_t* tmp = reinterpret_cast<int64_t*>(carve(8 * tmpw));
-    uint8_t* drop = reinterpret_cast<uint8_t*>(carve(std::max<int64_t>(m, 1)));
+    uint8_t* keepf = reinterpret_cast<uint8_t*>(carve(std::max<int64_t>(m, 1)));
     int32_t* kept = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
     int32_t* addcnt = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
     int32_t* cursor = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
+    int32_t* dcursor = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
     uint8_t* rowdirty = reinterpret_cast<uint8_t*>(carve(n + 1));
-    int32_t* dirty_rows = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
     int64_t* ndeg = reinterpret_cast<int64_t*>(carve(8 * (n + 1)));
     auto fail = [&](bisim_status code, const char* msg) {
         cudaFreeAsync(base, s);
@@ -508,35 +512,40 @@ bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
     }
     cudaMemsetAsync(killed, 0, n + 1, s);
     cudaMemsetAsync(counters, 0, 8 * 4, s);
+    for (int q = 3; q < 7; ++q) cudaMemsetAsync(tab_arrays[q], 0, 4 * static_cast<size_t>(tsize), s);
     if (nv > 0) {
         Launch L(site_ops, s, 0, 0, 16.0 * nv);
         k_vertex_final<<<grid_for(nv, 256), 256, 0, s>>>(V, ctx->alive, ctx->vlabel, killed, vchanged);
     }
     if (ne > 0) {
+        {
+            Launch L(site_ops, s, 0, 0, 32.0 * ne);
+            k_keys_insert<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, skhi, sklo, skp, ne, T, keyslot, &ctx->dstate->error);
+        }
+        if (m > 0) {
+            Launch L(site_ops, s, 0, m, 12.0 * m);
+            k_keys_count<<<grid_for(m, 256), 256, 0, s>>>(ctx->esrc, ctx->col, ctx->elab, m, T);
+        }
         Launch L(site_ops, s, 0, 0, 32.0 * ne);
-        k_fold_keys<<<grid_for(ne, 1), 128, 0, s>>>(V, skhi, sklo, skp, ne, ctx->row_ptr, ctx->col, ctx->elab, killed,
-                                                   rem, add, counters, rowchg);
+        k_fold_keys<<<grid_for(ne, 128), 128, 0, s>>>(V, skhi, sklo, skp, ne, keyslot, T, killed, add, counters,
+                                                     rowchg);
     }
     unsigned long long hc[2] = {0, 0};
     cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); return cuda_error(ctx, e, "fold edge operations"); }
-    const int64_t nrem = static_cast<int64_t>(hc[0]);
     const int64_t nadd = static_cast<int64_t>(hc[1]);
 
     // 3. rewrite the CSR
     BISIM_SITE(site_csr, "update_csr");
-    cudaMemsetAsync(drop, 0, std::max<int64_t>(m, 1), s);
     cudaMemsetAsync(kept, 0, 4 * (n + 1), s);
     cudaMemsetAsync(addcnt, 0, 4 * (n + 1), s);
     cudaMemsetAsync(cursor, 0, 4 * (n + 1), s);
+    cudaMemsetAsync(dcursor, 0, 4 * (n + 1), s);
     cudaMemsetAsync(rowdirty, 0, n + 1, s);
-    if (nrem > 0) {
-        Launch L(site_csr, s, 0, 0, 16.0 * nrem);
-        k_mark_removals<<<grid_for(nrem, 1), 128, 0, s>>>(rem, nrem, ctx->row_ptr, ctx->col, ctx->elab, drop);
-    }
     if (m > 0) {
-        Launch L(site_csr, s, 0, m, 9.0 * m);
-        k_count_kept<<<grid_for(m, 256), 256, 0, s>>>(ctx->esrc, ctx->col, m, killed, drop, kept, rowdirty, rowchg);
+        Launch L(site_csr, s, 0, m, 13.0 * m);
+        k_count_kept<<<grid_for(m, 256), 256, 0, s>>>(ctx->esrc, ctx->col, ctx->elab, m, killed, T, ne > 0 ? 1 : 0,
+                                                     keepf, kept, rowdirty, rowchg);
     }
     if (nadd > 0) {
         Launch L(site_csr, s, 0, 0, 16.0 * nadd);
@@ -554,13 +563,6 @@ bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
     exclusive_scan_i64(ndeg, nrp, n + 1, tmp, s);
     int64_t new_m = 0;
     cudaMemcpyAsync(&new_m, nrp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    unsigned long long ndirty = 0;
-    cudaMemsetAsync(counters + 2, 0, 8, s);
-    if (n > 0) {
-        Launch L(site_csr, s, n, 0, 5.0 * n);
-        k_rows_flagged<<<grid_for(n, 256), 256, 0, s>>>(rowdirty, n, dirty_rows, counters + 2);
-    }
-    cudaMemcpyAsync(&ndirty, counters + 2, 8, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); cudaFreeAsync(nrp, s); return cuda_error(ctx, e, "size new CSR"); }
     int32_t *ncol = nullptr, *nelab = nullptr, *nsrc = nullptr;
     const size_t cap = static_cast<size_t>(std::max<int64_t>(new_m, 1));
@@ -571,15 +573,9 @@ bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
         return cuda_error(ctx, e, "alloc new CSR");
     }
     if (m > 0) {
-        Launch L(site_csr, s, 0, m, 24.0 * m);
-        k_copy_clean<<<grid_for(m, 256), 256, 0, s>>>(ctx->esrc, ctx->col, ctx->elab, m, ctx->row_ptr, nrp, rowdirty,
-                                                     ncol, nelab, nsrc);
-    }
-    if (ndirty > 0) {
-        Launch L(site_csr, s, static_cast<int64_t>(ndirty), 0, 0.0);
-        k_copy_dirty<<<grid_for(static_cast<int64_t>(ndirty), 1), 128, 0, s>>>(dirty_rows, static_cast<int64_t>(ndirty),
-                                                                               ctx->col, ctx->elab, ctx->row_ptr, nrp,
-                                                                               killed, drop, ncol, nelab, nsrc);
+        Launch L(site_csr, s, 0, m, 26.0 * m);
+        k_copy_kept<<<grid_for(m, 256), 256, 0, s>>>(ctx->esrc, ctx->col, ctx->elab, m, ctx->row_ptr, nrp, rowdirty,
+                                                    keepf, dcursor, ncol, nelab, nsrc);
     }
     if (nadd > 0) {
         Launch L(site_csr, s, 0, nadd, 24.0 * nadd);

@@ -269,3 +269,57 @@ def update_stream(base: dict, n_batches: int, min_ops: int = 1000, max_ops: int 
                 alive_idx = np.flatnonzero(alive)
         out.append(dict(ops=ops, arrival_s=t))
     return out
+
+
+def update_batches(base: dict, n_batches: int, min_ops: int = 1000, max_ops: int = 1_000_000,
+                   fixed_size: int | None = None, p_add: float = 0.70, p_edel: float = 0.25,
+                   n_elabels: int = 1000, elabel_s: float = 1.1, p_copy: float = 0.8,
+                   rate_hz: float = 200.0, seed: int = 50) -> list:
+    """Update batches for a large base graph, drawn in bulk so that every batch is valid.
+
+    Per batch: 70% EDGE_ADD (src uniform among live vertices, dst copied from
+    the target of a uniform base edge with probability p_copy else uniform live,
+    label Zipf(elabel_s)), 25% EDGE_DEL of a uniform base edge (a no-op if it is
+    already gone), 5% VERTEX_DEL of distinct live vertices, placed last in the
+    batch so that no EDGE_ADD of the batch names a vertex deleted before it.
+    Sizes are log-uniform in [min_ops, max_ops] unless fixed_size is given;
+    arrival times are Poisson at rate_hz. Returns dicts with `ops` (int32
+    [n_ops, 4] rows kind, src, dst, label) and `arrival_s`.
+    """
+    rng = _rng(seed)
+    n = base["n"]
+    bsrc, bdst, blab = base["src"], base["dst"], base["elabel"]
+    m = len(bsrc)
+    alive = np.ones(n, dtype=bool)
+    out = []
+    t = 0.0
+    for _ in range(n_batches):
+        size = fixed_size if fixed_size is not None else \
+            int(math.floor(math.exp(rng.uniform(math.log(min_ops), math.log(max_ops)))))
+        na, nd, nv = rng.multinomial(size, [p_add, p_edel, 1.0 - p_add - p_edel])
+        live = np.flatnonzero(alive)
+        src = live[rng.integers(0, len(live), na)]
+        if m > 0:
+            cand = bdst[rng.integers(0, m, na)]
+        else:
+            cand = live[rng.integers(0, len(live), na)]
+        uni = live[rng.integers(0, len(live), na)]
+        dst = np.where((rng.random(na) < p_copy) & alive[cand], cand, uni)
+        lab = zipf_labels(rng, na, n_elabels, elabel_s)
+        adds = np.stack([np.zeros(na, np.int64), src, dst, lab], axis=1)
+        if m > 0 and nd > 0:
+            e = rng.integers(0, m, nd)
+            dels = np.stack([np.ones(nd, np.int64), bsrc[e], bdst[e], blab[e]], axis=1)
+        else:
+            dels = np.zeros((0, 4), np.int64)
+        nv = min(nv, max(0, len(live) - 1))
+        vd = rng.choice(live, size=nv, replace=False) if nv > 0 else np.zeros(0, np.int64)
+        vdel = np.stack([np.full(nv, OP_VERTEX_DEL, np.int64), vd, np.zeros(nv, np.int64),
+                         np.zeros(nv, np.int64)], axis=1)
+        body = np.concatenate([adds, dels])
+        body = body[rng.permutation(len(body))]
+        ops = np.concatenate([body, vdel]).astype(np.int32)
+        alive[vd] = False
+        t += rng.exponential(1.0 / rate_hz)
+        out.append(dict(ops=ops, arrival_s=t))
+    return out
