@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (smoke runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the update-batch latency section")
+    ap.add_argument("--serving-batches", type=int, default=40)
     return ap.parse_args()
 
 
@@ -285,6 +287,10 @@ def run_ours(args, world, rank, local):
                            "GB/s": round(p["alg_bytes"] / (p["total_ms"] / 1e3) / 1e9, 1) if p["total_ms"] else None}
                           for p in prof if p["launches"]), key=lambda x: -x["ms"])[:12]
 
+    serving_info = None
+    if not args.no_serving:
+        serving_info = run_serving(args, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.scale)
@@ -300,9 +306,119 @@ def run_ours(args, world, rank, local):
             "e2e": e2e, "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu,
             "gpu_launches": int(launches), "clocks": clock_info,
             "buckets": {"small": stats["n_small"], "mid": stats["n_mid"], "hub": stats["n_hub"]},
-            "collision_levels": stats["collision_levels"]}
+            "collision_levels": stats["collision_levels"], "serving": serving_info}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- update-batch latency
+
+SERVING = dict(n=5_000_000, m=50_000_000, k=2, rate_hz=200.0, min_ops=1000, max_ops=1_000_000, seed=5)
+
+
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs) * 1e3, q)) if len(xs) else None
+
+
+def run_serving(args, local):
+    """Resident 5M/50M graph at k=2 under update batches: incremental vs full recompute.
+
+    closed loop: fixed 1k-op batches, each applied and its partition read back
+    before the next; latency = apply_updates + get_partition, ops staged from
+    pinned host memory inside the timed call. Full recompute = the same batch
+    applied to a second resident context that recomputes all k rounds over the
+    whole edited graph (BISIM_FLAG_FULL_RECOMPUTE).
+    open loop: batches of log-uniform size in [1k, 1M] ops arriving as a
+    Poisson process at 200/s, submitted to the request loop as they arrive;
+    latency = result time - arrival time (queueing included).
+    """
+    import torch
+    from paper_2111_12493_gb300 import bisim, graphgen, serving
+    n = max(1000, int(SERVING["n"] * args.scale))
+    m = max(10_000, int(SERVING["m"] * args.scale))
+    g = graphgen.powerlaw_graph(n=n, m=m, exponent=WORKLOAD["exponent"], dmax=min(WORKLOAD["dmax"], m // 10),
+                                n_elabels=WORKLOAD["n_elabels"], n_vlabels=WORKLOAD["n_vlabels"],
+                                untyped_frac=WORKLOAD["untyped"], seed=SERVING["seed"])
+    dev = torch.device("cuda", local)
+    d = {k: torch.from_numpy(g[k]).to(dev) for k in ("src", "dst", "elabel", "vlabel")}
+    empty = torch.zeros((0, 4), dtype=torch.int32, device=dev)
+    out = {"workload": f"power-law digraph {n:,} vertices / {m:,} edges (generator as above), k=2 maintained "
+                       f"under update batches of 70% edge adds / 25% edge deletes / 5% vertex deletes"}
+
+    def ctx_for(flags):
+        c = bisim.summarize_init_coo(n, d["src"], d["dst"], d["elabel"], d["vlabel"],
+                                     options=bisim.default_options(k_incremental=SERVING["k"], flags=flags))
+        bisim.apply_updates(c, empty)
+        return c
+
+    # closed loop, 1k-op batches
+    fixed = graphgen.update_batches(g, 33, fixed_size=1000, seed=51)
+    pinned = [torch.from_numpy(b["ops"]).pin_memory() for b in fixed]
+    res = {}
+    for mode, flags in (("incremental", 0), ("full_recompute", bisim.FLAG_FULL_RECOMPUTE)):
+        ctx = ctx_for(flags)
+        part = torch.empty(n, dtype=torch.int32, device=dev)
+        lat, fr = [], []
+        for i, ops in enumerate(pinned):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bisim.apply_updates(ctx, ops)
+            bisim.get_partition(ctx, out=part)
+            torch.cuda.synchronize()
+            if i >= 3:                          # the first three batches are warm-up
+                lat.append(time.perf_counter() - t0)
+                fr.append(bisim.bisim_get_stats(ctx)["last_frontier"])
+        res[mode] = dict(p50_ms=_pct(lat, 50), p99_ms=_pct(lat, 99), batches=len(lat),
+                         mean_frontier=float(np.mean(fr)))
+        res[mode + "_P"] = part.cpu().numpy()
+        bisim.summarize_destroy(ctx)
+    same = bool(np.array_equal(res.pop("incremental_P"), res.pop("full_recompute_P")))
+    out["batch_1k"] = dict(res, identical_partitions=same,
+                           p99_speedup=res["full_recompute"]["p99_ms"] / res["incremental"]["p99_ms"])
+
+    # open loop through the request loop, log-uniform sizes, Poisson arrivals
+    batches = graphgen.update_batches(g, args.serving_batches, min_ops=SERVING["min_ops"],
+                                      max_ops=int(SERVING["max_ops"] * min(1.0, args.scale)),
+                                      rate_hz=SERVING["rate_hz"], seed=52)
+    pinned = [torch.from_numpy(b["ops"]).pin_memory() for b in batches]
+    srv = serving.Server(slots=2)
+    srv.summarize("g", n, d["src"], d["dst"], d["elabel"], d["vlabel"], k=SERVING["k"], keep=True,
+                  k_incremental=SERVING["k"]).result()
+    futs = []
+    t_start = time.perf_counter()
+    for b, ops in zip(batches, pinned):
+        wait = t_start + b["arrival_s"] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        futs.append(srv.update("g", ops))
+    for f in futs:
+        f.result()
+    span = time.perf_counter() - t_start
+    reqs = [r for r in srv.scheduler.completed if r.kind == "update"]
+    srv.close()
+    lat = [r.finished - r.arrival for r in reqs]
+    svc = [r.finished - r.started for r in reqs]
+    n_ops = int(sum(len(b["ops"]) for b in batches))
+    # the same batches as full recomputes (service time only)
+    ctx = ctx_for(bisim.FLAG_FULL_RECOMPUTE)
+    part = torch.empty(n, dtype=torch.int32, device=dev)
+    full = []
+    for ops in pinned:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bisim.apply_updates(ctx, ops)
+        bisim.get_partition(ctx, out=part)
+        torch.cuda.synchronize()
+        full.append(time.perf_counter() - t0)
+    bisim.summarize_destroy(ctx)
+    out["open_loop"] = dict(batches=len(reqs), ops=n_ops, sizes="log-uniform [1k, 1M] ops",
+                            arrival_rate_hz=SERVING["rate_hz"], wall_s=span,
+                            latency_p50_ms=_pct(lat, 50), latency_p99_ms=_pct(lat, 99),
+                            service_p50_ms=_pct(svc, 50), service_p99_ms=_pct(svc, 99),
+                            full_recompute_service_p50_ms=_pct(full, 50),
+                            full_recompute_service_p99_ms=_pct(full, 99),
+                            utilisation=sum(svc) / span)
+    return out
 
 
 # ----------------------------------------------------------------------------- oracle on the host cores
