@@ -217,14 +217,20 @@ bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s) {
 bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
                         int32_t* out_executed, int64_t* out_blocks) {
     cudaError_t e;
+    bisim_status pst = dense_prepare(ctx, s);
+    if (pst != BISIM_OK) return pst;
+    if (ctx->opt.mem_budget_bytes > 0 && ctx->device_bytes > ctx->opt.mem_budget_bytes)
+        return set_error(ctx, BISIM_ENOMEM, "context exceeds the memory budget");
     if (ctx->n > 0) cudaMemcpyAsync(ctx->P[0], ctx->P0, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToDevice, s);
+    dense_mark_dead(ctx, s);
     ctx->cur = 0;
     int64_t prev = ctx->last_blocks;   // |P_0|
     const int32_t limit = (k == BISIM_FIXPOINT) ? cap : k;
     int32_t rounds = limit, executed = 0;
     for (int32_t i = 0; i < limit; ++i) {
         int64_t blocks = 0;
-        bisim_status st = refine_round(ctx, s, &blocks);
+        pin_partition_in_l2(ctx, ctx->P[ctx->cur], s);
+        bisim_status st = dense_round(ctx, s, &blocks);
         if (st != BISIM_OK) {
             unpin_partition(ctx, s);
             return st;
@@ -442,6 +448,7 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
         free_temps(temps, s);
         if (st == BISIM_OK) {
             ctx->buckets_dirty = true;
+            ctx->dense_ready = false;
             if (!(ctx->opt.flags & BISIM_FLAG_FULL_RECOMPUTE) && ctx->inc_k == ctx->opt.k_incremental)
                 st = inc_update(ctx, vchanged, rowchg, s);
         }

@@ -22,6 +22,19 @@ constexpr int kClassHub = kSmallClasses + kMidClasses;   // 12
 constexpr int kNumClasses = kClassHub + 1;               // 13
 constexpr uint8_t kClassDead = 255;
 
+// Degree classes of the dense round layout (all live vertices every round):
+//   0..6   lane groups of G = 1, 1, 2, 4, 8, 16, 32 lanes per vertex for out-degree
+//          0, 1, 2, 3-4, 5-8, 9-16, 17-32
+//   7..9   one warp per vertex, shared-memory set of 2N slots, N = 64, 128, 256
+//   10..14 one CTA per vertex, N = 512 .. 8192
+//   15     hubs: chunks of one row spread over CTAs, set in global memory
+constexpr int kDGroupClasses = 7;
+constexpr int kDWarp0 = 7;
+constexpr int kDMid0 = 10;
+constexpr int kDHub = 15;
+constexpr int kDClasses = 16;
+constexpr uint32_t kDDead = 16;           // dead vertices sort after every class
+
 constexpr uint64_t kSaltKey = 0x243f6a8885a308d3ull;     // per-pair key -> m value
 constexpr uint64_t kSaltSig = 0x13198a2e03707344ull;     // own term of the signature hash
 constexpr uint64_t kSaltLabel = 0xa4093822299f31d0ull;   // label partition hash
@@ -101,7 +114,7 @@ struct DevState {
     unsigned int error;             // kErr* bits
     unsigned long long aux;
     unsigned int deferred;          // vertices whose set comparison is left to k_verify_deferred
-    unsigned int pad;
+    unsigned int pairs;             // dense rounds: small pairs left to a warp comparison
 };
 
 // Insert `h` (already masked) for vertex v; returns the slot index or ~0u on overflow.
@@ -139,6 +152,40 @@ __device__ __forceinline__ uint32_t table_insert(const TableRef& t, uint64_t h, 
 
 __device__ __forceinline__ int32_t table_rep(const Slot* slots, uint32_t pos) {
     return static_cast<int32_t>(static_cast<uint32_t>(slots[pos].w));
+}
+
+// ----------------------------------------------------------------------------- shared-memory sets
+
+// Inserts pair value mv into a shared-memory open-addressing set (0 = empty;
+// the value 0 itself is tracked by *zero). Returns true for the first inserter.
+__device__ __forceinline__ bool smem_set_insert(unsigned long long* tab, uint32_t mask, unsigned* zero,
+                                                unsigned long long mv) {
+    if (mv == 0ull) return atomicExch(zero, 1u) == 0u;
+    uint32_t pos = static_cast<uint32_t>(mv) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long cur = tab[pos];
+        if (cur == mv) return false;
+        if (cur == 0ull) {
+            const unsigned long long prev = atomicCAS(&tab[pos], 0ull, mv);
+            if (prev == 0ull) return true;
+            if (prev == mv) return false;
+        }
+        pos = (pos + 1) & mask;
+    }
+    return false;   // unreachable: the set has twice as many slots as keys
+}
+
+__device__ __forceinline__ bool smem_set_contains(const unsigned long long* tab, uint32_t mask, unsigned zero,
+                                                  unsigned long long mv) {
+    if (mv == 0ull) return zero != 0u;
+    uint32_t pos = static_cast<uint32_t>(mv) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long cur = tab[pos];
+        if (cur == mv) return true;
+        if (cur == 0ull) return false;
+        pos = (pos + 1) & mask;
+    }
+    return false;
 }
 
 // ----------------------------------------------------------------------------- hub tables
@@ -226,6 +273,30 @@ struct bisim_ctx {
     int64_t n_chunks = 0;
     bisim::HubAcc* hub_acc = nullptr;
 
+    // dense round layout: live vertices grouped by degree class (then the dead
+    // ones), their out-rows copied in that order as packed (label << 32 | target)
+    bool dense_ready = false;
+    int32_t* dvert = nullptr;                        // [n] position -> vertex
+    int32_t* dvpos = nullptr;                        // [n] vertex -> position
+    int64_t* dprp = nullptr;                         // [n_live + 1] row offsets into dpe
+    unsigned long long* dpe = nullptr;               // [m] packed edges in position order
+    int64_t dpe_cap = 0;
+    int64_t dbegin[bisim::kDClasses + 1] = {};       // class -> first position; dbegin[kDClasses] = n_live
+    int64_t dedge_begin[bisim::kDClasses + 1] = {};  // class -> first packed edge
+    uint32_t* dslot = nullptr;                       // [n] table slot per position
+    unsigned long long* dhash = nullptr;             // [n] signature hash per position
+    int32_t* dcnt = nullptr;                         // [n] |S| per position
+    int2* dpairs = nullptr;                          // [n] (position, representative's position) for a CTA compare
+    int2* dsmall = nullptr;                          // [n] the same for rows of at most 32 edges (warp compare)
+    bisim::HubChunk* dchunks = nullptr;
+    int64_t n_dchunks = 0;
+    int64_t* dtoff = nullptr;
+    uint32_t* dtmask = nullptr;
+    unsigned long long* dtab = nullptr;
+    int64_t dtab_words = 0;
+    bisim::HubAcc* dacc = nullptr;
+    int64_t n_dhub = 0;
+
     // collision resolution
     int32_t* ulist[2] = {nullptr, nullptr};
     int32_t* dlist = nullptr;      // vertices whose verification needs a set comparison
@@ -294,6 +365,8 @@ bisim_status build_buckets(bisim_ctx* ctx, cudaStream_t s);
 // ----------------------------------------------------------------------------- refinement (refine.cu)
 
 bisim_status compute_p0(bisim_ctx* ctx, cudaStream_t s);
+// Advances the signature table's epoch (clearing the table when it wraps).
+TableRef next_epoch(bisim_ctx* ctx, cudaStream_t s);
 bisim_status refine_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks);
 // One signature round over the vertices of `B` (all of them, or the `vcount`
 // listed in `vlist` for verification): Pout[v] = smallest listed vertex with
@@ -306,6 +379,7 @@ Buckets ctx_buckets(const bisim_ctx* ctx);
 // Groups the listed vertices by label: Pout[v] = smallest listed vertex with v's label.
 bisim_status label_group(bisim_ctx* ctx, const int32_t* vlist, int64_t vcount, int32_t* Pout, cudaStream_t s);
 bisim_status alloc_refine_state(bisim_ctx* ctx, cudaStream_t s);
+void pin_partition_in_l2(bisim_ctx* ctx, const int32_t* P, cudaStream_t s);
 void unpin_partition(bisim_ctx* ctx, cudaStream_t s);
 void launch_local_ids(const bisim_ctx* ctx, int32_t* out, cudaStream_t s);
 
@@ -321,6 +395,15 @@ bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
 bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
                         int32_t* out_executed, int64_t* out_blocks);
 bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- dense rounds (dense.cu)
+
+// Builds (or rebuilds after an edit) the dense round layout of the current CSR.
+bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s);
+// Writes -1 for the dead vertices into both partition buffers.
+void dense_mark_dead(bisim_ctx* ctx, cudaStream_t s);
+// One refinement round P[cur] -> P[cur ^ 1] over every live vertex.
+bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks);
 
 // ----------------------------------------------------------------------------- incremental levels (inc.cu)
 

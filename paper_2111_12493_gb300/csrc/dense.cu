@@ -1,0 +1,918 @@
+// Dense refinement rounds: every live vertex recomputes its signature in every
+// round (Algorithm 4, Section 3.3.1, made exact as in the definition of
+// Section 2.5).
+//
+// The out-CSR is copied once per graph version into a layout made for these
+// rounds. Live vertices are grouped by out-degree class ("positions", ascending
+// vertex id inside a class) and their rows are stored in position order as
+// packed 8-byte words (label << 32 | target). Consecutive threads then read
+// consecutive edges whatever the vertex ids are, and every class runs as one
+// kind of work unit:
+//   degree <= 32    a group of G lanes per vertex (G = next power of two >= d):
+//                   one edge per lane, duplicates found by a warp match on the
+//                   pair value, the set's size and sum reduced in the group;
+//   degree <= 256   one warp per vertex with a set in shared memory;
+//   degree <= 8192  one CTA per vertex with a set in shared memory;
+//   above           the row cut into chunks over many CTAs, deduplicated in a
+//                   per-hub set in global memory.
+// Each vertex's signature hash goes into the open-addressing table, whose slots
+// keep the smallest vertex (the canonical block id). A verification pass then
+// confirms every vertex against its slot's representative by recomputing both
+// pair sets (no list is stored): inside the lane group for small degrees, in a
+// CTA per pair otherwise. Vertices whose signature differs from their
+// representative's (a hash collision) are re-hashed with a new salt in further
+// levels; the smallest vertex of each level's group is final, so the loop ends
+// with the exact partition.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "prof.cuh"
+
+namespace bisim {
+
+namespace {
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+unsigned grid_for(int64_t n, int threads) {
+    return static_cast<unsigned>(std::max<int64_t>(1, cdiv(n, threads)));
+}
+
+constexpr int kMaxLevels = 1 << 16;
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+__device__ __forceinline__ unsigned long long pack_edge(int32_t label, int32_t target) {
+    return (static_cast<unsigned long long>(static_cast<uint32_t>(label)) << 32) | static_cast<uint32_t>(target);
+}
+
+__device__ __forceinline__ uint64_t packed_pair_value(unsigned long long pk, const int32_t* __restrict__ P) {
+    return pair_value(static_cast<int32_t>(pk >> 32), __ldg(P + static_cast<uint32_t>(pk)));
+}
+
+__device__ __forceinline__ int ceil_log2(int64_t d) {
+    return d <= 1 ? 0 : 64 - __clzll(static_cast<unsigned long long>(d - 1));
+}
+
+// Appends `flag` lanes' values to list[*counter ...] with one atomic per warp.
+template <class T>
+__device__ __forceinline__ void warp_push(bool flag, T value, T* list, unsigned* counter) {
+    const unsigned b = __ballot_sync(0xffffffffu, flag);
+    if (b == 0u) return;
+    const int leader = __ffs(b) - 1;
+    unsigned base = 0;
+    if (static_cast<int>(lane_id()) == leader) base = atomicAdd(counter, static_cast<unsigned>(__popc(b)));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (flag) list[base + __popc(b & lanemask_lt())] = value;
+}
+
+__device__ __forceinline__ void warp_count(bool flag, unsigned long long* counter) {
+    const unsigned b = __ballot_sync(0xffffffffu, flag);
+    if (b != 0u && static_cast<int>(lane_id()) == __ffs(b) - 1)
+        atomicAdd(counter, static_cast<unsigned long long>(__popc(b)));
+}
+
+// ----------------------------------------------------------------------------- layout kernels
+
+__global__ void k_dense_classify(const int64_t* __restrict__ rp, const uint8_t* __restrict__ alive, int32_t n,
+                                 int small_max, int mid_max, uint32_t* __restrict__ keys,
+                                 uint64_t* __restrict__ vals) {
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int64_t d = rp[v + 1] - rp[v];
+    uint32_t c;
+    if (alive != nullptr && !alive[v]) {
+        c = kDDead;
+    } else if (d == 0) {
+        c = 0;
+    } else if (d <= small_max) {
+        c = 1u + static_cast<uint32_t>(ceil_log2(d));                // 1..6
+    } else if (d <= mid_max) {
+        const int lg = max(6, ceil_log2(d));
+        c = lg <= 8 ? static_cast<uint32_t>(kDWarp0 + (lg - 6)) : static_cast<uint32_t>(kDMid0 + (lg - 9));
+    } else {
+        c = kDHub;
+    }
+    keys[v] = c;
+    vals[v] = static_cast<uint64_t>(v);
+}
+
+// begin[c] = first position of class c (classes absent in between start there too).
+__global__ void k_dense_bounds(const uint32_t* __restrict__ sk, int32_t n, int64_t* __restrict__ begin) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = static_cast<int>(min(sk[i], static_cast<uint32_t>(kDClasses)));
+    const int p = i == 0 ? -1 : static_cast<int>(min(sk[i - 1], static_cast<uint32_t>(kDClasses)));
+    for (int q = p + 1; q <= c; ++q) begin[q] = i;
+}
+
+__global__ void k_dense_vertices(const uint64_t* __restrict__ sv, int32_t n, int32_t* __restrict__ vert,
+                                 int32_t* __restrict__ vpos) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = static_cast<int32_t>(sv[i]);
+    vert[i] = v;
+    vpos[v] = static_cast<int32_t>(i);
+}
+
+__global__ void k_dense_degrees(const int32_t* __restrict__ vert, int64_t n_live, const int64_t* __restrict__ rp,
+                                int64_t* __restrict__ deg) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i > n_live) return;
+    if (i == n_live) {
+        deg[i] = 0;
+    } else {
+        const int32_t v = vert[i];
+        deg[i] = rp[v + 1] - rp[v];
+    }
+}
+
+// Rows of out-degree <= 32: one thread per position.
+__global__ void k_dense_pack_rows(const int32_t* __restrict__ vert, int64_t count, const int64_t* __restrict__ prp,
+                                  const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                  const int32_t* __restrict__ elab, unsigned long long* __restrict__ pe) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int32_t v = vert[i];
+    const int64_t b = rp[v];
+    const int64_t d = rp[v + 1] - b;
+    const int64_t o = prp[i];
+    for (int64_t j = 0; j < d; ++j) pe[o + j] = pack_edge(elab[b + j], col[b + j]);
+}
+
+// Longer rows: one CTA per position.
+__global__ void k_dense_pack_big(const int32_t* __restrict__ vert, int64_t first, const int64_t* __restrict__ prp,
+                                 const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                 const int32_t* __restrict__ elab, unsigned long long* __restrict__ pe) {
+    const int64_t i = first + blockIdx.x;
+    const int32_t v = vert[i];
+    const int64_t b = rp[v];
+    const int64_t d = rp[v + 1] - b;
+    const int64_t o = prp[i];
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) pe[o + j] = pack_edge(elab[b + j], col[b + j]);
+}
+
+__global__ void k_dense_dead(const int32_t* __restrict__ vert, int64_t first, int64_t n, int32_t* __restrict__ Pa,
+                             int32_t* __restrict__ Pb) {
+    const int64_t i = first + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = vert[i];
+    Pa[v] = -1;
+    Pb[v] = -1;
+}
+
+// ----------------------------------------------------------------------------- round kernels
+
+struct DenseView {
+    const int32_t* vert;               // position -> vertex
+    const int32_t* vpos;               // vertex -> position
+    const int64_t* prp;                // position -> offset into pe
+    const unsigned long long* pe;      // packed (label, target) rows
+    const int32_t* P;                  // P_i, by vertex
+    int32_t* cnt;                      // |S|, by position
+    unsigned long long* hash;          // signature hash, by position
+    uint32_t* slot;                    // table slot, by position
+};
+
+// The lane-group classes; CTAs are assigned to classes in order.
+struct GroupPlan {
+    int64_t cta_begin[kDGroupClasses + 1];
+    int64_t pos_begin[kDGroupClasses];
+    int64_t pos_end[kDGroupClasses];
+    int32_t gshift[kDGroupClasses];
+};
+
+struct WarpPlan {
+    int64_t cta_begin[4];
+    int64_t pos_begin[3];
+    int64_t pos_end[3];
+};
+
+__device__ __forceinline__ void finish_sig(const DenseView& D, int64_t pos, int32_t own, uint32_t c, uint64_t sum) {
+    D.cnt[pos] = static_cast<int32_t>(c);
+    D.hash[pos] = sig_hash(own, c, sum);
+}
+
+// Degree <= 32: one lane per edge in groups of G lanes per vertex.
+__global__ void __launch_bounds__(kThreads) k_dense_group_sig(const GroupPlan plan, const DenseView D) {
+    const int64_t b = blockIdx.x;
+    int c = 0;
+    while (c + 1 < kDGroupClasses && b >= plan.cta_begin[c + 1]) ++c;
+    const int gs = plan.gshift[c];
+    const unsigned G = 1u << gs;
+    const unsigned lane = lane_id();
+    const unsigned gl = lane & (G - 1u);
+    const unsigned gbase = lane & ~(G - 1u);
+    const unsigned gmask = G == 32u ? 0xffffffffu : ((1u << G) - 1u) << gbase;
+    const int64_t pos = plan.pos_begin[c] + (b - plan.cta_begin[c]) * (kThreads >> gs) + (threadIdx.x >> gs);
+    const bool valid = pos < plan.pos_end[c];
+    int32_t own = 0;
+    if (valid && gl == 0) own = D.P[D.vert[pos]];      // independent of the row: issued first
+    int64_t e0 = 0;
+    int d = 0;
+    if (valid) {
+        e0 = D.prp[pos];
+        d = static_cast<int>(D.prp[pos + 1] - e0);
+    }
+    const bool has = valid && static_cast<int>(gl) < d;
+    uint64_t mv = 0;
+    if (has) mv = packed_pair_value(__ldcs(D.pe + e0 + gl), D.P);
+    const unsigned hasm = __ballot_sync(0xffffffffu, has);
+    unsigned firstm = hasm;
+    if (G > 1u) {
+        // lanes holding the same pair value in one group: the lowest one counts it
+        const unsigned peers = __match_any_sync(0xffffffffu, static_cast<unsigned long long>(mv)) & hasm & gmask;
+        firstm = __ballot_sync(0xffffffffu, has && static_cast<unsigned>(__ffs(peers) - 1) == lane);
+    }
+    uint64_t sum = ((firstm >> lane) & 1u) ? mv : 0ull;
+    for (unsigned o = G >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (valid && gl == 0) finish_sig(D, pos, own, static_cast<uint32_t>(__popc(firstm & gmask)), sum);
+}
+
+// Degree <= 256: one warp per vertex, set of up to 512 slots in the warp's slice.
+constexpr int kWarpSlots = 512;
+__global__ void __launch_bounds__(kThreads) k_dense_warp_sig(const WarpPlan plan, const DenseView D) {
+    __shared__ unsigned long long sm_all[(kThreads / 32) * kWarpSlots];
+    __shared__ unsigned zero_all[kThreads / 32];
+    const int64_t b = blockIdx.x;
+    const int c = b >= plan.cta_begin[2] ? 2 : b >= plan.cta_begin[1] ? 1 : 0;
+    const int64_t cta0 = c == 2 ? plan.cta_begin[2] : c == 1 ? plan.cta_begin[1] : plan.cta_begin[0];
+    const int64_t pos0 = c == 2 ? plan.pos_begin[2] : c == 1 ? plan.pos_begin[1] : plan.pos_begin[0];
+    const int64_t pos1 = c == 2 ? plan.pos_end[2] : c == 1 ? plan.pos_end[1] : plan.pos_end[0];
+    const int warp = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    const int64_t pos = pos0 + (b - cta0) * (kThreads / 32) + warp;
+    if (pos >= pos1) return;                             // whole warp leaves together
+    const int32_t own = lane == 0 ? D.P[D.vert[pos]] : 0;
+    const int64_t e0 = D.prp[pos];
+    const int d = static_cast<int>(D.prp[pos + 1] - e0);
+    uint32_t S = 64;
+    while (S < 2u * static_cast<uint32_t>(d)) S <<= 1;
+    unsigned long long* tab = sm_all + warp * kWarpSlots;
+    for (uint32_t j = lane; j < S; j += 32) tab[j] = 0ull;
+    if (lane == 0) zero_all[warp] = 0u;
+    __syncwarp();
+    unsigned out = 0;
+    uint64_t mys = 0;
+    for (int j0 = 0; j0 < d; j0 += 32) {
+        const int j = j0 + static_cast<int>(lane);
+        bool fresh = false;
+        uint64_t mv = 0;
+        if (j < d) {
+            mv = packed_pair_value(__ldcs(D.pe + e0 + j), D.P);
+            fresh = smem_set_insert(tab, S - 1, &zero_all[warp], mv);
+        }
+        out += static_cast<unsigned>(__popc(__ballot_sync(0xffffffffu, fresh)));
+        if (fresh) mys += mv;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mys += __shfl_xor_sync(0xffffffffu, mys, o);
+    if (lane == 0) finish_sig(D, pos, own, out, mys);
+}
+
+// Degree <= N (N = 512 .. 8192): one CTA of T threads per vertex, set of 2N slots.
+template <int N, int T>
+__global__ void __launch_bounds__(T) k_dense_mid_sig(int64_t first, const DenseView D) {
+    extern __shared__ unsigned long long tab[];
+    __shared__ unsigned long long wsum[T / 32];
+    __shared__ unsigned wcnt[T / 32];
+    __shared__ unsigned zero;
+    constexpr uint32_t mask = 2 * N - 1;
+    const int64_t pos = first + blockIdx.x;
+    const int64_t e0 = D.prp[pos];
+    const int d = static_cast<int>(D.prp[pos + 1] - e0);
+    for (int j = threadIdx.x; j < 2 * N; j += T) tab[j] = 0ull;
+    if (threadIdx.x == 0) zero = 0u;
+    __syncthreads();
+    uint64_t mys = 0;
+    unsigned myc = 0;
+    for (int j = threadIdx.x; j < d; j += T) {
+        const uint64_t mv = packed_pair_value(__ldcs(D.pe + e0 + j), D.P);
+        if (smem_set_insert(tab, mask, &zero, mv)) {
+            mys += mv;
+            ++myc;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mys += __shfl_xor_sync(0xffffffffu, mys, o);
+        myc += __shfl_xor_sync(0xffffffffu, myc, o);
+    }
+    if (lane_id() == 0) {
+        wsum[threadIdx.x >> 5] = mys;
+        wcnt[threadIdx.x >> 5] = myc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t s = 0;
+        unsigned c = 0;
+        for (int w = 0; w < T / 32; ++w) {
+            s += wsum[w];
+            c += wcnt[w];
+        }
+        finish_sig(D, pos, D.P[D.vert[pos]], c, s);
+    }
+}
+
+struct HubSets {
+    int64_t first;                 // position of the first hub
+    int64_t n_hub;
+    const int64_t* toff;
+    const uint32_t* tmask;
+    unsigned long long* tab;
+    HubAcc* acc;
+};
+
+// Hubs, phase 1: every CTA inserts one chunk of a hub's row into the hub's set;
+// first inserters add their value to the hub's count and order-independent sum.
+__global__ void __launch_bounds__(kThreads) k_dense_hub_insert(const HubChunk* __restrict__ chunks, const DenseView D,
+                                                               const HubSets H, unsigned* err) {
+    __shared__ unsigned long long wsum[kThreads / 32];
+    __shared__ unsigned wcnt[kThreads / 32];
+    const HubChunk c = chunks[blockIdx.x];
+    unsigned long long* tab = H.tab + H.toff[c.hub];
+    const uint32_t mask = H.tmask[c.hub];
+    uint64_t lsum = 0;
+    unsigned lcnt = 0;
+    for (int64_t e = c.begin + threadIdx.x; e < c.end; e += kThreads) {
+        const uint64_t mv = packed_pair_value(__ldcs(D.pe + e), D.P);
+        bool fresh = false;
+        if (mv == 0ull) {
+            fresh = atomicOr(&H.acc[c.hub].zero, 1u) == 0u;
+        } else {
+            uint32_t p = static_cast<uint32_t>(mv) & mask;
+            uint32_t probe = 0;
+            for (; probe <= mask; ++probe) {
+                const unsigned long long cur = tab[p];
+                if (cur == mv) break;
+                if (cur == 0ull) {
+                    const unsigned long long prev = atomicCAS(&tab[p], 0ull, static_cast<unsigned long long>(mv));
+                    if (prev == 0ull) {
+                        fresh = true;
+                        break;
+                    }
+                    if (prev == mv) break;
+                }
+                p = (p + 1) & mask;
+            }
+            if (probe > mask) atomicOr(err, kErrHubFull);
+        }
+        if (fresh) {
+            lsum += mv;
+            ++lcnt;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        lcnt += __shfl_xor_sync(0xffffffffu, lcnt, o);
+    }
+    if (lane_id() == 0) {
+        wsum[threadIdx.x >> 5] = lsum;
+        wcnt[threadIdx.x >> 5] = lcnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t s = 0;
+        unsigned n = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            s += wsum[w];
+            n += wcnt[w];
+        }
+        if (n) {
+            atomicAdd(&H.acc[c.hub].sum, static_cast<unsigned long long>(s));
+            atomicAdd(&H.acc[c.hub].count, n);
+        }
+    }
+}
+
+// Hubs, phase 2: one thread per hub finishes its signature (the value 0, when
+// present, was counted by its first inserter).
+__global__ void k_dense_hub_finalize(const DenseView D, const HubSets H) {
+    const int64_t h = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (h >= H.n_hub) return;
+    const int64_t pos = H.first + h;
+    finish_sig(D, pos, D.P[D.vert[pos]], H.acc[h].count, H.acc[h].sum);
+}
+
+__device__ __forceinline__ bool hub_set_contains(const HubSets& H, int64_t h, uint64_t mv) {
+    if (mv == 0ull) return H.acc[h].zero != 0u;
+    const unsigned long long* tab = H.tab + H.toff[h];
+    const uint32_t mask = H.tmask[h];
+    uint32_t p = static_cast<uint32_t>(mv) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long cur = tab[p];
+        if (cur == mv) return true;
+        if (cur == 0ull) return false;
+        p = (p + 1) & mask;
+    }
+    return false;
+}
+
+// Table insert of every listed position (level 0: all live positions, list ==
+// null) with the level's salted hash. One thread per position.
+__global__ void __launch_bounds__(kThreads) k_dense_insert(const int32_t* __restrict__ list, int64_t count,
+                                                           const DenseView D, uint32_t level, const TableRef t,
+                                                           unsigned* err) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t pos = list ? list[i] : i;
+    const int32_t v = D.vert[pos];
+    D.slot[pos] = table_insert(t, level_hash(D.hash[pos], level, t.hmask), v, err);
+}
+
+struct VerifyOut {
+    int32_t* Pout;
+    int2* pairs;           // (position, representative's position) for k_dense_compare_cta
+    int2* small;           // the same for rows of at most 32 edges: k_dense_compare_warp
+    int32_t* next;         // positions for the next collision level
+    DevState* st;
+};
+
+// Confirms every listed position against its slot's representative r (its
+// smallest vertex). r itself: a block id. Different own block or set size: the
+// position moves to the next level. Otherwise the sets are compared: here when
+// both rows have at most two edges, else in a warp (rows <= 32) or a CTA.
+__global__ void __launch_bounds__(kThreads) k_dense_verify(const int32_t* __restrict__ list, int64_t count,
+                                                           const DenseView D, const Slot* __restrict__ slots,
+                                                           const VerifyOut O, int32_t n_total) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    bool own = false, push = false, small = false, big = false;
+    int64_t pos = -1, rpos = -1;
+    if (i < count) {
+        pos = list ? list[i] : i;
+        const int32_t v = D.vert[pos];
+        const uint32_t sv = D.slot[pos];
+        const int32_t r = sv == ~0u ? -1 : table_rep(slots, sv);
+        if (r < 0 || r >= n_total) {                     // failed insert, reported through st->error
+            atomicOr(&O.st->error, kErrTableFull);
+            O.Pout[v] = -1;
+        } else if (r == v) {
+            O.Pout[v] = v;
+            own = true;
+        } else {
+            rpos = D.vpos[r];
+            if (D.P[v] != D.P[r] || D.cnt[pos] != D.cnt[rpos]) {
+                push = true;
+            } else {
+                const int64_t ev = D.prp[pos], dv = D.prp[pos + 1] - ev;
+                const int64_t er = D.prp[rpos], dr = D.prp[rpos + 1] - er;
+                if (dv <= 2 && dr <= 2) {
+                    // S_v inside S_r with equal sizes means equal sets
+                    uint64_t b0 = 0, b1 = 0;
+                    if (dr > 0) b0 = packed_pair_value(D.pe[er], D.P);
+                    if (dr > 1) b1 = packed_pair_value(D.pe[er + 1], D.P);
+                    bool ok = true;
+                    for (int64_t j = 0; j < dv; ++j) {
+                        const uint64_t a = packed_pair_value(D.pe[ev + j], D.P);
+                        ok = ok && ((dr > 0 && a == b0) || (dr > 1 && a == b1));
+                    }
+                    if (ok) O.Pout[v] = r;
+                    else push = true;
+                } else if (dv <= 32 && dr <= 32) {
+                    small = true;
+                } else {
+                    big = true;
+                }
+            }
+        }
+    }
+    warp_count(own, &O.st->blocks);
+    warp_push(push, static_cast<int32_t>(pos), O.next, &O.st->unresolved);
+    warp_push(small, make_int2(static_cast<int32_t>(pos), static_cast<int32_t>(rpos)), O.small, &O.st->pairs);
+    warp_push(big, make_int2(static_cast<int32_t>(pos), static_cast<int32_t>(rpos)), O.pairs, &O.st->deferred);
+}
+
+constexpr int kCompareGrid = 304;                      // persistent grids: two CTAs per SM
+
+// Pairs whose rows have at most 32 edges: one warp per pair. Lane j holds the
+// j-th pair value of each row; S_v is inside S_r iff every value of v's row
+// matches one of r's. The pair count is read on the device.
+__global__ void __launch_bounds__(kThreads) k_dense_compare_warp(const int2* __restrict__ pairs, const DenseView D,
+                                                                 int32_t* __restrict__ Pout,
+                                                                 int32_t* __restrict__ next, DevState* st) {
+    const unsigned count = *reinterpret_cast<volatile unsigned*>(&st->pairs);
+    const unsigned lane = lane_id();
+    const unsigned warps = gridDim.x * (kThreads / 32);
+    for (unsigned i = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); i < count; i += warps) {
+        const int2 pr = pairs[i];
+        const int64_t ev = D.prp[pr.x], dv = D.prp[pr.x + 1] - ev;
+        const int64_t er = D.prp[pr.y], dr = D.prp[pr.y + 1] - er;
+        const bool ha = lane < dv, hb = lane < dr;
+        const uint64_t a = ha ? packed_pair_value(D.pe[ev + lane], D.P) : 0ull;
+        const uint64_t b = hb ? packed_pair_value(D.pe[er + lane], D.P) : 0ull;
+        bool found = false;
+        for (int k = 0; k < static_cast<int>(dr); ++k) {
+            const uint64_t bk = __shfl_sync(0xffffffffu, b, k);   // every lane takes part in every shuffle
+            found = found || bk == a;
+        }
+        const bool miss = __any_sync(0xffffffffu, ha && !found);
+        if (lane == 0) {
+            if (!miss) Pout[D.vert[pr.x]] = D.vert[pr.y];
+            else next[atomicAdd(&st->unresolved, 1u)] = pr.x;
+        }
+    }
+}
+
+constexpr int kCompareSlots = 2 * kMidMaxN;          // shared-memory set for sets up to 8192 values
+constexpr size_t kCompareSmem = sizeof(unsigned long long) * kCompareSlots;
+
+// Longer rows: one CTA per pair. S_r is rebuilt in shared memory from r's row
+// when it has at most 8192 values; a larger S_r belongs to a hub, whose set
+// from this round is probed instead.
+__global__ void __launch_bounds__(kThreads) k_dense_compare_cta(const int2* __restrict__ pairs, const DenseView D,
+                                                                const HubSets H, int32_t* __restrict__ Pout,
+                                                                int32_t* __restrict__ next, DevState* st) {
+    extern __shared__ unsigned long long tab[];
+    __shared__ unsigned zero;
+    const unsigned count = *reinterpret_cast<volatile unsigned*>(&st->deferred);
+    for (unsigned i = blockIdx.x; i < count; i += gridDim.x) {
+        const int2 pr = pairs[i];
+        const int32_t c = D.cnt[pr.y];
+        const int64_t ev = D.prp[pr.x], dv = D.prp[pr.x + 1] - ev;
+        const int64_t er = D.prp[pr.y], dr = D.prp[pr.y + 1] - er;
+        bool miss = false;
+        if (c > kMidMaxN) {
+            // |S_r| > 8192: r's row is longer than the CTA classes allow, so r is a hub
+            const int64_t h = static_cast<int64_t>(pr.y) - H.first;
+            if (h < 0 || h >= H.n_hub) {
+                miss = true;
+            } else {
+                for (int64_t j = threadIdx.x; j < dv && !miss; j += kThreads)
+                    miss = !hub_set_contains(H, h, packed_pair_value(D.pe[ev + j], D.P));
+            }
+        } else {
+            uint32_t size = 64;
+            while (size < 2u * static_cast<uint32_t>(c)) size <<= 1;
+            for (uint32_t j = threadIdx.x; j < size; j += kThreads) tab[j] = 0ull;
+            if (threadIdx.x == 0) zero = 0u;
+            __syncthreads();
+            for (int64_t j = threadIdx.x; j < dr; j += kThreads)
+                smem_set_insert(tab, size - 1, &zero, packed_pair_value(D.pe[er + j], D.P));
+            __syncthreads();
+            for (int64_t j = threadIdx.x; j < dv && !miss; j += kThreads)
+                miss = !smem_set_contains(tab, size - 1, zero, packed_pair_value(D.pe[ev + j], D.P));
+        }
+        const int any = __syncthreads_or(miss ? 1 : 0);
+        if (threadIdx.x == 0) {
+            if (!any) Pout[D.vert[pr.x]] = D.vert[pr.y];
+            else next[atomicAdd(&st->unresolved, 1u)] = pr.x;
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------- host helpers
+
+constexpr int kGroupShift[kDGroupClasses] = {0, 0, 1, 2, 3, 4, 5};
+
+GroupPlan group_plan(const bisim_ctx* ctx) {
+    GroupPlan p;
+    std::memset(&p, 0, sizeof(p));
+    int64_t cta = 0;
+    for (int c = 0; c < kDGroupClasses; ++c) {
+        p.cta_begin[c] = cta;
+        p.pos_begin[c] = ctx->dbegin[c];
+        p.pos_end[c] = ctx->dbegin[c + 1];
+        p.gshift[c] = kGroupShift[c];
+        cta += cdiv(p.pos_end[c] - p.pos_begin[c], kThreads >> p.gshift[c]);
+    }
+    p.cta_begin[kDGroupClasses] = cta;
+    return p;
+}
+
+WarpPlan warp_plan(const bisim_ctx* ctx) {
+    WarpPlan w;
+    int64_t cta = 0;
+    for (int c = 0; c < 3; ++c) {
+        w.cta_begin[c] = cta;
+        w.pos_begin[c] = ctx->dbegin[kDWarp0 + c];
+        w.pos_end[c] = ctx->dbegin[kDWarp0 + c + 1];
+        cta += cdiv(w.pos_end[c] - w.pos_begin[c], kThreads / 32);
+    }
+    w.cta_begin[3] = cta;
+    return w;
+}
+
+HubSets hub_sets(const bisim_ctx* ctx) {
+    return HubSets{ctx->dbegin[kDHub], ctx->n_dhub, ctx->dtoff, ctx->dtmask, ctx->dtab, ctx->dacc};
+}
+
+template <class K>
+void allow_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+}
+
+// Algorithmic bytes: the signature kernels move per edge the packed (label,
+// target) word 8 + the gathered P_i[w] 4, per vertex the row offset 8, the
+// vertex id 4, P_i[v] 4 and the 8-byte hash written; the insert moves per
+// vertex the hash 8, the vertex id 4, one 8-byte table slot and the 4-byte slot
+// index; the verification the slot index 4, the vertex id 4, one table slot 8
+// and P_{i+1}[v] 4.
+constexpr double kEdgeBytes = 12.0;
+constexpr double kSigVertexBytes = 24.0;
+constexpr double kInsertVertexBytes = 24.0;
+constexpr double kVerifyVertexBytes = 20.0;
+
+int64_t class_edges(const bisim_ctx* ctx, int c0, int c1) { return ctx->dedge_begin[c1] - ctx->dedge_begin[c0]; }
+
+template <int N, int T>
+void launch_mid(bisim_ctx* ctx, int cls, const DenseView& D, cudaStream_t s, int site) {
+    const int64_t first = ctx->dbegin[cls];
+    const int64_t count = ctx->dbegin[cls + 1] - first;
+    if (count <= 0) return;
+    const size_t smem = sizeof(unsigned long long) * 2 * N;
+    static bool attr = false;
+    if (!attr) {
+        allow_smem(k_dense_mid_sig<N, T>, smem);
+        attr = true;
+    }
+    const int64_t edges = class_edges(ctx, cls, cls + 1);
+    Launch L(site, s, count, edges, kSigVertexBytes * count + kEdgeBytes * edges);
+    k_dense_mid_sig<N, T><<<static_cast<unsigned>(count), T, smem, s>>>(first, D);
+}
+
+}  // namespace
+
+bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
+    if (ctx->dense_ready) return BISIM_OK;
+    const int32_t n = ctx->n;
+    const int64_t m = ctx->m;
+    const size_t nv = static_cast<size_t>(std::max(n, 1));
+    cudaError_t e;
+    if (ctx->dvert == nullptr) {
+        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dvert), sizeof(int32_t) * nv, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dvpos), sizeof(int32_t) * nv, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dprp), sizeof(int64_t) * (nv + 1), s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dslot), sizeof(uint32_t) * nv, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dhash), sizeof(unsigned long long) * nv, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dcnt), sizeof(int32_t) * nv, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dpairs), sizeof(int2) * nv, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dsmall), sizeof(int2) * nv, s)))
+            return cuda_error(ctx, e, "alloc dense round state");
+    }
+    if (m > ctx->dpe_cap || ctx->dpe == nullptr) {
+        ctx_free(ctx, ctx->dpe, sizeof(unsigned long long) * ctx->dpe_cap, s);
+        ctx->dpe = nullptr;
+        const int64_t cap = std::max<int64_t>(m, 1);
+        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dpe), sizeof(unsigned long long) * cap, s))) return cuda_error(ctx, e, "alloc packed rows");
+        ctx->dpe_cap = cap;
+    }
+    // the previous hub layout
+    ctx_free(ctx, ctx->dchunks, sizeof(HubChunk) * ctx->n_dchunks, s);
+    ctx_free(ctx, ctx->dtoff, sizeof(int64_t) * ctx->n_dhub, s);
+    ctx_free(ctx, ctx->dtmask, sizeof(uint32_t) * ctx->n_dhub, s);
+    ctx_free(ctx, ctx->dtab, sizeof(unsigned long long) * ctx->dtab_words, s);
+    ctx_free(ctx, ctx->dacc, sizeof(HubAcc) * ctx->n_dhub, s);
+    ctx->dchunks = nullptr;
+    ctx->dtoff = nullptr;
+    ctx->dtmask = nullptr;
+    ctx->dtab = nullptr;
+    ctx->dacc = nullptr;
+    ctx->n_dchunks = ctx->n_dhub = ctx->dtab_words = 0;
+
+    const size_t tmp_words = std::max(radix_temp_words(n), scan_temp_words(static_cast<int64_t>(n) + 1));
+    const size_t bytes = (sizeof(uint32_t) * 2 + sizeof(uint64_t) * 2) * nv + sizeof(int64_t) * (nv + 1) +
+                         sizeof(int64_t) * (tmp_words + kDClasses + 1) + 6 * 256;
+    char* scratch = nullptr;
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s))) return cuda_error(ctx, e, "alloc layout scratch");
+    char* base = scratch;
+    auto carve = [&](size_t b) { char* p = scratch; scratch += (b + 255) & ~size_t(255); return p; };
+    uint32_t* k0 = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * nv));
+    uint32_t* k1 = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * nv));
+    uint64_t* v0 = reinterpret_cast<uint64_t*>(carve(sizeof(uint64_t) * nv));
+    uint64_t* v1 = reinterpret_cast<uint64_t*>(carve(sizeof(uint64_t) * nv));
+    int64_t* deg = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * (nv + 1)));
+    int64_t* tmp = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * tmp_words));
+    int64_t* dbeg = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * (kDClasses + 1)));
+
+    int64_t begin[kDClasses + 1];
+    for (int c = 0; c <= kDClasses; ++c) begin[c] = n;
+    cudaMemcpyAsync(dbeg, begin, sizeof(begin), cudaMemcpyHostToDevice, s);
+    BISIM_SITE(site_c, "dense_classify");
+    BISIM_SITE(site_p, "dense_pack");
+    if (n > 0) {
+        {
+            Launch L(site_c, s, n, 0, 24.0 * n);
+            k_dense_classify<<<grid_for(n, 256), 256, 0, s>>>(ctx->row_ptr, ctx->alive, n, ctx->opt.small_max_degree,
+                                                             ctx->opt.mid_max_degree, k0, v0);
+        }
+        const int which = radix_sort_pairs(k0, v0, k1, v1, n, 5, tmp, s);
+        const uint32_t* sk = which ? k1 : k0;
+        const uint64_t* sv = which ? v1 : v0;
+        {
+            Launch L(site_c, s, n, 0, 8.0 * n);
+            k_dense_bounds<<<grid_for(n, 256), 256, 0, s>>>(sk, n, dbeg);
+        }
+        Launch L(site_c, s, n, 0, 12.0 * n);
+        k_dense_vertices<<<grid_for(n, 256), 256, 0, s>>>(sv, n, ctx->dvert, ctx->dvpos);
+    }
+    cudaMemcpyAsync(begin, dbeg, sizeof(begin), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) {
+        cudaFreeAsync(base, s);
+        return cuda_error(ctx, e, "classify vertices");
+    }
+    for (int c = kDClasses - 1; c >= 0; --c) begin[c] = std::min(begin[c], begin[c + 1]);
+    for (int c = 0; c <= kDClasses; ++c) ctx->dbegin[c] = begin[c];
+    const int64_t n_live = begin[kDClasses];
+    {
+        Launch L(site_c, s, n_live, 0, 28.0 * n_live);
+        k_dense_degrees<<<grid_for(n_live + 1, 256), 256, 0, s>>>(ctx->dvert, n_live, ctx->row_ptr, deg);
+    }
+    exclusive_scan_i64(deg, ctx->dprp, n_live + 1, tmp, s);
+    for (int c = 0; c <= kDClasses; ++c)
+        cudaMemcpyAsync(&ctx->dedge_begin[c], ctx->dprp + begin[c], sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    {
+        const int64_t small = begin[kDWarp0];
+        const int64_t big = n_live - small;
+        Launch L(site_p, s, n_live, m, 16.0 * m + 20.0 * n_live);
+        if (small > 0)
+            k_dense_pack_rows<<<grid_for(small, 256), 256, 0, s>>>(ctx->dvert, small, ctx->dprp, ctx->row_ptr, ctx->col,
+                                                                  ctx->elab, ctx->dpe);
+        if (big > 0)
+            k_dense_pack_big<<<static_cast<unsigned>(big), 256, 0, s>>>(ctx->dvert, small, ctx->dprp, ctx->row_ptr,
+                                                                       ctx->col, ctx->elab, ctx->dpe);
+    }
+
+    // hub chunks and sets (host-side layout; hubs are few)
+    const int64_t nh = begin[kDHub + 1] - begin[kDHub];
+    if (nh > 0) {
+        std::vector<int64_t> rows(nh + 1);
+        cudaMemcpyAsync(rows.data(), ctx->dprp + begin[kDHub], sizeof(int64_t) * (nh + 1), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s))) {
+            cudaFreeAsync(base, s);
+            return cuda_error(ctx, e, "read hub rows");
+        }
+        std::vector<HubChunk> chunks;
+        std::vector<int64_t> toff(nh);
+        std::vector<uint32_t> tmask(nh);
+        int64_t words = 0;
+        const int64_t csz = std::max(256, ctx->opt.hub_chunk);
+        for (int64_t h = 0; h < nh; ++h) {
+            const int64_t d = rows[h + 1] - rows[h];
+            uint64_t sz = 64;
+            while (sz < static_cast<uint64_t>(2 * d)) sz <<= 1;
+            toff[h] = words;
+            tmask[h] = static_cast<uint32_t>(sz - 1);
+            words += static_cast<int64_t>(sz);
+            for (int64_t b = rows[h]; b < rows[h + 1]; b += csz)
+                chunks.push_back(HubChunk{static_cast<int32_t>(h), -1, b, std::min(rows[h + 1], b + csz)});
+        }
+        ctx->n_dhub = nh;
+        ctx->n_dchunks = static_cast<int64_t>(chunks.size());
+        ctx->dtab_words = words;
+        if (!chunks.empty() &&
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dchunks), sizeof(HubChunk) * chunks.size(), s))) {
+            cudaFreeAsync(base, s);
+            return cuda_error(ctx, e, "alloc hub chunks");
+        }
+        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dtoff), sizeof(int64_t) * nh, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dtmask), sizeof(uint32_t) * nh, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dtab), sizeof(unsigned long long) * words, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dacc), sizeof(HubAcc) * nh, s))) {
+            cudaFreeAsync(base, s);
+            return cuda_error(ctx, e, "alloc hub sets");
+        }
+        if (!chunks.empty())
+            cudaMemcpyAsync(ctx->dchunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(ctx->dtoff, toff.data(), sizeof(int64_t) * nh, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(ctx->dtmask, tmask.data(), sizeof(uint32_t) * nh, cudaMemcpyHostToDevice, s);
+        // the host vectors die here: finish the uploads first
+        if ((e = cudaStreamSynchronize(s))) {
+            cudaFreeAsync(base, s);
+            return cuda_error(ctx, e, "upload hub layout");
+        }
+    }
+    cudaFreeAsync(base, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "build dense layout");
+    if ((e = cudaGetLastError())) return cuda_error(ctx, e, "build dense layout");
+    ctx->dense_ready = true;
+    ctx->stats.device_bytes = ctx->device_bytes;
+    return BISIM_OK;
+}
+
+void dense_mark_dead(bisim_ctx* ctx, cudaStream_t s) {
+    const int64_t n_live = ctx->dbegin[kDClasses];
+    if (n_live >= ctx->n) return;
+    BISIM_SITE(site, "dense_dead");
+    Launch L(site, s, ctx->n - n_live, 0, 12.0 * (ctx->n - n_live));
+    k_dense_dead<<<grid_for(ctx->n - n_live, 256), 256, 0, s>>>(ctx->dvert, n_live, ctx->n, ctx->P[0], ctx->P[1]);
+}
+
+bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
+    const int32_t n = ctx->n;
+    int32_t* Pout = ctx->P[ctx->cur ^ 1];
+    cudaError_t e;
+    const DenseView D{ctx->dvert, ctx->dvpos, ctx->dprp, ctx->dpe, ctx->P[ctx->cur], ctx->dcnt, ctx->dhash, ctx->dslot};
+    const HubSets H = hub_sets(ctx);
+    TableRef t = next_epoch(ctx, s);
+    unsigned* err = &ctx->dstate->error;
+    cudaMemsetAsync(ctx->dstate, 0, sizeof(DevState), s);
+    if (ctx->n_dhub > 0) {
+        cudaMemsetAsync(ctx->dtab, 0, sizeof(unsigned long long) * ctx->dtab_words, s);
+        cudaMemsetAsync(ctx->dacc, 0, sizeof(HubAcc) * ctx->n_dhub, s);
+    }
+    const int64_t* db = ctx->dbegin;
+    const int64_t n_live = db[kDClasses];
+
+    BISIM_SITE(site_g, "dense_group_sig");
+    BISIM_SITE(site_w, "dense_warp_sig");
+    static const int site_mid[5] = {prof_site("dense_mid_512"), prof_site("dense_mid_1024"),
+                                    prof_site("dense_mid_2048"), prof_site("dense_mid_4096"),
+                                    prof_site("dense_mid_8192")};
+    BISIM_SITE(site_hi, "dense_hub_insert");
+    BISIM_SITE(site_hf, "dense_hub_finalize");
+    BISIM_SITE(site_in, "dense_insert");
+    BISIM_SITE(site_v, "dense_verify");
+    BISIM_SITE(site_cw, "dense_compare_warp");
+    BISIM_SITE(site_cc, "dense_compare_cta");
+    // 1. signatures (hash and set size per position)
+    if (db[kDWarp0] > db[0]) {
+        const GroupPlan gp = group_plan(ctx);
+        const int64_t verts = db[kDWarp0] - db[0];
+        const int64_t edges = class_edges(ctx, 0, kDWarp0);
+        Launch L(site_g, s, verts, edges, kSigVertexBytes * verts + kEdgeBytes * edges);
+        k_dense_group_sig<<<static_cast<unsigned>(gp.cta_begin[kDGroupClasses]), kThreads, 0, s>>>(gp, D);
+    }
+    if (db[kDMid0] > db[kDWarp0]) {
+        const WarpPlan wp = warp_plan(ctx);
+        const int64_t verts = db[kDMid0] - db[kDWarp0];
+        const int64_t edges = class_edges(ctx, kDWarp0, kDMid0);
+        Launch L(site_w, s, verts, edges, kSigVertexBytes * verts + kEdgeBytes * edges);
+        k_dense_warp_sig<<<static_cast<unsigned>(wp.cta_begin[3]), kThreads, 0, s>>>(wp, D);
+    }
+    launch_mid<512, 256>(ctx, kDMid0 + 0, D, s, site_mid[0]);
+    launch_mid<1024, 256>(ctx, kDMid0 + 1, D, s, site_mid[1]);
+    launch_mid<2048, 512>(ctx, kDMid0 + 2, D, s, site_mid[2]);
+    launch_mid<4096, 512>(ctx, kDMid0 + 3, D, s, site_mid[3]);
+    launch_mid<8192, 512>(ctx, kDMid0 + 4, D, s, site_mid[4]);
+    if (ctx->n_dhub > 0) {
+        if (ctx->n_dchunks > 0) {
+            const int64_t edges = class_edges(ctx, kDHub, kDHub + 1);
+            Launch L(site_hi, s, 0, edges, kEdgeBytes * edges);
+            k_dense_hub_insert<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, 0, s>>>(ctx->dchunks, D, H, err);
+        }
+        Launch L(site_hf, s, ctx->n_dhub, 0, kSigVertexBytes * ctx->n_dhub);
+        k_dense_hub_finalize<<<grid_for(ctx->n_dhub, 128), 128, 0, s>>>(D, H);
+    }
+    static bool attr = false;
+    if (!attr) {
+        allow_smem(k_dense_compare_cta, kCompareSmem);
+        attr = true;
+    }
+    // 2. renumbering: table insert, verification, set comparisons; then the
+    // collision levels, which only the positions that differ from their
+    // representative's signature enter
+    int which = 0;
+    const int32_t* list = nullptr;
+    int64_t count = n_live;
+    for (uint32_t level = 0;; ++level) {
+        if (level > static_cast<uint32_t>(kMaxLevels))
+            return set_error(ctx, BISIM_ETIMEOUT, "hash collision resolution did not converge");
+        if (level > 0) {
+            t = next_epoch(ctx, s);
+            cudaMemsetAsync(&ctx->dstate->unresolved, 0, sizeof(unsigned), s);
+            cudaMemsetAsync(&ctx->dstate->deferred, 0, sizeof(unsigned), s);
+            cudaMemsetAsync(&ctx->dstate->pairs, 0, sizeof(unsigned), s);
+        }
+        int32_t* next = ctx->ulist[which];
+        const VerifyOut O{Pout, ctx->dpairs, ctx->dsmall, next, ctx->dstate};
+        if (count > 0) {
+            {
+                Launch L(site_in, s, count, 0, kInsertVertexBytes * count);
+                k_dense_insert<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, level, t, err);
+            }
+            {
+                Launch L(site_v, s, count, 0, kVerifyVertexBytes * count);
+                k_dense_verify<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, ctx->table, O, n);
+            }
+            {
+                Launch L(site_cw, s, 0, 0, 0.0);
+                k_dense_compare_warp<<<kCompareGrid, kThreads, 0, s>>>(ctx->dsmall, D, Pout, next, ctx->dstate);
+            }
+            {
+                Launch L(site_cc, s, 0, 0, 0.0);
+                k_dense_compare_cta<<<kCompareGrid, kThreads, kCompareSmem, s>>>(ctx->dpairs, D, H, Pout, next,
+                                                                                ctx->dstate);
+            }
+        }
+        cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, level ? "resolve hash collisions" : "dense round");
+        if (ctx->hstate->error != 0 || ctx->hstate->unresolved == 0) break;
+        list = next;
+        count = ctx->hstate->unresolved;
+        which ^= 1;
+        ctx->stats.collision_levels += 1;
+    }
+    if (ctx->hstate->error & kErrTableFull) return set_error(ctx, BISIM_ETIMEOUT, "signature table probe limit reached");
+    if (ctx->hstate->error & kErrHubFull) return set_error(ctx, BISIM_ETIMEOUT, "hub set probe limit reached");
+    if (ctx->hstate->error) return set_error(ctx, BISIM_EINVAL, "device reported invalid input");
+    *out_blocks = static_cast<int64_t>(ctx->hstate->blocks);
+    ctx->cur ^= 1;
+    return BISIM_OK;
+}
+
+}  // namespace bisim

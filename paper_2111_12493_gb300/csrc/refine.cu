@@ -206,38 +206,6 @@ __global__ void __launch_bounds__(128) k_sig_small(const int32_t* __restrict__ l
     slot[v] = table_insert(t, h, v, err);
 }
 
-// Inserts pair value mv into a shared-memory open-addressing set (0 = empty;
-// the value 0 itself is tracked by *zero). Returns true for the first inserter.
-__device__ __forceinline__ bool smem_set_insert(unsigned long long* tab, uint32_t mask, unsigned* zero,
-                                                unsigned long long mv) {
-    if (mv == 0ull) return atomicExch(zero, 1u) == 0u;
-    uint32_t pos = static_cast<uint32_t>(mv) & mask;
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        const unsigned long long cur = tab[pos];
-        if (cur == mv) return false;
-        if (cur == 0ull) {
-            const unsigned long long prev = atomicCAS(&tab[pos], 0ull, mv);
-            if (prev == 0ull) return true;
-            if (prev == mv) return false;
-        }
-        pos = (pos + 1) & mask;
-    }
-    return false;   // unreachable: the set has twice as many slots as keys
-}
-
-__device__ __forceinline__ bool smem_set_contains(const unsigned long long* tab, uint32_t mask, unsigned zero,
-                                                  unsigned long long mv) {
-    if (mv == 0ull) return zero != 0u;
-    uint32_t pos = static_cast<uint32_t>(mv) & mask;
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        const unsigned long long cur = tab[pos];
-        if (cur == mv) return true;
-        if (cur == 0ull) return false;
-        pos = (pos + 1) & mask;
-    }
-    return false;
-}
-
 // One warp per vertex of out-degree <= N (N <= 256), eight vertices per CTA:
 // duplicates are removed with a hash set in the warp's slice of shared memory
 // (2N slots), so the cost is linear in the degree and needs no CTA barrier.
@@ -560,6 +528,8 @@ __global__ void k_local_ids(const int32_t* __restrict__ P, const int32_t* __rest
 
 // ----------------------------------------------------------------------------- host side
 
+}  // namespace
+
 TableRef next_epoch(bisim_ctx* ctx, cudaStream_t s) {
     ctx->epoch32 += 1;
     const uint32_t e = ((ctx->epoch32 - 1) % kEpochCycle) + 1u;
@@ -573,6 +543,8 @@ TableRef next_epoch(bisim_ctx* ctx, cudaStream_t s) {
     t.hmask = hb >= 64 ? ~0ull : ((1ull << hb) - 1ull);
     return t;
 }
+
+namespace {
 
 template <class Mode>
 void launch_deferred(bisim_ctx* ctx, const Mode& M, int32_t* Pout, int32_t* next, cudaStream_t s) {
