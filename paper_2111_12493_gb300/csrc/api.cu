@@ -117,7 +117,6 @@ bisim_status copy_vertex_arrays(bisim_ctx* ctx, const int32_t* vlabel, const uin
 
 bisim_status finish_init(bisim_ctx* ctx, cudaStream_t s) {
     bisim_status st;
-    if ((st = build_buckets(ctx, s)) != BISIM_OK) return st;
     if ((st = alloc_refine_state(ctx, s)) != BISIM_OK) return st;
     if (ctx->opt.mem_budget_bytes > 0 && ctx->device_bytes > ctx->opt.mem_budget_bytes)
         return set_error(ctx, BISIM_ENOMEM, "context exceeds the memory budget");
@@ -196,7 +195,7 @@ bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s) {
     if (!ctx->buckets_dirty) return BISIM_OK;
     cudaError_t e;
     bisim_status st;
-    if (ctx->m > ctx->skey_cap) {
+    if (ctx->skey != nullptr && ctx->m > ctx->skey_cap) {
         ctx_free(ctx, ctx->skey, sizeof(unsigned long long) * ctx->skey_cap, s);
         ctx->skey = nullptr;
         const int64_t cap = ctx->m + ctx->m / 4 + 1024;
@@ -204,7 +203,7 @@ bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s) {
             return cuda_error(ctx, e, "grow signature lists");
         ctx->skey_cap = cap;
     }
-    if ((st = build_buckets(ctx, s)) != BISIM_OK) return st;
+    ctx->buckets_ready = false;   // rebuilt by the list-mode path when it next needs them
     if ((st = compute_p0(ctx, s)) != BISIM_OK) return st;
     ctx->buckets_dirty = false;
     ctx->stats.device_bytes = ctx->device_bytes;

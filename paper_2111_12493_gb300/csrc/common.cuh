@@ -117,14 +117,20 @@ struct DevState {
     unsigned int pairs;             // dense rounds: small pairs left to a warp comparison
 };
 
-// Insert `h` (already masked) for vertex v; returns the slot index or ~0u on overflow.
-__device__ __forceinline__ uint32_t table_insert(const TableRef& t, uint64_t h, int32_t v,
-                                                 unsigned* err) {
+__device__ __forceinline__ unsigned long long table_read(const TableRef& t, uint64_t pos) {
+    return *reinterpret_cast<volatile unsigned long long*>(&t.slots[pos].w);
+}
+
+// Insert `h` (already masked) for vertex v, given the first probe slot's value
+// `cur` as read by the caller (so that callers can issue several first reads
+// at once); returns the slot index or ~0u on overflow.
+__device__ __forceinline__ uint32_t table_insert_from(const TableRef& t, uint64_t h, int32_t v,
+                                                      unsigned long long cur, unsigned* err) {
     const unsigned long long tag = (h & ~0xfffffffffull) | t.epoch;
     const unsigned long long want = tag | static_cast<uint32_t>(v);
     uint64_t pos = h & t.mask;
     for (uint64_t probe = 0; probe <= t.mask; ++probe) {
-        unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&t.slots[pos].w);
+        if (probe > 0) cur = table_read(t, pos);
         for (;;) {
             if ((cur & kSlotEpochMask) != t.epoch) {            // free in this epoch: claim it
                 const unsigned long long prev = atomicCAS(&t.slots[pos].w, cur, want);
@@ -148,6 +154,11 @@ __device__ __forceinline__ uint32_t table_insert(const TableRef& t, uint64_t h, 
     }
     atomicOr(err, kErrTableFull);
     return ~0u;
+}
+
+// Insert `h` (already masked) for vertex v; returns the slot index or ~0u on overflow.
+__device__ __forceinline__ uint32_t table_insert(const TableRef& t, uint64_t h, int32_t v, unsigned* err) {
+    return table_insert_from(t, h, v, table_read(t, h & t.mask), err);
 }
 
 __device__ __forceinline__ int32_t table_rep(const Slot* slots, uint32_t pos) {
@@ -307,7 +318,8 @@ struct bisim_ctx {
     int32_t* esrc = nullptr;       // source vertex of every CSR edge (kept once updates start)
     int64_t esrc_cap = 0;
     int64_t skey_cap = 0;          // capacity of skey in values
-    bool buckets_dirty = false;    // degree buckets no longer match the CSR
+    bool buckets_dirty = false;    // the label partition and buckets no longer match the CSR
+    bool buckets_ready = false;    // degree buckets of the list-mode path are built
     int32_t cur_k = 0;             // rounds of the current partition
 
     // incremental maintenance (apply_updates): per level j = 0..inc_k, block ids
@@ -361,6 +373,9 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
 bisim_status build_from_csr(bisim_ctx* ctx, const int64_t* row_ptr, const int32_t* col,
                             const int32_t* elab, cudaStream_t s);
 bisim_status build_buckets(bisim_ctx* ctx, cudaStream_t s);
+// Builds the degree buckets of the list-mode (incremental) path on first use
+// after the graph changed.
+bisim_status ensure_buckets(bisim_ctx* ctx, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- refinement (refine.cu)
 

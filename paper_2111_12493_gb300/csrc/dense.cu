@@ -130,17 +130,41 @@ __global__ void k_dense_degrees(const int32_t* __restrict__ vert, int64_t n_live
     }
 }
 
-// Rows of out-degree <= 32: one thread per position.
-__global__ void k_dense_pack_rows(const int32_t* __restrict__ vert, int64_t count, const int64_t* __restrict__ prp,
-                                  const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                  const int32_t* __restrict__ elab, unsigned long long* __restrict__ pe) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const int32_t v = vert[i];
-    const int64_t b = rp[v];
-    const int64_t d = rp[v + 1] - b;
-    const int64_t o = prp[i];
-    for (int64_t j = 0; j < d; ++j) pe[o + j] = pack_edge(elab[b + j], col[b + j]);
+// Rows of out-degree <= 32: one warp per 32 consecutive positions. The warp's
+// output range is contiguous, so it is written word by word across the lanes;
+// each word finds its source row by a binary search over the warp's 33 row
+// offsets in shared memory.
+__global__ void __launch_bounds__(256) k_dense_pack_rows(const int32_t* __restrict__ vert, int64_t count,
+                                                         const int64_t* __restrict__ prp,
+                                                         const int64_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ col,
+                                                         const int32_t* __restrict__ elab,
+                                                         unsigned long long* __restrict__ pe) {
+    __shared__ int64_t off_all[8][33];
+    __shared__ int64_t src_all[8][32];
+    const int warp = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    const int64_t p0 = (static_cast<int64_t>(blockIdx.x) * 8 + warp) * 32;
+    if (p0 >= count) return;                             // whole warp leaves together
+    int64_t* off = off_all[warp];
+    int64_t* src = src_all[warp];
+    const int64_t pend = min(count, p0 + 32);
+    const int64_t p = p0 + lane;
+    const bool act = p < count;
+    off[lane] = prp[act ? p : pend];                     // rows past the end start at the end
+    if (lane == 0) off[32] = prp[pend];
+    src[lane] = act ? rp[vert[p]] : 0;
+    __syncwarp();
+    const int64_t o1 = off[32];
+    for (int64_t o = off[0] + lane; o < o1; o += 32) {
+        int lo = 0, hi = 31;                             // the last row starting at or before o
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= o) lo = mid; else hi = mid - 1;
+        }
+        const int64_t e = src[lo] + (o - off[lo]);
+        pe[o] = pack_edge(elab[e], col[e]);
+    }
 }
 
 // Longer rows: one CTA per position.
@@ -153,6 +177,17 @@ __global__ void k_dense_pack_big(const int32_t* __restrict__ vert, int64_t first
     const int64_t d = rp[v + 1] - b;
     const int64_t o = prp[i];
     for (int64_t j = threadIdx.x; j < d; j += blockDim.x) pe[o + j] = pack_edge(elab[b + j], col[b + j]);
+}
+
+// Hub rows: one CTA per chunk of a row.
+__global__ void k_dense_pack_chunks(const HubChunk* __restrict__ chunks, const int32_t* __restrict__ vert,
+                                    int64_t first, const int64_t* __restrict__ prp, const int64_t* __restrict__ rp,
+                                    const int32_t* __restrict__ col, const int32_t* __restrict__ elab,
+                                    unsigned long long* __restrict__ pe) {
+    const HubChunk c = chunks[blockIdx.x];
+    const int64_t pos = first + c.hub;
+    const int64_t src = rp[vert[pos]] - prp[pos];        // source index = packed index + src
+    for (int64_t o = c.begin + threadIdx.x; o < c.end; o += blockDim.x) pe[o] = pack_edge(elab[src + o], col[src + o]);
 }
 
 __global__ void k_dense_dead(const int32_t* __restrict__ vert, int64_t first, int64_t n, int32_t* __restrict__ Pa,
@@ -194,6 +229,34 @@ struct WarpPlan {
 __device__ __forceinline__ void finish_sig(const DenseView& D, int64_t pos, int32_t own, uint32_t c, uint64_t sum) {
     D.cnt[pos] = static_cast<int32_t>(c);
     D.hash[pos] = sig_hash(own, c, sum);
+}
+
+// Degree <= D: one thread per vertex. The row's pair values sit in registers;
+// a value counts when no earlier value of the row equals it.
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_dense_thread_sig(int64_t first, int64_t count, const DenseView V) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t pos = first + i;
+    const int32_t own = V.P[V.vert[pos]];
+    const int64_t e0 = V.prp[pos];
+    const int d = static_cast<int>(V.prp[pos + 1] - e0);
+    uint64_t v[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) v[j] = j < d ? packed_pair_value(__ldcs(V.pe + e0 + j), V.P) : 0ull;
+    uint64_t sum = 0;
+    uint32_t u = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        bool fresh = j < d;
+#pragma unroll
+        for (int q = 0; q < j; ++q) fresh = fresh && v[q] != v[j];
+        if (fresh) {
+            sum += v[j];
+            ++u;
+        }
+    }
+    finish_sig(V, pos, own, u, sum);
 }
 
 // Degree <= 32: one lane per edge in groups of G lanes per vertex.
@@ -326,8 +389,29 @@ struct HubSets {
     HubAcc* acc;
 };
 
+// Inserts mv (not 0) into a hub set, starting from the first probe slot's
+// value `cur`; true for the first inserter.
+__device__ __forceinline__ bool hub_set_insert_from(unsigned long long* tab, uint32_t mask, uint64_t mv,
+                                                    unsigned long long cur, unsigned* err) {
+    uint32_t p = static_cast<uint32_t>(mv) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        if (probe > 0) cur = tab[p];
+        if (cur == mv) return false;
+        if (cur == 0ull) {
+            const unsigned long long prev = atomicCAS(&tab[p], 0ull, static_cast<unsigned long long>(mv));
+            if (prev == 0ull) return true;
+            if (prev == mv) return false;
+        }
+        p = (p + 1) & mask;
+    }
+    atomicOr(err, kErrHubFull);
+    return false;
+}
+
 // Hubs, phase 1: every CTA inserts one chunk of a hub's row into the hub's set;
 // first inserters add their value to the hub's count and order-independent sum.
+// Each thread keeps kHubUnroll edges in flight (loads, gathers and first probes).
+constexpr int kHubUnroll = 4;
 __global__ void __launch_bounds__(kThreads) k_dense_hub_insert(const HubChunk* __restrict__ chunks, const DenseView D,
                                                                const HubSets H, unsigned* err) {
     __shared__ unsigned long long wsum[kThreads / 32];
@@ -337,32 +421,28 @@ __global__ void __launch_bounds__(kThreads) k_dense_hub_insert(const HubChunk* _
     const uint32_t mask = H.tmask[c.hub];
     uint64_t lsum = 0;
     unsigned lcnt = 0;
-    for (int64_t e = c.begin + threadIdx.x; e < c.end; e += kThreads) {
-        const uint64_t mv = packed_pair_value(__ldcs(D.pe + e), D.P);
-        bool fresh = false;
-        if (mv == 0ull) {
-            fresh = atomicOr(&H.acc[c.hub].zero, 1u) == 0u;
-        } else {
-            uint32_t p = static_cast<uint32_t>(mv) & mask;
-            uint32_t probe = 0;
-            for (; probe <= mask; ++probe) {
-                const unsigned long long cur = tab[p];
-                if (cur == mv) break;
-                if (cur == 0ull) {
-                    const unsigned long long prev = atomicCAS(&tab[p], 0ull, static_cast<unsigned long long>(mv));
-                    if (prev == 0ull) {
-                        fresh = true;
-                        break;
-                    }
-                    if (prev == mv) break;
-                }
-                p = (p + 1) & mask;
-            }
-            if (probe > mask) atomicOr(err, kErrHubFull);
+    for (int64_t e0 = c.begin + threadIdx.x; e0 < c.end; e0 += kThreads * kHubUnroll) {
+        uint64_t mv[kHubUnroll];
+        bool act[kHubUnroll];
+#pragma unroll
+        for (int k = 0; k < kHubUnroll; ++k) {
+            const int64_t e = e0 + static_cast<int64_t>(k) * kThreads;
+            act[k] = e < c.end;
+            mv[k] = act[k] ? packed_pair_value(__ldcs(D.pe + e), D.P) : 0ull;
         }
-        if (fresh) {
-            lsum += mv;
-            ++lcnt;
+        unsigned long long cur[kHubUnroll];
+#pragma unroll
+        for (int k = 0; k < kHubUnroll; ++k)
+            cur[k] = (act[k] && mv[k] != 0ull) ? tab[static_cast<uint32_t>(mv[k]) & mask] : 0ull;
+#pragma unroll
+        for (int k = 0; k < kHubUnroll; ++k) {
+            if (!act[k]) continue;
+            const bool fresh = mv[k] == 0ull ? atomicOr(&H.acc[c.hub].zero, 1u) == 0u
+                                             : hub_set_insert_from(tab, mask, mv[k], cur[k], err);
+            if (fresh) {
+                lsum += mv[k];
+                ++lcnt;
+            }
         }
     }
 #pragma unroll
@@ -413,15 +493,58 @@ __device__ __forceinline__ bool hub_set_contains(const HubSets& H, int64_t h, ui
 }
 
 // Table insert of every listed position (level 0: all live positions, list ==
-// null) with the level's salted hash. One thread per position.
+// null) with the level's salted hash. Each thread handles kPosUnroll positions
+// a CTA width apart, with their loads and first probes in flight together.
+constexpr int kPosUnroll = 4;
 __global__ void __launch_bounds__(kThreads) k_dense_insert(const int32_t* __restrict__ list, int64_t count,
                                                            const DenseView D, uint32_t level, const TableRef t,
                                                            unsigned* err) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const int64_t pos = list ? list[i] : i;
-    const int32_t v = D.vert[pos];
-    D.slot[pos] = table_insert(t, level_hash(D.hash[pos], level, t.hmask), v, err);
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * (kThreads * kPosUnroll) + threadIdx.x;
+    int64_t pos[kPosUnroll];
+    int32_t v[kPosUnroll];
+    uint64_t h[kPosUnroll];
+    unsigned long long cur[kPosUnroll];
+#pragma unroll
+    for (int k = 0; k < kPosUnroll; ++k) {
+        const int64_t i = base + static_cast<int64_t>(k) * kThreads;
+        pos[k] = i < count ? (list ? list[i] : i) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kPosUnroll; ++k) {
+        if (pos[k] < 0) continue;
+        v[k] = D.vert[pos[k]];
+        h[k] = level_hash(D.hash[pos[k]], level, t.hmask);
+    }
+#pragma unroll
+    for (int k = 0; k < kPosUnroll; ++k)
+        if (pos[k] >= 0) cur[k] = table_read(t, h[k] & t.mask);
+    // the common cases need one CAS on the first probe slot: issue them together
+    bool done[kPosUnroll];
+#pragma unroll
+    for (int k = 0; k < kPosUnroll; ++k) {
+        done[k] = false;
+        if (pos[k] < 0) continue;
+        const unsigned long long tag = (h[k] & ~0xfffffffffull) | t.epoch;
+        const unsigned long long want = tag | static_cast<uint32_t>(v[k]);
+        const uint64_t sp = h[k] & t.mask;
+        const bool free_slot = (cur[k] & kSlotEpochMask) != t.epoch;
+        const bool same = !free_slot && (cur[k] & kSlotKeyMask) == tag;
+        if (same && static_cast<uint32_t>(v[k]) >= static_cast<uint32_t>(cur[k])) {
+            D.slot[pos[k]] = static_cast<uint32_t>(sp);      // a smaller vertex is already recorded
+            done[k] = true;
+        } else if (free_slot || same) {
+            const unsigned long long prev = atomicCAS(&t.slots[sp].w, cur[k], want);
+            if (prev == cur[k]) {
+                D.slot[pos[k]] = static_cast<uint32_t>(sp);
+                done[k] = true;
+            } else {
+                cur[k] = prev;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kPosUnroll; ++k)
+        if (pos[k] >= 0 && !done[k]) D.slot[pos[k]] = table_insert_from(t, h[k], v[k], cur[k], err);
 }
 
 struct VerifyOut {
@@ -436,54 +559,73 @@ struct VerifyOut {
 // smallest vertex). r itself: a block id. Different own block or set size: the
 // position moves to the next level. Otherwise the sets are compared: here when
 // both rows have at most two edges, else in a warp (rows <= 32) or a CTA.
+// kPosUnroll positions per thread, their slot reads in flight together.
 __global__ void __launch_bounds__(kThreads) k_dense_verify(const int32_t* __restrict__ list, int64_t count,
                                                            const DenseView D, const Slot* __restrict__ slots,
                                                            const VerifyOut O, int32_t n_total) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    bool own = false, push = false, small = false, big = false;
-    int64_t pos = -1, rpos = -1;
-    if (i < count) {
-        pos = list ? list[i] : i;
-        const int32_t v = D.vert[pos];
-        const uint32_t sv = D.slot[pos];
-        const int32_t r = sv == ~0u ? -1 : table_rep(slots, sv);
-        if (r < 0 || r >= n_total) {                     // failed insert, reported through st->error
-            atomicOr(&O.st->error, kErrTableFull);
-            O.Pout[v] = -1;
-        } else if (r == v) {
-            O.Pout[v] = v;
-            own = true;
-        } else {
-            rpos = D.vpos[r];
-            if (D.P[v] != D.P[r] || D.cnt[pos] != D.cnt[rpos]) {
-                push = true;
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * (kThreads * kPosUnroll) + threadIdx.x;
+    int64_t pos[kPosUnroll];
+    int32_t v[kPosUnroll], r[kPosUnroll];
+    uint32_t sv[kPosUnroll];
+#pragma unroll
+    for (int k = 0; k < kPosUnroll; ++k) {
+        const int64_t i = base + static_cast<int64_t>(k) * kThreads;
+        pos[k] = i < count ? (list ? list[i] : i) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kPosUnroll; ++k) {
+        if (pos[k] < 0) continue;
+        v[k] = D.vert[pos[k]];
+        sv[k] = D.slot[pos[k]];
+    }
+#pragma unroll
+    for (int k = 0; k < kPosUnroll; ++k)
+        if (pos[k] >= 0) r[k] = sv[k] == ~0u ? -1 : table_rep(slots, sv[k]);
+#pragma unroll
+    for (int k = 0; k < kPosUnroll; ++k) {
+        bool own = false, push = false, small = false, big = false;
+        int64_t rpos = -1;
+        if (pos[k] >= 0) {
+            const int32_t vk = v[k], rk = r[k];
+            if (rk < 0 || rk >= n_total) {               // failed insert, reported through st->error
+                atomicOr(&O.st->error, kErrTableFull);
+                O.Pout[vk] = -1;
+            } else if (rk == vk) {
+                O.Pout[vk] = vk;
+                own = true;
             } else {
-                const int64_t ev = D.prp[pos], dv = D.prp[pos + 1] - ev;
-                const int64_t er = D.prp[rpos], dr = D.prp[rpos + 1] - er;
-                if (dv <= 2 && dr <= 2) {
-                    // S_v inside S_r with equal sizes means equal sets
-                    uint64_t b0 = 0, b1 = 0;
-                    if (dr > 0) b0 = packed_pair_value(D.pe[er], D.P);
-                    if (dr > 1) b1 = packed_pair_value(D.pe[er + 1], D.P);
-                    bool ok = true;
-                    for (int64_t j = 0; j < dv; ++j) {
-                        const uint64_t a = packed_pair_value(D.pe[ev + j], D.P);
-                        ok = ok && ((dr > 0 && a == b0) || (dr > 1 && a == b1));
-                    }
-                    if (ok) O.Pout[v] = r;
-                    else push = true;
-                } else if (dv <= 32 && dr <= 32) {
-                    small = true;
+                rpos = D.vpos[rk];
+                if (D.P[vk] != D.P[rk] || D.cnt[pos[k]] != D.cnt[rpos]) {
+                    push = true;
                 } else {
-                    big = true;
+                    const int64_t ev = D.prp[pos[k]], dv = D.prp[pos[k] + 1] - ev;
+                    const int64_t er = D.prp[rpos], dr = D.prp[rpos + 1] - er;
+                    if (dv <= 2 && dr <= 2) {
+                        // S_v inside S_r with equal sizes means equal sets
+                        uint64_t b0 = 0, b1 = 0;
+                        if (dr > 0) b0 = packed_pair_value(D.pe[er], D.P);
+                        if (dr > 1) b1 = packed_pair_value(D.pe[er + 1], D.P);
+                        bool ok = true;
+                        for (int64_t j = 0; j < dv; ++j) {
+                            const uint64_t a = packed_pair_value(D.pe[ev + j], D.P);
+                            ok = ok && ((dr > 0 && a == b0) || (dr > 1 && a == b1));
+                        }
+                        if (ok) O.Pout[vk] = rk;
+                        else push = true;
+                    } else if (dv <= 32 && dr <= 32) {
+                        small = true;
+                    } else {
+                        big = true;
+                    }
                 }
             }
         }
+        const int32_t p32 = static_cast<int32_t>(pos[k]);
+        warp_count(own, &O.st->blocks);
+        warp_push(push, p32, O.next, &O.st->unresolved);
+        warp_push(small, make_int2(p32, static_cast<int32_t>(rpos)), O.small, &O.st->pairs);
+        warp_push(big, make_int2(p32, static_cast<int32_t>(rpos)), O.pairs, &O.st->deferred);
     }
-    warp_count(own, &O.st->blocks);
-    warp_push(push, static_cast<int32_t>(pos), O.next, &O.st->unresolved);
-    warp_push(small, make_int2(static_cast<int32_t>(pos), static_cast<int32_t>(rpos)), O.small, &O.st->pairs);
-    warp_push(big, make_int2(static_cast<int32_t>(pos), static_cast<int32_t>(rpos)), O.pairs, &O.st->deferred);
 }
 
 constexpr int kCompareGrid = 304;                      // persistent grids: two CTAs per SM
@@ -569,14 +711,15 @@ __global__ void __launch_bounds__(kThreads) k_dense_compare_cta(const int2* __re
 
 constexpr int kGroupShift[kDGroupClasses] = {0, 0, 1, 2, 3, 4, 5};
 
-GroupPlan group_plan(const bisim_ctx* ctx) {
+// Lane groups for the classes from `first` on (the ones before run one thread per vertex).
+GroupPlan group_plan(const bisim_ctx* ctx, int first) {
     GroupPlan p;
     std::memset(&p, 0, sizeof(p));
     int64_t cta = 0;
     for (int c = 0; c < kDGroupClasses; ++c) {
         p.cta_begin[c] = cta;
-        p.pos_begin[c] = ctx->dbegin[c];
-        p.pos_end[c] = ctx->dbegin[c + 1];
+        p.pos_begin[c] = c < first ? 0 : ctx->dbegin[c];
+        p.pos_end[c] = c < first ? 0 : ctx->dbegin[c + 1];
         p.gshift[c] = kGroupShift[c];
         cta += cdiv(p.pos_end[c] - p.pos_begin[c], kThreads >> p.gshift[c]);
     }
@@ -718,6 +861,9 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
     for (int c = kDClasses - 1; c >= 0; --c) begin[c] = std::min(begin[c], begin[c + 1]);
     for (int c = 0; c <= kDClasses; ++c) ctx->dbegin[c] = begin[c];
     const int64_t n_live = begin[kDClasses];
+    ctx->stats.n_small = begin[kDWarp0] - begin[0];
+    ctx->stats.n_mid = begin[kDHub] - begin[kDWarp0];
+    ctx->stats.n_hub = begin[kDHub + 1] - begin[kDHub];
     {
         Launch L(site_c, s, n_live, 0, 28.0 * n_live);
         k_dense_degrees<<<grid_for(n_live + 1, 256), 256, 0, s>>>(ctx->dvert, n_live, ctx->row_ptr, deg);
@@ -727,13 +873,14 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
         cudaMemcpyAsync(&ctx->dedge_begin[c], ctx->dprp + begin[c], sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     {
         const int64_t small = begin[kDWarp0];
-        const int64_t big = n_live - small;
-        Launch L(site_p, s, n_live, m, 16.0 * m + 20.0 * n_live);
+        const int64_t mid = begin[kDHub] - small;
+        const int64_t edges = ctx->dedge_begin[kDHub];
+        Launch L(site_p, s, begin[kDHub], edges, 16.0 * edges + 20.0 * begin[kDHub]);
         if (small > 0)
-            k_dense_pack_rows<<<grid_for(small, 256), 256, 0, s>>>(ctx->dvert, small, ctx->dprp, ctx->row_ptr, ctx->col,
-                                                                  ctx->elab, ctx->dpe);
-        if (big > 0)
-            k_dense_pack_big<<<static_cast<unsigned>(big), 256, 0, s>>>(ctx->dvert, small, ctx->dprp, ctx->row_ptr,
+            k_dense_pack_rows<<<grid_for(small, 256), 256, 0, s>>>(ctx->dvert, small, ctx->dprp, ctx->row_ptr,
+                                                                  ctx->col, ctx->elab, ctx->dpe);
+        if (mid > 0)
+            k_dense_pack_big<<<static_cast<unsigned>(mid), 256, 0, s>>>(ctx->dvert, small, ctx->dprp, ctx->row_ptr,
                                                                        ctx->col, ctx->elab, ctx->dpe);
     }
 
@@ -780,6 +927,13 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
             cudaMemcpyAsync(ctx->dchunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(ctx->dtoff, toff.data(), sizeof(int64_t) * nh, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(ctx->dtmask, tmask.data(), sizeof(uint32_t) * nh, cudaMemcpyHostToDevice, s);
+        if (!chunks.empty()) {
+            // hub rows are copied chunk by chunk, like the rounds read them
+            const int64_t edges = m - ctx->dedge_begin[kDHub];
+            Launch L(site_p, s, nh, edges, 16.0 * edges);
+            k_dense_pack_chunks<<<static_cast<unsigned>(chunks.size()), 256, 0, s>>>(
+                ctx->dchunks, ctx->dvert, begin[kDHub], ctx->dprp, ctx->row_ptr, ctx->col, ctx->elab, ctx->dpe);
+        }
         // the host vectors die here: finish the uploads first
         if ((e = cudaStreamSynchronize(s))) {
             cudaFreeAsync(base, s);
@@ -818,6 +972,9 @@ bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     const int64_t* db = ctx->dbegin;
     const int64_t n_live = db[kDClasses];
 
+    BISIM_SITE(site_t8, "dense_thread_sig_8");
+    BISIM_SITE(site_t16, "dense_thread_sig_16");
+    BISIM_SITE(site_t32, "dense_thread_sig_32");
     BISIM_SITE(site_g, "dense_group_sig");
     BISIM_SITE(site_w, "dense_warp_sig");
     static const int site_mid[5] = {prof_site("dense_mid_512"), prof_site("dense_mid_1024"),
@@ -830,13 +987,17 @@ bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     BISIM_SITE(site_cw, "dense_compare_warp");
     BISIM_SITE(site_cc, "dense_compare_cta");
     // 1. signatures (hash and set size per position)
-    if (db[kDWarp0] > db[0]) {
-        const GroupPlan gp = group_plan(ctx);
-        const int64_t verts = db[kDWarp0] - db[0];
-        const int64_t edges = class_edges(ctx, 0, kDWarp0);
-        Launch L(site_g, s, verts, edges, kSigVertexBytes * verts + kEdgeBytes * edges);
-        k_dense_group_sig<<<static_cast<unsigned>(gp.cta_begin[kDGroupClasses]), kThreads, 0, s>>>(gp, D);
-    }
+    // classes 0..4 (degree <= 8), 5 (<= 16) and 6 (<= 32): one thread per vertex
+    auto thread_sig = [&](int c0, int c1, auto kernel, int site) {
+        const int64_t verts = db[c1] - db[c0];
+        if (verts <= 0) return;
+        const int64_t edges = class_edges(ctx, c0, c1);
+        Launch L(site, s, verts, edges, kSigVertexBytes * verts + kEdgeBytes * edges);
+        kernel<<<grid_for(verts, kThreads), kThreads, 0, s>>>(db[c0], verts, D);
+    };
+    thread_sig(0, 5, k_dense_thread_sig<8>, site_t8);
+    thread_sig(5, 6, k_dense_thread_sig<16>, site_t16);
+    thread_sig(6, 7, k_dense_thread_sig<32>, site_t32);
     if (db[kDMid0] > db[kDWarp0]) {
         const WarpPlan wp = warp_plan(ctx);
         const int64_t verts = db[kDMid0] - db[kDWarp0];
@@ -883,11 +1044,11 @@ bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
         if (count > 0) {
             {
                 Launch L(site_in, s, count, 0, kInsertVertexBytes * count);
-                k_dense_insert<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, level, t, err);
+                k_dense_insert<<<grid_for(count, kThreads * kPosUnroll), kThreads, 0, s>>>(list, count, D, level, t, err);
             }
             {
                 Launch L(site_v, s, count, 0, kVerifyVertexBytes * count);
-                k_dense_verify<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, ctx->table, O, n);
+                k_dense_verify<<<grid_for(count, kThreads * kPosUnroll), kThreads, 0, s>>>(list, count, D, ctx->table, O, n);
             }
             {
                 Launch L(site_cw, s, 0, 0, 0.0);

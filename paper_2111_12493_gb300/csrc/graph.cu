@@ -154,6 +154,15 @@ __global__ void k_take_low(const uint64_t* __restrict__ vals, int64_t n, int32_t
     if (i < n) out[i] = static_cast<int32_t>(vals[i]);
 }
 
+// Row bounds [row_ptr[v], row_ptr[v + 1]) of the listed hubs, interleaved.
+__global__ void k_hub_bounds(const int32_t* __restrict__ hubs, int64_t nh, const int64_t* __restrict__ rp,
+                             int64_t* __restrict__ out) {
+    const int64_t h = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (h >= nh) return;
+    out[2 * h] = rp[hubs[h]];
+    out[2 * h + 1] = rp[hubs[h] + 1];
+}
+
 int bits_for(int64_t n) {
     int b = 0;
     while ((static_cast<int64_t>(1) << b) < n) ++b;
@@ -246,6 +255,13 @@ bisim_status build_from_csr(bisim_ctx* ctx, const int64_t* row_ptr, const int32_
     return BISIM_OK;
 }
 
+bisim_status ensure_buckets(bisim_ctx* ctx, cudaStream_t s) {
+    if (ctx->buckets_ready) return BISIM_OK;
+    bisim_status st = build_buckets(ctx, s);
+    if (st == BISIM_OK) ctx->buckets_ready = true;
+    return st;
+}
+
 bisim_status build_buckets(bisim_ctx* ctx, cudaStream_t s) {
     const int32_t n = ctx->n;
     cudaError_t e;
@@ -308,22 +324,26 @@ bisim_status build_buckets(bisim_ctx* ctx, cudaStream_t s) {
     for (int c = kNumClasses - 1; c >= 0; --c) begin[c] = std::min(begin[c], begin[c + 1]);
     for (int c = 0; c <= kNumClasses; ++c) ctx->class_begin[c] = begin[c];
     for (int c = 0; c < kNumClasses; ++c) ctx->class_edges[c] = static_cast<int64_t>(cedges[c]);
-    ctx->stats.n_small = begin[kSmallClasses] - begin[0];
-    ctx->stats.n_mid = begin[kClassHub] - begin[kSmallClasses];
     ctx->hub_list = ctx->class_list + begin[kClassHub];
     ctx->n_hub = begin[kClassHub + 1] - begin[kClassHub];
-    ctx->stats.n_hub = ctx->n_hub;
 
     // hub chunks and dedup tables (host-side layout; the hub count is small)
     if (ctx->n_hub > 0) {
         std::vector<int32_t> hubs(ctx->n_hub);
+        std::vector<int64_t> bounds(2 * ctx->n_hub);
+        int64_t* dbounds = nullptr;
+        if ((e = cudaMallocAsync(reinterpret_cast<void**>(&dbounds), sizeof(int64_t) * 2 * ctx->n_hub, s)))
+            return cuda_error(ctx, e, "alloc hub bounds");
+        k_hub_bounds<<<grid_for(ctx->n_hub, 256), 256, 0, s>>>(ctx->hub_list, ctx->n_hub, ctx->row_ptr, dbounds);
         cudaMemcpyAsync(hubs.data(), ctx->hub_list, sizeof(int32_t) * ctx->n_hub, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(bounds.data(), dbounds, sizeof(int64_t) * 2 * ctx->n_hub, cudaMemcpyDeviceToHost, s);
+        cudaFreeAsync(dbounds, s);
+        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "read hub rows");
         std::vector<int64_t> rb(ctx->n_hub), re(ctx->n_hub);
         for (int64_t h = 0; h < ctx->n_hub; ++h) {
-            cudaMemcpyAsync(&rb[h], ctx->row_ptr + hubs[h], sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-            cudaMemcpyAsync(&re[h], ctx->row_ptr + hubs[h] + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            rb[h] = bounds[2 * h];
+            re[h] = bounds[2 * h + 1];
         }
-        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "read hub rows");
         std::vector<HubChunk> chunks;
         std::vector<int64_t> toff(ctx->n_hub);
         std::vector<uint32_t> tmask(ctx->n_hub);

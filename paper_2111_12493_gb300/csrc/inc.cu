@@ -738,6 +738,7 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t f, int64_t fl
         } else {
             Buckets B;
             if (all_static) {
+                if ((st = ensure_buckets(ctx, s)) != BISIM_OK) return st;
                 B = ctx_buckets(ctx);
             } else {
                 if ((st = list_buckets(ctx, W.FL, fl, S, LB, s)) != BISIM_OK) return st;

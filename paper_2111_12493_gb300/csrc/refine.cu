@@ -711,8 +711,8 @@ bisim_status alloc_refine_state(bisim_ctx* ctx, cudaStream_t s) {
     for (int i = 0; i < 2; ++i)
         if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ulist[i]), sizeof(int32_t) * nv, s))) return cuda_error(ctx, e, "alloc unresolved list");
     if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dlist), sizeof(int32_t) * nv, s))) return cuda_error(ctx, e, "alloc deferred list");
-    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->skey), sizeof(unsigned long long) * std::max<int64_t>(m, 1), s))) return cuda_error(ctx, e, "alloc signature lists");
-    ctx->skey_cap = std::max<int64_t>(m, 1);
+    // the pair lists (skey) of the list-mode path are allocated when that path first runs
+    (void)m;
     // load factor at most 0.6: 8 bytes per slot keeps the table near L2 size
     uint64_t ns = 1024;
     while (static_cast<double>(ns) * 0.6 < static_cast<double>(n)) ns <<= 1;
