@@ -58,6 +58,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the update-batch latency section")
     ap.add_argument("--serving-batches", type=int, default=40)
+    ap.add_argument("--workload", default="powerlaw", choices=["powerlaw", "chain", "batched"],
+                    help="powerlaw: 10M/100M to the fixpoint (the headline); chain: 1000 paths of 1000 "
+                         "+ 2M random edges to the fixpoint; batched: 4096 graphs in one context, k=3")
     return ap.parse_args()
 
 
@@ -68,6 +71,72 @@ def workload_graph(scale):
     return graphgen.powerlaw_graph(n=n, m=m, exponent=WORKLOAD["exponent"], dmax=min(WORKLOAD["dmax"], m // 10),
                                    n_elabels=WORKLOAD["n_elabels"], n_vlabels=WORKLOAD["n_vlabels"],
                                    untyped_frac=WORKLOAD["untyped"], seed=WORKLOAD["seed"])
+
+
+class Workload:
+    """Inputs, one step of the path and its accounting for one benchmark configuration."""
+
+    def __init__(self, name, scale):
+        from paper_2111_12493_gb300 import graphgen
+        self.name = name
+        self.batched = name == "batched"
+        if name == "powerlaw":
+            g = workload_graph(scale)
+            self.k, self.cap = -1, WORKLOAD["cap"]
+            self.arrays = [g[k] for k in ("src", "dst", "elabel", "vlabel")]
+            self.graph = g
+        elif name == "chain":
+            paths = max(10, int(1000 * scale))
+            g = graphgen.chain_graph(n_paths=paths, path_len=1000, extra=int(2_000_000 * scale), seed=3)
+            self.k, self.cap = -1, 10_000
+            self.arrays = [g[k] for k in ("src", "dst", "elabel", "vlabel")]
+            self.graph = g
+        else:
+            b = graphgen.batched_graphs(n_graphs=max(8, int(4096 * scale)), seed=4)
+            self.k, self.cap = 3, 0
+            self.arrays = [b["vertex_offsets"], b["edge_offsets"], b["src_local"], b["dst_local"], b["elabel"],
+                           b["vlabel"]]
+            self.graph = b
+        self.n = int(self.arrays[-1].shape[0])
+        self.m = int(self.arrays[-4 if self.batched else 0].shape[0])
+
+    def config(self, extra=None):
+        g = self.graph
+        if self.name == "powerlaw":
+            return config_dict(self.n, self.m, g, extra)
+        if self.name == "chain":
+            d = {"workload": f"{self.n // 1000:,} directed paths of 1000 vertices (path-major ids) + "
+                             f"{self.m - (self.n // 1000) * 999:,} uniform extra edges, 16 uniform edge labels, "
+                             f"2 vertex labels; refine to the fixpoint (cap 10000)",
+                 "n_vertices": self.n, "n_edges": self.m, "k": "fixpoint", "cap": 10_000,
+                 "l2": "inputs smaller than L2 (36 MB COO): a latency-bound many-round workload"}
+        else:
+            ng = np.diff(g["vertex_offsets"])
+            d = {"workload": f"{g['n_graphs']:,} independent graphs in one context, vertex counts log-uniform "
+                             f"[100, 100k] (realised {int(ng.min()):,}-{int(ng.max()):,}), power-law out-degree "
+                             f"(2.3) with mean 5, uniform in-graph targets, 64 Zipf(1.1) edge labels, 16 vertex "
+                             f"labels; k=3",
+                 "n_graphs": int(g["n_graphs"]), "n_vertices": self.n, "n_edges": self.m, "k": 3,
+                 "l2": "inputs larger than L2"}
+        if extra:
+            d.update(extra)
+        return d
+
+    def step(self, bisim, tensors, out):
+        if self.batched:
+            ctx = bisim.summarize_init_batched(*tensors)
+        else:
+            ctx = bisim.summarize_init_coo(self.n, *tensors)
+        rounds, blocks = bisim.bisim_iterate(ctx, self.k, self.cap)
+        bisim.get_partition(ctx, out=out)
+        executed = bisim.bisim_get_stats(ctx)["rounds_executed"]
+        bisim.summarize_destroy(ctx)
+        return rounds, blocks, executed
+
+    def init_only(self, bisim, tensors):
+        if self.batched:
+            return bisim.summarize_init_batched(*tensors)
+        return bisim.summarize_init_coo(self.n, *tensors)
 
 
 def config_dict(n, m, g=None, extra=None):
@@ -176,23 +245,19 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     from paper_2111_12493_gb300 import bisim
 
-    g = workload_graph(args.scale)
-    n, m = g["n"], len(g["src"])
+    W = Workload(args.workload, args.scale)
+    g = W.graph
+    n, m = W.n, W.m
     dev = torch.device("cuda", local)
-    d_src, d_dst, d_lab, d_vl = (torch.from_numpy(g[k]).to(dev) for k in ("src", "dst", "elabel", "vlabel"))
+    d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in W.arrays]
     d_out = torch.empty(n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(src, dst, lab, vl, out):
-        ctx = bisim.summarize_init_coo(n, src, dst, lab, vl)
-        rounds, blocks = bisim.bisim_iterate(ctx, bisim.FIXPOINT, WORKLOAD["cap"])
-        bisim.get_partition(ctx, out=out)
-        executed = bisim.bisim_get_stats(ctx)["rounds_executed"]
-        bisim.summarize_destroy(ctx)
-        return rounds, blocks, executed
+    def step(*tensors):
+        return W.step(bisim, tensors[:-1], tensors[-1])
 
     for _ in range(args.warmup):
-        rounds, blocks, executed = step(d_src, d_dst, d_lab, d_vl, d_out)
+        rounds, blocks, executed = step(*d_in, d_out)
     torch.cuda.synchronize()
 
     # timed region: K steps, inputs resident in HBM
@@ -207,7 +272,7 @@ def run_ours(args, world, rank, local):
     ev0.record(stream)
     edge_iters = 0
     for _ in range(args.steps):
-        rounds, blocks, executed = step(d_src, d_dst, d_lab, d_vl, d_out)
+        rounds, blocks, executed = step(*d_in, d_out)
         edge_iters += m * executed
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -221,10 +286,10 @@ def run_ours(args, world, rank, local):
     value = total_edge_iters / (t_ms / 1e3)
 
     # iterate-only throughput (CSR already built), one more untimed-for-value run
-    ctx = bisim.summarize_init_coo(n, d_src, d_dst, d_lab, d_vl)
+    ctx = W.init_only(bisim, d_in)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    r2, _ = bisim.bisim_iterate(ctx, bisim.FIXPOINT, WORKLOAD["cap"])
+    r2, _ = bisim.bisim_iterate(ctx, W.k, W.cap)
     e1.record(stream)
     torch.cuda.synchronize()
     it_exec = bisim.bisim_get_stats(ctx)["rounds_executed"]
@@ -234,15 +299,20 @@ def run_ours(args, world, rank, local):
 
     # sanity of the result that was timed: canonical ids (block id = its smallest member)
     P = d_out.cpu().numpy()
-    assert (P >= 0).all() and (P <= np.arange(n)).all() and (P[P] == P).all(), "non-canonical partition"
-    assert len(np.unique(P)) == blocks
+    if W.batched:   # graph-local ids: the block id is the smallest local id in the block
+        local = np.arange(n) - np.repeat(g["vertex_offsets"][:-1], np.diff(g["vertex_offsets"]))
+        glob = P + (np.arange(n) - local)
+        assert (P >= 0).all() and (P <= local).all() and (glob[glob] == glob).all(), "non-canonical partition"
+    else:
+        assert (P >= 0).all() and (P <= np.arange(n)).all() and (P[P] == P).all(), "non-canonical partition"
+        assert len(np.unique(P)) == blocks
 
     # end to end through the C-ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        h_src, h_dst, h_lab, h_vl = (torch.from_numpy(g[k]).pin_memory() for k in ("src", "dst", "elabel", "vlabel"))
+        h_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in W.arrays]
         h_out = torch.empty(n, dtype=torch.int32).pin_memory()
-        step(h_src, h_dst, h_lab, h_vl, h_out)
+        step(*h_in, h_out)
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
@@ -251,7 +321,7 @@ def run_ours(args, world, rank, local):
         f0.record(stream)
         ei = 0
         for _ in range(args.steps):
-            _, _, ex = step(h_src, h_dst, h_lab, h_vl, h_out)
+            _, _, ex = step(*h_in, h_out)
             torch.cuda.synchronize()           # the partition is in host memory now
             ei += m * ex
         f1.record(stream)
@@ -260,7 +330,8 @@ def run_ours(args, world, rank, local):
         e_ms = max_over_ranks(world, max(f0.elapsed_time(f1), wall * 1e3))
         assert np.array_equal(h_out.numpy(), P), "host-buffer run differs from the device run"
         e2e = {"value": sum_over_ranks(world, ei) / (e_ms / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(4 * (3 * m + n)), "d2h_bytes_per_step": int(4 * n)}
+               "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in h_in)),
+               "d2h_bytes_per_step": int(4 * n)}
 
     # roofline of the dominant kernel (largest event-timed share of the timed steps)
     peaks = {}
@@ -288,20 +359,19 @@ def run_ours(args, world, rank, local):
                           for p in prof if p["launches"]), key=lambda x: -x["ms"])[:12]
 
     serving_info = None
-    if not args.no_serving:
+    if not args.no_serving and W.name == "powerlaw":
         serving_info = run_serving(args, local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.scale)
+        cpu = cpu_baseline(args.scale, W)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32 ids, u64 hashes (integer only)",
             "data": "synthetic (seeded generator; stands in for the paper's BSBM/DyLDO graphs)",
-            "config": config_dict(n, m, g, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                                      "rounds": int(rounds), "rounds_executed": int(executed),
-                                      "blocks": int(blocks)}),
+            "config": W.config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                "rounds": int(rounds), "rounds_executed": int(executed), "blocks": int(blocks)}),
             "iterate_only": {"value": iterate_only, "unit": UNIT, "rounds_executed": int(it_exec)},
             "e2e": e2e, "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu,
             "gpu_launches": int(launches), "clocks": clock_info,
@@ -423,37 +493,52 @@ def run_serving(args, local):
 
 # ----------------------------------------------------------------------------- oracle on the host cores
 
-def cpu_sample_graph(scale):
+def cpu_sample_graph(scale, workload="powerlaw"):
+    """A bounded sample of the workload that one oracle round finishes in ~10 s."""
     from paper_2111_12493_gb300 import graphgen
-    # a quarter-size instance of the same generator: one oracle round takes ~10 s
+    if workload == "chain":
+        return graphgen.chain_graph(n_paths=max(10, int(1000 * scale)), path_len=1000,
+                                    extra=int(2_000_000 * scale), seed=3), "the whole graph"
+    if workload == "batched":
+        b = graphgen.batched_graphs(n_graphs=max(8, int(512 * scale)), seed=4)
+        u = graphgen.batched_union(b)
+        return u, f"the union of the first {b['n_graphs']} graphs of the generator"
+    # a quarter-size instance of the same generator
     n = max(1000, int(2_500_000 * scale))
     m = max(10_000, int(25_000_000 * scale))
-    return graphgen.powerlaw_graph(n=n, m=m, exponent=WORKLOAD["exponent"], dmax=min(WORKLOAD["dmax"], m // 10),
-                                   n_elabels=WORKLOAD["n_elabels"], n_vlabels=WORKLOAD["n_vlabels"],
-                                   untyped_frac=WORKLOAD["untyped"], seed=WORKLOAD["seed"])
+    g = graphgen.powerlaw_graph(n=n, m=m, exponent=WORKLOAD["exponent"], dmax=min(WORKLOAD["dmax"], m // 10),
+                                n_elabels=WORKLOAD["n_elabels"], n_vlabels=WORKLOAD["n_vlabels"],
+                                untyped_frac=WORKLOAD["untyped"], seed=WORKLOAD["seed"])
+    return g, "a quarter-size instance of the same generator"
 
 
 def time_oracle_round(g):
     import oracle
-    P0 = oracle.label_partition(g["n"], g["vlabel"])
+    P0 = oracle.label_partition(g["n"], g["vlabel"], graph=g.get("graph"))
     t0 = time.perf_counter()
-    oracle.refine_round(g["n"], g["src"], g["dst"], g["elabel"], g["vlabel"], P0)
+    oracle.refine_round(g["n"], g["src"], g["dst"], g["elabel"], g["vlabel"], P0, graph=g.get("graph"))
     return time.perf_counter() - t0
 
 
-def cpu_baseline(scale):
-    g = cpu_sample_graph(scale)
+def cpu_baseline(scale, W=None):
+    g, what = cpu_sample_graph(scale, W.name if W else "powerlaw")
     dt = time_oracle_round(g)
     m = len(g["src"])
     return {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one exact refinement round P_0 -> P_1 of the same generator at quarter size "
-                      f"({g['n']:,} vertices / {m:,} edges), single-threaded C++ oracle, {dt:.1f} s"}
+            "sample": f"one exact refinement round P_0 -> P_1 on {what} ({g['n']:,} vertices / {m:,} edges), "
+                      f"single-threaded C++ oracle, {dt:.1f} s"}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    g = cpu_sample_graph(args.scale)
+    extra = {"parallelism": "single CPU thread", "note": "oracle timed on a bounded sample of the workload"}
+    if args.workload == "powerlaw":
+        config = config_dict(max(1000, int(WORKLOAD["n"] * args.scale)), max(10_000, int(WORKLOAD["m"] * args.scale)),
+                             extra=extra)
+    else:
+        config = Workload(args.workload, args.scale).config(extra)
+    g, what = cpu_sample_graph(args.scale, args.workload)
     m = len(g["src"])
     for _ in range(args.warmup):
         time_oracle_round(g)
@@ -464,12 +549,9 @@ def run_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32 ids (exact signatures, no hashing)", "data": "synthetic",
-            "config": config_dict(max(1000, int(WORKLOAD["n"] * args.scale)), max(10_000, int(WORKLOAD["m"] * args.scale)),
-                                  extra={"parallelism": "single CPU thread",
-                                         "note": "oracle timed on a bounded sample of the workload"}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"one exact refinement round per step on the quarter-size instance "
-                                       f"({g['n']:,} vertices / {m:,} edges)"},
+            "config": config, "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                               "sample": f"one exact refinement round per step on {what} "
+                                                         f"({g['n']:,} vertices / {m:,} edges)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

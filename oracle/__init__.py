@@ -68,6 +68,8 @@ def _load():
             lib.oracle_round.restype = ctypes.c_int
             lib.oracle_label_partition.argtypes = [i32, p, p, p, p]
             lib.oracle_label_partition.restype = ctypes.c_int
+            lib.oracle_apply_ops.argtypes = [i32, p, p, i64, p, p, p, i32, p, p, i64, p, p, p, p, p]
+            lib.oracle_apply_ops.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -209,3 +211,33 @@ def apply_ops(state: dict, ops: np.ndarray) -> dict:
     arr = np.array(keep, dtype=np.int32).reshape(-1, 3)
     return dict(n=n, alive=np.array(alive, dtype=np.uint8), vlabel=np.array(vlabel, dtype=np.int32),
                 src=arr[:, 0].copy(), dst=arr[:, 1].copy(), elabel=arr[:, 2].copy())
+
+
+def apply_batches(state: dict, batches: list) -> tuple:
+    """Apply update batches in order (C++ restatement of ``apply_ops`` for large graphs).
+
+    A rejected batch changes nothing and the later ones still apply, as on
+    the device. Returns (new state, list of rejected batch indices).
+    """
+    lib = _load()
+    n = int(state["n"])
+    alive = np.array(state["alive"], dtype=np.uint8, copy=True)
+    vlabel = np.array(state["vlabel"], dtype=np.int32, copy=True)
+    src, dst, lab = (_i32(state[k]) for k in ("src", "dst", "elabel"))
+    ops = [np.ascontiguousarray(np.asarray(b, dtype=np.int32).reshape(-1, 4)) for b in batches]
+    offsets = np.zeros(len(ops) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum([len(o) for o in ops])
+    allops = np.concatenate(ops) if ops else np.zeros((0, 4), np.int32)
+    allops = np.ascontiguousarray(allops, dtype=np.int32)
+    cap = len(src) + int(offsets[-1]) + 1
+    osrc, odst, olab = (np.empty(cap, dtype=np.int32) for _ in range(3))
+    out_m = ctypes.c_int64(0)
+    rejected = np.zeros(max(1, len(ops)), dtype=np.uint8)
+    rc = lib.oracle_apply_ops(n, _ptr(alive), _ptr(vlabel), len(src), _ptr(src), _ptr(dst), _ptr(lab), len(ops),
+                              _ptr(offsets), _ptr(allops), cap, _ptr(osrc), _ptr(odst), _ptr(olab),
+                              ctypes.byref(out_m), _ptr(rejected))
+    if rc != 0:
+        raise ValueError(f"oracle_apply_ops failed (code {rc})")
+    k = out_m.value
+    new = dict(n=n, alive=alive, vlabel=vlabel, src=osrc[:k].copy(), dst=odst[:k].copy(), elabel=olab[:k].copy())
+    return new, [i for i in range(len(ops)) if rejected[i]]

@@ -38,6 +38,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <set>
 #include <tuple>
 #include <utility>
 #include <vector>
@@ -189,3 +190,112 @@ int oracle_label_partition(int32_t n, const uint8_t* alive, const int32_t* vlabe
 }
 
 }  // extern "C"
+
+// Update batches with sequential semantics (the incremental setting of Section
+// 3.2: additions, deletions and modifications of vertices and edges), restated
+// for graphs too large for the Python restatement `apply_ops`, which it must
+// agree with:
+//   EDGE_ADD (a, b, l)  both endpoints in range and alive at that point of the
+//                        batch, else the whole batch is rejected
+//   EDGE_DEL (a, b, l)  removes one live edge (a, b, l); nothing if none is left
+//   VERTEX_ADD (a, l)   makes a alive with label l (relabels a live vertex)
+//   VERTEX_DEL (a)      makes a dead and removes every live edge at a
+// Ids out of range or unknown kinds reject the batch. A rejected batch changes
+// nothing; the others apply in order. Edges come out in input order (removed
+// ones dropped) followed by the added ones still live.
+namespace {
+
+struct EdgeKey {
+    int32_t s, d, l;
+    bool operator<(const EdgeKey& o) const { return std::tie(s, d, l) < std::tie(o.s, o.d, o.l); }
+};
+
+}  // namespace
+
+extern "C" int oracle_apply_ops(int32_t n, uint8_t* alive, int32_t* vlabel, int64_t m, const int32_t* src,
+                                const int32_t* dst, const int32_t* elab, int32_t n_batches,
+                                const int64_t* batch_offsets, const int32_t* ops, int64_t cap, int32_t* out_src,
+                                int32_t* out_dst, int32_t* out_label, int64_t* out_m, uint8_t* rejected) {
+    if (n < 0 || m < 0 || n_batches < 0) return 1;
+    std::vector<int32_t> es(src, src + m), ed(dst, dst + m), el(elab, elab + m);
+    std::vector<uint8_t> live(static_cast<size_t>(m), 1);
+    // only the keys some EDGE_DEL names and the vertices some VERTEX_DEL names need an index
+    std::set<EdgeKey> del_keys;
+    std::set<int32_t> del_vertices;
+    const int64_t total = batch_offsets[n_batches];
+    for (int64_t i = 0; i < total; ++i) {
+        const int32_t* o = ops + 4 * i;
+        if (o[0] == 1) del_keys.insert(EdgeKey{o[1], o[2], o[3]});
+        if (o[0] == 3) del_vertices.insert(o[1]);
+    }
+    std::map<EdgeKey, std::vector<int64_t>> by_key;      // live edge indices per named key
+    std::map<int32_t, std::vector<int64_t>> incident;    // edge indices per named vertex
+    auto index_edge = [&](int64_t i) {
+        const EdgeKey k{es[i], ed[i], el[i]};
+        if (del_keys.count(k)) by_key[k].push_back(i);
+        if (del_vertices.count(es[i])) incident[es[i]].push_back(i);
+        if (ed[i] != es[i] && del_vertices.count(ed[i])) incident[ed[i]].push_back(i);
+    };
+    for (int64_t i = 0; i < m; ++i) index_edge(i);
+    for (int32_t b = 0; b < n_batches; ++b) {
+        const int64_t lo = batch_offsets[b], hi = batch_offsets[b + 1];
+        // dry run: the alive state each op sees, and the ops' validity
+        std::map<int32_t, uint8_t> shadow;
+        auto is_alive = [&](int32_t v) {
+            auto it = shadow.find(v);
+            return it != shadow.end() ? it->second != 0 : alive[v] != 0;
+        };
+        bool ok = true;
+        for (int64_t i = lo; i < hi && ok; ++i) {
+            const int32_t* o = ops + 4 * i;
+            const int32_t kind = o[0], a = o[1], c = o[2];
+            const bool ra = a >= 0 && a < n, rc = c >= 0 && c < n;
+            if (kind == 0) ok = ra && rc && is_alive(a) && is_alive(c);
+            else if (kind == 1) ok = ra && rc;
+            else if (kind == 2) { ok = ra; if (ok) shadow[a] = 1; }
+            else if (kind == 3) { ok = ra; if (ok) shadow[a] = 0; }
+            else ok = false;
+        }
+        rejected[b] = ok ? 0 : 1;
+        if (!ok) continue;
+        for (int64_t i = lo; i < hi; ++i) {
+            const int32_t* o = ops + 4 * i;
+            const int32_t kind = o[0], a = o[1], c = o[2], l = o[3];
+            if (kind == 0) {
+                es.push_back(a);
+                ed.push_back(c);
+                el.push_back(l);
+                live.push_back(1);
+                index_edge(static_cast<int64_t>(es.size()) - 1);
+            } else if (kind == 1) {
+                auto it = by_key.find(EdgeKey{a, c, l});
+                if (it == by_key.end()) continue;
+                std::vector<int64_t>& lst = it->second;
+                while (!lst.empty() && !live[lst.back()]) lst.pop_back();
+                if (!lst.empty()) {
+                    live[lst.back()] = 0;
+                    lst.pop_back();
+                }
+            } else if (kind == 2) {
+                alive[a] = 1;
+                vlabel[a] = l;
+            } else {
+                alive[a] = 0;
+                auto it = incident.find(a);
+                if (it != incident.end())
+                    for (int64_t e : it->second) live[e] = 0;
+            }
+        }
+    }
+    int64_t k = 0;
+    for (size_t i = 0; i < es.size(); ++i) {
+        if (!live[i]) continue;
+        if (k >= cap) return 2;
+        out_src[k] = es[i];
+        out_dst[k] = ed[i];
+        out_label[k] = el[i];
+        ++k;
+    }
+    *out_m = k;
+    return 0;
+}

@@ -359,3 +359,43 @@ def test_apply_ops_rejects_whole_batch():
         oracle.apply_ops(st, np.array([[oracle.OP_EDGE_ADD, 0, 3, 0]], np.int32))
     with pytest.raises(oracle.UpdateRejected):
         oracle.apply_ops(st, np.array([[9, 0, 1, 0]], np.int32))
+
+
+def _multiset(state):
+    return sorted(zip(state["src"].tolist(), state["dst"].tolist(), state["elabel"].tolist()))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_batch_applier_agrees_with_sequential_apply_ops(seed):
+    # the C++ applier used for large graphs must give what apply_ops gives, batch by batch
+    rng = np.random.default_rng(seed)
+    n = 12
+    m = 30
+    state = dict(n=n, alive=(rng.random(n) < 0.9).astype(np.uint8), vlabel=rng.integers(0, 3, n).astype(np.int32))
+    live = np.flatnonzero(state["alive"])
+    s = rng.choice(live, m)
+    d = rng.choice(live, m)
+    state.update(src=s.astype(np.int32), dst=d.astype(np.int32), elabel=rng.integers(0, 3, m).astype(np.int32))
+    batches = []
+    for _ in range(8):
+        ops = []
+        for _ in range(int(rng.integers(1, 12))):
+            kind = int(rng.choice([0, 0, 1, 1, 2, 3], p=[0.25, 0.1, 0.25, 0.15, 0.15, 0.1]))
+            a, b, lab = int(rng.integers(-1, n + 1)) if rng.random() < 0.05 else int(rng.integers(0, n)), \
+                int(rng.integers(0, n)), int(rng.integers(0, 3))
+            if kind == 1 and len(state["src"]) and rng.random() < 0.7:
+                i = int(rng.integers(len(state["src"])))
+                a, b, lab = int(state["src"][i]), int(state["dst"][i]), int(state["elabel"][i])
+            ops.append((kind, a, b, lab))
+        batches.append(np.array(ops, np.int32))
+    want = state
+    want_rejected = []
+    for i, ops in enumerate(batches):
+        try:
+            want = oracle.apply_ops(want, ops)
+        except oracle.UpdateRejected:
+            want_rejected.append(i)
+    got, rejected = oracle.apply_batches(state, batches)
+    assert rejected == want_rejected
+    assert _multiset(got) == _multiset(want)
+    assert np.array_equal(got["alive"], want["alive"]) and np.array_equal(got["vlabel"], want["vlabel"])
