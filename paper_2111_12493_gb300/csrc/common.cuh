@@ -23,12 +23,10 @@ constexpr int kNumClasses = kClassHub + 1;               // 13
 constexpr uint8_t kClassDead = 255;
 
 // Degree classes of the dense round layout (all live vertices every round):
-//   0..6   lane groups of G = 1, 1, 2, 4, 8, 16, 32 lanes per vertex for out-degree
-//          0, 1, 2, 3-4, 5-8, 9-16, 17-32
+//   0..6   one thread per vertex for out-degree 0, 1, 2, 3-4, 5-8, 9-16, 17-32
 //   7..9   one warp per vertex, shared-memory set of 2N slots, N = 64, 128, 256
 //   10..14 one CTA per vertex, N = 512 .. 8192
-//   15     hubs: chunks of one row spread over CTAs, set in global memory
-constexpr int kDGroupClasses = 7;
+//   15     hubs: rows cut into chunks over many CTAs, values deduplicated by bucket
 constexpr int kDWarp0 = 7;
 constexpr int kDMid0 = 10;
 constexpr int kDHub = 15;
@@ -106,6 +104,7 @@ struct TableRef {
     uint64_t mask;        // nslots - 1
     uint64_t epoch;       // 1..15, already shifted into bits 32..35
     uint64_t hmask;       // hash width mask (tests only narrow it)
+    uint64_t pmask;       // probing wraps inside aligned parts of pmask + 1 slots (pmask = mask: one part)
 };
 
 struct DevState {
@@ -129,7 +128,7 @@ __device__ __forceinline__ uint32_t table_insert_from(const TableRef& t, uint64_
     const unsigned long long tag = (h & ~0xfffffffffull) | t.epoch;
     const unsigned long long want = tag | static_cast<uint32_t>(v);
     uint64_t pos = h & t.mask;
-    for (uint64_t probe = 0; probe <= t.mask; ++probe) {
+    for (uint64_t probe = 0; probe <= t.pmask; ++probe) {
         if (probe > 0) cur = table_read(t, pos);
         for (;;) {
             if ((cur & kSlotEpochMask) != t.epoch) {            // free in this epoch: claim it
@@ -150,7 +149,7 @@ __device__ __forceinline__ uint32_t table_insert_from(const TableRef& t, uint64_
             }
             break;                                               // another signature: probe on
         }
-        pos = (pos + 1) & t.mask;
+        pos = (pos & ~t.pmask) | ((pos + 1) & t.pmask);
     }
     atomicOr(err, kErrTableFull);
     return ~0u;
@@ -299,14 +298,22 @@ struct bisim_ctx {
     int32_t* dcnt = nullptr;                         // [n] |S| per position
     int2* dpairs = nullptr;                          // [n] (position, representative's position) for a CTA compare
     int2* dsmall = nullptr;                          // [n] the same for rows of at most 32 edges (warp compare)
-    bisim::HubChunk* dchunks = nullptr;
+    bisim::HubChunk* dchunks = nullptr;              // hub rows cut into chunks of at most 4096 edges
     int64_t n_dchunks = 0;
-    int64_t* dtoff = nullptr;
-    uint32_t* dtmask = nullptr;
-    unsigned long long* dtab = nullptr;
-    int64_t dtab_words = 0;
-    bisim::HubAcc* dacc = nullptr;
     int64_t n_dhub = 0;
+    int32_t* hshift = nullptr;                       // [n_dhub] log2 of the hub's value-bucket count
+    int64_t* hbbase = nullptr;                       // [n_dhub] first bucket of the hub
+    int32_t* bhub = nullptr;                         // [n_buckets] hub of the bucket
+    unsigned long long* bcount = nullptr;            // [n_buckets] values per bucket, this round
+    unsigned* bfill = nullptr;                       // [n_buckets] values placed so far, this round
+    int64_t* boff = nullptr;                         // [n_buckets + 1] bucket ranges in bvals
+    unsigned long long* bvals = nullptr;             // [hub edges] pair values grouped by bucket
+    unsigned long long* bmv = nullptr;               // [hub edges] pair values in row order
+    int64_t* bscan = nullptr;                        // scan scratch
+    int64_t n_buckets = 0;
+    int64_t hub_edges = 0;
+    int64_t bscan_words = 0;
+    bisim::HubAcc* dacc = nullptr;
 
     // collision resolution
     int32_t* ulist[2] = {nullptr, nullptr};

@@ -8,13 +8,13 @@
 // packed 8-byte words (label << 32 | target). Consecutive threads then read
 // consecutive edges whatever the vertex ids are, and every class runs as one
 // kind of work unit:
-//   degree <= 32    a group of G lanes per vertex (G = next power of two >= d):
-//                   one edge per lane, duplicates found by a warp match on the
-//                   pair value, the set's size and sum reduced in the group;
+//   degree <= 32    one thread per vertex, the row's pair values in registers,
+//                   a value counted when no earlier one equals it;
 //   degree <= 256   one warp per vertex with a set in shared memory;
 //   degree <= 8192  one CTA per vertex with a set in shared memory;
-//   above           the row cut into chunks over many CTAs, deduplicated in a
-//                   per-hub set in global memory.
+//   above           the row cut into chunks over many CTAs; its values are
+//                   bucketed by a mix of their bits and every bucket is
+//                   deduplicated by one CTA in shared memory.
 // Each vertex's signature hash goes into the open-addressing table, whose slots
 // keep the smallest vertex (the canonical block id). A verification pass then
 // confirms every vertex against its slot's representative by recomputing both
@@ -40,6 +40,7 @@ unsigned grid_for(int64_t n, int threads) {
 }
 
 constexpr int kMaxLevels = 1 << 16;
+constexpr int kPartShift = 40;                  // signature table parts (2^40 slots: one part; splitting into L2-sized parts did not pay)
 constexpr int kThreads = 256;
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
@@ -212,14 +213,6 @@ struct DenseView {
     uint32_t* slot;                    // table slot, by position
 };
 
-// The lane-group classes; CTAs are assigned to classes in order.
-struct GroupPlan {
-    int64_t cta_begin[kDGroupClasses + 1];
-    int64_t pos_begin[kDGroupClasses];
-    int64_t pos_end[kDGroupClasses];
-    int32_t gshift[kDGroupClasses];
-};
-
 struct WarpPlan {
     int64_t cta_begin[4];
     int64_t pos_begin[3];
@@ -257,42 +250,6 @@ __global__ void __launch_bounds__(kThreads) k_dense_thread_sig(int64_t first, in
         }
     }
     finish_sig(V, pos, own, u, sum);
-}
-
-// Degree <= 32: one lane per edge in groups of G lanes per vertex.
-__global__ void __launch_bounds__(kThreads) k_dense_group_sig(const GroupPlan plan, const DenseView D) {
-    const int64_t b = blockIdx.x;
-    int c = 0;
-    while (c + 1 < kDGroupClasses && b >= plan.cta_begin[c + 1]) ++c;
-    const int gs = plan.gshift[c];
-    const unsigned G = 1u << gs;
-    const unsigned lane = lane_id();
-    const unsigned gl = lane & (G - 1u);
-    const unsigned gbase = lane & ~(G - 1u);
-    const unsigned gmask = G == 32u ? 0xffffffffu : ((1u << G) - 1u) << gbase;
-    const int64_t pos = plan.pos_begin[c] + (b - plan.cta_begin[c]) * (kThreads >> gs) + (threadIdx.x >> gs);
-    const bool valid = pos < plan.pos_end[c];
-    int32_t own = 0;
-    if (valid && gl == 0) own = D.P[D.vert[pos]];      // independent of the row: issued first
-    int64_t e0 = 0;
-    int d = 0;
-    if (valid) {
-        e0 = D.prp[pos];
-        d = static_cast<int>(D.prp[pos + 1] - e0);
-    }
-    const bool has = valid && static_cast<int>(gl) < d;
-    uint64_t mv = 0;
-    if (has) mv = packed_pair_value(__ldcs(D.pe + e0 + gl), D.P);
-    const unsigned hasm = __ballot_sync(0xffffffffu, has);
-    unsigned firstm = hasm;
-    if (G > 1u) {
-        // lanes holding the same pair value in one group: the lowest one counts it
-        const unsigned peers = __match_any_sync(0xffffffffu, static_cast<unsigned long long>(mv)) & hasm & gmask;
-        firstm = __ballot_sync(0xffffffffu, has && static_cast<unsigned>(__ffs(peers) - 1) == lane);
-    }
-    uint64_t sum = ((firstm >> lane) & 1u) ? mv : 0ull;
-    for (unsigned o = G >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (valid && gl == 0) finish_sig(D, pos, own, static_cast<uint32_t>(__popc(firstm & gmask)), sum);
 }
 
 // Degree <= 256: one warp per vertex, set of up to 512 slots in the warp's slice.
@@ -380,91 +337,182 @@ __global__ void __launch_bounds__(T) k_dense_mid_sig(int64_t first, const DenseV
     }
 }
 
+// Hub rows are deduplicated by value buckets: pass 1 counts, per hub, the row's
+// pair values per bucket (the top bits of a salted mix of the value); a scan
+// turns the counts into bucket ranges; pass 2 scatters the values into their
+// buckets; pass 3 gives every bucket a CTA that deduplicates it in a
+// shared-memory set. No value leaves its bucket, so the hub's set size and sum
+// are the sums over its buckets. Every pass streams; nothing in global memory
+// is probed at random.
 struct HubSets {
     int64_t first;                 // position of the first hub
     int64_t n_hub;
-    const int64_t* toff;
-    const uint32_t* tmask;
-    unsigned long long* tab;
+    const int32_t* shift;          // log2 of the hub's bucket count
+    const int64_t* bbase;          // first bucket of each hub
+    const int32_t* bhub;           // hub of each bucket
+    unsigned long long* bcount;    // values per bucket (pass 1)
+    unsigned* bfill;               // values placed per bucket (pass 2)
+    int64_t* boff;                 // bucket ranges in bvals (scan of bcount)
+    unsigned long long* bvals;     // the bucketed pair values
+    unsigned long long* bmv;       // the hub edges' pair values in row order (pass 1 -> pass 2)
+    int64_t e0;                    // first hub edge in the packed rows
     HubAcc* acc;
 };
 
-// Inserts mv (not 0) into a hub set, starting from the first probe slot's
-// value `cur`; true for the first inserter.
-__device__ __forceinline__ bool hub_set_insert_from(unsigned long long* tab, uint32_t mask, uint64_t mv,
-                                                    unsigned long long cur, unsigned* err) {
-    uint32_t p = static_cast<uint32_t>(mv) & mask;
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        if (probe > 0) cur = tab[p];
-        if (cur == mv) return false;
-        if (cur == 0ull) {
-            const unsigned long long prev = atomicCAS(&tab[p], 0ull, static_cast<unsigned long long>(mv));
-            if (prev == 0ull) return true;
-            if (prev == mv) return false;
-        }
-        p = (p + 1) & mask;
-    }
-    atomicOr(err, kErrHubFull);
-    return false;
+constexpr uint64_t kSaltBucket = 0x452821e638d01377ull;
+constexpr int kHubMaxBuckets = 2048;            // per hub
+constexpr int kHubBucketTarget = 1024;          // values per bucket aimed at
+constexpr int kHubSetSlots = 4096;              // shared-memory set of a bucket pass (32 KB)
+constexpr int kHubMaxSplits = 1 << 12;          // sub-ranges tried before a bucket is declared full
+
+__device__ __forceinline__ uint64_t bucket_mix(uint64_t mv) { return mix64(mv ^ kSaltBucket); }
+
+__device__ __forceinline__ uint32_t bucket_of(uint64_t mixed, int shift) {
+    return shift == 0 ? 0u : static_cast<uint32_t>(mixed >> (64 - shift));
 }
 
-// Hubs, phase 1: every CTA inserts one chunk of a hub's row into the hub's set;
-// first inserters add their value to the hub's count and order-independent sum.
-// Each thread keeps kHubUnroll edges in flight (loads, gathers and first probes).
-constexpr int kHubUnroll = 4;
-__global__ void __launch_bounds__(kThreads) k_dense_hub_insert(const HubChunk* __restrict__ chunks, const DenseView D,
-                                                               const HubSets H, unsigned* err) {
+// Sub-range `sub` of `splits` inside a bucket: the next bits of the mix after the bucket's.
+__device__ __forceinline__ uint32_t split_of(uint64_t mixed, int shift, uint32_t splits) {
+    return splits <= 1 ? 0u : static_cast<uint32_t>((mixed << shift) >> (64 - __ffs(splits) + 1));
+}
+
+// Pass 1: per-chunk histogram of bucket ids, added into the hub's bucket
+// counts; the pair values are kept in row order for pass 2.
+__global__ void __launch_bounds__(kThreads) k_hub_count(const HubChunk* __restrict__ chunks, const DenseView D,
+                                                        const HubSets H) {
+    __shared__ unsigned hist[kHubMaxBuckets];
+    const HubChunk c = chunks[blockIdx.x];
+    const int shift = H.shift[c.hub];
+    const int nb = 1 << shift;
+    for (int b = threadIdx.x; b < nb; b += kThreads) hist[b] = 0u;
+    __syncthreads();
+    for (int64_t e = c.begin + threadIdx.x; e < c.end; e += kThreads) {
+        const uint64_t mv = packed_pair_value(__ldcs(D.pe + e), D.P);
+        H.bmv[e - H.e0] = mv;
+        atomicAdd(&hist[bucket_of(bucket_mix(mv), shift)], 1u);
+    }
+    __syncthreads();
+    const int64_t base = H.bbase[c.hub];
+    for (int b = threadIdx.x; b < nb; b += kThreads)
+        if (hist[b]) atomicAdd(&H.bcount[base + b], static_cast<unsigned long long>(hist[b]));
+}
+
+// Pass 2: the chunk's values go to their buckets. Each CTA reserves one range
+// per bucket it touches, so the writes of a bucket are contiguous.
+constexpr int kHubStage = kHubChunkMax;
+__global__ void __launch_bounds__(kThreads) k_hub_scatter(const HubChunk* __restrict__ chunks, const HubSets H) {
+    extern __shared__ unsigned long long stage[];                  // kHubStage values
+    unsigned* where = reinterpret_cast<unsigned*>(stage + kHubStage);   // bucket << 16 | index in the CTA's range
+    __shared__ unsigned hist[kHubMaxBuckets];
+    __shared__ unsigned start[kHubMaxBuckets];
+    const HubChunk c = chunks[blockIdx.x];
+    const int shift = H.shift[c.hub];
+    const int nb = 1 << shift;
+    const int cnt = static_cast<int>(c.end - c.begin);
+    for (int b = threadIdx.x; b < nb; b += kThreads) hist[b] = 0u;
+    __syncthreads();
+    const unsigned long long* src = H.bmv + (c.begin - H.e0);
+    for (int j = threadIdx.x; j < cnt; j += kThreads) {
+        const uint64_t mv = __ldcs(src + j);
+        const uint32_t b = bucket_of(bucket_mix(mv), shift);
+        stage[j] = mv;
+        where[j] = (b << 16) | atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+    const int64_t base = H.bbase[c.hub];
+    for (int b = threadIdx.x; b < nb; b += kThreads)
+        start[b] = hist[b] ? atomicAdd(&H.bfill[base + b], hist[b]) : 0u;
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += kThreads) {
+        const unsigned w = where[j];
+        const int64_t gb = base + (w >> 16);
+        H.bvals[H.boff[gb] + start[w >> 16] + (w & 0xffffu)] = stage[j];
+    }
+}
+
+// Pass 3: one CTA per bucket. The bucket's distinct values are counted and
+// summed through a shared-memory set; a bucket with more distinct values than
+// the set takes (kHubSetLimit) is redone in 2, 4, ... sub-ranges of the mix,
+// one set pass each.
+constexpr int kHubSetLimit = 3072;
+constexpr int kDedupUnroll = 4;
+constexpr size_t kHubScatterSmem = (sizeof(unsigned long long) + sizeof(unsigned)) * kHubStage;
+constexpr size_t kHubDedupSmem = sizeof(unsigned long long) * kHubSetSlots;
+__global__ void __launch_bounds__(kThreads) k_hub_dedup(const HubSets H, unsigned* err) {
+    extern __shared__ unsigned long long tab[];                    // kHubSetSlots
+    __shared__ unsigned zero, used, over;
     __shared__ unsigned long long wsum[kThreads / 32];
     __shared__ unsigned wcnt[kThreads / 32];
-    const HubChunk c = chunks[blockIdx.x];
-    unsigned long long* tab = H.tab + H.toff[c.hub];
-    const uint32_t mask = H.tmask[c.hub];
-    uint64_t lsum = 0;
-    unsigned lcnt = 0;
-    for (int64_t e0 = c.begin + threadIdx.x; e0 < c.end; e0 += kThreads * kHubUnroll) {
-        uint64_t mv[kHubUnroll];
-        bool act[kHubUnroll];
-#pragma unroll
-        for (int k = 0; k < kHubUnroll; ++k) {
-            const int64_t e = e0 + static_cast<int64_t>(k) * kThreads;
-            act[k] = e < c.end;
-            mv[k] = act[k] ? packed_pair_value(__ldcs(D.pe + e), D.P) : 0ull;
-        }
-        unsigned long long cur[kHubUnroll];
-#pragma unroll
-        for (int k = 0; k < kHubUnroll; ++k)
-            cur[k] = (act[k] && mv[k] != 0ull) ? tab[static_cast<uint32_t>(mv[k]) & mask] : 0ull;
-#pragma unroll
-        for (int k = 0; k < kHubUnroll; ++k) {
-            if (!act[k]) continue;
-            const bool fresh = mv[k] == 0ull ? atomicOr(&H.acc[c.hub].zero, 1u) == 0u
-                                             : hub_set_insert_from(tab, mask, mv[k], cur[k], err);
-            if (fresh) {
-                lsum += mv[k];
-                ++lcnt;
+    volatile unsigned* overv = &over;
+    const int64_t gb = blockIdx.x;
+    const int h = H.bhub[gb];
+    const int shift = H.shift[h];
+    const int64_t lo = H.boff[gb], hi = H.boff[gb + 1];
+    uint64_t sum = 0;
+    unsigned cnt = 0;
+    bool done = false;
+    for (uint32_t splits = 1; splits <= static_cast<uint32_t>(kHubMaxSplits) && !done; splits <<= 1) {
+        sum = 0;
+        cnt = 0;
+        bool o = false;
+        for (uint32_t sub = 0; sub < splits && !o; ++sub) {
+            for (int j = threadIdx.x; j < kHubSetSlots; j += kThreads) tab[j] = 0ull;
+            if (threadIdx.x == 0) {
+                zero = 0u;
+                used = 0u;
+                over = 0u;
             }
+            __syncthreads();
+            for (int64_t e0 = lo + threadIdx.x; e0 < hi; e0 += kThreads * kDedupUnroll) {
+                if (*overv) break;
+                uint64_t mv[kDedupUnroll];
+#pragma unroll
+                for (int k = 0; k < kDedupUnroll; ++k) {
+                    const int64_t e = e0 + static_cast<int64_t>(k) * kThreads;
+                    mv[k] = e < hi ? __ldcs(H.bvals + e) : 0ull;
+                }
+#pragma unroll
+                for (int k = 0; k < kDedupUnroll; ++k) {
+                    if (e0 + static_cast<int64_t>(k) * kThreads >= hi) break;
+                    if (splits > 1 && split_of(bucket_mix(mv[k]), shift, splits) != sub) continue;
+                    if (smem_set_insert(tab, kHubSetSlots - 1, &zero, mv[k])) {
+                        sum += mv[k];
+                        ++cnt;
+                        if (mv[k] != 0ull && atomicAdd(&used, 1u) + 1u > static_cast<unsigned>(kHubSetLimit))
+                            *overv = 1u;
+                    }
+                }
+            }
+            __syncthreads();
+            o = *overv != 0u;               // the same for every thread
+            __syncthreads();
         }
+        done = !o;
+    }
+    if (!done) {
+        if (threadIdx.x == 0) atomicOr(err, kErrHubFull);
+        return;                             // uniform: every thread saw the same flags
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-        lcnt += __shfl_xor_sync(0xffffffffu, lcnt, o);
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o2);
     }
     if (lane_id() == 0) {
-        wsum[threadIdx.x >> 5] = lsum;
-        wcnt[threadIdx.x >> 5] = lcnt;
+        wsum[threadIdx.x >> 5] = sum;
+        wcnt[threadIdx.x >> 5] = cnt;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint64_t s = 0;
-        unsigned n = 0;
+        uint64_t s2 = 0;
+        unsigned c2 = 0;
         for (int w = 0; w < kThreads / 32; ++w) {
-            s += wsum[w];
-            n += wcnt[w];
+            s2 += wsum[w];
+            c2 += wcnt[w];
         }
-        if (n) {
-            atomicAdd(&H.acc[c.hub].sum, static_cast<unsigned long long>(s));
-            atomicAdd(&H.acc[c.hub].count, n);
+        if (c2) {
+            atomicAdd(&H.acc[h].sum, static_cast<unsigned long long>(s2));
+            atomicAdd(&H.acc[h].count, c2);
         }
     }
 }
@@ -478,73 +526,20 @@ __global__ void k_dense_hub_finalize(const DenseView D, const HubSets H) {
     finish_sig(D, pos, D.P[D.vert[pos]], H.acc[h].count, H.acc[h].sum);
 }
 
-__device__ __forceinline__ bool hub_set_contains(const HubSets& H, int64_t h, uint64_t mv) {
-    if (mv == 0ull) return H.acc[h].zero != 0u;
-    const unsigned long long* tab = H.tab + H.toff[h];
-    const uint32_t mask = H.tmask[h];
-    uint32_t p = static_cast<uint32_t>(mv) & mask;
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        const unsigned long long cur = tab[p];
-        if (cur == mv) return true;
-        if (cur == 0ull) return false;
-        p = (p + 1) & mask;
-    }
-    return false;
-}
 
 // Table insert of every listed position (level 0: all live positions, list ==
-// null) with the level's salted hash. Each thread handles kPosUnroll positions
-// a CTA width apart, with their loads and first probes in flight together.
-constexpr int kPosUnroll = 4;
+// null) with the level's salted hash. The table is split into parts small
+// enough for L2 (a position's part is given by its slot index); pass `part`
+// inserts only the positions of that part (part < 0: all).
 __global__ void __launch_bounds__(kThreads) k_dense_insert(const int32_t* __restrict__ list, int64_t count,
                                                            const DenseView D, uint32_t level, const TableRef t,
-                                                           unsigned* err) {
-    const int64_t base = static_cast<int64_t>(blockIdx.x) * (kThreads * kPosUnroll) + threadIdx.x;
-    int64_t pos[kPosUnroll];
-    int32_t v[kPosUnroll];
-    uint64_t h[kPosUnroll];
-    unsigned long long cur[kPosUnroll];
-#pragma unroll
-    for (int k = 0; k < kPosUnroll; ++k) {
-        const int64_t i = base + static_cast<int64_t>(k) * kThreads;
-        pos[k] = i < count ? (list ? list[i] : i) : -1;
-    }
-#pragma unroll
-    for (int k = 0; k < kPosUnroll; ++k) {
-        if (pos[k] < 0) continue;
-        v[k] = D.vert[pos[k]];
-        h[k] = level_hash(D.hash[pos[k]], level, t.hmask);
-    }
-#pragma unroll
-    for (int k = 0; k < kPosUnroll; ++k)
-        if (pos[k] >= 0) cur[k] = table_read(t, h[k] & t.mask);
-    // the common cases need one CAS on the first probe slot: issue them together
-    bool done[kPosUnroll];
-#pragma unroll
-    for (int k = 0; k < kPosUnroll; ++k) {
-        done[k] = false;
-        if (pos[k] < 0) continue;
-        const unsigned long long tag = (h[k] & ~0xfffffffffull) | t.epoch;
-        const unsigned long long want = tag | static_cast<uint32_t>(v[k]);
-        const uint64_t sp = h[k] & t.mask;
-        const bool free_slot = (cur[k] & kSlotEpochMask) != t.epoch;
-        const bool same = !free_slot && (cur[k] & kSlotKeyMask) == tag;
-        if (same && static_cast<uint32_t>(v[k]) >= static_cast<uint32_t>(cur[k])) {
-            D.slot[pos[k]] = static_cast<uint32_t>(sp);      // a smaller vertex is already recorded
-            done[k] = true;
-        } else if (free_slot || same) {
-            const unsigned long long prev = atomicCAS(&t.slots[sp].w, cur[k], want);
-            if (prev == cur[k]) {
-                D.slot[pos[k]] = static_cast<uint32_t>(sp);
-                done[k] = true;
-            } else {
-                cur[k] = prev;
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < kPosUnroll; ++k)
-        if (pos[k] >= 0 && !done[k]) D.slot[pos[k]] = table_insert_from(t, h[k], v[k], cur[k], err);
+                                                           int part, int pshift, unsigned* err) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t pos = list ? list[i] : i;
+    const uint64_t h = level_hash(D.hash[pos], level, t.hmask);
+    if (part >= 0 && static_cast<int>((h & t.mask) >> pshift) != part) return;
+    D.slot[pos] = table_insert(t, h, D.vert[pos], err);
 }
 
 struct VerifyOut {
@@ -559,73 +554,63 @@ struct VerifyOut {
 // smallest vertex). r itself: a block id. Different own block or set size: the
 // position moves to the next level. Otherwise the sets are compared: here when
 // both rows have at most two edges, else in a warp (rows <= 32) or a CTA.
-// kPosUnroll positions per thread, their slot reads in flight together.
+// Pass `part` takes the positions whose slot lies in that part of the table
+// (failed inserts in part 0; part < 0: all).
 __global__ void __launch_bounds__(kThreads) k_dense_verify(const int32_t* __restrict__ list, int64_t count,
                                                            const DenseView D, const Slot* __restrict__ slots,
-                                                           const VerifyOut O, int32_t n_total) {
-    const int64_t base = static_cast<int64_t>(blockIdx.x) * (kThreads * kPosUnroll) + threadIdx.x;
-    int64_t pos[kPosUnroll];
-    int32_t v[kPosUnroll], r[kPosUnroll];
-    uint32_t sv[kPosUnroll];
-#pragma unroll
-    for (int k = 0; k < kPosUnroll; ++k) {
-        const int64_t i = base + static_cast<int64_t>(k) * kThreads;
-        pos[k] = i < count ? (list ? list[i] : i) : -1;
+                                                           const VerifyOut O, int32_t n_total, int part,
+                                                           int pshift) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    bool own = false, push = false, small = false, big = false;
+    int64_t pos = -1, rpos = -1;
+    if (i < count) {
+        pos = list ? list[i] : i;
+        const uint32_t sv = D.slot[pos];
+        const int my_part = sv == ~0u ? 0 : static_cast<int>(sv >> pshift);
+        if (part >= 0 && my_part != part) pos = -1;
     }
-#pragma unroll
-    for (int k = 0; k < kPosUnroll; ++k) {
-        if (pos[k] < 0) continue;
-        v[k] = D.vert[pos[k]];
-        sv[k] = D.slot[pos[k]];
-    }
-#pragma unroll
-    for (int k = 0; k < kPosUnroll; ++k)
-        if (pos[k] >= 0) r[k] = sv[k] == ~0u ? -1 : table_rep(slots, sv[k]);
-#pragma unroll
-    for (int k = 0; k < kPosUnroll; ++k) {
-        bool own = false, push = false, small = false, big = false;
-        int64_t rpos = -1;
-        if (pos[k] >= 0) {
-            const int32_t vk = v[k], rk = r[k];
-            if (rk < 0 || rk >= n_total) {               // failed insert, reported through st->error
-                atomicOr(&O.st->error, kErrTableFull);
-                O.Pout[vk] = -1;
-            } else if (rk == vk) {
-                O.Pout[vk] = vk;
-                own = true;
+    if (pos >= 0) {
+        const int32_t v = D.vert[pos];
+        const uint32_t sv = D.slot[pos];
+        const int32_t r = sv == ~0u ? -1 : table_rep(slots, sv);
+        if (r < 0 || r >= n_total) {                     // failed insert, reported through st->error
+            atomicOr(&O.st->error, kErrTableFull);
+            O.Pout[v] = -1;
+        } else if (r == v) {
+            O.Pout[v] = v;
+            own = true;
+        } else {
+            rpos = D.vpos[r];
+            if (D.P[v] != D.P[r] || D.cnt[pos] != D.cnt[rpos]) {
+                push = true;
             } else {
-                rpos = D.vpos[rk];
-                if (D.P[vk] != D.P[rk] || D.cnt[pos[k]] != D.cnt[rpos]) {
-                    push = true;
-                } else {
-                    const int64_t ev = D.prp[pos[k]], dv = D.prp[pos[k] + 1] - ev;
-                    const int64_t er = D.prp[rpos], dr = D.prp[rpos + 1] - er;
-                    if (dv <= 2 && dr <= 2) {
-                        // S_v inside S_r with equal sizes means equal sets
-                        uint64_t b0 = 0, b1 = 0;
-                        if (dr > 0) b0 = packed_pair_value(D.pe[er], D.P);
-                        if (dr > 1) b1 = packed_pair_value(D.pe[er + 1], D.P);
-                        bool ok = true;
-                        for (int64_t j = 0; j < dv; ++j) {
-                            const uint64_t a = packed_pair_value(D.pe[ev + j], D.P);
-                            ok = ok && ((dr > 0 && a == b0) || (dr > 1 && a == b1));
-                        }
-                        if (ok) O.Pout[vk] = rk;
-                        else push = true;
-                    } else if (dv <= 32 && dr <= 32) {
-                        small = true;
-                    } else {
-                        big = true;
+                const int64_t ev = D.prp[pos], dv = D.prp[pos + 1] - ev;
+                const int64_t er = D.prp[rpos], dr = D.prp[rpos + 1] - er;
+                if (dv <= 2 && dr <= 2) {
+                    // S_v inside S_r with equal sizes means equal sets
+                    uint64_t b0 = 0, b1 = 0;
+                    if (dr > 0) b0 = packed_pair_value(D.pe[er], D.P);
+                    if (dr > 1) b1 = packed_pair_value(D.pe[er + 1], D.P);
+                    bool ok = true;
+                    for (int64_t j = 0; j < dv; ++j) {
+                        const uint64_t a = packed_pair_value(D.pe[ev + j], D.P);
+                        ok = ok && ((dr > 0 && a == b0) || (dr > 1 && a == b1));
                     }
+                    if (ok) O.Pout[v] = r;
+                    else push = true;
+                } else if (dv <= 32 && dr <= 32) {
+                    small = true;
+                } else {
+                    big = true;
                 }
             }
         }
-        const int32_t p32 = static_cast<int32_t>(pos[k]);
-        warp_count(own, &O.st->blocks);
-        warp_push(push, p32, O.next, &O.st->unresolved);
-        warp_push(small, make_int2(p32, static_cast<int32_t>(rpos)), O.small, &O.st->pairs);
-        warp_push(big, make_int2(p32, static_cast<int32_t>(rpos)), O.pairs, &O.st->deferred);
     }
+    const int32_t p32 = static_cast<int32_t>(pos);
+    warp_count(own, &O.st->blocks);
+    warp_push(push, p32, O.next, &O.st->unresolved);
+    warp_push(small, make_int2(p32, static_cast<int32_t>(rpos)), O.small, &O.st->pairs);
+    warp_push(big, make_int2(p32, static_cast<int32_t>(rpos)), O.pairs, &O.st->deferred);
 }
 
 constexpr int kCompareGrid = 304;                      // persistent grids: two CTAs per SM
@@ -659,17 +644,18 @@ __global__ void __launch_bounds__(kThreads) k_dense_compare_warp(const int2* __r
     }
 }
 
-constexpr int kCompareSlots = 2 * kMidMaxN;          // shared-memory set for sets up to 8192 values
+constexpr int kCompareSlots = 2 * kMidMaxN;          // shared-memory set of 16384 slots
+constexpr int kCompareLimit = 3 * kMidMaxN / 2;       // distinct values one pass may hold
 constexpr size_t kCompareSmem = sizeof(unsigned long long) * kCompareSlots;
 
-// Longer rows: one CTA per pair. S_r is rebuilt in shared memory from r's row
-// when it has at most 8192 values; a larger S_r belongs to a hub, whose set
-// from this round is probed instead.
+// Longer rows: one CTA per pair; S_v == S_r iff every value of v's row is in
+// S_r (the sizes are equal).
 __global__ void __launch_bounds__(kThreads) k_dense_compare_cta(const int2* __restrict__ pairs, const DenseView D,
                                                                 const HubSets H, int32_t* __restrict__ Pout,
                                                                 int32_t* __restrict__ next, DevState* st) {
     extern __shared__ unsigned long long tab[];
-    __shared__ unsigned zero;
+    __shared__ unsigned zero, used, over;
+    volatile unsigned* overv = &over;
     const unsigned count = *reinterpret_cast<volatile unsigned*>(&st->deferred);
     for (unsigned i = blockIdx.x; i < count; i += gridDim.x) {
         const int2 pr = pairs[i];
@@ -677,26 +663,47 @@ __global__ void __launch_bounds__(kThreads) k_dense_compare_cta(const int2* __re
         const int64_t ev = D.prp[pr.x], dv = D.prp[pr.x + 1] - ev;
         const int64_t er = D.prp[pr.y], dr = D.prp[pr.y + 1] - er;
         bool miss = false;
-        if (c > kMidMaxN) {
-            // |S_r| > 8192: r's row is longer than the CTA classes allow, so r is a hub
-            const int64_t h = static_cast<int64_t>(pr.y) - H.first;
-            if (h < 0 || h >= H.n_hub) {
-                miss = true;
-            } else {
-                for (int64_t j = threadIdx.x; j < dv && !miss; j += kThreads)
-                    miss = !hub_set_contains(H, h, packed_pair_value(D.pe[ev + j], D.P));
+        // S_r is rebuilt in shared memory, in sub-ranges of the value mix when
+        // it is too large for one set (a hub): each pass takes the values of
+        // both rows in one sub-range; more sub-ranges when a pass overflows
+        uint32_t splits = 1;
+        while (splits * static_cast<uint32_t>(kCompareLimit) < static_cast<uint32_t>(c)) splits <<= 1;
+        bool done = false;
+        for (; splits <= static_cast<uint32_t>(kHubMaxSplits) && !done && !miss; splits <<= 1) {
+            bool o = false;
+            for (uint32_t sub = 0; sub < splits && !o && !miss; ++sub) {
+                for (int j = threadIdx.x; j < kCompareSlots; j += kThreads) tab[j] = 0ull;
+                if (threadIdx.x == 0) {
+                    zero = 0u;
+                    used = 0u;
+                    over = 0u;
+                }
+                __syncthreads();
+                for (int64_t j = threadIdx.x; j < dr; j += kThreads) {
+                    if (*overv) break;
+                    const uint64_t mv = packed_pair_value(D.pe[er + j], D.P);
+                    if (split_of(bucket_mix(mv), 0, splits) != sub) continue;
+                    if (smem_set_insert(tab, kCompareSlots - 1, &zero, mv) && mv != 0ull &&
+                        atomicAdd(&used, 1u) + 1u > static_cast<unsigned>(kCompareLimit))
+                        *overv = 1u;
+                }
+                __syncthreads();
+                o = *overv != 0u;
+                bool my_miss = false;
+                if (!o) {
+                    for (int64_t j = threadIdx.x; j < dv && !my_miss; j += kThreads) {
+                        const uint64_t mv = packed_pair_value(D.pe[ev + j], D.P);
+                        if (split_of(bucket_mix(mv), 0, splits) != sub) continue;
+                        my_miss = !smem_set_contains(tab, kCompareSlots - 1, zero, mv);
+                    }
+                }
+                miss = __syncthreads_or(my_miss ? 1 : 0) != 0;
             }
-        } else {
-            uint32_t size = 64;
-            while (size < 2u * static_cast<uint32_t>(c)) size <<= 1;
-            for (uint32_t j = threadIdx.x; j < size; j += kThreads) tab[j] = 0ull;
-            if (threadIdx.x == 0) zero = 0u;
-            __syncthreads();
-            for (int64_t j = threadIdx.x; j < dr; j += kThreads)
-                smem_set_insert(tab, size - 1, &zero, packed_pair_value(D.pe[er + j], D.P));
-            __syncthreads();
-            for (int64_t j = threadIdx.x; j < dv && !miss; j += kThreads)
-                miss = !smem_set_contains(tab, size - 1, zero, packed_pair_value(D.pe[ev + j], D.P));
+            done = !o;
+        }
+        if (!done && !miss) {            // no split fits: report instead of guessing
+            if (threadIdx.x == 0) atomicOr(&st->error, kErrHubFull);
+            miss = true;
         }
         const int any = __syncthreads_or(miss ? 1 : 0);
         if (threadIdx.x == 0) {
@@ -708,24 +715,6 @@ __global__ void __launch_bounds__(kThreads) k_dense_compare_cta(const int2* __re
 }
 
 // ----------------------------------------------------------------------------- host helpers
-
-constexpr int kGroupShift[kDGroupClasses] = {0, 0, 1, 2, 3, 4, 5};
-
-// Lane groups for the classes from `first` on (the ones before run one thread per vertex).
-GroupPlan group_plan(const bisim_ctx* ctx, int first) {
-    GroupPlan p;
-    std::memset(&p, 0, sizeof(p));
-    int64_t cta = 0;
-    for (int c = 0; c < kDGroupClasses; ++c) {
-        p.cta_begin[c] = cta;
-        p.pos_begin[c] = c < first ? 0 : ctx->dbegin[c];
-        p.pos_end[c] = c < first ? 0 : ctx->dbegin[c + 1];
-        p.gshift[c] = kGroupShift[c];
-        cta += cdiv(p.pos_end[c] - p.pos_begin[c], kThreads >> p.gshift[c]);
-    }
-    p.cta_begin[kDGroupClasses] = cta;
-    return p;
-}
 
 WarpPlan warp_plan(const bisim_ctx* ctx) {
     WarpPlan w;
@@ -741,7 +730,8 @@ WarpPlan warp_plan(const bisim_ctx* ctx) {
 }
 
 HubSets hub_sets(const bisim_ctx* ctx) {
-    return HubSets{ctx->dbegin[kDHub], ctx->n_dhub, ctx->dtoff, ctx->dtmask, ctx->dtab, ctx->dacc};
+    return HubSets{ctx->dbegin[kDHub], ctx->n_dhub, ctx->hshift, ctx->hbbase, ctx->bhub, ctx->bcount,
+                   ctx->bfill, ctx->boff, ctx->bvals, ctx->bmv, ctx->dedge_begin[kDHub], ctx->dacc};
 }
 
 template <class K>
@@ -806,16 +796,28 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
     }
     // the previous hub layout
     ctx_free(ctx, ctx->dchunks, sizeof(HubChunk) * ctx->n_dchunks, s);
-    ctx_free(ctx, ctx->dtoff, sizeof(int64_t) * ctx->n_dhub, s);
-    ctx_free(ctx, ctx->dtmask, sizeof(uint32_t) * ctx->n_dhub, s);
-    ctx_free(ctx, ctx->dtab, sizeof(unsigned long long) * ctx->dtab_words, s);
+    ctx_free(ctx, ctx->hshift, sizeof(int32_t) * ctx->n_dhub, s);
+    ctx_free(ctx, ctx->hbbase, sizeof(int64_t) * ctx->n_dhub, s);
+    ctx_free(ctx, ctx->bhub, sizeof(int32_t) * ctx->n_buckets, s);
+    ctx_free(ctx, ctx->bcount, sizeof(unsigned long long) * (ctx->n_buckets + 1), s);
+    ctx_free(ctx, ctx->bfill, sizeof(unsigned) * ctx->n_buckets, s);
+    ctx_free(ctx, ctx->boff, sizeof(int64_t) * (ctx->n_buckets + 1), s);
+    ctx_free(ctx, ctx->bvals, sizeof(unsigned long long) * ctx->hub_edges, s);
+    ctx_free(ctx, ctx->bmv, sizeof(unsigned long long) * ctx->hub_edges, s);
+    ctx_free(ctx, ctx->bscan, sizeof(int64_t) * ctx->bscan_words, s);
     ctx_free(ctx, ctx->dacc, sizeof(HubAcc) * ctx->n_dhub, s);
     ctx->dchunks = nullptr;
-    ctx->dtoff = nullptr;
-    ctx->dtmask = nullptr;
-    ctx->dtab = nullptr;
+    ctx->hshift = nullptr;
+    ctx->hbbase = nullptr;
+    ctx->bhub = nullptr;
+    ctx->bcount = nullptr;
+    ctx->bfill = nullptr;
+    ctx->boff = nullptr;
+    ctx->bvals = nullptr;
+    ctx->bmv = nullptr;
+    ctx->bscan = nullptr;
     ctx->dacc = nullptr;
-    ctx->n_dchunks = ctx->n_dhub = ctx->dtab_words = 0;
+    ctx->n_dchunks = ctx->n_dhub = ctx->n_buckets = ctx->hub_edges = ctx->bscan_words = 0;
 
     const size_t tmp_words = std::max(radix_temp_words(n), scan_temp_words(static_cast<int64_t>(n) + 1));
     const size_t bytes = (sizeof(uint32_t) * 2 + sizeof(uint64_t) * 2) * nv + sizeof(int64_t) * (nv + 1) +
@@ -894,39 +896,45 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
             return cuda_error(ctx, e, "read hub rows");
         }
         std::vector<HubChunk> chunks;
-        std::vector<int64_t> toff(nh);
-        std::vector<uint32_t> tmask(nh);
-        int64_t words = 0;
+        std::vector<int32_t> shift(nh), bhub;
+        std::vector<int64_t> bbase(nh);
         const int64_t csz = std::max(256, ctx->opt.hub_chunk);
         for (int64_t h = 0; h < nh; ++h) {
             const int64_t d = rows[h + 1] - rows[h];
-            uint64_t sz = 64;
-            while (sz < static_cast<uint64_t>(2 * d)) sz <<= 1;
-            toff[h] = words;
-            tmask[h] = static_cast<uint32_t>(sz - 1);
-            words += static_cast<int64_t>(sz);
+            int sh = 0;
+            while ((int64_t{1} << sh) * kHubBucketTarget < d && (1 << sh) < kHubMaxBuckets) ++sh;
+            shift[h] = sh;
+            bbase[h] = static_cast<int64_t>(bhub.size());
+            for (int b = 0; b < (1 << sh); ++b) bhub.push_back(static_cast<int32_t>(h));
             for (int64_t b = rows[h]; b < rows[h + 1]; b += csz)
                 chunks.push_back(HubChunk{static_cast<int32_t>(h), -1, b, std::min(rows[h + 1], b + csz)});
         }
+        const int64_t nbk = static_cast<int64_t>(bhub.size());
         ctx->n_dhub = nh;
         ctx->n_dchunks = static_cast<int64_t>(chunks.size());
-        ctx->dtab_words = words;
-        if (!chunks.empty() &&
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dchunks), sizeof(HubChunk) * chunks.size(), s))) {
-            cudaFreeAsync(base, s);
-            return cuda_error(ctx, e, "alloc hub chunks");
-        }
-        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dtoff), sizeof(int64_t) * nh, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dtmask), sizeof(uint32_t) * nh, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dtab), sizeof(unsigned long long) * words, s)) ||
+        ctx->n_buckets = nbk;
+        ctx->hub_edges = std::max<int64_t>(rows[nh] - rows[0], 1);
+        ctx->bscan_words = static_cast<int64_t>(scan_temp_words(nbk + 1));
+        if ((!chunks.empty() &&
+             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dchunks), sizeof(HubChunk) * chunks.size(), s))) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->hshift), sizeof(int32_t) * nh, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->hbbase), sizeof(int64_t) * nh, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bhub), sizeof(int32_t) * nbk, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bcount), sizeof(unsigned long long) * (nbk + 1), s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bfill), sizeof(unsigned) * nbk, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->boff), sizeof(int64_t) * (nbk + 1), s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bvals), sizeof(unsigned long long) * ctx->hub_edges, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bmv), sizeof(unsigned long long) * ctx->hub_edges, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bscan), sizeof(int64_t) * ctx->bscan_words, s)) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dacc), sizeof(HubAcc) * nh, s))) {
             cudaFreeAsync(base, s);
-            return cuda_error(ctx, e, "alloc hub sets");
+            return cuda_error(ctx, e, "alloc hub buckets");
         }
         if (!chunks.empty())
             cudaMemcpyAsync(ctx->dchunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(ctx->dtoff, toff.data(), sizeof(int64_t) * nh, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(ctx->dtmask, tmask.data(), sizeof(uint32_t) * nh, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(ctx->hshift, shift.data(), sizeof(int32_t) * nh, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(ctx->hbbase, bbase.data(), sizeof(int64_t) * nh, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(ctx->bhub, bhub.data(), sizeof(int32_t) * nbk, cudaMemcpyHostToDevice, s);
         if (!chunks.empty()) {
             // hub rows are copied chunk by chunk, like the rounds read them
             const int64_t edges = m - ctx->dedge_begin[kDHub];
@@ -963,10 +971,20 @@ bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     const DenseView D{ctx->dvert, ctx->dvpos, ctx->dprp, ctx->dpe, ctx->P[ctx->cur], ctx->dcnt, ctx->dhash, ctx->dslot};
     const HubSets H = hub_sets(ctx);
     TableRef t = next_epoch(ctx, s);
+    // table parts of at most kPartSlots slots (32 MB), each filled and read in its own pass
+    int pshift = 0;
+    while ((uint64_t{1} << pshift) < ctx->nslots) ++pshift;
+    int nparts = 1;
+    while (pshift > kPartShift) {
+        --pshift;
+        nparts <<= 1;
+    }
+    t.pmask = (uint64_t{1} << pshift) - 1;
     unsigned* err = &ctx->dstate->error;
     cudaMemsetAsync(ctx->dstate, 0, sizeof(DevState), s);
     if (ctx->n_dhub > 0) {
-        cudaMemsetAsync(ctx->dtab, 0, sizeof(unsigned long long) * ctx->dtab_words, s);
+        cudaMemsetAsync(ctx->bcount, 0, sizeof(unsigned long long) * (ctx->n_buckets + 1), s);   // + the scan's end
+        cudaMemsetAsync(ctx->bfill, 0, sizeof(unsigned) * ctx->n_buckets, s);
         cudaMemsetAsync(ctx->dacc, 0, sizeof(HubAcc) * ctx->n_dhub, s);
     }
     const int64_t* db = ctx->dbegin;
@@ -975,12 +993,13 @@ bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     BISIM_SITE(site_t8, "dense_thread_sig_8");
     BISIM_SITE(site_t16, "dense_thread_sig_16");
     BISIM_SITE(site_t32, "dense_thread_sig_32");
-    BISIM_SITE(site_g, "dense_group_sig");
     BISIM_SITE(site_w, "dense_warp_sig");
     static const int site_mid[5] = {prof_site("dense_mid_512"), prof_site("dense_mid_1024"),
                                     prof_site("dense_mid_2048"), prof_site("dense_mid_4096"),
                                     prof_site("dense_mid_8192")};
-    BISIM_SITE(site_hi, "dense_hub_insert");
+    BISIM_SITE(site_hc, "hub_count");
+    BISIM_SITE(site_hs, "hub_scatter");
+    BISIM_SITE(site_hd, "hub_dedup");
     BISIM_SITE(site_hf, "dense_hub_finalize");
     BISIM_SITE(site_in, "dense_insert");
     BISIM_SITE(site_v, "dense_verify");
@@ -1011,10 +1030,29 @@ bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     launch_mid<4096, 512>(ctx, kDMid0 + 3, D, s, site_mid[3]);
     launch_mid<8192, 512>(ctx, kDMid0 + 4, D, s, site_mid[4]);
     if (ctx->n_dhub > 0) {
+        static bool hub_attr = false;
+        if (!hub_attr) {
+            cudaFuncSetAttribute(k_hub_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kHubScatterSmem));
+            cudaFuncSetAttribute(k_hub_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kHubDedupSmem));
+            hub_attr = true;
+        }
+        const int64_t edges = class_edges(ctx, kDHub, kDHub + 1);
         if (ctx->n_dchunks > 0) {
-            const int64_t edges = class_edges(ctx, kDHub, kDHub + 1);
-            Launch L(site_hi, s, 0, edges, kEdgeBytes * edges);
-            k_dense_hub_insert<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, 0, s>>>(ctx->dchunks, D, H, err);
+            {
+                Launch L(site_hc, s, 0, edges, (kEdgeBytes + 8.0) * edges);
+                k_hub_count<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, 0, s>>>(ctx->dchunks, D, H);
+            }
+            exclusive_scan_i64(reinterpret_cast<const int64_t*>(ctx->bcount), ctx->boff, ctx->n_buckets + 1,
+                               ctx->bscan, s);
+            {
+                Launch L(site_hs, s, 0, edges, 16.0 * edges);
+                k_hub_scatter<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, kHubScatterSmem, s>>>(ctx->dchunks,
+                                                                                                     H);
+            }
+            Launch L(site_hd, s, 0, edges, 8.0 * edges);
+            k_hub_dedup<<<static_cast<unsigned>(ctx->n_buckets), kThreads, kHubDedupSmem, s>>>(H, err);
         }
         Launch L(site_hf, s, ctx->n_dhub, 0, kSigVertexBytes * ctx->n_dhub);
         k_dense_hub_finalize<<<grid_for(ctx->n_dhub, 128), 128, 0, s>>>(D, H);
@@ -1035,6 +1073,7 @@ bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
             return set_error(ctx, BISIM_ETIMEOUT, "hash collision resolution did not converge");
         if (level > 0) {
             t = next_epoch(ctx, s);
+            t.pmask = (uint64_t{1} << pshift) - 1;
             cudaMemsetAsync(&ctx->dstate->unresolved, 0, sizeof(unsigned), s);
             cudaMemsetAsync(&ctx->dstate->deferred, 0, sizeof(unsigned), s);
             cudaMemsetAsync(&ctx->dstate->pairs, 0, sizeof(unsigned), s);
@@ -1042,13 +1081,17 @@ bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
         int32_t* next = ctx->ulist[which];
         const VerifyOut O{Pout, ctx->dpairs, ctx->dsmall, next, ctx->dstate};
         if (count > 0) {
-            {
-                Launch L(site_in, s, count, 0, kInsertVertexBytes * count);
-                k_dense_insert<<<grid_for(count, kThreads * kPosUnroll), kThreads, 0, s>>>(list, count, D, level, t, err);
+            // level 0 runs part by part, so that each pass's table part stays in L2
+            const int parts = level == 0 ? nparts : 1;
+            for (int q = 0; q < parts; ++q) {
+                Launch L(site_in, s, count, 0, kInsertVertexBytes * count / parts);
+                k_dense_insert<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, level, t,
+                                                                             parts > 1 ? q : -1, pshift, err);
             }
-            {
-                Launch L(site_v, s, count, 0, kVerifyVertexBytes * count);
-                k_dense_verify<<<grid_for(count, kThreads * kPosUnroll), kThreads, 0, s>>>(list, count, D, ctx->table, O, n);
+            for (int q = 0; q < parts; ++q) {
+                Launch L(site_v, s, count, 0, kVerifyVertexBytes * count / parts);
+                k_dense_verify<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, ctx->table, O, n,
+                                                                             parts > 1 ? q : -1, pshift);
             }
             {
                 Launch L(site_cw, s, 0, 0, 0.0);

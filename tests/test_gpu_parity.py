@@ -141,6 +141,31 @@ def test_self_loops_duplicates_and_a_duplicate_heavy_hub(B):
     check(B, g, [1, 2, oracle.FIXPOINT])
 
 
+def test_equal_hubs_are_compared_exactly(B):
+    # hubs 0 and 1 have identical rows of 30k distinct pairs (their sets are
+    # compared in sub-ranges); hub 2 differs from them in one edge label; hub 3
+    # repeats hub 0's row twice (a different degree, the same set)
+    n = 40_000
+    targets = np.arange(4, 30_004, dtype=np.int32)
+    labels = np.arange(len(targets), dtype=np.int32)          # 30k distinct pairs per row
+    lab2 = labels.copy()
+    lab2[12_345] = 1_000_000
+    src = np.concatenate([np.zeros_like(targets), np.ones_like(targets), np.full_like(targets, 2),
+                          np.full(2 * len(targets), 3, np.int32)])
+    dst = np.concatenate([targets, targets, targets, targets, targets])
+    lab = np.concatenate([labels, labels, lab2, labels, labels])
+    rng = np.random.default_rng(3)
+    extra_s = rng.integers(4, n, 50_000).astype(np.int32)
+    extra_d = rng.integers(0, n, 50_000).astype(np.int32)
+    g = dict(n=n, src=np.concatenate([src, extra_s]), dst=np.concatenate([dst, extra_d]),
+             elabel=np.concatenate([lab, rng.integers(0, 3, 50_000).astype(np.int32)]),
+             vlabel=np.zeros(n, np.int32))
+    for opts in (None, B.default_options(mid_max_degree=256, hub_chunk=256)):
+        check(B, g, [1, 2, oracle.FIXPOINT], options=opts)
+    P, _, _, _ = gpu_partition(B, g, 2)
+    assert P[1] == 0 and P[3] == 0 and P[2] == 2
+
+
 def test_dead_vertices(B):
     g = graphgen.uniform_graph(n=2000, m=8000, seed=8)
     alive = np.ones(g["n"], np.uint8)
