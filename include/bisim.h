@@ -68,6 +68,13 @@ enum { BISIM_FLAG_L2_PIN = 1 };
  * partition incrementally (same result; the reference point for latency). */
 enum { BISIM_FLAG_FULL_RECOMPUTE = 2 };
 
+/* BISIM_FLAG_EAGER: run the rounds of bisim_iterate as host-driven launch
+ * sequences, one round at a time. By default the round loop is one captured
+ * CUDA graph whose while node repeats a round until the block count stops
+ * changing or the round limit is reached, decided on the device; rounds also
+ * run eagerly while launch profiling (bisim_profile_enable) is on. */
+enum { BISIM_FLAG_EAGER = 4 };
+
 /* Update operations (Section 3.2, incremental summarization of evolving graphs:
  * additions, deletions and modifications of vertices and edges). */
 enum {

@@ -60,6 +60,7 @@ void free_temps(std::vector<void*>& temps, cudaStream_t s) {
 
 void destroy_ctx(bisim_ctx* ctx) {
     if (ctx == nullptr) return;
+    dense_release(ctx);
     for (void* p : ctx->allocs) cudaFreeAsync(p, 0);
     if (ctx->dstate) cudaFreeAsync(ctx->dstate, 0);
     if (ctx->hstate) cudaFreeHost(ctx->hstate);
@@ -214,7 +215,7 @@ bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s) {
 // with at most `cap` rounds. Equal block counts in two consecutive rounds prove
 // the fixpoint, since every round refines the previous partition.
 bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
-                        int32_t* out_executed, int64_t* out_blocks) {
+                        int32_t* out_executed, int64_t* out_blocks, bool allow_graph) {
     cudaError_t e;
     bisim_status pst = dense_prepare(ctx, s);
     if (pst != BISIM_OK) return pst;
@@ -224,9 +225,32 @@ bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, 
     dense_mark_dead(ctx, s);
     ctx->cur = 0;
     int64_t prev = ctx->last_blocks;   // |P_0|
-    const int32_t limit = (k == BISIM_FIXPOINT) ? cap : k;
+    const bool fixpoint = k == BISIM_FIXPOINT;
+    const int32_t limit = fixpoint ? cap : k;
     int32_t rounds = limit, executed = 0;
-    for (int32_t i = 0; i < limit; ++i) {
+    bool done = limit <= 0;
+    if (!done && allow_graph && dense_graph_usable(ctx)) {
+        // the round loop on the device: one graph launch
+        GraphRounds g{};
+        bisim_status st = dense_graph_rounds(ctx, s, limit, fixpoint, prev, &g);
+        if (st != BISIM_OK) return st;
+        executed = g.executed;
+        if (g.stop == 1) {
+            rounds = g.rounds;
+            prev = g.blocks;
+            done = true;
+        } else {
+            // the last round met a hash collision (or an error): finish it here
+            int64_t blocks = 0;
+            if ((st = dense_finish_round(ctx, s, &blocks)) != BISIM_OK) return st;
+            if (blocks == prev) {
+                rounds = fixpoint ? executed - 1 : k;
+                done = true;
+            }
+            prev = blocks;
+        }
+    }
+    for (int32_t i = executed; !done && i < limit; ++i) {
         int64_t blocks = 0;
         pin_partition_in_l2(ctx, ctx->P[ctx->cur], s);
         bisim_status st = dense_round(ctx, s, &blocks);
@@ -236,7 +260,7 @@ bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, 
         }
         ++executed;
         if (blocks == prev) {   // P_{i+1} refines P_i with as many blocks: P_{i+1} = P_i
-            rounds = (k == BISIM_FIXPOINT) ? i : k;
+            rounds = fixpoint ? i : k;
             break;
         }
         prev = blocks;
@@ -464,7 +488,8 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
     if ((st = refresh_after_edit(ctx, s)) != BISIM_OK) return st;
     int32_t rounds = 0, executed = 0;
     int64_t blocks = 0;
-    if ((st = run_rounds(ctx, ctx->opt.k_incremental, 0, s, &rounds, &executed, &blocks)) != BISIM_OK) return st;
+    if ((st = run_rounds(ctx, ctx->opt.k_incremental, 0, s, &rounds, &executed, &blocks, false)) != BISIM_OK)
+        return st;
     ctx->stats.last_frontier = ctx->n;
     return BISIM_OK;
 }

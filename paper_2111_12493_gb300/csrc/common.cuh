@@ -314,6 +314,11 @@ struct bisim_ctx {
     int64_t hub_edges = 0;
     int64_t bscan_words = 0;
     bisim::HubAcc* dacc = nullptr;
+    void* round_graph = nullptr;                     // cudaGraphExec_t of the device-side round loop
+    void* capture_stream = nullptr;                  // cudaStream_t used only to capture it
+    void* dloop = nullptr;                           // loop state on the device
+    void* hloop = nullptr;                           // its pinned host mirror
+    int64_t round_graph_launches = 0;                // kernels in one captured round
 
     // collision resolution
     int32_t* ulist[2] = {nullptr, nullptr};
@@ -414,8 +419,10 @@ bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
 
 // ----------------------------------------------------------------------------- rounds (api.cu)
 
+// allow_graph: the loop may run as the captured graph (callers that rebuild the
+// layout for every call, like the full recompute of an update batch, pass false).
 bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
-                        int32_t* out_executed, int64_t* out_blocks);
+                        int32_t* out_executed, int64_t* out_blocks, bool allow_graph = true);
 bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- dense rounds (dense.cu)
@@ -426,6 +433,22 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s);
 void dense_mark_dead(bisim_ctx* ctx, cudaStream_t s);
 // One refinement round P[cur] -> P[cur ^ 1] over every live vertex.
 bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks);
+// Finishes a round stopped by the device-side loop at a hash collision.
+bisim_status dense_finish_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks);
+struct GraphRounds {
+    int32_t executed;     // rounds run on the device
+    int32_t rounds;       // r when stop == 1
+    int64_t blocks;       // block count after the last round
+    int32_t stop;         // 1 done, 2 the last round needs its collision levels, 3 device error
+};
+// Whether the rounds may run as the captured device-side loop.
+bool dense_graph_usable(const bisim_ctx* ctx);
+// Runs up to `limit` rounds from P[0] as one graph launch (the loop checks the
+// block count on the device); the result is in P[0] unless stop == 2.
+bisim_status dense_graph_rounds(bisim_ctx* ctx, cudaStream_t s, int32_t limit, bool fixpoint, int64_t prev_blocks,
+                                GraphRounds* out);
+// Releases the graph, its capture stream and pinned mirror.
+void dense_release(bisim_ctx* ctx);
 
 // ----------------------------------------------------------------------------- incremental levels (inc.cu)
 

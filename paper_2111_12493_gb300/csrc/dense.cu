@@ -25,6 +25,7 @@
 // with the exact partition.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -40,7 +41,6 @@ unsigned grid_for(int64_t n, int threads) {
 }
 
 constexpr int kMaxLevels = 1 << 16;
-constexpr int kPartShift = 40;                  // signature table parts (2^40 slots: one part; splitting into L2-sized parts did not pay)
 constexpr int kThreads = 256;
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
@@ -528,18 +528,14 @@ __global__ void k_dense_hub_finalize(const DenseView D, const HubSets H) {
 
 
 // Table insert of every listed position (level 0: all live positions, list ==
-// null) with the level's salted hash. The table is split into parts small
-// enough for L2 (a position's part is given by its slot index); pass `part`
-// inserts only the positions of that part (part < 0: all).
+// null) with the level's salted hash.
 __global__ void __launch_bounds__(kThreads) k_dense_insert(const int32_t* __restrict__ list, int64_t count,
                                                            const DenseView D, uint32_t level, const TableRef t,
-                                                           int part, int pshift, unsigned* err) {
+                                                           unsigned* err) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const int64_t pos = list ? list[i] : i;
-    const uint64_t h = level_hash(D.hash[pos], level, t.hmask);
-    if (part >= 0 && static_cast<int>((h & t.mask) >> pshift) != part) return;
-    D.slot[pos] = table_insert(t, h, D.vert[pos], err);
+    D.slot[pos] = table_insert(t, level_hash(D.hash[pos], level, t.hmask), D.vert[pos], err);
 }
 
 struct VerifyOut {
@@ -554,21 +550,13 @@ struct VerifyOut {
 // smallest vertex). r itself: a block id. Different own block or set size: the
 // position moves to the next level. Otherwise the sets are compared: here when
 // both rows have at most two edges, else in a warp (rows <= 32) or a CTA.
-// Pass `part` takes the positions whose slot lies in that part of the table
-// (failed inserts in part 0; part < 0: all).
 __global__ void __launch_bounds__(kThreads) k_dense_verify(const int32_t* __restrict__ list, int64_t count,
                                                            const DenseView D, const Slot* __restrict__ slots,
-                                                           const VerifyOut O, int32_t n_total, int part,
-                                                           int pshift) {
+                                                           const VerifyOut O, int32_t n_total) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     bool own = false, push = false, small = false, big = false;
     int64_t pos = -1, rpos = -1;
-    if (i < count) {
-        pos = list ? list[i] : i;
-        const uint32_t sv = D.slot[pos];
-        const int my_part = sv == ~0u ? 0 : static_cast<int>(sv >> pshift);
-        if (part >= 0 && my_part != part) pos = -1;
-    }
+    if (i < count) pos = list ? list[i] : i;
     if (pos >= 0) {
         const int32_t v = D.vert[pos];
         const uint32_t sv = D.slot[pos];
@@ -714,6 +702,51 @@ __global__ void __launch_bounds__(kThreads) k_dense_compare_cta(const int2* __re
     }
 }
 
+// ----------------------------------------------------------------------------- device-side round loop
+
+// State of the round loop run by the captured graph (device memory).
+struct LoopState {
+    unsigned long long prev_blocks;   // block count of the partition the next round refines
+    unsigned long long blocks;        // block count after the last round
+    int32_t executed;                 // rounds run
+    int32_t limit;                    // rounds allowed
+    int32_t fixpoint;                 // 1: stop as soon as a round keeps the block count
+    int32_t rounds;                   // the result r (k, or the fixpoint round)
+    int32_t stop;                     // 0 go on, 1 done, 2 a hash collision to resolve on the host, 3 error
+    int32_t pad;
+};
+
+// After a round: decide whether the loop goes on (the while condition of the graph).
+__global__ void k_round_check(const DevState* __restrict__ st, LoopState* L, cudaGraphConditionalHandle cond) {
+    const unsigned long long blocks = st->blocks;
+    const int32_t executed = L->executed + 1;
+    int32_t stop = 0;
+    if (st->error != 0u) {
+        stop = 3;
+    } else if (st->unresolved != 0u) {
+        stop = 2;                     // the host finishes this round's collision levels
+    } else if (blocks == L->prev_blocks) {
+        stop = 1;                     // P_{i+1} refines P_i with as many blocks: the fixpoint
+        L->rounds = L->fixpoint ? executed - 1 : L->limit;
+    } else if (executed >= L->limit) {
+        stop = 1;
+        L->rounds = L->limit;
+    }
+    if (stop < 2) L->prev_blocks = blocks;
+    L->blocks = blocks;
+    L->executed = executed;
+    L->stop = stop;
+    cudaGraphSetConditional(cond, stop == 0 ? 1u : 0u);
+}
+
+// P_{i+1} becomes the input of the next round, unless the host has to finish this one.
+__global__ void k_round_copy(const int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t n,
+                             const LoopState* __restrict__ L) {
+    if (L->stop >= 2) return;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+}
+
 // ----------------------------------------------------------------------------- host helpers
 
 WarpPlan warp_plan(const bisim_ctx* ctx) {
@@ -758,20 +791,167 @@ void launch_mid(bisim_ctx* ctx, int cls, const DenseView& D, cudaStream_t s, int
     const int64_t count = ctx->dbegin[cls + 1] - first;
     if (count <= 0) return;
     const size_t smem = sizeof(unsigned long long) * 2 * N;
-    static bool attr = false;
-    if (!attr) {
-        allow_smem(k_dense_mid_sig<N, T>, smem);
-        attr = true;
-    }
     const int64_t edges = class_edges(ctx, cls, cls + 1);
     Launch L(site, s, count, edges, kSigVertexBytes * count + kEdgeBytes * edges);
     k_dense_mid_sig<N, T><<<static_cast<unsigned>(count), T, smem, s>>>(first, D);
+}
+
+// Kernel attributes (shared memory above 48 KB), set once before any launch or capture.
+void set_attributes() {
+    static std::once_flag once;
+    std::call_once(once, []() {
+        allow_smem(k_dense_mid_sig<512, 256>, sizeof(unsigned long long) * 2 * 512);
+        allow_smem(k_dense_mid_sig<1024, 256>, sizeof(unsigned long long) * 2 * 1024);
+        allow_smem(k_dense_mid_sig<2048, 512>, sizeof(unsigned long long) * 2 * 2048);
+        allow_smem(k_dense_mid_sig<4096, 512>, sizeof(unsigned long long) * 2 * 4096);
+        allow_smem(k_dense_mid_sig<8192, 512>, sizeof(unsigned long long) * 2 * 8192);
+        cudaFuncSetAttribute(k_hub_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kHubScatterSmem));
+        cudaFuncSetAttribute(k_hub_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kHubDedupSmem));
+        allow_smem(k_dense_compare_cta, kCompareSmem);
+    });
+}
+
+// Insert, verification and set comparisons of one level (level 0: every live
+// position; then the listed ones). Unresolved positions go to `next`.
+void launch_level(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const TableRef& t, uint32_t level,
+                  const int32_t* list, int64_t count, int32_t* next) {
+    BISIM_SITE(site_in, "dense_insert");
+    BISIM_SITE(site_v, "dense_verify");
+    BISIM_SITE(site_cw, "dense_compare_warp");
+    BISIM_SITE(site_cc, "dense_compare_cta");
+    if (count <= 0) return;
+    int32_t* Pout = ctx->P[ctx->cur ^ 1];
+    const VerifyOut O{Pout, ctx->dpairs, ctx->dsmall, next, ctx->dstate};
+    const HubSets H = hub_sets(ctx);
+    {
+        Launch L(site_in, s, count, 0, kInsertVertexBytes * count);
+        k_dense_insert<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, level, t, &ctx->dstate->error);
+    }
+    {
+        Launch L(site_v, s, count, 0, kVerifyVertexBytes * count);
+        k_dense_verify<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, ctx->table, O, ctx->n);
+    }
+    {
+        Launch L(site_cw, s, 0, 0, 0.0);
+        k_dense_compare_warp<<<kCompareGrid, kThreads, 0, s>>>(ctx->dsmall, D, Pout, next, ctx->dstate);
+    }
+    Launch L(site_cc, s, 0, 0, 0.0);
+    k_dense_compare_cta<<<kCompareGrid, kThreads, kCompareSmem, s>>>(ctx->dpairs, D, H, Pout, next, ctx->dstate);
+}
+
+DenseView dense_view(bisim_ctx* ctx) {
+    return DenseView{ctx->dvert, ctx->dvpos, ctx->dprp, ctx->dpe, ctx->P[ctx->cur], ctx->dcnt, ctx->dhash, ctx->dslot};
+}
+
+// Everything of one round P[cur] -> P[cur ^ 1] that needs no host decision:
+// signatures of every class, then level 0 of the renumbering.
+void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t) {
+    const DenseView D = dense_view(ctx);
+    const HubSets H = hub_sets(ctx);
+    unsigned* err = &ctx->dstate->error;
+    cudaMemsetAsync(ctx->dstate, 0, sizeof(DevState), s);
+    if (ctx->n_dhub > 0) {
+        cudaMemsetAsync(ctx->bcount, 0, sizeof(unsigned long long) * (ctx->n_buckets + 1), s);   // + the scan's end
+        cudaMemsetAsync(ctx->bfill, 0, sizeof(unsigned) * ctx->n_buckets, s);
+        cudaMemsetAsync(ctx->dacc, 0, sizeof(HubAcc) * ctx->n_dhub, s);
+    }
+    const int64_t* db = ctx->dbegin;
+    BISIM_SITE(site_t8, "dense_thread_sig_8");
+    BISIM_SITE(site_t16, "dense_thread_sig_16");
+    BISIM_SITE(site_t32, "dense_thread_sig_32");
+    BISIM_SITE(site_w, "dense_warp_sig");
+    static const int site_mid[5] = {prof_site("dense_mid_512"), prof_site("dense_mid_1024"),
+                                    prof_site("dense_mid_2048"), prof_site("dense_mid_4096"),
+                                    prof_site("dense_mid_8192")};
+    BISIM_SITE(site_hc, "hub_count");
+    BISIM_SITE(site_hs, "hub_scatter");
+    BISIM_SITE(site_hd, "hub_dedup");
+    BISIM_SITE(site_hf, "dense_hub_finalize");
+    // classes 0..4 (degree <= 8), 5 (<= 16) and 6 (<= 32): one thread per vertex
+    auto thread_sig = [&](int c0, int c1, auto kernel, int site) {
+        const int64_t verts = db[c1] - db[c0];
+        if (verts <= 0) return;
+        const int64_t edges = class_edges(ctx, c0, c1);
+        Launch L(site, s, verts, edges, kSigVertexBytes * verts + kEdgeBytes * edges);
+        kernel<<<grid_for(verts, kThreads), kThreads, 0, s>>>(db[c0], verts, D);
+    };
+    thread_sig(0, 5, k_dense_thread_sig<8>, site_t8);
+    thread_sig(5, 6, k_dense_thread_sig<16>, site_t16);
+    thread_sig(6, 7, k_dense_thread_sig<32>, site_t32);
+    if (db[kDMid0] > db[kDWarp0]) {
+        const WarpPlan wp = warp_plan(ctx);
+        const int64_t verts = db[kDMid0] - db[kDWarp0];
+        const int64_t edges = class_edges(ctx, kDWarp0, kDMid0);
+        Launch L(site_w, s, verts, edges, kSigVertexBytes * verts + kEdgeBytes * edges);
+        k_dense_warp_sig<<<static_cast<unsigned>(wp.cta_begin[3]), kThreads, 0, s>>>(wp, D);
+    }
+    launch_mid<512, 256>(ctx, kDMid0 + 0, D, s, site_mid[0]);
+    launch_mid<1024, 256>(ctx, kDMid0 + 1, D, s, site_mid[1]);
+    launch_mid<2048, 512>(ctx, kDMid0 + 2, D, s, site_mid[2]);
+    launch_mid<4096, 512>(ctx, kDMid0 + 3, D, s, site_mid[3]);
+    launch_mid<8192, 512>(ctx, kDMid0 + 4, D, s, site_mid[4]);
+    if (ctx->n_dhub > 0) {
+        const int64_t edges = class_edges(ctx, kDHub, kDHub + 1);
+        if (ctx->n_dchunks > 0) {
+            {
+                Launch L(site_hc, s, 0, edges, (kEdgeBytes + 8.0) * edges);
+                k_hub_count<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, 0, s>>>(ctx->dchunks, D, H);
+            }
+            exclusive_scan_i64(reinterpret_cast<const int64_t*>(ctx->bcount), ctx->boff, ctx->n_buckets + 1,
+                               ctx->bscan, s);
+            {
+                Launch L(site_hs, s, 0, edges, 16.0 * edges);
+                k_hub_scatter<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, kHubScatterSmem, s>>>(ctx->dchunks,
+                                                                                                     H);
+            }
+            Launch L(site_hd, s, 0, edges, 8.0 * edges);
+            k_hub_dedup<<<static_cast<unsigned>(ctx->n_buckets), kThreads, kHubDedupSmem, s>>>(H, err);
+        }
+        Launch L(site_hf, s, ctx->n_dhub, 0, kSigVertexBytes * ctx->n_dhub);
+        k_dense_hub_finalize<<<grid_for(ctx->n_dhub, 128), 128, 0, s>>>(D, H);
+    }
+    launch_level(ctx, s, D, t, 0, nullptr, ctx->dbegin[kDClasses], ctx->ulist[0]);
+}
+
+// Reads the state of a round whose level 0 has been launched, runs the
+// collision levels that are needed, and moves the current partition on.
+bisim_status finish_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
+    cudaError_t e;
+    const DenseView D = dense_view(ctx);
+    int which = 0;                    // level 0 pushed its unresolved positions to ulist[0]
+    for (uint32_t level = 1;; ++level) {
+        cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, level > 1 ? "resolve hash collisions" : "dense round");
+        if (ctx->hstate->error != 0 || ctx->hstate->unresolved == 0) break;
+        if (level > static_cast<uint32_t>(kMaxLevels))
+            return set_error(ctx, BISIM_ETIMEOUT, "hash collision resolution did not converge");
+        const int64_t count = ctx->hstate->unresolved;
+        TableRef t = next_epoch(ctx, s);
+        cudaMemsetAsync(&ctx->dstate->unresolved, 0, sizeof(unsigned), s);
+        cudaMemsetAsync(&ctx->dstate->deferred, 0, sizeof(unsigned), s);
+        cudaMemsetAsync(&ctx->dstate->pairs, 0, sizeof(unsigned), s);
+        launch_level(ctx, s, D, t, level, ctx->ulist[which], count, ctx->ulist[which ^ 1]);
+        which ^= 1;
+        ctx->stats.collision_levels += 1;
+    }
+    if (ctx->hstate->error & kErrTableFull) return set_error(ctx, BISIM_ETIMEOUT, "signature table probe limit reached");
+    if (ctx->hstate->error & kErrHubFull) return set_error(ctx, BISIM_ETIMEOUT, "hub set probe limit reached");
+    if (ctx->hstate->error) return set_error(ctx, BISIM_EINVAL, "device reported invalid input");
+    *out_blocks = static_cast<int64_t>(ctx->hstate->blocks);
+    ctx->cur ^= 1;
+    return BISIM_OK;
 }
 
 }  // namespace
 
 bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
     if (ctx->dense_ready) return BISIM_OK;
+    if (ctx->round_graph) {                    // captured for the previous layout
+        cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->round_graph));
+        ctx->round_graph = nullptr;
+    }
     const int32_t n = ctx->n;
     const int64_t m = ctx->m;
     const size_t nv = static_cast<size_t>(std::max(n, 1));
@@ -965,158 +1145,142 @@ void dense_mark_dead(bisim_ctx* ctx, cudaStream_t s) {
 }
 
 bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
-    const int32_t n = ctx->n;
-    int32_t* Pout = ctx->P[ctx->cur ^ 1];
-    cudaError_t e;
-    const DenseView D{ctx->dvert, ctx->dvpos, ctx->dprp, ctx->dpe, ctx->P[ctx->cur], ctx->dcnt, ctx->dhash, ctx->dslot};
-    const HubSets H = hub_sets(ctx);
-    TableRef t = next_epoch(ctx, s);
-    // table parts of at most kPartSlots slots (32 MB), each filled and read in its own pass
-    int pshift = 0;
-    while ((uint64_t{1} << pshift) < ctx->nslots) ++pshift;
-    int nparts = 1;
-    while (pshift > kPartShift) {
-        --pshift;
-        nparts <<= 1;
-    }
-    t.pmask = (uint64_t{1} << pshift) - 1;
-    unsigned* err = &ctx->dstate->error;
-    cudaMemsetAsync(ctx->dstate, 0, sizeof(DevState), s);
-    if (ctx->n_dhub > 0) {
-        cudaMemsetAsync(ctx->bcount, 0, sizeof(unsigned long long) * (ctx->n_buckets + 1), s);   // + the scan's end
-        cudaMemsetAsync(ctx->bfill, 0, sizeof(unsigned) * ctx->n_buckets, s);
-        cudaMemsetAsync(ctx->dacc, 0, sizeof(HubAcc) * ctx->n_dhub, s);
-    }
-    const int64_t* db = ctx->dbegin;
-    const int64_t n_live = db[kDClasses];
+    set_attributes();
+    const TableRef t = next_epoch(ctx, s);
+    launch_round(ctx, s, t);
+    return finish_round(ctx, s, out_blocks);
+}
 
-    BISIM_SITE(site_t8, "dense_thread_sig_8");
-    BISIM_SITE(site_t16, "dense_thread_sig_16");
-    BISIM_SITE(site_t32, "dense_thread_sig_32");
-    BISIM_SITE(site_w, "dense_warp_sig");
-    static const int site_mid[5] = {prof_site("dense_mid_512"), prof_site("dense_mid_1024"),
-                                    prof_site("dense_mid_2048"), prof_site("dense_mid_4096"),
-                                    prof_site("dense_mid_8192")};
-    BISIM_SITE(site_hc, "hub_count");
-    BISIM_SITE(site_hs, "hub_scatter");
-    BISIM_SITE(site_hd, "hub_dedup");
-    BISIM_SITE(site_hf, "dense_hub_finalize");
-    BISIM_SITE(site_in, "dense_insert");
-    BISIM_SITE(site_v, "dense_verify");
-    BISIM_SITE(site_cw, "dense_compare_warp");
-    BISIM_SITE(site_cc, "dense_compare_cta");
-    // 1. signatures (hash and set size per position)
-    // classes 0..4 (degree <= 8), 5 (<= 16) and 6 (<= 32): one thread per vertex
-    auto thread_sig = [&](int c0, int c1, auto kernel, int site) {
-        const int64_t verts = db[c1] - db[c0];
-        if (verts <= 0) return;
-        const int64_t edges = class_edges(ctx, c0, c1);
-        Launch L(site, s, verts, edges, kSigVertexBytes * verts + kEdgeBytes * edges);
-        kernel<<<grid_for(verts, kThreads), kThreads, 0, s>>>(db[c0], verts, D);
-    };
-    thread_sig(0, 5, k_dense_thread_sig<8>, site_t8);
-    thread_sig(5, 6, k_dense_thread_sig<16>, site_t16);
-    thread_sig(6, 7, k_dense_thread_sig<32>, site_t32);
-    if (db[kDMid0] > db[kDWarp0]) {
-        const WarpPlan wp = warp_plan(ctx);
-        const int64_t verts = db[kDMid0] - db[kDWarp0];
-        const int64_t edges = class_edges(ctx, kDWarp0, kDMid0);
-        Launch L(site_w, s, verts, edges, kSigVertexBytes * verts + kEdgeBytes * edges);
-        k_dense_warp_sig<<<static_cast<unsigned>(wp.cta_begin[3]), kThreads, 0, s>>>(wp, D);
+bisim_status dense_finish_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
+    return finish_round(ctx, s, out_blocks);
+}
+
+namespace {
+
+// The captured rounds clear the table at the start of every round and use one
+// fixed epoch; the eager rounds' epochs (next_epoch) never reuse it without a clear.
+TableRef fixed_table(const bisim_ctx* ctx) {
+    TableRef t;
+    t.slots = ctx->table;
+    t.mask = ctx->nslots - 1;
+    t.epoch = uint64_t{1} << 32;
+    const int hb = ctx->opt.hash_bits;
+    t.hmask = hb >= 64 ? ~0ull : ((1ull << hb) - 1ull);
+    t.pmask = t.mask;
+    return t;
+}
+
+// The round loop as one graph: a while node whose body is one round (table
+// clear, signatures, level 0 of the renumbering), the loop check and the copy
+// of P_{i+1} into the input buffer. The body reads P[0] and writes P[1].
+bisim_status build_round_graph(bisim_ctx* ctx) {
+    set_attributes();
+    cudaError_t e;
+    if (ctx->capture_stream == nullptr &&
+        (e = cudaStreamCreateWithFlags(reinterpret_cast<cudaStream_t*>(&ctx->capture_stream), cudaStreamNonBlocking)))
+        return cuda_error(ctx, e, "create capture stream");
+    if (ctx->dloop == nullptr) {
+        if ((e = ctx_alloc(ctx, &ctx->dloop, sizeof(LoopState), nullptr))) return cuda_error(ctx, e, "alloc loop state");
+        if ((e = cudaMallocHost(&ctx->hloop, sizeof(LoopState)))) return cuda_error(ctx, e, "alloc loop state mirror");
     }
-    launch_mid<512, 256>(ctx, kDMid0 + 0, D, s, site_mid[0]);
-    launch_mid<1024, 256>(ctx, kDMid0 + 1, D, s, site_mid[1]);
-    launch_mid<2048, 512>(ctx, kDMid0 + 2, D, s, site_mid[2]);
-    launch_mid<4096, 512>(ctx, kDMid0 + 3, D, s, site_mid[3]);
-    launch_mid<8192, 512>(ctx, kDMid0 + 4, D, s, site_mid[4]);
-    if (ctx->n_dhub > 0) {
-        static bool hub_attr = false;
-        if (!hub_attr) {
-            cudaFuncSetAttribute(k_hub_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(kHubScatterSmem));
-            cudaFuncSetAttribute(k_hub_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(kHubDedupSmem));
-            hub_attr = true;
-        }
-        const int64_t edges = class_edges(ctx, kDHub, kDHub + 1);
-        if (ctx->n_dchunks > 0) {
-            {
-                Launch L(site_hc, s, 0, edges, (kEdgeBytes + 8.0) * edges);
-                k_hub_count<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, 0, s>>>(ctx->dchunks, D, H);
-            }
-            exclusive_scan_i64(reinterpret_cast<const int64_t*>(ctx->bcount), ctx->boff, ctx->n_buckets + 1,
-                               ctx->bscan, s);
-            {
-                Launch L(site_hs, s, 0, edges, 16.0 * edges);
-                k_hub_scatter<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, kHubScatterSmem, s>>>(ctx->dchunks,
-                                                                                                     H);
-            }
-            Launch L(site_hd, s, 0, edges, 8.0 * edges);
-            k_hub_dedup<<<static_cast<unsigned>(ctx->n_buckets), kThreads, kHubDedupSmem, s>>>(H, err);
-        }
-        Launch L(site_hf, s, ctx->n_dhub, 0, kSigVertexBytes * ctx->n_dhub);
-        k_dense_hub_finalize<<<grid_for(ctx->n_dhub, 128), 128, 0, s>>>(D, H);
+    cudaStream_t cs = static_cast<cudaStream_t>(ctx->capture_stream);
+    cudaGraph_t g = nullptr;
+    if ((e = cudaGraphCreate(&g, 0))) return cuda_error(ctx, e, "create round graph");
+    cudaGraphConditionalHandle cond;
+    // the node parameters are a union without a default constructor: zeroed storage
+    alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
+    std::memset(pbuf, 0, sizeof(pbuf));
+    cudaGraphNodeParams& p = *reinterpret_cast<cudaGraphNodeParams*>(pbuf);
+    cudaGraphNode_t node;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault))) {
+        cudaGraphDestroy(g);
+        return cuda_error(ctx, e, "create loop condition");
     }
-    static bool attr = false;
-    if (!attr) {
-        allow_smem(k_dense_compare_cta, kCompareSmem);
-        attr = true;
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = cond;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p))) {
+        cudaGraphDestroy(g);
+        return cuda_error(ctx, e, "add loop node");
     }
-    // 2. renumbering: table insert, verification, set comparisons; then the
-    // collision levels, which only the positions that differ from their
-    // representative's signature enter
-    int which = 0;
-    const int32_t* list = nullptr;
-    int64_t count = n_live;
-    for (uint32_t level = 0;; ++level) {
-        if (level > static_cast<uint32_t>(kMaxLevels))
-            return set_error(ctx, BISIM_ETIMEOUT, "hash collision resolution did not converge");
-        if (level > 0) {
-            t = next_epoch(ctx, s);
-            t.pmask = (uint64_t{1} << pshift) - 1;
-            cudaMemsetAsync(&ctx->dstate->unresolved, 0, sizeof(unsigned), s);
-            cudaMemsetAsync(&ctx->dstate->deferred, 0, sizeof(unsigned), s);
-            cudaMemsetAsync(&ctx->dstate->pairs, 0, sizeof(unsigned), s);
-        }
-        int32_t* next = ctx->ulist[which];
-        const VerifyOut O{Pout, ctx->dpairs, ctx->dsmall, next, ctx->dstate};
-        if (count > 0) {
-            // level 0 runs part by part, so that each pass's table part stays in L2
-            const int parts = level == 0 ? nparts : 1;
-            for (int q = 0; q < parts; ++q) {
-                Launch L(site_in, s, count, 0, kInsertVertexBytes * count / parts);
-                k_dense_insert<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, level, t,
-                                                                             parts > 1 ? q : -1, pshift, err);
-            }
-            for (int q = 0; q < parts; ++q) {
-                Launch L(site_v, s, count, 0, kVerifyVertexBytes * count / parts);
-                k_dense_verify<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, ctx->table, O, n,
-                                                                             parts > 1 ? q : -1, pshift);
-            }
-            {
-                Launch L(site_cw, s, 0, 0, 0.0);
-                k_dense_compare_warp<<<kCompareGrid, kThreads, 0, s>>>(ctx->dsmall, D, Pout, next, ctx->dstate);
-            }
-            {
-                Launch L(site_cc, s, 0, 0, 0.0);
-                k_dense_compare_cta<<<kCompareGrid, kThreads, kCompareSmem, s>>>(ctx->dpairs, D, H, Pout, next,
-                                                                                ctx->dstate);
-            }
-        }
-        cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
-        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, level ? "resolve hash collisions" : "dense round");
-        if (ctx->hstate->error != 0 || ctx->hstate->unresolved == 0) break;
-        list = next;
-        count = ctx->hstate->unresolved;
-        which ^= 1;
-        ctx->stats.collision_levels += 1;
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    const int cur = ctx->cur;
+    ctx->cur = 0;
+    const int64_t before = bisim_launch_count();
+    BISIM_SITE(site_ck, "round_check");
+    BISIM_SITE(site_cp, "round_copy");
+    if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal))) {
+        ctx->cur = cur;
+        cudaGraphDestroy(g);
+        return cuda_error(ctx, e, "capture round");
     }
-    if (ctx->hstate->error & kErrTableFull) return set_error(ctx, BISIM_ETIMEOUT, "signature table probe limit reached");
-    if (ctx->hstate->error & kErrHubFull) return set_error(ctx, BISIM_ETIMEOUT, "hub set probe limit reached");
-    if (ctx->hstate->error) return set_error(ctx, BISIM_EINVAL, "device reported invalid input");
-    *out_blocks = static_cast<int64_t>(ctx->hstate->blocks);
-    ctx->cur ^= 1;
+    cudaMemsetAsync(ctx->table, 0, sizeof(Slot) * ctx->nslots, cs);
+    launch_round(ctx, cs, fixed_table(ctx));
+    LoopState* L = static_cast<LoopState*>(ctx->dloop);
+    {
+        Launch Lk(site_ck, cs, 0, 0, 0.0);
+        k_round_check<<<1, 1, 0, cs>>>(ctx->dstate, L, cond);
+    }
+    {
+        Launch Lk(site_cp, cs, ctx->n, 0, 8.0 * ctx->n);
+        k_round_copy<<<grid_for(std::min<int64_t>(ctx->n, int64_t{1} << 22), 256), 256, 0, cs>>>(ctx->P[1], ctx->P[0],
+                                                                                                 ctx->n, L);
+    }
+    e = cudaStreamEndCapture(cs, &body);
+    ctx->cur = cur;
+    ctx->round_graph_launches = bisim_launch_count() - before;
+    prof_add_launches(-ctx->round_graph_launches);      // counted when the rounds run
+    if (e == cudaSuccess) {
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, g, 0);
+        ctx->round_graph = exec;
+    }
+    cudaGraphDestroy(g);
+    if (e) {
+        ctx->round_graph = nullptr;
+        return cuda_error(ctx, e, "instantiate round graph");
+    }
     return BISIM_OK;
+}
+
+}  // namespace
+
+bool dense_graph_usable(const bisim_ctx* ctx) {
+    return ctx->dense_ready && ctx->n > 0 && !prof_enabled() &&
+           !(ctx->opt.flags & (BISIM_FLAG_EAGER | BISIM_FLAG_L2_PIN));
+}
+
+bisim_status dense_graph_rounds(bisim_ctx* ctx, cudaStream_t s, int32_t limit, bool fixpoint, int64_t prev_blocks,
+                                GraphRounds* out) {
+    bisim_status st;
+    if (ctx->round_graph == nullptr && (st = build_round_graph(ctx)) != BISIM_OK) return st;
+    LoopState* h = static_cast<LoopState*>(ctx->hloop);
+    std::memset(h, 0, sizeof(*h));
+    h->prev_blocks = static_cast<unsigned long long>(prev_blocks);
+    h->limit = limit;
+    h->fixpoint = fixpoint ? 1 : 0;
+    h->rounds = limit;
+    cudaError_t e;
+    cudaMemcpyAsync(ctx->dloop, h, sizeof(LoopState), cudaMemcpyHostToDevice, s);
+    if ((e = cudaGraphLaunch(static_cast<cudaGraphExec_t>(ctx->round_graph), s))) return cuda_error(ctx, e, "launch round graph");
+    cudaMemcpyAsync(h, ctx->dloop, sizeof(LoopState), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "round graph");
+    prof_add_launches(ctx->round_graph_launches * h->executed);
+    out->executed = h->executed;
+    out->rounds = h->rounds;
+    out->blocks = static_cast<int64_t>(h->blocks);
+    out->stop = h->stop;
+    return BISIM_OK;
+}
+
+void dense_release(bisim_ctx* ctx) {
+    if (ctx->round_graph) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->round_graph));
+    if (ctx->capture_stream) cudaStreamDestroy(static_cast<cudaStream_t>(ctx->capture_stream));
+    if (ctx->hloop) cudaFreeHost(ctx->hloop);
+    ctx->round_graph = nullptr;
+    ctx->capture_stream = nullptr;
+    ctx->hloop = nullptr;
 }
 
 }  // namespace bisim

@@ -73,6 +73,10 @@ int prof_site(const char* name) {
     return static_cast<int>(g_sites.size() - 1);
 }
 
+bool prof_enabled() { return g_enabled.load(std::memory_order_relaxed); }
+
+void prof_add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 Launch::Launch(int site, cudaStream_t s, int64_t vertices, int64_t edges, double alg_bytes)
     : site_(site), s_(s), vertices_(vertices), edges_(edges), bytes_(alg_bytes) {
     g_launches.fetch_add(1, std::memory_order_relaxed);

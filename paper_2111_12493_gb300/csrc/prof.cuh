@@ -10,6 +10,10 @@ namespace bisim {
 
 // Registers (once) and returns the index of a launch site.
 int prof_site(const char* name);
+// Whether launches are being timed (timed launches cannot sit in a captured graph).
+bool prof_enabled();
+// Adjusts the launch counter for kernels that run inside a graph replay.
+void prof_add_launches(int64_t n);
 
 // Brackets one kernel launch: counts it and, when profiling is enabled,
 // records events around it on stream `s`.

@@ -229,3 +229,26 @@ def test_host_memory_inputs_and_outputs(B):
     B.bisim_iterate(ctx, 2)
     assert np.array_equal(B.get_partition(ctx).cpu().numpy(), want)
     B.summarize_destroy(ctx)
+
+
+@pytest.mark.parametrize("bits", [64, 8])
+def test_device_round_loop_matches_eager_rounds(B, bits):
+    # default: the round loop runs as one captured graph (while node on the
+    # device); FLAG_EAGER and profiling run it round by round from the host
+    g = graphgen.powerlaw_graph(n=30_000, m=300_000, dmax=30_000, n_elabels=20, n_vlabels=5, seed=21)
+    want = {k: oracle.refine(g["n"], g["src"], g["dst"], g["elabel"], g["vlabel"], k, 10) for k in (1, 3, -1)}
+    for flags in (0, B.FLAG_EAGER):
+        opt = B.default_options(hash_bits=bits, flags=flags, mid_max_degree=1024)
+        ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]),
+                                   options=opt)
+        for k in (3, 1, -1, 3, -1):         # repeated calls replay the captured loop
+            rounds, blocks = B.bisim_iterate(ctx, k, 10)
+            P = B.get_partition(ctx).cpu().numpy()
+            wP, wr, _ = want[k]
+            assert np.array_equal(P, wP), (flags, k)
+            assert rounds == wr and blocks == len(np.unique(wP))
+        B.bisim_profile_enable(True)
+        rounds, _ = B.bisim_iterate(ctx, -1, 10)
+        B.bisim_profile_enable(False)
+        assert np.array_equal(B.get_partition(ctx).cpu().numpy(), want[-1][0]) and rounds == want[-1][1]
+        B.summarize_destroy(ctx)
