@@ -58,6 +58,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the update-batch latency section")
     ap.add_argument("--serving-batches", type=int, default=40)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default class thresholds")
     ap.add_argument("--workload", default="powerlaw", choices=["powerlaw", "chain", "batched"],
                     help="powerlaw: 10M/100M to the fixpoint (the headline); chain: 1000 paths of 1000 "
                          "+ 2M random edges to the fixpoint; batched: 4096 graphs in one context, k=3")
@@ -122,11 +123,10 @@ class Workload:
             d.update(extra)
         return d
 
+    options = None
+
     def step(self, bisim, tensors, out):
-        if self.batched:
-            ctx = bisim.summarize_init_batched(*tensors)
-        else:
-            ctx = bisim.summarize_init_coo(self.n, *tensors)
+        ctx = self.init_only(bisim, tensors)
         rounds, blocks = bisim.bisim_iterate(ctx, self.k, self.cap)
         bisim.get_partition(ctx, out=out)
         executed = bisim.bisim_get_stats(ctx)["rounds_executed"]
@@ -135,8 +135,8 @@ class Workload:
 
     def init_only(self, bisim, tensors):
         if self.batched:
-            return bisim.summarize_init_batched(*tensors)
-        return bisim.summarize_init_coo(self.n, *tensors)
+            return bisim.summarize_init_batched(*tensors, options=self.options)
+        return bisim.summarize_init_coo(self.n, *tensors, options=self.options)
 
 
 def config_dict(n, m, g=None, extra=None):
@@ -255,6 +255,15 @@ def run_ours(args, world, rank, local):
 
     def step(*tensors):
         return W.step(bisim, tensors[:-1], tensors[-1])
+
+    tuned = None
+    if not args.no_autotune:
+        # class thresholds and hub chunk timed on this graph, once, before the warm-up
+        ctx = W.init_only(bisim, d_in)
+        tuned = bisim.bisim_autotune(ctx, rounds=2)
+        bisim.summarize_destroy(ctx)
+        W.options = bisim.default_options(**{k: tuned[k] for k in ("small_max_degree", "mid_max_degree",
+                                                                   "hub_chunk")})
 
     for _ in range(args.warmup):
         rounds, blocks, executed = step(*d_in, d_out)
@@ -383,7 +392,9 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32 ids, u64 hashes (integer only)",
             "data": "synthetic (seeded generator; stands in for the paper's BSBM/DyLDO graphs)",
             "config": W.config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                                "rounds": int(rounds), "rounds_executed": int(executed), "blocks": int(blocks)}),
+                                "rounds": int(rounds), "rounds_executed": int(executed), "blocks": int(blocks),
+                                "autotuned": None if tuned is None else
+                                {k: tuned[k] for k in ("small_max_degree", "mid_max_degree", "hub_chunk")}}),
             "iterate_only": {"value": iterate_only, "unit": UNIT, "rounds_executed": int(it_exec),
                              "note": "bisim_iterate alone on a resident context (round graph already captured)"},
             "profiled_steps": {"ms_per_step": profiled_ms / args.steps,

@@ -200,6 +200,19 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
 bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream);
 
 /*
+ * bisim_autotune -- choose the degree-class thresholds of the round layout
+ * (mid_max_degree: rows above it take the hub path; small_max_degree: rows up
+ * to it take one thread each) and the hub chunk size for this context's graph
+ * by timing `rounds` refinement rounds (1..64) under each candidate value, one
+ * setting at a time, on `stream`. The chosen values stay in the context (and
+ * are written to *out when out is not NULL) and take effect from the next
+ * bisim_iterate or apply_updates. Results never depend on these settings.
+ * Leaves the context's partition undefined until the next bisim_iterate.
+ * Synchronises `stream`.
+ */
+bisim_status bisim_autotune(bisim_ctx* ctx, int32_t rounds, bisim_options* out, void* stream);
+
+/*
  * bisim_refine_round_noalloc -- one refinement round (block_in -> block_out)
  * that allocates no memory at all. The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory, such as a

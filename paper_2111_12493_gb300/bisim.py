@@ -75,6 +75,7 @@ def _load():
         "bisim_profile_read": (i32, [ctypes.POINTER(KernelProfile), i32]),
         "bisim_launch_count": (i64, []),
         "bisim_refine_round_noalloc": (ctypes.c_int, [i32, i64, p, p, p, p, p, ctypes.POINTER(i64), p]),
+        "bisim_autotune": (ctypes.c_int, [p, i32, ctypes.POINTER(Options), p]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -211,6 +212,17 @@ def get_partition(ctx: Context, out=None, stream=None):
     rc = _lib.get_partition(ctx.ptr, _ptr(out, torch.int32, "out", ctx.n_vertices), _stream(stream))
     _check(rc, ctx.ptr)
     return out
+
+
+def bisim_autotune(ctx: Context, rounds: int = 2, stream=None) -> dict:
+    """Time candidate class thresholds and hub chunk sizes on this graph; keep the fastest.
+
+    Returns the chosen options as a dict; they apply from the next
+    bisim_iterate (the current partition is left undefined until then).
+    """
+    o = Options()
+    _check(_lib.bisim_autotune(ctx.ptr, rounds, ctypes.byref(o), _stream(stream)), ctx.ptr)
+    return {name: getattr(o, name) for name, _ in Options._fields_}
 
 
 def bisim_get_stats(ctx: Context) -> dict:

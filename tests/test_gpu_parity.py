@@ -252,3 +252,17 @@ def test_device_round_loop_matches_eager_rounds(B, bits):
         B.bisim_profile_enable(False)
         assert np.array_equal(B.get_partition(ctx).cpu().numpy(), want[-1][0]) and rounds == want[-1][1]
         B.summarize_destroy(ctx)
+
+
+def test_autotune_keeps_results_and_picks_listed_settings(B):
+    g = graphgen.powerlaw_graph(n=40_000, m=400_000, dmax=40_000, n_elabels=30, n_vlabels=6, seed=31)
+    ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]))
+    tuned = B.bisim_autotune(ctx, rounds=2)
+    assert tuned["mid_max_degree"] in (2048, 4096, 8192)
+    assert tuned["small_max_degree"] in (8, 16, 32)
+    assert tuned["hub_chunk"] in (1024, 2048, 4096)
+    for k in (2, -1):
+        rounds, _ = B.bisim_iterate(ctx, k, 10)
+        want, wr, _ = oracle.refine(g["n"], g["src"], g["dst"], g["elabel"], g["vlabel"], k, 10)
+        assert np.array_equal(B.get_partition(ctx).cpu().numpy(), want) and rounds == wr
+    B.summarize_destroy(ctx)
