@@ -248,7 +248,9 @@ bisim_status bisim_refine_round_noalloc(int32_t n_vertices, int64_t n_edges, con
 /* Counters of the context (see bisim_stats). Synchronises nothing. */
 bisim_status bisim_get_stats(const bisim_ctx* ctx, bisim_stats* out);
 
-/* Free every device buffer of the context. NULL is accepted. */
+/* Free every device buffer of the context, in the order of the stream its
+ * last call used, and wait for that stream (so that the memory pool can hand
+ * the memory to the next context at once). NULL is accepted. */
 bisim_status summarize_destroy(bisim_ctx* ctx);
 
 /*

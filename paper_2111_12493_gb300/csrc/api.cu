@@ -14,6 +14,38 @@ namespace {
 
 thread_local std::string g_last_error = "no error";
 
+// Small pinned host blocks (status mirrors of contexts) come from slabs that
+// live for the whole process: allocating and freeing pinned memory per
+// context costs far more than the context's own work on small graphs, and
+// freeing it waits for the whole device.
+constexpr size_t kPinnedBlock = 256;
+constexpr size_t kPinnedSlab = 64 * 1024;
+std::mutex g_pinned_mu;
+std::vector<void*> g_pinned_free;
+
+}  // namespace
+
+void* pinned_take() {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    if (g_pinned_free.empty()) {
+        void* slab = nullptr;
+        if (cudaHostAlloc(&slab, kPinnedSlab, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+        for (size_t off = 0; off < kPinnedSlab; off += kPinnedBlock)
+            g_pinned_free.push_back(static_cast<char*>(slab) + off);
+    }
+    void* p = g_pinned_free.back();
+    g_pinned_free.pop_back();
+    return p;
+}
+
+void pinned_give(void* p) {
+    if (p == nullptr) return;
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    g_pinned_free.push_back(p);
+}
+
+namespace {
+
 void setup_pool(int device) {
     static std::once_flag once[64];
     if (device < 0 || device >= 64) return;
@@ -61,9 +93,14 @@ void free_temps(std::vector<void*>& temps, cudaStream_t s) {
 void destroy_ctx(bisim_ctx* ctx) {
     if (ctx == nullptr) return;
     dense_release(ctx);
-    for (void* p : ctx->allocs) cudaFreeAsync(p, 0);
-    if (ctx->dstate) cudaFreeAsync(ctx->dstate, 0);
-    if (ctx->hstate) cudaFreeHost(ctx->hstate);
+    // free in the order of the stream the context last worked on, and wait for
+    // it: the pool then hands the memory straight to the next context, which a
+    // free still pending on the device would make it map afresh
+    cudaStream_t s = static_cast<cudaStream_t>(ctx->last_stream);
+    for (void* p : ctx->allocs) cudaFreeAsync(p, s);
+    if (ctx->dstate) cudaFreeAsync(ctx->dstate, s);
+    cudaStreamSynchronize(s);
+    pinned_give(ctx->hstate);
     delete ctx;
 }
 
@@ -86,16 +123,21 @@ bisim_status new_ctx(bisim_ctx** out, int32_t n, int64_t m, const bisim_options*
     *out = nullptr;
     if (n < 0 || m < 0) return set_error(nullptr, BISIM_EINVAL, "negative vertex or edge count");
     bisim_ctx* ctx = new bisim_ctx();
+    ctx->last_stream = s;
     ctx->n = n;
     ctx->m = m;
     ctx->opt = resolve_options(opt);
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e) { delete ctx; return cuda_error(nullptr, e, "cudaGetDevice"); }
     setup_pool(ctx->device);
-    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&ctx->dstate), sizeof(DevState), s)) ||
-        (e = cudaHostAlloc(reinterpret_cast<void**>(&ctx->hstate), sizeof(DevState), cudaHostAllocDefault))) {
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&ctx->dstate), sizeof(DevState), s))) {
         destroy_ctx(ctx);
         return cuda_error(nullptr, e, "allocate context state");
+    }
+    ctx->hstate = static_cast<DevState*>(pinned_take());
+    if (ctx->hstate == nullptr) {
+        destroy_ctx(ctx);
+        return set_error(nullptr, BISIM_ENOMEM, "pinned host memory for the context state");
     }
     cudaMemsetAsync(ctx->dstate, 0, sizeof(DevState), s);
     std::memset(ctx->hstate, 0, sizeof(DevState));
@@ -432,6 +474,7 @@ bisim_status summarize_init_batched(bisim_ctx** out, int32_t n_graphs, const int
 bisim_status bisim_iterate(bisim_ctx* ctx, int32_t k, int32_t cap, int32_t* out_rounds, int64_t* out_num_blocks,
                            void* stream) {
     if (ctx == nullptr) return set_error(nullptr, BISIM_EINVAL, "ctx is NULL");
+    ctx->last_stream = stream;
     if (k < BISIM_FIXPOINT) return set_error(ctx, BISIM_EINVAL, "k must be >= 0 or BISIM_FIXPOINT");
     if (k == BISIM_FIXPOINT && cap < 0) return set_error(ctx, BISIM_EINVAL, "cap must be >= 0");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -447,6 +490,7 @@ bisim_status bisim_iterate(bisim_ctx* ctx, int32_t k, int32_t cap, int32_t* out_
 
 bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, void* stream) {
     if (ctx == nullptr) return set_error(nullptr, BISIM_EINVAL, "ctx is NULL");
+    ctx->last_stream = stream;
     if (n_ops < 0 || (n_ops > 0 && ops == nullptr)) return set_error(ctx, BISIM_EINVAL, "invalid op array");
     if (ctx->gid != nullptr) return set_error(ctx, BISIM_ESTATE, "apply_updates is not supported on batched contexts");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -496,6 +540,7 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
 
 bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream) {
     if (ctx == nullptr) return set_error(nullptr, BISIM_EINVAL, "ctx is NULL");
+    ctx->last_stream = stream;
     if (block == nullptr && ctx->n > 0) return set_error(ctx, BISIM_EINVAL, "output is NULL");
     if (ctx->n == 0) return BISIM_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -351,6 +351,7 @@ struct bisim_ctx {
     uint64_t isize = 0;            // index slots per level (power of two)
 
     // bookkeeping
+    void* last_stream = nullptr;   // stream of the last call (the context's memory is freed in its order)
     std::vector<void*> allocs;
     int64_t device_bytes = 0;
     bisim_stats stats{};
@@ -365,6 +366,9 @@ namespace bisim {
 bisim_status set_error(bisim_ctx* ctx, bisim_status st, const std::string& msg);
 bisim_status cuda_error(bisim_ctx* ctx, cudaError_t e, const char* what);
 cudaError_t ctx_alloc(bisim_ctx* ctx, void** p, size_t bytes, cudaStream_t s);
+// 256-byte pinned host blocks from process-lifetime slabs (nullptr if none can be had).
+void* pinned_take();
+void pinned_give(void* p);
 
 // ----------------------------------------------------------------------------- primitives (sort.cu)
 

@@ -1181,7 +1181,8 @@ bisim_status build_round_graph(bisim_ctx* ctx) {
         return cuda_error(ctx, e, "create capture stream");
     if (ctx->dloop == nullptr) {
         if ((e = ctx_alloc(ctx, &ctx->dloop, sizeof(LoopState), nullptr))) return cuda_error(ctx, e, "alloc loop state");
-        if ((e = cudaMallocHost(&ctx->hloop, sizeof(LoopState)))) return cuda_error(ctx, e, "alloc loop state mirror");
+        static_assert(sizeof(LoopState) <= 256, "pinned blocks hold 256 bytes");
+        if ((ctx->hloop = pinned_take()) == nullptr) return set_error(ctx, BISIM_ENOMEM, "pinned loop state mirror");
     }
     cudaStream_t cs = static_cast<cudaStream_t>(ctx->capture_stream);
     cudaGraph_t g = nullptr;
@@ -1277,7 +1278,7 @@ bisim_status dense_graph_rounds(bisim_ctx* ctx, cudaStream_t s, int32_t limit, b
 void dense_release(bisim_ctx* ctx) {
     if (ctx->round_graph) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->round_graph));
     if (ctx->capture_stream) cudaStreamDestroy(static_cast<cudaStream_t>(ctx->capture_stream));
-    if (ctx->hloop) cudaFreeHost(ctx->hloop);
+    pinned_give(ctx->hloop);
     ctx->round_graph = nullptr;
     ctx->capture_stream = nullptr;
     ctx->hloop = nullptr;

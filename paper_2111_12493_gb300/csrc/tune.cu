@@ -54,6 +54,7 @@ extern "C" bisim_status bisim_autotune(bisim_ctx* ctx, int32_t rounds, bisim_opt
     if (ctx == nullptr) return set_error(nullptr, BISIM_EINVAL, "ctx is NULL");
     if (rounds < 1 || rounds > 64) return set_error(ctx, BISIM_EINVAL, "rounds must be in [1, 64]");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ctx->last_stream = stream;
     bisim_status st;
     if ((st = refresh_after_edit(ctx, s)) != BISIM_OK) return st;
     if (ctx->n > 0) {
