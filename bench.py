@@ -44,7 +44,12 @@ WORKLOAD = dict(n=10_000_000, m=100_000_000, exponent=2.1, dmax=1_000_000, n_ela
                 untyped=0.1, k="fixpoint", cap=10, seed=2)
 # Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel from one ncu capture; None until captured for the current kernel.
-NCU_TRAFFIC_BYTES = {}
+NCU_TRAFFIC_BYTES = {
+    # k_radix_scatter (one 8-bit pass of the CSR build over (u32 key, u64 value) pairs): 715 MB read +
+    # 639 MB written per launch on the 5M / 50M instance (ncu --set full, 10 launches); traffic grows with
+    # the items, so x2 for the 100M-edge launch. Algorithmic: 24 B per item, 2.4 GB per launch.
+    "radix_scatter": 2 * (715.0e6 + 639.4e6),
+}
 
 
 def parse_args():

@@ -131,7 +131,7 @@ __global__ void k_dense_degrees(const int32_t* __restrict__ vert, int64_t n_live
     }
 }
 
-// Rows of out-degree <= 32: one warp per 32 consecutive positions. The warp's
+// Rows of out-degree <= 256: one warp per 32 consecutive positions. The warp's
 // output range is contiguous, so it is written word by word across the lanes;
 // each word finds its source row by a binary search over the warp's 33 row
 // offsets in shared memory.
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256) k_dense_pack_rows(const int32_t* __restri
     }
 }
 
-// Longer rows: one CTA per position.
+// Rows of out-degree <= 8192: one CTA per position.
 __global__ void k_dense_pack_big(const int32_t* __restrict__ vert, int64_t first, const int64_t* __restrict__ prp,
                                  const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                  const int32_t* __restrict__ elab, unsigned long long* __restrict__ pe) {
@@ -1054,7 +1054,7 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
     for (int c = 0; c <= kDClasses; ++c)
         cudaMemcpyAsync(&ctx->dedge_begin[c], ctx->dprp + begin[c], sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     {
-        const int64_t small = begin[kDWarp0];
+        const int64_t small = begin[kDMid0];                 // rows of at most 256 edges: a warp per 32 rows
         const int64_t mid = begin[kDHub] - small;
         const int64_t edges = ctx->dedge_begin[kDHub];
         Launch L(site_p, s, begin[kDHub], edges, 16.0 * edges + 20.0 * begin[kDHub]);
