@@ -495,7 +495,8 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
     if (ctx->gid != nullptr) return set_error(ctx, BISIM_ESTATE, "apply_updates is not supported on batched contexts");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
-    bisim_status st = BISIM_OK;
+    bisim_status st = ensure_vertex_csr(ctx, s);
+    if (st != BISIM_OK) return st;
     if (n_ops > 0) {
         std::vector<void*> temps;
         const void* d_ops = nullptr;

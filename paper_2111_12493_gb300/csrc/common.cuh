@@ -433,6 +433,15 @@ bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s);
 
 // Builds (or rebuilds after an edit) the dense round layout of the current CSR.
 bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s);
+// The layout's positions, classes and row offsets from the out-degrees (deg[n]).
+bisim_status dense_layout_positions(bisim_ctx* ctx, const int32_t* deg, cudaStream_t s);
+// The hub part of the layout, after the packed rows exist (or, with
+// pack_from_csr, copying the hub rows from the vertex-ordered CSR); marks the
+// layout ready.
+bisim_status dense_layout_hubs(bisim_ctx* ctx, bool pack_from_csr, cudaStream_t s);
+// The vertex-ordered CSR (row_ptr, col, elab), rebuilt from the layout when a
+// context was built straight into it (updates and list-mode paths need it).
+bisim_status ensure_vertex_csr(bisim_ctx* ctx, cudaStream_t s);
 // Writes -1 for the dead vertices into both partition buffers.
 void dense_mark_dead(bisim_ctx* ctx, cudaStream_t s);
 // One refinement round P[cur] -> P[cur ^ 1] over every live vertex.

@@ -78,12 +78,17 @@ __device__ __forceinline__ void warp_count(bool flag, unsigned long long* counte
 
 // ----------------------------------------------------------------------------- layout kernels
 
-__global__ void k_dense_classify(const int64_t* __restrict__ rp, const uint8_t* __restrict__ alive, int32_t n,
+__global__ void k_deg_from_rows(const int64_t* __restrict__ rp, int32_t n, int32_t* __restrict__ deg) {
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v < n) deg[v] = static_cast<int32_t>(rp[v + 1] - rp[v]);
+}
+
+__global__ void k_dense_classify(const int32_t* __restrict__ deg, const uint8_t* __restrict__ alive, int32_t n,
                                  int small_max, int mid_max, uint32_t* __restrict__ keys,
                                  uint64_t* __restrict__ vals) {
     const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (v >= n) return;
-    const int64_t d = rp[v + 1] - rp[v];
+    const int64_t d = deg[v];
     uint32_t c;
     if (alive != nullptr && !alive[v]) {
         c = kDDead;
@@ -119,15 +124,91 @@ __global__ void k_dense_vertices(const uint64_t* __restrict__ sv, int32_t n, int
     vpos[v] = static_cast<int32_t>(i);
 }
 
-__global__ void k_dense_degrees(const int32_t* __restrict__ vert, int64_t n_live, const int64_t* __restrict__ rp,
-                                int64_t* __restrict__ deg) {
+__global__ void k_dense_degrees(const int32_t* __restrict__ vert, int64_t n_live, const int32_t* __restrict__ deg,
+                                int64_t* __restrict__ out) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i > n_live) return;
-    if (i == n_live) {
-        deg[i] = 0;
-    } else {
-        const int32_t v = vert[i];
-        deg[i] = rp[v + 1] - rp[v];
+    out[i] = i == n_live ? 0 : deg[vert[i]];
+}
+
+// Vertex-ordered out-degrees back from the layout (dead vertices: 0).
+__global__ void k_vertex_degrees(const int32_t* __restrict__ vpos, int32_t n, int64_t n_live,
+                                 const int64_t* __restrict__ prp, int64_t* __restrict__ deg) {
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v > n) return;
+    if (v == n) {
+        deg[v] = 0;
+        return;
+    }
+    const int64_t p = vpos[v];
+    deg[v] = p < n_live ? prp[p + 1] - prp[p] : 0;
+}
+
+// Vertex-ordered rows of at most 256 edges from the packed rows: one warp per
+// 32 consecutive vertices. The warp's short rows are numbered consecutively
+// (a warp scan of their lengths); every word finds its row by a binary search
+// over the 33 prefix values in shared memory. Longer rows are left to
+// k_unpack_big and k_unpack_chunks.
+__global__ void __launch_bounds__(256) k_unpack_rows(const int32_t* __restrict__ vpos, int32_t n, int64_t n_live,
+                                                     const int64_t* __restrict__ prp,
+                                                     const unsigned long long* __restrict__ pe,
+                                                     const int64_t* __restrict__ rp, int32_t* __restrict__ col,
+                                                     int32_t* __restrict__ elab) {
+    __shared__ int64_t pre_all[8][33];
+    __shared__ int64_t dst_all[8][32];
+    __shared__ int64_t src_all[8][32];
+    const int warp = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
+    const int64_t v0 = (static_cast<int64_t>(blockIdx.x) * 8 + warp) * 32;
+    if (v0 >= n) return;                                 // whole warp leaves together
+    int64_t* pre = pre_all[warp];
+    int64_t* dst = dst_all[warp];
+    int64_t* src = src_all[warp];
+    const int64_t v = v0 + lane;
+    int64_t a = 0, d = 0, sp = 0;
+    if (v < n) {
+        a = rp[v];
+        d = rp[v + 1] - a;
+        if (d > 256) d = 0;
+        const int64_t p = vpos[v];
+        sp = p < n_live ? prp[p] : 0;
+    }
+    int64_t incl = d;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (static_cast<int>(lane) >= o) incl += y;
+    }
+    pre[lane] = incl - d;
+    dst[lane] = a;
+    src[lane] = sp;
+    if (lane == 31) pre[32] = incl;
+    __syncwarp();
+    const int64_t total = pre[32];
+    for (int64_t t = lane; t < total; t += 32) {
+        int lo = 0, hi = 31;                             // the last row starting at or before t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const int64_t off = t - pre[lo];
+        const unsigned long long w = pe[src[lo] + off];
+        col[dst[lo] + off] = static_cast<int32_t>(static_cast<uint32_t>(w));
+        elab[dst[lo] + off] = static_cast<int32_t>(w >> 32);
+    }
+}
+
+// Longer rows (CTA classes): one CTA per position.
+__global__ void k_unpack_big(const int32_t* __restrict__ vert, int64_t first, const int64_t* __restrict__ prp,
+                             const unsigned long long* __restrict__ pe, const int64_t* __restrict__ rp,
+                             int32_t* __restrict__ col, int32_t* __restrict__ elab) {
+    const int64_t i = first + blockIdx.x;
+    const int64_t o = rp[vert[i]];
+    const int64_t b = prp[i], d = prp[i + 1] - b;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        const unsigned long long w = pe[b + j];
+        col[o + j] = static_cast<int32_t>(static_cast<uint32_t>(w));
+        elab[o + j] = static_cast<int32_t>(w >> 32);
     }
 }
 
@@ -189,6 +270,21 @@ __global__ void k_dense_pack_chunks(const HubChunk* __restrict__ chunks, const i
     const int64_t pos = first + c.hub;
     const int64_t src = rp[vert[pos]] - prp[pos];        // source index = packed index + src
     for (int64_t o = c.begin + threadIdx.x; o < c.end; o += blockDim.x) pe[o] = pack_edge(elab[src + o], col[src + o]);
+}
+
+// Hub rows back to vertex order: one CTA per chunk.
+__global__ void k_unpack_chunks(const HubChunk* __restrict__ chunks, const int32_t* __restrict__ vert, int64_t first,
+                                const int64_t* __restrict__ prp, const unsigned long long* __restrict__ pe,
+                                const int64_t* __restrict__ rp, int32_t* __restrict__ col,
+                                int32_t* __restrict__ elab) {
+    const HubChunk c = chunks[blockIdx.x];
+    const int64_t pos = first + c.hub;
+    const int64_t dst = rp[vert[pos]] - prp[pos];        // vertex-ordered index = packed index + dst
+    for (int64_t e = c.begin + threadIdx.x; e < c.end; e += blockDim.x) {
+        const unsigned long long w = pe[e];
+        col[dst + e] = static_cast<int32_t>(static_cast<uint32_t>(w));
+        elab[dst + e] = static_cast<int32_t>(w >> 32);
+    }
 }
 
 __global__ void k_dense_dead(const int32_t* __restrict__ vert, int64_t first, int64_t n, int32_t* __restrict__ Pa,
@@ -946,35 +1042,25 @@ bisim_status finish_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
 
 }  // namespace
 
-bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
-    if (ctx->dense_ready) return BISIM_OK;
-    if (ctx->round_graph) {                    // captured for the previous layout
-        cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->round_graph));
-        ctx->round_graph = nullptr;
-    }
-    const int32_t n = ctx->n;
-    const int64_t m = ctx->m;
-    const size_t nv = static_cast<size_t>(std::max(n, 1));
+namespace {
+
+bisim_status alloc_round_state(bisim_ctx* ctx, cudaStream_t s) {
+    if (ctx->dvert != nullptr) return BISIM_OK;
+    const size_t nv = static_cast<size_t>(std::max(ctx->n, 1));
     cudaError_t e;
-    if (ctx->dvert == nullptr) {
-        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dvert), sizeof(int32_t) * nv, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dvpos), sizeof(int32_t) * nv, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dprp), sizeof(int64_t) * (nv + 1), s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dslot), sizeof(uint32_t) * nv, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dhash), sizeof(unsigned long long) * nv, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dcnt), sizeof(int32_t) * nv, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dpairs), sizeof(int2) * nv, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dsmall), sizeof(int2) * nv, s)))
-            return cuda_error(ctx, e, "alloc dense round state");
-    }
-    if (m > ctx->dpe_cap || ctx->dpe == nullptr) {
-        ctx_free(ctx, ctx->dpe, sizeof(unsigned long long) * ctx->dpe_cap, s);
-        ctx->dpe = nullptr;
-        const int64_t cap = std::max<int64_t>(m, 1);
-        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dpe), sizeof(unsigned long long) * cap, s))) return cuda_error(ctx, e, "alloc packed rows");
-        ctx->dpe_cap = cap;
-    }
-    // the previous hub layout
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dvert), sizeof(int32_t) * nv, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dvpos), sizeof(int32_t) * nv, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dprp), sizeof(int64_t) * (nv + 1), s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dslot), sizeof(uint32_t) * nv, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dhash), sizeof(unsigned long long) * nv, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dcnt), sizeof(int32_t) * nv, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dpairs), sizeof(int2) * nv, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dsmall), sizeof(int2) * nv, s)))
+        return cuda_error(ctx, e, "alloc dense round state");
+    return BISIM_OK;
+}
+
+void free_hub_layout(bisim_ctx* ctx, cudaStream_t s) {
     ctx_free(ctx, ctx->dchunks, sizeof(HubChunk) * ctx->n_dchunks, s);
     ctx_free(ctx, ctx->hshift, sizeof(int32_t) * ctx->n_dhub, s);
     ctx_free(ctx, ctx->hbbase, sizeof(int64_t) * ctx->n_dhub, s);
@@ -998,7 +1084,33 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
     ctx->bscan = nullptr;
     ctx->dacc = nullptr;
     ctx->n_dchunks = ctx->n_dhub = ctx->n_buckets = ctx->hub_edges = ctx->bscan_words = 0;
+}
 
+// Copies the rows of the vertex-ordered CSR into the packed rows (all but hubs).
+void pack_rows_from_csr(bisim_ctx* ctx, cudaStream_t s) {
+    BISIM_SITE(site_p, "dense_pack");
+    const int64_t* begin = ctx->dbegin;
+    const int64_t small = begin[kDMid0];                 // rows of at most 256 edges: a warp per 32 rows
+    const int64_t mid = begin[kDHub] - small;
+    const int64_t edges = ctx->dedge_begin[kDHub];
+    Launch L(site_p, s, begin[kDHub], edges, 16.0 * edges + 20.0 * begin[kDHub]);
+    if (small > 0)
+        k_dense_pack_rows<<<grid_for(small, 256), 256, 0, s>>>(ctx->dvert, small, ctx->dprp, ctx->row_ptr, ctx->col,
+                                                              ctx->elab, ctx->dpe);
+    if (mid > 0)
+        k_dense_pack_big<<<static_cast<unsigned>(mid), 256, 0, s>>>(ctx->dvert, small, ctx->dprp, ctx->row_ptr,
+                                                                   ctx->col, ctx->elab, ctx->dpe);
+}
+
+}  // namespace
+
+bisim_status dense_layout_positions(bisim_ctx* ctx, const int32_t* deg, cudaStream_t s) {
+    const int32_t n = ctx->n;
+    const size_t nv = static_cast<size_t>(std::max(n, 1));
+    cudaError_t e;
+    bisim_status st;
+    if ((st = alloc_round_state(ctx, s)) != BISIM_OK) return st;
+    free_hub_layout(ctx, s);
     const size_t tmp_words = std::max(radix_temp_words(n), scan_temp_words(static_cast<int64_t>(n) + 1));
     const size_t bytes = (sizeof(uint32_t) * 2 + sizeof(uint64_t) * 2) * nv + sizeof(int64_t) * (nv + 1) +
                          sizeof(int64_t) * (tmp_words + kDClasses + 1) + 6 * 256;
@@ -1010,19 +1122,17 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
     uint32_t* k1 = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * nv));
     uint64_t* v0 = reinterpret_cast<uint64_t*>(carve(sizeof(uint64_t) * nv));
     uint64_t* v1 = reinterpret_cast<uint64_t*>(carve(sizeof(uint64_t) * nv));
-    int64_t* deg = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * (nv + 1)));
+    int64_t* pdeg = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * (nv + 1)));
     int64_t* tmp = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * tmp_words));
     int64_t* dbeg = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * (kDClasses + 1)));
-
     int64_t begin[kDClasses + 1];
     for (int c = 0; c <= kDClasses; ++c) begin[c] = n;
     cudaMemcpyAsync(dbeg, begin, sizeof(begin), cudaMemcpyHostToDevice, s);
     BISIM_SITE(site_c, "dense_classify");
-    BISIM_SITE(site_p, "dense_pack");
     if (n > 0) {
         {
-            Launch L(site_c, s, n, 0, 24.0 * n);
-            k_dense_classify<<<grid_for(n, 256), 256, 0, s>>>(ctx->row_ptr, ctx->alive, n, ctx->opt.small_max_degree,
+            Launch L(site_c, s, n, 0, 12.0 * n);
+            k_dense_classify<<<grid_for(n, 256), 256, 0, s>>>(deg, ctx->alive, n, ctx->opt.small_max_degree,
                                                              ctx->opt.mid_max_degree, k0, v0);
         }
         const int which = radix_sort_pairs(k0, v0, k1, v1, n, 5, tmp, s);
@@ -1047,34 +1157,27 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
     ctx->stats.n_mid = begin[kDHub] - begin[kDWarp0];
     ctx->stats.n_hub = begin[kDHub + 1] - begin[kDHub];
     {
-        Launch L(site_c, s, n_live, 0, 28.0 * n_live);
-        k_dense_degrees<<<grid_for(n_live + 1, 256), 256, 0, s>>>(ctx->dvert, n_live, ctx->row_ptr, deg);
+        Launch L(site_c, s, n_live, 0, 12.0 * n_live);
+        k_dense_degrees<<<grid_for(n_live + 1, 256), 256, 0, s>>>(ctx->dvert, n_live, deg, pdeg);
     }
-    exclusive_scan_i64(deg, ctx->dprp, n_live + 1, tmp, s);
+    exclusive_scan_i64(pdeg, ctx->dprp, n_live + 1, tmp, s);
     for (int c = 0; c <= kDClasses; ++c)
         cudaMemcpyAsync(&ctx->dedge_begin[c], ctx->dprp + begin[c], sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    {
-        const int64_t small = begin[kDMid0];                 // rows of at most 256 edges: a warp per 32 rows
-        const int64_t mid = begin[kDHub] - small;
-        const int64_t edges = ctx->dedge_begin[kDHub];
-        Launch L(site_p, s, begin[kDHub], edges, 16.0 * edges + 20.0 * begin[kDHub]);
-        if (small > 0)
-            k_dense_pack_rows<<<grid_for(small, 256), 256, 0, s>>>(ctx->dvert, small, ctx->dprp, ctx->row_ptr,
-                                                                  ctx->col, ctx->elab, ctx->dpe);
-        if (mid > 0)
-            k_dense_pack_big<<<static_cast<unsigned>(mid), 256, 0, s>>>(ctx->dvert, small, ctx->dprp, ctx->row_ptr,
-                                                                       ctx->col, ctx->elab, ctx->dpe);
-    }
+    cudaFreeAsync(base, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "row offsets");
+    return BISIM_OK;
+}
 
-    // hub chunks and sets (host-side layout; hubs are few)
+bisim_status dense_layout_hubs(bisim_ctx* ctx, bool pack_from_csr, cudaStream_t s) {
+    cudaError_t e;
+    const int64_t* begin = ctx->dbegin;
+    const int64_t m = ctx->m;
     const int64_t nh = begin[kDHub + 1] - begin[kDHub];
+    BISIM_SITE(site_p, "dense_pack");
     if (nh > 0) {
         std::vector<int64_t> rows(nh + 1);
         cudaMemcpyAsync(rows.data(), ctx->dprp + begin[kDHub], sizeof(int64_t) * (nh + 1), cudaMemcpyDeviceToHost, s);
-        if ((e = cudaStreamSynchronize(s))) {
-            cudaFreeAsync(base, s);
-            return cuda_error(ctx, e, "read hub rows");
-        }
+        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "read hub rows");
         std::vector<HubChunk> chunks;
         std::vector<int32_t> shift(nh), bhub;
         std::vector<int64_t> bbase(nh);
@@ -1106,16 +1209,14 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bvals), sizeof(unsigned long long) * ctx->hub_edges, s)) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bmv), sizeof(unsigned long long) * ctx->hub_edges, s)) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bscan), sizeof(int64_t) * ctx->bscan_words, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dacc), sizeof(HubAcc) * nh, s))) {
-            cudaFreeAsync(base, s);
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dacc), sizeof(HubAcc) * nh, s)))
             return cuda_error(ctx, e, "alloc hub buckets");
-        }
         if (!chunks.empty())
             cudaMemcpyAsync(ctx->dchunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(ctx->hshift, shift.data(), sizeof(int32_t) * nh, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(ctx->hbbase, bbase.data(), sizeof(int64_t) * nh, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(ctx->bhub, bhub.data(), sizeof(int32_t) * nbk, cudaMemcpyHostToDevice, s);
-        if (!chunks.empty()) {
+        if (pack_from_csr && !chunks.empty()) {
             // hub rows are copied chunk by chunk, like the rounds read them
             const int64_t edges = m - ctx->dedge_begin[kDHub];
             Launch L(site_p, s, nh, edges, 16.0 * edges);
@@ -1123,15 +1224,78 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
                 ctx->dchunks, ctx->dvert, begin[kDHub], ctx->dprp, ctx->row_ptr, ctx->col, ctx->elab, ctx->dpe);
         }
         // the host vectors die here: finish the uploads first
-        if ((e = cudaStreamSynchronize(s))) {
-            cudaFreeAsync(base, s);
-            return cuda_error(ctx, e, "upload hub layout");
-        }
+        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "upload hub layout");
     }
-    cudaFreeAsync(base, s);
-    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "build dense layout");
     if ((e = cudaGetLastError())) return cuda_error(ctx, e, "build dense layout");
     ctx->dense_ready = true;
+    ctx->stats.device_bytes = ctx->device_bytes;
+    return BISIM_OK;
+}
+
+bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
+    if (ctx->dense_ready) return BISIM_OK;
+    if (ctx->round_graph) {                    // captured for the previous layout
+        cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->round_graph));
+        ctx->round_graph = nullptr;
+    }
+    bisim_status st;
+    if ((st = ensure_vertex_csr(ctx, s)) != BISIM_OK) return st;
+    const int32_t n = ctx->n;
+    const int64_t m = ctx->m;
+    cudaError_t e;
+    if (m > ctx->dpe_cap || ctx->dpe == nullptr) {
+        ctx_free(ctx, ctx->dpe, sizeof(unsigned long long) * ctx->dpe_cap, s);
+        ctx->dpe = nullptr;
+        const int64_t cap = std::max<int64_t>(m, 1);
+        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dpe), sizeof(unsigned long long) * cap, s))) return cuda_error(ctx, e, "alloc packed rows");
+        ctx->dpe_cap = cap;
+    }
+    int32_t* deg = nullptr;
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&deg), sizeof(int32_t) * std::max(n, 1), s))) return cuda_error(ctx, e, "alloc degrees");
+    if (n > 0) k_deg_from_rows<<<grid_for(n, 256), 256, 0, s>>>(ctx->row_ptr, n, deg);
+    st = dense_layout_positions(ctx, deg, s);
+    cudaFreeAsync(deg, s);
+    if (st != BISIM_OK) return st;
+    pack_rows_from_csr(ctx, s);
+    return dense_layout_hubs(ctx, true, s);
+}
+
+bisim_status ensure_vertex_csr(bisim_ctx* ctx, cudaStream_t s) {
+    if (ctx->row_ptr != nullptr) return BISIM_OK;
+    if (!ctx->dense_ready) return set_error(ctx, BISIM_ESTATE, "no graph layout to rebuild the CSR from");
+    const int32_t n = ctx->n;
+    const int64_t m = ctx->m;
+    cudaError_t e;
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->row_ptr), sizeof(int64_t) * (n + 1), s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->col), sizeof(int32_t) * std::max<int64_t>(m, 1), s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->elab), sizeof(int32_t) * std::max<int64_t>(m, 1), s)))
+        return cuda_error(ctx, e, "alloc vertex-ordered CSR");
+    const size_t tmp_words = scan_temp_words(static_cast<int64_t>(n) + 1);
+    int64_t* scratch = nullptr;
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(int64_t) * (n + 1 + tmp_words), s)))
+        return cuda_error(ctx, e, "alloc CSR scratch");
+    const int64_t n_live = ctx->dbegin[kDClasses];
+    BISIM_SITE(site, "csr_from_layout");
+    {
+        Launch L(site, s, n, 0, 24.0 * n);
+        k_vertex_degrees<<<grid_for(n + 1, 256), 256, 0, s>>>(ctx->dvpos, n, n_live, ctx->dprp, scratch);
+    }
+    exclusive_scan_i64(scratch, ctx->row_ptr, n + 1, scratch + n + 1, s);
+    {
+        Launch L(site, s, n, m, 16.0 * m);
+        if (n > 0)
+            k_unpack_rows<<<grid_for(n, 256), 256, 0, s>>>(ctx->dvpos, n, n_live, ctx->dprp, ctx->dpe, ctx->row_ptr,
+                                                          ctx->col, ctx->elab);
+        const int64_t mid = ctx->dbegin[kDHub] - ctx->dbegin[kDMid0];
+        if (mid > 0)
+            k_unpack_big<<<static_cast<unsigned>(mid), 256, 0, s>>>(ctx->dvert, ctx->dbegin[kDMid0], ctx->dprp, ctx->dpe,
+                                                                   ctx->row_ptr, ctx->col, ctx->elab);
+        if (ctx->n_dchunks > 0)
+            k_unpack_chunks<<<static_cast<unsigned>(ctx->n_dchunks), 256, 0, s>>>(
+                ctx->dchunks, ctx->dvert, ctx->dbegin[kDHub], ctx->dprp, ctx->dpe, ctx->row_ptr, ctx->col, ctx->elab);
+    }
+    cudaFreeAsync(scratch, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "rebuild vertex-ordered CSR");
     ctx->stats.device_bytes = ctx->device_bytes;
     return BISIM_OK;
 }

@@ -47,19 +47,11 @@ __global__ void k_pack_coo(const int32_t* __restrict__ src, const int32_t* __res
     }
 }
 
-__global__ void k_widen(const int32_t* __restrict__ in, int64_t* __restrict__ out, int64_t n) {
-    int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = in[i];
-}
-
-__global__ void k_unpack(const uint64_t* __restrict__ vals, int64_t m, int32_t* __restrict__ col,
-                         int32_t* __restrict__ elab) {
+// Edge sort keys become positions of the layout: the sorted edges are then its packed rows.
+__global__ void k_rekey(uint32_t* __restrict__ keys, int64_t m, const int32_t* __restrict__ vpos) {
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        uint64_t v = vals[e];
-        col[e] = static_cast<int32_t>(static_cast<uint32_t>(v));
-        elab[e] = static_cast<int32_t>(static_cast<uint32_t>(v >> 32));
-    }
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        keys[e] = static_cast<uint32_t>(vpos[keys[e]]);
 }
 
 __global__ void k_validate_csr(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -171,36 +163,37 @@ int bits_for(int64_t n) {
 
 }  // namespace
 
+// COO -> the round layout directly: out-degrees, then the positions of the
+// layout (vertices grouped by degree class), then one stable LSD radix sort of
+// the edges keyed by their source's position. The sorted (label, target)
+// words are the layout's packed rows; the vertex-ordered CSR is rebuilt from
+// them only if an update or the list-mode path asks for it.
 bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* dst,
                             const int32_t* elab, cudaStream_t s) {
     const int32_t n = ctx->n;
     const int64_t m = ctx->m;
+    const int64_t cap = std::max<int64_t>(m, 1);
     cudaError_t e;
-    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->row_ptr), sizeof(int64_t) * (n + 1), s))) return cuda_error(ctx, e, "alloc row_ptr");
-    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->col), sizeof(int32_t) * std::max<int64_t>(m, 1), s))) return cuda_error(ctx, e, "alloc col");
-    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->elab), sizeof(int32_t) * std::max<int64_t>(m, 1), s))) return cuda_error(ctx, e, "alloc elab");
-    // scratch: keys x2, vals x2, degree counts, scan temp
     const size_t tmp_words = std::max(radix_temp_words(m), scan_temp_words(n + 1));
-    const size_t bytes = sizeof(uint32_t) * 2 * std::max<int64_t>(m, 1) + sizeof(uint64_t) * 2 * std::max<int64_t>(m, 1) +
-                         sizeof(int32_t) * (n + 1) + sizeof(int64_t) * (n + 1) + sizeof(int64_t) * tmp_words + 256 * 8;
+    const size_t bytes = sizeof(uint32_t) * 2 * cap + sizeof(int32_t) * (n + 1) + sizeof(int64_t) * tmp_words + 256 * 4;
     char* scratch = nullptr;
     if ((e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s))) return cuda_error(ctx, e, "alloc CSR scratch");
     auto carve = [&](size_t b) { char* p = scratch; scratch += (b + 255) & ~size_t(255); return p; };
     char* base = scratch;
-    uint32_t* k0 = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * std::max<int64_t>(m, 1)));
-    uint32_t* k1 = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * std::max<int64_t>(m, 1)));
-    uint64_t* v0 = reinterpret_cast<uint64_t*>(carve(sizeof(uint64_t) * std::max<int64_t>(m, 1)));
-    uint64_t* v1 = reinterpret_cast<uint64_t*>(carve(sizeof(uint64_t) * std::max<int64_t>(m, 1)));
+    uint32_t* k0 = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * cap));
+    uint32_t* k1 = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * cap));
     int32_t* deg = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (n + 1)));
-    int64_t* deg64 = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * (n + 1)));
     int64_t* tmp = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * tmp_words));
-    (void)bytes;
+    uint64_t *v0 = nullptr, *v1 = nullptr;
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&v0), sizeof(uint64_t) * cap, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&v1), sizeof(uint64_t) * cap, s))) {
+        cudaFreeAsync(base, s);
+        return cuda_error(ctx, e, "alloc packed rows");
+    }
 
     cudaMemsetAsync(&ctx->dstate->error, 0, sizeof(unsigned), s);
     BISIM_SITE(site_val, "validate_edges");
     BISIM_SITE(site_pack, "csr_pack");
-    BISIM_SITE(site_unpack, "csr_unpack");
-    BISIM_SITE(site_rp, "csr_row_ptr");
     if (m > 0)
         Launch(site_val, s, 0, m, 8.0 * m),
         k_validate_coo<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(src, dst, m, n, ctx->alive, &ctx->dstate->error);
@@ -212,22 +205,30 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
     }
     cudaMemsetAsync(deg, 0, sizeof(int32_t) * (n + 1), s);
     if (m > 0) {
+        Launch L(site_pack, s, 0, m, 24.0 * m);   // read src, dst, label; write key + value
+        k_pack_coo<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(src, dst, elab, m, k0, v0, deg);
+    }
+    bisim_status st = dense_layout_positions(ctx, deg, s);
+    if (st != BISIM_OK) {
+        cudaFreeAsync(base, s);
+        return st;
+    }
+    int which = 0;
+    if (m > 0) {
         {
-            Launch L(site_pack, s, 0, m, 24.0 * m);   // read src, dst, label; write key + value
-            k_pack_coo<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(src, dst, elab, m, k0, v0, deg);
+            Launch L(site_pack, s, 0, m, 12.0 * m);
+            k_rekey<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(k0, m, ctx->dvpos);
         }
-        int which = radix_sort_pairs(k0, v0, k1, v1, m, bits_for(n), tmp, s);
-        Launch L(site_unpack, s, 0, m, 16.0 * m);
-        k_unpack<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(which ? v1 : v0, m, ctx->col, ctx->elab);
+        which = radix_sort_pairs(k0, v0, k1, v1, m, bits_for(n), tmp, s);
     }
-    {
-        Launch L(site_rp, s, n + 1, 0, 12.0 * (n + 1));
-        k_widen<<<grid_for(n + 1, 256), 256, 0, s>>>(deg, deg64, n + 1);
-    }
-    exclusive_scan_i64(deg64, ctx->row_ptr, n + 1, tmp, s);
+    uint64_t* rows = which ? v1 : v0;
+    ctx_free(ctx, which ? v0 : v1, sizeof(uint64_t) * cap, s);
+    ctx_free(ctx, ctx->dpe, sizeof(unsigned long long) * ctx->dpe_cap, s);
+    ctx->dpe = reinterpret_cast<unsigned long long*>(rows);
+    ctx->dpe_cap = cap;
     cudaFreeAsync(base, s);
-    if ((e = cudaGetLastError())) return cuda_error(ctx, e, "build CSR");
-    return BISIM_OK;
+    if ((e = cudaGetLastError())) return cuda_error(ctx, e, "build layout");
+    return dense_layout_hubs(ctx, false, s);
 }
 
 bisim_status build_from_csr(bisim_ctx* ctx, const int64_t* row_ptr, const int32_t* col,
@@ -257,7 +258,9 @@ bisim_status build_from_csr(bisim_ctx* ctx, const int64_t* row_ptr, const int32_
 
 bisim_status ensure_buckets(bisim_ctx* ctx, cudaStream_t s) {
     if (ctx->buckets_ready) return BISIM_OK;
-    bisim_status st = build_buckets(ctx, s);
+    bisim_status st = ensure_vertex_csr(ctx, s);
+    if (st != BISIM_OK) return st;
+    st = build_buckets(ctx, s);
     if (st == BISIM_OK) ctx->buckets_ready = true;
     return st;
 }

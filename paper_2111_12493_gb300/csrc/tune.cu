@@ -57,6 +57,8 @@ extern "C" bisim_status bisim_autotune(bisim_ctx* ctx, int32_t rounds, bisim_opt
     ctx->last_stream = stream;
     bisim_status st;
     if ((st = refresh_after_edit(ctx, s)) != BISIM_OK) return st;
+    // candidates rebuild the layout from the vertex-ordered CSR
+    if ((st = dense_prepare(ctx, s)) != BISIM_OK || (st = ensure_vertex_csr(ctx, s)) != BISIM_OK) return st;
     if (ctx->n > 0) {
         struct Setting {
             int32_t* field;

@@ -381,6 +381,8 @@ void ctx_free(bisim_ctx* ctx, void* p, size_t bytes, cudaStream_t s) {
 // Per-edge source array for the current CSR (needed to rewrite it edge-parallel).
 bisim_status ensure_edge_sources(bisim_ctx* ctx, cudaStream_t s) {
     if (ctx->esrc != nullptr) return BISIM_OK;
+    bisim_status st = ensure_vertex_csr(ctx, s);
+    if (st != BISIM_OK) return st;
     cudaError_t e;
     if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->esrc), sizeof(int32_t) * std::max<int64_t>(ctx->m, 1), s)))
         return cuda_error(ctx, e, "alloc edge sources");
