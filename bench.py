@@ -373,7 +373,8 @@ def run_ours(args, world, rank, local):
     kernels = None
     if top and top["total_ms"] > 0:
         achieved = top["alg_bytes"] / (top["total_ms"] / 1e3) / 1e9
-        traffic = NCU_TRAFFIC_BYTES.get(top["name"])
+        # the captured traffic is for the headline launch size only
+        traffic = NCU_TRAFFIC_BYTES.get(top["name"]) if (W.name == "powerlaw" and args.scale == 1.0) else None
         roofline = {"bound": "hbm", "kernel": top["name"], "achieved": round(achieved, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
                     "traffic": traffic, "alg_bytes_per_launch": top["alg_bytes"] / max(1, top["launches"]),

@@ -458,6 +458,7 @@ bisim_status summarize_init_batched(bisim_ctx** out, int32_t n_graphs, const int
     }
     if (st == BISIM_OK)
         st = build_from_coo(ctx, gsrc, gdst, static_cast<const int32_t*>(dl), s);
+    if (st == BISIM_OK) st = dense_region_table(ctx, hv.data(), n_graphs, s);
     free_temps(temps, s);
     if (deoff) cudaFreeAsync(deoff, s);
     if (gsrc) cudaFreeAsync(gsrc, s);

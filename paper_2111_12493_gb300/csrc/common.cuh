@@ -104,14 +104,13 @@ struct TableRef {
     uint64_t mask;        // nslots - 1
     uint64_t epoch;       // 1..15, already shifted into bits 32..35
     uint64_t hmask;       // hash width mask (tests only narrow it)
-    uint64_t pmask;       // probing wraps inside aligned parts of pmask + 1 slots (pmask = mask: one part)
 };
 
 struct DevState {
     unsigned long long blocks;      // vertices that are the minimum of their block
     unsigned int unresolved;        // vertices pushed to the next collision level
     unsigned int error;             // kErr* bits
-    unsigned long long aux;
+    unsigned long long aux;         // dense rounds: row words read by the exact set comparisons
     unsigned int deferred;          // vertices whose set comparison is left to k_verify_deferred
     unsigned int pairs;             // dense rounds: small pairs left to a warp comparison
 };
@@ -120,16 +119,17 @@ __device__ __forceinline__ unsigned long long table_read(const TableRef& t, uint
     return *reinterpret_cast<volatile unsigned long long*>(&t.slots[pos].w);
 }
 
-// Insert `h` (already masked) for vertex v, given the first probe slot's value
-// `cur` as read by the caller (so that callers can issue several first reads
-// at once); returns the slot index or ~0u on overflow.
-__device__ __forceinline__ uint32_t table_insert_from(const TableRef& t, uint64_t h, int32_t v,
-                                                      unsigned long long cur, unsigned* err) {
+// Insert `h` (already masked) for vertex v into the region [base, base + mask]
+// of the table (mask + 1 a power of two; probing wraps inside the region);
+// returns the slot index or ~0u on overflow.
+__device__ __forceinline__ uint32_t table_insert_in(const TableRef& t, uint64_t h, int32_t v, uint64_t base,
+                                                    uint64_t mask, unsigned* err) {
     const unsigned long long tag = (h & ~0xfffffffffull) | t.epoch;
     const unsigned long long want = tag | static_cast<uint32_t>(v);
-    uint64_t pos = h & t.mask;
-    for (uint64_t probe = 0; probe <= t.pmask; ++probe) {
-        if (probe > 0) cur = table_read(t, pos);
+    uint64_t off = h & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+        const uint64_t pos = base + off;
+        unsigned long long cur = table_read(t, pos);
         for (;;) {
             if ((cur & kSlotEpochMask) != t.epoch) {            // free in this epoch: claim it
                 const unsigned long long prev = atomicCAS(&t.slots[pos].w, cur, want);
@@ -149,15 +149,15 @@ __device__ __forceinline__ uint32_t table_insert_from(const TableRef& t, uint64_
             }
             break;                                               // another signature: probe on
         }
-        pos = (pos & ~t.pmask) | ((pos + 1) & t.pmask);
+        off = (off + 1) & mask;
     }
     atomicOr(err, kErrTableFull);
     return ~0u;
 }
 
-// Insert `h` (already masked) for vertex v; returns the slot index or ~0u on overflow.
+// Insert `h` (already masked) for vertex v anywhere in the table.
 __device__ __forceinline__ uint32_t table_insert(const TableRef& t, uint64_t h, int32_t v, unsigned* err) {
-    return table_insert_from(t, h, v, table_read(t, h & t.mask), err);
+    return table_insert_in(t, h, v, 0, t.mask, err);
 }
 
 __device__ __forceinline__ int32_t table_rep(const Slot* slots, uint32_t pos) {
@@ -293,6 +293,10 @@ struct bisim_ctx {
     int64_t dpe_cap = 0;
     int64_t dbegin[bisim::kDClasses + 1] = {};       // class -> first position; dbegin[kDClasses] = n_live
     int64_t dedge_begin[bisim::kDClasses + 1] = {};  // class -> first packed edge
+    bisim::Slot* rtable = nullptr;                   // batched contexts: one table region per graph
+    uint64_t n_rslots = 0;
+    int64_t* rbase = nullptr;                        // [n_graphs] first slot of the graph's region
+    uint32_t* rmask = nullptr;                       // [n_graphs] region size - 1 (a power of two)
     uint32_t* dslot = nullptr;                       // [n] table slot per position
     unsigned long long* dhash = nullptr;             // [n] signature hash per position
     int32_t* dcnt = nullptr;                         // [n] |S| per position
@@ -439,6 +443,9 @@ bisim_status dense_layout_positions(bisim_ctx* ctx, const int32_t* deg, cudaStre
 // pack_from_csr, copying the hub rows from the vertex-ordered CSR); marks the
 // layout ready.
 bisim_status dense_layout_hubs(bisim_ctx* ctx, bool pack_from_csr, cudaStream_t s);
+// Batched contexts: one signature-table region per graph (sized for the graph,
+// load <= 0.6), so that the inserts of a graph's vertices stay in a small span.
+bisim_status dense_region_table(bisim_ctx* ctx, const int64_t* voff_host, int32_t n_graphs, cudaStream_t s);
 // The vertex-ordered CSR (row_ptr, col, elab), rebuilt from the layout when a
 // context was built straight into it (updates and list-mode paths need it).
 bisim_status ensure_vertex_csr(bisim_ctx* ctx, cudaStream_t s);

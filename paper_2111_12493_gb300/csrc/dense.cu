@@ -307,6 +307,9 @@ struct DenseView {
     int32_t* cnt;                      // |S|, by position
     unsigned long long* hash;          // signature hash, by position
     uint32_t* slot;                    // table slot, by position
+    const int32_t* gid;                // batched contexts: graph of each vertex (null: one graph)
+    const int64_t* rbase;              // batched contexts: the graph's table region
+    const uint32_t* rmask;
 };
 
 struct WarpPlan {
@@ -631,7 +634,16 @@ __global__ void __launch_bounds__(kThreads) k_dense_insert(const int32_t* __rest
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const int64_t pos = list ? list[i] : i;
-    D.slot[pos] = table_insert(t, level_hash(D.hash[pos], level, t.hmask), D.vert[pos], err);
+    const int32_t v = D.vert[pos];
+    const uint64_t h = level_hash(D.hash[pos], level, t.hmask);
+    if (D.gid) {
+        // batched graphs: each graph has its own region of the table, so that
+        // the inserts of consecutive positions (mostly one graph) stay close
+        const int32_t g = D.gid[v];
+        D.slot[pos] = table_insert_in(t, h, v, static_cast<uint64_t>(D.rbase[g]), D.rmask[g], err);
+    } else {
+        D.slot[pos] = table_insert(t, h, v, err);
+    }
 }
 
 struct VerifyOut {
@@ -698,6 +710,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_verify(const int32_t* __rest
 }
 
 constexpr int kCompareGrid = 304;                      // persistent grids: two CTAs per SM
+constexpr int kCompareWarpGrid = 1216;                 // eight per SM: a warp per pair, all warps in flight
 
 // Pairs whose rows have at most 32 edges: one warp per pair. Lane j holds the
 // j-th pair value of each row; S_v is inside S_r iff every value of v's row
@@ -715,6 +728,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_compare_warp(const int2* __r
         const bool ha = lane < dv, hb = lane < dr;
         const uint64_t a = ha ? packed_pair_value(D.pe[ev + lane], D.P) : 0ull;
         const uint64_t b = hb ? packed_pair_value(D.pe[er + lane], D.P) : 0ull;
+        if (lane == 0) atomicAdd(&st->aux, static_cast<unsigned long long>(dv + dr));
         bool found = false;
         for (int k = 0; k < static_cast<int>(dr); ++k) {
             const uint64_t bk = __shfl_sync(0xffffffffu, b, k);   // every lane takes part in every shuffle
@@ -791,6 +805,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_compare_cta(const int2* __re
         }
         const int any = __syncthreads_or(miss ? 1 : 0);
         if (threadIdx.x == 0) {
+            atomicAdd(&st->aux, static_cast<unsigned long long>((dv + dr) * static_cast<int64_t>(splits > 1 ? splits / 2 : 1)));
             if (!any) Pout[D.vert[pr.x]] = D.vert[pr.y];
             else next[atomicAdd(&st->unresolved, 1u)] = pr.x;
         }
@@ -909,6 +924,23 @@ void set_attributes() {
     });
 }
 
+// The table the rounds insert into: the global one, or the per-graph regions of a batched context.
+Slot* round_slots(const bisim_ctx* ctx) { return ctx->rtable ? ctx->rtable : ctx->table; }
+
+// A fresh level of the renumbering: a new epoch of the global table, or a
+// cleared region table (epoch 1) for batched contexts.
+TableRef level_table(bisim_ctx* ctx, cudaStream_t s) {
+    if (ctx->rtable == nullptr) return next_epoch(ctx, s);
+    cudaMemsetAsync(ctx->rtable, 0, sizeof(Slot) * ctx->n_rslots, s);
+    TableRef t;
+    t.slots = ctx->rtable;
+    t.mask = ctx->n_rslots - 1;     // not used by region inserts
+    t.epoch = uint64_t{1} << 32;
+    const int hb = ctx->opt.hash_bits;
+    t.hmask = hb >= 64 ? ~0ull : ((1ull << hb) - 1ull);
+    return t;
+}
+
 // Insert, verification and set comparisons of one level (level 0: every live
 // position; then the listed ones). Unresolved positions go to `next`.
 void launch_level(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const TableRef& t, uint32_t level,
@@ -927,19 +959,22 @@ void launch_level(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const Tabl
     }
     {
         Launch L(site_v, s, count, 0, kVerifyVertexBytes * count);
-        k_dense_verify<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, ctx->table, O, ctx->n);
+        k_dense_verify<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, round_slots(ctx), O, ctx->n);
     }
     {
         Launch L(site_cw, s, 0, 0, 0.0);
-        k_dense_compare_warp<<<kCompareGrid, kThreads, 0, s>>>(ctx->dsmall, D, Pout, next, ctx->dstate);
+        k_dense_compare_warp<<<kCompareWarpGrid, kThreads, 0, s>>>(ctx->dsmall, D, Pout, next, ctx->dstate);
     }
     Launch L(site_cc, s, 0, 0, 0.0);
     k_dense_compare_cta<<<kCompareGrid, kThreads, kCompareSmem, s>>>(ctx->dpairs, D, H, Pout, next, ctx->dstate);
 }
 
 DenseView dense_view(bisim_ctx* ctx) {
-    return DenseView{ctx->dvert, ctx->dvpos, ctx->dprp, ctx->dpe, ctx->P[ctx->cur], ctx->dcnt, ctx->dhash, ctx->dslot};
+    const bool regions = ctx->rtable != nullptr;
+    return DenseView{ctx->dvert, ctx->dvpos, ctx->dprp, ctx->dpe, ctx->P[ctx->cur], ctx->dcnt, ctx->dhash, ctx->dslot,
+                     regions ? ctx->gid : nullptr, ctx->rbase, ctx->rmask};
 }
+
 
 // Everything of one round P[cur] -> P[cur ^ 1] that needs no host decision:
 // signatures of every class, then level 0 of the renumbering.
@@ -1024,13 +1059,20 @@ bisim_status finish_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
         if (level > static_cast<uint32_t>(kMaxLevels))
             return set_error(ctx, BISIM_ETIMEOUT, "hash collision resolution did not converge");
         const int64_t count = ctx->hstate->unresolved;
-        TableRef t = next_epoch(ctx, s);
+        TableRef t = level_table(ctx, s);
         cudaMemsetAsync(&ctx->dstate->unresolved, 0, sizeof(unsigned), s);
         cudaMemsetAsync(&ctx->dstate->deferred, 0, sizeof(unsigned), s);
         cudaMemsetAsync(&ctx->dstate->pairs, 0, sizeof(unsigned), s);
         launch_level(ctx, s, D, t, level, ctx->ulist[which], count, ctx->ulist[which ^ 1]);
         which ^= 1;
         ctx->stats.collision_levels += 1;
+    }
+    if (prof_enabled()) {
+        // the exact comparisons' work is known only now: 12 bytes per row word read
+        // (packed word + gathered block id) plus two row offsets per pair
+        BISIM_SITE(site_cmp, "dense_compare_warp");
+        const double pairs = static_cast<double>(ctx->hstate->pairs) + static_cast<double>(ctx->hstate->deferred);
+        prof_add_bytes(site_cmp, 12.0 * static_cast<double>(ctx->hstate->aux) + 32.0 * pairs);
     }
     if (ctx->hstate->error & kErrTableFull) return set_error(ctx, BISIM_ETIMEOUT, "signature table probe limit reached");
     if (ctx->hstate->error & kErrHubFull) return set_error(ctx, BISIM_ETIMEOUT, "hub set probe limit reached");
@@ -1260,6 +1302,31 @@ bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
     return dense_layout_hubs(ctx, true, s);
 }
 
+bisim_status dense_region_table(bisim_ctx* ctx, const int64_t* voff_host, int32_t n_graphs, cudaStream_t s) {
+    std::vector<int64_t> base(n_graphs);
+    std::vector<uint32_t> mask(n_graphs);
+    uint64_t total = 0;
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        const int64_t ng = voff_host[g + 1] - voff_host[g];
+        uint64_t sz = 64;
+        while (static_cast<double>(sz) * 0.6 < static_cast<double>(ng)) sz <<= 1;
+        base[g] = static_cast<int64_t>(total);
+        mask[g] = static_cast<uint32_t>(sz - 1);
+        total += sz;
+    }
+    if (total >= (uint64_t{1} << 32)) return BISIM_OK;     // slot indices are 32-bit: keep the global table
+    cudaError_t e;
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->rtable), sizeof(Slot) * total, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->rbase), sizeof(int64_t) * n_graphs, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->rmask), sizeof(uint32_t) * n_graphs, s)))
+        return cuda_error(ctx, e, "alloc table regions");
+    ctx->n_rslots = total;
+    cudaMemcpyAsync(ctx->rbase, base.data(), sizeof(int64_t) * n_graphs, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(ctx->rmask, mask.data(), sizeof(uint32_t) * n_graphs, cudaMemcpyHostToDevice, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "upload table regions");
+    return BISIM_OK;
+}
+
 bisim_status ensure_vertex_csr(bisim_ctx* ctx, cudaStream_t s) {
     if (ctx->row_ptr != nullptr) return BISIM_OK;
     if (!ctx->dense_ready) return set_error(ctx, BISIM_ESTATE, "no graph layout to rebuild the CSR from");
@@ -1310,7 +1377,7 @@ void dense_mark_dead(bisim_ctx* ctx, cudaStream_t s) {
 
 bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     set_attributes();
-    const TableRef t = next_epoch(ctx, s);
+    const TableRef t = level_table(ctx, s);
     launch_round(ctx, s, t);
     return finish_round(ctx, s, out_blocks);
 }
@@ -1325,12 +1392,11 @@ namespace {
 // fixed epoch; the eager rounds' epochs (next_epoch) never reuse it without a clear.
 TableRef fixed_table(const bisim_ctx* ctx) {
     TableRef t;
-    t.slots = ctx->table;
-    t.mask = ctx->nslots - 1;
+    t.slots = round_slots(ctx);
+    t.mask = ctx->rtable ? ctx->n_rslots - 1 : ctx->nslots - 1;
     t.epoch = uint64_t{1} << 32;
     const int hb = ctx->opt.hash_bits;
     t.hmask = hb >= 64 ? ~0ull : ((1ull << hb) - 1ull);
-    t.pmask = t.mask;
     return t;
 }
 
@@ -1380,7 +1446,7 @@ bisim_status build_round_graph(bisim_ctx* ctx) {
         cudaGraphDestroy(g);
         return cuda_error(ctx, e, "capture round");
     }
-    cudaMemsetAsync(ctx->table, 0, sizeof(Slot) * ctx->nslots, cs);
+    cudaMemsetAsync(round_slots(ctx), 0, sizeof(Slot) * (ctx->rtable ? ctx->n_rslots : ctx->nslots), cs);
     launch_round(ctx, cs, fixed_table(ctx));
     LoopState* L = static_cast<LoopState*>(ctx->dloop);
     {

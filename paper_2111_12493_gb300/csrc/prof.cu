@@ -77,6 +77,11 @@ bool prof_enabled() { return g_enabled.load(std::memory_order_relaxed); }
 
 void prof_add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+void prof_add_bytes(int site, double bytes) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (site >= 0 && site < static_cast<int>(g_sites.size())) g_sites[site].bytes += bytes;
+}
+
 Launch::Launch(int site, cudaStream_t s, int64_t vertices, int64_t edges, double alg_bytes)
     : site_(site), s_(s), vertices_(vertices), edges_(edges), bytes_(alg_bytes) {
     g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -14,6 +14,8 @@ int prof_site(const char* name);
 bool prof_enabled();
 // Adjusts the launch counter for kernels that run inside a graph replay.
 void prof_add_launches(int64_t n);
+// Adds algorithmic bytes to a site after its launches (work known only once they ran).
+void prof_add_bytes(int site, double bytes);
 
 // Brackets one kernel launch: counts it and, when profiling is enabled,
 // records events around it on stream `s`.

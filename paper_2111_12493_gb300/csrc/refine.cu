@@ -541,7 +541,6 @@ TableRef next_epoch(bisim_ctx* ctx, cudaStream_t s) {
     t.epoch = static_cast<uint64_t>(e) << 32;
     const int hb = ctx->opt.hash_bits;
     t.hmask = hb >= 64 ? ~0ull : ((1ull << hb) - 1ull);
-    t.pmask = t.mask;
     return t;
 }
 
