@@ -264,7 +264,7 @@ bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, 
     if (ctx->opt.mem_budget_bytes > 0 && ctx->device_bytes > ctx->opt.mem_budget_bytes)
         return set_error(ctx, BISIM_ENOMEM, "context exceeds the memory budget");
     if (ctx->n > 0) cudaMemcpyAsync(ctx->P[0], ctx->P0, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToDevice, s);
-    dense_mark_dead(ctx, s);
+    dense_start(ctx, s);
     ctx->cur = 0;
     int64_t prev = ctx->last_blocks;   // |P_0|
     const bool fixpoint = k == BISIM_FIXPOINT;

@@ -113,6 +113,8 @@ struct DevState {
     unsigned long long aux;         // dense rounds: row words read by the exact set comparisons
     unsigned int deferred;          // vertices whose set comparison is left to k_verify_deferred
     unsigned int pairs;             // dense rounds: small pairs left to a warp comparison
+    unsigned int listed;            // dense rounds: positions that need the table this round
+    unsigned int pad;
 };
 
 __device__ __forceinline__ unsigned long long table_read(const TableRef& t, uint64_t pos) {
@@ -302,6 +304,8 @@ struct bisim_ctx {
     int32_t* dcnt = nullptr;                         // [n] |S| per position
     int2* dpairs = nullptr;                          // [n] (position, representative's position) for a CTA compare
     int2* dsmall = nullptr;                          // [n] the same for rows of at most 32 edges (warp compare)
+    uint8_t* djoined = nullptr;                      // [n] by position: another vertex joined this one's block last round
+    uint8_t* downs = nullptr;                        // [n] by position: the vertex was its block's id last round
     bisim::HubChunk* dchunks = nullptr;              // hub rows cut into chunks of at most 4096 edges
     int64_t n_dchunks = 0;
     int64_t n_dhub = 0;
@@ -451,6 +455,8 @@ bisim_status dense_region_table(bisim_ctx* ctx, const int64_t* voff_host, int32_
 bisim_status ensure_vertex_csr(bisim_ctx* ctx, cudaStream_t s);
 // Writes -1 for the dead vertices into both partition buffers.
 void dense_mark_dead(bisim_ctx* ctx, cudaStream_t s);
+// Prepares a run of rounds from P_0: dead vertices, and no block known to be a singleton.
+void dense_start(bisim_ctx* ctx, cudaStream_t s);
 // One refinement round P[cur] -> P[cur ^ 1] over every live vertex.
 bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks);
 // Finishes a round stopped by the device-side loop at a hash collision.

@@ -58,22 +58,34 @@ __device__ __forceinline__ int ceil_log2(int64_t d) {
     return d <= 1 ? 0 : 64 - __clzll(static_cast<unsigned long long>(d - 1));
 }
 
-// Appends `flag` lanes' values to list[*counter ...] with one atomic per warp.
-template <class T>
-__device__ __forceinline__ void warp_push(bool flag, T value, T* list, unsigned* counter) {
-    const unsigned b = __ballot_sync(0xffffffffu, flag);
-    if (b == 0u) return;
-    const int leader = __ffs(b) - 1;
-    unsigned base = 0;
-    if (static_cast<int>(lane_id()) == leader) base = atomicAdd(counter, static_cast<unsigned>(__popc(b)));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (flag) list[base + __popc(b & lanemask_lt())] = value;
+// Block-aggregated list appends and counts: one atomic per CTA rather than per warp, which
+// matters when a whole grid adds to a single counter (tens of thousands of
+// warps on one address serialise in L2). Every thread of the CTA must call
+// them; `sh` holds kThreads / 32 + 1 words of shared memory.
+__device__ __forceinline__ void block_count(bool flag, unsigned long long* counter) {
+    const int c = __syncthreads_count(flag);
+    if (threadIdx.x == 0 && c) atomicAdd(counter, static_cast<unsigned long long>(c));
 }
 
-__device__ __forceinline__ void warp_count(bool flag, unsigned long long* counter) {
+template <class T>
+__device__ __forceinline__ void block_push(bool flag, T value, T* list, unsigned* counter, unsigned* sh) {
+    constexpr int W = kThreads / 32;
     const unsigned b = __ballot_sync(0xffffffffu, flag);
-    if (b != 0u && static_cast<int>(lane_id()) == __ffs(b) - 1)
-        atomicAdd(counter, static_cast<unsigned long long>(__popc(b)));
+    const int w = static_cast<int>(threadIdx.x >> 5);
+    if (lane_id() == 0) sh[w] = static_cast<unsigned>(__popc(b));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned total = 0;
+        for (int q = 0; q < W; ++q) {
+            const unsigned c = sh[q];
+            sh[q] = total;
+            total += c;
+        }
+        sh[W] = total ? atomicAdd(counter, total) : 0u;
+    }
+    __syncthreads();
+    if (flag) list[sh[W] + sh[w] + __popc(b & lanemask_lt())] = value;
+    __syncthreads();                                 // sh is free for the next call
 }
 
 // ----------------------------------------------------------------------------- layout kernels
@@ -307,6 +319,8 @@ struct DenseView {
     int32_t* cnt;                      // |S|, by position
     unsigned long long* hash;          // signature hash, by position
     uint32_t* slot;                    // table slot, by position
+    uint8_t* joined;                   // by position: another vertex joined its block in the last round
+    uint8_t* own;                      // by position: the vertex was its block's id (smallest member) in the last round
     const int32_t* gid;                // batched contexts: graph of each vertex (null: one graph)
     const int64_t* rbase;              // batched contexts: the graph's table region
     const uint32_t* rmask;
@@ -317,6 +331,13 @@ struct WarpPlan {
     int64_t pos_begin[3];
     int64_t pos_end[3];
 };
+
+// A vertex alone in its block of P_i stays alone in P_{i+1}: no signature is
+// needed (the level-0 scan settles it without the table). Read before that scan
+// clears the joined flags.
+__device__ __forceinline__ bool alone_last_round(const DenseView& D, int64_t pos) {
+    return D.own[pos] && !D.joined[pos];
+}
 
 __device__ __forceinline__ void finish_sig(const DenseView& D, int64_t pos, int32_t own, uint32_t c, uint64_t sum) {
     D.cnt[pos] = static_cast<int32_t>(c);
@@ -330,6 +351,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_thread_sig(int64_t first, in
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const int64_t pos = first + i;
+    if (alone_last_round(V, pos)) return;
     const int32_t own = V.P[V.vert[pos]];
     const int64_t e0 = V.prp[pos];
     const int d = static_cast<int>(V.prp[pos + 1] - e0);
@@ -364,7 +386,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_warp_sig(const WarpPlan plan
     const int warp = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     const int64_t pos = pos0 + (b - cta0) * (kThreads / 32) + warp;
-    if (pos >= pos1) return;                             // whole warp leaves together
+    if (pos >= pos1 || alone_last_round(D, pos)) return;  // whole warp leaves together
     const int32_t own = lane == 0 ? D.P[D.vert[pos]] : 0;
     const int64_t e0 = D.prp[pos];
     const int d = static_cast<int>(D.prp[pos + 1] - e0);
@@ -401,6 +423,7 @@ __global__ void __launch_bounds__(T) k_dense_mid_sig(int64_t first, const DenseV
     __shared__ unsigned zero;
     constexpr uint32_t mask = 2 * N - 1;
     const int64_t pos = first + blockIdx.x;
+    if (alone_last_round(D, pos)) return;               // whole CTA leaves together
     const int64_t e0 = D.prp[pos];
     const int d = static_cast<int>(D.prp[pos + 1] - e0);
     for (int j = threadIdx.x; j < 2 * N; j += T) tab[j] = 0ull;
@@ -459,6 +482,7 @@ struct HubSets {
 };
 
 constexpr uint64_t kSaltBucket = 0x452821e638d01377ull;
+constexpr uint64_t kSaltGraph = 0xbe5466cf34e90c6cull;
 constexpr int kHubMaxBuckets = 2048;            // per hub
 constexpr int kHubBucketTarget = 1024;          // values per bucket aimed at
 constexpr int kHubSetSlots = 4096;              // shared-memory set of a bucket pass (32 KB)
@@ -628,21 +652,71 @@ __global__ void k_dense_hub_finalize(const DenseView D, const HubSets H) {
 
 // Table insert of every listed position (level 0: all live positions, list ==
 // null) with the level's salted hash.
+// Level 0 of a round, first pass: a vertex alone in its block of P_i stays
+// alone in P_{i+1} (every round refines the last) and needs no slot; the other
+// positions are listed for the table. Alone vertices are counted as blocks and,
+// unless the output buffer already holds P_i, get P_{i+1}[v] = v here. The
+// joined flags are cleared for this round's verification to set again.
+__global__ void __launch_bounds__(kThreads) k_alone_scan(int64_t count, const DenseView D, int32_t* __restrict__ Pout,
+                                                         bool out_has_in, int32_t* __restrict__ list, DevState* st) {
+    const int64_t pos = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    bool alone = false, listed = false;
+    if (pos < count) {
+        alone = alone_last_round(D, pos);
+        D.joined[pos] = 0;
+        listed = !alone;
+        if (alone && !out_has_in) {
+            const int32_t v = D.vert[pos];
+            Pout[v] = v;
+        }
+    }
+    __shared__ unsigned sh[kThreads / 32 + 1];
+    block_count(alone, &st->blocks);
+    block_push(listed, static_cast<int32_t>(pos), list, &st->listed, sh);
+}
+
+// Table insert of the listed positions with the level's salted hash. The count
+// is read on the device when `dcount` is given (level 0), else it is `count`.
+constexpr int kPersistGrid = 152 * 8;            // full occupancy of 256-thread CTAs
 __global__ void __launch_bounds__(kThreads) k_dense_insert(const int32_t* __restrict__ list, int64_t count,
-                                                           const DenseView D, uint32_t level, const TableRef t,
-                                                           unsigned* err) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const int64_t pos = list ? list[i] : i;
-    const int32_t v = D.vert[pos];
-    const uint64_t h = level_hash(D.hash[pos], level, t.hmask);
-    if (D.gid) {
-        // batched graphs: each graph has its own region of the table, so that
-        // the inserts of consecutive positions (mostly one graph) stay close
-        const int32_t g = D.gid[v];
-        D.slot[pos] = table_insert_in(t, h, v, static_cast<uint64_t>(D.rbase[g]), D.rmask[g], err);
-    } else {
-        D.slot[pos] = table_insert(t, h, v, err);
+                                                           const unsigned* dcount, const DenseView D, uint32_t level,
+                                                           const TableRef t, unsigned* err) {
+    if (dcount) count = *reinterpret_cast<const volatile unsigned*>(dcount);
+    const unsigned lane = lane_id();
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < count; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        const bool ins = i < count;
+        int64_t pos = -1;
+        int32_t v = -1;
+        uint64_t h = 0, key = 0;
+        if (ins) {
+            pos = list[i];
+            v = D.vert[pos];
+            h = level_hash(D.hash[pos], level, t.hmask);
+            key = D.gid ? h ^ mix64(static_cast<uint64_t>(D.gid[v]) + kSaltGraph) : h;
+        }
+        const unsigned insm = __ballot_sync(0xffffffffu, ins);
+        // lanes inserting one hash (of one graph) share the slot: only the smallest
+        // vertex among them goes to the table, which keeps popular signatures (big
+        // blocks) from piling atomics onto one slot
+        const unsigned peers = __match_any_sync(0xffffffffu, ins ? key : ~static_cast<uint64_t>(lane)) & insm;
+        if (ins) {
+            const unsigned vmin = __reduce_min_sync(peers, static_cast<unsigned>(v));
+            const int leader = __ffs(__ballot_sync(peers, static_cast<unsigned>(v) == vmin)) - 1;
+            uint32_t slot = 0;
+            if (static_cast<int>(lane) == leader) {
+                if (D.gid) {
+                    // batched graphs: each graph has its own region of the table, so
+                    // that the inserts of one graph's vertices stay close together
+                    const int32_t g = D.gid[v];
+                    slot = table_insert_in(t, h, v, static_cast<uint64_t>(D.rbase[g]), D.rmask[g], err);
+                } else {
+                    slot = table_insert(t, h, v, err);
+                }
+            }
+            D.slot[pos] = __shfl_sync(peers, slot, leader);
+        }
     }
 }
 
@@ -659,54 +733,65 @@ struct VerifyOut {
 // position moves to the next level. Otherwise the sets are compared: here when
 // both rows have at most two edges, else in a warp (rows <= 32) or a CTA.
 __global__ void __launch_bounds__(kThreads) k_dense_verify(const int32_t* __restrict__ list, int64_t count,
-                                                           const DenseView D, const Slot* __restrict__ slots,
-                                                           const VerifyOut O, int32_t n_total) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    bool own = false, push = false, small = false, big = false;
-    int64_t pos = -1, rpos = -1;
-    if (i < count) pos = list ? list[i] : i;
-    if (pos >= 0) {
-        const int32_t v = D.vert[pos];
-        const uint32_t sv = D.slot[pos];
-        const int32_t r = sv == ~0u ? -1 : table_rep(slots, sv);
-        if (r < 0 || r >= n_total) {                     // failed insert, reported through st->error
-            atomicOr(&O.st->error, kErrTableFull);
-            O.Pout[v] = -1;
-        } else if (r == v) {
-            O.Pout[v] = v;
-            own = true;
-        } else {
-            rpos = D.vpos[r];
-            if (D.P[v] != D.P[r] || D.cnt[pos] != D.cnt[rpos]) {
-                push = true;
+                                                           const unsigned* dcount, const DenseView D,
+                                                           const Slot* __restrict__ slots, const VerifyOut O,
+                                                           int32_t n_total) {
+    __shared__ unsigned sh[kThreads / 32 + 1];
+    if (dcount) count = *reinterpret_cast<const volatile unsigned*>(dcount);
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < count; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        bool own = false, push = false, small = false, big = false;
+        int64_t pos = -1, rpos = -1;
+        if (i < count) pos = list[i];
+        if (pos >= 0) {
+            const int32_t v = D.vert[pos];
+            const uint32_t sv = D.slot[pos];
+            const int32_t r = sv == ~0u ? -1 : table_rep(slots, sv);
+            if (r < 0 || r >= n_total) {                     // failed insert, reported through st->error
+                atomicOr(&O.st->error, kErrTableFull);
+                O.Pout[v] = -1;
+            } else if (r == v) {
+                O.Pout[v] = v;
+                D.own[pos] = 1;
+                own = true;
             } else {
-                const int64_t ev = D.prp[pos], dv = D.prp[pos + 1] - ev;
-                const int64_t er = D.prp[rpos], dr = D.prp[rpos + 1] - er;
-                if (dv <= 2 && dr <= 2) {
-                    // S_v inside S_r with equal sizes means equal sets
-                    uint64_t b0 = 0, b1 = 0;
-                    if (dr > 0) b0 = packed_pair_value(D.pe[er], D.P);
-                    if (dr > 1) b1 = packed_pair_value(D.pe[er + 1], D.P);
-                    bool ok = true;
-                    for (int64_t j = 0; j < dv; ++j) {
-                        const uint64_t a = packed_pair_value(D.pe[ev + j], D.P);
-                        ok = ok && ((dr > 0 && a == b0) || (dr > 1 && a == b1));
-                    }
-                    if (ok) O.Pout[v] = r;
-                    else push = true;
-                } else if (dv <= 32 && dr <= 32) {
-                    small = true;
+                rpos = D.vpos[r];
+                D.own[pos] = 0;
+                if (D.P[v] != D.P[r] || D.cnt[pos] != D.cnt[rpos]) {
+                    push = true;
                 } else {
-                    big = true;
+                    const int64_t ev = D.prp[pos], dv = D.prp[pos + 1] - ev;
+                    const int64_t er = D.prp[rpos], dr = D.prp[rpos + 1] - er;
+                    if (dv <= 2 && dr <= 2) {
+                        // S_v inside S_r with equal sizes means equal sets
+                        uint64_t b0 = 0, b1 = 0;
+                        if (dr > 0) b0 = packed_pair_value(D.pe[er], D.P);
+                        if (dr > 1) b1 = packed_pair_value(D.pe[er + 1], D.P);
+                        bool ok = true;
+                        for (int64_t j = 0; j < dv; ++j) {
+                            const uint64_t a = packed_pair_value(D.pe[ev + j], D.P);
+                            ok = ok && ((dr > 0 && a == b0) || (dr > 1 && a == b1));
+                        }
+                        if (ok) {
+                            O.Pout[v] = r;
+                            D.joined[rpos] = 1;
+                        }
+                        else push = true;
+                    } else if (dv <= 32 && dr <= 32) {
+                        small = true;
+                    } else {
+                        big = true;
+                    }
                 }
             }
         }
+        const int32_t p32 = static_cast<int32_t>(pos);
+        block_count(own, &O.st->blocks);
+        block_push(push, p32, O.next, &O.st->unresolved, sh);
+        block_push(small, make_int2(p32, static_cast<int32_t>(rpos)), O.small, &O.st->pairs, sh);
+        block_push(big, make_int2(p32, static_cast<int32_t>(rpos)), O.pairs, &O.st->deferred, sh);
     }
-    const int32_t p32 = static_cast<int32_t>(pos);
-    warp_count(own, &O.st->blocks);
-    warp_push(push, p32, O.next, &O.st->unresolved);
-    warp_push(small, make_int2(p32, static_cast<int32_t>(rpos)), O.small, &O.st->pairs);
-    warp_push(big, make_int2(p32, static_cast<int32_t>(rpos)), O.pairs, &O.st->deferred);
 }
 
 constexpr int kCompareGrid = 304;                      // persistent grids: two CTAs per SM
@@ -736,7 +821,10 @@ __global__ void __launch_bounds__(kThreads) k_dense_compare_warp(const int2* __r
         }
         const bool miss = __any_sync(0xffffffffu, ha && !found);
         if (lane == 0) {
-            if (!miss) Pout[D.vert[pr.x]] = D.vert[pr.y];
+            if (!miss) {
+                Pout[D.vert[pr.x]] = D.vert[pr.y];
+                D.joined[pr.y] = 1;
+            }
             else next[atomicAdd(&st->unresolved, 1u)] = pr.x;
         }
     }
@@ -806,7 +894,10 @@ __global__ void __launch_bounds__(kThreads) k_dense_compare_cta(const int2* __re
         const int any = __syncthreads_or(miss ? 1 : 0);
         if (threadIdx.x == 0) {
             atomicAdd(&st->aux, static_cast<unsigned long long>((dv + dr) * static_cast<int64_t>(splits > 1 ? splits / 2 : 1)));
-            if (!any) Pout[D.vert[pr.x]] = D.vert[pr.y];
+            if (!any) {
+                Pout[D.vert[pr.x]] = D.vert[pr.y];
+                D.joined[pr.y] = 1;
+            }
             else next[atomicAdd(&st->unresolved, 1u)] = pr.x;
         }
         __syncthreads();
@@ -944,7 +1035,7 @@ TableRef level_table(bisim_ctx* ctx, cudaStream_t s) {
 // Insert, verification and set comparisons of one level (level 0: every live
 // position; then the listed ones). Unresolved positions go to `next`.
 void launch_level(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const TableRef& t, uint32_t level,
-                  const int32_t* list, int64_t count, int32_t* next) {
+                  const int32_t* list, int64_t count, int32_t* next, bool out_has_in = false) {
     BISIM_SITE(site_in, "dense_insert");
     BISIM_SITE(site_v, "dense_verify");
     BISIM_SITE(site_cw, "dense_compare_warp");
@@ -953,13 +1044,33 @@ void launch_level(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const Tabl
     int32_t* Pout = ctx->P[ctx->cur ^ 1];
     const VerifyOut O{Pout, ctx->dpairs, ctx->dsmall, next, ctx->dstate};
     const HubSets H = hub_sets(ctx);
-    {
-        Launch L(site_in, s, count, 0, kInsertVertexBytes * count);
-        k_dense_insert<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, level, t, &ctx->dstate->error);
-    }
-    {
+    BISIM_SITE(site_as, "dense_alone_scan");
+    if (level == 0) {
+        // every live position: the ones alone in their block are done here,
+        // the others are listed (in ulist[1]) for the table passes, whose grid
+        // reads their number on the device
+        {
+            Launch L(site_as, s, count, 0, 11.0 * count);
+            k_alone_scan<<<grid_for(count, kThreads), kThreads, 0, s>>>(count, D, Pout, out_has_in, ctx->ulist[1],
+                                                                         ctx->dstate);
+        }
+        const unsigned grid = static_cast<unsigned>(std::min<int64_t>(kPersistGrid, cdiv(count, kThreads)));
+        const unsigned* dcount = &ctx->dstate->listed;
+        {
+            Launch L(site_in, s, count, 0, kInsertVertexBytes * count);
+            k_dense_insert<<<grid, kThreads, 0, s>>>(ctx->ulist[1], 0, dcount, D, 0, t, &ctx->dstate->error);
+        }
         Launch L(site_v, s, count, 0, kVerifyVertexBytes * count);
-        k_dense_verify<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, D, round_slots(ctx), O, ctx->n);
+        k_dense_verify<<<grid, kThreads, 0, s>>>(ctx->ulist[1], 0, dcount, D, round_slots(ctx), O, ctx->n);
+    } else {
+        {
+            Launch L(site_in, s, count, 0, kInsertVertexBytes * count);
+            k_dense_insert<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, nullptr, D, level, t,
+                                                                         &ctx->dstate->error);
+        }
+        Launch L(site_v, s, count, 0, kVerifyVertexBytes * count);
+        k_dense_verify<<<grid_for(count, kThreads), kThreads, 0, s>>>(list, count, nullptr, D, round_slots(ctx), O,
+                                                                     ctx->n);
     }
     {
         Launch L(site_cw, s, 0, 0, 0.0);
@@ -972,13 +1083,14 @@ void launch_level(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const Tabl
 DenseView dense_view(bisim_ctx* ctx) {
     const bool regions = ctx->rtable != nullptr;
     return DenseView{ctx->dvert, ctx->dvpos, ctx->dprp, ctx->dpe, ctx->P[ctx->cur], ctx->dcnt, ctx->dhash, ctx->dslot,
-                     regions ? ctx->gid : nullptr, ctx->rbase, ctx->rmask};
+                     ctx->djoined, ctx->downs, regions ? ctx->gid : nullptr, ctx->rbase, ctx->rmask};
 }
 
 
 // Everything of one round P[cur] -> P[cur ^ 1] that needs no host decision:
 // signatures of every class, then level 0 of the renumbering.
-void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t) {
+// in_loop: the captured loop, whose output buffer already holds P_i.
+void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, bool in_loop = false) {
     const DenseView D = dense_view(ctx);
     const HubSets H = hub_sets(ctx);
     unsigned* err = &ctx->dstate->error;
@@ -1043,7 +1155,7 @@ void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t) {
         Launch L(site_hf, s, ctx->n_dhub, 0, kSigVertexBytes * ctx->n_dhub);
         k_dense_hub_finalize<<<grid_for(ctx->n_dhub, 128), 128, 0, s>>>(D, H);
     }
-    launch_level(ctx, s, D, t, 0, nullptr, ctx->dbegin[kDClasses], ctx->ulist[0]);
+    launch_level(ctx, s, D, t, 0, nullptr, ctx->dbegin[kDClasses], ctx->ulist[0], in_loop);
 }
 
 // Reads the state of a round whose level 0 has been launched, runs the
@@ -1097,7 +1209,9 @@ bisim_status alloc_round_state(bisim_ctx* ctx, cudaStream_t s) {
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dhash), sizeof(unsigned long long) * nv, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dcnt), sizeof(int32_t) * nv, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dpairs), sizeof(int2) * nv, s)) ||
-        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dsmall), sizeof(int2) * nv, s)))
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dsmall), sizeof(int2) * nv, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->djoined), nv, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->downs), nv, s)))
         return cuda_error(ctx, e, "alloc dense round state");
     return BISIM_OK;
 }
@@ -1367,6 +1481,12 @@ bisim_status ensure_vertex_csr(bisim_ctx* ctx, cudaStream_t s) {
     return BISIM_OK;
 }
 
+void dense_start(bisim_ctx* ctx, cudaStream_t s) {
+    // P_0's block sizes are not known: no vertex counts as alone in the first round
+    if (ctx->n > 0) cudaMemsetAsync(ctx->djoined, 1, static_cast<size_t>(ctx->n), s);
+    dense_mark_dead(ctx, s);
+}
+
 void dense_mark_dead(bisim_ctx* ctx, cudaStream_t s) {
     const int64_t n_live = ctx->dbegin[kDClasses];
     if (n_live >= ctx->n) return;
@@ -1447,7 +1567,7 @@ bisim_status build_round_graph(bisim_ctx* ctx) {
         return cuda_error(ctx, e, "capture round");
     }
     cudaMemsetAsync(round_slots(ctx), 0, sizeof(Slot) * (ctx->rtable ? ctx->n_rslots : ctx->nslots), cs);
-    launch_round(ctx, cs, fixed_table(ctx));
+    launch_round(ctx, cs, fixed_table(ctx), true);
     LoopState* L = static_cast<LoopState*>(ctx->dloop);
     {
         Launch Lk(site_ck, cs, 0, 0, 0.0);

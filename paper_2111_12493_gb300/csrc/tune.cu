@@ -30,7 +30,7 @@ bisim_status time_rounds(bisim_ctx* ctx, cudaStream_t s, int32_t rounds, float* 
     int64_t blocks = 0;
     for (int pass = 0; pass < 2 && st == BISIM_OK; ++pass) {      // pass 0 warms up
         cudaMemcpyAsync(ctx->P[0], ctx->P0, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToDevice, s);
-        dense_mark_dead(ctx, s);
+        dense_start(ctx, s);
         ctx->cur = 0;
         cudaEventRecord(a, s);
         for (int32_t r = 0; r < (pass == 0 ? 1 : rounds) && st == BISIM_OK; ++r) st = dense_round(ctx, s, &blocks);
