@@ -496,8 +496,12 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
     if (ctx->gid != nullptr) return set_error(ctx, BISIM_ESTATE, "apply_updates is not supported on batched contexts");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
-    bisim_status st = ensure_vertex_csr(ctx, s);
-    if (st != BISIM_OK) return st;
+    bisim_status st;
+    const bool full = (ctx->opt.flags & BISIM_FLAG_FULL_RECOMPUTE) != 0;
+    // batches edit the incremental path's row store in place once its state is
+    // built; otherwise (and for full recomputes) they rewrite the CSR
+    const bool incremental = !full && ctx->inc_k == ctx->opt.k_incremental && ctx->store_ready;
+    if (!incremental && (st = ensure_vertex_csr(ctx, s)) != BISIM_OK) return st;
     if (n_ops > 0) {
         std::vector<void*> temps;
         const void* d_ops = nullptr;
@@ -512,22 +516,29 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
         cudaMemsetAsync(flags, 0, fb, s);
         uint8_t* vchanged = flags;
         uint8_t* rowchg = flags + (ctx->n + 1);
-        st = apply_ops_to_graph(ctx, static_cast<const bisim_op*>(d_ops), n_ops, vchanged, rowchg,
-                                flags + 2 * (ctx->n + 1), s);
+        uint8_t* killed = flags + 2 * (ctx->n + 1);
+        const bisim_op* dops = static_cast<const bisim_op*>(d_ops);
+        st = incremental ? apply_ops_to_store(ctx, dops, n_ops, vchanged, rowchg, killed, s)
+                         : apply_ops_to_graph(ctx, dops, n_ops, vchanged, rowchg, killed, s);
         free_temps(temps, s);
         if (st == BISIM_OK) {
             ctx->buckets_dirty = true;
             ctx->dense_ready = false;
-            if (!(ctx->opt.flags & BISIM_FLAG_FULL_RECOMPUTE) && ctx->inc_k == ctx->opt.k_incremental)
+            if (incremental) {
                 st = inc_update(ctx, vchanged, rowchg, s);
+            } else {
+                // the CSR moved on: the row store and any incremental state describe the old graph
+                inc_release(ctx, s);
+                store_release(ctx, s);
+            }
         }
         cudaFreeAsync(flags, s);
         if (st != BISIM_OK) return st;
-        if (!(ctx->opt.flags & BISIM_FLAG_FULL_RECOMPUTE) && ctx->inc_k == ctx->opt.k_incremental) return BISIM_OK;
+        if (incremental) return BISIM_OK;
     }
-    if (!(ctx->opt.flags & BISIM_FLAG_FULL_RECOMPUTE)) {
+    if (!full) {
         // first batch (or k changed): build the incremental state of the current graph
-        if (ctx->inc_k != ctx->opt.k_incremental) return inc_build(ctx, s);
+        if (ctx->inc_k != ctx->opt.k_incremental || !ctx->store_ready) return inc_build(ctx, s);
         return write_current(ctx, s);
     }
     // full recompute at k_incremental rounds

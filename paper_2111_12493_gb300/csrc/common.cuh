@@ -342,6 +342,26 @@ struct bisim_ctx {
     bool buckets_ready = false;    // degree buckets of the list-mode path are built
     int32_t cur_k = 0;             // rounds of the current partition
 
+    // dynamic adjacency of the incremental path (built with its state): out-rows
+    // and in-rows with spare capacity in two pools, edited in place by batches;
+    // while csr_stale is set, the CSR above lags behind it and is rebuilt from it
+    // before any other path reads the graph
+    bool store_ready = false;
+    bool csr_stale = false;
+    int64_t* xro = nullptr;        // [n] out-row offset into xpe
+    int32_t* xlen = nullptr;       // [n] entries in use (deleted ones included)
+    int32_t* xcap = nullptr;       // [n] capacity
+    unsigned long long* xpe = nullptr;   // out-pool: packed (label << 32 | target), ~0 deleted
+    int64_t xpool = 0;             // out-pool entries
+    int64_t* yro = nullptr;        // [n] in-row offset into ype
+    int32_t* ylen = nullptr;
+    int32_t* ycap = nullptr;
+    int32_t* ype = nullptr;        // in-pool: source vertices
+    int64_t ypool = 0;
+    int64_t* dtail = nullptr;      // [4] device: out-pool and in-pool tails, room the last plan asked for
+    int32_t* addo = nullptr;       // [n] per-batch adds per out-row (kept zero between batches)
+    int32_t* addi = nullptr;       // [n] per-batch adds per in-row
+
     // incremental maintenance (apply_updates): per level j = 0..inc_k, block ids
     // per vertex, |S| per vertex, block records and a hash index key -> block
     int32_t inc_k = -1;            // levels built (-1: no incremental state)
@@ -401,6 +421,15 @@ bisim_status build_buckets(bisim_ctx* ctx, cudaStream_t s);
 // after the graph changed.
 bisim_status ensure_buckets(bisim_ctx* ctx, cudaStream_t s);
 
+// ----------------------------------------------------------------------------- dynamic adjacency (store.cu)
+
+// Builds the out-/in-row store from the current CSR (all rows with spare
+// capacity, and at least room_out / room_in free entries at the pools' tails).
+bisim_status store_build(bisim_ctx* ctx, cudaStream_t s, int64_t room_out = 0, int64_t room_in = 0);
+void store_release(bisim_ctx* ctx, cudaStream_t s);
+// Rebuilds row_ptr / col / elab (and m) from the store when batches edited it.
+bisim_status csr_from_store(bisim_ctx* ctx, cudaStream_t s);
+
 // ----------------------------------------------------------------------------- refinement (refine.cu)
 
 bisim_status compute_p0(bisim_ctx* ctx, cudaStream_t s);
@@ -427,6 +456,9 @@ void launch_local_ids(const bisim_ctx* ctx, int32_t* out, cudaStream_t s);
 void ctx_free(bisim_ctx* ctx, void* p, size_t bytes, cudaStream_t s);
 bisim_status ensure_edge_sources(bisim_ctx* ctx, cudaStream_t s);
 bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, uint8_t* vchanged,
+                                uint8_t* rowchg, uint8_t* killed, cudaStream_t s);
+// The same batch applied in place to the row store (the CSR becomes stale).
+bisim_status apply_ops_to_store(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, uint8_t* vchanged,
                                 uint8_t* rowchg, uint8_t* killed, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- rounds (api.cu)

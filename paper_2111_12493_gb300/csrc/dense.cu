@@ -1442,6 +1442,7 @@ bisim_status dense_region_table(bisim_ctx* ctx, const int64_t* voff_host, int32_
 }
 
 bisim_status ensure_vertex_csr(bisim_ctx* ctx, cudaStream_t s) {
+    if (ctx->csr_stale) return csr_from_store(ctx, s);     // batches edited the row store
     if (ctx->row_ptr != nullptr) return BISIM_OK;
     if (!ctx->dense_ready) return set_error(ctx, BISIM_ESTATE, "no graph layout to rebuild the CSR from");
     const int32_t n = ctx->n;

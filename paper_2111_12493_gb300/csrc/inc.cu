@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "prof.cuh"
+#include "rows.cuh"
 
 namespace bisim {
 
@@ -108,13 +109,32 @@ __global__ void k_compact(const uint8_t* __restrict__ flag, const uint8_t* __res
     if (f) out[base + __popc(ball & ((1u << lane_id()) - 1u))] = static_cast<int32_t>(v);
 }
 
-// mark[src] for every edge into a vertex whose previous-level block changed
-__global__ void k_in_neighbours(const int32_t* __restrict__ esrc, const int32_t* __restrict__ col, int64_t m,
-                                const uint8_t* __restrict__ changed, uint8_t* __restrict__ mark) {
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        if (changed[col[e]]) mark[esrc[e]] = 1;
+// In-row tasks of the listed vertices (those whose previous-level block changed).
+__global__ void k_in_row_tasks(const int32_t* __restrict__ list, const unsigned long long* __restrict__ count,
+                               const int64_t* __restrict__ yro, const int32_t* __restrict__ ylen, TierLists L) {
+    const int64_t c = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(count));
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t b0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; b0 < c; b0 += stride) {
+        const int64_t i = b0 + threadIdx.x;
+        bool has = false;
+        RowTask t{0, 0, 0};
+        if (i < c) {
+            const int32_t w = list[i];
+            has = true;
+            t = RowTask{yro[w], ylen[w], w};
+        }
+        tier_push(L, has, t);
+    }
 }
+
+// mark[u] for every source u in the in-rows (a superset of the in-neighbours).
+struct MarkSources {
+    const int32_t* ype;
+    uint8_t* mark;
+    __device__ void operator()(const RowTask&, int64_t e, bool in) const {
+        if (in) mark[ype[e]] = 1;
+    }
+};
 
 __global__ void k_or_into(uint8_t* __restrict__ a, const uint8_t* __restrict__ b, const uint8_t* __restrict__ c,
                           int32_t n) {
@@ -129,12 +149,12 @@ __global__ void k_set_flags(const int32_t* __restrict__ list, int64_t count, uin
 
 // ----------------------------------------------------------------------------- frontier degree buckets
 
-__global__ void k_list_classify(const int32_t* __restrict__ list, int64_t count, const int64_t* __restrict__ rp,
+__global__ void k_list_classify(const int32_t* __restrict__ list, int64_t count, const int32_t* __restrict__ rl,
                                 int small_max, int mid_max, uint32_t* __restrict__ keys, uint64_t* __restrict__ vals) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const int32_t v = list[i];
-    const int64_t d = rp[v + 1] - rp[v];
+    const int64_t d = rl[v];
     uint32_t c;
     if (d <= small_max || d == 0) {
         c = d <= 4 ? 0u : d <= 8 ? 1u : d <= 16 ? 2u : 3u;
@@ -150,7 +170,7 @@ __global__ void k_list_classify(const int32_t* __restrict__ list, int64_t count,
 }
 
 __global__ void k_list_bounds(const uint32_t* __restrict__ cls, const uint64_t* __restrict__ vals, int64_t count,
-                              const int64_t* __restrict__ rp, int64_t* __restrict__ begin,
+                              const int32_t* __restrict__ rl, int64_t* __restrict__ begin,
                               unsigned long long* __restrict__ edges, int32_t* __restrict__ out) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= count) return;
@@ -159,15 +179,15 @@ __global__ void k_list_bounds(const uint32_t* __restrict__ cls, const uint64_t* 
     for (int q = p + 1; q <= c; ++q) begin[q] = i;
     const int32_t v = static_cast<int32_t>(vals[i]);
     out[i] = v;
-    atomicAdd(&edges[c], static_cast<unsigned long long>(rp[v + 1] - rp[v]));
+    atomicAdd(&edges[c], static_cast<unsigned long long>(rl[v]));
 }
 
-__global__ void k_row_bounds(const int32_t* __restrict__ list, int64_t count, const int64_t* __restrict__ rp,
-                             int64_t* __restrict__ out) {
+__global__ void k_row_bounds(const int32_t* __restrict__ list, int64_t count, const int64_t* __restrict__ ro,
+                             const int32_t* __restrict__ rl, int64_t* __restrict__ out) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i < count) {
-        out[2 * i] = rp[list[i]];
-        out[2 * i + 1] = rp[list[i] + 1];
+        out[2 * i] = ro[list[i]];
+        out[2 * i + 1] = ro[list[i]] + rl[list[i]];
     }
 }
 
@@ -302,7 +322,17 @@ __device__ __forceinline__ bool cset_has(const unsigned long long* tab, uint32_t
     return false;
 }
 
-__device__ __forceinline__ uint64_t pair_value_dev(int32_t label, int32_t block) { return pair_value(label, block); }
+// Pair value of store entry e over the block ids `lid`; false for a deleted
+// entry or an edge into a dead vertex (no block).
+__device__ __forceinline__ bool row_entry(const unsigned long long* pe, int64_t e, const int32_t* lid,
+                                          unsigned long long* mv) {
+    const unsigned long long x = pe[e];
+    if (x == kRowTomb) return false;
+    const int32_t b = lid[static_cast<int32_t>(static_cast<uint32_t>(x))];
+    if (b < 0) return false;
+    *mv = pair_value(static_cast<int32_t>(x >> 32), b);
+    return true;
+}
 
 // 3b. exact comparison of a representative g with a candidate block's
 // smallest member r: same previous-level block, same set size, and every pair
@@ -311,8 +341,8 @@ __device__ __forceinline__ uint64_t pair_value_dev(int32_t label, int32_t block)
 // dedup table. One CTA per candidate.
 template <int SLOTS>
 __global__ void __launch_bounds__(kCmpThreads) k_compare(int64_t ncand, Level L, Level Lprev, Work W,
-                                                         const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                         const int32_t* __restrict__ elab,
+                                                         const int64_t* __restrict__ ro, const int32_t* __restrict__ rl,
+                                                         const unsigned long long* __restrict__ pe,
                                                          const int32_t* __restrict__ cnt,
                                                          const unsigned long long* __restrict__ skey,
                                                          const int32_t* __restrict__ hub_list, int64_t n_hub,
@@ -341,11 +371,13 @@ __global__ void __launch_bounds__(kCmpThreads) k_compare(int64_t ncand, Level L,
                 for (uint32_t j = threadIdx.x; j < size; j += kCmpThreads) tab[j] = 0ull;
                 if (threadIdx.x == 0) zero = 0u;
                 __syncthreads();
-                const unsigned long long* lg = skey + rp[g];
+                const unsigned long long* lg = skey + ro[g];
                 for (int32_t j = threadIdx.x; j < c; j += kCmpThreads) cset_insert(tab, size - 1, &zero, lg[j]);
                 __syncthreads();
-                for (int64_t e = rp[r] + threadIdx.x; e < rp[r + 1] && !miss; e += kCmpThreads)
-                    miss = !cset_has(tab, size - 1, zero, pair_value_dev(elab[e], Lprev.lid[col[e]]));
+                for (int64_t e = ro[r] + threadIdx.x; e < ro[r] + rl[r] && !miss; e += kCmpThreads) {
+                    unsigned long long mv;
+                    if (row_entry(pe, e, Lprev.lid, &mv)) miss = !cset_has(tab, size - 1, zero, mv);
+                }
             } else {
                 // hub representative: its dedup table from the frontier's hub path
                 int64_t lo = 0, hi = n_hub - 1;
@@ -355,8 +387,9 @@ __global__ void __launch_bounds__(kCmpThreads) k_compare(int64_t ncand, Level L,
                 }
                 const unsigned long long* ht = tab_all + toff[lo];
                 const uint32_t mask = tmask[lo];
-                for (int64_t e = rp[r] + threadIdx.x; e < rp[r + 1] && !miss; e += kCmpThreads) {
-                    const unsigned long long mv = pair_value_dev(elab[e], Lprev.lid[col[e]]);
+                for (int64_t e = ro[r] + threadIdx.x; e < ro[r] + rl[r] && !miss; e += kCmpThreads) {
+                    unsigned long long mv;
+                    if (!row_entry(pe, e, Lprev.lid, &mv)) continue;
                     bool found = false;
                     if (mv == 0ull) {
                         found = acc[lo].zero != 0u;
@@ -540,6 +573,9 @@ struct Scratch {
     int32_t* blist = nullptr;
     int64_t* dbegin = nullptr;
     unsigned long long* dedges = nullptr;
+    int32_t* clist = nullptr;          // [n] vertices whose block changed one level down
+    unsigned long long* ccount = nullptr;
+    TierLists tiers{};                 // in-row tasks, [n] per tier
 };
 
 cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
@@ -554,6 +590,7 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     need(8 * 2); need(32);
     need(4 * n); need(4 * n); need(8 * n); need(8 * n); need(8 * tw); need(4 * n);
     need(8 * (kNumClasses + 1)); need(8 * kNumClasses);
+    need(4 * n); need(3 * sizeof(RowTask) * n); need(16); need(16);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&S.base), bytes, s);
     if (e) return e;
     char* p = S.base;
@@ -593,6 +630,10 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     S.blist = reinterpret_cast<int32_t*>(carve(4 * n));
     S.dbegin = reinterpret_cast<int64_t*>(carve(8 * (kNumClasses + 1)));
     S.dedges = reinterpret_cast<unsigned long long*>(carve(8 * kNumClasses));
+    S.clist = reinterpret_cast<int32_t*>(carve(4 * n));
+    RowTask* tasks = reinterpret_cast<RowTask*>(carve(3 * sizeof(RowTask) * n));
+    S.tiers = TierLists{{tasks, tasks + n, tasks + 2 * n}, reinterpret_cast<unsigned*>(carve(16))};
+    S.ccount = reinterpret_cast<unsigned long long*>(carve(16));
     // per-block flags start (and are kept) at zero
     cudaMemsetAsync(W.cntF, 0, 4 * bc, s);
     cudaMemsetAsync(W.touched, 0, 4 * bc, s);
@@ -620,11 +661,11 @@ bisim_status list_buckets(bisim_ctx* ctx, const int32_t* list, int64_t count, Sc
     if (count > 0) {
         BISIM_SITE(site, "inc_buckets");
         Launch L(site, s, count, 0, 24.0 * count);
-        k_list_classify<<<grid_for(count, 256), 256, 0, s>>>(list, count, ctx->row_ptr, ctx->opt.small_max_degree,
+        k_list_classify<<<grid_for(count, 256), 256, 0, s>>>(list, count, ctx->xlen, ctx->opt.small_max_degree,
                                                             ctx->opt.mid_max_degree, S.ck0, S.cv0);
         const int w = radix_sort_pairs(S.ck0, S.cv0, S.ck1, S.cv1, count, 8, S.ctmp, s);
         k_list_bounds<<<grid_for(count, 256), 256, 0, s>>>(w ? S.ck1 : S.ck0, w ? S.cv1 : S.cv0, count,
-                                                          ctx->row_ptr, S.dbegin, S.dedges, S.blist);
+                                                          ctx->xlen, S.dbegin, S.dedges, S.blist);
     }
     cudaMemcpyAsync(begin, S.dbegin, sizeof(begin), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(edges, S.dedges, sizeof(edges), cudaMemcpyDeviceToHost, s);
@@ -641,7 +682,7 @@ bisim_status list_buckets(bisim_ctx* ctx, const int32_t* list, int64_t count, Sc
     std::vector<int64_t> bounds(2 * B.n_hub);
     // the two sort value buffers are free again and adjacent: 16 bytes x n >= 2 x 8 bytes x hubs
     int64_t* dbounds = reinterpret_cast<int64_t*>(S.cv0);
-    k_row_bounds<<<grid_for(B.n_hub, 256), 256, 0, s>>>(B.hub_list, B.n_hub, ctx->row_ptr, dbounds);
+    k_row_bounds<<<grid_for(B.n_hub, 256), 256, 0, s>>>(B.hub_list, B.n_hub, ctx->xro, ctx->xlen, dbounds);
     cudaMemcpyAsync(hubs.data(), B.hub_list, sizeof(int32_t) * B.n_hub, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(bounds.data(), dbounds, sizeof(int64_t) * 2 * B.n_hub, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "read frontier hubs");
@@ -690,11 +731,13 @@ bisim_status list_buckets(bisim_ctx* ctx, const int32_t* list, int64_t count, Sc
     return BISIM_OK;
 }
 
+// The signature lists of the list-mode kernels sit at the rows' offsets in the
+// out-pool of the row store.
 bisim_status ensure_skey(bisim_ctx* ctx, cudaStream_t s) {
-    if (ctx->m <= ctx->skey_cap) return BISIM_OK;
+    if (ctx->xpool <= ctx->skey_cap) return BISIM_OK;
     ctx_free(ctx, ctx->skey, sizeof(unsigned long long) * ctx->skey_cap, s);
     ctx->skey = nullptr;
-    const int64_t cap = ctx->m + ctx->m / 4 + 1024;
+    const int64_t cap = ctx->xpool;
     cudaError_t e;
     if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->skey), sizeof(unsigned long long) * cap, s)))
         return cuda_error(ctx, e, "grow signature lists");
@@ -703,8 +746,8 @@ bisim_status ensure_skey(bisim_ctx* ctx, cudaStream_t s) {
 }
 
 // One level: frontier F (f vertices, live or dead) with live part FL (fl).
-bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t f, int64_t fl, bool all_static,
-                        int64_t* rebuild, cudaStream_t s) {
+bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t f, int64_t fl, int64_t* rebuild,
+                        cudaStream_t s) {
     Work& W = S.W;
     Level L = level_view(ctx, j);
     const int32_t n = ctx->n;
@@ -736,17 +779,10 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t f, int64_t fl
             k_label_keys<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, ctx->vlabel, W.h,
                                                           ctx->opt.hash_bits >= 64 ? ~0ull : ((1ull << ctx->opt.hash_bits) - 1));
         } else {
-            Buckets B;
-            if (all_static) {
-                if ((st = ensure_buckets(ctx, s)) != BISIM_OK) return st;
-                B = ctx_buckets(ctx);
-            } else {
-                if ((st = list_buckets(ctx, W.FL, fl, S, LB, s)) != BISIM_OK) return st;
-                B = LB.B;
-            }
+            if ((st = list_buckets(ctx, W.FL, fl, S, LB, s)) != BISIM_OK) return st;
+            const Buckets& B = LB.B;
             int64_t blocks = 0;
-            st = signature_round(ctx, B, ctx->lid[j - 1], W.grp, all_static ? nullptr : W.FL, all_static ? 0 : fl,
-                                 W.h, s, &blocks);
+            st = signature_round(ctx, B, ctx->lid[j - 1], W.grp, W.FL, fl, W.h, s, &blocks);
             if (st != BISIM_OK) {
                 if (LB.hubmem) cudaFreeAsync(LB.hubmem, s);
                 return st;
@@ -780,14 +816,14 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t f, int64_t fl
         const unsigned grid = static_cast<unsigned>(std::min<unsigned long long>(ncand, 4096));
         Launch Lk(site, s, static_cast<int64_t>(ncand), 0, 0.0);
         k_compare<kCmpSmallSlots><<<grid, kCmpThreads, sizeof(unsigned long long) * kCmpSmallSlots, s>>>(
-            static_cast<int64_t>(ncand), L, Lp, W, ctx->row_ptr, ctx->col, ctx->elab, ctx->cnt, ctx->skey,
+            static_cast<int64_t>(ncand), L, Lp, W, ctx->xro, ctx->xlen, ctx->xpe, ctx->cnt, ctx->skey,
             B.hub_list, B.n_hub, B.toff, B.tmask, B.tab, B.acc, 0, kCmpSmallSlots / 2);
         k_compare<kCmpLargeSlots><<<grid, kCmpThreads, sizeof(unsigned long long) * kCmpLargeSlots, s>>>(
-            static_cast<int64_t>(ncand), L, Lp, W, ctx->row_ptr, ctx->col, ctx->elab, ctx->cnt, ctx->skey,
+            static_cast<int64_t>(ncand), L, Lp, W, ctx->xro, ctx->xlen, ctx->xpe, ctx->cnt, ctx->skey,
             B.hub_list, B.n_hub, B.toff, B.tmask, B.tab, B.acc, kCmpSmallSlots / 2 + 1, kCmpLargeSlots / 2);
         if (B.n_hub > 0)
-            k_compare<0><<<grid, kCmpThreads, 0, s>>>(static_cast<int64_t>(ncand), L, Lp, W, ctx->row_ptr, ctx->col,
-                                                      ctx->elab, ctx->cnt, ctx->skey, B.hub_list, B.n_hub, B.toff,
+            k_compare<0><<<grid, kCmpThreads, 0, s>>>(static_cast<int64_t>(ncand), L, Lp, W, ctx->xro, ctx->xlen,
+                                                      ctx->xpe, ctx->cnt, ctx->skey, B.hub_list, B.n_hub, B.toff,
                                                       B.tmask, B.tab, B.acc, kCmpLargeSlots / 2 + 1, INT_MAX);
     }
     if (LB.hubmem) cudaFreeAsync(LB.hubmem, s);
@@ -891,7 +927,7 @@ bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s) {
     if (K > kMaxIncLevels) return set_error(ctx, BISIM_EINVAL, "k_incremental exceeds 16");
     inc_release(ctx, s);
     bisim_status st;
-    if ((st = ensure_edge_sources(ctx, s)) != BISIM_OK) return st;
+    if ((st = store_build(ctx, s)) != BISIM_OK) return st;
     if ((st = refresh_after_edit(ctx, s)) != BISIM_OK) return st;
     if ((st = ensure_skey(ctx, s)) != BISIM_OK) return st;
     const size_t n = static_cast<size_t>(std::max(ctx->n, 1));
@@ -925,7 +961,7 @@ bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s) {
     Scratch& S = *Sp;
     int64_t f = 0, fl = 0, rebuild = 0;
     st = make_frontier(ctx, S, nullptr, &f, &fl, s);
-    for (int j = 0; st == BISIM_OK && j <= K; ++j) st = level_pass(ctx, j, S, f, fl, true, &rebuild, s);
+    for (int j = 0; st == BISIM_OK && j <= K; ++j) st = level_pass(ctx, j, S, f, fl, &rebuild, s);
     if (st == BISIM_OK && rebuild) st = set_error(ctx, BISIM_ENOMEM, "incremental state overflow during build");
     if (st == BISIM_OK) st = write_output(ctx, s);
     if (st != BISIM_OK) {
@@ -957,12 +993,17 @@ bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* 
     st = make_frontier(ctx, S, vchanged, &f, &fl, s);
     for (int j = 0; st == BISIM_OK && j <= K; ++j) {
         if (j > 0) {
-            // F_j: block changed one level down, out-edges changed, or an out-edge into a changed vertex
+            // F_j: block changed one level down, out-edges changed, or an out-edge into a
+            // changed vertex (its source is in the changed vertex's in-row)
             cudaMemsetAsync(W.next, 0, n, s);
-            if (ctx->m > 0) {
+            cudaMemsetAsync(S.ccount, 0, 8, s);
+            cudaMemsetAsync(S.tiers.cnt, 0, 16, s);
+            if (n > 0) {
                 BISIM_SITE(site, "inc_in_neighbours");
-                Launch L(site, s, 0, ctx->m, 8.0 * ctx->m);
-                k_in_neighbours<<<grid_for(ctx->m, 256), 256, 0, s>>>(ctx->esrc, ctx->col, ctx->m, W.changed, W.next);
+                Launch L(site, s, n, 0, 1.0 * n);
+                k_compact<<<grid_for(n, 256), 256, 0, s>>>(W.changed, ctx->alive, n, 0, S.clist, S.ccount);
+                k_in_row_tasks<<<kTierGrid, kTierThreads, 0, s>>>(S.clist, S.ccount, ctx->yro, ctx->ylen, S.tiers);
+                run_tiers(S.tiers, MarkSources{ctx->ype, W.next}, s);
             }
             k_or_into<<<grid_for(n, 256), 256, 0, s>>>(W.next, W.changed, rowchg, n);
             st = make_frontier(ctx, S, W.next, &f, &fl, s);
@@ -972,7 +1013,7 @@ bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* 
             cudaMemsetAsync(W.changed, 0, n, s);
         }
         total += fl;
-        st = level_pass(ctx, j, S, f, fl, false, &rebuild, s);
+        st = level_pass(ctx, j, S, f, fl, &rebuild, s);
         if (st == BISIM_OK && rebuild) break;
     }
     if (st != BISIM_OK) {

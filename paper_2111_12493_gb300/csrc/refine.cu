@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "prof.cuh"
+#include "rows.cuh"
 
 namespace bisim {
 
@@ -39,13 +40,36 @@ __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1
 
 // ----------------------------------------------------------------------------- views
 
+// Rows come from the CSR (row v = [rp[v], rp[v + 1]) of col / elab) or from the
+// incremental path's row store (row v = rl[v] packed entries from rp[v], some
+// deleted, some pointing at dead vertices: those do not count).
 struct GraphView {
     const int64_t* rp;
+    const int32_t* rl;                 // store row lengths (null: CSR)
     const int32_t* col;
     const int32_t* elab;
-    const int32_t* P;        // P_i
-    unsigned long long* hout;   // nullable: receives each vertex's signature hash
+    const unsigned long long* pe;      // store entries (null: CSR)
+    const int32_t* P;                  // P_i (-1 for a dead vertex)
+    unsigned long long* hout;          // nullable: receives each vertex's signature hash
 };
+
+__device__ __forceinline__ int row_len(const GraphView& G, int32_t v) {
+    return G.rl ? G.rl[v] : static_cast<int>(G.rp[v + 1] - G.rp[v]);
+}
+
+// Pair value of row entry e; false when the entry does not count.
+__device__ __forceinline__ bool entry_value(const GraphView& G, int64_t e, unsigned long long* mv) {
+    if (G.pe) {
+        const unsigned long long x = __ldcs(G.pe + e);
+        if (x == kRowTomb) return false;
+        const int32_t p = __ldg(G.P + static_cast<int32_t>(static_cast<uint32_t>(x)));
+        if (p < 0) return false;
+        *mv = pair_value(static_cast<int32_t>(x >> 32), p);
+        return true;
+    }
+    *mv = pair_value(__ldcs(G.elab + e), __ldg(G.P + __ldcs(G.col + e)));
+    return true;
+}
 
 struct HubView {
     const int32_t* hub_list;   // ascending vertex ids
@@ -108,7 +132,7 @@ struct SigMode {
         const int32_t c = cnt[v];
         if (c != cnt[r]) return 0;
         const int64_t bv = G.rp[v], br = G.rp[r];
-        const int64_t dv = G.rp[v + 1] - bv, dr = G.rp[r + 1] - br;
+        const int64_t dv = row_len(G, v), dr = row_len(G, r);
         const bool sorted = (dv == 0 || dv <= small_max) && (dr == 0 || dr <= small_max);
         if (!sorted) return 2;
         const unsigned long long* lv = skey + bv;
@@ -177,24 +201,22 @@ __global__ void __launch_bounds__(128) k_sig_small(const int32_t* __restrict__ l
     if (i >= count) return;
     const int32_t v = list[i];
     const int64_t b = G.rp[v];
-    const int d = static_cast<int>(G.rp[v + 1] - b);
+    const int d = row_len(G, v);
     uint64_t s[D];
+    int live = 0;                                   // entries that count sort first
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        if (j < d) {
-            const int32_t w = __ldcs(G.col + b + j);
-            const int32_t l = __ldcs(G.elab + b + j);
-            s[j] = pair_value(l, __ldg(G.P + w));
-        } else {
-            s[j] = ~0ull;
-        }
+        unsigned long long mv = ~0ull;
+        if (j < d && entry_value(G, b + j, &mv)) ++live;
+        else mv = ~0ull;
+        s[j] = mv;
     }
     bitonic_regs<D>(s);
     uint32_t u = 0;
     uint64_t sum = 0;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        if (j < d && (j == 0 || s[j] != s[j - 1])) {
+        if (j < live && (j == 0 || s[j] != s[j - 1])) {
             skey[b + u] = s[j];
             sum += s[j];
             ++u;
@@ -230,19 +252,14 @@ __global__ void __launch_bounds__(256) k_sig_warp(const int32_t* __restrict__ li
     __syncwarp();
     const int32_t v = list[i];
     const int64_t b = G.rp[v];
-    const int d = static_cast<int>(G.rp[v + 1] - b);
+    const int d = row_len(G, v);
     unsigned out = 0;
     unsigned long long mys = 0;
     for (int j0 = 0; j0 < d; j0 += 32) {
         const int j = j0 + static_cast<int>(lane);
         bool fresh = false;
         unsigned long long mv = 0;
-        if (j < d) {
-            const int32_t w = __ldcs(G.col + b + j);
-            const int32_t l = __ldcs(G.elab + b + j);
-            mv = pair_value(l, __ldg(G.P + w));
-            fresh = smem_set_insert(tab, S - 1, &zero_all[warp], mv);
-        }
+        if (j < d && entry_value(G, b + j, &mv)) fresh = smem_set_insert(tab, S - 1, &zero_all[warp], mv);
         const unsigned ball = __ballot_sync(0xffffffffu, fresh);
         if (fresh) {
             skey[b + out + __popc(ball & lanemask_lt())] = mv;
@@ -274,7 +291,7 @@ __global__ void __launch_bounds__(T) k_sig_mid(const int32_t* __restrict__ list,
     constexpr uint32_t mask = 2 * N - 1;
     const int32_t v = list[blockIdx.x];
     const int64_t b = G.rp[v];
-    const int d = static_cast<int>(G.rp[v + 1] - b);
+    const int d = row_len(G, v);
     for (int j = threadIdx.x; j < 2 * N; j += T) tab[j] = 0ull;
     if (threadIdx.x == 0) {
         n_out = 0;
@@ -286,12 +303,7 @@ __global__ void __launch_bounds__(T) k_sig_mid(const int32_t* __restrict__ list,
         const int j = j0 + static_cast<int>(threadIdx.x);
         bool fresh = false;
         unsigned long long mv = 0;
-        if (j < d) {
-            const int32_t w = __ldcs(G.col + b + j);
-            const int32_t l = __ldcs(G.elab + b + j);
-            mv = pair_value(l, __ldg(G.P + w));
-            fresh = smem_set_insert(tab, mask, &zero, mv);
-        }
+        if (j < d && entry_value(G, b + j, &mv)) fresh = smem_set_insert(tab, mask, &zero, mv);
         const unsigned ball = __ballot_sync(0xffffffffu, fresh);
         if (ball) {
             const int leader = __ffs(ball) - 1;
@@ -339,10 +351,7 @@ __global__ void __launch_bounds__(256) k_hub_insert(const HubChunk* __restrict__
         const int64_t e = e0 + threadIdx.x;
         bool fresh = false;
         unsigned long long mv = 0;
-        if (e < c.end) {
-            const int32_t w = __ldcs(G.col + e);
-            const int32_t l = __ldcs(G.elab + e);
-            mv = pair_value(l, __ldg(G.P + w));
+        if (e < c.end && entry_value(G, e, &mv)) {
             if (mv == 0ull) {
                 fresh = atomicOr(&acc[c.hub].zero, 1u) == 0u;
             } else {
@@ -761,7 +770,9 @@ Buckets ctx_buckets(const bisim_ctx* ctx) {
 bisim_status signature_round(bisim_ctx* ctx, const Buckets& B, const int32_t* Pin, int32_t* Pout,
                              const int32_t* vlist, int64_t vcount, unsigned long long* hout, cudaStream_t s,
                              int64_t* out_blocks) {
-    GraphView G{ctx->row_ptr, ctx->col, ctx->elab, Pin, hout};
+    const GraphView G = ctx->store_ready
+                            ? GraphView{ctx->xro, ctx->xlen, nullptr, nullptr, ctx->xpe, Pin, hout}
+                            : GraphView{ctx->row_ptr, nullptr, ctx->col, ctx->elab, nullptr, Pin, hout};
     TableRef t = next_epoch(ctx, s);
     if (B.n_hub > 0) {
         cudaMemsetAsync(B.tab, 0, sizeof(unsigned long long) * B.tab_words, s);

@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "prof.cuh"
+#include "rows.cuh"
 
 namespace bisim {
 
@@ -55,6 +56,7 @@ __global__ void k_ops_check(const bisim_op* __restrict__ ops, int64_t nops, int3
         vkey[i] = (ok && !edge) ? static_cast<uint32_t>(o.src) : 0xffffffffu;
         vval[i] = static_cast<uint64_t>(i);
         if (ok && !edge) atomicAdd(&st->aux, 1ull);
+        if (ok && o.kind == BISIM_OP_VERTEX_ADD) atomicAdd(&st->pairs, 1u);
     }
 }
 
@@ -94,8 +96,10 @@ __device__ int64_t last_kill(const VertexOps& V, int32_t x) {
 }
 
 // Final state of every vertex named by a vertex operation.
+// revived (nullable): live after the batch but dead before it or deleted in it.
 __global__ void k_vertex_final(VertexOps V, uint8_t* __restrict__ alive, int32_t* __restrict__ vlabel,
-                               uint8_t* __restrict__ killed, uint8_t* __restrict__ vchanged) {
+                               uint8_t* __restrict__ killed, uint8_t* __restrict__ vchanged,
+                               uint8_t* __restrict__ revived) {
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < V.nv;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const uint32_t x = V.key[i];
@@ -108,6 +112,7 @@ __global__ void k_vertex_final(VertexOps V, uint8_t* __restrict__ alive, int32_t
             alive[x] = 1;
             vlabel[x] = o.label;
             if (!was || lab != o.label) vchanged[x] = 1;
+            if (revived && (!was || last_kill(V, static_cast<int32_t>(x)) >= 0)) revived[x] = 1;
         } else {
             alive[x] = 0;
             if (was) vchanged[x] = 1;
@@ -367,6 +372,253 @@ __global__ void k_fill_src(const int64_t* __restrict__ rp, int32_t n, int32_t* _
     for (int64_t e = rp[v] + (threadIdx.x & 31); e < rp[v + 1]; e += 32) esrc[e] = static_cast<int32_t>(v);
 }
 
+// ----------------------------------------------------------------------------- row-store edits
+
+// Out-row tasks of the batch's distinct keys: mode 0 counts a key's copies
+// present before the batch (keys without a deleted endpoint whose endpoints
+// were live), mode 1 deletes the copies the fold removed.
+__global__ void k_key_tasks(const int64_t* __restrict__ keyslot, int64_t ne, KeyTable T,
+                            const uint8_t* __restrict__ killed, const uint8_t* __restrict__ alive0, StoreView S,
+                            int mode, TierLists L) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t b0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; b0 < ne; b0 += stride) {
+        const int64_t i = b0 + threadIdx.x;
+        bool has = false;
+        RowTask t{0, 0, 0};
+        if (i < ne && keyslot[i] >= 0) {
+            const int32_t slot = static_cast<int32_t>(keyslot[i]);
+            const int32_t u = T.u[slot], w = T.w[slot];
+            has = mode == 0 ? (!killed[u] && !killed[w] && alive0[u] && alive0[w]) : T.rem[slot] > 0;
+            if (has) t = RowTask{S.xro[u], S.xlen[u], slot};
+        }
+        tier_push(L, has, t);
+    }
+}
+
+struct KeyCount {
+    const unsigned long long* xpe;
+    KeyTable T;
+    __device__ void operator()(const RowTask& t, int64_t e, bool in) const {
+        const bool hit = in && xpe[e] == pack_edge(T.l[t.arg], T.w[t.arg]);
+        const unsigned b = __ballot_sync(0xffffffffu, hit);
+        if ((threadIdx.x & 31u) == 0u && b) atomicAdd(&T.c0[t.arg], __popc(b));
+    }
+};
+
+struct KeyRemove {
+    unsigned long long* xpe;
+    KeyTable T;
+    __device__ void operator()(const RowTask& t, int64_t e, bool in) const {
+        if (in && xpe[e] == pack_edge(T.l[t.arg], T.w[t.arg]) && atomicAdd(&T.taken[t.arg], 1) < T.rem[t.arg])
+            xpe[e] = kRowTomb;
+    }
+};
+
+// In-row tasks of every vertex deleted or brought back by the batch (the last
+// operation of each named vertex files it). With `need` set, only adds the
+// in-row lengths of the revived vertices there.
+__global__ void k_vertex_tasks(VertexOps V, const uint8_t* __restrict__ killed, const uint8_t* __restrict__ revived,
+                               StoreView S, TierLists L, unsigned long long* need) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t b0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; b0 < V.nv; b0 += stride) {
+        const int64_t i = b0 + threadIdx.x;
+        bool has = false;
+        RowTask t{0, 0, 0};
+        if (i < V.nv && (i + 1 == V.nv || V.key[i + 1] != V.key[i])) {
+            const int32_t x = static_cast<int32_t>(V.key[i]);
+            if (need) {
+                if (revived[x]) atomicAdd(need, static_cast<unsigned long long>(S.ylen[x]));
+            } else if (killed[x] || revived[x]) {
+                has = true;
+                t = RowTask{S.yro[x], S.ylen[x], x};
+            }
+        }
+        if (!need) tier_push(L, has, t);
+    }
+}
+
+// Sources of a deleted vertex lose an out-edge; the out-rows of a revived
+// vertex's former sources are searched for entries left pointing at it.
+struct VertexSources {
+    const int32_t* ype;
+    const uint8_t* killed;
+    const uint8_t* revived;
+    uint8_t* rowchg;
+    StoreView S;
+    TierLists P;
+    __device__ void operator()(const RowTask& t, int64_t e, bool in) const {
+        const int32_t x = t.arg;
+        int32_t u = 0;
+        if (in) {
+            u = ype[e];
+            if (killed[x]) rowchg[u] = 1;
+        }
+        const bool purge = in && revived[x] != 0;
+        RowTask pt{0, 0, x};
+        if (purge) pt = RowTask{S.xro[u], S.xlen[u], x};
+        tier_push(P, purge, pt);
+    }
+};
+
+struct PurgeTarget {
+    unsigned long long* xpe;
+    __device__ void operator()(const RowTask& t, int64_t e, bool in) const {
+        if (in && static_cast<uint32_t>(xpe[e]) == static_cast<uint32_t>(t.arg)) xpe[e] = kRowTomb;
+    }
+};
+
+// A deleted vertex's out-row empties; a revived vertex's in-row starts afresh
+// (its former sources were purged).
+__global__ void k_vertex_rows(VertexOps V, const uint8_t* __restrict__ killed, const uint8_t* __restrict__ revived,
+                              StoreView S) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < V.nv;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (i + 1 < V.nv && V.key[i + 1] == V.key[i]) continue;
+        const int32_t x = static_cast<int32_t>(V.key[i]);
+        if (killed[x]) S.xlen[x] = 0;
+        if (revived[x]) S.ylen[x] = 0;
+    }
+}
+
+// Adds per out-row and per in-row; every row that receives one is listed once.
+__global__ void k_add_rows(const AddRec* __restrict__ add, const unsigned long long* __restrict__ nadd,
+                           int32_t* __restrict__ addo, int32_t* __restrict__ addi, int32_t* __restrict__ touched_o,
+                           int32_t* __restrict__ touched_i, unsigned* __restrict__ n_touched) {
+    const int64_t count = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(nadd));
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const AddRec a = add[i];
+        if (atomicAdd(&addo[a.u], 1) == 0) touched_o[atomicAdd(&n_touched[0], 1u)] = a.u;
+        if (atomicAdd(&addi[a.w], 1) == 0) touched_i[atomicAdd(&n_touched[1], 1u)] = a.w;
+    }
+}
+
+struct RowMove {
+    int64_t off;     // new offset (-1: the row stays)
+    int32_t cap;
+    int32_t len;     // entries copied so far
+};
+
+// A row that cannot take its adds moves to the pool's tail with room for half
+// as much again. A move that would pass the pool's end is not made (the tail
+// still advances, so the host sees the overflow and rebuilds the store before
+// any add is placed); `wanted` sums the room all moves asked for.
+__global__ void k_plan_rows(const int32_t* __restrict__ touched, const unsigned* __restrict__ n_touched,
+                            const int32_t* __restrict__ addc, const int32_t* __restrict__ len,
+                            const int32_t* __restrict__ cap, int64_t* __restrict__ tail, int64_t pool,
+                            int64_t* __restrict__ wanted, RowMove* __restrict__ moves) {
+    const unsigned count = *reinterpret_cast<const volatile unsigned*>(n_touched);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const int32_t v = touched[i];
+        const int64_t need = static_cast<int64_t>(len[v]) + addc[v];
+        RowMove mv{-1, 0, 0};
+        if (need > cap[v]) {
+            const int64_t want = need + need / 2 + 8;
+            const int64_t nc = want < 0x7fffffff ? want : 0x7fffffff;
+            const int64_t off = static_cast<int64_t>(atomicAdd(reinterpret_cast<unsigned long long*>(tail),
+                                                               static_cast<unsigned long long>(nc)));
+            atomicAdd(reinterpret_cast<unsigned long long*>(wanted), static_cast<unsigned long long>(nc));
+            if (off + nc <= pool) mv = RowMove{off, static_cast<int32_t>(nc), 0};
+        }
+        moves[i] = mv;
+    }
+}
+
+__global__ void k_move_tasks(const int32_t* __restrict__ touched, const unsigned* __restrict__ n_touched,
+                             const RowMove* __restrict__ moves, const int64_t* __restrict__ ro,
+                             const int32_t* __restrict__ len, TierLists L) {
+    const unsigned count = *reinterpret_cast<const volatile unsigned*>(n_touched);
+    for (unsigned b0 = blockIdx.x * blockDim.x; b0 < count; b0 += gridDim.x * blockDim.x) {
+        const unsigned i = b0 + threadIdx.x;
+        bool has = false;
+        RowTask t{0, 0, static_cast<int32_t>(i)};
+        if (i < count && moves[i].off >= 0) {
+            has = true;
+            t.off = ro[touched[i]];
+            t.len = len[touched[i]];
+        }
+        tier_push(L, has, t);
+    }
+}
+
+// Copies the live entries of a moving out-row (deleted entries and edges into
+// dead vertices are dropped).
+struct MoveOut {
+    unsigned long long* xpe;
+    const uint8_t* alive;
+    RowMove* moves;
+    __device__ void operator()(const RowTask& t, int64_t e, bool in) const {
+        unsigned long long x = 0;
+        bool ok = false;
+        if (in) {
+            x = xpe[e];
+            ok = x != kRowTomb && alive[static_cast<int32_t>(static_cast<uint32_t>(x))];
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, ok);
+        if (b == 0u) return;
+        int base = 0;
+        if ((threadIdx.x & 31u) == 0u) base = atomicAdd(&moves[t.arg].len, __popc(b));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ok) xpe[moves[t.arg].off + base + __popc(b & ((1u << (threadIdx.x & 31u)) - 1u))] = x;
+    }
+};
+
+// The same for a moving in-row (entries of dead sources are dropped).
+struct MoveIn {
+    int32_t* ype;
+    const uint8_t* alive;
+    RowMove* moves;
+    __device__ void operator()(const RowTask& t, int64_t e, bool in) const {
+        int32_t x = 0;
+        bool ok = false;
+        if (in) {
+            x = ype[e];
+            ok = alive[x] != 0;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, ok);
+        if (b == 0u) return;
+        int base = 0;
+        if ((threadIdx.x & 31u) == 0u) base = atomicAdd(&moves[t.arg].len, __popc(b));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ok) ype[moves[t.arg].off + base + __popc(b & ((1u << (threadIdx.x & 31u)) - 1u))] = x;
+    }
+};
+
+__global__ void k_finish_moves(const int32_t* __restrict__ touched, const unsigned* __restrict__ n_touched,
+                               const RowMove* __restrict__ moves, int64_t* __restrict__ ro, int32_t* __restrict__ len,
+                               int32_t* __restrict__ cap) {
+    const unsigned count = *reinterpret_cast<const volatile unsigned*>(n_touched);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const RowMove mv = moves[i];
+        if (mv.off < 0) continue;
+        const int32_t v = touched[i];
+        ro[v] = mv.off;
+        len[v] = mv.len;
+        cap[v] = mv.cap;
+    }
+}
+
+// Appends every added copy to its out-row and its target's in-row.
+__global__ void k_place_adds_rows(const AddRec* __restrict__ add, const unsigned long long* __restrict__ nadd,
+                                  StoreView S) {
+    const int64_t count = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(nadd));
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const AddRec a = add[i];
+        const int32_t p = atomicAdd(&S.xlen[a.u], 1);
+        S.xpe[S.xro[a.u] + p] = pack_edge(a.l, a.w);
+        const int32_t q = atomicAdd(&S.ylen[a.w], 1);
+        S.ype[S.yro[a.w] + q] = a.u;
+    }
+}
+
+__global__ void k_clear_rows(const int32_t* __restrict__ touched, const unsigned* __restrict__ n_touched,
+                             int32_t* __restrict__ addc) {
+    const unsigned count = *reinterpret_cast<const volatile unsigned*>(n_touched);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        addc[touched[i]] = 0;
+}
+
 }  // namespace
 
 // Frees one buffer owned by ctx (stream-ordered).
@@ -400,36 +652,49 @@ bisim_status ensure_edge_sources(bisim_ctx* ctx, cudaStream_t s) {
     return BISIM_OK;
 }
 
-bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, uint8_t* vchanged,
-                                uint8_t* rowchg, uint8_t* killed, cudaStream_t s) {
-    const int32_t n = ctx->n;
-    const int64_t m = ctx->m;
-    cudaError_t e;
-    bisim_status st;
-    if ((st = ensure_edge_sources(ctx, s)) != BISIM_OK) return st;
+namespace {
 
-    // scratch for the batch
+// Scratch and results of the steps both batch paths share.
+struct Batch {
+    char* base = nullptr;
+    VertexOps V{};
+    int64_t nv = 0, ne = 0, vadds = 0;
+    const uint32_t* skhi = nullptr;
+    const uint32_t* sklo = nullptr;
+    const uint64_t* skp = nullptr;
+    KeyTable T{};
+    int64_t* keyslot = nullptr;
+    AddRec* add = nullptr;
+    unsigned long long* counters = nullptr;
+    int64_t* tmp = nullptr;
+    char* extra = nullptr;           // the path's own scratch
+};
+
+// The steps both paths share: checks (nothing of the graph changes before they
+// pass), grouping by vertex and by edge key, the final state of every named
+// vertex, and the batch's key table. `extra` bytes of path-specific scratch
+// follow the shared buffers; `alive0` (nullable) receives the liveness before
+// the batch and `revived` (nullable) the vertices that come back.
+bisim_status batch_begin(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, size_t extra, uint8_t* vchanged,
+                         uint8_t* killed, uint8_t* revived, uint8_t* alive0, Batch& B, cudaStream_t s) {
+    const int32_t n = ctx->n;
+    cudaError_t e;
     const size_t tmpw = std::max(radix_temp_words(std::max<int64_t>(nops, 1)), scan_temp_words(n + 1));
     const size_t nb = static_cast<size_t>(std::max<int64_t>(nops, 1));
+    uint32_t tsize = 64;
+    while (tsize < 2u * static_cast<uint32_t>(std::min<int64_t>(nops, 1 << 30))) tsize <<= 1;
     size_t bytes = 0;
     auto need = [&](size_t b) { bytes += (b + 255) & ~size_t(255); };
     need(4 * nb); need(4 * nb); need(8 * nb); need(8 * nb);          // vertex-op keys / values (x2)
     need(4 * nb); need(4 * nb); need(4 * nb); need(4 * nb);          // edge key halves (x2 each)
     need(8 * nb); need(8 * nb); need(8 * nb); need(8 * nb);          // edge positions (x4)
-    uint32_t tsize = 64;
-    while (tsize < 2u * static_cast<uint32_t>(std::min<int64_t>(nops, 1 << 30))) tsize <<= 1;
     need(sizeof(AddRec) * nb); need(8 * nb);                          // additions, key slots
     for (int q = 0; q < 7; ++q) need(4 * static_cast<size_t>(tsize)); // key table
     need(8 * 4);
     need(8 * tmpw);
-    need(std::max<int64_t>(m, 1));                                    // keep flags
-    need(4 * (n + 1)); need(4 * (n + 1)); need(4 * (n + 1));          // kept, addcnt, cursor
-    need(4 * (n + 1));                                                // dirty-row cursor
-    need(1 * (n + 1));                                                // rowdirty
-    need(8 * (n + 1));                                                // new degree
-    char* scratch = nullptr;
-    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s))) return cuda_error(ctx, e, "alloc update scratch");
-    char* base = scratch;
+    need(extra);
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&B.base), bytes, s))) return cuda_error(ctx, e, "alloc update scratch");
+    char* scratch = B.base;
     auto carve = [&](size_t b) { char* p = scratch; scratch += (b + 255) & ~size_t(255); return p; };
     uint32_t* vk0 = reinterpret_cast<uint32_t*>(carve(4 * nb));
     uint32_t* vk1 = reinterpret_cast<uint32_t*>(carve(4 * nb));
@@ -443,30 +708,18 @@ bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
     uint64_t* kp1 = reinterpret_cast<uint64_t*>(carve(8 * nb));
     uint64_t* kp2 = reinterpret_cast<uint64_t*>(carve(8 * nb));
     uint64_t* kp3 = reinterpret_cast<uint64_t*>(carve(8 * nb));
-    AddRec* add = reinterpret_cast<AddRec*>(carve(sizeof(AddRec) * nb));
-    int64_t* keyslot = reinterpret_cast<int64_t*>(carve(8 * nb));
-    KeyTable T;
+    B.add = reinterpret_cast<AddRec*>(carve(sizeof(AddRec) * nb));
+    B.keyslot = reinterpret_cast<int64_t*>(carve(8 * nb));
     int32_t* tab_arrays[7];
     for (int q = 0; q < 7; ++q) tab_arrays[q] = reinterpret_cast<int32_t*>(carve(4 * static_cast<size_t>(tsize)));
-    T.u = tab_arrays[0];
-    T.w = tab_arrays[1];
-    T.l = tab_arrays[2];
-    T.used = tab_arrays[3];
-    T.c0 = tab_arrays[4];
-    T.rem = tab_arrays[5];
-    T.taken = tab_arrays[6];
-    T.mask = tsize - 1;
-    unsigned long long* counters = reinterpret_cast<unsigned long long*>(carve(8 * 4));
-    int64_t* tmp = reinterpret_cast<int64_t*>(carve(8 * tmpw));
-    uint8_t* keepf = reinterpret_cast<uint8_t*>(carve(std::max<int64_t>(m, 1)));
-    int32_t* kept = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
-    int32_t* addcnt = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
-    int32_t* cursor = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
-    int32_t* dcursor = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
-    uint8_t* rowdirty = reinterpret_cast<uint8_t*>(carve(n + 1));
-    int64_t* ndeg = reinterpret_cast<int64_t*>(carve(8 * (n + 1)));
+    B.T = KeyTable{tab_arrays[0], tab_arrays[1], tab_arrays[2], tab_arrays[3], tab_arrays[4], tab_arrays[5],
+                   tab_arrays[6], tsize - 1};
+    B.counters = reinterpret_cast<unsigned long long*>(carve(8 * 4));
+    B.tmp = reinterpret_cast<int64_t*>(carve(8 * tmpw));
+    B.extra = carve(extra);
     auto fail = [&](bisim_status code, const char* msg) {
-        cudaFreeAsync(base, s);
+        cudaFreeAsync(B.base, s);
+        B.base = nullptr;
         return set_error(ctx, code, msg);
     };
 
@@ -477,65 +730,118 @@ bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
         Launch L(site_ops, s, 0, 0, 16.0 * nops);
         k_ops_check<<<grid_for(nops, 256), 256, 0, s>>>(d_ops, nops, n, ctx->dstate, vk0, vv0);
     }
-    int which = radix_sort_pairs(vk0, vv0, vk1, vv1, nops, 32, tmp, s);
+    const int which = radix_sort_pairs(vk0, vv0, vk1, vv1, nops, 32, B.tmp, s);
     const uint32_t* vkey = which ? vk1 : vk0;
     const uint64_t* vpos = which ? vv1 : vv0;
     cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); return cuda_error(ctx, e, "check update batch"); }
+    if ((e = cudaStreamSynchronize(s))) {
+        cudaFreeAsync(B.base, s);
+        B.base = nullptr;
+        return cuda_error(ctx, e, "check update batch");
+    }
     if (ctx->hstate->error & kErrBadOp) return fail(BISIM_EINVAL, "update batch names an out-of-range vertex or an unknown kind");
-    const int64_t nv = static_cast<int64_t>(ctx->hstate->aux);
-    const int64_t ne = nops - nv;
-    VertexOps V{vkey, vpos, nv, d_ops, ctx->alive};
+    B.nv = static_cast<int64_t>(ctx->hstate->aux);
+    B.vadds = static_cast<int64_t>(ctx->hstate->pairs);
+    B.ne = nops - B.nv;
+    B.V = VertexOps{vkey, vpos, B.nv, d_ops, ctx->alive};
+    const int64_t nv = B.nv, ne = B.ne;
 
     // 2. EDGE_ADD liveness and edge-key hashes, then group edge operations by key
     if (ne > 0) {
         Launch L(site_ops, s, 0, 0, 24.0 * ne);
-        k_edge_ops<<<grid_for(ne, 256), 256, 0, s>>>(V, vpos + nv, ne, klo0, khi0, kp0, ctx->dstate);
+        k_edge_ops<<<grid_for(ne, 256), 256, 0, s>>>(B.V, vpos + nv, ne, klo0, khi0, kp0, ctx->dstate);
     }
     cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); return cuda_error(ctx, e, "check edge operations"); }
+    if ((e = cudaStreamSynchronize(s))) {
+        cudaFreeAsync(B.base, s);
+        B.base = nullptr;
+        return cuda_error(ctx, e, "check edge operations");
+    }
     if (ctx->hstate->error & kErrDeadEndpoint) return fail(BISIM_EINVAL, "EDGE_ADD with an endpoint that is dead at that point of the batch");
 
     // ---- from here on the batch is valid and the graph changes ----
     // stable LSD sort of the edge operations by key hash: low half, then high
     // half; operations of one key stay in batch order
-    const uint32_t *skhi = khi0, *sklo = klo0;
-    const uint64_t* skp = kp0;
+    B.skhi = khi0;
+    B.sklo = klo0;
+    B.skp = kp0;
     if (ne > 0) {
-        const int wa = radix_sort_pairs(klo0, kp0, klo1, kp1, ne, 32, tmp, s);
+        const int wa = radix_sort_pairs(klo0, kp0, klo1, kp1, ne, 32, B.tmp, s);
         const uint64_t* posA = wa ? kp1 : kp0;
         k_key_halves<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, posA, ne, nullptr, khi0);
         cudaMemcpyAsync(kp2, posA, 8 * ne, cudaMemcpyDeviceToDevice, s);
-        const int wb = radix_sort_pairs(khi0, kp2, khi1, kp3, ne, 32, tmp, s);
-        skhi = wb ? khi1 : khi0;
-        skp = wb ? kp3 : kp2;
-        k_key_halves<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, skp, ne, klo0, nullptr);
-        sklo = klo0;
+        const int wb = radix_sort_pairs(khi0, kp2, khi1, kp3, ne, 32, B.tmp, s);
+        B.skhi = wb ? khi1 : khi0;
+        B.skp = wb ? kp3 : kp2;
+        k_key_halves<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, B.skp, ne, klo0, nullptr);
+        B.sklo = klo0;
     }
     cudaMemsetAsync(killed, 0, n + 1, s);
-    cudaMemsetAsync(counters, 0, 8 * 4, s);
+    cudaMemsetAsync(B.counters, 0, 8 * 4, s);
     for (int q = 3; q < 7; ++q) cudaMemsetAsync(tab_arrays[q], 0, 4 * static_cast<size_t>(tsize), s);
+    if (alive0 && n > 0) cudaMemcpyAsync(alive0, ctx->alive, n, cudaMemcpyDeviceToDevice, s);
     if (nv > 0) {
         Launch L(site_ops, s, 0, 0, 16.0 * nv);
-        k_vertex_final<<<grid_for(nv, 256), 256, 0, s>>>(V, ctx->alive, ctx->vlabel, killed, vchanged);
+        k_vertex_final<<<grid_for(nv, 256), 256, 0, s>>>(B.V, ctx->alive, ctx->vlabel, killed, vchanged, revived);
     }
     if (ne > 0) {
-        {
-            Launch L(site_ops, s, 0, 0, 32.0 * ne);
-            k_keys_insert<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, skhi, sklo, skp, ne, T, keyslot, &ctx->dstate->error);
-        }
-        if (m > 0) {
-            Launch L(site_ops, s, 0, m, 12.0 * m);
-            k_keys_count<<<grid_for(m, 256), 256, 0, s>>>(ctx->esrc, ctx->col, ctx->elab, m, T);
-        }
         Launch L(site_ops, s, 0, 0, 32.0 * ne);
-        k_fold_keys<<<grid_for(ne, 128), 128, 0, s>>>(V, skhi, sklo, skp, ne, keyslot, T, killed, add, counters,
-                                                     rowchg);
+        k_keys_insert<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, B.skhi, B.sklo, B.skp, ne, B.T, B.keyslot,
+                                                       &ctx->dstate->error);
     }
+    return BISIM_OK;
+}
+
+// Net effect of every key: copies to remove and copies to add (after the key
+// table's c0 holds the copies present before the batch).
+void fold_keys(const Batch& B, const uint8_t* killed, uint8_t* rowchg, cudaStream_t s) {
+    if (B.ne <= 0) return;
+    BISIM_SITE(site_ops, "update_ops");
+    Launch L(site_ops, s, 0, 0, 32.0 * B.ne);
+    k_fold_keys<<<grid_for(B.ne, 128), 128, 0, s>>>(B.V, B.skhi, B.sklo, B.skp, B.ne, B.keyslot, B.T, killed, B.add,
+                                                   B.counters, rowchg);
+}
+
+}  // namespace
+
+bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, uint8_t* vchanged,
+                                uint8_t* rowchg, uint8_t* killed, cudaStream_t s) {
+    const int32_t n = ctx->n;
+    const int64_t m = ctx->m;
+    cudaError_t e;
+    bisim_status st;
+    if ((st = ensure_edge_sources(ctx, s)) != BISIM_OK) return st;
+    size_t extra = 0;
+    auto need = [&](size_t b) { extra += (b + 255) & ~size_t(255); };
+    need(std::max<int64_t>(m, 1));                                    // keep flags
+    need(4 * (n + 1)); need(4 * (n + 1)); need(4 * (n + 1));          // kept, addcnt, cursor
+    need(4 * (n + 1));                                                // dirty-row cursor
+    need(1 * (n + 1));                                                // rowdirty
+    need(8 * (n + 1));                                                // new degree
+    Batch B;
+    if ((st = batch_begin(ctx, d_ops, nops, extra, vchanged, killed, nullptr, nullptr, B, s)) != BISIM_OK) return st;
+    char* scratch = B.extra;
+    auto carve = [&](size_t b) { char* p = scratch; scratch += (b + 255) & ~size_t(255); return p; };
+    uint8_t* keepf = reinterpret_cast<uint8_t*>(carve(std::max<int64_t>(m, 1)));
+    int32_t* kept = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
+    int32_t* addcnt = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
+    int32_t* cursor = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
+    int32_t* dcursor = reinterpret_cast<int32_t*>(carve(4 * (n + 1)));
+    uint8_t* rowdirty = reinterpret_cast<uint8_t*>(carve(n + 1));
+    int64_t* ndeg = reinterpret_cast<int64_t*>(carve(8 * (n + 1)));
+    const int64_t ne = B.ne;
+    KeyTable& T = B.T;
+    BISIM_SITE(site_ops, "update_ops");
+    if (ne > 0 && m > 0) {
+        Launch L(site_ops, s, 0, m, 12.0 * m);
+        k_keys_count<<<grid_for(m, 256), 256, 0, s>>>(ctx->esrc, ctx->col, ctx->elab, m, T);
+    }
+    fold_keys(B, killed, rowchg, s);
     unsigned long long hc[2] = {0, 0};
-    cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); return cuda_error(ctx, e, "fold edge operations"); }
+    cudaMemcpyAsync(hc, B.counters, sizeof(hc), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(B.base, s); return cuda_error(ctx, e, "fold edge operations"); }
     const int64_t nadd = static_cast<int64_t>(hc[1]);
+    AddRec* add = B.add;
 
     // 3. rewrite the CSR
     BISIM_SITE(site_csr, "update_csr");
@@ -559,19 +865,19 @@ bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
     }
     int64_t* nrp = nullptr;
     if ((e = cudaMallocAsync(reinterpret_cast<void**>(&nrp), sizeof(int64_t) * (n + 1), s))) {
-        cudaFreeAsync(base, s);
+        cudaFreeAsync(B.base, s);
         return cuda_error(ctx, e, "alloc row_ptr");
     }
-    exclusive_scan_i64(ndeg, nrp, n + 1, tmp, s);
+    exclusive_scan_i64(ndeg, nrp, n + 1, B.tmp, s);
     int64_t new_m = 0;
     cudaMemcpyAsync(&new_m, nrp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); cudaFreeAsync(nrp, s); return cuda_error(ctx, e, "size new CSR"); }
+    if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(B.base, s); cudaFreeAsync(nrp, s); return cuda_error(ctx, e, "size new CSR"); }
     int32_t *ncol = nullptr, *nelab = nullptr, *nsrc = nullptr;
     const size_t cap = static_cast<size_t>(std::max<int64_t>(new_m, 1));
     if ((e = cudaMallocAsync(reinterpret_cast<void**>(&ncol), 4 * cap, s)) ||
         (e = cudaMallocAsync(reinterpret_cast<void**>(&nelab), 4 * cap, s)) ||
         (e = cudaMallocAsync(reinterpret_cast<void**>(&nsrc), 4 * cap, s))) {
-        cudaFreeAsync(base, s);
+        cudaFreeAsync(B.base, s);
         return cuda_error(ctx, e, "alloc new CSR");
     }
     if (m > 0) {
@@ -595,12 +901,156 @@ bisim_status apply_ops_to_graph(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
     ctx->device_bytes += 12 * static_cast<int64_t>(cap);
     cudaMemcpyAsync(ctx->row_ptr, nrp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s);
     cudaFreeAsync(nrp, s);
-    cudaFreeAsync(base, s);
+    cudaFreeAsync(B.base, s);
     ctx->m = new_m;
     ctx->stats.n_edges = new_m;
     ctx->stats.updates_applied += nops;
     if ((e = cudaGetLastError())) return cuda_error(ctx, e, "apply update batch");
     return BISIM_OK;
+}
+
+// The same batch applied to the row store: rows are edited in place, so the
+// cost follows the rows the batch touches. Order: copies of every key present
+// before the batch, the fold, deletion of the removed copies, deleted and
+// revived vertices, then the added copies (rows that run out of room move to
+// the pool's tail first). The CSR is left stale.
+bisim_status apply_ops_to_store(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, uint8_t* vchanged,
+                                uint8_t* rowchg, uint8_t* killed, cudaStream_t s) {
+    const int32_t n = ctx->n;
+    const size_t nn = static_cast<size_t>(std::max(n, 1)) + 1;
+    const size_t nb = static_cast<size_t>(std::max<int64_t>(nops, 1));
+    cudaError_t e;
+    bisim_status st;
+    // extra scratch: revived and alive0 flags, two task lists of nops rows per tier,
+    // touched rows and their moves (out and in), counters
+    size_t extra = 0;
+    auto need = [&](size_t b) { extra += (b + 255) & ~size_t(255); };
+    need(nn); need(nn);
+    need(3 * sizeof(RowTask) * nb); need(3 * sizeof(RowTask) * nb);
+    need(4 * nb); need(4 * nb); need(sizeof(RowMove) * nb); need(sizeof(RowMove) * nb);
+    need(64);
+    Batch B;
+    uint8_t* revived = nullptr;
+    uint8_t* alive0 = nullptr;
+    {
+        // the flags are carved first, before batch_begin needs them: allocate them separately
+        if ((e = cudaMallocAsync(reinterpret_cast<void**>(&revived), 2 * nn, s))) return cuda_error(ctx, e, "alloc update flags");
+        alive0 = revived + nn;
+        cudaMemsetAsync(revived, 0, nn, s);
+    }
+    if ((st = batch_begin(ctx, d_ops, nops, extra, vchanged, killed, revived, alive0, B, s)) != BISIM_OK) {
+        cudaFreeAsync(revived, s);
+        return st;
+    }
+    auto done = [&](bisim_status r) {
+        cudaFreeAsync(B.base, s);
+        cudaFreeAsync(revived, s);
+        return r;
+    };
+    char* scratch = B.extra;
+    auto carve = [&](size_t b) { char* p = scratch; scratch += (b + 255) & ~size_t(255); return p; };
+    carve(nn);
+    carve(nn);
+    RowTask* ta = reinterpret_cast<RowTask*>(carve(3 * sizeof(RowTask) * nb));
+    RowTask* tb = reinterpret_cast<RowTask*>(carve(3 * sizeof(RowTask) * nb));
+    int32_t* touched_o = reinterpret_cast<int32_t*>(carve(4 * nb));
+    int32_t* touched_i = reinterpret_cast<int32_t*>(carve(4 * nb));
+    RowMove* moves_o = reinterpret_cast<RowMove*>(carve(sizeof(RowMove) * nb));
+    RowMove* moves_i = reinterpret_cast<RowMove*>(carve(sizeof(RowMove) * nb));
+    unsigned* cnts = reinterpret_cast<unsigned*>(carve(64));     // [0..2] list A, [4..6] list B, [8..9] touched
+    TierLists LA{{ta, ta + nb, ta + 2 * nb}, cnts};
+    TierLists LB{{tb, tb + nb, tb + 2 * nb}, cnts + 4};
+    unsigned* n_touched = cnts + 8;
+    const StoreView S{ctx->xro, ctx->xlen, ctx->xcap, ctx->xpe, ctx->yro, ctx->ylen, ctx->ycap, ctx->ype};
+    const int64_t nv = B.nv, ne = B.ne;
+    KeyTable& T = B.T;
+    const int grid = kTierGrid;
+    BISIM_SITE(site, "update_rows");
+
+    // copies present before the batch, the fold, and the deletions of copies
+    if (ne > 0) {
+        Launch L(site, s, 0, 0, 0.0);
+        cudaMemsetAsync(cnts, 0, 16, s);
+        k_key_tasks<<<grid_for(ne, 256), 256, 0, s>>>(B.keyslot, ne, T, killed, alive0, S, 0, LA);
+        run_tiers(LA, KeyCount{ctx->xpe, T}, s);
+    }
+    fold_keys(B, killed, rowchg, s);
+    if (ne > 0) {
+        Launch L(site, s, 0, 0, 0.0);
+        cudaMemsetAsync(cnts, 0, 16, s);
+        k_key_tasks<<<grid_for(ne, 256), 256, 0, s>>>(B.keyslot, ne, T, killed, alive0, S, 1, LA);
+        run_tiers(LA, KeyRemove{ctx->xpe, T}, s);
+    }
+    // deleted and revived vertices
+    if (nv > 0) {
+        RowTask* pt = tb;
+        void* pmem = nullptr;
+        int64_t pcap = static_cast<int64_t>(nb);
+        if (B.vadds > 0) {
+            // revived vertices: one purge task per entry of their in-rows
+            unsigned long long* dneed = reinterpret_cast<unsigned long long*>(cnts + 12);
+            cudaMemsetAsync(dneed, 0, 8, s);
+            k_vertex_tasks<<<grid_for(nv, 256), 256, 0, s>>>(B.V, killed, revived, S, LA, dneed);
+            unsigned long long hneed = 0;
+            cudaMemcpyAsync(&hneed, dneed, 8, cudaMemcpyDeviceToHost, s);
+            if ((e = cudaStreamSynchronize(s))) return done(cuda_error(ctx, e, "size revival purge"));
+            if (static_cast<int64_t>(hneed) > pcap) {
+                pcap = static_cast<int64_t>(hneed);
+                if ((e = cudaMallocAsync(&pmem, 3 * sizeof(RowTask) * static_cast<size_t>(pcap), s)))
+                    return done(cuda_error(ctx, e, "alloc revival purge"));
+                pt = static_cast<RowTask*>(pmem);
+            }
+        }
+        const TierLists LP{{pt, pt + pcap, pt + 2 * pcap}, cnts + 4};
+        Launch L(site, s, 0, 0, 0.0);
+        cudaMemsetAsync(cnts, 0, 32, s);
+        k_vertex_tasks<<<grid_for(nv, 256), 256, 0, s>>>(B.V, killed, revived, S, LA, nullptr);
+        run_tiers(LA, VertexSources{ctx->ype, killed, revived, rowchg, S, LP}, s);
+        run_tiers(LP, PurgeTarget{ctx->xpe}, s);
+        k_vertex_rows<<<grid_for(nv, 256), 256, 0, s>>>(B.V, killed, revived, S);
+        if (pmem) cudaFreeAsync(pmem, s);
+    }
+    // added copies: rows that cannot take them move first
+    for (int attempt = 0;; ++attempt) {
+        {
+            Launch L(site, s, 0, 0, 0.0);
+            cudaMemsetAsync(n_touched, 0, 8, s);
+            cudaMemsetAsync(ctx->dtail + 2, 0, 16, s);
+            k_add_rows<<<grid, 256, 0, s>>>(B.add, B.counters + 1, ctx->addo, ctx->addi, touched_o, touched_i, n_touched);
+            k_plan_rows<<<grid, 256, 0, s>>>(touched_o, n_touched, ctx->addo, ctx->xlen, ctx->xcap, ctx->dtail,
+                                             ctx->xpool, ctx->dtail + 2, moves_o);
+            k_plan_rows<<<grid, 256, 0, s>>>(touched_i, n_touched + 1, ctx->addi, ctx->ylen, ctx->ycap, ctx->dtail + 1,
+                                             ctx->ypool, ctx->dtail + 3, moves_i);
+        }
+        int64_t tails[4] = {0, 0, 0, 0};       // out / in tails, out / in room asked for
+        cudaMemcpyAsync(tails, ctx->dtail, sizeof(tails), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s))) return done(cuda_error(ctx, e, "plan row moves"));
+        if (tails[0] <= ctx->xpool && tails[1] <= ctx->ypool) break;
+        if (attempt > 0) return done(set_error(ctx, BISIM_ENOMEM, "row store full after a rebuild"));
+        // a pool is full: rebuild the store (compacted, with room for these moves) and plan again
+        k_clear_rows<<<grid, 256, 0, s>>>(touched_o, n_touched, ctx->addo);
+        k_clear_rows<<<grid, 256, 0, s>>>(touched_i, n_touched + 1, ctx->addi);
+        ctx->csr_stale = true;
+        if ((st = store_build(ctx, s, 2 * tails[2], 2 * tails[3])) != BISIM_OK) return done(st);
+    }
+    {
+        const StoreView S2{ctx->xro, ctx->xlen, ctx->xcap, ctx->xpe, ctx->yro, ctx->ylen, ctx->ycap, ctx->ype};
+        Launch L(site, s, 0, 0, 0.0);
+        cudaMemsetAsync(cnts, 0, 32, s);
+        k_move_tasks<<<grid, 256, 0, s>>>(touched_o, n_touched, moves_o, ctx->xro, ctx->xlen, LA);
+        k_move_tasks<<<grid, 256, 0, s>>>(touched_i, n_touched + 1, moves_i, ctx->yro, ctx->ylen, LB);
+        run_tiers(LA, MoveOut{ctx->xpe, ctx->alive, moves_o}, s);
+        run_tiers(LB, MoveIn{ctx->ype, ctx->alive, moves_i}, s);
+        k_finish_moves<<<grid, 256, 0, s>>>(touched_o, n_touched, moves_o, ctx->xro, ctx->xlen, ctx->xcap);
+        k_finish_moves<<<grid, 256, 0, s>>>(touched_i, n_touched + 1, moves_i, ctx->yro, ctx->ylen, ctx->ycap);
+        k_place_adds_rows<<<grid, 256, 0, s>>>(B.add, B.counters + 1, S2);
+        k_clear_rows<<<grid, 256, 0, s>>>(touched_o, n_touched, ctx->addo);
+        k_clear_rows<<<grid, 256, 0, s>>>(touched_i, n_touched + 1, ctx->addi);
+    }
+    ctx->csr_stale = true;
+    ctx->stats.updates_applied += nops;
+    if ((e = cudaGetLastError())) return done(cuda_error(ctx, e, "apply update batch"));
+    return done(BISIM_OK);
 }
 
 }  // namespace bisim
