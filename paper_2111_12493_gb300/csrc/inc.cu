@@ -42,6 +42,9 @@ constexpr int32_t kNew = -3;
 constexpr int kCmpThreads = 256;
 constexpr int kCmpSmallSlots = 4096;     // shared-memory set for lists up to 2048 values
 constexpr int kCmpLargeSlots = 16384;    // ... up to 8192 values
+constexpr int kCmpGrid = 304;            // compare CTAs (the candidate count is read on the device)
+// list classes kSmallClasses + 6 and up hold rows of more than 2^11 entries
+static_assert(kCmpSmallSlots / 2 == 1 << 11, "small compare set reach and class boundary differ");
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 unsigned grid_for(int64_t n, int threads) {
@@ -147,77 +150,147 @@ __global__ void k_set_flags(const int32_t* __restrict__ list, int64_t count, uin
     if (i < count) flag[list[i]] = v;
 }
 
+// Kernels launched before the host knows the frontier's size read it on the
+// device and stride over it with a fixed grid.
+constexpr int kDevGrid = 152 * 8;
+
+__device__ __forceinline__ int64_t dev_count(const unsigned long long* c) {
+    return static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(c));
+}
+
 // ----------------------------------------------------------------------------- frontier degree buckets
 
-__global__ void k_list_classify(const int32_t* __restrict__ list, int64_t count, const int32_t* __restrict__ rl,
-                                int small_max, int mid_max, uint32_t* __restrict__ keys, uint64_t* __restrict__ vals) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const int32_t v = list[i];
-    const int64_t d = rl[v];
-    uint32_t c;
-    if (d <= small_max || d == 0) {
-        c = d <= 4 ? 0u : d <= 8 ? 1u : d <= 16 ? 2u : 3u;
-    } else if (d <= mid_max) {
+// A hub of the live frontier with its row bounds (read back to lay out its chunks).
+struct HubInfo {
+    int32_t v;
+    int32_t len;
+    int64_t off;
+};
+
+__device__ __forceinline__ int list_class(int64_t d, int small_max, int mid_max) {
+    if (d <= small_max || d == 0) return d <= 4 ? 0 : d <= 8 ? 1 : d <= 16 ? 2 : 3;
+    if (d <= mid_max) {
         int lg = 64 - __clzll(static_cast<unsigned long long>(d - 1));
         lg = lg < 6 ? 6 : lg;
-        c = static_cast<uint32_t>(kSmallClasses + (lg - 6));
-    } else {
-        c = kClassHub;
+        return kSmallClasses + (lg - 6);
     }
-    keys[i] = c;
-    vals[i] = static_cast<uint64_t>(v);
+    return kClassHub;
 }
 
-__global__ void k_list_bounds(const uint32_t* __restrict__ cls, const uint64_t* __restrict__ vals, int64_t count,
-                              const int32_t* __restrict__ rl, int64_t* __restrict__ begin,
-                              unsigned long long* __restrict__ edges, int32_t* __restrict__ out) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const int c = static_cast<int>(cls[i]);
-    const int p = i == 0 ? -1 : static_cast<int>(cls[i - 1]);
-    for (int q = p + 1; q <= c; ++q) begin[q] = i;
-    const int32_t v = static_cast<int32_t>(vals[i]);
-    out[i] = v;
-    atomicAdd(&edges[c], static_cast<unsigned long long>(rl[v]));
+// Vertices and row entries per class over the live frontier (W.counters[7]
+// vertices), one atomic per class per CTA.
+__global__ void __launch_bounds__(256) k_class_count(const int32_t* __restrict__ FL,
+                                                     const unsigned long long* __restrict__ dfl,
+                                                     const int32_t* __restrict__ rl, int small_max, int mid_max,
+                                                     unsigned long long* __restrict__ ccount,
+                                                     unsigned long long* __restrict__ cedges) {
+    __shared__ unsigned sc[kNumClasses];
+    __shared__ unsigned long long se[kNumClasses];
+    if (threadIdx.x < kNumClasses) {
+        sc[threadIdx.x] = 0u;
+        se[threadIdx.x] = 0ull;
+    }
+    __syncthreads();
+    const int64_t fl = dev_count(dfl);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < fl;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t d = rl[FL[i]];
+        const int c = list_class(d, small_max, mid_max);
+        atomicAdd(&sc[c], 1u);
+        atomicAdd(&se[c], static_cast<unsigned long long>(d));
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumClasses && sc[threadIdx.x]) {
+        atomicAdd(&ccount[threadIdx.x], static_cast<unsigned long long>(sc[threadIdx.x]));
+        atomicAdd(&cedges[threadIdx.x], se[threadIdx.x]);
+    }
 }
 
-__global__ void k_row_bounds(const int32_t* __restrict__ list, int64_t count, const int64_t* __restrict__ ro,
-                             const int32_t* __restrict__ rl, int64_t* __restrict__ out) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < count) {
-        out[2 * i] = ro[list[i]];
-        out[2 * i + 1] = ro[list[i]] + rl[list[i]];
+__global__ void k_class_scan(const unsigned long long* __restrict__ ccount, int64_t* __restrict__ begin,
+                             unsigned long long* __restrict__ cursor) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t acc = 0;
+    for (int c = 0; c < kNumClasses; ++c) {
+        begin[c] = acc;
+        cursor[c] = static_cast<unsigned long long>(acc);
+        acc += static_cast<int64_t>(ccount[c]);
+    }
+    begin[kNumClasses] = acc;
+}
+
+// Places every live frontier vertex in its class's range (any order inside a
+// class); hubs also go to `hubs` with their row bounds.
+__global__ void __launch_bounds__(256) k_class_scatter(const int32_t* __restrict__ FL,
+                                                       const unsigned long long* __restrict__ dfl,
+                                                       const int64_t* __restrict__ ro, const int32_t* __restrict__ rl,
+                                                       int small_max, int mid_max,
+                                                       unsigned long long* __restrict__ cursor,
+                                                       int32_t* __restrict__ out, HubInfo* __restrict__ hubs,
+                                                       unsigned* __restrict__ n_hubs) {
+    __shared__ unsigned cnt[kNumClasses];
+    __shared__ unsigned long long base[kNumClasses];
+    const int64_t fl = dev_count(dfl);
+    for (int64_t b0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; b0 < fl;
+         b0 += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (threadIdx.x < kNumClasses) cnt[threadIdx.x] = 0u;
+        __syncthreads();
+        const int64_t i = b0 + threadIdx.x;
+        int c = -1;
+        int32_t v = 0;
+        unsigned rank = 0;
+        if (i < fl) {
+            v = FL[i];
+            c = list_class(rl[v], small_max, mid_max);
+            rank = atomicAdd(&cnt[c], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < kNumClasses && cnt[threadIdx.x])
+            base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], static_cast<unsigned long long>(cnt[threadIdx.x]));
+        __syncthreads();
+        if (c >= 0) {
+            out[base[c] + rank] = v;
+            if (c == kClassHub) hubs[atomicAdd(n_hubs, 1u)] = HubInfo{v, rl[v], ro[v]};
+        }
+        __syncthreads();
     }
 }
 
 // ----------------------------------------------------------------------------- level passes
 
-// 1. frontier vertices leave their old blocks
-__global__ void k_remove(const int32_t* __restrict__ F, int64_t f, Level L, Work W) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= f) return;
-    const int32_t v = F[i];
-    const int32_t b = L.lid[v];
-    W.old[v] = b;
-    if (b < 0) return;
-    atomicSub(&L.bcnt[b], 1);
-    atomicAdd(&W.cntF[b], 1u);
-    if (atomicExch(&W.touched[b], 1u) == 0u) W.tlist[atomicAdd(&W.counters[0], 1ull)] = b;
-    if (L.bmin[b] == v && atomicExch(&W.dirty[b], 1u) == 0u) W.dlist[atomicAdd(&W.counters[1], 1ull)] = b;
+// 1. frontier vertices (W.counters[6] of them) are flagged and leave their old blocks
+__global__ void k_remove(const int32_t* __restrict__ F, Level L, Work W) {
+    const int64_t f = dev_count(&W.counters[6]);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < f;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t v = F[i];
+        W.inF[v] = 1;
+        const int32_t b = L.lid[v];
+        W.old[v] = b;
+        if (b < 0) continue;
+        atomicSub(&L.bcnt[b], 1);
+        atomicAdd(&W.cntF[b], 1u);
+        if (atomicExch(&W.touched[b], 1u) == 0u) W.tlist[atomicAdd(&W.counters[0], 1ull)] = b;
+        if (L.bmin[b] == v && atomicExch(&W.dirty[b], 1u) == 0u) W.dlist[atomicAdd(&W.counters[1], 1ull)] = b;
+    }
 }
 
-__global__ void k_dirty_reset(const int32_t* __restrict__ dlist, int64_t nd, Level L) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < nd) L.bmin[dlist[i]] = INT_MAX;
+__global__ void k_dirty_reset(const int32_t* __restrict__ dlist, Level L, Work W) {
+    const int64_t nd = dev_count(&W.counters[1]);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nd;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        L.bmin[dlist[i]] = INT_MAX;
 }
 
-// smallest remaining member of every block whose minimum left
+// smallest remaining member of every block whose minimum left (nothing to do
+// when no minimum left)
 __global__ void k_rescan(int32_t n, const uint8_t* __restrict__ alive, Level L, Work W) {
-    const int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (u >= n || !alive[u] || W.inF[u]) return;
-    const int32_t b = L.lid[u];
-    if (b >= 0 && W.dirty[b]) atomicMin(&L.bmin[b], static_cast<int32_t>(u));
+    if (dev_count(&W.counters[1]) == 0) return;
+    for (int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; u < n;
+         u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (!alive[u] || W.inF[u]) continue;
+        const int32_t b = L.lid[u];
+        if (b >= 0 && W.dirty[b]) atomicMin(&L.bmin[b], static_cast<int32_t>(u));
+    }
 }
 
 // group statistics of the live frontier
@@ -340,7 +413,7 @@ __device__ __forceinline__ bool row_entry(const unsigned long long* pe, int64_t 
 // list of a hub representative (above 8192 values) is looked up in its
 // dedup table. One CTA per candidate.
 template <int SLOTS>
-__global__ void __launch_bounds__(kCmpThreads) k_compare(int64_t ncand, Level L, Level Lprev, Work W,
+__global__ void __launch_bounds__(kCmpThreads) k_compare(const unsigned long long* dcand, Level L, Level Lprev, Work W,
                                                          const int64_t* __restrict__ ro, const int32_t* __restrict__ rl,
                                                          const unsigned long long* __restrict__ pe,
                                                          const int32_t* __restrict__ cnt,
@@ -352,6 +425,7 @@ __global__ void __launch_bounds__(kCmpThreads) k_compare(int64_t ncand, Level L,
                                                          const HubAcc* __restrict__ acc, int lo_c, int hi_c) {
     extern __shared__ unsigned long long tab[];
     __shared__ unsigned zero;
+    const int64_t ncand = dev_count(dcand);
     for (int64_t i = blockIdx.x; i < ncand; i += gridDim.x) {
         const int32_t g = W.cand[i];
         const int32_t b = W.candb[i];
@@ -414,6 +488,7 @@ __global__ void __launch_bounds__(kCmpThreads) k_compare(int64_t ncand, Level L,
 
 // 4. groups without a live match: keep the old id if the membership is that
 // of one old block, else take a fresh id. Also (re)keys the index.
+// acc[0] index tombstones made, acc[1] rebuild flags, acc[2] tombstones reused
 __global__ void k_settle(const int32_t* __restrict__ FL, int64_t fl, Level L, Work W, int64_t* __restrict__ bnext,
                          int64_t bcap, unsigned long long* __restrict__ counters) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -438,7 +513,7 @@ __global__ void k_settle(const int32_t* __restrict__ FL, int64_t fl, Level L, Wo
                 if (L.ikey[pos] == kIdxEmpty) break;
                 if (L.ikey[pos] == okey && L.ibid[pos] == b) {
                     L.ikey[pos] = kIdxTomb;
-                    atomicAdd(&counters[3], 1ull);
+                    atomicAdd(&counters[0], 1ull);
                     break;
                 }
                 pos = (pos + 1) & L.imask;
@@ -451,7 +526,7 @@ __global__ void k_settle(const int32_t* __restrict__ FL, int64_t fl, Level L, Wo
     } else {
         const long long nb = atomicAdd(reinterpret_cast<unsigned long long*>(bnext), 1ull);
         if (nb >= bcap) {
-            atomicOr(reinterpret_cast<unsigned*>(&counters[4]), 1u);   // out of block ids: rebuild
+            atomicOr(reinterpret_cast<unsigned*>(&counters[1]), 1u);   // out of block ids: rebuild
             W.decision[g] = kNew;
             return;
         }
@@ -468,14 +543,14 @@ __global__ void k_settle(const int32_t* __restrict__ FL, int64_t fl, Level L, Wo
             const unsigned long long prev = atomicCAS(&L.ikey[pos], cur, key);
             if (prev == cur) {
                 L.ibid[pos] = b;
-                if (cur == kIdxTomb) atomicAdd(&counters[5], 1ull);   // a tombstone reused
+                if (cur == kIdxTomb) atomicAdd(&counters[2], 1ull);   // a tombstone reused
                 return;
             }
             continue;                                       // lost the slot: look at it again
         }
         pos = (pos + 1) & L.imask;
     }
-    atomicOr(reinterpret_cast<unsigned*>(&counters[4]), 2u);   // index full
+    atomicOr(reinterpret_cast<unsigned*>(&counters[1]), 2u);   // index full
 }
 
 // 5. frontier vertices take their blocks
@@ -513,6 +588,7 @@ __global__ void k_retire(const int32_t* __restrict__ tlist, int64_t nt, Level L,
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nt) return;
     const int32_t b = tlist[i];
+    // (counters: the level's accumulators, as for k_settle)
     W.touched[b] = 0u;
     W.dirty[b] = 0u;
     W.cntF[b] = 0u;
@@ -524,7 +600,7 @@ __global__ void k_retire(const int32_t* __restrict__ tlist, int64_t nt, Level L,
         if (k == kIdxEmpty) return;
         if (k == key && L.ibid[pos] == b) {
             L.ikey[pos] = kIdxTomb;
-            atomicAdd(&counters[3], 1ull);
+            atomicAdd(&counters[0], 1ull);
             return;
         }
         pos = (pos + 1) & L.imask;
@@ -560,39 +636,61 @@ Level level_view(const bisim_ctx* ctx, int j) {
                  ctx->isize - 1};
 }
 
-// Scratch that lives for one batch.
+constexpr int kHubPrefetch = 2048;     // hub records read back with the level's counts
+
+// Host copies of everything a level pass reads back, in pinned memory so that
+// the copies queue behind the level's kernels and one synchronisation covers them.
+struct HostStage {
+    unsigned long long counters[8];
+    int64_t begin[kNumClasses + 1];
+    unsigned long long edges[kNumClasses];
+    unsigned n_hubs;
+    unsigned err;
+    unsigned long long ncand;
+    int64_t bnext[kMaxIncLevels + 1];
+    unsigned long long acc[kMaxIncLevels + 1][4];
+    HubInfo hubs[kHubPrefetch];
+};
+
+// Work buffers of the incremental path, kept between batches.
 struct Scratch {
     char* base = nullptr;
     Work W{};
-    int64_t* dbnext = nullptr;
-    uint32_t* ck0 = nullptr;
-    uint32_t* ck1 = nullptr;
-    uint64_t* cv0 = nullptr;
-    uint64_t* cv1 = nullptr;
-    int64_t* ctmp = nullptr;
-    int32_t* blist = nullptr;
-    int64_t* dbegin = nullptr;
-    unsigned long long* dedges = nullptr;
+    int64_t* dbnext = nullptr;         // [kMaxIncLevels + 1] next unused block id per level
+    unsigned long long* dacc = nullptr;   // [kMaxIncLevels + 1][4] per-level accumulators (k_settle)
+    int32_t* blist = nullptr;          // [n] live frontier grouped by class
+    int64_t* dbegin = nullptr;         // [kNumClasses + 1]
+    unsigned long long* ccount = nullptr;   // [kNumClasses] vertices per class
+    unsigned long long* cedges = nullptr;   // [kNumClasses] row entries per class
+    unsigned long long* ccursor = nullptr;  // [kNumClasses]
+    HubInfo* hubs = nullptr;           // [n]
+    unsigned* n_hubs = nullptr;
     int32_t* clist = nullptr;          // [n] vertices whose block changed one level down
-    unsigned long long* ccount = nullptr;
+    unsigned long long* chcount = nullptr;
     TierLists tiers{};                 // in-row tasks, [n] per tier
+    HostStage* h = nullptr;            // pinned
 };
 
 cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     const size_t n = static_cast<size_t>(std::max(ctx->n, 1));
     const size_t bc = static_cast<size_t>(ctx->bcap);
-    const size_t tw = radix_temp_words(static_cast<int64_t>(n));
+    constexpr size_t L = kMaxIncLevels + 1;
     size_t bytes = 0;
     auto need = [&](size_t b) { bytes += (b + 255) & ~size_t(255); };
     need(4 * n); need(4 * n); need(8 * n); need(4 * n); need(4 * n); need(4 * n); need(4 * n); need(8 * n);
     need(4 * bc); need(4 * bc); need(4 * bc); need(4 * bc); need(4 * bc);
     need(4 * n); need(4 * n); need(8 * 8); need(4 * n); need(4 * n); need(n); need(n); need(n);
-    need(8 * 2); need(32);
-    need(4 * n); need(4 * n); need(8 * n); need(8 * n); need(8 * tw); need(4 * n);
-    need(8 * (kNumClasses + 1)); need(8 * kNumClasses);
-    need(4 * n); need(3 * sizeof(RowTask) * n); need(16); need(16);
+    need(8 * L); need(32 * L); need(32);
+    need(4 * n); need(8 * (kNumClasses + 1)); need(8 * kNumClasses); need(8 * kNumClasses); need(8 * kNumClasses);
+    need(sizeof(HubInfo) * std::max<size_t>(n, kHubPrefetch)); need(16);
+    need(4 * n); need(16); need(3 * sizeof(RowTask) * n); need(16);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&S.base), bytes, s);
     if (e) return e;
+    if ((e = cudaHostAlloc(reinterpret_cast<void**>(&S.h), sizeof(HostStage), cudaHostAllocDefault))) {
+        cudaFreeAsync(S.base, s);
+        S.base = nullptr;
+        return e;
+    }
     char* p = S.base;
     auto carve = [&](size_t b) { char* q = p; p += (b + 255) & ~size_t(255); return q; };
     Work& W = S.W;
@@ -617,23 +715,25 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     W.inF = reinterpret_cast<uint8_t*>(carve(n));
     W.changed = reinterpret_cast<uint8_t*>(carve(n));
     W.next = reinterpret_cast<uint8_t*>(carve(n));
-    S.dbnext = reinterpret_cast<int64_t*>(carve(8 * 2));
+    S.dbnext = reinterpret_cast<int64_t*>(carve(8 * L));
+    S.dacc = reinterpret_cast<unsigned long long*>(carve(32 * L));
     W.err = reinterpret_cast<unsigned*>(carve(32));
     W.n = ctx->n;
     W.bcap = ctx->bcap;
-    cudaMemsetAsync(W.err, 0, 32, s);
-    S.ck0 = reinterpret_cast<uint32_t*>(carve(4 * n));
-    S.ck1 = reinterpret_cast<uint32_t*>(carve(4 * n));
-    S.cv0 = reinterpret_cast<uint64_t*>(carve(8 * n));
-    S.cv1 = reinterpret_cast<uint64_t*>(carve(8 * n));
-    S.ctmp = reinterpret_cast<int64_t*>(carve(8 * tw));
     S.blist = reinterpret_cast<int32_t*>(carve(4 * n));
     S.dbegin = reinterpret_cast<int64_t*>(carve(8 * (kNumClasses + 1)));
-    S.dedges = reinterpret_cast<unsigned long long*>(carve(8 * kNumClasses));
+    S.ccount = reinterpret_cast<unsigned long long*>(carve(8 * kNumClasses));
+    S.cedges = reinterpret_cast<unsigned long long*>(carve(8 * kNumClasses));
+    S.ccursor = reinterpret_cast<unsigned long long*>(carve(8 * kNumClasses));
+    S.hubs = reinterpret_cast<HubInfo*>(carve(sizeof(HubInfo) * std::max<size_t>(n, kHubPrefetch)));
+    S.n_hubs = reinterpret_cast<unsigned*>(carve(16));
     S.clist = reinterpret_cast<int32_t*>(carve(4 * n));
+    S.chcount = reinterpret_cast<unsigned long long*>(carve(16));
     RowTask* tasks = reinterpret_cast<RowTask*>(carve(3 * sizeof(RowTask) * n));
     S.tiers = TierLists{{tasks, tasks + n, tasks + 2 * n}, reinterpret_cast<unsigned*>(carve(16))};
-    S.ccount = reinterpret_cast<unsigned long long*>(carve(16));
+    cudaMemsetAsync(W.err, 0, 32, s);
+    cudaMemsetAsync(S.dbnext, 0, 8 * L, s);
+    cudaMemsetAsync(S.dacc, 0, 32 * L, s);
     // per-block flags start (and are kept) at zero
     cudaMemsetAsync(W.cntF, 0, 4 * bc, s);
     cudaMemsetAsync(W.touched, 0, 4 * bc, s);
@@ -643,71 +743,77 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     return cudaSuccess;
 }
 
-// Degree buckets of the live frontier (and a hub layout for its hubs).
+void free_scratch(Scratch* S, cudaStream_t s) {
+    if (S->base) cudaFreeAsync(S->base, s);
+    if (S->h) {
+        cudaStreamSynchronize(s);                          // no copy into the stage is left in flight
+        cudaFreeHost(S->h);
+    }
+    delete S;
+}
+
+// Degree buckets of the live frontier, launched before the level's read-back.
+void launch_buckets(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
+    const unsigned long long* dfl = &S.W.counters[7];
+    cudaMemsetAsync(S.ccount, 0, 8 * kNumClasses, s);
+    cudaMemsetAsync(S.cedges, 0, 8 * kNumClasses, s);
+    cudaMemsetAsync(S.n_hubs, 0, 4, s);
+    BISIM_SITE(site, "inc_buckets");
+    Launch L(site, s, 0, 0, 0.0);
+    const int sm = ctx->opt.small_max_degree, mm = ctx->opt.mid_max_degree;
+    k_class_count<<<kDevGrid, 256, 0, s>>>(S.W.FL, dfl, ctx->xlen, sm, mm, S.ccount, S.cedges);
+    k_class_scan<<<1, 32, 0, s>>>(S.ccount, S.dbegin, S.ccursor);
+    k_class_scatter<<<kDevGrid, 256, 0, s>>>(S.W.FL, dfl, ctx->xro, ctx->xlen, sm, mm, S.ccursor, S.blist, S.hubs,
+                                            S.n_hubs);
+    cudaMemcpyAsync(S.h->begin, S.dbegin, sizeof(S.h->begin), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(S.h->edges, S.cedges, sizeof(S.h->edges), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&S.h->n_hubs, S.n_hubs, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(S.h->hubs, S.hubs, sizeof(S.h->hubs), cudaMemcpyDeviceToHost, s);
+}
+
+// After the read-back: the Buckets view, and the hub chunks laid out on the
+// host (hubs in ascending vertex order, as the hub lookups expect).
 struct ListBuckets {
     Buckets B;
     void* hubmem = nullptr;
 };
 
-bisim_status list_buckets(bisim_ctx* ctx, const int32_t* list, int64_t count, Scratch& S, ListBuckets& out,
-                          cudaStream_t s) {
+bisim_status finish_buckets(bisim_ctx* ctx, Scratch& S, ListBuckets& out, cudaStream_t s) {
     Buckets& B = out.B;
     cudaError_t e;
-    int64_t begin[kNumClasses + 1];
-    unsigned long long edges[kNumClasses];
-    for (int c = 0; c <= kNumClasses; ++c) begin[c] = count;
-    cudaMemcpyAsync(S.dbegin, begin, sizeof(begin), cudaMemcpyHostToDevice, s);
-    cudaMemsetAsync(S.dedges, 0, sizeof(edges), s);
-    if (count > 0) {
-        BISIM_SITE(site, "inc_buckets");
-        Launch L(site, s, count, 0, 24.0 * count);
-        k_list_classify<<<grid_for(count, 256), 256, 0, s>>>(list, count, ctx->xlen, ctx->opt.small_max_degree,
-                                                            ctx->opt.mid_max_degree, S.ck0, S.cv0);
-        const int w = radix_sort_pairs(S.ck0, S.cv0, S.ck1, S.cv1, count, 8, S.ctmp, s);
-        k_list_bounds<<<grid_for(count, 256), 256, 0, s>>>(w ? S.ck1 : S.ck0, w ? S.cv1 : S.cv0, count,
-                                                          ctx->xlen, S.dbegin, S.dedges, S.blist);
-    }
-    cudaMemcpyAsync(begin, S.dbegin, sizeof(begin), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(edges, S.dedges, sizeof(edges), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "bucket frontier");
-    for (int c = kNumClasses - 1; c >= 0; --c) begin[c] = std::min(begin[c], begin[c + 1]);
     B.class_list = S.blist;
-    for (int c = 0; c <= kNumClasses; ++c) B.begin[c] = begin[c];
-    for (int c = 0; c < kNumClasses; ++c) B.edges[c] = static_cast<int64_t>(edges[c]);
-    B.hub_list = S.blist + begin[kClassHub];
-    B.n_hub = begin[kClassHub + 1] - begin[kClassHub];
+    for (int c = 0; c <= kNumClasses; ++c) B.begin[c] = S.h->begin[c];
+    for (int c = 0; c < kNumClasses; ++c) B.edges[c] = static_cast<int64_t>(S.h->edges[c]);
+    B.n_hub = S.h->n_hubs;
     if (B.n_hub == 0) return BISIM_OK;
-    // hub layout on the host: few vertices, their row bounds gathered in one copy
-    std::vector<int32_t> hubs(B.n_hub);
-    std::vector<int64_t> bounds(2 * B.n_hub);
-    // the two sort value buffers are free again and adjacent: 16 bytes x n >= 2 x 8 bytes x hubs
-    int64_t* dbounds = reinterpret_cast<int64_t*>(S.cv0);
-    k_row_bounds<<<grid_for(B.n_hub, 256), 256, 0, s>>>(B.hub_list, B.n_hub, ctx->xro, ctx->xlen, dbounds);
-    cudaMemcpyAsync(hubs.data(), B.hub_list, sizeof(int32_t) * B.n_hub, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(bounds.data(), dbounds, sizeof(int64_t) * 2 * B.n_hub, cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "read frontier hubs");
-    std::vector<int64_t> rb(B.n_hub), re(B.n_hub);
-    for (int64_t h = 0; h < B.n_hub; ++h) {
-        rb[h] = bounds[2 * h];
-        re[h] = bounds[2 * h + 1];
+    std::vector<HubInfo> hubs(S.h->hubs, S.h->hubs + std::min<int64_t>(B.n_hub, kHubPrefetch));
+    if (B.n_hub > kHubPrefetch) {
+        hubs.resize(B.n_hub);
+        cudaMemcpyAsync(hubs.data() + kHubPrefetch, S.hubs + kHubPrefetch, sizeof(HubInfo) * (B.n_hub - kHubPrefetch),
+                        cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "read frontier hubs");
     }
+    std::sort(hubs.begin(), hubs.end(), [](const HubInfo& a, const HubInfo& b) { return a.v < b.v; });
+    std::vector<int32_t> ids(B.n_hub);
     std::vector<HubChunk> chunks;
     std::vector<int64_t> toff(B.n_hub);
     std::vector<uint32_t> tmask(B.n_hub);
     int64_t words = 0;
     const int64_t csz = ctx->opt.hub_chunk;
     for (int64_t h = 0; h < B.n_hub; ++h) {
+        ids[h] = hubs[h].v;
+        const int64_t rb = hubs[h].off, re = hubs[h].off + hubs[h].len;
         uint64_t sz = 64;
-        while (sz < static_cast<uint64_t>(2 * (re[h] - rb[h]))) sz <<= 1;
+        while (sz < static_cast<uint64_t>(2 * (re - rb))) sz <<= 1;
         toff[h] = words;
         tmask[h] = static_cast<uint32_t>(sz - 1);
         words += static_cast<int64_t>(sz);
-        for (int64_t b = rb[h]; b < re[h]; b += csz)
-            chunks.push_back(HubChunk{static_cast<int32_t>(h), hubs[h], b, std::min(re[h], b + csz)});
+        for (int64_t b = rb; b < re; b += csz)
+            chunks.push_back(HubChunk{static_cast<int32_t>(h), hubs[h].v, b, std::min(re, b + csz)});
     }
     const size_t bytes = sizeof(HubChunk) * chunks.size() + 256 + sizeof(int64_t) * B.n_hub + 256 +
                          sizeof(uint32_t) * B.n_hub + 256 + sizeof(unsigned long long) * words + 256 +
-                         sizeof(HubAcc) * B.n_hub + 256;
+                         sizeof(HubAcc) * B.n_hub + 256 + sizeof(int32_t) * B.n_hub + 256;
     char* p = nullptr;
     if ((e = cudaMallocAsync(reinterpret_cast<void**>(&p), bytes, s))) return cuda_error(ctx, e, "alloc frontier hubs");
     out.hubmem = p;
@@ -717,10 +823,13 @@ bisim_status list_buckets(bisim_ctx* ctx, const int32_t* list, int64_t count, Sc
     uint32_t* dtmask = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * B.n_hub));
     unsigned long long* dtab = reinterpret_cast<unsigned long long*>(carve(sizeof(unsigned long long) * words));
     HubAcc* dacc = reinterpret_cast<HubAcc*>(carve(sizeof(HubAcc) * B.n_hub));
+    int32_t* dids = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * B.n_hub));
+    // pageable sources: each copy has taken its data when the call returns
     cudaMemcpyAsync(dchunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dtoff, toff.data(), sizeof(int64_t) * B.n_hub, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dtmask, tmask.data(), sizeof(uint32_t) * B.n_hub, cudaMemcpyHostToDevice, s);
-    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "upload frontier hubs");
+    cudaMemcpyAsync(dids, ids.data(), sizeof(int32_t) * B.n_hub, cudaMemcpyHostToDevice, s);
+    B.hub_list = dids;
     B.chunks = dchunks;
     B.n_chunks = static_cast<int64_t>(chunks.size());
     B.toff = dtoff;
@@ -745,31 +854,44 @@ bisim_status ensure_skey(bisim_ctx* ctx, cudaStream_t s) {
     return BISIM_OK;
 }
 
-// One level: frontier F (f vertices, live or dead) with live part FL (fl).
-bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t f, int64_t fl, int64_t* rebuild,
-                        cudaStream_t s) {
+// Frontier lists from `flags` (every live vertex when null): F (live or dead)
+// and its live part FL; their sizes stay on the device (W.counters[6], [7]).
+void launch_frontier(bisim_ctx* ctx, Scratch& S, const uint8_t* flags, cudaStream_t s) {
+    Work& W = S.W;
+    const int32_t n = ctx->n;
+    cudaMemsetAsync(&W.counters[6], 0, 16, s);
+    if (n > 0) {
+        k_compact<<<grid_for(n, 256), 256, 0, s>>>(flags, ctx->alive, n, 0, W.F, &W.counters[6]);
+        k_compact<<<grid_for(n, 256), 256, 0, s>>>(flags, ctx->alive, n, 1, W.FL, &W.counters[7]);
+    }
+}
+
+// One level over the frontier launch_frontier made. Host round trips: one
+// read-back of the frontier's sizes and buckets, the signature round's own,
+// and one per probe round that still has candidates. The level's block-id and
+// index checks are read back once for all levels by inc_finish.
+bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t* frontier, cudaStream_t s) {
     Work& W = S.W;
     Level L = level_view(ctx, j);
     const int32_t n = ctx->n;
     cudaError_t e;
     bisim_status st;
     BISIM_SITE(site, "inc_level");
-    cudaMemsetAsync(W.counters, 0, 8 * 8, s);
-    if (f > 0) {
-        Launch Lk(site, s, f, 0, 16.0 * f);
-        k_set_flags<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, W.inF, 1);
-        k_remove<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, L, W);
+    // 1. frontier vertices leave their old blocks (sizes read on the device)
+    cudaMemsetAsync(W.counters, 0, 8 * 6, s);
+    {
+        Launch Lk(site, s, 0, 0, 0.0);
+        k_remove<<<kDevGrid, 256, 0, s>>>(W.F, L, W);
+        k_dirty_reset<<<kDevGrid, 256, 0, s>>>(W.dlist, L, W);
+        k_rescan<<<kDevGrid, 256, 0, s>>>(n, ctx->alive, L, W);
     }
-    unsigned long long hc[8];
-    cudaMemcpyAsync(hc, W.counters, sizeof(hc), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "leave old blocks");
-    const int64_t ntouched = static_cast<int64_t>(hc[0]);
-    const int64_t ndirty = static_cast<int64_t>(hc[1]);
-    if (ndirty > 0) {
-        Launch Lk(site, s, n, 0, 8.0 * n);
-        k_dirty_reset<<<grid_for(ndirty, 256), 256, 0, s>>>(W.dlist, ndirty, L);
-        k_rescan<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->alive, L, W);
-    }
+    if (j > 0) launch_buckets(ctx, S, s);
+    cudaMemcpyAsync(S.h->counters, W.counters, sizeof(S.h->counters), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "frontier sizes");
+    const int64_t ntouched = static_cast<int64_t>(S.h->counters[0]);
+    const int64_t f = static_cast<int64_t>(S.h->counters[6]);
+    const int64_t fl = static_cast<int64_t>(S.h->counters[7]);
+    *frontier = fl;
     // 2. exact groups within the live frontier
     ListBuckets LB;
     if (fl > 0) {
@@ -779,10 +901,9 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t f, int64_t fl
             k_label_keys<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, ctx->vlabel, W.h,
                                                           ctx->opt.hash_bits >= 64 ? ~0ull : ((1ull << ctx->opt.hash_bits) - 1));
         } else {
-            if ((st = list_buckets(ctx, W.FL, fl, S, LB, s)) != BISIM_OK) return st;
-            const Buckets& B = LB.B;
+            if ((st = finish_buckets(ctx, S, LB, s)) != BISIM_OK) return st;
             int64_t blocks = 0;
-            st = signature_round(ctx, B, ctx->lid[j - 1], W.grp, W.FL, fl, W.h, s, &blocks);
+            st = signature_round(ctx, LB.B, ctx->lid[j - 1], W.grp, W.FL, fl, W.h, s, &blocks);
             if (st != BISIM_OK) {
                 if (LB.hubmem) cudaFreeAsync(LB.hubmem, s);
                 return st;
@@ -792,19 +913,20 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t f, int64_t fl
         k_group_init<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, W);
         k_group_stats<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, W);
     }
-    // 3. match live blocks
+    // 3. match live blocks: probe, compare the candidates (their number is read
+    // on the device), probe again; the host only looks when a probe round
+    // still leaves candidates (different signatures under one hash)
     const uint64_t hmask = ctx->opt.hash_bits >= 64 ? ~0ull : ((1ull << ctx->opt.hash_bits) - 1);
-    for (int iter = 0; fl > 0; ++iter) {
-        if (iter > 1 << 16) return set_error(ctx, BISIM_ETIMEOUT, "incremental block matching did not converge");
+    if (fl > 0) {
+        Launch Lk(site, s, fl, 0, 32.0 * fl);
         cudaMemsetAsync(&W.counters[2], 0, 8, s);
-        {
-            Launch Lk(site, s, fl, 0, 32.0 * fl);
-            k_probe<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, L, W, j, ctx->vlabel, hmask);
+        k_probe<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, L, W, j, ctx->vlabel, hmask);
+    }
+    for (int iter = 0; fl > 0 && j > 0; ++iter) {
+        if (iter > 1 << 16) {
+            if (LB.hubmem) cudaFreeAsync(LB.hubmem, s);
+            return set_error(ctx, BISIM_ETIMEOUT, "incremental block matching did not converge");
         }
-        unsigned long long ncand = 0;
-        cudaMemcpyAsync(&ncand, &W.counters[2], 8, cudaMemcpyDeviceToHost, s);
-        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "probe blocks");
-        if (ncand == 0 || j == 0) break;
         Level Lp = level_view(ctx, j - 1);
         const Buckets& B = LB.B;
         static bool attr = false;
@@ -813,25 +935,34 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t f, int64_t fl
                                  static_cast<int>(sizeof(unsigned long long) * kCmpLargeSlots));
             attr = true;
         }
-        const unsigned grid = static_cast<unsigned>(std::min<unsigned long long>(ncand, 4096));
-        Launch Lk(site, s, static_cast<int64_t>(ncand), 0, 0.0);
-        k_compare<kCmpSmallSlots><<<grid, kCmpThreads, sizeof(unsigned long long) * kCmpSmallSlots, s>>>(
-            static_cast<int64_t>(ncand), L, Lp, W, ctx->xro, ctx->xlen, ctx->xpe, ctx->cnt, ctx->skey,
-            B.hub_list, B.n_hub, B.toff, B.tmask, B.tab, B.acc, 0, kCmpSmallSlots / 2);
-        k_compare<kCmpLargeSlots><<<grid, kCmpThreads, sizeof(unsigned long long) * kCmpLargeSlots, s>>>(
-            static_cast<int64_t>(ncand), L, Lp, W, ctx->xro, ctx->xlen, ctx->xpe, ctx->cnt, ctx->skey,
-            B.hub_list, B.n_hub, B.toff, B.tmask, B.tab, B.acc, kCmpSmallSlots / 2 + 1, kCmpLargeSlots / 2);
-        if (B.n_hub > 0)
-            k_compare<0><<<grid, kCmpThreads, 0, s>>>(static_cast<int64_t>(ncand), L, Lp, W, ctx->xro, ctx->xlen,
-                                                      ctx->xpe, ctx->cnt, ctx->skey, B.hub_list, B.n_hub, B.toff,
-                                                      B.tmask, B.tab, B.acc, kCmpLargeSlots / 2 + 1, INT_MAX);
+        {
+            Launch Lk(site, s, 0, 0, 0.0);
+            k_compare<kCmpSmallSlots><<<kCmpGrid, kCmpThreads, sizeof(unsigned long long) * kCmpSmallSlots, s>>>(
+                &W.counters[2], L, Lp, W, ctx->xro, ctx->xlen, ctx->xpe, ctx->cnt, ctx->skey, B.hub_list, B.n_hub,
+                B.toff, B.tmask, B.tab, B.acc, 0, kCmpSmallSlots / 2);
+            // a representative's set is no larger than its row: the larger variants only
+            // run when the frontier has rows above the small set's reach
+            if (B.begin[kNumClasses] > B.begin[kSmallClasses + 6])
+                k_compare<kCmpLargeSlots><<<kCmpGrid, kCmpThreads, sizeof(unsigned long long) * kCmpLargeSlots, s>>>(
+                    &W.counters[2], L, Lp, W, ctx->xro, ctx->xlen, ctx->xpe, ctx->cnt, ctx->skey, B.hub_list, B.n_hub,
+                    B.toff, B.tmask, B.tab, B.acc, kCmpSmallSlots / 2 + 1, kCmpLargeSlots / 2);
+            if (B.n_hub > 0)
+                k_compare<0><<<kCmpGrid, kCmpThreads, 0, s>>>(&W.counters[2], L, Lp, W, ctx->xro, ctx->xlen, ctx->xpe,
+                                                              ctx->cnt, ctx->skey, B.hub_list, B.n_hub, B.toff, B.tmask,
+                                                              B.tab, B.acc, kCmpLargeSlots / 2 + 1, INT_MAX);
+            cudaMemsetAsync(&W.counters[2], 0, 8, s);
+            k_probe<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, L, W, j, ctx->vlabel, hmask);
+        }
+        cudaMemcpyAsync(&S.h->ncand, &W.counters[2], 8, cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "probe blocks");
+        if (S.h->ncand == 0) break;
     }
     if (LB.hubmem) cudaFreeAsync(LB.hubmem, s);
     // 4. keep or create ids; 5. assign; retire empty blocks
-    cudaMemcpyAsync(S.dbnext, &ctx->bnext[j], sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    unsigned long long* acc = S.dacc + 4 * j;
     if (fl > 0) {
         Launch Lk(site, s, fl, 0, 24.0 * fl);
-        k_settle<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, L, W, S.dbnext, ctx->bcap, W.counters);
+        k_settle<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, L, W, S.dbnext + j, ctx->bcap, acc);
     }
     if (f > 0) {
         Launch Lk(site, s, f, 0, 24.0 * f);
@@ -840,40 +971,46 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t f, int64_t fl
     }
     if (ntouched > 0) {
         Launch Lk(site, s, ntouched, 0, 16.0 * ntouched);
-        k_retire<<<grid_for(ntouched, 256), 256, 0, s>>>(W.tlist, ntouched, L, W, W.counters);
+        k_retire<<<grid_for(ntouched, 256), 256, 0, s>>>(W.tlist, ntouched, L, W, acc);
     }
-    cudaMemcpyAsync(&ctx->bnext[j], S.dbnext, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(hc, W.counters, sizeof(hc), cudaMemcpyDeviceToHost, s);
-    unsigned chk = 0;
-    cudaMemcpyAsync(&chk, W.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "settle blocks");
-    if (chk) {
-        char msg[96];
-        std::snprintf(msg, sizeof(msg), "incremental level %d self-check failed (bits 0x%x)", j, chk);
-        return set_error(ctx, BISIM_EINVAL, msg);
-    }
-    ctx->itomb[j] += static_cast<int64_t>(hc[3]) - static_cast<int64_t>(hc[5]);
-    *rebuild = static_cast<int64_t>(hc[4]);
-    if (ctx->bnext[j] > ctx->bcap) ctx->bnext[j] = ctx->bcap;
     return BISIM_OK;
 }
 
-// Builds the frontier list(s) from W.next (or all live vertices when flags == null).
-bisim_status make_frontier(bisim_ctx* ctx, Scratch& S, const uint8_t* flags, int64_t* f, int64_t* fl,
-                           cudaStream_t s) {
-    Work& W = S.W;
-    const int32_t n = ctx->n;
-    cudaError_t e;
-    cudaMemsetAsync(&W.counters[6], 0, 16, s);
-    if (n > 0) {
-        k_compact<<<grid_for(n, 256), 256, 0, s>>>(flags, ctx->alive, n, 0, W.F, &W.counters[6]);
-        k_compact<<<grid_for(n, 256), 256, 0, s>>>(flags, ctx->alive, n, 1, W.FL, &W.counters[7]);
+// The partition P_k (smallest member of each level-k block) and every level's
+// deferred checks, read back together. *rebuild is set when a level ran out of
+// block ids or index room (the state must then be rebuilt).
+bisim_status inc_finish(bisim_ctx* ctx, Scratch& S, bool* rebuild, cudaStream_t s) {
+    const int K = ctx->inc_k;
+    constexpr int L = kMaxIncLevels + 1;
+    if (ctx->n > 0) {
+        BISIM_SITE(site, "inc_output");
+        Launch Lk(site, s, ctx->n, 0, 13.0 * ctx->n);
+        cudaMemsetAsync(&ctx->dstate->error, 0, sizeof(unsigned), s);
+        k_output<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, ctx->alive, ctx->lid[K], ctx->bmin[K], ctx->bcap,
+                                                      ctx->P[0], &ctx->dstate->error);
     }
-    unsigned long long c[2] = {0, 0};
-    cudaMemcpyAsync(c, &W.counters[6], sizeof(c), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "compact frontier");
-    *f = static_cast<int64_t>(c[0]);
-    *fl = static_cast<int64_t>(c[1]);
+    cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(S.h->bnext, S.dbnext, 8 * L, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(S.h->acc, S.dacc, 32 * L, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&S.h->err, S.W.err, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemsetAsync(S.dacc, 0, 32 * L, s);
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "incremental update");
+    if (S.h->err) {
+        char msg[96];
+        std::snprintf(msg, sizeof(msg), "incremental state self-check failed (bits 0x%x)", S.h->err);
+        return set_error(ctx, BISIM_EINVAL, msg);
+    }
+    *rebuild = false;
+    for (int j = 0; j <= K; ++j) {
+        ctx->itomb[j] += static_cast<int64_t>(S.h->acc[j][0]) - static_cast<int64_t>(S.h->acc[j][2]);
+        if (S.h->acc[j][1]) *rebuild = true;
+        ctx->bnext[j] = std::min<int64_t>(S.h->bnext[j], ctx->bcap);
+    }
+    if (!*rebuild && ctx->n > 0 && ctx->hstate->error)
+        return set_error(ctx, BISIM_EINVAL, "incremental state inconsistent at output");
+    ctx->cur = 0;
+    ctx->cur_k = K;
     return BISIM_OK;
 }
 
@@ -900,9 +1037,7 @@ bisim_status write_output(bisim_ctx* ctx, cudaStream_t s) {
 void inc_release(bisim_ctx* ctx, cudaStream_t s) {
     const size_t n = static_cast<size_t>(std::max(ctx->n, 1));
     if (ctx->inc_ws != nullptr) {
-        Scratch* S = static_cast<Scratch*>(ctx->inc_ws);
-        cudaFreeAsync(S->base, s);
-        delete S;
+        free_scratch(static_cast<Scratch*>(ctx->inc_ws), s);
         ctx->inc_ws = nullptr;
     }
     for (int j = 0; j <= kMaxIncLevels; ++j) {
@@ -959,18 +1094,20 @@ bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s) {
     }
     ctx->inc_ws = Sp;
     Scratch& S = *Sp;
-    int64_t f = 0, fl = 0, rebuild = 0;
-    st = make_frontier(ctx, S, nullptr, &f, &fl, s);
-    for (int j = 0; st == BISIM_OK && j <= K; ++j) st = level_pass(ctx, j, S, f, fl, &rebuild, s);
+    int64_t fl = 0;
+    st = BISIM_OK;
+    for (int j = 0; st == BISIM_OK && j <= K; ++j) {
+        launch_frontier(ctx, S, nullptr, s);
+        st = level_pass(ctx, j, S, &fl, s);
+    }
+    bool rebuild = false;
+    if (st == BISIM_OK) st = inc_finish(ctx, S, &rebuild, s);
     if (st == BISIM_OK && rebuild) st = set_error(ctx, BISIM_ENOMEM, "incremental state overflow during build");
-    if (st == BISIM_OK) st = write_output(ctx, s);
     if (st != BISIM_OK) {
         inc_release(ctx, s);
         return st;
     }
     ctx->stats.last_frontier = fl;
-    cudaError_t e2 = cudaStreamSynchronize(s);
-    if (e2) return cuda_error(ctx, e2, "build incremental state");
     return BISIM_OK;
 }
 
@@ -986,49 +1123,46 @@ bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* 
     if ((st = ensure_skey(ctx, s)) != BISIM_OK) return st;
     const int K = ctx->inc_k;
     const int32_t n = ctx->n;
-    cudaError_t e;
     Scratch& S = *static_cast<Scratch*>(ctx->inc_ws);
     Work& W = S.W;
-    int64_t f = 0, fl = 0, total = 0, rebuild = 0;
-    st = make_frontier(ctx, S, vchanged, &f, &fl, s);
+    int64_t total = 0;
     for (int j = 0; st == BISIM_OK && j <= K; ++j) {
         if (j > 0) {
             // F_j: block changed one level down, out-edges changed, or an out-edge into a
             // changed vertex (its source is in the changed vertex's in-row)
             cudaMemsetAsync(W.next, 0, n, s);
-            cudaMemsetAsync(S.ccount, 0, 8, s);
+            cudaMemsetAsync(S.chcount, 0, 8, s);
             cudaMemsetAsync(S.tiers.cnt, 0, 16, s);
             if (n > 0) {
                 BISIM_SITE(site, "inc_in_neighbours");
                 Launch L(site, s, n, 0, 1.0 * n);
-                k_compact<<<grid_for(n, 256), 256, 0, s>>>(W.changed, ctx->alive, n, 0, S.clist, S.ccount);
-                k_in_row_tasks<<<kTierGrid, kTierThreads, 0, s>>>(S.clist, S.ccount, ctx->yro, ctx->ylen, S.tiers);
+                k_compact<<<grid_for(n, 256), 256, 0, s>>>(W.changed, ctx->alive, n, 0, S.clist, S.chcount);
+                k_in_row_tasks<<<kTierGrid, kTierThreads, 0, s>>>(S.clist, S.chcount, ctx->yro, ctx->ylen, S.tiers);
                 run_tiers(S.tiers, MarkSources{ctx->ype, W.next}, s);
+                k_or_into<<<grid_for(n, 256), 256, 0, s>>>(W.next, W.changed, rowchg, n);
             }
-            k_or_into<<<grid_for(n, 256), 256, 0, s>>>(W.next, W.changed, rowchg, n);
-            st = make_frontier(ctx, S, W.next, &f, &fl, s);
-            if (st != BISIM_OK) break;
-            cudaMemsetAsync(W.changed, 0, n, s);
+            launch_frontier(ctx, S, W.next, s);
         } else {
-            cudaMemsetAsync(W.changed, 0, n, s);
+            launch_frontier(ctx, S, vchanged, s);
         }
+        cudaMemsetAsync(W.changed, 0, n, s);
+        int64_t fl = 0;
+        st = level_pass(ctx, j, S, &fl, s);
         total += fl;
-        st = level_pass(ctx, j, S, f, fl, &rebuild, s);
-        if (st == BISIM_OK && rebuild) break;
     }
+    bool rebuild = false;
+    if (st == BISIM_OK) st = inc_finish(ctx, S, &rebuild, s);
     if (st != BISIM_OK) {
         inc_release(ctx, s);      // the state may be half-updated: the next batch rebuilds it
         return st;
     }
     // out of block ids or index slots: start over from the current graph
-    bool full = rebuild != 0;
+    bool full = rebuild;
     for (int j = 0; j <= K; ++j)
         if (ctx->bnext[j] + n >= ctx->bcap || static_cast<uint64_t>(ctx->bnext[j] + ctx->itomb[j]) * 10 > ctx->isize * 7)
             full = true;
     if (full) return inc_build(ctx, s);
     ctx->stats.last_frontier = total;
-    if ((st = write_output(ctx, s)) != BISIM_OK) return st;
-    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "incremental update");
     return BISIM_OK;
 }
 

@@ -1,11 +1,11 @@
 // Work over the entries of many rows whose lengths range from a few entries
 // to a million (power-law degrees). Every row is a task; a producer files it
-// in one of three tiers by length and each tier's consumer gives it a matching
-// share of the GPU:
+// in one of three tiers by length and each tier gets a matching share of the
+// GPU:
 //   warp tier  len <= kWarpTierMax   one warp per task
 //   CTA tier   len <= kCtaTierMax    one CTA per task, its warps striding the row
 //   grid tier  longer                every warp of the grid strides the row
-// The consumers are persistent grids that read the task counts on the device,
+// The consumer is a persistent grid that reads the task counts on the device,
 // so filing and consuming need no host round trip. The per-entry work is a
 // functor called by whole warps (`in` is false past the row's end), so it may
 // use warp collectives.
@@ -53,47 +53,38 @@ __device__ __forceinline__ void tier_push(const TierLists& L, bool has, const Ro
     }
 }
 
+// One persistent grid runs the three tiers in turn: the warp tier's tasks over
+// all warps, then the CTA tier's over all CTAs, then every grid-tier row over
+// all warps together. Tasks are independent, so no grid-wide barrier is needed
+// between the phases.
 template <class F>
-__global__ void __launch_bounds__(kTierThreads) k_tier_warp(const TierLists L, F f) {
-    const unsigned count = *reinterpret_cast<volatile unsigned*>(&L.cnt[0]);
+__global__ void __launch_bounds__(kTierThreads) k_tiers(const TierLists L, F f) {
     const int lane = static_cast<int>(threadIdx.x & 31u);
+    const int warp = static_cast<int>(threadIdx.x >> 5);
     const unsigned warps = gridDim.x * (kTierThreads / 32);
-    for (unsigned i = blockIdx.x * (kTierThreads / 32) + (threadIdx.x >> 5); i < count; i += warps) {
+    const unsigned gw = blockIdx.x * (kTierThreads / 32) + warp;
+    const unsigned c0 = *reinterpret_cast<volatile unsigned*>(&L.cnt[0]);
+    for (unsigned i = gw; i < c0; i += warps) {
         const RowTask t = L.t[0][i];
         for (int32_t j0 = 0; j0 < t.len; j0 += 32) f(t, t.off + j0 + lane, j0 + lane < t.len);
     }
-}
-
-template <class F>
-__global__ void __launch_bounds__(kTierThreads) k_tier_cta(const TierLists L, F f) {
-    const unsigned count = *reinterpret_cast<volatile unsigned*>(&L.cnt[1]);
-    const int lane = static_cast<int>(threadIdx.x & 31u);
-    const int warp = static_cast<int>(threadIdx.x >> 5);
-    for (unsigned i = blockIdx.x; i < count; i += gridDim.x) {
+    const unsigned c1 = *reinterpret_cast<volatile unsigned*>(&L.cnt[1]);
+    for (unsigned i = blockIdx.x; i < c1; i += gridDim.x) {
         const RowTask t = L.t[1][i];
         for (int32_t j0 = warp * 32; j0 < t.len; j0 += kTierThreads) f(t, t.off + j0 + lane, j0 + lane < t.len);
     }
-}
-
-template <class F>
-__global__ void __launch_bounds__(kTierThreads) k_tier_grid(const TierLists L, F f) {
-    const unsigned count = *reinterpret_cast<volatile unsigned*>(&L.cnt[2]);
-    const int lane = static_cast<int>(threadIdx.x & 31u);
-    const int64_t gw = static_cast<int64_t>(blockIdx.x) * (kTierThreads / 32) + (threadIdx.x >> 5);
-    const int64_t step = static_cast<int64_t>(gridDim.x) * kTierThreads;
-    for (unsigned i = 0; i < count; ++i) {
+    const unsigned c2 = *reinterpret_cast<volatile unsigned*>(&L.cnt[2]);
+    const int64_t step = static_cast<int64_t>(warps) * 32;
+    for (unsigned i = 0; i < c2; ++i) {
         const RowTask t = L.t[2][i];
-        for (int64_t j0 = gw * 32; j0 < t.len; j0 += step) f(t, t.off + j0 + lane, j0 + lane < t.len);
+        for (int64_t j0 = static_cast<int64_t>(gw) * 32; j0 < t.len; j0 += step) f(t, t.off + j0 + lane, j0 + lane < t.len);
     }
 }
 
-// Runs the three consumers of `L` (in stream order; the functor sees every
-// filed entry exactly once).
+// Runs every task filed in `L` (the functor sees each filed entry exactly once).
 template <class F>
 void run_tiers(const TierLists& L, const F& f, cudaStream_t s) {
-    k_tier_warp<F><<<kTierGrid, kTierThreads, 0, s>>>(L, f);
-    k_tier_cta<F><<<kTierGrid, kTierThreads, 0, s>>>(L, f);
-    k_tier_grid<F><<<kTierGrid, kTierThreads, 0, s>>>(L, f);
+    k_tiers<F><<<kTierGrid, kTierThreads, 0, s>>>(L, f);
 }
 
 // ----------------------------------------------------------------------------- dynamic adjacency

@@ -137,6 +137,44 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Inputs of at most kSmallSortMax pairs (update batches, small frontiers): one
+// CTA sorts (key bits, input index) composites by a bitonic network in shared
+// memory, which is stable by construction and costs one launch instead of
+// three per 8-bit digit.
+constexpr int kSmallSortMax = 4096;
+constexpr int kSmallSortThreads = 1024;
+
+__global__ void __launch_bounds__(kSmallSortThreads) k_small_sort(const uint32_t* __restrict__ k0,
+                                                                  const uint64_t* __restrict__ v0,
+                                                                  uint32_t* __restrict__ k1, uint64_t* __restrict__ v1,
+                                                                  int m, int p, uint32_t kmask) {
+    __shared__ unsigned long long c[kSmallSortMax];
+    for (int i = threadIdx.x; i < p; i += kSmallSortThreads)
+        c[i] = i < m ? (static_cast<unsigned long long>(k0[i] & kmask) << 32) | static_cast<unsigned>(i) : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= p; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < p; i += kSmallSortThreads) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = c[i], b = c[l];
+                    const bool up = (i & k) == 0;
+                    if (up ? a > b : a < b) {
+                        c[i] = b;
+                        c[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < m; i += kSmallSortThreads) {
+        const unsigned idx = static_cast<unsigned>(c[i]);
+        k1[i] = k0[idx];
+        v1[i] = v0[idx];
+    }
+}
+
 }  // namespace
 
 size_t scan_temp_words(int64_t n) {
@@ -175,6 +213,15 @@ size_t radix_temp_words(int64_t m) {
 int radix_sort_pairs(uint32_t* k0, uint64_t* v0, uint32_t* k1, uint64_t* v1, int64_t m, int bits,
                      int64_t* tmp, cudaStream_t s) {
     if (m <= 0 || bits <= 0) return 0;
+    if (m <= kSmallSortMax) {
+        int p = 64;
+        while (p < m) p <<= 1;
+        const uint32_t kmask = bits >= 32 ? ~0u : ((1u << bits) - 1u);
+        BISIM_SITE(site_small, "small_sort");
+        Launch L(site_small, s, 0, m, 24.0 * m);
+        k_small_sort<<<1, kSmallSortThreads, 0, s>>>(k0, v0, k1, v1, static_cast<int>(m), p, kmask);
+        return 1;
+    }
     const int64_t ntiles = cdiv(m, kRadixTile);
     const int64_t nc = ntiles * kRadixBins;
     int64_t* counts = tmp;

@@ -121,15 +121,22 @@ __global__ void k_vertex_final(VertexOps V, uint8_t* __restrict__ alive, int32_t
 }
 
 // Every EDGE_ADD needs both endpoints live at its position; also emits the
-// edge-key hash of every edge operation for grouping.
-__global__ void k_edge_ops(VertexOps V, const uint64_t* __restrict__ epos, int64_t ne,
+// edge-key hash of every edge operation for grouping. The vertex operations
+// come first in the sorted order; their number is read on the device
+// (st->aux), so this runs before the host has seen the batch's checks: an
+// operation that fails them is skipped here and rejects the batch anyway.
+__global__ void k_edge_ops(VertexOps V, const uint64_t* __restrict__ vpos, int64_t nops, int32_t n,
                            uint32_t* __restrict__ klo, uint32_t* __restrict__ khi, uint64_t* __restrict__ kval,
                            DevState* st) {
+    V.nv = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(&st->aux));
+    const int64_t ne = nops - V.nv;
     for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < ne;
          j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const uint64_t p = epos[j];
+        const uint64_t p = vpos[V.nv + j];
         const bisim_op o = V.ops[p];
-        if (o.kind == BISIM_OP_EDGE_ADD && (!alive_before(V, o.src, p) || !alive_before(V, o.dst, p)))
+        const bool valid = (o.kind == BISIM_OP_EDGE_ADD || o.kind == BISIM_OP_EDGE_DEL) && o.src >= 0 && o.src < n &&
+                           o.dst >= 0 && o.dst < n;
+        if (valid && o.kind == BISIM_OP_EDGE_ADD && (!alive_before(V, o.src, p) || !alive_before(V, o.dst, p)))
             atomicOr(&st->error, kErrDeadEndpoint);
         const uint64_t h = edge_key_hash(o.src, o.dst, o.label);
         klo[j] = static_cast<uint32_t>(h);
@@ -733,6 +740,13 @@ bisim_status batch_begin(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, si
     const int which = radix_sort_pairs(vk0, vv0, vk1, vv1, nops, 32, B.tmp, s);
     const uint32_t* vkey = which ? vk1 : vk0;
     const uint64_t* vpos = which ? vv1 : vv0;
+    // 2. EDGE_ADD liveness and edge-key hashes (before the host looks: one read-back
+    // covers both checks)
+    if (nops > 0) {
+        Launch L(site_ops, s, 0, 0, 24.0 * nops);
+        B.V = VertexOps{vkey, vpos, 0, d_ops, ctx->alive};
+        k_edge_ops<<<grid_for(nops, 256), 256, 0, s>>>(B.V, vpos, nops, n, klo0, khi0, kp0, ctx->dstate);
+    }
     cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) {
         cudaFreeAsync(B.base, s);
@@ -740,24 +754,12 @@ bisim_status batch_begin(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, si
         return cuda_error(ctx, e, "check update batch");
     }
     if (ctx->hstate->error & kErrBadOp) return fail(BISIM_EINVAL, "update batch names an out-of-range vertex or an unknown kind");
+    if (ctx->hstate->error & kErrDeadEndpoint) return fail(BISIM_EINVAL, "EDGE_ADD with an endpoint that is dead at that point of the batch");
     B.nv = static_cast<int64_t>(ctx->hstate->aux);
     B.vadds = static_cast<int64_t>(ctx->hstate->pairs);
     B.ne = nops - B.nv;
     B.V = VertexOps{vkey, vpos, B.nv, d_ops, ctx->alive};
     const int64_t nv = B.nv, ne = B.ne;
-
-    // 2. EDGE_ADD liveness and edge-key hashes, then group edge operations by key
-    if (ne > 0) {
-        Launch L(site_ops, s, 0, 0, 24.0 * ne);
-        k_edge_ops<<<grid_for(ne, 256), 256, 0, s>>>(B.V, vpos + nv, ne, klo0, khi0, kp0, ctx->dstate);
-    }
-    cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
-    if ((e = cudaStreamSynchronize(s))) {
-        cudaFreeAsync(B.base, s);
-        B.base = nullptr;
-        return cuda_error(ctx, e, "check edge operations");
-    }
-    if (ctx->hstate->error & kErrDeadEndpoint) return fail(BISIM_EINVAL, "EDGE_ADD with an endpoint that is dead at that point of the batch");
 
     // ---- from here on the batch is valid and the graph changes ----
     // stable LSD sort of the edge operations by key hash: low half, then high
