@@ -99,17 +99,29 @@ constexpr unsigned kChkGroup = 1u, kChkProbe = 2u, kChkMin = 4u, kChkCompare = 8
 
 // ----------------------------------------------------------------------------- frontier
 
-__global__ void k_compact(const uint8_t* __restrict__ flag, const uint8_t* __restrict__ alive, int32_t n,
-                          int live_only, int32_t* __restrict__ out, unsigned long long* __restrict__ count) {
-    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const bool f = v < n && (flag == nullptr || flag[v]) && (!live_only || alive[v]);
+__device__ __forceinline__ void warp_list_push(bool f, int32_t v, int32_t* out, unsigned long long* count) {
     const unsigned ball = __ballot_sync(0xffffffffu, f);
     if (!ball) return;
     const int leader = __ffs(ball) - 1;
     unsigned long long base = 0;
     if (static_cast<int>(lane_id()) == leader) base = atomicAdd(count, static_cast<unsigned long long>(__popc(ball)));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (f) out[base + __popc(ball & ((1u << lane_id()) - 1u))] = static_cast<int32_t>(v);
+    if (f) out[base + __popc(ball & ((1u << lane_id()) - 1u))] = v;
+}
+
+// The level's frontier in one pass: F = vertices with any of the flags a, b, c
+// set (a null `a` flags every vertex), FL = its live part.
+__global__ void k_frontier(const uint8_t* __restrict__ a, const uint8_t* __restrict__ b,
+                           const uint8_t* __restrict__ c, const uint8_t* __restrict__ alive, int32_t n,
+                           int32_t* __restrict__ F, int32_t* __restrict__ FL, unsigned long long* __restrict__ count) {
+    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    bool f = false, live = false;
+    if (v < n) {
+        f = a == nullptr || a[v] || (b && b[v]) || (c && c[v]);
+        live = f && alive[v];
+    }
+    warp_list_push(f, static_cast<int32_t>(v), F, &count[0]);
+    warp_list_push(live, static_cast<int32_t>(v), FL, &count[1]);
 }
 
 // In-row tasks of the listed vertices (those whose previous-level block changed).
@@ -138,12 +150,6 @@ struct MarkSources {
         if (in) mark[ype[e]] = 1;
     }
 };
-
-__global__ void k_or_into(uint8_t* __restrict__ a, const uint8_t* __restrict__ b, const uint8_t* __restrict__ c,
-                          int32_t n) {
-    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (v < n) a[v] = static_cast<uint8_t>(a[v] | b[v] | (c ? c[v] : 0));
-}
 
 __global__ void k_set_flags(const int32_t* __restrict__ list, int64_t count, uint8_t* __restrict__ flag, uint8_t v) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -554,8 +560,11 @@ __global__ void k_settle(const int32_t* __restrict__ FL, int64_t fl, Level L, Wo
 }
 
 // 5. frontier vertices take their blocks
+// Vertices whose block changed are flagged in W.changed and listed in `clist`
+// (for the next level's in-neighbour search).
 __global__ void k_assign(const int32_t* __restrict__ F, int64_t f, const uint8_t* __restrict__ alive, Level L,
-                         Work W, const int32_t* __restrict__ cnt_now, int level) {
+                         Work W, const int32_t* __restrict__ cnt_now, int level, int32_t* __restrict__ clist,
+                         unsigned long long* __restrict__ ccount) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= f) return;
     const int32_t v = F[i];
@@ -576,9 +585,11 @@ __global__ void k_assign(const int32_t* __restrict__ F, int64_t f, const uint8_t
         atomicMin(&L.bmin[b], v);
         if (level > 0) L.lcnt[v] = cnt_now[v];
         W.changed[v] = b != o;
+        if (b != o) clist[atomicAdd(ccount, 1ull)] = v;
     } else {
         L.lid[v] = -1;
         W.changed[v] = o != -1;
+        if (o != -1) clist[atomicAdd(ccount, 1ull)] = v;
     }
 }
 
@@ -760,7 +771,8 @@ void launch_buckets(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     cudaMemsetAsync(S.n_hubs, 0, 4, s);
     BISIM_SITE(site, "inc_buckets");
     Launch L(site, s, 0, 0, 0.0);
-    const int sm = ctx->opt.small_max_degree, mm = ctx->opt.mid_max_degree;
+    // frontiers are small: every row gets at least a warp (no thread-per-vertex classes)
+    const int sm = 0, mm = ctx->opt.mid_max_degree;
     k_class_count<<<kDevGrid, 256, 0, s>>>(S.W.FL, dfl, ctx->xlen, sm, mm, S.ccount, S.cedges);
     k_class_scan<<<1, 32, 0, s>>>(S.ccount, S.dbegin, S.ccursor);
     k_class_scatter<<<kDevGrid, 256, 0, s>>>(S.W.FL, dfl, ctx->xro, ctx->xlen, sm, mm, S.ccursor, S.blist, S.hubs,
@@ -854,16 +866,15 @@ bisim_status ensure_skey(bisim_ctx* ctx, cudaStream_t s) {
     return BISIM_OK;
 }
 
-// Frontier lists from `flags` (every live vertex when null): F (live or dead)
-// and its live part FL; their sizes stay on the device (W.counters[6], [7]).
-void launch_frontier(bisim_ctx* ctx, Scratch& S, const uint8_t* flags, cudaStream_t s) {
+// Frontier lists from the flags a | b | c (every vertex when a is null): F
+// (live or dead) and its live part FL; their sizes stay on the device
+// (W.counters[6], [7]).
+void launch_frontier(bisim_ctx* ctx, Scratch& S, const uint8_t* a, const uint8_t* b, const uint8_t* c,
+                     cudaStream_t s) {
     Work& W = S.W;
     const int32_t n = ctx->n;
     cudaMemsetAsync(&W.counters[6], 0, 16, s);
-    if (n > 0) {
-        k_compact<<<grid_for(n, 256), 256, 0, s>>>(flags, ctx->alive, n, 0, W.F, &W.counters[6]);
-        k_compact<<<grid_for(n, 256), 256, 0, s>>>(flags, ctx->alive, n, 1, W.FL, &W.counters[7]);
-    }
+    if (n > 0) k_frontier<<<grid_for(n, 256), 256, 0, s>>>(a, b, c, ctx->alive, n, W.F, W.FL, &W.counters[6]);
 }
 
 // One level over the frontier launch_frontier made. Host round trips: one
@@ -966,7 +977,7 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t* frontier, cu
     }
     if (f > 0) {
         Launch Lk(site, s, f, 0, 24.0 * f);
-        k_assign<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, ctx->alive, L, W, ctx->cnt, j);
+        k_assign<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, ctx->alive, L, W, ctx->cnt, j, S.clist, S.chcount);
         k_set_flags<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, W.inF, 0);
     }
     if (ntouched > 0) {
@@ -1097,7 +1108,8 @@ bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s) {
     int64_t fl = 0;
     st = BISIM_OK;
     for (int j = 0; st == BISIM_OK && j <= K; ++j) {
-        launch_frontier(ctx, S, nullptr, s);
+        launch_frontier(ctx, S, nullptr, nullptr, nullptr, s);
+        cudaMemsetAsync(S.chcount, 0, 8, s);          // k_assign lists changed vertices (at most n)
         st = level_pass(ctx, j, S, &fl, s);
     }
     bool rebuild = false;
@@ -1131,21 +1143,19 @@ bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* 
             // F_j: block changed one level down, out-edges changed, or an out-edge into a
             // changed vertex (its source is in the changed vertex's in-row)
             cudaMemsetAsync(W.next, 0, n, s);
-            cudaMemsetAsync(S.chcount, 0, 8, s);
             cudaMemsetAsync(S.tiers.cnt, 0, 16, s);
             if (n > 0) {
                 BISIM_SITE(site, "inc_in_neighbours");
                 Launch L(site, s, n, 0, 1.0 * n);
-                k_compact<<<grid_for(n, 256), 256, 0, s>>>(W.changed, ctx->alive, n, 0, S.clist, S.chcount);
                 k_in_row_tasks<<<kTierGrid, kTierThreads, 0, s>>>(S.clist, S.chcount, ctx->yro, ctx->ylen, S.tiers);
                 run_tiers(S.tiers, MarkSources{ctx->ype, W.next}, s);
-                k_or_into<<<grid_for(n, 256), 256, 0, s>>>(W.next, W.changed, rowchg, n);
             }
-            launch_frontier(ctx, S, W.next, s);
+            launch_frontier(ctx, S, W.next, W.changed, rowchg, s);
         } else {
-            launch_frontier(ctx, S, vchanged, s);
+            launch_frontier(ctx, S, vchanged, nullptr, nullptr, s);
         }
         cudaMemsetAsync(W.changed, 0, n, s);
+        cudaMemsetAsync(S.chcount, 0, 8, s);          // the level lists its changed vertices
         int64_t fl = 0;
         st = level_pass(ctx, j, S, &fl, s);
         total += fl;
