@@ -525,7 +525,7 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
             ctx->buckets_dirty = true;
             ctx->dense_ready = false;
             if (incremental) {
-                st = inc_update(ctx, vchanged, rowchg, s);
+                st = inc_update(ctx, vchanged, rowchg, n_ops, s);
             } else {
                 // the CSR moved on: the row store and any incremental state describe the old graph
                 inc_release(ctx, s);

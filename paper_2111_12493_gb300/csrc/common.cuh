@@ -306,6 +306,7 @@ struct bisim_ctx {
     int2* dsmall = nullptr;                          // [n] the same for rows of at most 32 edges (warp compare)
     uint8_t* djoined = nullptr;                      // [n] by position: another vertex joined this one's block last round
     uint8_t* downs = nullptr;                        // [n] by position: the vertex was its block's id last round
+    unsigned long long* dwork = nullptr;             // launch profiling: signature work counters of a round
     bisim::HubChunk* dchunks = nullptr;              // hub rows cut into chunks of at most 4096 edges
     int64_t n_dchunks = 0;
     int64_t n_dhub = 0;
@@ -361,6 +362,8 @@ struct bisim_ctx {
     int64_t* dtail = nullptr;      // [4] device: out-pool and in-pool tails, room the last plan asked for
     int32_t* addo = nullptr;       // [n] per-batch adds per out-row (kept zero between batches)
     int32_t* addi = nullptr;       // [n] per-batch adds per in-row
+    uint32_t* xmark = nullptr;     // [n] per-batch: out-row already listed (kept zero between batches)
+    int32_t inc_small_max = 0;     // thread-per-vertex limit of the incremental path's current frontiers
 
     // incremental maintenance (apply_updates): per level j = 0..inc_k, block ids
     // per vertex, |S| per vertex, block records and a hash index key -> block
@@ -511,7 +514,8 @@ void dense_release(bisim_ctx* ctx);
 // ----------------------------------------------------------------------------- incremental levels (inc.cu)
 
 bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s);
-bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* rowchg, cudaStream_t s);
+bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* rowchg, int64_t n_ops,
+                        cudaStream_t s);
 void inc_release(bisim_ctx* ctx, cudaStream_t s);
 bisim_status write_current(bisim_ctx* ctx, cudaStream_t s);
 

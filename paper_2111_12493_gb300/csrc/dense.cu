@@ -324,7 +324,39 @@ struct DenseView {
     const int32_t* gid;                // batched contexts: graph of each vertex (null: one graph)
     const int64_t* rbase;              // batched contexts: the graph's table region
     const uint32_t* rmask;
+    unsigned long long* work;          // launch profiling only: rows and row entries each group processed
 };
+
+// Work counters of the signature kernels, filled only while launch profiling
+// is on (vertices alone in their block skip their row, so the work done per
+// round is known only on the device). Groups follow the launch sites: thread
+// classes 8 / 16 / 32, the warp classes, the five CTA classes, the hubs; each
+// counter is spread over kWorkSpread words to keep atomics off one address.
+constexpr int kWorkGroups = 10;
+constexpr int kWorkSpread = 16;
+constexpr int kWorkWords = kWorkGroups * 2 * kWorkSpread;
+constexpr int kWorkHub = 9;
+
+__device__ __forceinline__ void work_add(const DenseView& D, int g, unsigned long long rows,
+                                         unsigned long long edges) {
+    const int k = static_cast<int>(blockIdx.x) & (kWorkSpread - 1);
+    if (rows) atomicAdd(&D.work[(g * 2) * kWorkSpread + k], rows);
+    if (edges) atomicAdd(&D.work[(g * 2 + 1) * kWorkSpread + k], edges);
+}
+
+// CTA-wide sum of the active threads' rows and entries (every thread calls it).
+__device__ __forceinline__ void work_block(const DenseView& D, int g, bool active, unsigned d) {
+    if (D.work == nullptr) return;                    // uniform: the same for the whole grid
+    __shared__ unsigned long long esum;
+    if (threadIdx.x == 0) esum = 0ull;
+    unsigned long long w = active ? d : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    __syncthreads();
+    if ((threadIdx.x & 31u) == 0u && w) atomicAdd(&esum, w);
+    const int rows = __syncthreads_count(active);
+    if (threadIdx.x == 0) work_add(D, g, static_cast<unsigned long long>(rows), esum);
+}
 
 struct WarpPlan {
     int64_t cta_begin[4];
@@ -347,30 +379,34 @@ __device__ __forceinline__ void finish_sig(const DenseView& D, int64_t pos, int3
 // Degree <= D: one thread per vertex. The row's pair values sit in registers;
 // a value counts when no earlier value of the row equals it.
 template <int D>
-__global__ void __launch_bounds__(kThreads) k_dense_thread_sig(int64_t first, int64_t count, const DenseView V) {
+__global__ void __launch_bounds__(kThreads) k_dense_thread_sig(int64_t first, int64_t count, const DenseView V,
+                                                               int group) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= count) return;
     const int64_t pos = first + i;
-    if (alone_last_round(V, pos)) return;
-    const int32_t own = V.P[V.vert[pos]];
-    const int64_t e0 = V.prp[pos];
-    const int d = static_cast<int>(V.prp[pos + 1] - e0);
-    uint64_t v[D];
+    const bool active = i < count && !alone_last_round(V, pos);
+    int d = 0;
+    if (active) {
+        const int32_t own = V.P[V.vert[pos]];
+        const int64_t e0 = V.prp[pos];
+        d = static_cast<int>(V.prp[pos + 1] - e0);
+        uint64_t v[D];
 #pragma unroll
-    for (int j = 0; j < D; ++j) v[j] = j < d ? packed_pair_value(__ldcs(V.pe + e0 + j), V.P) : 0ull;
-    uint64_t sum = 0;
-    uint32_t u = 0;
+        for (int j = 0; j < D; ++j) v[j] = j < d ? packed_pair_value(__ldcs(V.pe + e0 + j), V.P) : 0ull;
+        uint64_t sum = 0;
+        uint32_t u = 0;
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-        bool fresh = j < d;
+        for (int j = 0; j < D; ++j) {
+            bool fresh = j < d;
 #pragma unroll
-        for (int q = 0; q < j; ++q) fresh = fresh && v[q] != v[j];
-        if (fresh) {
-            sum += v[j];
-            ++u;
+            for (int q = 0; q < j; ++q) fresh = fresh && v[q] != v[j];
+            if (fresh) {
+                sum += v[j];
+                ++u;
+            }
         }
+        finish_sig(V, pos, own, u, sum);
     }
-    finish_sig(V, pos, own, u, sum);
+    work_block(V, group, active, static_cast<unsigned>(d));
 }
 
 // Degree <= 256: one warp per vertex, set of up to 512 slots in the warp's slice.
@@ -386,7 +422,9 @@ __global__ void __launch_bounds__(kThreads) k_dense_warp_sig(const WarpPlan plan
     const int warp = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     const int64_t pos = pos0 + (b - cta0) * (kThreads / 32) + warp;
-    if (pos >= pos1 || alone_last_round(D, pos)) return;  // whole warp leaves together
+    const bool active = pos < pos1 && !alone_last_round(D, pos);   // the same for the whole warp
+    if (D.work) work_block(D, 3, active && lane == 0, active ? static_cast<unsigned>(D.prp[pos + 1] - D.prp[pos]) : 0u);
+    if (!active) return;
     const int32_t own = lane == 0 ? D.P[D.vert[pos]] : 0;
     const int64_t e0 = D.prp[pos];
     const int d = static_cast<int>(D.prp[pos + 1] - e0);
@@ -416,7 +454,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_warp_sig(const WarpPlan plan
 
 // Degree <= N (N = 512 .. 8192): one CTA of T threads per vertex, set of 2N slots.
 template <int N, int T>
-__global__ void __launch_bounds__(T) k_dense_mid_sig(int64_t first, const DenseView D) {
+__global__ void __launch_bounds__(T) k_dense_mid_sig(int64_t first, const DenseView D, int group) {
     extern __shared__ unsigned long long tab[];
     __shared__ unsigned long long wsum[T / 32];
     __shared__ unsigned wcnt[T / 32];
@@ -426,6 +464,7 @@ __global__ void __launch_bounds__(T) k_dense_mid_sig(int64_t first, const DenseV
     if (alone_last_round(D, pos)) return;               // whole CTA leaves together
     const int64_t e0 = D.prp[pos];
     const int d = static_cast<int>(D.prp[pos + 1] - e0);
+    if (D.work && threadIdx.x == 0) work_add(D, group, 1, static_cast<unsigned long long>(d));
     for (int j = threadIdx.x; j < 2 * N; j += T) tab[j] = 0ull;
     if (threadIdx.x == 0) zero = 0u;
     __syncthreads();
@@ -505,6 +544,9 @@ __global__ void __launch_bounds__(kThreads) k_hub_count(const HubChunk* __restri
                                                         const HubSets H) {
     __shared__ unsigned hist[kHubMaxBuckets];
     const HubChunk c = chunks[blockIdx.x];
+    if (alone_last_round(D, H.first + c.hub)) return;    // whole CTA: the hub needs no signature
+    if (D.work && threadIdx.x == 0) work_add(D, kWorkHub, c.begin == D.prp[H.first + c.hub] ? 1 : 0,
+                                             static_cast<unsigned long long>(c.end - c.begin));
     const int shift = H.shift[c.hub];
     const int nb = 1 << shift;
     for (int b = threadIdx.x; b < nb; b += kThreads) hist[b] = 0u;
@@ -523,12 +565,14 @@ __global__ void __launch_bounds__(kThreads) k_hub_count(const HubChunk* __restri
 // Pass 2: the chunk's values go to their buckets. Each CTA reserves one range
 // per bucket it touches, so the writes of a bucket are contiguous.
 constexpr int kHubStage = kHubChunkMax;
-__global__ void __launch_bounds__(kThreads) k_hub_scatter(const HubChunk* __restrict__ chunks, const HubSets H) {
+__global__ void __launch_bounds__(kThreads) k_hub_scatter(const HubChunk* __restrict__ chunks, const DenseView D,
+                                                          const HubSets H) {
     extern __shared__ unsigned long long stage[];                  // kHubStage values
     unsigned* where = reinterpret_cast<unsigned*>(stage + kHubStage);   // bucket << 16 | index in the CTA's range
     __shared__ unsigned hist[kHubMaxBuckets];
     __shared__ unsigned start[kHubMaxBuckets];
     const HubChunk c = chunks[blockIdx.x];
+    if (alone_last_round(D, H.first + c.hub)) return;    // counted nothing in pass 1
     const int shift = H.shift[c.hub];
     const int nb = 1 << shift;
     const int cnt = static_cast<int>(c.end - c.begin);
@@ -571,6 +615,7 @@ __global__ void __launch_bounds__(kThreads) k_hub_dedup(const HubSets H, unsigne
     const int h = H.bhub[gb];
     const int shift = H.shift[h];
     const int64_t lo = H.boff[gb], hi = H.boff[gb + 1];
+    if (lo == hi) return;                                // empty bucket (or a hub left out this round)
     uint64_t sum = 0;
     unsigned cnt = 0;
     bool done = false;
@@ -646,6 +691,7 @@ __global__ void k_dense_hub_finalize(const DenseView D, const HubSets H) {
     const int64_t h = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (h >= H.n_hub) return;
     const int64_t pos = H.first + h;
+    if (alone_last_round(D, pos)) return;
     finish_sig(D, pos, D.P[D.vert[pos]], H.acc[h].count, H.acc[h].sum);
 }
 
@@ -994,8 +1040,8 @@ void launch_mid(bisim_ctx* ctx, int cls, const DenseView& D, cudaStream_t s, int
     if (count <= 0) return;
     const size_t smem = sizeof(unsigned long long) * 2 * N;
     const int64_t edges = class_edges(ctx, cls, cls + 1);
-    Launch L(site, s, count, edges, kSigVertexBytes * count + kEdgeBytes * edges);
-    k_dense_mid_sig<N, T><<<static_cast<unsigned>(count), T, smem, s>>>(first, D);
+    Launch L(site, s, count, edges, 0.0);                  // bytes: from the round's work counters
+    k_dense_mid_sig<N, T><<<static_cast<unsigned>(count), T, smem, s>>>(first, D, 4 + (cls - kDMid0));
 }
 
 // Kernel attributes (shared memory above 48 KB), set once before any launch or capture.
@@ -1056,11 +1102,12 @@ void launch_level(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const Tabl
         }
         const unsigned grid = static_cast<unsigned>(std::min<int64_t>(kPersistGrid, cdiv(count, kThreads)));
         const unsigned* dcount = &ctx->dstate->listed;
+        // their bytes follow the listed count, added after the round
         {
-            Launch L(site_in, s, count, 0, kInsertVertexBytes * count);
+            Launch L(site_in, s, count, 0, 0.0);
             k_dense_insert<<<grid, kThreads, 0, s>>>(ctx->ulist[1], 0, dcount, D, 0, t, &ctx->dstate->error);
         }
-        Launch L(site_v, s, count, 0, kVerifyVertexBytes * count);
+        Launch L(site_v, s, count, 0, 0.0);
         k_dense_verify<<<grid, kThreads, 0, s>>>(ctx->ulist[1], 0, dcount, D, round_slots(ctx), O, ctx->n);
     } else {
         {
@@ -1083,7 +1130,8 @@ void launch_level(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const Tabl
 DenseView dense_view(bisim_ctx* ctx) {
     const bool regions = ctx->rtable != nullptr;
     return DenseView{ctx->dvert, ctx->dvpos, ctx->dprp, ctx->dpe, ctx->P[ctx->cur], ctx->dcnt, ctx->dhash, ctx->dslot,
-                     ctx->djoined, ctx->downs, regions ? ctx->gid : nullptr, ctx->rbase, ctx->rmask};
+                     ctx->djoined, ctx->downs, regions ? ctx->gid : nullptr, ctx->rbase, ctx->rmask,
+                     prof_enabled() ? ctx->dwork : nullptr};
 }
 
 
@@ -1113,21 +1161,23 @@ void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, bool in_loo
     BISIM_SITE(site_hd, "hub_dedup");
     BISIM_SITE(site_hf, "dense_hub_finalize");
     // classes 0..4 (degree <= 8), 5 (<= 16) and 6 (<= 32): one thread per vertex
-    auto thread_sig = [&](int c0, int c1, auto kernel, int site) {
+    if (D.work) cudaMemsetAsync(D.work, 0, sizeof(unsigned long long) * kWorkWords, s);
+    // the signature kernels' bytes are added after the round from the work counters
+    auto thread_sig = [&](int c0, int c1, auto kernel, int site, int group) {
         const int64_t verts = db[c1] - db[c0];
         if (verts <= 0) return;
         const int64_t edges = class_edges(ctx, c0, c1);
-        Launch L(site, s, verts, edges, kSigVertexBytes * verts + kEdgeBytes * edges);
-        kernel<<<grid_for(verts, kThreads), kThreads, 0, s>>>(db[c0], verts, D);
+        Launch L(site, s, verts, edges, 0.0);
+        kernel<<<grid_for(verts, kThreads), kThreads, 0, s>>>(db[c0], verts, D, group);
     };
-    thread_sig(0, 5, k_dense_thread_sig<8>, site_t8);
-    thread_sig(5, 6, k_dense_thread_sig<16>, site_t16);
-    thread_sig(6, 7, k_dense_thread_sig<32>, site_t32);
+    thread_sig(0, 5, k_dense_thread_sig<8>, site_t8, 0);
+    thread_sig(5, 6, k_dense_thread_sig<16>, site_t16, 1);
+    thread_sig(6, 7, k_dense_thread_sig<32>, site_t32, 2);
     if (db[kDMid0] > db[kDWarp0]) {
         const WarpPlan wp = warp_plan(ctx);
         const int64_t verts = db[kDMid0] - db[kDWarp0];
         const int64_t edges = class_edges(ctx, kDWarp0, kDMid0);
-        Launch L(site_w, s, verts, edges, kSigVertexBytes * verts + kEdgeBytes * edges);
+        Launch L(site_w, s, verts, edges, 0.0);
         k_dense_warp_sig<<<static_cast<unsigned>(wp.cta_begin[3]), kThreads, 0, s>>>(wp, D);
     }
     launch_mid<512, 256>(ctx, kDMid0 + 0, D, s, site_mid[0]);
@@ -1139,20 +1189,20 @@ void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, bool in_loo
         const int64_t edges = class_edges(ctx, kDHub, kDHub + 1);
         if (ctx->n_dchunks > 0) {
             {
-                Launch L(site_hc, s, 0, edges, (kEdgeBytes + 8.0) * edges);
+                Launch L(site_hc, s, 0, edges, 0.0);
                 k_hub_count<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, 0, s>>>(ctx->dchunks, D, H);
             }
             exclusive_scan_i64(reinterpret_cast<const int64_t*>(ctx->bcount), ctx->boff, ctx->n_buckets + 1,
                                ctx->bscan, s);
             {
-                Launch L(site_hs, s, 0, edges, 16.0 * edges);
-                k_hub_scatter<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, kHubScatterSmem, s>>>(ctx->dchunks,
+                Launch L(site_hs, s, 0, edges, 0.0);
+                k_hub_scatter<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, kHubScatterSmem, s>>>(ctx->dchunks, D,
                                                                                                      H);
             }
-            Launch L(site_hd, s, 0, edges, 8.0 * edges);
+            Launch L(site_hd, s, 0, edges, 0.0);
             k_hub_dedup<<<static_cast<unsigned>(ctx->n_buckets), kThreads, kHubDedupSmem, s>>>(H, err);
         }
-        Launch L(site_hf, s, ctx->n_dhub, 0, kSigVertexBytes * ctx->n_dhub);
+        Launch L(site_hf, s, ctx->n_dhub, 0, 0.0);
         k_dense_hub_finalize<<<grid_for(ctx->n_dhub, 128), 128, 0, s>>>(D, H);
     }
     launch_level(ctx, s, D, t, 0, nullptr, ctx->dbegin[kDClasses], ctx->ulist[0], in_loop);
@@ -1160,6 +1210,38 @@ void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, bool in_loo
 
 // Reads the state of a round whose level 0 has been launched, runs the
 // collision levels that are needed, and moves the current partition on.
+// Launch profiling: the signature kernels' algorithmic bytes from the rows and
+// row entries they processed this round (vertices alone in their block are
+// skipped), the level-0 table passes' from the positions listed for them.
+void add_round_work(bisim_ctx* ctx, double listed) {
+    unsigned long long w[kWorkWords];
+    if (cudaMemcpy(w, ctx->dwork, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return;
+    double rows[kWorkGroups] = {}, edges[kWorkGroups] = {};
+    for (int g = 0; g < kWorkGroups; ++g)
+        for (int k = 0; k < kWorkSpread; ++k) {
+            rows[g] += static_cast<double>(w[(g * 2) * kWorkSpread + k]);
+            edges[g] += static_cast<double>(w[(g * 2 + 1) * kWorkSpread + k]);
+        }
+    static const int sites[9] = {prof_site("dense_thread_sig_8"), prof_site("dense_thread_sig_16"),
+                                 prof_site("dense_thread_sig_32"), prof_site("dense_warp_sig"),
+                                 prof_site("dense_mid_512"), prof_site("dense_mid_1024"), prof_site("dense_mid_2048"),
+                                 prof_site("dense_mid_4096"), prof_site("dense_mid_8192")};
+    for (int g = 0; g < 9; ++g) prof_add_bytes(sites[g], kSigVertexBytes * rows[g] + kEdgeBytes * edges[g]);
+    BISIM_SITE(site_hc, "hub_count");
+    BISIM_SITE(site_hs, "hub_scatter");
+    BISIM_SITE(site_hd, "hub_dedup");
+    BISIM_SITE(site_hf, "dense_hub_finalize");
+    const double he = edges[kWorkHub];
+    prof_add_bytes(site_hc, (kEdgeBytes + 8.0) * he);
+    prof_add_bytes(site_hs, 16.0 * he);
+    prof_add_bytes(site_hd, 8.0 * he);
+    prof_add_bytes(site_hf, kSigVertexBytes * rows[kWorkHub]);
+    BISIM_SITE(site_in, "dense_insert");
+    BISIM_SITE(site_v, "dense_verify");
+    prof_add_bytes(site_in, kInsertVertexBytes * listed);
+    prof_add_bytes(site_v, kVerifyVertexBytes * listed);
+}
+
 bisim_status finish_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     cudaError_t e;
     const DenseView D = dense_view(ctx);
@@ -1185,6 +1267,7 @@ bisim_status finish_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
         BISIM_SITE(site_cmp, "dense_compare_warp");
         const double pairs = static_cast<double>(ctx->hstate->pairs) + static_cast<double>(ctx->hstate->deferred);
         prof_add_bytes(site_cmp, 12.0 * static_cast<double>(ctx->hstate->aux) + 32.0 * pairs);
+        add_round_work(ctx, static_cast<double>(ctx->hstate->listed));
     }
     if (ctx->hstate->error & kErrTableFull) return set_error(ctx, BISIM_ETIMEOUT, "signature table probe limit reached");
     if (ctx->hstate->error & kErrHubFull) return set_error(ctx, BISIM_ETIMEOUT, "hub set probe limit reached");
@@ -1210,6 +1293,7 @@ bisim_status alloc_round_state(bisim_ctx* ctx, cudaStream_t s) {
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dcnt), sizeof(int32_t) * nv, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dpairs), sizeof(int2) * nv, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dsmall), sizeof(int2) * nv, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dwork), sizeof(unsigned long long) * kWorkWords, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->djoined), nv, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->downs), nv, s)))
         return cuda_error(ctx, e, "alloc dense round state");

@@ -648,6 +648,7 @@ Level level_view(const bisim_ctx* ctx, int j) {
 }
 
 constexpr int kHubPrefetch = 2048;     // hub records read back with the level's counts
+constexpr int64_t kThreadClassOps = 20000;   // batches above this use thread-per-vertex classes
 
 // Host copies of everything a level pass reads back, in pinned memory so that
 // the copies queue behind the level's kernels and one synchronisation covers them.
@@ -771,8 +772,7 @@ void launch_buckets(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     cudaMemsetAsync(S.n_hubs, 0, 4, s);
     BISIM_SITE(site, "inc_buckets");
     Launch L(site, s, 0, 0, 0.0);
-    // frontiers are small: every row gets at least a warp (no thread-per-vertex classes)
-    const int sm = 0, mm = ctx->opt.mid_max_degree;
+    const int sm = ctx->inc_small_max, mm = ctx->opt.mid_max_degree;
     k_class_count<<<kDevGrid, 256, 0, s>>>(S.W.FL, dfl, ctx->xlen, sm, mm, S.ccount, S.cedges);
     k_class_scan<<<1, 32, 0, s>>>(S.ccount, S.dbegin, S.ccursor);
     k_class_scatter<<<kDevGrid, 256, 0, s>>>(S.W.FL, dfl, ctx->xro, ctx->xlen, sm, mm, S.ccursor, S.blist, S.hubs,
@@ -1070,6 +1070,7 @@ void inc_release(bisim_ctx* ctx, cudaStream_t s) {
 // an empty state at every level.
 bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s) {
     const int K = ctx->opt.k_incremental;
+    ctx->inc_small_max = ctx->opt.small_max_degree;     // every vertex is the frontier
     if (K > kMaxIncLevels) return set_error(ctx, BISIM_EINVAL, "k_incremental exceeds 16");
     inc_release(ctx, s);
     bisim_status st;
@@ -1130,7 +1131,11 @@ bisim_status write_current(bisim_ctx* ctx, cudaStream_t s) {
     return e ? cuda_error(ctx, e, "write partition") : BISIM_OK;
 }
 
-bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* rowchg, cudaStream_t s) {
+// n_ops sizes the frontiers to expect: small batches give every frontier row at
+// least a warp (thread-per-vertex classes need many rows to fill the GPU).
+bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* rowchg, int64_t n_ops,
+                        cudaStream_t s) {
+    ctx->inc_small_max = n_ops > kThreadClassOps ? ctx->opt.small_max_degree : 0;
     bisim_status st;
     if ((st = ensure_skey(ctx, s)) != BISIM_OK) return st;
     const int K = ctx->inc_k;

@@ -827,9 +827,9 @@ bisim_status signature_round(bisim_ctx* ctx, const Buckets& B, const int32_t* Pi
     M.cnt = ctx->cnt;
     M.skey = ctx->skey;
     M.H = HubView{B.hub_list, B.n_hub, B.toff, B.tmask, B.tab, B.acc};
-    // the incremental path buckets its frontiers without thread-per-vertex classes
-    // (so no list is sorted); the CSR path sorts lists of up to small_max entries
-    M.small_max = ctx->store_ready ? 0 : ctx->opt.small_max_degree;
+    // lists of up to small_max entries are sorted (thread-per-vertex classes); the
+    // incremental path sets its own limit per batch
+    M.small_max = ctx->store_ready ? ctx->inc_small_max : ctx->opt.small_max_degree;
     M.mid_max = ctx->opt.mid_max_degree;
     return resolve(ctx, M, Pout, vlist, vcount, s, out_blocks);
 }

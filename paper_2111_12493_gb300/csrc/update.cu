@@ -172,6 +172,7 @@ struct KeyTable {
     int32_t* c0;
     int32_t* rem;
     int32_t* taken;
+    int32_t* hdel;     // the key has an EDGE_DEL in the batch (only then do its old copies matter)
     uint32_t mask;
 };
 
@@ -381,43 +382,76 @@ __global__ void k_fill_src(const int64_t* __restrict__ rp, int32_t n, int32_t* _
 
 // ----------------------------------------------------------------------------- row-store edits
 
-// Out-row tasks of the batch's distinct keys: mode 0 counts a key's copies
-// present before the batch (keys without a deleted endpoint whose endpoints
-// were live), mode 1 deletes the copies the fold removed.
-__global__ void k_key_tasks(const int64_t* __restrict__ keyslot, int64_t ne, KeyTable T,
-                            const uint8_t* __restrict__ killed, const uint8_t* __restrict__ alive0, StoreView S,
-                            int mode, TierLists L) {
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t b0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; b0 < ne; b0 += stride) {
-        const int64_t i = b0 + threadIdx.x;
+// Keys with a deletion: a key that is only added to ends with its old copies
+// plus its adds whatever the old count, so only these need the count.
+__global__ void k_mark_deletes(const bisim_op* __restrict__ ops, const uint64_t* __restrict__ kpos, int64_t ne,
+                               KeyTable T) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < ne;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const bisim_op o = ops[kpos[i]];
+        if (o.kind != BISIM_OP_EDGE_DEL) continue;
+        const int64_t k = key_find(T, o.src, o.dst, o.label);
+        if (k >= 0) T.hdel[k] = 1;
+    }
+}
+
+// Source rows of the batch's keys that have a deletion, each listed once
+// (xmark is kept zero between batches).
+__global__ void k_key_rows(const int64_t* __restrict__ keyslot, int64_t ne, KeyTable T, uint32_t* __restrict__ xmark,
+                           int32_t* __restrict__ rows, unsigned* __restrict__ n_rows) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < ne;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (keyslot[i] < 0 || !T.hdel[keyslot[i]]) continue;
+        const int32_t u = T.u[keyslot[i]];
+        if (atomicExch(&xmark[u], 1u) == 0u) rows[atomicAdd(n_rows, 1u)] = u;
+    }
+}
+
+__global__ void k_rows_to_tasks(const int32_t* __restrict__ rows, const unsigned* __restrict__ n_rows, StoreView S,
+                                uint32_t* __restrict__ xmark, int clear, TierLists L) {
+    const unsigned count = *reinterpret_cast<const volatile unsigned*>(n_rows);
+    for (unsigned b0 = blockIdx.x * blockDim.x; b0 < count; b0 += gridDim.x * blockDim.x) {
+        const unsigned i = b0 + threadIdx.x;
         bool has = false;
         RowTask t{0, 0, 0};
-        if (i < ne && keyslot[i] >= 0) {
-            const int32_t slot = static_cast<int32_t>(keyslot[i]);
-            const int32_t u = T.u[slot], w = T.w[slot];
-            has = mode == 0 ? (!killed[u] && !killed[w] && alive0[u] && alive0[w]) : T.rem[slot] > 0;
-            if (has) t = RowTask{S.xro[u], S.xlen[u], slot};
+        if (i < count) {
+            const int32_t u = rows[i];
+            has = true;
+            t = RowTask{S.xro[u], S.xlen[u], u};
+            if (clear) xmark[u] = 0u;
         }
         tier_push(L, has, t);
     }
 }
 
-struct KeyCount {
+// Copies of each batch key present before the batch: every touched source row
+// is scanned once and its entries looked up in the batch's key table. An
+// entry into a vertex that was dead before the batch is not an edge.
+struct KeyCountRows {
     const unsigned long long* xpe;
+    const uint8_t* alive0;
     KeyTable T;
     __device__ void operator()(const RowTask& t, int64_t e, bool in) const {
-        const bool hit = in && xpe[e] == pack_edge(T.l[t.arg], T.w[t.arg]);
-        const unsigned b = __ballot_sync(0xffffffffu, hit);
-        if ((threadIdx.x & 31u) == 0u && b) atomicAdd(&T.c0[t.arg], __popc(b));
+        if (!in) return;
+        const unsigned long long x = xpe[e];
+        if (x == kRowTomb) return;
+        const int32_t w = static_cast<int32_t>(static_cast<uint32_t>(x));
+        if (!alive0[w]) return;
+        const int64_t k = key_find(T, t.arg, w, static_cast<int32_t>(x >> 32));
+        if (k >= 0 && T.hdel[k]) atomicAdd(&T.c0[k], 1);
     }
 };
 
-struct KeyRemove {
+// Deletes the copies the fold removed (any copies of a key are interchangeable).
+struct KeyRemoveRows {
     unsigned long long* xpe;
     KeyTable T;
     __device__ void operator()(const RowTask& t, int64_t e, bool in) const {
-        if (in && xpe[e] == pack_edge(T.l[t.arg], T.w[t.arg]) && atomicAdd(&T.taken[t.arg], 1) < T.rem[t.arg])
-            xpe[e] = kRowTomb;
+        if (!in) return;
+        const unsigned long long x = xpe[e];
+        if (x == kRowTomb) return;
+        const int64_t k = key_find(T, t.arg, static_cast<int32_t>(static_cast<uint32_t>(x)), static_cast<int32_t>(x >> 32));
+        if (k >= 0 && T.rem[k] > 0 && atomicAdd(&T.taken[k], 1) < T.rem[k]) xpe[e] = kRowTomb;
     }
 };
 
@@ -696,7 +730,7 @@ bisim_status batch_begin(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, si
     need(4 * nb); need(4 * nb); need(4 * nb); need(4 * nb);          // edge key halves (x2 each)
     need(8 * nb); need(8 * nb); need(8 * nb); need(8 * nb);          // edge positions (x4)
     need(sizeof(AddRec) * nb); need(8 * nb);                          // additions, key slots
-    for (int q = 0; q < 7; ++q) need(4 * static_cast<size_t>(tsize)); // key table
+    for (int q = 0; q < 8; ++q) need(4 * static_cast<size_t>(tsize)); // key table
     need(8 * 4);
     need(8 * tmpw);
     need(extra);
@@ -717,10 +751,10 @@ bisim_status batch_begin(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, si
     uint64_t* kp3 = reinterpret_cast<uint64_t*>(carve(8 * nb));
     B.add = reinterpret_cast<AddRec*>(carve(sizeof(AddRec) * nb));
     B.keyslot = reinterpret_cast<int64_t*>(carve(8 * nb));
-    int32_t* tab_arrays[7];
-    for (int q = 0; q < 7; ++q) tab_arrays[q] = reinterpret_cast<int32_t*>(carve(4 * static_cast<size_t>(tsize)));
+    int32_t* tab_arrays[8];
+    for (int q = 0; q < 8; ++q) tab_arrays[q] = reinterpret_cast<int32_t*>(carve(4 * static_cast<size_t>(tsize)));
     B.T = KeyTable{tab_arrays[0], tab_arrays[1], tab_arrays[2], tab_arrays[3], tab_arrays[4], tab_arrays[5],
-                   tab_arrays[6], tsize - 1};
+                   tab_arrays[6], tab_arrays[7], tsize - 1};
     B.counters = reinterpret_cast<unsigned long long*>(carve(8 * 4));
     B.tmp = reinterpret_cast<int64_t*>(carve(8 * tmpw));
     B.extra = carve(extra);
@@ -780,7 +814,7 @@ bisim_status batch_begin(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, si
     }
     cudaMemsetAsync(killed, 0, n + 1, s);
     cudaMemsetAsync(B.counters, 0, 8 * 4, s);
-    for (int q = 3; q < 7; ++q) cudaMemsetAsync(tab_arrays[q], 0, 4 * static_cast<size_t>(tsize), s);
+    for (int q = 3; q < 8; ++q) cudaMemsetAsync(tab_arrays[q], 0, 4 * static_cast<size_t>(tsize), s);
     if (alive0 && n > 0) cudaMemcpyAsync(alive0, ctx->alive, n, cudaMemcpyDeviceToDevice, s);
     if (nv > 0) {
         Launch L(site_ops, s, 0, 0, 16.0 * nv);
@@ -969,20 +1003,19 @@ bisim_status apply_ops_to_store(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
     const int grid = kTierGrid;
     BISIM_SITE(site, "update_rows");
 
-    // copies present before the batch, the fold, and the deletions of copies
+    // copies present before the batch, the fold, and the deletions of copies; each
+    // source row a key names is scanned once per pass
     if (ne > 0) {
         Launch L(site, s, 0, 0, 0.0);
         cudaMemsetAsync(cnts, 0, 16, s);
-        k_key_tasks<<<grid_for(ne, 256), 256, 0, s>>>(B.keyslot, ne, T, killed, alive0, S, 0, LA);
-        run_tiers(LA, KeyCount{ctx->xpe, T}, s);
+        cudaMemsetAsync(n_touched, 0, 4, s);
+        k_mark_deletes<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, B.skp, ne, T);
+        k_key_rows<<<grid_for(ne, 256), 256, 0, s>>>(B.keyslot, ne, T, ctx->xmark, touched_o, n_touched);
+        k_rows_to_tasks<<<grid, 256, 0, s>>>(touched_o, n_touched, S, ctx->xmark, 1, LA);
+        run_tiers(LA, KeyCountRows{ctx->xpe, alive0, T}, s);
     }
     fold_keys(B, killed, rowchg, s);
-    if (ne > 0) {
-        Launch L(site, s, 0, 0, 0.0);
-        cudaMemsetAsync(cnts, 0, 16, s);
-        k_key_tasks<<<grid_for(ne, 256), 256, 0, s>>>(B.keyslot, ne, T, killed, alive0, S, 1, LA);
-        run_tiers(LA, KeyRemove{ctx->xpe, T}, s);
-    }
+    if (ne > 0) run_tiers(LA, KeyRemoveRows{ctx->xpe, T}, s);
     // deleted and revived vertices
     if (nv > 0) {
         RowTask* pt = tb;
