@@ -55,7 +55,7 @@ NCU_TRAFFIC_BYTES = {
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (smoke runs only)")
@@ -64,6 +64,10 @@ def parse_args():
     ap.add_argument("--no-serving", action="store_true", help="skip the update-batch latency section")
     ap.add_argument("--serving-batches", type=int, default=40)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default class thresholds")
+    ap.add_argument("--profile-updates", type=int, default=0, metavar="K",
+                    help="profiler capture window only: run the 1k-op update batches of the serving section "
+                         "alone and bracket K incremental batches (after eight) with cudaProfilerStart/Stop, "
+                         "for ncu --profile-from-start off; prints the batches' latencies, not a bench line")
     ap.add_argument("--workload", default="powerlaw", choices=["powerlaw", "chain", "batched"],
                     help="powerlaw: 10M/100M to the fixpoint (the headline); chain: 1000 paths of 1000 "
                          "+ 2M random edges to the fixpoint; batched: 4096 graphs in one context, k=3")
@@ -213,7 +217,7 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -589,9 +593,44 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def profile_updates(args, local):
+    """The serving section's closed loop of 1k-op batches, incremental only, with a
+    profiler window around K batches (launch lists of the update path)."""
+    import torch
+    from paper_2111_12493_gb300 import bisim, graphgen
+    n, m = SERVING["n"], SERVING["m"]
+    g = graphgen.powerlaw_graph(n=n, m=m, exponent=WORKLOAD["exponent"], dmax=min(WORKLOAD["dmax"], m // 10),
+                                n_elabels=WORKLOAD["n_elabels"], n_vlabels=WORKLOAD["n_vlabels"],
+                                untyped_frac=WORKLOAD["untyped"], seed=SERVING["seed"])
+    dev = torch.device("cuda", local)
+    d = {k: torch.from_numpy(g[k]).to(dev) for k in ("src", "dst", "elabel", "vlabel")}
+    ctx = bisim.summarize_init_coo(n, d["src"], d["dst"], d["elabel"], d["vlabel"],
+                                   options=bisim.default_options(k_incremental=SERVING["k"]))
+    bisim.apply_updates(ctx, torch.zeros((0, 4), dtype=torch.int32, device=dev))
+    batches = graphgen.update_batches(g, 8 + args.profile_updates, fixed_size=1000, seed=51)
+    part = torch.empty(n, dtype=torch.int32, device=dev)
+    lat = []
+    for i, b in enumerate(batches):
+        ops = torch.from_numpy(b["ops"]).pin_memory()
+        torch.cuda.synchronize()
+        if i == 8:
+            torch.cuda.profiler.start()
+        t0 = time.perf_counter()
+        bisim.apply_updates(ctx, ops)
+        bisim.get_partition(ctx, out=part)
+        torch.cuda.synchronize()
+        lat.append(1e3 * (time.perf_counter() - t0))
+    torch.cuda.profiler.stop()
+    bisim.summarize_destroy(ctx)
+    print(json.dumps({"profile_updates": args.profile_updates, "batch_ms": lat}))
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_init()
+    if args.profile_updates > 0:
+        profile_updates(args, local)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

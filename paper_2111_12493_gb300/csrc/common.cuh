@@ -363,6 +363,7 @@ struct bisim_ctx {
     int32_t* addo = nullptr;       // [n] per-batch adds per out-row (kept zero between batches)
     int32_t* addi = nullptr;       // [n] per-batch adds per in-row
     uint32_t* xmark = nullptr;     // [n] per-batch: out-row already listed (kept zero between batches)
+    uint32_t* dmark = nullptr;     // [n / 32 + 1] per-batch bitmap: target of a deleted key (kept zero)
     int32_t inc_small_max = 0;     // thread-per-vertex limit of the incremental path's current frontiers
 
     // incremental maintenance (apply_updates): per level j = 0..inc_k, block ids

@@ -177,9 +177,10 @@ void store_release(bisim_ctx* ctx, cudaStream_t s) {
     ctx_free(ctx, ctx->addo, 4 * n, s);
     ctx_free(ctx, ctx->addi, 4 * n, s);
     ctx_free(ctx, ctx->xmark, 4 * n, s);
+    ctx_free(ctx, ctx->dmark, 4 * (n / 32 + 1), s);
     ctx->xro = ctx->yro = ctx->dtail = nullptr;
     ctx->xlen = ctx->xcap = ctx->ylen = ctx->ycap = ctx->ype = ctx->addo = ctx->addi = nullptr;
-    ctx->xmark = nullptr;
+    ctx->xmark = ctx->dmark = nullptr;
     ctx->xpe = nullptr;
     ctx->xpool = ctx->ypool = 0;
     ctx->store_ready = false;
@@ -203,7 +204,8 @@ bisim_status store_build(bisim_ctx* ctx, cudaStream_t s, int64_t room_out, int64
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dtail), 8 * 4, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->addo), 4 * nn, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->addi), 4 * nn, s)) ||
-        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->xmark), 4 * nn, s)))
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->xmark), 4 * nn, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dmark), 4 * (nn / 32 + 1), s)))
         return cuda_error(ctx, e, "alloc row store");
     const size_t tw = scan_temp_words(static_cast<int64_t>(n) + 1);
     int64_t* scratch = nullptr;
@@ -215,6 +217,7 @@ bisim_status store_build(bisim_ctx* ctx, cudaStream_t s, int64_t room_out, int64
     cudaMemsetAsync(ctx->addo, 0, 4 * nn, s);
     cudaMemsetAsync(ctx->addi, 0, 4 * nn, s);
     cudaMemsetAsync(ctx->xmark, 0, 4 * nn, s);
+    cudaMemsetAsync(ctx->dmark, 0, 4 * (nn / 32 + 1), s);
     cudaMemsetAsync(ctx->ylen, 0, 4 * nn, s);
     int64_t totals[2] = {0, 0};
     {

@@ -247,11 +247,15 @@ __global__ void k_fold_keys(VertexOps V, const uint32_t* __restrict__ khi, const
         const bisim_op oa = V.ops[kpos[i]];
         const int32_t u = oa.src, w = oa.dst, l = oa.label;
         const bool dropped = killed[u] || killed[w];           // initial copies go with the deletion
-        const int c0 = dropped ? 0 : T.c0[slot];
-        const int64_t lk = max(last_kill(V, u), last_kill(V, w));
-        int c = c0;
         int64_t end = i;
         while (end < ne && khi[end] == khi[i] && klo[end] == klo[i]) ++end;
+        // a key that is only deleted removes one copy per deletion, as far as copies
+        // exist: an old count at least its number of operations gives exactly that
+        // (the row-store path does not count such keys; the removal stops when the
+        // row has no copy left)
+        const int c0 = dropped ? 0 : (T.hdel[slot] == 1 ? static_cast<int>(end - i) : T.c0[slot]);
+        const int64_t lk = max(last_kill(V, u), last_kill(V, w));
+        int c = c0;
         for (int64_t b = i; b < end; ++b) {
             const uint64_t p = kpos[b];
             const bisim_op ob = V.ops[p];
@@ -382,29 +386,46 @@ __global__ void k_fill_src(const int64_t* __restrict__ rp, int32_t n, int32_t* _
 
 // ----------------------------------------------------------------------------- row-store edits
 
-// Keys with a deletion: a key that is only added to ends with its old copies
-// plus its adds whatever the old count, so only these need the count.
-__global__ void k_mark_deletes(const bisim_op* __restrict__ ops, const uint64_t* __restrict__ kpos, int64_t ne,
-                               KeyTable T) {
+// Operation kinds per key: bit 0 a deletion, bit 1 an addition. A key that is
+// only added to ends with its old copies plus its adds whatever the old count;
+// one that is only deleted removes a copy per deletion while copies last; only
+// keys with both need their old copies counted.
+__global__ void k_mark_kinds(const bisim_op* __restrict__ ops, const uint64_t* __restrict__ kpos, int64_t ne,
+                             KeyTable T) {
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < ne;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const bisim_op o = ops[kpos[i]];
-        if (o.kind != BISIM_OP_EDGE_DEL) continue;
         const int64_t k = key_find(T, o.src, o.dst, o.label);
-        if (k >= 0) T.hdel[k] = 1;
+        if (k >= 0) atomicOr(&T.hdel[k], o.kind == BISIM_OP_EDGE_DEL ? 1 : 2);
     }
 }
 
-// Source rows of the batch's keys that have a deletion, each listed once
-// (xmark is kept zero between batches).
+// Source rows of the keys with a deletion (rows_del) and of the keys with both
+// kinds (rows_mix), each listed once per list (xmark is kept zero between batches).
+// Their targets are also flagged in the bitmap `dmark` (kept zero between
+// batches), which lets the row scans skip most entries without a table lookup.
 __global__ void k_key_rows(const int64_t* __restrict__ keyslot, int64_t ne, KeyTable T, uint32_t* __restrict__ xmark,
-                           int32_t* __restrict__ rows, unsigned* __restrict__ n_rows) {
+                           uint32_t* __restrict__ dmark, int32_t* __restrict__ rows_del,
+                           int32_t* __restrict__ rows_mix, unsigned* __restrict__ n_rows) {
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < ne;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        if (keyslot[i] < 0 || !T.hdel[keyslot[i]]) continue;
+        if (keyslot[i] < 0) continue;
+        const int kinds = T.hdel[keyslot[i]];
+        if (!(kinds & 1)) continue;
         const int32_t u = T.u[keyslot[i]];
-        if (atomicExch(&xmark[u], 1u) == 0u) rows[atomicAdd(n_rows, 1u)] = u;
+        const int32_t w = T.w[keyslot[i]];
+        atomicOr(&dmark[w >> 5], 1u << (w & 31));
+        const unsigned old = atomicOr(&xmark[u], kinds == 3 ? 3u : 1u);
+        if (!(old & 1u)) rows_del[atomicAdd(&n_rows[0], 1u)] = u;
+        if (kinds == 3 && !(old & 2u)) rows_mix[atomicAdd(&n_rows[1], 1u)] = u;
     }
+}
+
+__global__ void k_clear_dmark(const int64_t* __restrict__ keyslot, int64_t ne, KeyTable T,
+                              uint32_t* __restrict__ dmark) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < ne;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        if (keyslot[i] >= 0 && (T.hdel[keyslot[i]] & 1)) dmark[T.w[keyslot[i]] >> 5] = 0u;
 }
 
 __global__ void k_rows_to_tasks(const int32_t* __restrict__ rows, const unsigned* __restrict__ n_rows, StoreView S,
@@ -427,30 +448,38 @@ __global__ void k_rows_to_tasks(const int32_t* __restrict__ rows, const unsigned
 // Copies of each batch key present before the batch: every touched source row
 // is scanned once and its entries looked up in the batch's key table. An
 // entry into a vertex that was dead before the batch is not an edge.
+__device__ __forceinline__ bool dmarked(const uint32_t* dmark, int32_t w) {
+    return (dmark[w >> 5] >> (w & 31)) & 1u;
+}
+
 struct KeyCountRows {
     const unsigned long long* xpe;
     const uint8_t* alive0;
+    const uint32_t* dmark;
     KeyTable T;
     __device__ void operator()(const RowTask& t, int64_t e, bool in) const {
         if (!in) return;
         const unsigned long long x = xpe[e];
         if (x == kRowTomb) return;
         const int32_t w = static_cast<int32_t>(static_cast<uint32_t>(x));
-        if (!alive0[w]) return;
+        if (!dmarked(dmark, w) || !alive0[w]) return;
         const int64_t k = key_find(T, t.arg, w, static_cast<int32_t>(x >> 32));
-        if (k >= 0 && T.hdel[k]) atomicAdd(&T.c0[k], 1);
+        if (k >= 0 && T.hdel[k] == 3) atomicAdd(&T.c0[k], 1);
     }
 };
 
 // Deletes the copies the fold removed (any copies of a key are interchangeable).
 struct KeyRemoveRows {
     unsigned long long* xpe;
+    const uint32_t* dmark;
     KeyTable T;
     __device__ void operator()(const RowTask& t, int64_t e, bool in) const {
         if (!in) return;
         const unsigned long long x = xpe[e];
         if (x == kRowTomb) return;
-        const int64_t k = key_find(T, t.arg, static_cast<int32_t>(static_cast<uint32_t>(x)), static_cast<int32_t>(x >> 32));
+        const int32_t w = static_cast<int32_t>(static_cast<uint32_t>(x));
+        if (!dmarked(dmark, w)) return;
+        const int64_t k = key_find(T, t.arg, w, static_cast<int32_t>(x >> 32));
         if (k >= 0 && T.rem[k] > 0 && atomicAdd(&T.taken[k], 1) < T.rem[k]) xpe[e] = kRowTomb;
     }
 };
@@ -1007,15 +1036,20 @@ bisim_status apply_ops_to_store(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
     // source row a key names is scanned once per pass
     if (ne > 0) {
         Launch L(site, s, 0, 0, 0.0);
-        cudaMemsetAsync(cnts, 0, 16, s);
-        cudaMemsetAsync(n_touched, 0, 4, s);
-        k_mark_deletes<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, B.skp, ne, T);
-        k_key_rows<<<grid_for(ne, 256), 256, 0, s>>>(B.keyslot, ne, T, ctx->xmark, touched_o, n_touched);
+        cudaMemsetAsync(cnts, 0, 32, s);
+        cudaMemsetAsync(n_touched, 0, 8, s);
+        k_mark_kinds<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, B.skp, ne, T);
+        k_key_rows<<<grid_for(ne, 256), 256, 0, s>>>(B.keyslot, ne, T, ctx->xmark, ctx->dmark, touched_o, touched_i,
+                                                     n_touched);
+        k_rows_to_tasks<<<grid, 256, 0, s>>>(touched_i, n_touched + 1, S, ctx->xmark, 0, LB);
         k_rows_to_tasks<<<grid, 256, 0, s>>>(touched_o, n_touched, S, ctx->xmark, 1, LA);
-        run_tiers(LA, KeyCountRows{ctx->xpe, alive0, T}, s);
+        run_tiers(LB, KeyCountRows{ctx->xpe, alive0, ctx->dmark, T}, s);
     }
     fold_keys(B, killed, rowchg, s);
-    if (ne > 0) run_tiers(LA, KeyRemoveRows{ctx->xpe, T}, s);
+    if (ne > 0) {
+        run_tiers(LA, KeyRemoveRows{ctx->xpe, ctx->dmark, T}, s);
+        k_clear_dmark<<<grid_for(ne, 256), 256, 0, s>>>(B.keyslot, ne, T, ctx->dmark);
+    }
     // deleted and revived vertices
     if (nv > 0) {
         RowTask* pt = tb;
