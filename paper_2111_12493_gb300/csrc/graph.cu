@@ -13,45 +13,42 @@ unsigned grid_for(int64_t n, int threads) {
     return static_cast<unsigned>(std::max<int64_t>(1, cdiv(n, threads)));
 }
 
+// Checks every edge and counts out-degrees (one atomic per distinct source in
+// a warp; edge lists are often grouped by source). Degrees of a list that fails
+// the check are never used.
 __global__ void k_validate_coo(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                                int64_t m, int32_t n, const uint8_t* __restrict__ alive,
-                               unsigned* err) {
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        int32_t s = src[e], d = dst[e];
-        bool ok = s >= 0 && s < n && d >= 0 && d < n;
-        if (ok && alive != nullptr) ok = alive[s] && alive[d];
-        if (!ok) atomicOr(err, kErrBadInput);
-    }
-}
-
-__global__ void k_pack_coo(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                           const int32_t* __restrict__ elab, int64_t m, uint32_t* __restrict__ keys,
-                           uint64_t* __restrict__ vals, int32_t* __restrict__ deg) {
+                               int32_t* __restrict__ deg, unsigned* err) {
     // trip count is uniform across the warp so the match below sees every lane
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t e0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; e0 < m; e0 += stride) {
         const int64_t e = e0 + threadIdx.x;
-        const bool valid = e < m;
         int32_t s = -1;
-        if (valid) {
+        if (e < m) {
             s = src[e];
-            keys[e] = static_cast<uint32_t>(s);
-            vals[e] = (static_cast<uint64_t>(static_cast<uint32_t>(elab[e])) << 32) |
-                      static_cast<uint32_t>(dst[e]);
+            const int32_t d = dst[e];
+            bool ok = s >= 0 && s < n && d >= 0 && d < n;
+            if (ok && alive != nullptr) ok = alive[s] && alive[d];
+            if (!ok) {
+                atomicOr(err, kErrBadInput);
+                s = -1;
+            }
         }
-        // one atomic per distinct source in the warp (edge lists are often grouped by source)
         const unsigned peers = __match_any_sync(0xffffffffu, s);
-        if (valid && (threadIdx.x & 31) == static_cast<unsigned>(__ffs(peers) - 1))
-            atomicAdd(&deg[s], __popc(peers));
+        if (s >= 0 && (threadIdx.x & 31) == static_cast<unsigned>(__ffs(peers) - 1)) atomicAdd(&deg[s], __popc(peers));
     }
 }
 
-// Edge sort keys become positions of the layout: the sorted edges are then its packed rows.
-__global__ void k_rekey(uint32_t* __restrict__ keys, int64_t m, const int32_t* __restrict__ vpos) {
+// Sort keys are the sources' positions in the layout (so the sorted edges are
+// its packed rows); values are the packed (label, target) words.
+__global__ void k_pack_coo(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                           const int32_t* __restrict__ elab, int64_t m, const int32_t* __restrict__ vpos,
+                           uint32_t* __restrict__ keys, uint64_t* __restrict__ vals) {
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        keys[e] = static_cast<uint32_t>(vpos[keys[e]]);
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        keys[e] = static_cast<uint32_t>(vpos[src[e]]);
+        vals[e] = (static_cast<uint64_t>(static_cast<uint32_t>(elab[e])) << 32) | static_cast<uint32_t>(dst[e]);
+    }
 }
 
 __global__ void k_validate_csr(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -192,21 +189,18 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
     }
 
     cudaMemsetAsync(&ctx->dstate->error, 0, sizeof(unsigned), s);
+    cudaMemsetAsync(deg, 0, sizeof(int32_t) * (n + 1), s);
     BISIM_SITE(site_val, "validate_edges");
     BISIM_SITE(site_pack, "csr_pack");
     if (m > 0)
         Launch(site_val, s, 0, m, 8.0 * m),
-        k_validate_coo<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(src, dst, m, n, ctx->alive, &ctx->dstate->error);
+        k_validate_coo<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(src, dst, m, n, ctx->alive, deg,
+                                                                                   &ctx->dstate->error);
     cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); return cuda_error(ctx, e, "validate edges"); }
     if (ctx->hstate->error & kErrBadInput) {
         cudaFreeAsync(base, s);
         return set_error(ctx, BISIM_EINVAL, "edge endpoint out of range [0, n) or on a dead vertex");
-    }
-    cudaMemsetAsync(deg, 0, sizeof(int32_t) * (n + 1), s);
-    if (m > 0) {
-        Launch L(site_pack, s, 0, m, 24.0 * m);   // read src, dst, label; write key + value
-        k_pack_coo<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(src, dst, elab, m, k0, v0, deg);
     }
     bisim_status st = dense_layout_positions(ctx, deg, s);
     if (st != BISIM_OK) {
@@ -216,8 +210,10 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
     int which = 0;
     if (m > 0) {
         {
-            Launch L(site_pack, s, 0, m, 12.0 * m);
-            k_rekey<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(k0, m, ctx->dvpos);
+            // read src, dst, label and the source's position; write key + value
+            Launch L(site_pack, s, 0, m, 28.0 * m);
+            k_pack_coo<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(src, dst, elab, m, ctx->dvpos, k0,
+                                                                                    v0);
         }
         which = radix_sort_pairs(k0, v0, k1, v1, m, bits_for(n), tmp, s);
     }
