@@ -370,6 +370,7 @@ struct bisim_ctx {
     // per vertex, |S| per vertex, block records and a hash index key -> block
     int32_t inc_k = -1;            // levels built (-1: no incremental state)
     int32_t* lid[bisim::kMaxIncLevels + 1] = {};
+    uint8_t* lstale[bisim::kMaxIncLevels + 1] = {};  // per vertex: its block at this level has no current index key
     int32_t* lcnt[bisim::kMaxIncLevels + 1] = {};
     unsigned long long* bkey[bisim::kMaxIncLevels + 1] = {};
     int32_t* bcnt[bisim::kMaxIncLevels + 1] = {};

@@ -703,22 +703,78 @@ __global__ void k_dense_hub_finalize(const DenseView D, const HubSets H) {
 // positions are listed for the table. Alone vertices are counted as blocks and,
 // unless the output buffer already holds P_i, get P_{i+1}[v] = v here. The
 // joined flags are cleared for this round's verification to set again.
+// Each thread takes kScanRun consecutive positions (16-byte loads of the
+// flags), so the CTA's one scan and one atomic cover 4096 positions.
+constexpr int kScanRun = 16;
 __global__ void __launch_bounds__(kThreads) k_alone_scan(int64_t count, const DenseView D, int32_t* __restrict__ Pout,
                                                          bool out_has_in, int32_t* __restrict__ list, DevState* st) {
-    const int64_t pos = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    bool alone = false, listed = false;
-    if (pos < count) {
-        alone = alone_last_round(D, pos);
-        D.joined[pos] = 0;
-        listed = !alone;
-        if (alone && !out_has_in) {
-            const int32_t v = D.vert[pos];
+    __shared__ unsigned wlisted[kThreads / 32];
+    __shared__ unsigned walone[kThreads / 32];
+    __shared__ unsigned base;
+    const int64_t p0 = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) * kScanRun;
+    const unsigned lane = lane_id();
+    const int warp = static_cast<int>(threadIdx.x >> 5);
+    uint32_t listed = 0u;                           // bit k: position p0 + k needs the table
+    unsigned alone = 0u;
+    if (p0 + kScanRun <= count) {
+        const uint4 ow = *reinterpret_cast<const uint4*>(D.own + p0);
+        const uint4 jw = *reinterpret_cast<const uint4*>(D.joined + p0);
+        *reinterpret_cast<uint4*>(D.joined + p0) = make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t o[4] = {ow.x, ow.y, ow.z, ow.w}, j[4] = {jw.x, jw.y, jw.z, jw.w};
+#pragma unroll
+        for (int k = 0; k < kScanRun; ++k) {
+            const bool a = ((o[k >> 2] >> (8 * (k & 3))) & 0xffu) && !((j[k >> 2] >> (8 * (k & 3))) & 0xffu);
+            if (!a) listed |= 1u << k;
+        }
+    } else {
+        for (int k = 0; k < kScanRun && p0 + k < count; ++k) {
+            const int64_t pos = p0 + k;
+            if (!alone_last_round(D, pos)) listed |= 1u << k;
+            D.joined[pos] = 0;
+        }
+    }
+    const int valid = p0 >= count ? 0 : (p0 + kScanRun <= count ? kScanRun : static_cast<int>(count - p0));
+    const uint32_t vmask = valid == 32 ? ~0u : ((1u << valid) - 1u);
+    alone = static_cast<unsigned>(__popc(vmask & ~listed));
+    if (alone && !out_has_in) {
+        uint32_t am = vmask & ~listed;
+        while (am) {
+            const int k = __ffs(am) - 1;
+            am &= am - 1u;
+            const int32_t v = D.vert[p0 + k];
             Pout[v] = v;
         }
     }
-    __shared__ unsigned sh[kThreads / 32 + 1];
-    block_count(alone, &st->blocks);
-    block_push(listed, static_cast<int32_t>(pos), list, &st->listed, sh);
+    // CTA-wide exclusive scan of the listed counts, one atomic for the CTA's range
+    const unsigned mine = static_cast<unsigned>(__popc(listed));
+    unsigned inc = mine, al = alone;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= static_cast<unsigned>(o)) inc += y;
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+    }
+    if (lane == 31) wlisted[warp] = inc;
+    if (lane == 0) walone[warp] = al;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0, atot = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const unsigned c = wlisted[w];
+            wlisted[w] = tot;
+            tot += c;
+            atot += walone[w];
+        }
+        base = tot ? atomicAdd(&st->listed, tot) : 0u;
+        if (atot) atomicAdd(&st->blocks, static_cast<unsigned long long>(atot));
+    }
+    __syncthreads();
+    unsigned at = base + wlisted[warp] + inc - mine;
+    while (listed) {
+        const int k = __ffs(listed) - 1;
+        listed &= listed - 1u;
+        list[at++] = static_cast<int32_t>(p0 + k);
+    }
 }
 
 // Table insert of the listed positions with the level's salted hash. The count
@@ -1097,8 +1153,8 @@ void launch_level(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const Tabl
         // reads their number on the device
         {
             Launch L(site_as, s, count, 0, 11.0 * count);
-            k_alone_scan<<<grid_for(count, kThreads), kThreads, 0, s>>>(count, D, Pout, out_has_in, ctx->ulist[1],
-                                                                         ctx->dstate);
+            k_alone_scan<<<grid_for(cdiv(count, kScanRun), kThreads), kThreads, 0, s>>>(count, D, Pout, out_has_in,
+                                                                                          ctx->ulist[1], ctx->dstate);
         }
         const unsigned grid = static_cast<unsigned>(std::min<int64_t>(kPersistGrid, cdiv(count, kThreads)));
         const unsigned* dcount = &ctx->dstate->listed;

@@ -56,6 +56,7 @@ __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // Per-level device view.
 struct Level {
+    uint8_t* stale;               // levels >= 1: the vertex's block has no current index key (see k_settle_single)
     int32_t* lid;                 // block id per vertex (-1 dead)
     int32_t* lcnt;                // |S| per vertex (levels >= 1)
     unsigned long long* bkey;     // per block: signature index key
@@ -89,6 +90,7 @@ struct Work {
     uint8_t* inF;                 // [n]
     uint8_t* changed;             // [n]
     uint8_t* next;                // [n]
+    uint8_t* recomp;              // [n] vertices the next level must recompute (their block gained a member)
     int32_t n;
     int64_t bcap;
     unsigned* err;                // self-check bits: an index out of range was skipped
@@ -109,19 +111,32 @@ __device__ __forceinline__ void warp_list_push(bool f, int32_t v, int32_t* out, 
     if (f) out[base + __popc(ball & ((1u << lane_id()) - 1u))] = v;
 }
 
-// The level's frontier in one pass: F = vertices with any of the flags a, b, c
-// set (a null `a` flags every vertex), FL = its live part.
+// The level's frontier in one pass: F = vertices with any of the flags a, b,
+// c, d set (a null `a` flags every vertex), split by liveness and, from level
+// 1 on, by the size of the vertex's block one level down: a vertex alone in
+// its level-(j-1) block is alone at level j too (each level refines the last),
+// so it goes to FX and needs no signature; the other live ones go to FL.
+// count: [0] |F|, [1] |FL|, [2] |FX|.
 __global__ void k_frontier(const uint8_t* __restrict__ a, const uint8_t* __restrict__ b,
-                           const uint8_t* __restrict__ c, const uint8_t* __restrict__ alive, int32_t n,
-                           int32_t* __restrict__ F, int32_t* __restrict__ FL, unsigned long long* __restrict__ count) {
+                           const uint8_t* __restrict__ c, const uint8_t* __restrict__ d,
+                           const uint8_t* __restrict__ alive, int32_t n, const int32_t* __restrict__ lid_prev,
+                           const int32_t* __restrict__ bcnt_prev, uint8_t* __restrict__ stale,
+                           int32_t* __restrict__ F, int32_t* __restrict__ FL, int32_t* __restrict__ FX,
+                           unsigned long long* __restrict__ count) {
     const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    bool f = false, live = false;
+    bool f = false, live = false, alone = false;
     if (v < n) {
-        f = a == nullptr || a[v] || (b && b[v]) || (c && c[v]);
+        f = a == nullptr || a[v] || (b && b[v]) || (c && c[v]) || (d && d[v]);
         live = f && alive[v];
+        if (live && lid_prev) {
+            const int32_t pb = lid_prev[v];
+            alone = pb >= 0 && bcnt_prev[pb] == 1;
+            stale[v] = alone ? 1 : 0;
+        }
     }
     warp_list_push(f, static_cast<int32_t>(v), F, &count[0]);
-    warp_list_push(live, static_cast<int32_t>(v), FL, &count[1]);
+    warp_list_push(live && !alone, static_cast<int32_t>(v), FL, &count[1]);
+    warp_list_push(alone, static_cast<int32_t>(v), FX, &count[2]);
 }
 
 // In-row tasks of the listed vertices (those whose previous-level block changed).
@@ -559,12 +574,53 @@ __global__ void k_settle(const int32_t* __restrict__ FL, int64_t fl, Level L, Wo
     atomicOr(reinterpret_cast<unsigned*>(&counters[1]), 2u);   // index full
 }
 
+// 4b. frontier vertices alone in their block one level down (FX): alone here
+// too. A vertex that was its old block's only member keeps that block (and its
+// index entry, now possibly stale); otherwise it gets a new block without an
+// index entry. Neither can be matched wrongly (every match is an exact
+// compare), and one is never missed: another vertex can share its signature
+// only by joining its block one level down, which puts it back into the
+// frontier (k_assign's recomp flags).
+__global__ void k_settle_single(const int32_t* __restrict__ FX, int64_t fx, Level L, Work W,
+                                int64_t* __restrict__ bnext, int64_t bcap, unsigned long long* __restrict__ counters) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= fx) return;
+    const int32_t v = FX[i];
+    const int32_t o = W.old[v];
+    W.grp[v] = v;
+    if (o >= W.bcap) {
+        atomicOr(W.err, kChkSettle);
+        W.decision[v] = kNew;
+        return;
+    }
+    if (o >= 0 && L.bcnt[o] == 0 && W.cntF[o] == 1u) {
+        W.decision[v] = o;
+        L.bmin[o] = INT_MAX;
+        return;
+    }
+    const long long nb = atomicAdd(reinterpret_cast<unsigned long long*>(bnext), 1ull);
+    if (nb >= bcap) {
+        atomicOr(reinterpret_cast<unsigned*>(&counters[1]), 1u);   // out of block ids: rebuild
+        W.decision[v] = kNew;
+        return;
+    }
+    const int32_t b = static_cast<int32_t>(nb);
+    L.bcnt[b] = 0;
+    L.bkey[b] = 0ull;                                      // no index entry
+    L.bmin[b] = INT_MAX;
+    W.decision[v] = b;
+}
+
 // 5. frontier vertices take their blocks
 // Vertices whose block changed are flagged in W.changed and listed in `clist`
 // (for the next level's in-neighbour search).
+// A vertex that joins a block whose only member u was alone one level down
+// (so u's next-level block may have no current index key) flags u in
+// W.recomp for the next level (stale_next: that level's stale flags, null at
+// the last level).
 __global__ void k_assign(const int32_t* __restrict__ F, int64_t f, const uint8_t* __restrict__ alive, Level L,
                          Work W, const int32_t* __restrict__ cnt_now, int level, int32_t* __restrict__ clist,
-                         unsigned long long* __restrict__ ccount) {
+                         unsigned long long* __restrict__ ccount, const uint8_t* __restrict__ stale_next) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= f) return;
     const int32_t v = F[i];
@@ -582,8 +638,9 @@ __global__ void k_assign(const int32_t* __restrict__ F, int64_t f, const uint8_t
         }
         L.lid[v] = b;
         atomicAdd(&L.bcnt[b], 1);
-        atomicMin(&L.bmin[b], v);
-        if (level > 0) L.lcnt[v] = cnt_now[v];
+        const int32_t before = atomicMin(&L.bmin[b], v);
+        if (stale_next && b != o && before != INT_MAX && before != v && stale_next[before]) W.recomp[before] = 1;
+        if (level > 0 && !L.stale[v]) L.lcnt[v] = cnt_now[v];
         W.changed[v] = b != o;
         if (b != o) clist[atomicAdd(ccount, 1ull)] = v;
     } else {
@@ -643,7 +700,8 @@ __global__ void k_output(int32_t n, const uint8_t* __restrict__ alive, const int
 // ----------------------------------------------------------------------------- host side
 
 Level level_view(const bisim_ctx* ctx, int j) {
-    return Level{ctx->lid[j], ctx->lcnt[j], ctx->bkey[j], ctx->bcnt[j], ctx->bmin[j], ctx->ikey[j], ctx->ibid[j],
+    return Level{ctx->lstale[j], ctx->lid[j], ctx->lcnt[j], ctx->bkey[j], ctx->bcnt[j], ctx->bmin[j], ctx->ikey[j],
+                 ctx->ibid[j],
                  ctx->isize - 1};
 }
 
@@ -653,7 +711,7 @@ constexpr int64_t kThreadClassOps = 20000;   // batches above this use thread-pe
 // Host copies of everything a level pass reads back, in pinned memory so that
 // the copies queue behind the level's kernels and one synchronisation covers them.
 struct HostStage {
-    unsigned long long counters[8];
+    unsigned long long counters[16];
     int64_t begin[kNumClasses + 1];
     unsigned long long edges[kNumClasses];
     unsigned n_hubs;
@@ -681,6 +739,7 @@ struct Scratch {
     unsigned long long* chcount = nullptr;
     TierLists tiers{};                 // in-row tasks, [n] per tier
     HostStage* h = nullptr;            // pinned
+    int32_t* FX = nullptr;             // [n] live frontier vertices alone in their block one level down
 };
 
 cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
@@ -691,7 +750,7 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     auto need = [&](size_t b) { bytes += (b + 255) & ~size_t(255); };
     need(4 * n); need(4 * n); need(8 * n); need(4 * n); need(4 * n); need(4 * n); need(4 * n); need(8 * n);
     need(4 * bc); need(4 * bc); need(4 * bc); need(4 * bc); need(4 * bc);
-    need(4 * n); need(4 * n); need(8 * 8); need(4 * n); need(4 * n); need(n); need(n); need(n);
+    need(4 * n); need(4 * n); need(8 * 16); need(4 * n); need(4 * n); need(n); need(n); need(n); need(n); need(4 * n);
     need(8 * L); need(32 * L); need(32);
     need(4 * n); need(8 * (kNumClasses + 1)); need(8 * kNumClasses); need(8 * kNumClasses); need(8 * kNumClasses);
     need(sizeof(HubInfo) * std::max<size_t>(n, kHubPrefetch)); need(16);
@@ -721,12 +780,14 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     W.dlist = reinterpret_cast<int32_t*>(carve(4 * bc));
     W.cand = reinterpret_cast<int32_t*>(carve(4 * n));
     W.candb = reinterpret_cast<int32_t*>(carve(4 * n));
-    W.counters = reinterpret_cast<unsigned long long*>(carve(8 * 8));
+    W.counters = reinterpret_cast<unsigned long long*>(carve(8 * 16));
     W.F = reinterpret_cast<int32_t*>(carve(4 * n));
     W.FL = reinterpret_cast<int32_t*>(carve(4 * n));
     W.inF = reinterpret_cast<uint8_t*>(carve(n));
     W.changed = reinterpret_cast<uint8_t*>(carve(n));
     W.next = reinterpret_cast<uint8_t*>(carve(n));
+    W.recomp = reinterpret_cast<uint8_t*>(carve(n));
+    S.FX = reinterpret_cast<int32_t*>(carve(4 * n));
     S.dbnext = reinterpret_cast<int64_t*>(carve(8 * L));
     S.dacc = reinterpret_cast<unsigned long long*>(carve(32 * L));
     W.err = reinterpret_cast<unsigned*>(carve(32));
@@ -752,6 +813,7 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     cudaMemsetAsync(W.dirty, 0, 4 * bc, s);
     cudaMemsetAsync(W.changed, 0, n, s);
     cudaMemsetAsync(W.inF, 0, n, s);                       // pool memory is recycled: start clean
+    cudaMemsetAsync(W.recomp, 0, n, s);
     return cudaSuccess;
 }
 
@@ -866,15 +928,18 @@ bisim_status ensure_skey(bisim_ctx* ctx, cudaStream_t s) {
     return BISIM_OK;
 }
 
-// Frontier lists from the flags a | b | c (every vertex when a is null): F
-// (live or dead) and its live part FL; their sizes stay on the device
-// (W.counters[6], [7]).
-void launch_frontier(bisim_ctx* ctx, Scratch& S, const uint8_t* a, const uint8_t* b, const uint8_t* c,
-                     cudaStream_t s) {
+// Frontier lists from the flags a | b | c | d (every vertex when a is null):
+// F (live or dead), its live part split into FL and FX (see k_frontier);
+// their sizes stay on the device (W.counters[6], [7], [8]).
+void launch_frontier(bisim_ctx* ctx, Scratch& S, int j, const uint8_t* a, const uint8_t* b, const uint8_t* c,
+                     const uint8_t* d, cudaStream_t s) {
     Work& W = S.W;
     const int32_t n = ctx->n;
-    cudaMemsetAsync(&W.counters[6], 0, 16, s);
-    if (n > 0) k_frontier<<<grid_for(n, 256), 256, 0, s>>>(a, b, c, ctx->alive, n, W.F, W.FL, &W.counters[6]);
+    cudaMemsetAsync(&W.counters[6], 0, 24, s);
+    if (n > 0)
+        k_frontier<<<grid_for(n, 256), 256, 0, s>>>(a, b, c, d, ctx->alive, n, j > 0 ? ctx->lid[j - 1] : nullptr,
+                                                    j > 0 ? ctx->bcnt[j - 1] : nullptr, ctx->lstale[j], W.F, W.FL,
+                                                    S.FX, &W.counters[6]);
 }
 
 // One level over the frontier launch_frontier made. Host round trips: one
@@ -902,7 +967,14 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t* frontier, cu
     const int64_t ntouched = static_cast<int64_t>(S.h->counters[0]);
     const int64_t f = static_cast<int64_t>(S.h->counters[6]);
     const int64_t fl = static_cast<int64_t>(S.h->counters[7]);
-    *frontier = fl;
+    const int64_t fx = static_cast<int64_t>(S.h->counters[8]);
+    *frontier = fl + fx;
+    unsigned long long* acc = S.dacc + 4 * j;
+    if (fx > 0) {
+        // alone one level down: no signature, see k_settle_single
+        Launch Lk(site, s, fx, 0, 16.0 * fx);
+        k_settle_single<<<grid_for(fx, 256), 256, 0, s>>>(S.FX, fx, L, W, S.dbnext + j, ctx->bcap, acc);
+    }
     // 2. exact groups within the live frontier
     ListBuckets LB;
     if (fl > 0) {
@@ -970,14 +1042,14 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t* frontier, cu
     }
     if (LB.hubmem) cudaFreeAsync(LB.hubmem, s);
     // 4. keep or create ids; 5. assign; retire empty blocks
-    unsigned long long* acc = S.dacc + 4 * j;
     if (fl > 0) {
         Launch Lk(site, s, fl, 0, 24.0 * fl);
         k_settle<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, L, W, S.dbnext + j, ctx->bcap, acc);
     }
     if (f > 0) {
         Launch Lk(site, s, f, 0, 24.0 * f);
-        k_assign<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, ctx->alive, L, W, ctx->cnt, j, S.clist, S.chcount);
+        k_assign<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, ctx->alive, L, W, ctx->cnt, j, S.clist, S.chcount,
+                                                 j < ctx->inc_k ? ctx->lstale[j + 1] : nullptr);
         k_set_flags<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, W.inF, 0);
     }
     if (ntouched > 0) {
@@ -1059,6 +1131,8 @@ void inc_release(bisim_ctx* ctx, cudaStream_t s) {
         ctx_free(ctx, ctx->bmin[j], 4 * static_cast<size_t>(ctx->bcap), s);
         ctx_free(ctx, ctx->ikey[j], 8 * ctx->isize, s);
         ctx_free(ctx, ctx->ibid[j], 4 * ctx->isize, s);
+        ctx_free(ctx, ctx->lstale[j], n, s);
+        ctx->lstale[j] = nullptr;
         ctx->lid[j] = ctx->lcnt[j] = ctx->bcnt[j] = ctx->bmin[j] = ctx->ibid[j] = nullptr;
         ctx->bkey[j] = ctx->ikey[j] = nullptr;
         ctx->bnext[j] = ctx->itomb[j] = 0;
@@ -1090,8 +1164,10 @@ bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s) {
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bcnt[j]), 4 * static_cast<size_t>(ctx->bcap), s)) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bmin[j]), 4 * static_cast<size_t>(ctx->bcap), s)) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ikey[j]), 8 * is, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ibid[j]), 4 * is, s)))
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ibid[j]), 4 * is, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->lstale[j]), n, s)))
             return cuda_error(ctx, e, "alloc incremental state");
+        cudaMemsetAsync(ctx->lstale[j], 0, n, s);
         cudaMemsetAsync(ctx->lid[j], 0xff, 4 * n, s);        // -1: no block yet
         cudaMemsetAsync(ctx->lcnt[j], 0, 4 * n, s);
         cudaMemsetAsync(ctx->bcnt[j], 0, 4 * static_cast<size_t>(ctx->bcap), s);
@@ -1109,9 +1185,10 @@ bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s) {
     int64_t fl = 0;
     st = BISIM_OK;
     for (int j = 0; st == BISIM_OK && j <= K; ++j) {
-        launch_frontier(ctx, S, nullptr, nullptr, nullptr, s);
+        launch_frontier(ctx, S, j, nullptr, nullptr, nullptr, nullptr, s);
         cudaMemsetAsync(S.chcount, 0, 8, s);          // k_assign lists changed vertices (at most n)
         st = level_pass(ctx, j, S, &fl, s);
+        cudaMemsetAsync(S.W.recomp, 0, static_cast<size_t>(std::max(ctx->n, 1)), s);   // every vertex was in F
     }
     bool rebuild = false;
     if (st == BISIM_OK) st = inc_finish(ctx, S, &rebuild, s);
@@ -1155,9 +1232,10 @@ bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* 
                 k_in_row_tasks<<<kTierGrid, kTierThreads, 0, s>>>(S.clist, S.chcount, ctx->yro, ctx->ylen, S.tiers);
                 run_tiers(S.tiers, MarkSources{ctx->ype, W.next}, s);
             }
-            launch_frontier(ctx, S, W.next, W.changed, rowchg, s);
+            launch_frontier(ctx, S, j, W.next, W.changed, rowchg, W.recomp, s);
+            cudaMemsetAsync(W.recomp, 0, n, s);       // this level's assign flags the next level's
         } else {
-            launch_frontier(ctx, S, vchanged, nullptr, nullptr, s);
+            launch_frontier(ctx, S, j, vchanged, nullptr, nullptr, nullptr, s);
         }
         cudaMemsetAsync(W.changed, 0, n, s);
         cudaMemsetAsync(S.chcount, 0, 8, s);          // the level lists its changed vertices
