@@ -288,3 +288,31 @@ def test_revived_vertices_do_not_keep_old_in_edges(B):
         B.apply_updates(ctx, _dev(ops))
         check_partition(B, ctx, state, 3)
     B.summarize_destroy(ctx)
+
+
+def test_vertex_joining_a_singleton_block_one_level_down(B):
+    """Vertices alone in their block one level down are not re-hashed; when another
+    vertex later joins that block, the singleton must be compared again (here u is
+    the only vertex with label 7 until x is relabelled to 7, and both point to w
+    with the same edge label, so they become bisimilar at every level)."""
+    n = 8
+    u, x, w = 0, 1, 2
+    src = np.array([u, x, w, 3, 4, 5], np.int32)
+    dst = np.array([w, w, 3, 4, 5, 6], np.int32)
+    lab = np.array([1, 1, 2, 2, 2, 2], np.int32)
+    vl = np.array([7, 0, 0, 0, 0, 0, 0, 0], np.int32)
+    state = dict(n=n, alive=np.ones(n, np.uint8), vlabel=vl.copy(), src=src, dst=dst, elabel=lab)
+    for k in (1, 2, 3):
+        ctx = B.summarize_init_coo(n, _dev(src), _dev(dst), _dev(lab), _dev(vl),
+                                   options=B.default_options(k_incremental=k))
+        B.apply_updates(ctx, _dev(np.zeros((0, 4), np.int32)))
+        st = state
+        for ops in ([[2, x, 0, 7]],                    # x joins u's label block
+                    [[2, x, 0, 0]],                    # and leaves it again
+                    [[2, 7, 0, 7], [0, 7, w, 1]],      # a third vertex with u's label and row
+                    [[1, u, w, 1], [0, u, 3, 1]]):     # u's row changes
+            ops = np.array(ops, np.int32)
+            st = oracle.apply_ops(st, ops)
+            B.apply_updates(ctx, _dev(ops))
+            check_partition(B, ctx, st, k)
+        B.summarize_destroy(ctx)
