@@ -508,15 +508,18 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
         if ((e = stage(ops, sizeof(bisim_op) * static_cast<size_t>(n_ops), s, &d_ops, temps)))
             return cuda_error(ctx, e, "stage update batch");
         uint8_t* flags = nullptr;
-        const size_t fb = 3 * static_cast<size_t>(ctx->n + 1);
+        // three flag arrays of n + 1 bytes, each starting on a 256-byte boundary
+        // (the frontier kernels read them 16 bytes at a time)
+        const size_t fs = (static_cast<size_t>(ctx->n + 1) + 255) & ~size_t(255);
+        const size_t fb = 3 * fs;
         if ((e = cudaMallocAsync(reinterpret_cast<void**>(&flags), fb, s))) {
             free_temps(temps, s);
             return cuda_error(ctx, e, "alloc update flags");
         }
         cudaMemsetAsync(flags, 0, fb, s);
         uint8_t* vchanged = flags;
-        uint8_t* rowchg = flags + (ctx->n + 1);
-        uint8_t* killed = flags + 2 * (ctx->n + 1);
+        uint8_t* rowchg = flags + fs;
+        uint8_t* killed = flags + 2 * fs;
         const bisim_op* dops = static_cast<const bisim_op*>(d_ops);
         st = incremental ? apply_ops_to_store(ctx, dops, n_ops, vchanged, rowchg, killed, s)
                          : apply_ops_to_graph(ctx, dops, n_ops, vchanged, rowchg, killed, s);

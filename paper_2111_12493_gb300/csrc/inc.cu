@@ -111,32 +111,96 @@ __device__ __forceinline__ void warp_list_push(bool f, int32_t v, int32_t* out, 
     if (f) out[base + __popc(ball & ((1u << lane_id()) - 1u))] = v;
 }
 
+// 16 flag bytes starting at v (a multiple of 16) as a 16-bit mask; null
+// flags nothing, a misaligned array is read byte by byte.
+__device__ __forceinline__ uint32_t flag_mask16(const uint8_t* f, int64_t v) {
+    if (f == nullptr) return 0u;
+    uint32_t m = 0u;
+    if ((reinterpret_cast<uintptr_t>(f + v) & 15u) == 0u) {
+        const uint4 w = *reinterpret_cast<const uint4*>(f + v);
+        const uint32_t q[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if ((q[k >> 2] >> (8 * (k & 3))) & 0xffu) m |= 1u << k;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (f[v + k]) m |= 1u << k;
+    }
+    return m;
+}
+
+// Appends the positions v0 + k for the set bits k of `mask` to out, one atomic per warp.
+__device__ __forceinline__ void warp_push_mask(uint32_t mask, int64_t v0, int32_t* out,
+                                               unsigned long long* count) {
+    const unsigned lane = lane_id();
+    const unsigned mine = static_cast<unsigned>(__popc(mask));
+    unsigned inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= static_cast<unsigned>(o)) inc += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, inc, 31);
+    if (total == 0u) return;
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(count, static_cast<unsigned long long>(total));
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned long long at = base + inc - mine;
+    while (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        out[at++] = static_cast<int32_t>(v0 + k);
+    }
+}
+
 // The level's frontier in one pass: F = vertices with any of the flags a, b,
 // c, d set (a null `a` flags every vertex), split by liveness and, from level
 // 1 on, by the size of the vertex's block one level down: a vertex alone in
 // its level-(j-1) block is alone at level j too (each level refines the last),
 // so it goes to FX and needs no signature; the other live ones go to FL.
-// count: [0] |F|, [1] |FL|, [2] |FX|.
+// count: [0] |F|, [1] |FL|, [2] |FX|. Each thread takes 16 vertices; most
+// have no flag set and cost one 16-byte read per flag array.
 __global__ void k_frontier(const uint8_t* __restrict__ a, const uint8_t* __restrict__ b,
                            const uint8_t* __restrict__ c, const uint8_t* __restrict__ d,
                            const uint8_t* __restrict__ alive, int32_t n, const int32_t* __restrict__ lid_prev,
                            const int32_t* __restrict__ bcnt_prev, uint8_t* __restrict__ stale,
                            int32_t* __restrict__ F, int32_t* __restrict__ FL, int32_t* __restrict__ FX,
                            unsigned long long* __restrict__ count) {
-    const int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    bool f = false, live = false, alone = false;
-    if (v < n) {
-        f = a == nullptr || a[v] || (b && b[v]) || (c && c[v]) || (d && d[v]);
-        live = f && alive[v];
-        if (live && lid_prev) {
-            const int32_t pb = lid_prev[v];
-            alone = pb >= 0 && bcnt_prev[pb] == 1;
-            stale[v] = alone ? 1 : 0;
+    const int64_t v0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * 16;
+    uint32_t mf = 0u, ml = 0u, mx = 0u;
+    if (v0 < n) {
+        const int valid = v0 + 16 <= n ? 16 : static_cast<int>(n - v0);
+        const uint32_t vm = valid == 16 ? 0xffffu : ((1u << valid) - 1u);
+        if (valid == 16) {
+            mf = a == nullptr ? 0xffffu : (flag_mask16(a, v0) | flag_mask16(b, v0) | flag_mask16(c, v0) |
+                                           flag_mask16(d, v0));
+        } else {
+            for (int k = 0; k < valid; ++k) {
+                const int64_t v = v0 + k;
+                if (a == nullptr || a[v] || (b && b[v]) || (c && c[v]) || (d && d[v])) mf |= 1u << k;
+            }
+        }
+        mf &= vm;
+        uint32_t m = mf;
+        while (m) {
+            const int k = __ffs(m) - 1;
+            m &= m - 1u;
+            const int64_t v = v0 + k;
+            if (!alive[v]) continue;
+            bool alone = false;
+            if (lid_prev) {
+                const int32_t pb = lid_prev[v];
+                alone = pb >= 0 && bcnt_prev[pb] == 1;
+                stale[v] = alone ? 1 : 0;
+            }
+            if (alone) mx |= 1u << k;
+            else ml |= 1u << k;
         }
     }
-    warp_list_push(f, static_cast<int32_t>(v), F, &count[0]);
-    warp_list_push(live && !alone, static_cast<int32_t>(v), FL, &count[1]);
-    warp_list_push(alone, static_cast<int32_t>(v), FX, &count[2]);
+    warp_push_mask(mf, v0, F, &count[0]);
+    warp_push_mask(ml, v0, FL, &count[1]);
+    warp_push_mask(mx, v0, FX, &count[2]);
 }
 
 // In-row tasks of the listed vertices (those whose previous-level block changed).
@@ -304,13 +368,48 @@ __global__ void k_dirty_reset(const int32_t* __restrict__ dlist, Level L, Work W
 
 // smallest remaining member of every block whose minimum left (nothing to do
 // when no minimum left)
-__global__ void k_rescan(int32_t n, const uint8_t* __restrict__ alive, Level L, Work W) {
-    if (dev_count(&W.counters[1]) == 0) return;
+// The dirty blocks (usually a few hundred) are first loaded into a
+// shared-memory set, so the pass over all vertices reads only lid, alive and
+// inF and looks blocks up on chip; with more dirty blocks than the set holds
+// it reads W.dirty instead.
+constexpr int kRescanSlots = 4096;
+__global__ void __launch_bounds__(256) k_rescan(int32_t n, const uint8_t* __restrict__ alive, Level L, Work W) {
+    __shared__ int32_t set[kRescanSlots];
+    const int64_t nd = dev_count(&W.counters[1]);
+    if (nd == 0) return;
+    const bool on_chip = nd <= kRescanSlots / 2;
+    if (on_chip) {
+        for (int k = threadIdx.x; k < kRescanSlots; k += blockDim.x) set[k] = -1;
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < nd; i += blockDim.x) {
+            const int32_t b = W.dlist[i];
+            uint32_t pos = static_cast<uint32_t>(mix64(static_cast<uint64_t>(b))) & (kRescanSlots - 1);
+            for (int probe = 0; probe < kRescanSlots; ++probe) {
+                const int32_t prev = atomicCAS(&set[pos], -1, b);
+                if (prev == -1 || prev == b) break;
+                pos = (pos + 1) & (kRescanSlots - 1);
+            }
+        }
+        __syncthreads();
+    }
     for (int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; u < n;
          u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        if (!alive[u] || W.inF[u]) continue;
         const int32_t b = L.lid[u];
-        if (b >= 0 && W.dirty[b]) atomicMin(&L.bmin[b], static_cast<int32_t>(u));
+        if (b < 0 || !alive[u] || W.inF[u]) continue;
+        bool dirty;
+        if (on_chip) {
+            dirty = false;
+            uint32_t pos = static_cast<uint32_t>(mix64(static_cast<uint64_t>(b))) & (kRescanSlots - 1);
+            for (int probe = 0; probe < kRescanSlots; ++probe) {
+                const int32_t cur = set[pos];
+                if (cur == b) { dirty = true; break; }
+                if (cur == -1) break;
+                pos = (pos + 1) & (kRescanSlots - 1);
+            }
+        } else {
+            dirty = W.dirty[b] != 0u;
+        }
+        if (dirty) atomicMin(&L.bmin[b], static_cast<int32_t>(u));
     }
 }
 
@@ -937,7 +1036,7 @@ void launch_frontier(bisim_ctx* ctx, Scratch& S, int j, const uint8_t* a, const 
     const int32_t n = ctx->n;
     cudaMemsetAsync(&W.counters[6], 0, 24, s);
     if (n > 0)
-        k_frontier<<<grid_for(n, 256), 256, 0, s>>>(a, b, c, d, ctx->alive, n, j > 0 ? ctx->lid[j - 1] : nullptr,
+        k_frontier<<<grid_for(cdiv(n, 16), 256), 256, 0, s>>>(a, b, c, d, ctx->alive, n, j > 0 ? ctx->lid[j - 1] : nullptr,
                                                     j > 0 ? ctx->bcnt[j - 1] : nullptr, ctx->lstale[j], W.F, W.FL,
                                                     S.FX, &W.counters[6]);
 }
