@@ -316,3 +316,29 @@ def test_vertex_joining_a_singleton_block_one_level_down(B):
             B.apply_updates(ctx, _dev(ops))
             check_partition(B, ctx, st, k)
         B.summarize_destroy(ctx)
+
+
+@pytest.mark.parametrize("n", [1, 2, 17])
+def test_updates_from_an_empty_edge_set(B, n):
+    """Graphs that start without edges (rows of capacity two), grow by batches
+    that fill and move rows, and lose vertices again: every result exact."""
+    rng = np.random.default_rng(300 + n)
+    vl = (np.arange(n) % 2).astype(np.int32)
+    empty = np.zeros(0, np.int32)
+    state = dict(n=n, alive=np.ones(n, np.uint8), vlabel=vl.copy(), src=empty, dst=empty, elabel=empty)
+    ctx = B.summarize_init_coo(n, _dev(empty), _dev(empty), _dev(empty), _dev(vl),
+                               options=B.default_options(k_incremental=2))
+    B.apply_updates(ctx, _dev(np.zeros((0, 4), np.int32)))
+    check_partition(B, ctx, state, 2)
+    for step in range(6):
+        size = int(rng.integers(1, 40))
+        ops = np.stack([np.zeros(size), rng.integers(0, n, size), rng.integers(0, n, size),
+                        rng.integers(0, 3, size)], axis=1).astype(np.int32)
+        if step == 4 and n > 1:
+            ops = np.concatenate([ops, np.array([[3, n - 1, 0, 0]], np.int32)])
+        if step == 5 and n > 1:
+            ops = np.array([[2, n - 1, 0, 1], [0, n - 1, 0, 2], [0, 0, n - 1, 2]], np.int32)
+        state = oracle.apply_ops(state, ops)
+        B.apply_updates(ctx, _dev(ops))
+        check_partition(B, ctx, state, 2)
+    B.summarize_destroy(ctx)
