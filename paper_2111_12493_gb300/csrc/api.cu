@@ -246,7 +246,6 @@ bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s) {
             return cuda_error(ctx, e, "grow signature lists");
         ctx->skey_cap = cap;
     }
-    ctx->buckets_ready = false;   // rebuilt by the list-mode path when it next needs them
     if ((st = compute_p0(ctx, s)) != BISIM_OK) return st;
     ctx->buckets_dirty = false;
     ctx->stats.device_bytes = ctx->device_bytes;

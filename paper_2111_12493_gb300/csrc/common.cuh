@@ -339,8 +339,7 @@ struct bisim_ctx {
     int32_t* esrc = nullptr;       // source vertex of every CSR edge (kept once updates start)
     int64_t esrc_cap = 0;
     int64_t skey_cap = 0;          // capacity of skey in values
-    bool buckets_dirty = false;    // the label partition and buckets no longer match the CSR
-    bool buckets_ready = false;    // degree buckets of the list-mode path are built
+    bool buckets_dirty = false;    // the label partition no longer matches the graph
     int32_t cur_k = 0;             // rounds of the current partition
 
     // dynamic adjacency of the incremental path (built with its state): out-rows
@@ -421,10 +420,7 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
                             const int32_t* elab, cudaStream_t s);
 bisim_status build_from_csr(bisim_ctx* ctx, const int64_t* row_ptr, const int32_t* col,
                             const int32_t* elab, cudaStream_t s);
-bisim_status build_buckets(bisim_ctx* ctx, cudaStream_t s);
-// Builds the degree buckets of the list-mode (incremental) path on first use
-// after the graph changed.
-bisim_status ensure_buckets(bisim_ctx* ctx, cudaStream_t s);
+
 
 // ----------------------------------------------------------------------------- dynamic adjacency (store.cu)
 
@@ -449,8 +445,6 @@ bisim_status signature_round(bisim_ctx* ctx, const Buckets& B, const int32_t* Pi
                              const int32_t* vlist, int64_t vcount, unsigned long long* hout, cudaStream_t s,
                              int64_t* out_blocks);
 Buckets ctx_buckets(const bisim_ctx* ctx);
-// Groups the listed vertices by label: Pout[v] = smallest listed vertex with v's label.
-bisim_status label_group(bisim_ctx* ctx, const int32_t* vlist, int64_t vcount, int32_t* Pout, cudaStream_t s);
 bisim_status alloc_refine_state(bisim_ctx* ctx, cudaStream_t s);
 void pin_partition_in_l2(bisim_ctx* ctx, const int32_t* P, cudaStream_t s);
 void unpin_partition(bisim_ctx* ctx, cudaStream_t s);

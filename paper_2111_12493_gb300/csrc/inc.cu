@@ -774,6 +774,67 @@ __global__ void k_retire(const int32_t* __restrict__ tlist, int64_t nt, Level L,
     }
 }
 
+// Level 0 groups the live frontier by vertex label. A label is a 32-bit key,
+// so an open-addressing table that stores the label itself groups exactly in
+// one pass (no fingerprint to verify, no host round trip): a slot holds
+// (label << 32 | smallest vertex), ~0 when empty.
+__global__ void k_label_insert(const int32_t* __restrict__ FL, int64_t fl, const int32_t* __restrict__ vlabel,
+                               unsigned long long* __restrict__ tab, uint64_t mask, unsigned* err) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < fl;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t v = FL[i];
+        const uint64_t key = static_cast<uint32_t>(vlabel[v]);
+        const unsigned long long want = (key << 32) | static_cast<uint32_t>(v);
+        uint64_t pos = mix64(key) & mask;
+        bool placed = false;
+        for (uint64_t probe = 0; probe <= mask && !placed; ++probe) {
+            unsigned long long cur = tab[pos];
+            if (cur == ~0ull) {
+                const unsigned long long prev = atomicCAS(&tab[pos], ~0ull, want);
+                if (prev == ~0ull) {
+                    placed = true;
+                    break;
+                }
+                cur = prev;
+            }
+            if ((cur >> 32) == key) {
+                while (static_cast<uint32_t>(v) < static_cast<uint32_t>(cur)) {
+                    const unsigned long long prev = atomicCAS(&tab[pos], cur, want);
+                    if (prev == cur) break;
+                    cur = prev;
+                }
+                placed = true;
+                break;
+            }
+            pos = (pos + 1) & mask;
+        }
+        if (!placed) atomicOr(err, kChkGroup);
+    }
+}
+
+__global__ void k_label_read(const int32_t* __restrict__ FL, int64_t fl, const int32_t* __restrict__ vlabel,
+                             const unsigned long long* __restrict__ tab, uint64_t mask, int32_t* __restrict__ grp,
+                             unsigned* err) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < fl;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t v = FL[i];
+        const uint64_t key = static_cast<uint32_t>(vlabel[v]);
+        uint64_t pos = mix64(key) & mask;
+        int32_t g = -1;
+        for (uint64_t probe = 0; probe <= mask; ++probe) {
+            const unsigned long long cur = tab[pos];
+            if (cur == ~0ull) break;
+            if ((cur >> 32) == key) {
+                g = static_cast<int32_t>(static_cast<uint32_t>(cur));
+                break;
+            }
+            pos = (pos + 1) & mask;
+        }
+        if (g < 0) atomicOr(err, kChkGroup);
+        grp[v] = g;
+    }
+}
+
 __global__ void k_label_keys(const int32_t* __restrict__ FL, int64_t fl, const int32_t* __restrict__ vlabel,
                              unsigned long long* __restrict__ h, uint64_t hmask) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -839,6 +900,7 @@ struct Scratch {
     TierLists tiers{};                 // in-row tasks, [n] per tier
     HostStage* h = nullptr;            // pinned
     int32_t* FX = nullptr;             // [n] live frontier vertices alone in their block one level down
+    unsigned long long* ltab = nullptr;   // level-0 label table, a power of two >= 2n slots
 };
 
 cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
@@ -850,6 +912,9 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     need(4 * n); need(4 * n); need(8 * n); need(4 * n); need(4 * n); need(4 * n); need(4 * n); need(8 * n);
     need(4 * bc); need(4 * bc); need(4 * bc); need(4 * bc); need(4 * bc);
     need(4 * n); need(4 * n); need(8 * 16); need(4 * n); need(4 * n); need(n); need(n); need(n); need(n); need(4 * n);
+    size_t lslots = 64;
+    while (lslots < 2 * n) lslots <<= 1;
+    need(8 * lslots);
     need(8 * L); need(32 * L); need(32);
     need(4 * n); need(8 * (kNumClasses + 1)); need(8 * kNumClasses); need(8 * kNumClasses); need(8 * kNumClasses);
     need(sizeof(HubInfo) * std::max<size_t>(n, kHubPrefetch)); need(16);
@@ -887,6 +952,7 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     W.next = reinterpret_cast<uint8_t*>(carve(n));
     W.recomp = reinterpret_cast<uint8_t*>(carve(n));
     S.FX = reinterpret_cast<int32_t*>(carve(4 * n));
+    S.ltab = reinterpret_cast<unsigned long long*>(carve(8 * lslots));
     S.dbnext = reinterpret_cast<int64_t*>(carve(8 * L));
     S.dacc = reinterpret_cast<unsigned long long*>(carve(32 * L));
     W.err = reinterpret_cast<unsigned*>(carve(32));
@@ -1078,8 +1144,12 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t* frontier, cu
     ListBuckets LB;
     if (fl > 0) {
         if (j == 0) {
-            if ((st = label_group(ctx, W.FL, fl, W.grp, s)) != BISIM_OK) return st;
-            Launch Lk(site, s, fl, 0, 12.0 * fl);
+            uint64_t slots = 64;
+            while (slots < 2 * static_cast<uint64_t>(fl)) slots <<= 1;
+            Launch Lk(site, s, fl, 0, 40.0 * fl);
+            cudaMemsetAsync(S.ltab, 0xff, sizeof(unsigned long long) * slots, s);
+            k_label_insert<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, ctx->vlabel, S.ltab, slots - 1, W.err);
+            k_label_read<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, ctx->vlabel, S.ltab, slots - 1, W.grp, W.err);
             k_label_keys<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, ctx->vlabel, W.h,
                                                           ctx->opt.hash_bits >= 64 ? ~0ull : ((1ull << ctx->opt.hash_bits) - 1));
         } else {

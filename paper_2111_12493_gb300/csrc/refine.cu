@@ -834,19 +834,6 @@ bisim_status signature_round(bisim_ctx* ctx, const Buckets& B, const int32_t* Pi
     return resolve(ctx, M, Pout, vlist, vcount, s, out_blocks);
 }
 
-bisim_status label_group(bisim_ctx* ctx, const int32_t* vlist, int64_t vcount, int32_t* Pout, cudaStream_t s) {
-    TableRef t = next_epoch(ctx, s);
-    LabelMode M{ctx->vlabel, ctx->gid};
-    if (vcount > 0) {
-        BISIM_SITE(site, "label_insert");
-        Launch L(site, s, vcount, 0, 20.0 * vcount);
-        k_resolve_insert<LabelMode><<<grid_for(vcount, 256), 256, 0, s>>>(vlist, vcount, ctx->alive, M, 0u, ctx->slot,
-                                                                          t, &ctx->dstate->error);
-    }
-    int64_t blocks = 0;
-    return resolve(ctx, M, Pout, vlist, vcount, s, &blocks);
-}
-
 bisim_status refine_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     const int32_t* P = ctx->P[ctx->cur];
     pin_partition_in_l2(ctx, P, s);

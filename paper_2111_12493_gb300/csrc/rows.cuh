@@ -4,7 +4,7 @@
 // GPU:
 //   warp tier  len <= kWarpTierMax   one warp per task
 //   CTA tier   len <= kCtaTierMax    one CTA per task, its warps striding the row
-//   grid tier  longer                every warp of the grid strides the row
+//   grid tier  longer                the row's 32-entry chunks go round-robin to every warp
 // The consumer is a persistent grid that reads the task counts on the device,
 // so filing and consuming need no host round trip. The per-entry work is a
 // functor called by whole warps (`in` is false past the row's end), so it may
@@ -58,7 +58,7 @@ __device__ __forceinline__ void tier_push(const TierLists& L, bool has, const Ro
 // all warps together. Tasks are independent, so no grid-wide barrier is needed
 // between the phases.
 template <class F>
-__global__ void __launch_bounds__(kTierThreads) k_tiers(const TierLists L, F f) {
+__global__ void __launch_bounds__(kTierThreads) k_tiers(const TierLists L, F f, bool grid_tier) {
     const int lane = static_cast<int>(threadIdx.x & 31u);
     const int warp = static_cast<int>(threadIdx.x >> 5);
     const unsigned warps = gridDim.x * (kTierThreads / 32);
@@ -73,18 +73,25 @@ __global__ void __launch_bounds__(kTierThreads) k_tiers(const TierLists L, F f) 
         const RowTask t = L.t[1][i];
         for (int32_t j0 = warp * 32; j0 < t.len; j0 += kTierThreads) f(t, t.off + j0 + lane, j0 + lane < t.len);
     }
-    const unsigned c2 = *reinterpret_cast<volatile unsigned*>(&L.cnt[2]);
-    const int64_t step = static_cast<int64_t>(warps) * 32;
+    // grid tier: the rows' 32-entry chunks are dealt round-robin to the warps
+    // across all rows, so every warp stays busy whatever the row lengths
+    const unsigned c2 = grid_tier ? *reinterpret_cast<volatile unsigned*>(&L.cnt[2]) : 0u;
+    int64_t first = 0;                              // global index of the row's first chunk
     for (unsigned i = 0; i < c2; ++i) {
         const RowTask t = L.t[2][i];
-        for (int64_t j0 = static_cast<int64_t>(gw) * 32; j0 < t.len; j0 += step) f(t, t.off + j0 + lane, j0 + lane < t.len);
+        const int64_t nch = (static_cast<int64_t>(t.len) + 31) / 32;
+        int64_t k = (static_cast<int64_t>(gw) - first) % static_cast<int64_t>(warps);
+        if (k < 0) k += warps;
+        for (; k < nch; k += warps) f(t, t.off + k * 32 + lane, k * 32 + lane < t.len);
+        first += nch;
     }
 }
 
-// Runs every task filed in `L` (the functor sees each filed entry exactly once).
+// Runs every task filed in `L` (the functor sees each filed entry exactly
+// once); with grid_tier false the caller handles the grid tier itself.
 template <class F>
-void run_tiers(const TierLists& L, const F& f, cudaStream_t s) {
-    k_tiers<F><<<kTierGrid, kTierThreads, 0, s>>>(L, f);
+void run_tiers(const TierLists& L, const F& f, cudaStream_t s, bool grid_tier = true) {
+    k_tiers<F><<<kTierGrid, kTierThreads, 0, s>>>(L, f, grid_tier);
 }
 
 // ----------------------------------------------------------------------------- dynamic adjacency

@@ -86,10 +86,9 @@ extern "C" bisim_status bisim_autotune(bisim_ctx* ctx, int32_t rounds, bisim_opt
             }
             *set.field = best;
         }
-        // the next bisim_iterate builds the layout with the chosen settings;
-        // the list-mode buckets follow them too
+        // the next bisim_iterate builds the layout with the chosen settings (the
+        // incremental path buckets its frontiers with them on every batch)
         ctx->dense_ready = false;
-        ctx->buckets_ready = false;
     }
     if (out) *out = ctx->opt;
     return BISIM_OK;

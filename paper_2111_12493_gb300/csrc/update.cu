@@ -484,6 +484,41 @@ struct KeyRemoveRows {
     }
 };
 
+// KeyRemoveRows for the grid tier (rows longer than kCtaTierMax, the hubs).
+// The rows are cut into chunks of kLongChunk entries dealt round-robin to the
+// CTAs across all rows (so every CTA stays busy whatever the row lengths), and
+// every thread loads its kLongRun consecutive entries before it looks at any.
+constexpr int kLongRun = 8;
+constexpr int64_t kLongChunk = static_cast<int64_t>(kTierThreads) * kLongRun;
+__global__ void __launch_bounds__(kTierThreads) k_remove_long(const TierLists L, unsigned long long* __restrict__ xpe,
+                                                              const uint32_t* __restrict__ dmark, KeyTable T) {
+    const unsigned c2 = *reinterpret_cast<volatile unsigned*>(&L.cnt[2]);
+    const int64_t G = gridDim.x;
+    int64_t first = 0;                               // global index of the row's first chunk
+    for (unsigned i = 0; i < c2; ++i) {
+        const RowTask t = L.t[2][i];
+        const int64_t nch = (t.len + kLongChunk - 1) / kLongChunk;
+        int64_t k = (static_cast<int64_t>(blockIdx.x) - first) % G;
+        if (k < 0) k += G;
+        for (; k < nch; k += G) {
+            const int64_t j0 = k * kLongChunk + static_cast<int64_t>(threadIdx.x) * kLongRun;
+            unsigned long long x[kLongRun];
+#pragma unroll
+            for (int q = 0; q < kLongRun; ++q) x[q] = j0 + q < t.len ? xpe[t.off + j0 + q] : kRowTomb;
+#pragma unroll
+            for (int q = 0; q < kLongRun; ++q) {
+                if (x[q] == kRowTomb) continue;
+                const int32_t w = static_cast<int32_t>(static_cast<uint32_t>(x[q]));
+                if (!dmarked(dmark, w)) continue;
+                const int64_t key = key_find(T, t.arg, w, static_cast<int32_t>(x[q] >> 32));
+                if (key >= 0 && T.rem[key] > 0 && atomicAdd(&T.taken[key], 1) < T.rem[key])
+                    xpe[t.off + j0 + q] = kRowTomb;
+            }
+        }
+        first += nch;
+    }
+}
+
 // In-row tasks of every vertex deleted or brought back by the batch (the last
 // operation of each named vertex files it). With `need` set, only adds the
 // in-row lengths of the revived vertices there.
@@ -1047,7 +1082,8 @@ bisim_status apply_ops_to_store(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
     }
     fold_keys(B, killed, rowchg, s);
     if (ne > 0) {
-        run_tiers(LA, KeyRemoveRows{ctx->xpe, ctx->dmark, T}, s);
+        run_tiers(LA, KeyRemoveRows{ctx->xpe, ctx->dmark, T}, s, false);
+        k_remove_long<<<kTierGrid, kTierThreads, 0, s>>>(LA, ctx->xpe, ctx->dmark, T);
         k_clear_dmark<<<grid_for(ne, 256), 256, 0, s>>>(B.keyslot, ne, T, ctx->dmark);
     }
     // deleted and revived vertices
