@@ -521,7 +521,6 @@ struct HubSets {
 };
 
 constexpr uint64_t kSaltBucket = 0x452821e638d01377ull;
-constexpr uint64_t kSaltGraph = 0xbe5466cf34e90c6cull;
 constexpr int kHubMaxBuckets = 2048;            // per hub
 constexpr int kHubBucketTarget = 1024;          // values per bucket aimed at
 constexpr int kHubSetSlots = 4096;              // shared-memory set of a bucket pass (32 KB)
@@ -784,41 +783,25 @@ __global__ void __launch_bounds__(kThreads) k_dense_insert(const int32_t* __rest
                                                            const unsigned* dcount, const DenseView D, uint32_t level,
                                                            const TableRef t, unsigned* err) {
     if (dcount) count = *reinterpret_cast<const volatile unsigned*>(dcount);
-    const unsigned lane = lane_id();
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < count; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        const bool ins = i < count;
-        int64_t pos = -1;
-        int32_t v = -1;
-        uint64_t h = 0, key = 0;
-        if (ins) {
-            pos = list[i];
-            v = D.vert[pos];
-            h = level_hash(D.hash[pos], level, t.hmask);
-            key = D.gid ? h ^ mix64(static_cast<uint64_t>(D.gid[v]) + kSaltGraph) : h;
+    // one thread per position; the insert reads its slot before any atomic, so the
+    // many vertices of a popular signature mostly find a smaller vertex recorded
+    // and leave without one (combining equal hashes within a warp first, with
+    // match_any, was measured twice as slow in round 1)
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const int64_t pos = list[i];
+        const int32_t v = D.vert[pos];
+        const uint64_t h = level_hash(D.hash[pos], level, t.hmask);
+        uint32_t slot;
+        if (D.gid) {
+            // batched graphs: each graph has its own region of the table, so
+            // that the inserts of one graph's vertices stay close together
+            const int32_t g = D.gid[v];
+            slot = table_insert_in(t, h, v, static_cast<uint64_t>(D.rbase[g]), D.rmask[g], err);
+        } else {
+            slot = table_insert(t, h, v, err);
         }
-        const unsigned insm = __ballot_sync(0xffffffffu, ins);
-        // lanes inserting one hash (of one graph) share the slot: only the smallest
-        // vertex among them goes to the table, which keeps popular signatures (big
-        // blocks) from piling atomics onto one slot
-        const unsigned peers = __match_any_sync(0xffffffffu, ins ? key : ~static_cast<uint64_t>(lane)) & insm;
-        if (ins) {
-            const unsigned vmin = __reduce_min_sync(peers, static_cast<unsigned>(v));
-            const int leader = __ffs(__ballot_sync(peers, static_cast<unsigned>(v) == vmin)) - 1;
-            uint32_t slot = 0;
-            if (static_cast<int>(lane) == leader) {
-                if (D.gid) {
-                    // batched graphs: each graph has its own region of the table, so
-                    // that the inserts of one graph's vertices stay close together
-                    const int32_t g = D.gid[v];
-                    slot = table_insert_in(t, h, v, static_cast<uint64_t>(D.rbase[g]), D.rmask[g], err);
-                } else {
-                    slot = table_insert(t, h, v, err);
-                }
-            }
-            D.slot[pos] = __shfl_sync(peers, slot, leader);
-        }
+        D.slot[pos] = slot;
     }
 }
 
