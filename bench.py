@@ -68,6 +68,9 @@ def parse_args():
                     help="profiler capture window only: run the 1k-op update batches of the serving section "
                          "alone and bracket K incremental batches (after eight) with cudaProfilerStart/Stop, "
                          "for ncu --profile-from-start off; prints the batches' latencies, not a bench line")
+    ap.add_argument("--union-rounds", action="store_true",
+                    help="batched workload: run the union through the single-graph round kernels instead of the "
+                         "persistent per-graph kernel")
     ap.add_argument("--workload", default="powerlaw", choices=["powerlaw", "chain", "batched"],
                     help="powerlaw: 10M/100M to the fixpoint (the headline); chain: 1000 paths of 1000 "
                          "+ 2M random edges to the fixpoint; batched: 4096 graphs in one context, k=3")
@@ -127,12 +130,15 @@ class Workload:
                              f"(2.3) with mean 5, uniform in-graph targets, 64 Zipf(1.1) edge labels, 16 vertex "
                              f"labels; k=3",
                  "n_graphs": int(g["n_graphs"]), "n_vertices": self.n, "n_edges": self.m, "k": 3,
+                 "round_path": "union through the single-graph round kernels" if self.union_rounds else
+                           "one persistent kernel, a CTA per graph from a largest-first queue",
                  "l2": "inputs larger than L2"}
         if extra:
             d.update(extra)
         return d
 
     options = None
+    union_rounds = False
 
     def step(self, bisim, tensors, out):
         ctx = self.init_only(bisim, tensors)
@@ -255,6 +261,7 @@ def run_ours(args, world, rank, local):
     from paper_2111_12493_gb300 import bisim
 
     W = Workload(args.workload, args.scale)
+    W.union_rounds = bool(args.union_rounds)
     g = W.graph
     n, m = W.n, W.m
     dev = torch.device("cuda", local)
@@ -273,6 +280,10 @@ def run_ours(args, world, rank, local):
         bisim.summarize_destroy(ctx)
         W.options = bisim.default_options(**{k: tuned[k] for k in ("small_max_degree", "mid_max_degree",
                                                                    "hub_chunk")})
+
+    if W.batched and args.union_rounds:
+        W.options = W.options or bisim.default_options()
+        W.options.flags |= bisim.FLAG_UNION_ROUNDS
 
     for _ in range(args.warmup):
         rounds, blocks, executed = step(*d_in, d_out)

@@ -75,6 +75,14 @@ enum { BISIM_FLAG_FULL_RECOMPUTE = 2 };
  * run eagerly while launch profiling (bisim_profile_enable) is on. */
 enum { BISIM_FLAG_EAGER = 4 };
 
+/* BISIM_FLAG_UNION_ROUNDS: batched contexts run the rounds of the disjoint
+ * union through the single-graph round kernels instead of the persistent
+ * per-graph kernel (same partition; kept to compare the two). By default
+ * bisim_iterate on a batched context is one launch of a persistent kernel
+ * whose CTAs take the graphs from a work queue, largest first, and run each
+ * graph's rounds, renumbering and collision levels to the end. */
+enum { BISIM_FLAG_UNION_ROUNDS = 8 };
+
 /* Update operations (Section 3.2, incremental summarization of evolving graphs:
  * additions, deletions and modifications of vertices and edges). */
 enum {

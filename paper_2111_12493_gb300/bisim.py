@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbisim_gb300.so")
 
 FIXPOINT = -1
-FLAG_L2_PIN, FLAG_FULL_RECOMPUTE, FLAG_EAGER = 1, 2, 4
+FLAG_L2_PIN, FLAG_FULL_RECOMPUTE, FLAG_EAGER, FLAG_UNION_ROUNDS = 1, 2, 4, 8
 OP_EDGE_ADD, OP_EDGE_DEL, OP_VERTEX_ADD, OP_VERTEX_DEL = 0, 1, 2, 3
 
 _STATUS = {0: "BISIM_OK", 1: "BISIM_EINVAL", 2: "BISIM_ENOMEM", 3: "BISIM_ECUDA",

@@ -101,6 +101,7 @@ void destroy_ctx(bisim_ctx* ctx) {
     if (ctx->dstate) cudaFreeAsync(ctx->dstate, s);
     cudaStreamSynchronize(s);
     pinned_give(ctx->hstate);
+    pinned_give(ctx->seg_host);
     delete ctx;
 }
 
@@ -257,6 +258,8 @@ bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s) {
 // the fixpoint, since every round refines the previous partition.
 bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
                         int32_t* out_executed, int64_t* out_blocks, bool allow_graph) {
+    // batched contexts: every graph's rounds in one persistent launch
+    if (segment_usable(ctx)) return segment_rounds(ctx, k, cap, s, out_rounds, out_executed, out_blocks);
     cudaError_t e;
     bisim_status pst = dense_prepare(ctx, s);
     if (pst != BISIM_OK) return pst;
@@ -458,6 +461,7 @@ bisim_status summarize_init_batched(bisim_ctx** out, int32_t n_graphs, const int
     if (st == BISIM_OK)
         st = build_from_coo(ctx, gsrc, gdst, static_cast<const int32_t*>(dl), s);
     if (st == BISIM_OK) st = dense_region_table(ctx, hv.data(), n_graphs, s);
+    if (st == BISIM_OK) st = segment_init(ctx, hv.data(), he.data(), n_graphs, s);
     free_temps(temps, s);
     if (deoff) cudaFreeAsync(deoff, s);
     if (gsrc) cudaFreeAsync(gsrc, s);

@@ -329,6 +329,15 @@ struct bisim_ctx {
     void* hloop = nullptr;                           // its pinned host mirror
     int64_t round_graph_launches = 0;                // kernels in one captured round
 
+    // batched contexts: the persistent per-graph kernel (segment.cu)
+    int32_t* seg_order = nullptr;                    // [n_graphs] work queue, largest graph first
+    unsigned long long* seg_hash = nullptr;          // [n] signature hash by vertex
+    uint8_t* seg_own = nullptr;                      // [n] the vertex was its block's id last round
+    uint8_t* seg_joined = nullptr;                   // [n] another vertex joined its block last round
+    int32_t* seg_lists = nullptr;                    // [4 n] per-graph lists of a round
+    void* seg_state = nullptr;                       // device SegState
+    void* seg_host = nullptr;                        // its pinned mirror
+
     // collision resolution
     int32_t* ulist[2] = {nullptr, nullptr};
     int32_t* dlist = nullptr;      // vertices whose verification needs a set comparison
@@ -481,6 +490,17 @@ bisim_status dense_layout_hubs(bisim_ctx* ctx, bool pack_from_csr, cudaStream_t 
 // Batched contexts: one signature-table region per graph (sized for the graph,
 // load <= 0.6), so that the inserts of a graph's vertices stay in a small span.
 bisim_status dense_region_table(bisim_ctx* ctx, const int64_t* voff_host, int32_t n_graphs, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- batched rounds (segment.cu)
+
+// Uploads the work queue of the persistent batched kernel (graphs by size, largest first).
+bisim_status segment_init(bisim_ctx* ctx, const int64_t* voff_host, const int64_t* eoff_host, int32_t n_graphs,
+                          cudaStream_t s);
+// Whether bisim_iterate runs the persistent per-graph kernel for this context.
+bool segment_usable(const bisim_ctx* ctx);
+// All rounds of every graph of a batched context in one launch; the partition ends in P[0].
+bisim_status segment_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
+                            int32_t* out_executed, int64_t* out_blocks);
 // The vertex-ordered CSR (row_ptr, col, elab), rebuilt from the layout when a
 // context was built straight into it (updates and list-mode paths need it).
 bisim_status ensure_vertex_csr(bisim_ctx* ctx, cudaStream_t s);
