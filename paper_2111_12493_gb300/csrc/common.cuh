@@ -288,6 +288,7 @@ struct bisim_ctx {
     // dense round layout: live vertices grouped by degree class (then the dead
     // ones), their out-rows copied in that order as packed (label << 32 | target)
     bool dense_ready = false;
+    int64_t layout_version = 0;                      // counts the layouts built
     int32_t* dvert = nullptr;                        // [n] position -> vertex
     int32_t* dvpos = nullptr;                        // [n] vertex -> position
     int64_t* dprp = nullptr;                         // [n_live + 1] row offsets into dpe
@@ -331,6 +332,9 @@ struct bisim_ctx {
 
     // batched contexts: the persistent per-graph kernel (segment.cu)
     int32_t* seg_order = nullptr;                    // [n_graphs] work queue, largest graph first
+    int64_t* seg_e0 = nullptr;                       // [n] first entry of the vertex's row in dpe
+    int32_t* seg_deg = nullptr;                      // [n] its length
+    int64_t seg_rows_version = -1;                   // layout_version the two arrays were taken from
     unsigned long long* seg_hash = nullptr;          // [n] signature hash by vertex
     uint8_t* seg_own = nullptr;                      // [n] the vertex was its block's id last round
     uint8_t* seg_joined = nullptr;                   // [n] another vertex joined its block last round

@@ -1507,6 +1507,7 @@ bisim_status dense_layout_hubs(bisim_ctx* ctx, bool pack_from_csr, cudaStream_t 
     }
     if ((e = cudaGetLastError())) return cuda_error(ctx, e, "build dense layout");
     ctx->dense_ready = true;
+    ++ctx->layout_version;
     ctx->stats.device_bytes = ctx->device_bytes;
     return BISIM_OK;
 }

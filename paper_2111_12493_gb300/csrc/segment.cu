@@ -26,8 +26,9 @@
 //                the vertex is inserted again at the next level with another
 //                salt. The smallest vertex of every slot is final at each level,
 //                so the levels end.
-// Data written inside the launch is read back with L2 loads (__ldcg), never
-// through the read-only path.
+// Data written inside the launch is never read through the read-only path:
+// block ids with plain loads (a graph's are written and read by its own CTA,
+// a barrier apart), the rest with L2 loads (__ldcg).
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -64,9 +65,9 @@ struct SegArgs {
     const int64_t* voff;            // [G + 1] vertex segments of the union
     const int32_t* order;           // [G] queue: graphs, largest first
     int32_t G;
-    const int32_t* vpos;            // vertex -> position of its row in the round layout
-    const int64_t* prp;             // position -> first entry of the row in pe
-    const unsigned long long* pe;   // rows as packed (label << 32 | target) entries
+    const int64_t* re0;             // vertex -> first entry of its row in pe
+    const int32_t* rdeg;            // vertex -> row length
+    const unsigned long long* pe;   // rows as packed (label << 32 | target) entries (the round layout)
     const int32_t* P0;              // label partition
     int32_t* P[2];                  // round outputs; the final partition ends in P[0]
     unsigned long long* hash;       // [n] signature hash
@@ -96,17 +97,17 @@ struct SegShared {
 
 __device__ __forceinline__ unsigned seg_lane() { return threadIdx.x & 31u; }
 
+// The block ids of a graph are written and read by its own CTA only, with a
+// CTA barrier in between, so the gathers may go through L1.
 __device__ __forceinline__ uint64_t seg_pair(const SegArgs& A, const int32_t* Pin, int64_t e) {
     const unsigned long long pk = __ldg(A.pe + e);
-    return pair_value(static_cast<int32_t>(pk >> 32), __ldcg(Pin + static_cast<uint32_t>(pk)));
+    return pair_value(static_cast<int32_t>(pk >> 32), Pin[static_cast<uint32_t>(pk)]);
 }
 
 // First entry and length of v's row.
 __device__ __forceinline__ int64_t seg_row(const SegArgs& A, int32_t v, int64_t& d) {
-    const int32_t p = __ldg(A.vpos + v);
-    const int64_t e0 = __ldg(A.prp + p);
-    d = __ldg(A.prp + p + 1) - e0;
-    return e0;
+    d = __ldg(A.rdeg + v);
+    return __ldg(A.re0 + v);
 }
 
 // Sub-range of a pair value when a set is built in several passes.
@@ -337,7 +338,7 @@ __device__ void seg_graph(const SegArgs& A, int32_t g, unsigned long long* set, 
                                 s += x[j];
                             }
                         }
-                        const uint64_t h = sig_hash(__ldcg(Pin + v), c, s);
+                        const uint64_t h = sig_hash(Pin[v], c, s);
                         A.cnt[v] = static_cast<int32_t>(c);
                         A.hash[v] = h;
                         A.slot[v] = table_insert_in(t, level_hash(h, 0, t.hmask), static_cast<int32_t>(v), base, mask,
@@ -384,7 +385,7 @@ __device__ void seg_graph(const SegArgs& A, int32_t g, unsigned long long* set, 
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
                 if (lane == 0) {
-                    const uint64_t h = sig_hash(__ldcg(Pin + v), c, s);
+                    const uint64_t h = sig_hash(Pin[v], c, s);
                     A.cnt[v] = static_cast<int32_t>(c);
                     A.hash[v] = h;
                     A.slot[v] = table_insert_in(t, level_hash(h, 0, t.hmask), v, base, mask, err);
@@ -404,7 +405,7 @@ __device__ void seg_graph(const SegArgs& A, int32_t g, unsigned long long* set, 
                 unsigned long long s = 0;
                 seg_cta_set(A, Pin, e0, d, set, S, c, s);
                 if (tid == 0) {
-                    const uint64_t h = sig_hash(__ldcg(Pin + v), c, s);
+                    const uint64_t h = sig_hash(Pin[v], c, s);
                     A.cnt[v] = static_cast<int32_t>(c);
                     A.hash[v] = h;
                     A.slot[v] = table_insert_in(t, level_hash(h, 0, t.hmask), v, base, mask, err);
@@ -443,7 +444,7 @@ __device__ void seg_graph(const SegArgs& A, int32_t g, unsigned long long* set, 
                         Pout[v] = v;
                         A.own[v] = 1;
                         ++my_blocks;
-                    } else if (__ldcg(Pin + v) != __ldcg(Pin + r) || __ldcg(A.cnt + v) != __ldcg(A.cnt + r)) {
+                    } else if (Pin[v] != Pin[r] || __ldcg(A.cnt + v) != __ldcg(A.cnt + r)) {
                         push = true;
                     } else {
                         int64_t dv = 0, dr = 0;
@@ -584,6 +585,16 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_segments(const SegArgs A) {
     }
 }
 
+__global__ void k_seg_rows(const int32_t* __restrict__ vpos, const int64_t* __restrict__ prp, int32_t n,
+                           int64_t* __restrict__ e0, int32_t* __restrict__ deg) {
+    const int32_t v = static_cast<int32_t>(blockIdx.x * blockDim.x + threadIdx.x);
+    if (v >= n) return;
+    const int32_t p = vpos[v];
+    const int64_t a = prp[p];
+    e0[v] = a;
+    deg[v] = static_cast<int32_t>(prp[p + 1] - a);
+}
+
 int seg_grid(int32_t G) {
     static int per_sm = -1, sms = 0;
     if (per_sm < 0) {
@@ -639,7 +650,9 @@ bisim_status segment_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->seg_own), nv, s)) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->seg_joined), nv, s)) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->seg_lists), sizeof(int32_t) * 4 * nv, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->seg_state), sizeof(SegState), s)))
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->seg_state), sizeof(SegState), s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->seg_e0), sizeof(int64_t) * nv, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->seg_deg), sizeof(int32_t) * nv, s)))
             return cuda_error(ctx, e, "alloc batched round state");
         if (ctx->seg_host == nullptr && (ctx->seg_host = pinned_take()) == nullptr)
             return set_error(ctx, BISIM_ENOMEM, "pinned host memory for the batched round state");
@@ -647,6 +660,14 @@ bisim_status segment_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t
     }
     if (ctx->opt.mem_budget_bytes > 0 && ctx->device_bytes > ctx->opt.mem_budget_bytes)
         return set_error(ctx, BISIM_ENOMEM, "context exceeds the memory budget");
+    if (ctx->seg_rows_version != ctx->layout_version && n > 0) {
+        // every vertex's row by vertex id (the layout keeps rows by position)
+        BISIM_SITE(site_r, "segment_rows");
+        Launch L(site_r, s, n, 0, 24.0 * n);
+        k_seg_rows<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(ctx->dvpos, ctx->dprp, n, ctx->seg_e0,
+                                                                         ctx->seg_deg);
+        ctx->seg_rows_version = ctx->layout_version;
+    }
     SegState* dst = static_cast<SegState*>(ctx->seg_state);
     SegState* hst = static_cast<SegState*>(ctx->seg_host);
     cudaMemsetAsync(dst, 0, sizeof(SegState), s);
@@ -655,8 +676,8 @@ bisim_status segment_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t
         A.voff = ctx->voff;
         A.order = ctx->seg_order;
         A.G = ctx->n_graphs;
-        A.vpos = ctx->dvpos;
-        A.prp = ctx->dprp;
+        A.re0 = ctx->seg_e0;
+        A.rdeg = ctx->seg_deg;
         A.pe = ctx->dpe;
         A.P0 = ctx->P0;
         A.P[0] = ctx->P[0];
