@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_insert(const int32_t* __rest
     // one thread per position; the insert reads its slot before any atomic, so the
     // many vertices of a popular signature mostly find a smaller vertex recorded
     // and leave without one (combining equal hashes within a warp first, with
-    // match_any, was measured twice as slow in round 1)
+    // match_any, was measured twice as slow)
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride) {
         const int64_t pos = list[i];
         const int32_t v = D.vert[pos];

@@ -284,7 +284,7 @@ __device__ void seg_graph(const SegArgs& A, int32_t g, unsigned long long* set, 
     unsigned* err = &A.st->error;
 
     for (uint32_t j = tid; j <= mask; j += kSegThreads) A.slots[base + j].w = 0ull;
-    for (int64_t v = v0 + tid; v < v1; v += kSegThreads) A.own[v] = 0;     // nobody is alone before round 1
+    for (int64_t v = v0 + tid; v < v1; v += kSegThreads) A.own[v] = 0;     // nobody is alone before the first round
     int epoch = 0;
     const int32_t* Pin = A.P0;
     int32_t* Pout = A.P[0];

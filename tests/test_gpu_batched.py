@@ -142,7 +142,7 @@ def test_persistent_kernel_long_rows_and_row_copies(B):
         P, rounds, blocks, _ = run_batched(B, b, k, cap=10)
         _same(P, want, f"k={k}")
         assert (rounds, blocks) == (wr, wb)
-    # the two long rows, and every group of copies, share a block after round 1
+    # the two long rows, and every group of copies, share a block after one round
     P, _, _, _ = run_batched(B, b, 1)
     v0 = int(b["vertex_offsets"][1])
     for lo, hi in ((0, 2), (2, 5), (5, 12), (12, 30), (30, 60), (60, 62)):
