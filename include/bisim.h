@@ -167,7 +167,15 @@ bisim_status summarize_init_coo(bisim_ctx** out, int32_t n_vertices, int64_t n_e
  * of each graph, stored graph after graph; edge_label int32[total edges];
  * vertex_label int32[total vertices]. No block ever crosses two graphs, and
  * get_partition returns graph-local canonical ids. The result for every graph
- * equals refining that graph alone.
+ * equals refining that graph alone. bisim_iterate on such a context is one
+ * launch of a persistent kernel: its CTAs take the graphs from a device queue
+ * (largest first) and each runs one graph's rounds, renumbering and collision
+ * levels to the end; out_rounds is then the largest fixpoint round over the
+ * graphs (k for a fixed k) and out_num_blocks the sum of their block counts,
+ * as for the union refined as one graph. The per-graph table regions need
+ * fewer than 2^32 slots in total, else the union's round kernels run instead
+ * (as with BISIM_FLAG_UNION_ROUNDS). apply_updates is not supported on
+ * batched contexts (BISIM_ESTATE).
  */
 bisim_status summarize_init_batched(bisim_ctx** out, int32_t n_graphs,
                                     const int64_t* vertex_offsets, const int64_t* edge_offsets,
@@ -209,6 +217,8 @@ bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream);
 
 /*
  * bisim_autotune -- choose the degree-class thresholds of the round layout
+ * (the single-graph round kernels; the persistent batched kernel's tiers are
+ * fixed)
  * (mid_max_degree: rows above it take the hub path; small_max_degree: rows up
  * to it take one thread each) and the hub chunk size for this context's graph
  * by timing `rounds` refinement rounds (1..64) under each candidate value, one
