@@ -217,11 +217,10 @@ bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream);
 
 /*
  * bisim_autotune -- choose the degree-class thresholds of the round layout
- * (the single-graph round kernels; the persistent batched kernel's tiers are
- * fixed)
- * (mid_max_degree: rows above it take the hub path; small_max_degree: rows up
- * to it take one thread each) and the hub chunk size for this context's graph
- * by timing `rounds` refinement rounds (1..64) under each candidate value, one
+ * of the single-graph round kernels (mid_max_degree: rows above it take the
+ * hub path; small_max_degree: rows up to it take one thread each) and the hub
+ * chunk size for this context's graph (the persistent batched kernel's tiers
+ * are fixed) by timing `rounds` refinement rounds (1..64) under each candidate value, one
  * setting at a time, on `stream`. The chosen values stay in the context (and
  * are written to *out when out is not NULL) and take effect from the next
  * bisim_iterate or apply_updates. Results never depend on these settings.
