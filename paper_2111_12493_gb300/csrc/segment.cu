@@ -709,8 +709,8 @@ bisim_status segment_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t
     }
     cudaMemcpyAsync(hst, dst, sizeof(SegState), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "batched rounds");
-    if (hst->error & kErrHubFull) return set_error(ctx, BISIM_ENOMEM, "a row's set does not fit the shared-memory passes");
-    if (hst->error) return set_error(ctx, BISIM_ENOMEM, "signature table region full");
+    if (hst->error & kErrHubFull) return set_error(ctx, BISIM_ETIMEOUT, "row set passes reached their split limit");
+    if (hst->error) return set_error(ctx, BISIM_ETIMEOUT, "signature table probe limit reached");
     int32_t rounds = limit, executed = 0;
     int64_t blocks = ctx->last_blocks;
     if (limit > 0 && n == 0) {
