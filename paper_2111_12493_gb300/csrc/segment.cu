@@ -704,6 +704,7 @@ bisim_status segment_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t
         // so this is an upper bound
         Launch L(site, s, n, ctx->m, static_cast<double>(limit) * (12.0 * ctx->m + 40.0 * n));
         k_segments<<<seg_grid(ctx->n_graphs), kSegThreads, kSegSmem, s>>>(A);
+        if ((e = cudaGetLastError())) return cuda_error(ctx, e, "launch batched rounds");
     } else if (n > 0) {
         cudaMemcpyAsync(ctx->P[0], ctx->P0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
     }
