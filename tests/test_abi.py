@@ -54,3 +54,28 @@ def test_default_options_without_gpu():
     assert (o.k_incremental, o.hash_bits, o.small_max_degree, o.mid_max_degree) == (2, 64, 32, 8192)
     lib.bisim_last_error.restype = ctypes.c_char_p
     assert lib.bisim_last_error(None) is not None
+
+
+def test_calls_fail_loudly_without_a_gpu():
+    """No CPU fallback: without a device every call returns an error status (and the binding raises)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import numpy as np
+    from paper_2111_12493_gb300 import build
+    try:
+        path = build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    lib = ctypes.CDLL(path)
+    lib.bisim_last_error.restype = ctypes.c_char_p
+    out = ctypes.c_void_p()
+    vl = np.zeros(2, np.int32)
+    rc = lib.summarize_init_coo(ctypes.byref(out), 2, ctypes.c_int64(0), None, None, None,
+                                vl.ctypes.data_as(ctypes.c_void_p), None, None, None)
+    assert rc == 3 and out.value is None           # BISIM_ECUDA, no context
+    assert lib.bisim_last_error(None)
+    from paper_2111_12493_gb300 import bisim
+    with pytest.raises(RuntimeError):
+        bisim.summarize_init_coo(2, torch.zeros(0, dtype=torch.int32), torch.zeros(0, dtype=torch.int32),
+                                 torch.zeros(0, dtype=torch.int32), torch.zeros(2, dtype=torch.int32))
