@@ -82,6 +82,15 @@ __device__ __forceinline__ uint64_t level_hash(uint64_t h0, uint32_t level, uint
     return h & hmask;
 }
 
+// Signature of one position of the dense rounds: the hash of (own block, |S|,
+// pair values), |S| and the own block P_i[v], in one 16-byte record, so that
+// the verification reads one sector per side to compare two of them.
+struct __align__(16) SigRec {
+    unsigned long long hash;
+    int32_t cnt;
+    int32_t own;
+};
+
 // ----------------------------------------------------------------------------- signature table
 
 // One 8-byte slot of the open-addressing signature table:
@@ -123,15 +132,17 @@ __device__ __forceinline__ unsigned long long table_read(const TableRef& t, uint
 
 // Insert `h` (already masked) for vertex v into the region [base, base + mask]
 // of the table (mask + 1 a power of two; probing wraps inside the region);
-// returns the slot index or ~0u on overflow.
-__device__ __forceinline__ uint32_t table_insert_in(const TableRef& t, uint64_t h, int32_t v, uint64_t base,
-                                                    uint64_t mask, unsigned* err) {
+// returns the slot index or ~0u on overflow. `first` is the word already read
+// from the home slot base + (h & mask) (callers issue that read early to
+// overlap it with other work).
+__device__ __forceinline__ uint32_t table_insert_at(const TableRef& t, uint64_t h, int32_t v, uint64_t base,
+                                                    uint64_t mask, unsigned long long first, unsigned* err) {
     const unsigned long long tag = (h & ~0xfffffffffull) | t.epoch;
     const unsigned long long want = tag | static_cast<uint32_t>(v);
     uint64_t off = h & mask;
     for (uint64_t probe = 0; probe <= mask; ++probe) {
         const uint64_t pos = base + off;
-        unsigned long long cur = table_read(t, pos);
+        unsigned long long cur = probe == 0 ? first : table_read(t, pos);
         for (;;) {
             if ((cur & kSlotEpochMask) != t.epoch) {            // free in this epoch: claim it
                 const unsigned long long prev = atomicCAS(&t.slots[pos].w, cur, want);
@@ -155,6 +166,11 @@ __device__ __forceinline__ uint32_t table_insert_in(const TableRef& t, uint64_t 
     }
     atomicOr(err, kErrTableFull);
     return ~0u;
+}
+
+__device__ __forceinline__ uint32_t table_insert_in(const TableRef& t, uint64_t h, int32_t v, uint64_t base,
+                                                    uint64_t mask, unsigned* err) {
+    return table_insert_at(t, h, v, base, mask, table_read(t, base + (h & mask)), err);
 }
 
 // Insert `h` (already masked) for vertex v anywhere in the table.
@@ -301,12 +317,19 @@ struct bisim_ctx {
     int64_t* rbase = nullptr;                        // [n_graphs] first slot of the graph's region
     uint32_t* rmask = nullptr;                       // [n_graphs] region size - 1 (a power of two)
     uint32_t* dslot = nullptr;                       // [n] table slot per position
-    unsigned long long* dhash = nullptr;             // [n] signature hash per position
-    int32_t* dcnt = nullptr;                         // [n] |S| per position
+    bisim::SigRec* dsig = nullptr;                   // [n] signature hash, |S| and own block per position
     int2* dpairs = nullptr;                          // [n] (position, representative's position) for a CTA compare
     int2* dsmall = nullptr;                          // [n] the same for rows of at most 32 edges (warp compare)
     uint8_t* djoined = nullptr;                      // [n] by position: another vertex joined this one's block last round
     uint8_t* downs = nullptr;                        // [n] by position: the vertex was its block's id last round
+    // active list of the dense rounds: the positions whose vertex is not alone
+    // in its block (ascending, hence grouped by degree class); a vertex alone in
+    // its block stays alone in every later round, so the list only shrinks
+    int32_t* dact = nullptr;                         // [n] active positions
+    int32_t* dact2 = nullptr;                        // [n] the next round's list while it is compacted
+    int64_t* daoff = nullptr;                        // [kDClasses + 1] class c's entries: dact[daoff[c] .. daoff[c+1])
+    int64_t* dtile = nullptr;                        // [tiles + 2 + kDClasses] survivors per tile, then their offsets; the new length; survivors per class
+    int64_t n_tiles = 0;                             // tiles of kActTile entries covering all live positions
     unsigned long long* dwork = nullptr;             // launch profiling: signature work counters of a round
     bisim::HubChunk* dchunks = nullptr;              // hub rows cut into chunks of at most 4096 edges
     int64_t n_dchunks = 0;

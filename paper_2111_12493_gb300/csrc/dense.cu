@@ -316,8 +316,7 @@ struct DenseView {
     const int64_t* prp;                // position -> offset into pe
     const unsigned long long* pe;      // packed (label, target) rows
     const int32_t* P;                  // P_i, by vertex
-    int32_t* cnt;                      // |S|, by position
-    unsigned long long* hash;          // signature hash, by position
+    SigRec* sig;                       // signature hash, |S| and own block, by position
     uint32_t* slot;                    // table slot, by position
     uint8_t* joined;                   // by position: another vertex joined its block in the last round
     uint8_t* own;                      // by position: the vertex was its block's id (smallest member) in the last round
@@ -325,6 +324,9 @@ struct DenseView {
     const int64_t* rbase;              // batched contexts: the graph's table region
     const uint32_t* rmask;
     unsigned long long* work;          // launch profiling only: rows and row entries each group processed
+    const int32_t* act;                // active positions (not alone in their block), ascending
+    const int64_t* aoff;               // [kDClasses + 1] class c's entries are act[aoff[c] .. aoff[c+1])
+    const int32_t* round_no;           // captured loop: rounds run so far, which picks the table epoch (null: eager)
 };
 
 // Work counters of the signature kernels, filled only while launch profiling
@@ -358,143 +360,184 @@ __device__ __forceinline__ void work_block(const DenseView& D, int g, bool activ
     if (threadIdx.x == 0) work_add(D, g, static_cast<unsigned long long>(rows), esum);
 }
 
-struct WarpPlan {
-    int64_t cta_begin[4];
-    int64_t pos_begin[3];
-    int64_t pos_end[3];
-};
-
 // A vertex alone in its block of P_i stays alone in P_{i+1}: no signature is
-// needed (the level-0 scan settles it without the table). Read before that scan
-// clears the joined flags.
+// needed. The hub passes test this per chunk; every other kernel of a round
+// walks the active list, which holds only the vertices that are not alone.
+// The flags are those of the previous round until the level-0 insert clears
+// the joined flags of the listed positions.
 __device__ __forceinline__ bool alone_last_round(const DenseView& D, int64_t pos) {
     return D.own[pos] && !D.joined[pos];
 }
 
 __device__ __forceinline__ void finish_sig(const DenseView& D, int64_t pos, int32_t own, uint32_t c, uint64_t sum) {
-    D.cnt[pos] = static_cast<int32_t>(c);
-    D.hash[pos] = sig_hash(own, c, sum);
+    SigRec r;
+    r.hash = sig_hash(own, c, sum);
+    r.cnt = static_cast<int32_t>(c);
+    r.own = own;
+    D.sig[pos] = r;
 }
 
-// Degree <= D: one thread per vertex. The row's pair values sit in registers;
-// a value counts when no earlier value of the row equals it.
+// Degree <= D: one thread per active vertex of the classes [c0, c1). The row's
+// pair values sit in registers; a value counts when no earlier value of the
+// row equals it.
 template <int D>
-__global__ void __launch_bounds__(kThreads) k_dense_thread_sig(int64_t first, int64_t count, const DenseView V,
-                                                               int group) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int64_t pos = first + i;
-    const bool active = i < count && !alone_last_round(V, pos);
-    int d = 0;
-    if (active) {
-        const int32_t own = V.P[V.vert[pos]];
-        const int64_t e0 = V.prp[pos];
-        d = static_cast<int>(V.prp[pos + 1] - e0);
-        uint64_t v[D];
+__global__ void __launch_bounds__(kThreads) k_dense_thread_sig(int c0, int c1, const DenseView V, int group) {
+    const int64_t a0 = V.aoff[c0];
+    const int64_t count = V.aoff[c1] - a0;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x;
+    int32_t next = base + threadIdx.x < count ? V.act[a0 + base + threadIdx.x] : 0;
+    for (; base < count; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        const bool active = i < count;
+        const int64_t pos = next;
+        if (i + stride < count) next = V.act[a0 + i + stride];     // the next entry's load overlaps this one
+        int d = 0;
+        if (active) {
+            const int32_t own = V.P[V.vert[pos]];
+            const int64_t e0 = V.prp[pos];
+            d = static_cast<int>(V.prp[pos + 1] - e0);
+            uint64_t v[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) v[j] = j < d ? packed_pair_value(__ldcs(V.pe + e0 + j), V.P) : 0ull;
-        uint64_t sum = 0;
-        uint32_t u = 0;
+            for (int j = 0; j < D; ++j) v[j] = j < d ? packed_pair_value(__ldcs(V.pe + e0 + j), V.P) : 0ull;
+            uint64_t sum = 0;
+            uint32_t u = 0;
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-            bool fresh = j < d;
+            for (int j = 0; j < D; ++j) {
+                bool fresh = j < d;
 #pragma unroll
-            for (int q = 0; q < j; ++q) fresh = fresh && v[q] != v[j];
-            if (fresh) {
-                sum += v[j];
-                ++u;
+                for (int q = 0; q < j; ++q) fresh = fresh && v[q] != v[j];
+                if (fresh) {
+                    sum += v[j];
+                    ++u;
+                }
             }
+            finish_sig(V, pos, own, u, sum);
         }
-        finish_sig(V, pos, own, u, sum);
+        work_block(V, group, active, static_cast<unsigned>(d));
     }
-    work_block(V, group, active, static_cast<unsigned>(d));
 }
 
-// Degree <= 256: one warp per vertex, set of up to 512 slots in the warp's slice.
+// Degree <= 256: one warp per active vertex, set of up to 512 slots in the
+// warp's slice of shared memory. All of the row's words are loaded, then all
+// of their block ids gathered, before the first set insert, so that a warp
+// keeps up to eight loads of each kind in flight.
 constexpr int kWarpSlots = 512;
-__global__ void __launch_bounds__(kThreads) k_dense_warp_sig(const WarpPlan plan, const DenseView D) {
+constexpr int kWarpChunks = 8;                         // 256 / 32
+__global__ void __launch_bounds__(kThreads) k_dense_warp_sig(const DenseView D) {
     __shared__ unsigned long long sm_all[(kThreads / 32) * kWarpSlots];
     __shared__ unsigned zero_all[kThreads / 32];
-    const int64_t b = blockIdx.x;
-    const int c = b >= plan.cta_begin[2] ? 2 : b >= plan.cta_begin[1] ? 1 : 0;
-    const int64_t cta0 = c == 2 ? plan.cta_begin[2] : c == 1 ? plan.cta_begin[1] : plan.cta_begin[0];
-    const int64_t pos0 = c == 2 ? plan.pos_begin[2] : c == 1 ? plan.pos_begin[1] : plan.pos_begin[0];
-    const int64_t pos1 = c == 2 ? plan.pos_end[2] : c == 1 ? plan.pos_end[1] : plan.pos_end[0];
+    const int64_t a0 = D.aoff[kDWarp0];
+    const int64_t count = D.aoff[kDMid0] - a0;
     const int warp = threadIdx.x >> 5;
     const unsigned lane = lane_id();
-    const int64_t pos = pos0 + (b - cta0) * (kThreads / 32) + warp;
-    const bool active = pos < pos1 && !alone_last_round(D, pos);   // the same for the whole warp
-    if (D.work) work_block(D, 3, active && lane == 0, active ? static_cast<unsigned>(D.prp[pos + 1] - D.prp[pos]) : 0u);
-    if (!active) return;
-    const int32_t own = lane == 0 ? D.P[D.vert[pos]] : 0;
-    const int64_t e0 = D.prp[pos];
-    const int d = static_cast<int>(D.prp[pos + 1] - e0);
-    uint32_t S = 64;
-    while (S < 2u * static_cast<uint32_t>(d)) S <<= 1;
     unsigned long long* tab = sm_all + warp * kWarpSlots;
-    for (uint32_t j = lane; j < S; j += 32) tab[j] = 0ull;
-    if (lane == 0) zero_all[warp] = 0u;
-    __syncwarp();
-    unsigned out = 0;
-    uint64_t mys = 0;
-    for (int j0 = 0; j0 < d; j0 += 32) {
-        const int j = j0 + static_cast<int>(lane);
-        bool fresh = false;
-        uint64_t mv = 0;
-        if (j < d) {
-            mv = packed_pair_value(__ldcs(D.pe + e0 + j), D.P);
-            fresh = smem_set_insert(tab, S - 1, &zero_all[warp], mv);
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * (kThreads / 32);
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * (kThreads / 32); base < count; base += stride) {
+        const int64_t w = base + warp;
+        const bool active = w < count;                 // the same for the whole warp
+        int64_t pos = 0, e0 = 0;
+        int d = 0;
+        if (active) {
+            pos = D.act[a0 + w];
+            e0 = D.prp[pos];
+            d = static_cast<int>(D.prp[pos + 1] - e0);
         }
-        out += static_cast<unsigned>(__popc(__ballot_sync(0xffffffffu, fresh)));
-        if (fresh) mys += mv;
-    }
+        if (D.work) work_block(D, 3, active && lane == 0, active ? static_cast<unsigned>(d) : 0u);
+        if (!active) continue;
+        const int32_t own = lane == 0 ? D.P[D.vert[pos]] : 0;
+        uint64_t mv[kWarpChunks];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mys += __shfl_xor_sync(0xffffffffu, mys, o);
-    if (lane == 0) finish_sig(D, pos, own, out, mys);
+        for (int k = 0; k < kWarpChunks; ++k) {
+            const int j = k * 32 + static_cast<int>(lane);
+            mv[k] = j < d ? __ldcs(D.pe + e0 + j) : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < kWarpChunks; ++k)
+            if (k * 32 + static_cast<int>(lane) < d) mv[k] = packed_pair_value(mv[k], D.P);
+        uint32_t S = 64;
+        while (S < 2u * static_cast<uint32_t>(d)) S <<= 1;
+        for (uint32_t j = lane; j < S; j += 32) tab[j] = 0ull;
+        if (lane == 0) zero_all[warp] = 0u;
+        __syncwarp();
+        unsigned out = 0;
+        uint64_t mys = 0;
+#pragma unroll
+        for (int k = 0; k < kWarpChunks; ++k) {
+            if (k * 32 >= d) break;                    // the same for the whole warp
+            const int j = k * 32 + static_cast<int>(lane);
+            const bool fresh = j < d && smem_set_insert(tab, S - 1, &zero_all[warp], mv[k]);
+            out += static_cast<unsigned>(__popc(__ballot_sync(0xffffffffu, fresh)));
+            if (fresh) mys += mv[k];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mys += __shfl_xor_sync(0xffffffffu, mys, o);
+        if (lane == 0) finish_sig(D, pos, own, out, mys);
+        __syncwarp();                                  // the slice is cleared for the warp's next vertex
+    }
 }
 
-// Degree <= N (N = 512 .. 8192): one CTA of T threads per vertex, set of 2N slots.
+// Degree <= N (N = 512 .. 8192): one CTA of T threads per active vertex of
+// class `cls`, set of 2N slots; each thread loads four words before it
+// gathers and inserts them.
+constexpr int kMidUnroll = 4;
 template <int N, int T>
-__global__ void __launch_bounds__(T) k_dense_mid_sig(int64_t first, const DenseView D, int group) {
+__global__ void __launch_bounds__(T) k_dense_mid_sig(int cls, const DenseView D, int group) {
     extern __shared__ unsigned long long tab[];
     __shared__ unsigned long long wsum[T / 32];
     __shared__ unsigned wcnt[T / 32];
     __shared__ unsigned zero;
     constexpr uint32_t mask = 2 * N - 1;
-    const int64_t pos = first + blockIdx.x;
-    if (alone_last_round(D, pos)) return;               // whole CTA leaves together
-    const int64_t e0 = D.prp[pos];
-    const int d = static_cast<int>(D.prp[pos + 1] - e0);
-    if (D.work && threadIdx.x == 0) work_add(D, group, 1, static_cast<unsigned long long>(d));
-    for (int j = threadIdx.x; j < 2 * N; j += T) tab[j] = 0ull;
-    if (threadIdx.x == 0) zero = 0u;
-    __syncthreads();
-    uint64_t mys = 0;
-    unsigned myc = 0;
-    for (int j = threadIdx.x; j < d; j += T) {
-        const uint64_t mv = packed_pair_value(__ldcs(D.pe + e0 + j), D.P);
-        if (smem_set_insert(tab, mask, &zero, mv)) {
-            mys += mv;
-            ++myc;
-        }
-    }
+    const int64_t a0 = D.aoff[cls];
+    const int64_t count = D.aoff[cls + 1] - a0;
+    for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+        const int64_t pos = D.act[a0 + it];
+        const int64_t e0 = D.prp[pos];
+        const int d = static_cast<int>(D.prp[pos + 1] - e0);
+        if (D.work && threadIdx.x == 0) work_add(D, group, 1, static_cast<unsigned long long>(d));
+        for (int j = threadIdx.x; j < 2 * N; j += T) tab[j] = 0ull;
+        if (threadIdx.x == 0) zero = 0u;
+        __syncthreads();
+        uint64_t mys = 0;
+        unsigned myc = 0;
+        for (int j0 = threadIdx.x; j0 < d; j0 += kMidUnroll * T) {
+            uint64_t mv[kMidUnroll];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        mys += __shfl_xor_sync(0xffffffffu, mys, o);
-        myc += __shfl_xor_sync(0xffffffffu, myc, o);
-    }
-    if (lane_id() == 0) {
-        wsum[threadIdx.x >> 5] = mys;
-        wcnt[threadIdx.x >> 5] = myc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint64_t s = 0;
-        unsigned c = 0;
-        for (int w = 0; w < T / 32; ++w) {
-            s += wsum[w];
-            c += wcnt[w];
+            for (int k = 0; k < kMidUnroll; ++k) {
+                const int j = j0 + k * T;
+                mv[k] = j < d ? __ldcs(D.pe + e0 + j) : 0ull;
+            }
+#pragma unroll
+            for (int k = 0; k < kMidUnroll; ++k)
+                if (j0 + k * T < d) mv[k] = packed_pair_value(mv[k], D.P);
+#pragma unroll
+            for (int k = 0; k < kMidUnroll; ++k) {
+                if (j0 + k * T < d && smem_set_insert(tab, mask, &zero, mv[k])) {
+                    mys += mv[k];
+                    ++myc;
+                }
+            }
         }
-        finish_sig(D, pos, D.P[D.vert[pos]], c, s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mys += __shfl_xor_sync(0xffffffffu, mys, o);
+            myc += __shfl_xor_sync(0xffffffffu, myc, o);
+        }
+        if (lane_id() == 0) {
+            wsum[threadIdx.x >> 5] = mys;
+            wcnt[threadIdx.x >> 5] = myc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t sm = 0;
+            unsigned c = 0;
+            for (int w = 0; w < T / 32; ++w) {
+                sm += wsum[w];
+                c += wcnt[w];
+            }
+            finish_sig(D, pos, D.P[D.vert[pos]], c, sm);
+        }
+        __syncthreads();                               // the set is cleared for the CTA's next vertex
     }
 }
 
@@ -695,113 +738,74 @@ __global__ void k_dense_hub_finalize(const DenseView D, const HubSets H) {
 }
 
 
-// Table insert of every listed position (level 0: all live positions, list ==
-// null) with the level's salted hash.
-// Level 0 of a round, first pass: a vertex alone in its block of P_i stays
-// alone in P_{i+1} (every round refines the last) and needs no slot; the other
-// positions are listed for the table. Alone vertices are counted as blocks and,
-// unless the output buffer already holds P_i, get P_{i+1}[v] = v here. The
-// joined flags are cleared for this round's verification to set again.
-// Each thread takes kScanRun consecutive positions (16-byte loads of the
-// flags), so the CTA's one scan and one atomic cover 4096 positions.
-constexpr int kScanRun = 16;
-__global__ void __launch_bounds__(kThreads) k_alone_scan(int64_t count, const DenseView D, int32_t* __restrict__ Pout,
-                                                         bool out_has_in, int32_t* __restrict__ list, DevState* st) {
-    __shared__ unsigned wlisted[kThreads / 32];
-    __shared__ unsigned walone[kThreads / 32];
-    __shared__ unsigned base;
-    const int64_t p0 = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) * kScanRun;
-    const unsigned lane = lane_id();
-    const int warp = static_cast<int>(threadIdx.x >> 5);
-    uint32_t listed = 0u;                           // bit k: position p0 + k needs the table
-    unsigned alone = 0u;
-    if (p0 + kScanRun <= count) {
-        const uint4 ow = *reinterpret_cast<const uint4*>(D.own + p0);
-        const uint4 jw = *reinterpret_cast<const uint4*>(D.joined + p0);
-        *reinterpret_cast<uint4*>(D.joined + p0) = make_uint4(0u, 0u, 0u, 0u);
-        const uint32_t o[4] = {ow.x, ow.y, ow.z, ow.w}, j[4] = {jw.x, jw.y, jw.z, jw.w};
-#pragma unroll
-        for (int k = 0; k < kScanRun; ++k) {
-            const bool a = ((o[k >> 2] >> (8 * (k & 3))) & 0xffu) && !((j[k >> 2] >> (8 * (k & 3))) & 0xffu);
-            if (!a) listed |= 1u << k;
-        }
-    } else {
-        for (int k = 0; k < kScanRun && p0 + k < count; ++k) {
-            const int64_t pos = p0 + k;
-            if (!alone_last_round(D, pos)) listed |= 1u << k;
-            D.joined[pos] = 0;
-        }
-    }
-    const int valid = p0 >= count ? 0 : (p0 + kScanRun <= count ? kScanRun : static_cast<int>(count - p0));
-    const uint32_t vmask = valid == 32 ? ~0u : ((1u << valid) - 1u);
-    alone = static_cast<unsigned>(__popc(vmask & ~listed));
-    if (alone && !out_has_in) {
-        uint32_t am = vmask & ~listed;
-        while (am) {
-            const int k = __ffs(am) - 1;
-            am &= am - 1u;
-            const int32_t v = D.vert[p0 + k];
-            Pout[v] = v;
-        }
-    }
-    // CTA-wide exclusive scan of the listed counts, one atomic for the CTA's range
-    const unsigned mine = static_cast<unsigned>(__popc(listed));
-    unsigned inc = mine, al = alone;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= static_cast<unsigned>(o)) inc += y;
-        al += __shfl_xor_sync(0xffffffffu, al, o);
-    }
-    if (lane == 31) wlisted[warp] = inc;
-    if (lane == 0) walone[warp] = al;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned tot = 0, atot = 0;
-        for (int w = 0; w < kThreads / 32; ++w) {
-            const unsigned c = wlisted[w];
-            wlisted[w] = tot;
-            tot += c;
-            atot += walone[w];
-        }
-        base = tot ? atomicAdd(&st->listed, tot) : 0u;
-        if (atot) atomicAdd(&st->blocks, static_cast<unsigned long long>(atot));
-    }
-    __syncthreads();
-    unsigned at = base + wlisted[warp] + inc - mine;
-    while (listed) {
-        const int k = __ffs(listed) - 1;
-        listed &= listed - 1u;
-        list[at++] = static_cast<int32_t>(p0 + k);
-    }
+// Start of a round: the status word, with the vertices that are not listed
+// (alone in their block of P_i, hence alone in P_{i+1}) already counted as
+// blocks and the list's length as the positions that need the table.
+__global__ void k_round_begin(DevState* st, const int64_t* __restrict__ aoff, int64_t n_live) {
+    const int64_t listed = aoff[kDClasses];
+    DevState z{};
+    z.blocks = static_cast<unsigned long long>(n_live - listed);
+    z.listed = static_cast<unsigned>(listed);
+    *st = z;
 }
 
 // Table insert of the listed positions with the level's salted hash. The count
 // is read on the device when `dcount` is given (level 0), else it is `count`.
+// Level 0 also clears the listed positions' joined flags, which this round's
+// verification sets again. One entry per thread and iteration: the kernel is
+// bound by the latency of its dependent loads (list, hash, table slot), and
+// taking several entries per thread to overlap their chains was measured
+// slower (0.58 against 0.27 ms for 10M positions), because the registers that
+// needs halve the resident warps (the same holds for the verification, 108
+// registers and a quarter of the warps at four entries per thread).
 constexpr int kPersistGrid = 152 * 8;            // full occupancy of 256-thread CTAs
+constexpr int kIlp = 1;
 __global__ void __launch_bounds__(kThreads) k_dense_insert(const int32_t* __restrict__ list, int64_t count,
                                                            const unsigned* dcount, const DenseView D, uint32_t level,
                                                            const TableRef t, unsigned* err) {
     if (dcount) count = *reinterpret_cast<const volatile unsigned*>(dcount);
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    // one thread per position; the insert reads its slot before any atomic, so the
-    // many vertices of a popular signature mostly find a smaller vertex recorded
-    // and leave without one (combining equal hashes within a warp first, with
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x * kIlp;
+    TableRef tt = t;
+    if (D.round_no) tt.epoch = static_cast<uint64_t>((*D.round_no % kEpochCycle) + 1u) << 32;
+    // the insert reads its slot before any atomic, so the many vertices of a
+    // popular signature mostly find a smaller vertex recorded and leave
+    // without one (combining equal hashes within a warp first, with
     // match_any, was measured twice as slow)
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride) {
-        const int64_t pos = list[i];
-        const int32_t v = D.vert[pos];
-        const uint64_t h = level_hash(D.hash[pos], level, t.hmask);
-        uint32_t slot;
-        if (D.gid) {
-            // batched graphs: each graph has its own region of the table, so
-            // that the inserts of one graph's vertices stay close together
-            const int32_t g = D.gid[v];
-            slot = table_insert_in(t, h, v, static_cast<uint64_t>(D.rbase[g]), D.rmask[g], err);
-        } else {
-            slot = table_insert(t, h, v, err);
+    for (int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x * kIlp + threadIdx.x; b < count; b += stride) {
+        int32_t pos[kIlp], v[kIlp];
+        uint64_t h[kIlp], base[kIlp], mask[kIlp];
+        unsigned long long first[kIlp];
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) {
+            const int64_t i = b + static_cast<int64_t>(k) * blockDim.x;
+            pos[k] = i < count ? list[i] : -1;
         }
-        D.slot[pos] = slot;
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) {
+            if (pos[k] < 0) continue;
+            v[k] = D.vert[pos[k]];
+            h[k] = level_hash(D.sig[pos[k]].hash, level, tt.hmask);
+        }
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) {
+            if (pos[k] < 0) continue;
+            base[k] = 0;
+            mask[k] = tt.mask;
+            if (D.gid) {
+                // batched graphs: each graph has its own region of the table, so
+                // that the inserts of one graph's vertices stay close together
+                const int32_t g = D.gid[v[k]];
+                base[k] = static_cast<uint64_t>(D.rbase[g]);
+                mask[k] = D.rmask[g];
+            }
+            first[k] = table_read(tt, base[k] + (h[k] & mask[k]));
+        }
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) {
+            if (pos[k] < 0) continue;
+            D.slot[pos[k]] = table_insert_at(tt, h[k], v[k], base[k], mask[k], first[k], err);
+            if (level == 0) D.joined[pos[k]] = 0;
+        }
     }
 }
 
@@ -815,19 +819,27 @@ struct VerifyOut {
 
 // Confirms every listed position against its slot's representative r (its
 // smallest vertex). r itself: a block id. Different own block or set size: the
-// position moves to the next level. Otherwise the sets are compared: here when
-// both rows have at most two edges, else in a warp (rows <= 32) or a CTA.
+// position moves to the next level. Equal sizes of at most one pair: the full
+// hashes decide exactly. Otherwise the sets are compared: here when both rows
+// have at most two edges, else in a warp (rows <= 32) or a CTA. The three
+// lists and the block count of a CTA's iteration share one scan: per warp four
+// ballot counts, one pass of four threads over the warps (one atomic per
+// list) and two barriers; the shared words alternate between iterations.
 __global__ void __launch_bounds__(kThreads) k_dense_verify(const int32_t* __restrict__ list, int64_t count,
                                                            const unsigned* dcount, const DenseView D,
                                                            const Slot* __restrict__ slots, const VerifyOut O,
                                                            int32_t n_total) {
-    __shared__ unsigned sh[kThreads / 32 + 1];
+    constexpr int W = kThreads / 32;
+    __shared__ unsigned sh[2][4][W + 1];
     if (dcount) count = *reinterpret_cast<const volatile unsigned*>(dcount);
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < count; base += stride) {
+    const int warp = static_cast<int>(threadIdx.x >> 5);
+    const unsigned lt = lanemask_lt();
+    int par = 0;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < count; base += stride, par ^= 1) {
         const int64_t i = base + threadIdx.x;
         bool own = false, push = false, small = false, big = false;
-        int64_t pos = -1, rpos = -1;
+        int32_t pos = -1, rpos = -1;
         if (i < count) pos = list[i];
         if (pos >= 0) {
             const int32_t v = D.vert[pos];
@@ -843,8 +855,18 @@ __global__ void __launch_bounds__(kThreads) k_dense_verify(const int32_t* __rest
             } else {
                 rpos = D.vpos[r];
                 D.own[pos] = 0;
-                if (D.P[v] != D.P[r] || D.cnt[pos] != D.cnt[rpos]) {
+                const SigRec a = D.sig[pos], c = D.sig[rpos];
+                bool join = false;
+                if (a.own != c.own || a.cnt != c.cnt) {
                     push = true;
+                } else if (a.cnt <= 1) {
+                    // |S| <= 1: with equal own blocks and sizes the hashes are
+                    // equal iff the sums of the pair values are (sig_hash is a
+                    // bijection of the sum), and a one-value sum is the pair
+                    // value itself, a bijection of (label, block): equal full
+                    // hashes are equal signatures
+                    join = a.hash == c.hash;
+                    push = !join;
                 } else {
                     const int64_t ev = D.prp[pos], dv = D.prp[pos + 1] - ev;
                     const int64_t er = D.prp[rpos], dr = D.prp[rpos + 1] - er;
@@ -855,28 +877,231 @@ __global__ void __launch_bounds__(kThreads) k_dense_verify(const int32_t* __rest
                         if (dr > 1) b1 = packed_pair_value(D.pe[er + 1], D.P);
                         bool ok = true;
                         for (int64_t j = 0; j < dv; ++j) {
-                            const uint64_t a = packed_pair_value(D.pe[ev + j], D.P);
-                            ok = ok && ((dr > 0 && a == b0) || (dr > 1 && a == b1));
+                            const uint64_t x = packed_pair_value(D.pe[ev + j], D.P);
+                            ok = ok && ((dr > 0 && x == b0) || (dr > 1 && x == b1));
                         }
-                        if (ok) {
-                            O.Pout[v] = r;
-                            D.joined[rpos] = 1;
-                        }
-                        else push = true;
+                        join = ok;
+                        push = !ok;
                     } else if (dv <= 32 && dr <= 32) {
                         small = true;
                     } else {
                         big = true;
                     }
                 }
+                if (join) {
+                    O.Pout[v] = r;
+                    D.joined[rpos] = 1;
+                }
             }
         }
-        const int32_t p32 = static_cast<int32_t>(pos);
-        block_count(own, &O.st->blocks);
-        block_push(push, p32, O.next, &O.st->unresolved, sh);
-        block_push(small, make_int2(p32, static_cast<int32_t>(rpos)), O.small, &O.st->pairs, sh);
-        block_push(big, make_int2(p32, static_cast<int32_t>(rpos)), O.pairs, &O.st->deferred, sh);
+        const unsigned bo = __ballot_sync(0xffffffffu, own), bp = __ballot_sync(0xffffffffu, push);
+        const unsigned bs = __ballot_sync(0xffffffffu, small), bb = __ballot_sync(0xffffffffu, big);
+        unsigned (*c)[W + 1] = sh[par];
+        if (lane_id() == 0) {
+            c[0][warp] = static_cast<unsigned>(__popc(bo));
+            c[1][warp] = static_cast<unsigned>(__popc(bp));
+            c[2][warp] = static_cast<unsigned>(__popc(bs));
+            c[3][warp] = static_cast<unsigned>(__popc(bb));
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            const int q = static_cast<int>(threadIdx.x);
+            unsigned tot = 0;
+            for (int w2 = 0; w2 < W; ++w2) {
+                const unsigned x = c[q][w2];
+                c[q][w2] = tot;
+                tot += x;
+            }
+            unsigned at = 0;
+            if (tot) {
+                if (q == 0) atomicAdd(&O.st->blocks, static_cast<unsigned long long>(tot));
+                else at = atomicAdd(q == 1 ? &O.st->unresolved : q == 2 ? &O.st->pairs : &O.st->deferred, tot);
+            }
+            c[q][W] = at;
+        }
+        __syncthreads();
+        if (push) O.next[c[1][W] + c[1][warp] + __popc(bp & lt)] = pos;
+        if (small) O.small[c[2][W] + c[2][warp] + __popc(bs & lt)] = make_int2(pos, rpos);
+        if (big) O.pairs[c[3][W] + c[3][warp] + __popc(bb & lt)] = make_int2(pos, rpos);
     }
+}
+
+// ----------------------------------------------------------------------------- active list
+
+// End of a round (after its collision levels): every listed vertex's
+// P_{i+1} goes into the input buffer (the two buffers already agree on every
+// vertex that is not listed), and the list keeps the positions that are still
+// not alone in their block, in order. Tiles of kActTile entries, eight
+// consecutive entries per thread; `stop` (the captured loop's decision, null
+// for host-driven rounds) skips all of it when the host must first resolve
+// the round's hash collisions.
+constexpr int kActPer = 8;
+constexpr int kActTile = kThreads * kActPer;
+
+struct ClassBounds {
+    int64_t b[kDClasses + 1];
+};
+
+__device__ __forceinline__ bool stays_listed(const DenseView& D, int64_t pos) {
+    return !alone_last_round(D, pos);
+}
+
+// Pass 1: copy P_{i+1} back for the listed vertices, count each tile's
+// survivors and each class's. When every live position is listed (round 1)
+// the whole array is copied in order instead of vertex by vertex.
+__global__ void __launch_bounds__(kThreads) k_active_count(const DenseView D, const int32_t* __restrict__ Pout,
+                                                           int32_t* __restrict__ Pin, int64_t n, int64_t n_live,
+                                                           int64_t* __restrict__ tcount,
+                                                           unsigned long long* __restrict__ ccount,
+                                                           const ClassBounds cb, const int32_t* stop) {
+    __shared__ unsigned wsum[kThreads / 32];
+    __shared__ unsigned csum[kDClasses];
+    if (stop != nullptr && *stop >= 2) return;
+    const int64_t count = D.aoff[kDClasses];
+    const bool full = count == n_live;
+    if (full) {
+        const int64_t st = static_cast<int64_t>(gridDim.x) * blockDim.x;
+        for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += st) Pin[i] = Pout[i];
+    }
+    if (threadIdx.x < kDClasses) csum[threadIdx.x] = 0u;
+    __syncthreads();
+    const int64_t tiles = (count + kActTile - 1) / kActTile;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t e0 = t * kActTile + static_cast<int64_t>(threadIdx.x) * kActPer;
+        unsigned keep = 0;
+        int c = 0;
+#pragma unroll
+        for (int k = 0; k < kActPer; ++k) {
+            if (e0 + k < count) {
+                const int32_t pos = D.act[e0 + k];
+                if (!full) {
+                    const int32_t v = D.vert[pos];
+                    Pin[v] = Pout[v];
+                }
+                if (stays_listed(D, pos)) {
+                    ++keep;
+                    while (c + 1 < kDClasses && pos >= cb.b[c + 1]) ++c;      // entries ascend: c only grows
+                    atomicAdd(&csum[c], 1u);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+        if (lane_id() == 0) wsum[threadIdx.x >> 5] = keep;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned tot = 0;
+            for (int w = 0; w < kThreads / 32; ++w) tot += wsum[w];
+            tcount[t] = tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < kDClasses && csum[threadIdx.x])
+        atomicAdd(&ccount[threadIdx.x], static_cast<unsigned long long>(csum[threadIdx.x]));
+}
+
+// Pass 2 (one CTA): exclusive scan of the tile counts; the new length goes to tcount[slot_total].
+__global__ void __launch_bounds__(1024) k_active_scan(const int64_t* __restrict__ aoff, int64_t* __restrict__ tcount,
+                                                      int64_t slot_total, const int32_t* stop) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry;
+    if (stop != nullptr && *stop >= 2) return;
+    const int64_t tiles = (aoff[kDClasses] + kActTile - 1) / kActTile;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < tiles; b += 1024) {
+        const int64_t t = b + threadIdx.x;
+        const int64_t x = t < tiles ? tcount[t] : 0;
+        int64_t inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (static_cast<int>(lane_id()) >= o) inc += y;
+        }
+        if (lane_id() == 31) wsum[threadIdx.x >> 5] = inc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int64_t w = wsum[threadIdx.x];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (static_cast<int>(threadIdx.x) >= o) w += y;
+            }
+            wsum[threadIdx.x] = w;                       // inclusive over warps
+        }
+        __syncthreads();
+        const int64_t before = carry + (threadIdx.x >= 32 ? wsum[(threadIdx.x >> 5) - 1] : 0) + inc - x;
+        if (t < tiles) tcount[t] = before;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = before + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tcount[slot_total] = carry;
+}
+
+// Pass 3: every tile writes its survivors at its offset into the next list.
+__global__ void __launch_bounds__(kThreads) k_active_scatter(const DenseView D, const int64_t* __restrict__ toff,
+                                                             int32_t* __restrict__ next, const int32_t* stop) {
+    __shared__ unsigned wpre[kThreads / 32];
+    if (stop != nullptr && *stop >= 2) return;
+    const int64_t count = D.aoff[kDClasses];
+    const int64_t tiles = (count + kActTile - 1) / kActTile;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t e0 = t * kActTile + static_cast<int64_t>(threadIdx.x) * kActPer;
+        int32_t p[kActPer];
+        unsigned keepm = 0;
+#pragma unroll
+        for (int k = 0; k < kActPer; ++k) {
+            p[k] = e0 + k < count ? D.act[e0 + k] : -1;
+            if (p[k] >= 0 && stays_listed(D, p[k])) keepm |= 1u << k;
+        }
+        const unsigned mine = static_cast<unsigned>(__popc(keepm));
+        unsigned inc = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane_id() >= static_cast<unsigned>(o)) inc += y;
+        }
+        if (lane_id() == 31) wpre[threadIdx.x >> 5] = inc;
+        __syncthreads();
+        unsigned wbase = 0;
+        for (int w = 0; w < static_cast<int>(threadIdx.x >> 5); ++w) wbase += wpre[w];
+        int64_t at = toff[t] + wbase + inc - mine;
+#pragma unroll
+        for (int k = 0; k < kActPer; ++k)
+            if (keepm & (1u << k)) next[at++] = p[k];
+        __syncthreads();
+    }
+}
+
+// Pass 4: the next list replaces the current one; its class offsets from the
+// classes' survivor counts (which are cleared for the next round).
+__global__ void __launch_bounds__(kThreads) k_active_finish(const int32_t* __restrict__ next, int32_t* __restrict__ act,
+                                                            int64_t* __restrict__ aoff, const int64_t* __restrict__ total,
+                                                            unsigned long long* __restrict__ ccount, const int32_t* stop) {
+    if (stop != nullptr && *stop >= 2) return;
+    const int64_t len = *total;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int c = 0; c < kDClasses; ++c) {
+            aoff[c] = run;
+            run += static_cast<int64_t>(ccount[c]);
+            ccount[c] = 0ull;
+        }
+        aoff[kDClasses] = len;
+    }
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < len; i += stride) act[i] = next[i];
+}
+
+// Start of a run of rounds: every live position is listed.
+__global__ void k_active_init(int32_t* __restrict__ act, int64_t n_live, int64_t* __restrict__ aoff,
+                              unsigned long long* __restrict__ ccount, const ClassBounds cb) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t0 <= kDClasses) aoff[t0] = cb.b[t0];
+    if (t0 < kDClasses) ccount[t0] = 0ull;
+    for (int64_t i = t0; i < n_live; i += stride) act[i] = static_cast<int32_t>(i);
 }
 
 constexpr int kCompareGrid = 304;                      // persistent grids: two CTAs per SM
@@ -930,7 +1155,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_compare_cta(const int2* __re
     const unsigned count = *reinterpret_cast<volatile unsigned*>(&st->deferred);
     for (unsigned i = blockIdx.x; i < count; i += gridDim.x) {
         const int2 pr = pairs[i];
-        const int32_t c = D.cnt[pr.y];
+        const int32_t c = D.sig[pr.y].cnt;
         const int64_t ev = D.prp[pr.x], dv = D.prp[pr.x + 1] - ev;
         const int64_t er = D.prp[pr.y], dr = D.prp[pr.y + 1] - er;
         bool miss = false;
@@ -1026,28 +1251,20 @@ __global__ void k_round_check(const DevState* __restrict__ st, LoopState* L, cud
     cudaGraphSetConditional(cond, stop == 0 ? 1u : 0u);
 }
 
-// P_{i+1} becomes the input of the next round, unless the host has to finish this one.
-__global__ void k_round_copy(const int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t n,
-                             const LoopState* __restrict__ L) {
-    if (L->stop >= 2) return;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+// Start of a captured round: the table is blanked when the epoch of this
+// round (rounds run % 15, plus one) starts a new cycle, so a slot written by
+// any earlier round of the cycle carries another epoch and counts as free.
+__global__ void __launch_bounds__(kThreads) k_table_clear_round(const LoopState* __restrict__ L, Slot* slots,
+                                                                uint64_t nslots) {
+    if (L->executed % static_cast<int32_t>(kEpochCycle) != 0) return;
+    uint4* w = reinterpret_cast<uint4*>(slots);          // two slots per 16-byte store
+    const uint64_t words = nslots / 2;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < words; i += stride)
+        w[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // ----------------------------------------------------------------------------- host helpers
-
-WarpPlan warp_plan(const bisim_ctx* ctx) {
-    WarpPlan w;
-    int64_t cta = 0;
-    for (int c = 0; c < 3; ++c) {
-        w.cta_begin[c] = cta;
-        w.pos_begin[c] = ctx->dbegin[kDWarp0 + c];
-        w.pos_end[c] = ctx->dbegin[kDWarp0 + c + 1];
-        cta += cdiv(w.pos_end[c] - w.pos_begin[c], kThreads / 32);
-    }
-    w.cta_begin[3] = cta;
-    return w;
-}
 
 HubSets hub_sets(const bisim_ctx* ctx) {
     return HubSets{ctx->dbegin[kDHub], ctx->n_dhub, ctx->hshift, ctx->hbbase, ctx->bhub, ctx->bcount,
@@ -1060,27 +1277,59 @@ void allow_smem(K kernel, size_t bytes) {
 }
 
 // Algorithmic bytes: the signature kernels move per edge the packed (label,
-// target) word 8 + the gathered P_i[w] 4, per vertex the row offset 8, the
-// vertex id 4, P_i[v] 4 and the 8-byte hash written; the insert moves per
-// vertex the hash 8, the vertex id 4, one 8-byte table slot and the 4-byte slot
-// index; the verification the slot index 4, the vertex id 4, one table slot 8
-// and P_{i+1}[v] 4.
+// target) word 8 + the gathered P_i[w] 4, per vertex the list entry 4, the row
+// offset 8, the vertex id 4, P_i[v] 4 and the 16-byte signature record written
+// (minus the 4-byte list entry: 32); the insert moves per vertex the hash 8,
+// the vertex id 4, one 8-byte table slot and the 4-byte slot index; the
+// verification the slot index 4, the vertex id 4, one table slot 8 and
+// P_{i+1}[v] 4.
 constexpr double kEdgeBytes = 12.0;
-constexpr double kSigVertexBytes = 24.0;
+constexpr double kSigVertexBytes = 32.0;
 constexpr double kInsertVertexBytes = 24.0;
 constexpr double kVerifyVertexBytes = 20.0;
 
 int64_t class_edges(const bisim_ctx* ctx, int c0, int c1) { return ctx->dedge_begin[c1] - ctx->dedge_begin[c0]; }
 
+// Persistent grids: as many CTAs as stay resident on all SMs at once (from the
+// occupancy calculator, per kernel and dynamic shared memory size), so that no
+// CTA waits for a second wave. Looked up before any capture (set_attributes)
+// and cached.
+unsigned resident_grid(const void* kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void*, size_t>, unsigned>> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto& c : cache)
+        if (c.first.first == kernel && c.first.second == smem) return c.second;
+    int dev = 0, sms = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const unsigned g = static_cast<unsigned>(std::max(1, sms) * per_sm);
+    cache.push_back({{kernel, smem}, g});
+    return g;
+}
+
+template <class K>
+unsigned persistent_grid(K kernel, int threads, size_t smem, int64_t ctas_needed) {
+    const unsigned g = resident_grid(reinterpret_cast<const void*>(kernel), threads, smem);
+    return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(g, ctas_needed)));
+}
+
+// The grids of the list-driven kernels are sized for the whole class (the
+// list of round 1) and capped at the resident grid; each kernel reads its
+// class's current entries on the device and strides over them.
 template <int N, int T>
 void launch_mid(bisim_ctx* ctx, int cls, const DenseView& D, cudaStream_t s, int site) {
-    const int64_t first = ctx->dbegin[cls];
-    const int64_t count = ctx->dbegin[cls + 1] - first;
+    const int64_t count = ctx->dbegin[cls + 1] - ctx->dbegin[cls];
     if (count <= 0) return;
     const size_t smem = sizeof(unsigned long long) * 2 * N;
     const int64_t edges = class_edges(ctx, cls, cls + 1);
     Launch L(site, s, count, edges, 0.0);                  // bytes: from the round's work counters
-    k_dense_mid_sig<N, T><<<static_cast<unsigned>(count), T, smem, s>>>(first, D, 4 + (cls - kDMid0));
+    const unsigned grid = persistent_grid(k_dense_mid_sig<N, T>, T, smem, count);
+    k_dense_mid_sig<N, T><<<grid, T, smem, s>>>(cls, D, 4 + (cls - kDMid0));
 }
 
 // Kernel attributes (shared memory above 48 KB), set once before any launch or capture.
@@ -1097,6 +1346,20 @@ void set_attributes() {
         cudaFuncSetAttribute(k_hub_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kHubDedupSmem));
         allow_smem(k_dense_compare_cta, kCompareSmem);
+        persistent_grid(k_dense_thread_sig<8>, kThreads, 0, 1);
+        persistent_grid(k_dense_thread_sig<16>, kThreads, 0, 1);
+        persistent_grid(k_dense_thread_sig<32>, kThreads, 0, 1);
+        persistent_grid(k_dense_warp_sig, kThreads, 0, 1);
+        persistent_grid(k_dense_mid_sig<512, 256>, 256, sizeof(unsigned long long) * 2 * 512, 1);
+        persistent_grid(k_dense_mid_sig<1024, 256>, 256, sizeof(unsigned long long) * 2 * 1024, 1);
+        persistent_grid(k_dense_mid_sig<2048, 512>, 512, sizeof(unsigned long long) * 2 * 2048, 1);
+        persistent_grid(k_dense_mid_sig<4096, 512>, 512, sizeof(unsigned long long) * 2 * 4096, 1);
+        persistent_grid(k_dense_mid_sig<8192, 512>, 512, sizeof(unsigned long long) * 2 * 8192, 1);
+        persistent_grid(k_dense_insert, kThreads, 0, 1);
+        persistent_grid(k_dense_verify, kThreads, 0, 1);
+        persistent_grid(k_active_count, kThreads, 0, 1);
+        persistent_grid(k_active_finish, kThreads, 0, 1);
+        persistent_grid(k_table_clear_round, kThreads, 0, 1);
     });
 }
 
@@ -1117,37 +1380,31 @@ TableRef level_table(bisim_ctx* ctx, cudaStream_t s) {
     return t;
 }
 
-// Insert, verification and set comparisons of one level (level 0: every live
-// position; then the listed ones). Unresolved positions go to `next`.
+// Insert, verification and set comparisons of one level (level 0: the active
+// list, whose length is read on the device; then the listed unresolved
+// positions). Unresolved positions go to `next`.
 void launch_level(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const TableRef& t, uint32_t level,
-                  const int32_t* list, int64_t count, int32_t* next, bool out_has_in = false) {
+                  const int32_t* list, int64_t count, int32_t* next) {
     BISIM_SITE(site_in, "dense_insert");
     BISIM_SITE(site_v, "dense_verify");
     BISIM_SITE(site_cw, "dense_compare_warp");
     BISIM_SITE(site_cc, "dense_compare_cta");
     if (count <= 0) return;
-    int32_t* Pout = ctx->P[ctx->cur ^ 1];
+    int32_t* Pout = ctx->P[1];
     const VerifyOut O{Pout, ctx->dpairs, ctx->dsmall, next, ctx->dstate};
     const HubSets H = hub_sets(ctx);
-    BISIM_SITE(site_as, "dense_alone_scan");
     if (level == 0) {
-        // every live position: the ones alone in their block are done here,
-        // the others are listed (in ulist[1]) for the table passes, whose grid
-        // reads their number on the device
-        {
-            Launch L(site_as, s, count, 0, 11.0 * count);
-            k_alone_scan<<<grid_for(cdiv(count, kScanRun), kThreads), kThreads, 0, s>>>(count, D, Pout, out_has_in,
-                                                                                          ctx->ulist[1], ctx->dstate);
-        }
-        const unsigned grid = static_cast<unsigned>(std::min<int64_t>(kPersistGrid, cdiv(count, kThreads)));
+        // `count` bounds the grid; the kernels read the list's length, and
+        // their bytes follow it (added after the round)
         const unsigned* dcount = &ctx->dstate->listed;
-        // their bytes follow the listed count, added after the round
         {
             Launch L(site_in, s, count, 0, 0.0);
-            k_dense_insert<<<grid, kThreads, 0, s>>>(ctx->ulist[1], 0, dcount, D, 0, t, &ctx->dstate->error);
+            k_dense_insert<<<persistent_grid(k_dense_insert, kThreads, 0, cdiv(count, kThreads)), kThreads, 0, s>>>(
+                ctx->dact, 0, dcount, D, 0, t, &ctx->dstate->error);
         }
         Launch L(site_v, s, count, 0, 0.0);
-        k_dense_verify<<<grid, kThreads, 0, s>>>(ctx->ulist[1], 0, dcount, D, round_slots(ctx), O, ctx->n);
+        k_dense_verify<<<persistent_grid(k_dense_verify, kThreads, 0, cdiv(count, kThreads)), kThreads, 0, s>>>(
+            ctx->dact, 0, dcount, D, round_slots(ctx), O, ctx->n);
     } else {
         {
             Launch L(site_in, s, count, 0, kInsertVertexBytes * count);
@@ -1166,22 +1423,62 @@ void launch_level(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const Tabl
     k_dense_compare_cta<<<kCompareGrid, kThreads, kCompareSmem, s>>>(ctx->dpairs, D, H, Pout, next, ctx->dstate);
 }
 
+// Survivor counts per class at the end of a round: the words after the tile
+// counts and the list's new length in dtile.
+unsigned long long* class_counts(const bisim_ctx* ctx) {
+    return reinterpret_cast<unsigned long long*>(ctx->dtile + ctx->n_tiles + 2);
+}
+
+ClassBounds class_bounds(const bisim_ctx* ctx) {
+    ClassBounds cb;
+    for (int c = 0; c <= kDClasses; ++c) cb.b[c] = ctx->dbegin[c];
+    return cb;
+}
+
+// End of a round: P_{i+1} of the listed vertices into the input buffer and the
+// list compacted to the vertices still not alone (see k_active_count). `stop`
+// is the captured loop's decision, or null for host-driven rounds.
+void launch_round_end(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const int32_t* stop) {
+    BISIM_SITE(site, "active_compact");
+    const int64_t n_live = ctx->dbegin[kDClasses];
+    if (n_live <= 0) return;
+    const unsigned grid = persistent_grid(k_active_count, kThreads, 0, cdiv(n_live, kActTile));
+    const int64_t slot_total = ctx->n_tiles;
+    // bytes: per listed entry the list 4 + vertex 4 + P read 4 + P written 4 + two flags,
+    // then the list and flags again, and 8 per survivor (written, copied)
+    Launch L(site, s, 0, 0, 0.0);
+    unsigned long long* ccount = class_counts(ctx);
+    k_active_count<<<grid, kThreads, 0, s>>>(D, ctx->P[1], ctx->P[0], ctx->n, n_live, ctx->dtile, ccount,
+                                             class_bounds(ctx), stop);
+    k_active_scan<<<1, 1024, 0, s>>>(ctx->daoff, ctx->dtile, slot_total, stop);
+    k_active_scatter<<<grid, kThreads, 0, s>>>(D, ctx->dtile, ctx->dact2, stop);
+    k_active_finish<<<persistent_grid(k_active_finish, kThreads, 0, cdiv(n_live, kThreads)), kThreads, 0, s>>>(
+        ctx->dact2, ctx->dact, ctx->daoff, ctx->dtile + slot_total, ccount, stop);
+}
+
 DenseView dense_view(bisim_ctx* ctx) {
     const bool regions = ctx->rtable != nullptr;
-    return DenseView{ctx->dvert, ctx->dvpos, ctx->dprp, ctx->dpe, ctx->P[ctx->cur], ctx->dcnt, ctx->dhash, ctx->dslot,
+    return DenseView{ctx->dvert, ctx->dvpos, ctx->dprp, ctx->dpe, ctx->P[0], ctx->dsig, ctx->dslot,
                      ctx->djoined, ctx->downs, regions ? ctx->gid : nullptr, ctx->rbase, ctx->rmask,
-                     prof_enabled() ? ctx->dwork : nullptr};
+                     prof_enabled() ? ctx->dwork : nullptr, ctx->dact, ctx->daoff, nullptr};
 }
 
 
-// Everything of one round P[cur] -> P[cur ^ 1] that needs no host decision:
-// signatures of every class, then level 0 of the renumbering.
-// in_loop: the captured loop, whose output buffer already holds P_i.
-void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, bool in_loop = false) {
-    const DenseView D = dense_view(ctx);
+// Everything of one round P[0] -> P[1] that needs no host decision:
+// signatures of the listed vertices of every class, then level 0 of the
+// renumbering. P[1] already holds P_i (the end of the previous round copied
+// it back, and in round 1 every vertex is listed), so vertices alone in
+// their block need no write.
+void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, const int32_t* round_no = nullptr) {
+    DenseView D = dense_view(ctx);
+    D.round_no = round_no;
     const HubSets H = hub_sets(ctx);
     unsigned* err = &ctx->dstate->error;
-    cudaMemsetAsync(ctx->dstate, 0, sizeof(DevState), s);
+    BISIM_SITE(site_rb, "round_begin");
+    {
+        Launch L(site_rb, s, 0, 0, 0.0);
+        k_round_begin<<<1, 1, 0, s>>>(ctx->dstate, ctx->daoff, ctx->dbegin[kDClasses]);
+    }
     if (ctx->n_dhub > 0) {
         cudaMemsetAsync(ctx->bcount, 0, sizeof(unsigned long long) * (ctx->n_buckets + 1), s);   // + the scan's end
         cudaMemsetAsync(ctx->bfill, 0, sizeof(unsigned) * ctx->n_buckets, s);
@@ -1207,17 +1504,16 @@ void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, bool in_loo
         if (verts <= 0) return;
         const int64_t edges = class_edges(ctx, c0, c1);
         Launch L(site, s, verts, edges, 0.0);
-        kernel<<<grid_for(verts, kThreads), kThreads, 0, s>>>(db[c0], verts, D, group);
+        kernel<<<persistent_grid(kernel, kThreads, 0, cdiv(verts, kThreads)), kThreads, 0, s>>>(c0, c1, D, group);
     };
     thread_sig(0, 5, k_dense_thread_sig<8>, site_t8, 0);
     thread_sig(5, 6, k_dense_thread_sig<16>, site_t16, 1);
     thread_sig(6, 7, k_dense_thread_sig<32>, site_t32, 2);
     if (db[kDMid0] > db[kDWarp0]) {
-        const WarpPlan wp = warp_plan(ctx);
         const int64_t verts = db[kDMid0] - db[kDWarp0];
         const int64_t edges = class_edges(ctx, kDWarp0, kDMid0);
         Launch L(site_w, s, verts, edges, 0.0);
-        k_dense_warp_sig<<<static_cast<unsigned>(wp.cta_begin[3]), kThreads, 0, s>>>(wp, D);
+        k_dense_warp_sig<<<persistent_grid(k_dense_warp_sig, kThreads, 0, cdiv(verts, kThreads / 32)), kThreads, 0, s>>>(D);
     }
     launch_mid<512, 256>(ctx, kDMid0 + 0, D, s, site_mid[0]);
     launch_mid<1024, 256>(ctx, kDMid0 + 1, D, s, site_mid[1]);
@@ -1244,7 +1540,7 @@ void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, bool in_loo
         Launch L(site_hf, s, ctx->n_dhub, 0, 0.0);
         k_dense_hub_finalize<<<grid_for(ctx->n_dhub, 128), 128, 0, s>>>(D, H);
     }
-    launch_level(ctx, s, D, t, 0, nullptr, ctx->dbegin[kDClasses], ctx->ulist[0], in_loop);
+    launch_level(ctx, s, D, t, 0, nullptr, ctx->dbegin[kDClasses], ctx->ulist[0]);
 }
 
 // Reads the state of a round whose level 0 has been launched, runs the
@@ -1281,6 +1577,12 @@ void add_round_work(bisim_ctx* ctx, double listed) {
     prof_add_bytes(site_v, kVerifyVertexBytes * listed);
 }
 
+// Algorithmic bytes of the end of a round over `listed` entries with `kept` survivors:
+// per entry the list 4, the vertex id 4, P_{i+1} read 4 and written back 4 and the
+// two flags 2, read again by the scatter (list 4, flags 2); per survivor the
+// position written 4, read and copied 8.
+double round_end_bytes(double listed, double kept) { return 24.0 * listed + 12.0 * kept; }
+
 bisim_status finish_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     cudaError_t e;
     const DenseView D = dense_view(ctx);
@@ -1312,7 +1614,14 @@ bisim_status finish_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {
     if (ctx->hstate->error & kErrHubFull) return set_error(ctx, BISIM_ETIMEOUT, "hub set probe limit reached");
     if (ctx->hstate->error) return set_error(ctx, BISIM_EINVAL, "device reported invalid input");
     *out_blocks = static_cast<int64_t>(ctx->hstate->blocks);
-    ctx->cur ^= 1;
+    launch_round_end(ctx, s, D, nullptr);
+    if (prof_enabled() && ctx->dbegin[kDClasses] > 0) {
+        int64_t kept = 0;
+        cudaMemcpyAsync(&kept, ctx->dtile + ctx->n_tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "compact the active list");
+        BISIM_SITE(site_ac, "active_compact");
+        prof_add_bytes(site_ac, round_end_bytes(static_cast<double>(ctx->hstate->listed), static_cast<double>(kept)));
+    }
     return BISIM_OK;
 }
 
@@ -1328,14 +1637,19 @@ bisim_status alloc_round_state(bisim_ctx* ctx, cudaStream_t s) {
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dvpos), sizeof(int32_t) * nv, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dprp), sizeof(int64_t) * (nv + 1), s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dslot), sizeof(uint32_t) * nv, s)) ||
-        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dhash), sizeof(unsigned long long) * nv, s)) ||
-        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dcnt), sizeof(int32_t) * nv, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dsig), sizeof(SigRec) * nv, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dpairs), sizeof(int2) * nv, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dsmall), sizeof(int2) * nv, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dwork), sizeof(unsigned long long) * kWorkWords, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->djoined), nv, s)) ||
         (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->downs), nv, s)))
         return cuda_error(ctx, e, "alloc dense round state");
+    ctx->n_tiles = cdiv(static_cast<int64_t>(nv), kActTile);
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dact), sizeof(int32_t) * nv, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dact2), sizeof(int32_t) * nv, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->daoff), sizeof(int64_t) * (kDClasses + 1), s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dtile), sizeof(int64_t) * (ctx->n_tiles + 2 + kDClasses), s)))
+        return cuda_error(ctx, e, "alloc active list");
     return BISIM_OK;
 }
 
@@ -1607,8 +1921,15 @@ bisim_status ensure_vertex_csr(bisim_ctx* ctx, cudaStream_t s) {
 }
 
 void dense_start(bisim_ctx* ctx, cudaStream_t s) {
-    // P_0's block sizes are not known: no vertex counts as alone in the first round
+    // P_0's block sizes are not known: every live position is listed, and no
+    // hub counts as alone in the first round
     if (ctx->n > 0) cudaMemsetAsync(ctx->djoined, 1, static_cast<size_t>(ctx->n), s);
+    const int64_t n_live = ctx->dbegin[kDClasses];
+    BISIM_SITE(site, "active_init");
+    Launch L(site, s, n_live, 0, 4.0 * n_live);
+    k_active_init<<<static_cast<unsigned>(std::min<int64_t>(kPersistGrid, cdiv(std::max<int64_t>(n_live, kDClasses + 1),
+                                                                                kThreads))),
+                    kThreads, 0, s>>>(ctx->dact, n_live, ctx->daoff, class_counts(ctx), class_bounds(ctx));
     dense_mark_dead(ctx, s);
 }
 
@@ -1633,8 +1954,9 @@ bisim_status dense_finish_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blo
 
 namespace {
 
-// The captured rounds clear the table at the start of every round and use one
-// fixed epoch; the eager rounds' epochs (next_epoch) never reuse it without a clear.
+// The table of the captured rounds. Its epoch field is only a placeholder: the
+// insert takes round r's epoch (r % 15 + 1) from the loop state, and the table
+// is blanked whenever that epoch starts a new cycle (k_table_clear_round).
 TableRef fixed_table(const bisim_ctx* ctx) {
     TableRef t;
     t.slots = round_slots(ctx);
@@ -1646,8 +1968,10 @@ TableRef fixed_table(const bisim_ctx* ctx) {
 }
 
 // The round loop as one graph: a while node whose body is one round (table
-// clear, signatures, level 0 of the renumbering), the loop check and the copy
-// of P_{i+1} into the input buffer. The body reads P[0] and writes P[1].
+// clear when the epoch cycle restarts, signatures and level 0 of the
+// renumbering over the active list), the loop check, and the end of the round
+// (P_{i+1} of the listed vertices copied into the input buffer, the list
+// compacted). The body reads P[0] and writes P[1].
 bisim_status build_round_graph(bisim_ctx* ctx) {
     set_attributes();
     cudaError_t e;
@@ -1685,24 +2009,26 @@ bisim_status build_round_graph(bisim_ctx* ctx) {
     ctx->cur = 0;
     const int64_t before = bisim_launch_count();
     BISIM_SITE(site_ck, "round_check");
-    BISIM_SITE(site_cp, "round_copy");
+    BISIM_SITE(site_tc, "table_clear");
     if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal))) {
         ctx->cur = cur;
         cudaGraphDestroy(g);
         return cuda_error(ctx, e, "capture round");
     }
-    cudaMemsetAsync(round_slots(ctx), 0, sizeof(Slot) * (ctx->rtable ? ctx->n_rslots : ctx->nslots), cs);
-    launch_round(ctx, cs, fixed_table(ctx), true);
     LoopState* L = static_cast<LoopState*>(ctx->dloop);
+    {
+        const uint64_t ns = ctx->rtable ? ctx->n_rslots : ctx->nslots;     // a power of two >= 64
+        Launch Lk(site_tc, cs, 0, 0, 0.0);
+        k_table_clear_round<<<persistent_grid(k_table_clear_round, kThreads, 0,
+                                              static_cast<int64_t>((ns / 2 + kThreads - 1) / kThreads)),
+                              kThreads, 0, cs>>>(L, round_slots(ctx), ns);
+    }
+    launch_round(ctx, cs, fixed_table(ctx), &L->executed);
     {
         Launch Lk(site_ck, cs, 0, 0, 0.0);
         k_round_check<<<1, 1, 0, cs>>>(ctx->dstate, L, cond);
     }
-    {
-        Launch Lk(site_cp, cs, ctx->n, 0, 8.0 * ctx->n);
-        k_round_copy<<<grid_for(std::min<int64_t>(ctx->n, int64_t{1} << 22), 256), 256, 0, cs>>>(ctx->P[1], ctx->P[0],
-                                                                                                 ctx->n, L);
-    }
+    launch_round_end(ctx, cs, dense_view(ctx), &L->stop);
     e = cudaStreamEndCapture(cs, &body);
     ctx->cur = cur;
     ctx->round_graph_launches = bisim_launch_count() - before;
@@ -1741,6 +2067,9 @@ bisim_status dense_graph_rounds(bisim_ctx* ctx, cudaStream_t s, int32_t limit, b
     cudaMemcpyAsync(ctx->dloop, h, sizeof(LoopState), cudaMemcpyHostToDevice, s);
     if ((e = cudaGraphLaunch(static_cast<cudaGraphExec_t>(ctx->round_graph), s))) return cuda_error(ctx, e, "launch round graph");
     cudaMemcpyAsync(h, ctx->dloop, sizeof(LoopState), cudaMemcpyDeviceToHost, s);
+    // the loop's slots carry epochs of its own: the next host-driven level of
+    // the global table (next_epoch) must start from a blank table
+    ctx->epoch32 = kEpochCycle;
     if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "round graph");
     prof_add_launches(ctx->round_graph_launches * h->executed);
     out->executed = h->executed;
