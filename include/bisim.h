@@ -105,9 +105,11 @@ typedef struct {
                                   collisions and exist to test the exact check; results are
                                   identical at every width, only slower. */
     int32_t small_max_degree;  /* out-degree <= this: one thread per vertex (default 32, max 32) */
-    int32_t mid_max_degree;    /* out-degree <= this: one CTA per vertex, keys staged in shared
-                                  memory (default 8192, max 8192); above it: hub path, many CTAs
-                                  per vertex with a global dedup table */
+    int32_t mid_max_degree;    /* out-degree <= this: one warp (up to 256) or one CTA per vertex,
+                                  pair values deduplicated in a shared-memory set (default 8192,
+                                  max 8192); above it: hub path, the row cut into chunks over many
+                                  CTAs, its pair values bucketed by a mix of their bits and each
+                                  bucket deduplicated by one CTA in shared memory */
     int32_t hub_chunk;         /* edges per CTA on the hub path (default 4096, 256..4096) */
     int32_t flags;             /* BISIM_FLAG_* bits (default 0) */
     int64_t mem_budget_bytes;  /* refuse (BISIM_ENOMEM) contexts whose device footprint would

@@ -60,13 +60,19 @@ void setup_pool(int device) {
     });
 }
 
+// Whether the kernels of the current device may read `p` in place: managed
+// memory, or device memory of the current device. Memory of another GPU is
+// not (no peer mapping is assumed): it is staged through a copy like host memory.
 bool device_accessible(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    if (a.type != cudaMemoryTypeDevice) return false;
+    int cur = -1;
+    return cudaGetDevice(&cur) == cudaSuccess && a.device == cur;
 }
 
 // Device-resident view of a caller array: the array itself if the GPU can

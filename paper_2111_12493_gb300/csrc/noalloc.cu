@@ -84,13 +84,17 @@ cudaError_t scratch_address(int device, unsigned char** out) {
     return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// Whether the kernels of `device` may read or write `p` in place: managed
+// memory, or device memory of that same device (memory of another GPU would
+// need a peer mapping, which this call does not assume).
+bool on_device(const void* p, int device) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 int mid_class_for(int64_t maxdeg) {
@@ -122,14 +126,15 @@ extern "C" bisim_status bisim_refine_round_noalloc(int32_t n_vertices, int64_t n
     if (row_ptr == nullptr || block_in == nullptr || block_out == nullptr ||
         (m > 0 && (col == nullptr || edge_label == nullptr)))
         return set_error(nullptr, BISIM_EINVAL, "a required array is NULL");
-    if (!on_device(row_ptr) || !on_device(block_in) || !on_device(block_out) ||
-        (m > 0 && (!on_device(col) || !on_device(edge_label))))
-        return set_error(nullptr, BISIM_EINVAL, "the allocation-free round needs device-resident arrays");
-    if (block_in == block_out) return set_error(nullptr, BISIM_EINVAL, "block_in and block_out must differ");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e) return cuda_error(nullptr, e, "cudaGetDevice");
+    if (!on_device(row_ptr, device) || !on_device(block_in, device) || !on_device(block_out, device) ||
+        (m > 0 && (!on_device(col, device) || !on_device(edge_label, device))))
+        return set_error(nullptr, BISIM_EINVAL,
+                         "the allocation-free round needs arrays in the current device's memory");
+    if (block_in == block_out) return set_error(nullptr, BISIM_EINVAL, "block_in and block_out must differ");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* base = nullptr;
     if ((e = scratch_address(device, &base))) return cuda_error(nullptr, e, "cudaGetSymbolAddress(scratch)");
 
@@ -150,6 +155,8 @@ extern "C" bisim_status bisim_refine_round_noalloc(int32_t n_vertices, int64_t n
         k_noalloc_prepare<<<static_cast<unsigned>(std::min<int64_t>((work + 255) / 256, 4096)), 256, 0, s>>>(
             row_ptr, col, n, m, list, dstate);
     }
+    // a launch that failed would leave the status word blank (largest degree 0)
+    if ((e = cudaGetLastError())) return cuda_error(nullptr, e, "check CSR");
     cudaMemcpyAsync(&host_state, dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) return cuda_error(nullptr, e, "check CSR");
     if (host_state.error & kErrBadInput)
@@ -159,7 +166,8 @@ extern "C" bisim_status bisim_refine_round_noalloc(int32_t n_vertices, int64_t n
         return set_error(nullptr, BISIM_EINVAL, "an out-degree exceeds the allocation-free limit of 8192");
 
     // A context on the stack whose every buffer lies in the fixed array: all
-    // vertices go through the shared-memory (CTA) signature path.
+    // vertices go through one degree class sized for the largest out-degree
+    // (a warp per vertex up to 256 edges, a CTA per vertex above).
     bisim_ctx tc;
     tc.n = n;
     tc.m = m;
