@@ -16,9 +16,17 @@ get_partition, through the C-ABI.
            its algorithmic bytes / its summed launch time, against the measured
            HBM copy bandwidth
 
---impl reference times the CPU oracle (exact signatures in an ordered map)
-on a bounded sample of the same workload. --gpus N > 1 runs N independent
-replicas (the refinement of one graph has no sharded form here), one per rank.
+  rounds_roofline = per refinement round: the algorithmic bytes of the rows and
+           vertices that round processed (12 B per row entry + 44 B per listed
+           vertex, counted on the device) over the round's event time
+  cpu_baseline = the oracle (exact signatures in an ordered map) on the same
+           graph: one thread on a range of the vertices, and the same round
+           on all host cores
+
+--impl reference times the CPU oracle on the same graph: each step is one
+exact refinement round over the next 1/K of the vertices, so K steps cover one
+whole round. --gpus N > 1 runs N independent replicas (the refinement of one
+graph has no sharded form here), one per rank.
 """
 
 from __future__ import annotations
@@ -50,6 +58,12 @@ NCU_TRAFFIC_BYTES = {
     # the items, so x2 for the 100M-edge launch. Algorithmic: 24 B per item, 2.4 GB per launch.
     "radix_scatter": 2 * (715.0e6 + 639.4e6),
 }
+# Per-round algorithmic bytes of a refinement round (the row entries and vertices it processed).
+ROUND_EDGE_BYTES = 12.0     # packed (label, target) word 8 + gathered block id 4
+ROUND_VERTEX_BYTES = 44.0   # row offset 4 + own block 4 + new block written 4 + two 16-byte table accesses
+SIG_SITES = ("dense_thread_sig_8", "dense_thread_sig_16", "dense_thread_sig_32", "dense_warp_sig",
+             "dense_mid_512", "dense_mid_1024", "dense_mid_2048", "dense_mid_4096", "dense_mid_8192",
+             "hub_count", "dense_hub_finalize")
 
 
 def parse_args():
@@ -71,9 +85,11 @@ def parse_args():
     ap.add_argument("--union-rounds", action="store_true",
                     help="batched workload: run the union through the single-graph round kernels instead of the "
                          "persistent per-graph kernel")
-    ap.add_argument("--workload", default="powerlaw", choices=["powerlaw", "chain", "batched"],
+    ap.add_argument("--workload", default="powerlaw", choices=["powerlaw", "chain", "paths", "batched"],
                     help="powerlaw: 10M/100M to the fixpoint (the headline); chain: 1000 paths of 1000 "
-                         "+ 2M random edges to the fixpoint; batched: 4096 graphs in one context, k=3")
+                         "+ 2M random edges to the fixpoint; paths: 1000 paths of 1000 with one vertex and one "
+                         "edge label (999 rounds, every vertex listed in each); batched: 4096 graphs in one "
+                         "context, k=3")
     return ap.parse_args()
 
 
@@ -104,6 +120,12 @@ class Workload:
             self.k, self.cap = -1, 10_000
             self.arrays = [g[k] for k in ("src", "dst", "elabel", "vlabel")]
             self.graph = g
+        elif name == "paths":
+            paths = max(10, int(1000 * scale))
+            g = graphgen.chain_graph(n_paths=paths, path_len=1000, extra=0, n_elabels=1, n_vlabels=1, seed=3)
+            self.k, self.cap = -1, 10_000
+            self.arrays = [g[k] for k in ("src", "dst", "elabel", "vlabel")]
+            self.graph = g
         else:
             b = graphgen.batched_graphs(n_graphs=max(8, int(4096 * scale)), seed=4)
             self.k, self.cap = 3, 0
@@ -123,6 +145,14 @@ class Workload:
                              f"2 vertex labels; refine to the fixpoint (cap 10000)",
                  "n_vertices": self.n, "n_edges": self.m, "k": "fixpoint", "cap": 10_000,
                  "l2": "inputs smaller than L2 (36 MB COO): a latency-bound many-round workload"}
+        elif self.name == "paths":
+            d = {"workload": f"{self.n // 1000:,} directed paths of 1000 vertices (path-major ids), one vertex "
+                             f"label and one edge label; refine to the fixpoint (cap 10000): every round splits "
+                             f"one vertex off each path and every vertex stays listed, 999 rounds (the long "
+                             f"k-chaining regime; a supplement to the chains configuration, whose random extra "
+                             f"edges separate the paths by round 4)",
+                 "n_vertices": self.n, "n_edges": self.m, "k": "fixpoint", "cap": 10_000,
+                 "l2": "inputs smaller than L2 (12 MB COO): a latency-bound many-round workload"}
         else:
             ng = np.diff(g["vertex_offsets"])
             d = {"workload": f"{g['n_graphs']:,} independent graphs in one context, vertex counts log-uniform "
@@ -251,6 +281,70 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- per-round roofline
+
+def _iterate_ms(bisim, torch, ctx, k, stream, reps=3):
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bisim.bisim_iterate(ctx, k, 0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return best
+
+
+def _round_work(bisim, ctx, k):
+    """Listed vertices and row entries processed by k rounds from P_0 (device-counted)."""
+    bisim.bisim_profile_reset()
+    bisim.bisim_profile_enable(True)
+    bisim.bisim_iterate(ctx, k, 0)
+    bisim.bisim_profile_enable(False)
+    prof = {p["name"]: p for p in bisim.bisim_profile_read()}
+    listed = prof.get("dense_insert", {}).get("vertices", 0)
+    entries = sum(prof.get(n, {}).get("edges", 0) for n in SIG_SITES)
+    return listed, entries
+
+
+def rounds_roofline(bisim, torch, W, d_in, stream, peak, executed):
+    """Per round i: survey bytes of the rows and vertices it processed / its event time.
+
+    Round i's time is T(i) - T(i-1), T(k) the best event time of bisim_iterate(k)
+    on a resident context (captured device-side loop); its work is counted on the
+    device in an eager profiled run of the same k. Workloads with many rounds
+    report rounds 1-3 and the mean of the rest."""
+    ctx = W.init_only(bisim, d_in)
+    bisim.bisim_iterate(ctx, W.k, W.cap)            # captures the round graph
+    ks = list(range(0, executed + 1)) if executed <= 12 else [0, 1, 2, 3, executed]
+    T = {k: _iterate_ms(bisim, torch, ctx, k, stream) for k in ks}
+    work = {0: (0, 0)}
+    for k in ks[1:]:
+        work[k] = _round_work(bisim, ctx, k)
+    bisim.summarize_destroy(ctx)
+    out = []
+    for a, b in zip(ks[:-1], ks[1:]):
+        ms = T[b] - T[a]
+        listed = work[b][0] - work[a][0]
+        entries = work[b][1] - work[a][1]
+        byts = ROUND_EDGE_BYTES * entries + ROUND_VERTEX_BYTES * listed
+        gbs = byts / (ms / 1e3) / 1e9 if ms > 0 else None
+        out.append({"rounds": f"{a + 1}" if b == a + 1 else f"{a + 1}-{b} (mean)", "ms": round(ms / (b - a), 4),
+                    "listed_vertices": int(listed / (b - a)), "row_entries": int(entries / (b - a)),
+                    "alg_bytes": byts / (b - a), "GB/s": round(gbs, 1) if gbs else None,
+                    "frac": round(gbs / peak, 4) if gbs else None})
+    plain = ROUND_EDGE_BYTES * W.m + ROUND_VERTEX_BYTES * W.n
+    total_ms = T[ks[-1]] - T[0]
+    return {"per_round": out, "unit": "GB/s", "peak": peak,
+            "bytes_formula": "12 B per row entry processed + 44 B per listed vertex (counted on the device)",
+            "plain_round_effective": {
+                "GB/s": round(plain * executed / (total_ms / 1e3) / 1e9, 1),
+                "note": "every executed round credited with a plain round's bytes (12 B per edge + 44 B per "
+                        "vertex), although rounds after the first skip the vertices alone in their block: an "
+                        "effective rate, not achieved bandwidth"}}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -395,10 +489,19 @@ def run_ours(args, world, rank, local):
                     "traffic": traffic, "alg_bytes_per_launch": top["alg_bytes"] / max(1, top["launches"]),
                     "avg_launch_ms": top["total_ms"] / max(1, top["launches"]),
                     "share_of_kernel_time": round(top["total_ms"] / total_kernel_ms, 4)}
+        if traffic is not None:
+            roofline["traffic_vs_alg"] = round(traffic / roofline["alg_bytes_per_launch"], 3)
+            roofline["traffic_note"] = ("ncu DRAM bytes of one pass over 50M items x2 (traffic grows with the "
+                                        "items); every launch of this site is a pass over all edges, so the "
+                                        "per-launch figures describe the same launch")
         kernels = sorted(({"name": p["name"], "launches": p["launches"], "ms": round(p["total_ms"], 3),
                            "share": round(p["total_ms"] / total_kernel_ms, 4),
                            "GB/s": round(p["alg_bytes"] / (p["total_ms"] / 1e3) / 1e9, 1) if p["total_ms"] else None}
                           for p in prof if p["launches"]), key=lambda x: -x["ms"])[:12]
+
+    rr = None
+    if not W.batched:
+        rr = rounds_roofline(bisim, torch, W, d_in, stream, peak, int(it_exec))
 
     serving_info = None
     if not args.no_serving and W.name == "powerlaw":
@@ -406,7 +509,7 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.scale, W)
+        cpu = cpu_baseline(W)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -414,6 +517,9 @@ def run_ours(args, world, rank, local):
             "data": "synthetic (seeded generator; stands in for the paper's BSBM/DyLDO graphs)",
             "config": W.config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                                 "rounds": int(rounds), "rounds_executed": int(executed), "blocks": int(blocks),
+                                "edge_iterations": f"edges x rounds_executed ({int(executed)}) per step; r = "
+                                                   f"{int(rounds)} is the result, the round after it confirms "
+                                                   f"the fixpoint and is counted because it runs",
                                 "autotuned": None if tuned is None else
                                 {k: tuned[k] for k in ("small_max_degree", "mid_max_degree", "hub_chunk")}}),
             "iterate_only": {"value": iterate_only, "unit": UNIT, "rounds_executed": int(it_exec),
@@ -421,7 +527,7 @@ def run_ours(args, world, rank, local):
             "profiled_steps": {"ms_per_step": profiled_ms / args.steps,
                                "note": "the timed steps again with per-launch CUDA events (rounds run eagerly); "
                                        "kernels and roofline come from these"},
-            "e2e": e2e, "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu,
+            "e2e": e2e, "roofline": roofline, "rounds_roofline": rr, "kernels": kernels, "cpu_baseline": cpu,
             "gpu_launches": int(launches), "clocks": clock_info,
             "buckets": {"small": stats["n_small"], "mid": stats["n_mid"], "hub": stats["n_hub"]},
             "collision_levels": stats["collision_levels"], "serving": serving_info}
@@ -541,65 +647,97 @@ def run_serving(args, local):
 
 # ----------------------------------------------------------------------------- oracle on the host cores
 
-def cpu_sample_graph(scale, workload="powerlaw"):
-    """A bounded sample of the workload that one oracle round finishes in ~10 s."""
+def oracle_graph(W):
+    """The graph the CPU baselines run on: the workload's own graph (for the
+    batched workload, the union of its first 512 graphs)."""
     from paper_2111_12493_gb300 import graphgen
-    if workload == "chain":
-        return graphgen.chain_graph(n_paths=max(10, int(1000 * scale)), path_len=1000,
-                                    extra=int(2_000_000 * scale), seed=3), "the whole graph"
-    if workload == "batched":
-        b = graphgen.batched_graphs(n_graphs=max(8, int(512 * scale)), seed=4)
-        u = graphgen.batched_union(b)
-        return u, f"the union of the first {b['n_graphs']} graphs of the generator"
-    # a quarter-size instance of the same generator
-    n = max(1000, int(2_500_000 * scale))
-    m = max(10_000, int(25_000_000 * scale))
-    g = graphgen.powerlaw_graph(n=n, m=m, exponent=WORKLOAD["exponent"], dmax=min(WORKLOAD["dmax"], m // 10),
-                                n_elabels=WORKLOAD["n_elabels"], n_vlabels=WORKLOAD["n_vlabels"],
-                                untyped_frac=WORKLOAD["untyped"], seed=WORKLOAD["seed"])
-    return g, "a quarter-size instance of the same generator"
+    if W.batched:
+        b = graphgen.batched_graphs(n_graphs=min(512, int(W.graph["n_graphs"])), seed=4)
+        return graphgen.batched_union(b), f"the union of the first {b['n_graphs']} graphs of the generator"
+    return W.graph, "the same graph"
 
 
-def time_oracle_round(g):
+def _ranges(n, parts):
+    cuts = [n * i // parts for i in range(parts + 1)]
+    return list(zip(cuts[:-1], cuts[1:]))
+
+
+def _range_edges(g, ranges):
+    """Edges whose source lies in each vertex range (the edges one range's round processes)."""
+    cnt = np.bincount(g["src"], minlength=g["n"]).astype(np.int64)
+    pre = np.concatenate([[0], np.cumsum(cnt)])
+    return [int(pre[b] - pre[a]) for a, b in ranges]
+
+
+def time_oracle_range(g, P0, v0, v1, out):
     import oracle
-    P0 = oracle.label_partition(g["n"], g["vlabel"], graph=g.get("graph"))
     t0 = time.perf_counter()
-    oracle.refine_round(g["n"], g["src"], g["dst"], g["elabel"], g["vlabel"], P0, graph=g.get("graph"))
+    oracle.refine_round_range(g["n"], g["src"], g["dst"], g["elabel"], g["vlabel"], P0, v0, v1, out=out,
+                              graph=g.get("graph"))
     return time.perf_counter() - t0
 
 
-def cpu_baseline(scale, W=None):
-    g, what = cpu_sample_graph(scale, W.name if W else "powerlaw")
-    dt = time_oracle_round(g)
+def cpu_baseline(W):
+    """The oracle as it stands on the host cores: one thread over 1/8 of the
+    vertices of one exact round, and the same round over all vertices on every
+    host thread (the multi-threaded restatement, pinned to the oracle)."""
+    import oracle
+    g, what = oracle_graph(W)
+    n = g["n"]
+    P0 = oracle.label_partition(n, g["vlabel"], graph=g.get("graph"))
+    parts = 8 if n >= 1_000_000 else 1
+    (v0, v1), = _ranges(n, parts)[:1]
+    m_range = _range_edges(g, [(v0, v1)])[0]
+    out = np.empty(n, np.int32)
+    dt = time_oracle_range(g, P0, v0, v1, out)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.refine_round_threads(n, g["src"], g["dst"], g["elabel"], P0, threads=threads, graph=g.get("graph"))
+    dt_all = time.perf_counter() - t0
     m = len(g["src"])
-    return {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one exact refinement round P_0 -> P_1 on {what} ({g['n']:,} vertices / {m:,} edges), "
-                      f"single-threaded C++ oracle, {dt:.1f} s"}
+    return {"value": m_range / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "host_cores": threads,
+            "sample": f"one exact refinement round P_0 -> P_1 over vertices [{v0:,}, {v1:,}) of {what} "
+                      f"({n:,} vertices / {m:,} edges; {m_range:,} edges in the range), single-threaded C++ "
+                      f"oracle, {dt:.1f} s",
+            "all_cores": {"value": m / dt_all, "unit": UNIT, "cores": threads, "kind": "oracle, threaded",
+                          "sample": f"the whole round P_0 -> P_1 of {what} on {threads} host threads "
+                                    f"(the oracle's round with signatures gathered and maps built per shard in "
+                                    f"parallel), {dt_all:.1f} s"}}
 
 
 def run_reference(args, world, rank):
+    """The CPU oracle on the same workload: step j is one exact refinement round
+    P_0 -> P_1 over the j-th of `steps` consecutive vertex ranges, so the timed
+    steps together cover one whole round of the full graph; warm-up steps repeat
+    the first range."""
     if rank != 0:
         return
-    extra = {"parallelism": "single CPU thread", "note": "oracle timed on a bounded sample of the workload"}
-    if args.workload == "powerlaw":
-        config = config_dict(max(1000, int(WORKLOAD["n"] * args.scale)), max(10_000, int(WORKLOAD["m"] * args.scale)),
-                             extra=extra)
-    else:
-        config = Workload(args.workload, args.scale).config(extra)
-    g, what = cpu_sample_graph(args.scale, args.workload)
-    m = len(g["src"])
+    import oracle
+    W = Workload(args.workload, args.scale)
+    g, what = oracle_graph(W)
+    n = g["n"]
+    P0 = oracle.label_partition(n, g["vlabel"], graph=g.get("graph"))
+    ranges = _ranges(n, max(1, args.steps))
+    medges = _range_edges(g, ranges)
+    out = np.empty(n, np.int32)
     for _ in range(args.warmup):
-        time_oracle_round(g)
-    t = [time_oracle_round(g) for _ in range(args.steps)]
+        time_oracle_range(g, P0, ranges[0][0], ranges[0][1], out)
+    t = [time_oracle_range(g, P0, a, b, out) for a, b in ranges]
     total = sum(t)
-    value = m * args.steps / total
+    value = sum(medges) / total
+    extra = {"parallelism": "single CPU thread",
+             "note": f"the oracle on {what}; each step one exact round over 1/{len(ranges)} of the vertices"}
+    config = W.config(extra)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ranges),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32 ids (exact signatures, no hashing)", "data": "synthetic",
-            "config": config, "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                               "sample": f"one exact refinement round per step on {what} "
-                                                         f"({g['n']:,} vertices / {m:,} edges)"},
+            "config": config,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "host_cores": os.cpu_count(),
+                             "sample": f"one exact refinement round P_0 -> P_1 per step over consecutive vertex "
+                                       f"ranges of {what} ({n:,} vertices / {len(g['src']):,} edges); the "
+                                       f"{len(ranges)} steps cover the whole round"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -26,6 +26,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bisim_oracle.cpp")
+_SRC_THREADS = os.path.join(_HERE, "bisim_oracle_threads.cpp")
 _LIB = os.path.join(_HERE, "libbisim_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -47,9 +48,10 @@ OP_VERTEX_DEL = 3
 
 def build(force: bool = False) -> str:
     """Compile the oracle shared library with the host C++ compiler."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    srcs = [_SRC, _SRC_THREADS]
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in srcs):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-o", tmp, *srcs])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -66,6 +68,10 @@ def _load():
             lib.oracle_refine.restype = ctypes.c_int
             lib.oracle_round.argtypes = [i32, p, p, p, i64, p, p, p, p, i32, p]
             lib.oracle_round.restype = ctypes.c_int
+            lib.oracle_round_range.argtypes = [i32, p, p, p, i64, p, p, p, p, i32, i32, p]
+            lib.oracle_round_range.restype = ctypes.c_int
+            lib.oracle_round_threads.argtypes = [i32, p, p, i64, p, p, p, p, i32, p]
+            lib.oracle_round_threads.restype = ctypes.c_int
             lib.oracle_label_partition.argtypes = [i32, p, p, p, p]
             lib.oracle_label_partition.restype = ctypes.c_int
             lib.oracle_apply_ops.argtypes = [i32, p, p, i64, p, p, p, i32, p, p, i64, p, p, p, p, p]
@@ -118,6 +124,35 @@ def refine_round(n, src, dst, elabel, vlabel, P, alive=None, graph=None, variant
                           _ptr(dst), _ptr(elabel), _ptr(P), variant, _ptr(out))
     if rc != 0:
         raise ValueError(f"oracle_round rejected its input (code {rc})")
+    return out
+
+
+def refine_round_range(n, src, dst, elabel, vlabel, P, v0, v1, out=None, alive=None, graph=None):
+    """One exact round restricted to the vertices [v0, v1) (block ids: smallest
+    vertex of the range with the same signature); `out` outside the range is
+    left as it is. The CPU baseline times ranges of a large graph with it."""
+    lib = _load()
+    src, dst, elabel, vlabel, graph, P = map(_i32, (src, dst, elabel, vlabel, graph, P))
+    alive = None if alive is None else np.ascontiguousarray(alive, dtype=np.uint8)
+    out = np.full(n, -2, dtype=np.int32) if out is None else out
+    rc = lib.oracle_round_range(n, _ptr(alive), _ptr(vlabel), _ptr(graph), len(src), _ptr(src), _ptr(dst),
+                                _ptr(elabel), _ptr(P), int(v0), int(v1), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_round_range rejected its input (code {rc})")
+    return out
+
+
+def refine_round_threads(n, src, dst, elabel, P, threads=0, alive=None, graph=None):
+    """The same round as refine_round on `threads` host threads (0: all of them);
+    a CPU baseline that uses every core, pinned to refine_round by the tests."""
+    lib = _load()
+    src, dst, elabel, graph, P = map(_i32, (src, dst, elabel, graph, P))
+    alive = None if alive is None else np.ascontiguousarray(alive, dtype=np.uint8)
+    out = np.empty(n, dtype=np.int32)
+    rc = lib.oracle_round_threads(n, _ptr(alive), _ptr(graph), len(src), _ptr(src), _ptr(dst), _ptr(elabel),
+                                  _ptr(P), int(threads), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_round_threads rejected its input (code {rc})")
     return out
 
 

@@ -84,23 +84,26 @@ void label_partition(const Graph& G, int32_t* P0) {
 }
 
 // One refinement round: vertices stay together iff they were together and
-// their sets of (edge label, neighbour block) agree.
-void refine_round(const Graph& G, const int32_t* P, int32_t variant, int32_t* Pnext) {
+// their sets of (edge label, neighbour block) agree. Only the vertices of
+// [v0, v1) are refined (the whole round is [0, n)); a vertex range lets the
+// CPU baseline time a bounded part of a large graph's round.
+void refine_round(const Graph& G, const int32_t* P, int32_t variant, int32_t* Pnext, int32_t v0, int32_t v1) {
     std::vector<std::vector<Pair>> S(G.n);
     for (int64_t e = 0; e < G.m; ++e) {
         int32_t v = G.src[e], w = G.dst[e];
         if (!G.is_alive(v) || !G.is_alive(w)) continue;
         if (variant & VARIANT_REVERSE) std::swap(v, w);
+        if (v < v0 || v >= v1) continue;
         int32_t l = (variant & VARIANT_DROP_EDGE_LABEL) ? 0 : G.elabel[e];
         S[v].emplace_back(l, P[w]);
     }
-    for (int32_t v = 0; v < G.n; ++v) {
+    for (int32_t v = v0; v < v1; ++v) {
         std::sort(S[v].begin(), S[v].end());
         if (!(variant & VARIANT_MULTISET))
             S[v].erase(std::unique(S[v].begin(), S[v].end()), S[v].end());
     }
     std::map<Signature, int32_t> rep;
-    for (int32_t v = 0; v < G.n; ++v) {
+    for (int32_t v = v0; v < v1; ++v) {
         if (!G.is_alive(v)) { Pnext[v] = -1; continue; }
         int32_t a = P[v], b = 0;
         if (variant & VARIANT_OWN_LABEL) { a = G.graph_of(v); b = G.vlabel[v]; }
@@ -142,7 +145,7 @@ int oracle_refine(int32_t n, const uint8_t* alive, const int32_t* vlabel, const 
     int32_t rounds = 0, executed = 0;
     if (k >= 0) {
         for (int32_t i = 0; i < k; ++i) {
-            refine_round(G, P.data(), variant, Q.data());
+            refine_round(G, P.data(), variant, Q.data(), 0, n);
             P.swap(Q);
             ++executed;
             record(executed, P);
@@ -151,7 +154,7 @@ int oracle_refine(int32_t n, const uint8_t* alive, const int32_t* vlabel, const 
     } else {
         rounds = cap;
         for (int32_t i = 0; i < cap; ++i) {
-            refine_round(G, P.data(), variant, Q.data());
+            refine_round(G, P.data(), variant, Q.data(), 0, n);
             ++executed;
             if (same(P, Q)) { rounds = i; break; }
             P.swap(Q);
@@ -166,9 +169,7 @@ int oracle_refine(int32_t n, const uint8_t* alive, const int32_t* vlabel, const 
 
 // One round from a given partition P (int32[n], -1 for dead vertices):
 // writes P_next. Used to check a refinement round at sizes where a full run
-// from P_0 would take too long. If `vertex_begin < vertex_end` the signature
-// map is built over all vertices but only [vertex_begin, vertex_end) is
-// written -- the other entries of out_P are left untouched.
+// from P_0 would take too long.
 int oracle_round(int32_t n, const uint8_t* alive, const int32_t* vlabel, const int32_t* gid,
                  int64_t m, const int32_t* src, const int32_t* dst, const int32_t* elabel,
                  const int32_t* P, int32_t variant, int32_t* out_P) {
@@ -176,7 +177,24 @@ int oracle_round(int32_t n, const uint8_t* alive, const int32_t* vlabel, const i
     for (int64_t e = 0; e < m; ++e)
         if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return 2;
     Graph G{n, alive, vlabel, gid, m, src, dst, elabel};
-    refine_round(G, P, variant, out_P);
+    refine_round(G, P, variant, out_P, 0, n);
+    return 0;
+}
+
+// The same round restricted to the vertices [v0, v1): their signatures over
+// the whole P, each numbered by the smallest vertex of the range with the same
+// signature; out_P outside the range is left untouched. On [0, n) it is
+// oracle_round. The CPU baseline times consecutive ranges of a large graph as
+// bounded samples of one round (the per-vertex work is the round's; only the
+// map is smaller).
+int oracle_round_range(int32_t n, const uint8_t* alive, const int32_t* vlabel, const int32_t* gid,
+                       int64_t m, const int32_t* src, const int32_t* dst, const int32_t* elabel,
+                       const int32_t* P, int32_t v0, int32_t v1, int32_t* out_P) {
+    if (n < 0 || m < 0 || v0 < 0 || v1 > n || v0 > v1) return 1;
+    for (int64_t e = 0; e < m; ++e)
+        if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return 2;
+    Graph G{n, alive, vlabel, gid, m, src, dst, elabel};
+    refine_round(G, P, VARIANT_DEFINITION, out_P, v0, v1);
     return 0;
 }
 

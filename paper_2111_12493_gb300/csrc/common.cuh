@@ -447,8 +447,9 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp
 // Stable LSD radix sort of (u32 key, u64 value) pairs on the low `bits` key bits.
 // Buffers are ping-ponged; returns 0 if the result ended in (k0, v0), 1 if in (k1, v1).
 size_t radix_temp_words(int64_t m);
+// `site_name` names the launch-timing sites of the passes ("<name>_hist", "<name>_scatter").
 int radix_sort_pairs(uint32_t* k0, uint64_t* v0, uint32_t* k1, uint64_t* v1, int64_t m, int bits,
-                     int64_t* tmp, cudaStream_t s);
+                     int64_t* tmp, cudaStream_t s, const char* site_name = "radix");
 
 // ----------------------------------------------------------------------------- graph build (graph.cu)
 

@@ -1288,8 +1288,6 @@ constexpr double kSigVertexBytes = 32.0;
 constexpr double kInsertVertexBytes = 24.0;
 constexpr double kVerifyVertexBytes = 20.0;
 
-int64_t class_edges(const bisim_ctx* ctx, int c0, int c1) { return ctx->dedge_begin[c1] - ctx->dedge_begin[c0]; }
-
 // Persistent grids: as many CTAs as stay resident on all SMs at once (from the
 // occupancy calculator, per kernel and dynamic shared memory size), so that no
 // CTA waits for a second wave. Looked up before any capture (set_attributes)
@@ -1326,8 +1324,7 @@ void launch_mid(bisim_ctx* ctx, int cls, const DenseView& D, cudaStream_t s, int
     const int64_t count = ctx->dbegin[cls + 1] - ctx->dbegin[cls];
     if (count <= 0) return;
     const size_t smem = sizeof(unsigned long long) * 2 * N;
-    const int64_t edges = class_edges(ctx, cls, cls + 1);
-    Launch L(site, s, count, edges, 0.0);                  // bytes: from the round's work counters
+    Launch L(site, s, 0, 0, 0.0);                          // work and bytes: from the round's work counters
     const unsigned grid = persistent_grid(k_dense_mid_sig<N, T>, T, smem, count);
     k_dense_mid_sig<N, T><<<grid, T, smem, s>>>(cls, D, 4 + (cls - kDMid0));
 }
@@ -1398,11 +1395,11 @@ void launch_level(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const Tabl
         // their bytes follow it (added after the round)
         const unsigned* dcount = &ctx->dstate->listed;
         {
-            Launch L(site_in, s, count, 0, 0.0);
+            Launch L(site_in, s, 0, 0, 0.0);
             k_dense_insert<<<persistent_grid(k_dense_insert, kThreads, 0, cdiv(count, kThreads)), kThreads, 0, s>>>(
                 ctx->dact, 0, dcount, D, 0, t, &ctx->dstate->error);
         }
-        Launch L(site_v, s, count, 0, 0.0);
+        Launch L(site_v, s, 0, 0, 0.0);
         k_dense_verify<<<persistent_grid(k_dense_verify, kThreads, 0, cdiv(count, kThreads)), kThreads, 0, s>>>(
             ctx->dact, 0, dcount, D, round_slots(ctx), O, ctx->n);
     } else {
@@ -1502,8 +1499,7 @@ void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, const int32
     auto thread_sig = [&](int c0, int c1, auto kernel, int site, int group) {
         const int64_t verts = db[c1] - db[c0];
         if (verts <= 0) return;
-        const int64_t edges = class_edges(ctx, c0, c1);
-        Launch L(site, s, verts, edges, 0.0);
+        Launch L(site, s, 0, 0, 0.0);
         kernel<<<persistent_grid(kernel, kThreads, 0, cdiv(verts, kThreads)), kThreads, 0, s>>>(c0, c1, D, group);
     };
     thread_sig(0, 5, k_dense_thread_sig<8>, site_t8, 0);
@@ -1511,8 +1507,7 @@ void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, const int32
     thread_sig(6, 7, k_dense_thread_sig<32>, site_t32, 2);
     if (db[kDMid0] > db[kDWarp0]) {
         const int64_t verts = db[kDMid0] - db[kDWarp0];
-        const int64_t edges = class_edges(ctx, kDWarp0, kDMid0);
-        Launch L(site_w, s, verts, edges, 0.0);
+        Launch L(site_w, s, 0, 0, 0.0);
         k_dense_warp_sig<<<persistent_grid(k_dense_warp_sig, kThreads, 0, cdiv(verts, kThreads / 32)), kThreads, 0, s>>>(D);
     }
     launch_mid<512, 256>(ctx, kDMid0 + 0, D, s, site_mid[0]);
@@ -1521,23 +1516,22 @@ void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, const int32
     launch_mid<4096, 512>(ctx, kDMid0 + 3, D, s, site_mid[3]);
     launch_mid<8192, 512>(ctx, kDMid0 + 4, D, s, site_mid[4]);
     if (ctx->n_dhub > 0) {
-        const int64_t edges = class_edges(ctx, kDHub, kDHub + 1);
         if (ctx->n_dchunks > 0) {
             {
-                Launch L(site_hc, s, 0, edges, 0.0);
+                Launch L(site_hc, s, 0, 0, 0.0);
                 k_hub_count<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, 0, s>>>(ctx->dchunks, D, H);
             }
             exclusive_scan_i64(reinterpret_cast<const int64_t*>(ctx->bcount), ctx->boff, ctx->n_buckets + 1,
                                ctx->bscan, s);
             {
-                Launch L(site_hs, s, 0, edges, 0.0);
+                Launch L(site_hs, s, 0, 0, 0.0);
                 k_hub_scatter<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, kHubScatterSmem, s>>>(ctx->dchunks, D,
                                                                                                      H);
             }
-            Launch L(site_hd, s, 0, edges, 0.0);
+            Launch L(site_hd, s, 0, 0, 0.0);
             k_hub_dedup<<<static_cast<unsigned>(ctx->n_buckets), kThreads, kHubDedupSmem, s>>>(H, err);
         }
-        Launch L(site_hf, s, ctx->n_dhub, 0, 0.0);
+        Launch L(site_hf, s, 0, 0, 0.0);
         k_dense_hub_finalize<<<grid_for(ctx->n_dhub, 128), 128, 0, s>>>(D, H);
     }
     launch_level(ctx, s, D, t, 0, nullptr, ctx->dbegin[kDClasses], ctx->ulist[0]);
@@ -1561,7 +1555,10 @@ void add_round_work(bisim_ctx* ctx, double listed) {
                                  prof_site("dense_thread_sig_32"), prof_site("dense_warp_sig"),
                                  prof_site("dense_mid_512"), prof_site("dense_mid_1024"), prof_site("dense_mid_2048"),
                                  prof_site("dense_mid_4096"), prof_site("dense_mid_8192")};
-    for (int g = 0; g < 9; ++g) prof_add_bytes(sites[g], kSigVertexBytes * rows[g] + kEdgeBytes * edges[g]);
+    for (int g = 0; g < 9; ++g) {
+        prof_add_bytes(sites[g], kSigVertexBytes * rows[g] + kEdgeBytes * edges[g]);
+        prof_add_work(sites[g], static_cast<int64_t>(rows[g]), static_cast<int64_t>(edges[g]));
+    }
     BISIM_SITE(site_hc, "hub_count");
     BISIM_SITE(site_hs, "hub_scatter");
     BISIM_SITE(site_hd, "hub_dedup");
@@ -1571,10 +1568,14 @@ void add_round_work(bisim_ctx* ctx, double listed) {
     prof_add_bytes(site_hs, 16.0 * he);
     prof_add_bytes(site_hd, 8.0 * he);
     prof_add_bytes(site_hf, kSigVertexBytes * rows[kWorkHub]);
+    prof_add_work(site_hc, 0, static_cast<int64_t>(he));
+    prof_add_work(site_hf, static_cast<int64_t>(rows[kWorkHub]), 0);
     BISIM_SITE(site_in, "dense_insert");
     BISIM_SITE(site_v, "dense_verify");
     prof_add_bytes(site_in, kInsertVertexBytes * listed);
     prof_add_bytes(site_v, kVerifyVertexBytes * listed);
+    prof_add_work(site_in, static_cast<int64_t>(listed), 0);
+    prof_add_work(site_v, static_cast<int64_t>(listed), 0);
 }
 
 // Algorithmic bytes of the end of a round over `listed` entries with `kept` survivors:
@@ -1728,7 +1729,7 @@ bisim_status dense_layout_positions(bisim_ctx* ctx, const int32_t* deg, cudaStre
             k_dense_classify<<<grid_for(n, 256), 256, 0, s>>>(deg, ctx->alive, n, ctx->opt.small_max_degree,
                                                              ctx->opt.mid_max_degree, k0, v0);
         }
-        const int which = radix_sort_pairs(k0, v0, k1, v1, n, 5, tmp, s);
+        const int which = radix_sort_pairs(k0, v0, k1, v1, n, 5, tmp, s, "class_radix");
         const uint32_t* sk = which ? k1 : k0;
         const uint64_t* sv = which ? v1 : v0;
         {

@@ -82,6 +82,14 @@ void prof_add_bytes(int site, double bytes) {
     if (site >= 0 && site < static_cast<int>(g_sites.size())) g_sites[site].bytes += bytes;
 }
 
+void prof_add_work(int site, int64_t vertices, int64_t edges) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (site >= 0 && site < static_cast<int>(g_sites.size())) {
+        g_sites[site].vertices += vertices;
+        g_sites[site].edges += edges;
+    }
+}
+
 Launch::Launch(int site, cudaStream_t s, int64_t vertices, int64_t edges, double alg_bytes)
     : site_(site), s_(s), vertices_(vertices), edges_(edges), bytes_(alg_bytes) {
     g_launches.fetch_add(1, std::memory_order_relaxed);

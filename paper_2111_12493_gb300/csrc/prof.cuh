@@ -16,6 +16,8 @@ bool prof_enabled();
 void prof_add_launches(int64_t n);
 // Adds algorithmic bytes to a site after its launches (work known only once they ran).
 void prof_add_bytes(int site, double bytes);
+// Adds the vertices and edges a site's launches processed, when only the device knew them.
+void prof_add_work(int site, int64_t vertices, int64_t edges);
 
 // Brackets one kernel launch: counts it and, when profiling is enabled,
 // records events around it on stream `s`.

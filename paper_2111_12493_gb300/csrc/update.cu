@@ -835,7 +835,7 @@ bisim_status batch_begin(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, si
         Launch L(site_ops, s, 0, 0, 16.0 * nops);
         k_ops_check<<<grid_for(nops, 256), 256, 0, s>>>(d_ops, nops, n, ctx->dstate, vk0, vv0);
     }
-    const int which = radix_sort_pairs(vk0, vv0, vk1, vv1, nops, 32, B.tmp, s);
+    const int which = radix_sort_pairs(vk0, vv0, vk1, vv1, nops, 32, B.tmp, s, "update_radix");
     const uint32_t* vkey = which ? vk1 : vk0;
     const uint64_t* vpos = which ? vv1 : vv0;
     // 2. EDGE_ADD liveness and edge-key hashes (before the host looks: one read-back
@@ -866,11 +866,11 @@ bisim_status batch_begin(bisim_ctx* ctx, const bisim_op* d_ops, int64_t nops, si
     B.sklo = klo0;
     B.skp = kp0;
     if (ne > 0) {
-        const int wa = radix_sort_pairs(klo0, kp0, klo1, kp1, ne, 32, B.tmp, s);
+        const int wa = radix_sort_pairs(klo0, kp0, klo1, kp1, ne, 32, B.tmp, s, "update_radix");
         const uint64_t* posA = wa ? kp1 : kp0;
         k_key_halves<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, posA, ne, nullptr, khi0);
         cudaMemcpyAsync(kp2, posA, 8 * ne, cudaMemcpyDeviceToDevice, s);
-        const int wb = radix_sort_pairs(khi0, kp2, khi1, kp3, ne, 32, B.tmp, s);
+        const int wb = radix_sort_pairs(khi0, kp2, khi1, kp3, ne, 32, B.tmp, s, "update_radix");
         B.skhi = wb ? khi1 : khi0;
         B.skp = wb ? kp3 : kp2;
         k_key_halves<<<grid_for(ne, 256), 256, 0, s>>>(d_ops, B.skp, ne, klo0, nullptr);

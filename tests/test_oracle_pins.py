@@ -258,6 +258,47 @@ def test_batched_graph_ids_keep_graphs_apart():
     assert (P - off).tolist() == local.tolist()
 
 
+# --------------------------------------------------------------------------- CPU baselines
+
+@pytest.mark.parametrize("seed", range(4))
+def test_round_over_a_vertex_range_numbers_by_the_range_minimum(seed):
+    # within a range, v's id is the smallest vertex of the range in v's block
+    # of the full round (computed here from the full round by numpy)
+    n, s, d, l, vl = _rand_graph(seed, n=300, m=900, L=2, V=2)
+    P0 = oracle.label_partition(n, vl)
+    full = oracle.refine_round(n, s, d, l, vl, P0)
+    assert oracle.refine_round_range(n, s, d, l, vl, P0, 0, n).tolist() == full.tolist()
+    cuts = [0, 37, 150, 151, 299, 300]
+    out = np.full(n, -7, np.int32)
+    for v0, v1 in zip(cuts[:-1], cuts[1:]):
+        oracle.refine_round_range(n, s, d, l, vl, P0, v0, v1, out=out)
+        blk = full[v0:v1]
+        first = {}
+        for i, b in enumerate(blk.tolist()):
+            first.setdefault(b, v0 + i)
+        assert out[v0:v1].tolist() == [first[b] for b in blk.tolist()]
+    with pytest.raises(ValueError):
+        oracle.refine_round_range(n, s, d, l, vl, P0, 10, 5)
+
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 7])
+def test_threaded_round_equals_the_oracle_round(threads):
+    for seed in range(5):
+        n, s, d, l, vl = _rand_graph(seed, n=400, m=1500, L=3, V=3)
+        alive = (np.random.default_rng(seed).random(n) > 0.1).astype(np.uint8)
+        P, _, _ = oracle.refine(n, s, d, l, vl, 2, alive=alive)
+        want = oracle.refine_round(n, s, d, l, vl, P, alive=alive)
+        got = oracle.refine_round_threads(n, s, d, l, P, threads=threads, alive=alive)
+        assert got.tolist() == want.tolist()
+    from paper_2111_12493_gb300 import graphgen
+    b = graphgen.batched_graphs(n_graphs=10, nmin=5, nmax=80, seed=5)
+    u = graphgen.batched_union(b)
+    P, _, _ = oracle.refine(u["n"], u["src"], u["dst"], u["elabel"], u["vlabel"], 1, graph=u["graph"])
+    want = oracle.refine_round(u["n"], u["src"], u["dst"], u["elabel"], u["vlabel"], P, graph=u["graph"])
+    got = oracle.refine_round_threads(u["n"], u["src"], u["dst"], u["elabel"], P, threads=threads, graph=u["graph"])
+    assert got.tolist() == want.tolist()
+
+
 # --------------------------------------------------------------------------- planted mistakes
 
 PINS = []
