@@ -218,6 +218,37 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
 bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream);
 
 /*
+ * get_block_sizes -- the count payload of the summary (Section 3.1: the payload
+ * of a vertex summary counts the vertices it summarizes; merging summaries adds
+ * the counts): sizes[b] = number of vertices whose block id is b, 0 for every b
+ * that is not a block id (dead vertices belong to no block).
+ *   sizes  int32[n] output, device or host memory (batched contexts: int32[total
+ *          vertices], indexed by the union's vertex id; the block with
+ *          graph-local id b of graph g is entry vertex_offsets[g] + b)
+ * Synchronises `stream`.
+ */
+bisim_status get_block_sizes(bisim_ctx* ctx, int32_t* sizes, void* stream);
+
+/*
+ * get_summary_edges -- the edges of the summary graph (Section 2.6: one vertex
+ * per block, an edge labelled l from the block of u to the block of w for every
+ * edge (u, w) with label l of the data graph, parallel edges of one label
+ * between two blocks collapsed into one): the distinct triples
+ * (P[u], l, P[w]) over the live edges, in lexicographic order of (source
+ * block, label as a signed int32, target block). Block ids are those of
+ * get_partition, except that batched contexts report the union's vertex ids
+ * (the block's smallest vertex over the union).
+ *   src_block, label, dst_block  int32[capacity] outputs, device or host memory;
+ *                                may be NULL when capacity is 0
+ *   capacity   entries the outputs hold; min(capacity, count) are written
+ *   out_count  the number of distinct triples (call with capacity 0 to size
+ *              the outputs)
+ * Uses about 36 bytes of temporary device memory per edge. Synchronises `stream`.
+ */
+bisim_status get_summary_edges(bisim_ctx* ctx, int32_t* src_block, int32_t* label, int32_t* dst_block,
+                               int64_t capacity, int64_t* out_count, void* stream);
+
+/*
  * bisim_autotune -- choose the degree-class thresholds of the round layout
  * of the single-graph round kernels (mid_max_degree: rows above it take the
  * hub path; small_max_degree: rows up to it take one thread each) and the hub

@@ -156,6 +156,27 @@ def refine_round_threads(n, src, dst, elabel, P, threads=0, alive=None, graph=No
     return out
 
 
+def summary_edges(src, dst, elabel, P):
+    """Edges of the summary graph of partition P (Section 2.6): one per distinct
+    (P[u], l, P[w]) over the edges (u, w, l) whose endpoints are in a block,
+    sorted lexicographically. Plain Python: a set of tuples."""
+    out = set()
+    for u, w, l in zip(np.asarray(src).tolist(), np.asarray(dst).tolist(), np.asarray(elabel).tolist()):
+        a, b = int(P[u]), int(P[w])
+        if a >= 0 and b >= 0:
+            out.add((a, int(l), b))
+    return sorted(out)
+
+
+def block_sizes(P):
+    """The count payload (Section 3.1): vertices per block id, 0 for ids that name no block."""
+    sizes = [0] * len(P)
+    for b in np.asarray(P).tolist():
+        if b >= 0:
+            sizes[b] += 1
+    return np.array(sizes, dtype=np.int32)
+
+
 def label_partition(n, vlabel, alive=None, graph=None):
     lib = _load()
     vlabel, graph = _i32(vlabel), _i32(graph)

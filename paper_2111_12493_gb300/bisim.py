@@ -76,6 +76,8 @@ def _load():
         "bisim_launch_count": (i64, []),
         "bisim_refine_round_noalloc": (ctypes.c_int, [i32, i64, p, p, p, p, p, ctypes.POINTER(i64), p]),
         "bisim_autotune": (ctypes.c_int, [p, i32, ctypes.POINTER(Options), p]),
+        "get_block_sizes": (ctypes.c_int, [p, p, p]),
+        "get_summary_edges": (ctypes.c_int, [p, p, p, p, i64, ctypes.POINTER(i64), p]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -212,6 +214,28 @@ def get_partition(ctx: Context, out=None, stream=None):
     rc = _lib.get_partition(ctx.ptr, _ptr(out, torch.int32, "out", ctx.n_vertices), _stream(stream))
     _check(rc, ctx.ptr)
     return out
+
+
+def get_block_sizes(ctx: Context, out=None, stream=None):
+    """Vertices per block: out[b] = |{v : P[v] = b}| (0 where b is not a block id)."""
+    if out is None:
+        out = torch.empty(ctx.n_vertices, dtype=torch.int32, device="cuda")
+    _check(_lib.get_block_sizes(ctx.ptr, _ptr(out, torch.int32, "out", ctx.n_vertices), _stream(stream)), ctx.ptr)
+    return out
+
+
+def get_summary_edges(ctx: Context, stream=None):
+    """The summary graph's edges as three int32 device tensors (source block,
+    label, target block), distinct and sorted lexicographically."""
+    count = ctypes.c_int64()
+    cap = max(1, int(bisim_get_stats(ctx)["n_edges"]))
+    while True:
+        outs = [torch.empty(cap, dtype=torch.int32, device="cuda") for _ in range(3)]
+        _check(_lib.get_summary_edges(ctx.ptr, *[ctypes.c_void_p(o.data_ptr()) for o in outs], cap,
+                                      ctypes.byref(count), _stream(stream)), ctx.ptr)
+        if count.value <= cap:
+            return tuple(o[:count.value] for o in outs)
+        cap = count.value
 
 
 def bisim_autotune(ctx: Context, rounds: int = 2, stream=None) -> dict:

@@ -104,7 +104,7 @@ def coarsest_stable(n, edges, vlabel, alive=None):
 
 def parse_golden(name):
     """Read a fixture: n, edges, labelled modes, expectations and op rows."""
-    g = dict(n=0, edges=[], vlabel={}, expect={}, ops={})
+    g = dict(n=0, edges=[], vlabel={}, expect={}, ops={}, summary={}, sizes={})
     with open(os.path.join(GOLDEN, name)) as f:
         for raw in f:
             line = raw.split("#", 1)[0].strip()
@@ -121,6 +121,10 @@ def parse_golden(name):
                 g["expect"][(tok[1], int(tok[2]))] = np.array([int(x) for x in tok[3:]], dtype=np.int32)
             elif tok[0] == "op":
                 g["ops"].setdefault(tok[1], []).append([int(x) for x in tok[2:6]])
+            elif tok[0] == "summary":
+                g["summary"].setdefault(int(tok[1]), []).append(tuple(int(x) for x in tok[2:5]))
+            elif tok[0] == "sizes":
+                g["sizes"][int(tok[1])] = np.array([int(x) for x in tok[2:]], dtype=np.int32)
     return g
 
 

@@ -4,6 +4,8 @@
   element. The oracle recomputes P_0 and, from the device's P_i, the exact
   P_{i+1} (one oracle round each, independent of one another, so they run in
   parallel processes); by induction the device's fixpoint partition is exact.
+  The summary graph and block sizes of that partition are checked against a
+  numpy sort and count of its edge images.
 - chains (1000 paths of 1000 + 2M random edges) to the fixpoint: the whole
   oracle run.
 - 4096 batched graphs at k = 3: a seeded sample of the graphs (plus the
@@ -84,6 +86,22 @@ def test_powerlaw_10M_100M_every_round(B):
     ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]))
     r, blocks = B.bisim_iterate(ctx, B.FIXPOINT, 10)
     final = B.get_partition(ctx).cpu().numpy()
+    # the summary graph and count payload of the fixpoint partition (which the
+    # rounds below check against the oracle); numpy's sort stands in for the
+    # oracle's set at this size
+    es, el, et = (x.cpu().numpy() for x in B.get_summary_edges(ctx))
+    sizes = B.get_block_sizes(ctx).cpu().numpy()
+    assert np.array_equal(sizes, np.bincount(final, minlength=g["n"]).astype(np.int32))
+    sb, tb = final[g["src"]].astype(np.int64), final[g["dst"]].astype(np.int64)
+    key = (sb << 32) | (g["elabel"].astype(np.int64) + 2 ** 31)
+    order = np.lexsort((tb, key))
+    ks, ts = key[order], tb[order]
+    head = np.ones(len(ks), bool)
+    head[1:] = (ks[1:] != ks[:-1]) | (ts[1:] != ts[:-1])
+    assert np.array_equal(es, (ks[head] >> 32).astype(np.int32))
+    assert np.array_equal(el, ((ks[head] & 0xffffffff) - 2 ** 31).astype(np.int32))
+    assert np.array_equal(et, ts[head].astype(np.int32))
+    del sb, tb, key, order, ks, ts, head
     P = []
     for k in range(r + 2):
         B.bisim_iterate(ctx, k, 0)

@@ -258,6 +258,72 @@ def test_batched_graph_ids_keep_graphs_apart():
     assert (P - off).tolist() == local.tolist()
 
 
+# --------------------------------------------------------------------------- summary graph and payload
+
+def test_summary_of_the_worked_example():
+    gf = parse_golden("fig3_worked_example.txt")
+    s, d, l = edges_to_arrays(gf["edges"])
+    for mode in ("T", "L"):
+        P, _, _ = oracle.refine(gf["n"], s, d, l, np.array(gf["vlabel"][mode], np.int32), 2)
+        assert oracle.summary_edges(s, d, l, P) == gf["summary"][2]
+        assert oracle.block_sizes(P).tolist() == gf["sizes"][2].tolist()
+
+
+@pytest.mark.parametrize("m", [1, 4, 9])
+def test_summary_of_a_directed_path(m):
+    # after k rounds: vertices 0..m-k form block 0, the rest are alone; the
+    # summary keeps the path's direction and label
+    s = np.arange(m, dtype=np.int32)
+    d = s + 1
+    l = np.full(m, 3, np.int32)
+    for k in range(0, m + 2):
+        P, _, _ = oracle.refine(m + 1, s, d, l, np.zeros(m + 1, np.int32), k)
+        head = max(0, m - k)                        # last vertex of block 0
+        want = set()
+        for u in range(m):
+            a = 0 if u <= head else u
+            b = 0 if u + 1 <= head else u + 1
+            want.add((a, 3, b))
+        assert oracle.summary_edges(s, d, l, P) == sorted(want), k
+        sizes = [0] * (m + 1)
+        sizes[0] = head + 1
+        for v in range(head + 1, m + 1):
+            sizes[v] = 1
+        assert oracle.block_sizes(P).tolist() == sizes
+
+
+def test_summary_collapses_parallel_edges_of_one_label():
+    # a directed cycle with uniform labels is one block: its n edges collapse
+    # into one self-loop per label
+    n = 6
+    s = np.arange(n, dtype=np.int32)
+    d = ((s + 1) % n).astype(np.int32)
+    for labels, want in ((np.zeros(n, np.int32), [(0, 0, 0)]),):
+        P, _, _ = oracle.refine(n, s, d, labels, np.zeros(n, np.int32), oracle.FIXPOINT)
+        assert oracle.summary_edges(s, d, labels, P) == want
+        assert oracle.block_sizes(P).tolist() == [n] + [0] * (n - 1)
+    # an out-star whose leaves share one class but are reached by three labels:
+    # one summary edge per label
+    s = np.zeros(5, np.int32)
+    d = np.arange(1, 6, dtype=np.int32)
+    l = np.array([7, 8, 7, 9, 8], np.int32)
+    P, _, _ = oracle.refine(6, s, d, l, np.zeros(6, np.int32), 2)
+    assert P.tolist() == [0, 1, 1, 1, 1, 1]
+    assert oracle.summary_edges(s, d, l, P) == [(0, 7, 1), (0, 8, 1), (0, 9, 1)]
+
+
+def test_summary_skips_dead_vertices_and_every_edge_has_a_witness():
+    n, s, d, l, vl = _rand_graph(11, n=80, m=300, L=3, V=2)
+    alive = (np.random.default_rng(3).random(n) > 0.2).astype(np.uint8)
+    P, _, _ = oracle.refine(n, s, d, l, vl, 2, alive=alive)
+    E = oracle.summary_edges(s, d, l, P)
+    images = {(int(P[u]), int(x), int(P[w])) for u, w, x in zip(s, d, l) if alive[u] and alive[w]}
+    assert set(E) == images and len(E) == len(images)
+    sizes = oracle.block_sizes(P)
+    assert sizes.sum() == int(alive.sum())
+    assert sorted(np.flatnonzero(sizes).tolist()) == sorted(set(int(b) for b in P if b >= 0))
+
+
 # --------------------------------------------------------------------------- CPU baselines
 
 @pytest.mark.parametrize("seed", range(4))
