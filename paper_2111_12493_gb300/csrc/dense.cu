@@ -1706,12 +1706,15 @@ bisim_status dense_layout_positions(bisim_ctx* ctx, const int32_t* deg, cudaStre
     if ((st = alloc_round_state(ctx, s)) != BISIM_OK) return st;
     free_hub_layout(ctx, s);
     const size_t tmp_words = std::max(radix_temp_words(n), scan_temp_words(static_cast<int64_t>(n) + 1));
-    const size_t bytes = (sizeof(uint32_t) * 2 + sizeof(uint64_t) * 2) * nv + sizeof(int64_t) * (nv + 1) +
-                         sizeof(int64_t) * (tmp_words + kDClasses + 1) + 6 * 256;
+    // every piece starts on a 256-byte boundary: the allocation is the sum of the rounded sizes
+    auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t bytes = 2 * r256(sizeof(uint32_t) * nv) + 2 * r256(sizeof(uint64_t) * nv) +
+                         r256(sizeof(int64_t) * (nv + 1)) + r256(sizeof(int64_t) * tmp_words) +
+                         r256(sizeof(int64_t) * (kDClasses + 1));
     char* scratch = nullptr;
     if ((e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s))) return cuda_error(ctx, e, "alloc layout scratch");
     char* base = scratch;
-    auto carve = [&](size_t b) { char* p = scratch; scratch += (b + 255) & ~size_t(255); return p; };
+    auto carve = [&](size_t b) { char* p = scratch; scratch += r256(b); return p; };
     uint32_t* k0 = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * nv));
     uint32_t* k1 = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * nv));
     uint64_t* v0 = reinterpret_cast<uint64_t*>(carve(sizeof(uint64_t) * nv));
