@@ -83,6 +83,12 @@ enum { BISIM_FLAG_EAGER = 4 };
  * graph's rounds, renumbering and collision levels to the end. */
 enum { BISIM_FLAG_UNION_ROUNDS = 8 };
 
+/* Direction of the edges that make up a vertex's signature (Section 2.5:
+ * forward bisimulation compares outgoing edges, backward bisimulation incoming
+ * ones; the forward-backward variant compares both, an out-pair never equal to
+ * an in-pair). BISIM_DIR_BOTH needs every edge label in [-2^30, 2^30). */
+enum { BISIM_DIR_FORWARD = 0, BISIM_DIR_BACKWARD = 1, BISIM_DIR_BOTH = 2 };
+
 /* Update operations (Section 3.2, incremental summarization of evolving graphs:
  * additions, deletions and modifications of vertices and edges). */
 enum {
@@ -114,6 +120,12 @@ typedef struct {
     int32_t flags;             /* BISIM_FLAG_* bits (default 0) */
     int64_t mem_budget_bytes;  /* refuse (BISIM_ENOMEM) contexts whose device footprint would
                                   exceed this; 0 = no limit */
+    int32_t direction;         /* BISIM_DIR_* (default BISIM_DIR_FORWARD) */
+    int32_t n_label_filter;    /* > 0: only edges whose label is one of label_filter[0 .. n)
+                                  take part (the label-parameterized edge relation of Section
+                                  2.4.2); update operations on other labels are ignored.
+                                  0 (default): every edge */
+    const int32_t* label_filter;  /* host or device memory, read while the context is created */
 } bisim_options;
 
 typedef struct {

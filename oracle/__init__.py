@@ -40,6 +40,10 @@ VARIANT_OWN_LABEL = 16
 
 FIXPOINT = -1
 
+# Direction of the edges that make up a vertex's set (Section 2.5): forward
+# uses out-edges, backward in-edges, both the two sets with each pair tagged.
+DIRECTIONS = {"forward": 0, "backward": 1, "both": 2}
+
 OP_EDGE_ADD = 0
 OP_EDGE_DEL = 1
 OP_VERTEX_ADD = 2
@@ -64,9 +68,9 @@ def _load():
             lib = ctypes.CDLL(_LIB)
             p = ctypes.c_void_p
             i32, i64 = ctypes.c_int32, ctypes.c_int64
-            lib.oracle_refine.argtypes = [i32, p, p, p, i64, p, p, p, i32, i32, i32, p, p, p, p, i32]
+            lib.oracle_refine.argtypes = [i32, p, p, p, i64, p, p, p, i32, i32, i32, i32, p, p, p, p, i32]
             lib.oracle_refine.restype = ctypes.c_int
-            lib.oracle_round.argtypes = [i32, p, p, p, i64, p, p, p, p, i32, p]
+            lib.oracle_round.argtypes = [i32, p, p, p, i64, p, p, p, p, i32, i32, p]
             lib.oracle_round.restype = ctypes.c_int
             lib.oracle_round_range.argtypes = [i32, p, p, p, i64, p, p, p, p, i32, i32, p]
             lib.oracle_round_range.restype = ctypes.c_int
@@ -88,14 +92,25 @@ def _i32(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.int32)
 
 
+def _filtered(src, dst, elabel, label_filter):
+    """The edges whose label is in label_filter (all edges when it is None)."""
+    if label_filter is None:
+        return src, dst, elabel
+    keep = np.isin(np.asarray(elabel), np.asarray(label_filter, dtype=np.int64))
+    return np.asarray(src)[keep], np.asarray(dst)[keep], np.asarray(elabel)[keep]
+
+
 def refine(n, src, dst, elabel, vlabel, k, cap=10_000, alive=None, graph=None,
-           variant=VARIANT_DEFINITION, history=False):
+           variant=VARIANT_DEFINITION, history=False, direction="forward", label_filter=None):
     """Exact partition after k rounds (k >= 0) or at the fixpoint (k = FIXPOINT).
 
     Returns (P, rounds, executed[, history]) where P is int32 [n] of canonical
     block ids (smallest vertex id of the block, -1 for dead vertices).
+    `direction` picks the edges of a vertex's set (forward, backward, both);
+    `label_filter`, when given, keeps only the edges with one of its labels.
     """
     lib = _load()
+    src, dst, elabel = _filtered(src, dst, elabel, label_filter)
     src, dst, elabel, vlabel, graph = map(_i32, (src, dst, elabel, vlabel, graph))
     alive = None if alive is None else np.ascontiguousarray(alive, dtype=np.uint8)
     m = len(src)
@@ -105,7 +120,7 @@ def refine(n, src, dst, elabel, vlabel, k, cap=10_000, alive=None, graph=None,
     rows = (k if k >= 0 else cap) + 1
     hist = np.full((rows, n), -2, dtype=np.int32) if history else None
     rc = lib.oracle_refine(n, _ptr(alive), _ptr(vlabel), _ptr(graph), m, _ptr(src), _ptr(dst),
-                           _ptr(elabel), k, cap, variant, _ptr(P), ctypes.byref(rounds),
+                           _ptr(elabel), k, cap, variant, DIRECTIONS[direction], _ptr(P), ctypes.byref(rounds),
                            ctypes.byref(executed), _ptr(hist), rows if history else 0)
     if rc != 0:
         raise ValueError(f"oracle_refine rejected its input (code {rc})")
@@ -114,14 +129,16 @@ def refine(n, src, dst, elabel, vlabel, k, cap=10_000, alive=None, graph=None,
     return P, rounds.value, executed.value
 
 
-def refine_round(n, src, dst, elabel, vlabel, P, alive=None, graph=None, variant=VARIANT_DEFINITION):
+def refine_round(n, src, dst, elabel, vlabel, P, alive=None, graph=None, variant=VARIANT_DEFINITION,
+                 direction="forward", label_filter=None):
     """One exact refinement round from partition P."""
     lib = _load()
+    src, dst, elabel = _filtered(src, dst, elabel, label_filter)
     src, dst, elabel, vlabel, graph, P = map(_i32, (src, dst, elabel, vlabel, graph, P))
     alive = None if alive is None else np.ascontiguousarray(alive, dtype=np.uint8)
     out = np.empty(n, dtype=np.int32)
     rc = lib.oracle_round(n, _ptr(alive), _ptr(vlabel), _ptr(graph), len(src), _ptr(src),
-                          _ptr(dst), _ptr(elabel), _ptr(P), variant, _ptr(out))
+                          _ptr(dst), _ptr(elabel), _ptr(P), variant, DIRECTIONS[direction], _ptr(out))
     if rc != 0:
         raise ValueError(f"oracle_round rejected its input (code {rc})")
     return out
@@ -156,10 +173,11 @@ def refine_round_threads(n, src, dst, elabel, P, threads=0, alive=None, graph=No
     return out
 
 
-def summary_edges(src, dst, elabel, P):
+def summary_edges(src, dst, elabel, P, label_filter=None):
     """Edges of the summary graph of partition P (Section 2.6): one per distinct
     (P[u], l, P[w]) over the edges (u, w, l) whose endpoints are in a block,
     sorted lexicographically. Plain Python: a set of tuples."""
+    src, dst, elabel = _filtered(src, dst, elabel, label_filter)
     out = set()
     for u, w, l in zip(np.asarray(src).tolist(), np.asarray(dst).tolist(), np.asarray(elabel).tolist()):
         a, b = int(P[u]), int(P[w])

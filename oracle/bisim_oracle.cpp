@@ -19,6 +19,8 @@
 //
 //   P_0[v]     = min { u alive : (g[u], L[u]) = (g[v], L[v]) }       (label partition)
 //   S_i(v)     = set of pairs (l, P_i[w]) over out-edges (v, w, l)   (duplicates count once)
+//                (backward: over in-edges (w, v, l); both: the two sets, each pair tagged
+//                with its direction)
 //   sig_i(v)   = (P_i[v], S_i(v))
 //   P_{i+1}[v] = min { u alive : sig_i(u) = sig_i(v) }
 //
@@ -54,8 +56,14 @@ enum : int32_t {
     VARIANT_OWN_LABEL = 16,        // legitimate: own term is the vertex label, not P_i[v]
 };
 
-using Pair = std::pair<int32_t, int32_t>;                       // (edge label, neighbour block)
+// (direction, edge label, neighbour block); direction 0 = an out-edge, 1 = an in-edge
+using Pair = std::tuple<int32_t, int32_t, int32_t>;
 using Signature = std::tuple<int32_t, int32_t, std::vector<Pair>>;  // (own a, own b, S)
+
+// Which edges make up a vertex's set (Section 2.5: forward bisimulation uses
+// outgoing edges, backward bisimulation incoming ones; both = the two sets
+// together, each pair tagged with its direction).
+enum : int32_t { DIR_FORWARD = 0, DIR_BACKWARD = 1, DIR_BOTH = 2 };
 
 struct Graph {
     int32_t n;
@@ -84,18 +92,19 @@ void label_partition(const Graph& G, int32_t* P0) {
 }
 
 // One refinement round: vertices stay together iff they were together and
-// their sets of (edge label, neighbour block) agree. Only the vertices of
-// [v0, v1) are refined (the whole round is [0, n)); a vertex range lets the
-// CPU baseline time a bounded part of a large graph's round.
-void refine_round(const Graph& G, const int32_t* P, int32_t variant, int32_t* Pnext, int32_t v0, int32_t v1) {
+// their sets of (direction, edge label, neighbour block) agree. Only the
+// vertices of [v0, v1) are refined (the whole round is [0, n)); a vertex range
+// lets the CPU baseline time a bounded part of a large graph's round.
+void refine_round(const Graph& G, const int32_t* P, int32_t variant, int32_t* Pnext, int32_t v0, int32_t v1,
+                  int32_t direction = DIR_FORWARD) {
     std::vector<std::vector<Pair>> S(G.n);
     for (int64_t e = 0; e < G.m; ++e) {
         int32_t v = G.src[e], w = G.dst[e];
         if (!G.is_alive(v) || !G.is_alive(w)) continue;
         if (variant & VARIANT_REVERSE) std::swap(v, w);
-        if (v < v0 || v >= v1) continue;
         int32_t l = (variant & VARIANT_DROP_EDGE_LABEL) ? 0 : G.elabel[e];
-        S[v].emplace_back(l, P[w]);
+        if (direction != DIR_BACKWARD && v >= v0 && v < v1) S[v].emplace_back(0, l, P[w]);   // out-edge of v
+        if (direction != DIR_FORWARD && w >= v0 && w < v1) S[w].emplace_back(1, l, P[v]);    // in-edge of w
     }
     for (int32_t v = v0; v < v1; ++v) {
         std::sort(S[v].begin(), S[v].end());
@@ -128,9 +137,10 @@ extern "C" {
 // history: nullable int32[(max_rounds+1) * n]; row i receives P_i.
 int oracle_refine(int32_t n, const uint8_t* alive, const int32_t* vlabel, const int32_t* gid,
                   int64_t m, const int32_t* src, const int32_t* dst, const int32_t* elabel,
-                  int32_t k, int32_t cap, int32_t variant,
+                  int32_t k, int32_t cap, int32_t variant, int32_t direction,
                   int32_t* out_P, int32_t* out_rounds, int32_t* out_executed,
                   int32_t* history, int32_t history_rows) {
+    if (direction < DIR_FORWARD || direction > DIR_BOTH) return 1;
     if (n < 0 || m < 0 || (n > 0 && (vlabel == nullptr || out_P == nullptr))) return 1;
     for (int64_t e = 0; e < m; ++e)
         if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return 2;
@@ -145,7 +155,7 @@ int oracle_refine(int32_t n, const uint8_t* alive, const int32_t* vlabel, const 
     int32_t rounds = 0, executed = 0;
     if (k >= 0) {
         for (int32_t i = 0; i < k; ++i) {
-            refine_round(G, P.data(), variant, Q.data(), 0, n);
+            refine_round(G, P.data(), variant, Q.data(), 0, n, direction);
             P.swap(Q);
             ++executed;
             record(executed, P);
@@ -154,7 +164,7 @@ int oracle_refine(int32_t n, const uint8_t* alive, const int32_t* vlabel, const 
     } else {
         rounds = cap;
         for (int32_t i = 0; i < cap; ++i) {
-            refine_round(G, P.data(), variant, Q.data(), 0, n);
+            refine_round(G, P.data(), variant, Q.data(), 0, n, direction);
             ++executed;
             if (same(P, Q)) { rounds = i; break; }
             P.swap(Q);
@@ -172,12 +182,12 @@ int oracle_refine(int32_t n, const uint8_t* alive, const int32_t* vlabel, const 
 // from P_0 would take too long.
 int oracle_round(int32_t n, const uint8_t* alive, const int32_t* vlabel, const int32_t* gid,
                  int64_t m, const int32_t* src, const int32_t* dst, const int32_t* elabel,
-                 const int32_t* P, int32_t variant, int32_t* out_P) {
-    if (n < 0 || m < 0) return 1;
+                 const int32_t* P, int32_t variant, int32_t direction, int32_t* out_P) {
+    if (n < 0 || m < 0 || direction < DIR_FORWARD || direction > DIR_BOTH) return 1;
     for (int64_t e = 0; e < m; ++e)
         if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return 2;
     Graph G{n, alive, vlabel, gid, m, src, dst, elabel};
-    refine_round(G, P, variant, out_P, 0, n);
+    refine_round(G, P, variant, out_P, 0, n, direction);
     return 0;
 }
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libbisim_gb300.so")
 
 FIXPOINT = -1
 FLAG_L2_PIN, FLAG_FULL_RECOMPUTE, FLAG_EAGER, FLAG_UNION_ROUNDS = 1, 2, 4, 8
+DIR_FORWARD, DIR_BACKWARD, DIR_BOTH = 0, 1, 2
 OP_EDGE_ADD, OP_EDGE_DEL, OP_VERTEX_ADD, OP_VERTEX_DEL = 0, 1, 2, 3
 
 _STATUS = {0: "BISIM_OK", 1: "BISIM_EINVAL", 2: "BISIM_ENOMEM", 3: "BISIM_ECUDA",
@@ -36,7 +37,8 @@ class Options(ctypes.Structure):
     _fields_ = [("k_incremental", ctypes.c_int32), ("hash_bits", ctypes.c_int32),
                 ("small_max_degree", ctypes.c_int32), ("mid_max_degree", ctypes.c_int32),
                 ("hub_chunk", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("mem_budget_bytes", ctypes.c_int64)]
+                ("mem_budget_bytes", ctypes.c_int64), ("direction", ctypes.c_int32),
+                ("n_label_filter", ctypes.c_int32), ("label_filter", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -90,10 +92,18 @@ _lib = _load()
 
 
 def default_options(**overrides) -> Options:
+    """bisim_default_options with fields overridden; `label_filter` takes a
+    sequence of edge labels (kept alive with the options)."""
     o = Options()
     _lib.bisim_default_options(ctypes.byref(o))
+    labels = overrides.pop("label_filter", None)
     for k, v in overrides.items():
         setattr(o, k, v)
+    if labels is not None:
+        arr = (ctypes.c_int32 * max(1, len(labels)))(*[int(x) for x in labels])
+        o._label_filter_keep = arr
+        o.n_label_filter = len(labels)
+        o.label_filter = ctypes.cast(arr, ctypes.c_void_p)
     return o
 
 

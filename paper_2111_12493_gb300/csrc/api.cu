@@ -129,6 +129,9 @@ bisim_status new_ctx(bisim_ctx** out, int32_t n, int64_t m, const bisim_options*
     if (out == nullptr) return set_error(nullptr, BISIM_EINVAL, "out pointer is NULL");
     *out = nullptr;
     if (n < 0 || m < 0) return set_error(nullptr, BISIM_EINVAL, "negative vertex or edge count");
+    if (opt != nullptr && (opt->direction < BISIM_DIR_FORWARD || opt->direction > BISIM_DIR_BOTH))
+        return set_error(nullptr, BISIM_EINVAL, "direction must be BISIM_DIR_FORWARD, _BACKWARD or _BOTH");
+    if (opt != nullptr && opt->n_label_filter < 0) return set_error(nullptr, BISIM_EINVAL, "n_label_filter < 0");
     bisim_ctx* ctx = new bisim_ctx();
     ctx->last_stream = s;
     ctx->n = n;
@@ -148,8 +151,29 @@ bisim_status new_ctx(bisim_ctx** out, int32_t n, int64_t m, const bisim_options*
     }
     cudaMemsetAsync(ctx->dstate, 0, sizeof(DevState), s);
     std::memset(ctx->hstate, 0, sizeof(DevState));
+    bisim_status st = edge_view_setup(ctx, opt, s);
+    if (st != BISIM_OK) {
+        const std::string msg = ctx->err;
+        destroy_ctx(ctx);
+        return set_error(nullptr, st, msg);
+    }
     *made = ctx;
     return BISIM_OK;
+}
+
+// Builds the context's graph from device COO arrays through its edge view
+// (direction and label filter); the view's edge count becomes the context's.
+bisim_status build_from_coo_view(bisim_ctx* ctx, const int32_t* src, const int32_t* dst, const int32_t* lab,
+                                 cudaStream_t s) {
+    if (edge_view_identity(ctx)) return build_from_coo(ctx, src, dst, lab, s);
+    EdgeView v;
+    bisim_status st = edge_view_coo(ctx, src, dst, lab, ctx->m, nullptr, 0, s, &v);
+    if (st == BISIM_OK) {
+        ctx->m = v.m;
+        st = build_from_coo(ctx, v.src, v.dst, v.lab, s);
+    }
+    edge_view_free(&v, s);
+    return st;
 }
 
 bisim_status copy_vertex_arrays(bisim_ctx* ctx, const int32_t* vlabel, const uint8_t* alive, cudaStream_t s) {
@@ -356,9 +380,30 @@ bisim_status summarize_init(bisim_ctx** out, int32_t n_vertices, int64_t n_edges
         destroy_ctx(ctx);
         return set_error(nullptr, BISIM_EINVAL, "a required array is NULL");
     }
-    if ((st = copy_vertex_arrays(ctx, vertex_label, alive, s)) == BISIM_OK &&
-        (st = build_from_csr(ctx, row_ptr, col, edge_label, s)) == BISIM_OK &&
-        (st = finish_init(ctx, s)) == BISIM_OK) {
+    if (!edge_view_identity(ctx) && (st = copy_vertex_arrays(ctx, vertex_label, alive, s)) == BISIM_OK) {
+        // another direction or a label filter: the CSR's edges as a list, then the view's COO path
+        std::vector<void*> temps;
+        const void *drp = nullptr, *dc = nullptr, *dl = nullptr;
+        int32_t* dsrc = nullptr;
+        cudaError_t e;
+        const size_t eb = sizeof(int32_t) * static_cast<size_t>(n_edges);
+        if ((e = stage(row_ptr, sizeof(int64_t) * (static_cast<size_t>(n_vertices) + 1), s, &drp, temps)) ||
+            (e = stage(col, eb, s, &dc, temps)) || (e = stage(edge_label, eb, s, &dl, temps)) ||
+            (e = cudaMallocAsync(reinterpret_cast<void**>(&dsrc), std::max<size_t>(eb, 4), s)))
+            st = cuda_error(ctx, e, "stage CSR arrays");
+        if (st == BISIM_OK)
+            st = csr_sources(ctx, static_cast<const int64_t*>(drp), n_vertices, n_edges, dsrc, s);
+        if (st == BISIM_OK)
+            st = build_from_coo_view(ctx, dsrc, static_cast<const int32_t*>(dc), static_cast<const int32_t*>(dl), s);
+        if (dsrc) cudaFreeAsync(dsrc, s);
+        free_temps(temps, s);
+        if (st == BISIM_OK && (st = finish_init(ctx, s)) == BISIM_OK) {
+            *out = ctx;
+            return BISIM_OK;
+        }
+    } else if (edge_view_identity(ctx) && (st = copy_vertex_arrays(ctx, vertex_label, alive, s)) == BISIM_OK &&
+               (st = build_from_csr(ctx, row_ptr, col, edge_label, s)) == BISIM_OK &&
+               (st = finish_init(ctx, s)) == BISIM_OK) {
         *out = ctx;
         return BISIM_OK;
     }
@@ -389,8 +434,8 @@ bisim_status summarize_init_coo(bisim_ctx** out, int32_t n_vertices, int64_t n_e
             st = cuda_error(ctx, e, "stage edge arrays");
     }
     if (st == BISIM_OK)
-        st = build_from_coo(ctx, static_cast<const int32_t*>(ds), static_cast<const int32_t*>(dd),
-                            static_cast<const int32_t*>(dl), s);
+        st = build_from_coo_view(ctx, static_cast<const int32_t*>(ds), static_cast<const int32_t*>(dd),
+                                 static_cast<const int32_t*>(dl), s);
     free_temps(temps, s);
     if (st == BISIM_OK && (st = finish_init(ctx, s)) == BISIM_OK) {
         *out = ctx;
@@ -464,8 +509,20 @@ bisim_status summarize_init_batched(bisim_ctx** out, int32_t n_graphs, const int
         if ((e = cudaStreamSynchronize(s))) st = cuda_error(ctx, e, "globalize batched edges");
         else if (ctx->hstate->error & kErrBadInput) st = set_error(ctx, BISIM_EINVAL, "a graph-local edge endpoint is out of range");
     }
+    EdgeView view;
+    const int32_t* bl = static_cast<const int32_t*>(dl);
+    if (st == BISIM_OK && !edge_view_identity(ctx)) {
+        // another direction or a label filter: the view keeps every graph's edges together
+        if ((st = edge_view_coo(ctx, gsrc, gdst, bl, m, deoff, n_graphs, s, &view)) == BISIM_OK) {
+            ctx->m = view.m;
+            if ((e = cudaMemcpyAsync(he.data(), view.eoff, sizeof(int64_t) * (n_graphs + 1), cudaMemcpyDeviceToHost, s)) ||
+                (e = cudaStreamSynchronize(s)))
+                st = cuda_error(ctx, e, "read view offsets");
+        }
+    }
     if (st == BISIM_OK)
-        st = build_from_coo(ctx, gsrc, gdst, static_cast<const int32_t*>(dl), s);
+        st = build_from_coo(ctx, view.src ? view.src : gsrc, view.src ? view.dst : gdst, view.src ? view.lab : bl, s);
+    edge_view_free(&view, s);
     if (st == BISIM_OK) st = dense_region_table(ctx, hv.data(), n_graphs, s);
     if (st == BISIM_OK) st = segment_init(ctx, hv.data(), he.data(), n_graphs, s);
     free_temps(temps, s);
@@ -511,11 +568,27 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
     // built; otherwise (and for full recomputes) they rewrite the CSR
     const bool incremental = !full && ctx->inc_k == ctx->opt.k_incremental && ctx->store_ready;
     if (!incremental && (st = ensure_vertex_csr(ctx, s)) != BISIM_OK) return st;
+    std::vector<void*> temps;
+    const void* d_ops = nullptr;
     if (n_ops > 0) {
-        std::vector<void*> temps;
-        const void* d_ops = nullptr;
         if ((e = stage(ops, sizeof(bisim_op) * static_cast<size_t>(n_ops), s, &d_ops, temps)))
             return cuda_error(ctx, e, "stage update batch");
+        if (!edge_view_identity(ctx)) {
+            // another direction or a label filter: the operations on the context's own edge list
+            bisim_op* vops = nullptr;
+            int64_t vn = 0;
+            st = edge_view_ops(ctx, static_cast<const bisim_op*>(d_ops), n_ops, s, &vops, &vn);
+            if (vops) temps.push_back(vops);
+            if (st != BISIM_OK) {
+                free_temps(temps, s);
+                return st;
+            }
+            d_ops = vops;
+            n_ops = vn;
+        }
+    }
+    if (n_ops == 0) free_temps(temps, s);
+    if (n_ops > 0) {
         uint8_t* flags = nullptr;
         // three flag arrays of n + 1 bytes, each starting on a 256-byte boundary
         // (the frontier kernels read them 16 bytes at a time)

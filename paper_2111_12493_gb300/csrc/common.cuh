@@ -418,6 +418,10 @@ struct bisim_ctx {
     int64_t bcap = 0;              // block records per level
     uint64_t isize = 0;            // index slots per level (power of two)
 
+    // direction and label filter of the summarized edges (direction.cu)
+    int32_t* dfilter = nullptr;    // [nfilter] listed edge labels, sorted, unique
+    int32_t nfilter = 0;           // 0: every label
+
     // bookkeeping
     void* last_stream = nullptr;   // stream of the last call (the context's memory is freed in its order)
     std::vector<void*> allocs;
@@ -554,6 +558,34 @@ bisim_status dense_graph_rounds(bisim_ctx* ctx, cudaStream_t s, int32_t limit, b
                                 GraphRounds* out);
 // Releases the graph, its capture stream and pinned mirror.
 void dense_release(bisim_ctx* ctx);
+
+// ----------------------------------------------------------------------------- direction and label filter (direction.cu)
+
+// An edge list in device memory that the library owns (freed by edge_view_free).
+struct EdgeView {
+    int32_t* src = nullptr;
+    int32_t* dst = nullptr;
+    int32_t* lab = nullptr;
+    int64_t* eoff = nullptr;       // batched: per-graph offsets of the view's edges [G + 1]
+    int64_t m = 0;
+};
+// Whether the context refines the caller's edges unchanged (forward, no filter).
+bool edge_view_identity(const bisim_ctx* ctx);
+// Copies the options' label filter (sorted, unique) into the context.
+bisim_status edge_view_setup(bisim_ctx* ctx, const bisim_options* opt, cudaStream_t s);
+// The internal edge list of the context's direction and filter for device
+// arrays (src, dst, lab)[m]; eoff (device, [G + 1]) gives per-graph offsets
+// of batched inputs, or is null.
+bisim_status edge_view_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* dst, const int32_t* lab, int64_t m,
+                           const int64_t* eoff, int32_t G, cudaStream_t s, EdgeView* out);
+void edge_view_free(EdgeView* v, cudaStream_t s);
+// An update batch mapped onto the internal edge list (device arrays; *out is
+// freed by the caller with cudaFreeAsync).
+bisim_status edge_view_ops(bisim_ctx* ctx, const bisim_op* ops, int64_t n, cudaStream_t s, bisim_op** out,
+                           int64_t* out_n);
+// Source vertex of every edge of a CSR (src[m]); a row_ptr that is not a
+// prefix sum of [0, m] gives BISIM_EINVAL and writes nothing out of range.
+bisim_status csr_sources(bisim_ctx* ctx, const int64_t* row_ptr, int32_t n, int64_t m, int32_t* src, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- incremental levels (inc.cu)
 

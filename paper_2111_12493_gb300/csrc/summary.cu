@@ -63,11 +63,14 @@ __device__ __forceinline__ int32_t row_of(const int64_t* __restrict__ rp, int64_
 // that they sort after every live triple. Each CTA takes a tile of edges and
 // narrows the search for their source rows to the rows the tile spans.
 constexpr int kKeyTile = 2048;
+// The context's own edges map back to the caller's (direction.cu): backward
+// contexts hold every edge reversed; forward-backward contexts hold (u, w, 2l)
+// and the in-edge copy (w, u, 2l + 1), which is left out here.
 __global__ void __launch_bounds__(256) k_summary_keys(const int64_t* __restrict__ rp, int32_t n,
                                                       const int32_t* __restrict__ col,
                                                       const int32_t* __restrict__ elab, int64_t m,
-                                                      const int32_t* __restrict__ P, uint32_t* __restrict__ key,
-                                                      uint64_t* __restrict__ val) {
+                                                      const int32_t* __restrict__ P, int32_t dir,
+                                                      uint32_t* __restrict__ key, uint64_t* __restrict__ val) {
     __shared__ int32_t span[2];
     const int64_t tiles = cdiv(m, kKeyTile);
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
@@ -78,11 +81,19 @@ __global__ void __launch_bounds__(256) k_summary_keys(const int64_t* __restrict_
         const int32_t lo = span[0], hi = span[1];
         for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
             const int32_t u = row_of(rp, e, lo, hi);
-            const int32_t sb = P[u], tb = P[col[e]];
-            const bool live = sb >= 0 && tb >= 0;
+            int32_t sb = P[u], tb = P[col[e]], l = elab[e];
+            bool live = sb >= 0 && tb >= 0;
+            if (dir == BISIM_DIR_BACKWARD) {
+                const int32_t t = sb;
+                sb = tb;
+                tb = t;
+            } else if (dir == BISIM_DIR_BOTH) {
+                live = live && (l & 1) == 0;
+                l >>= 1;                                   // arithmetic: 2l -> l for negative l too
+            }
             key[e] = live ? static_cast<uint32_t>(tb) : 0u;
             val[e] = (static_cast<uint64_t>(live ? static_cast<uint32_t>(sb) : static_cast<uint32_t>(n)) << 32) |
-                     (static_cast<uint32_t>(elab[e]) ^ kLabelFlip);
+                     (static_cast<uint32_t>(l) ^ kLabelFlip);
         }
         __syncthreads();
     }
@@ -214,7 +225,7 @@ bisim_status get_summary_edges(bisim_ctx* ctx, int32_t* src_block, int32_t* labe
     {
         Launch L(site, s, n, m, 48.0 * m);
         k_summary_keys<<<grid_for(cdiv(m, kKeyTile) * 256, 256), 256, 0, s>>>(ctx->row_ptr, n, ctx->col, ctx->elab, m,
-                                                                                P, k0, v0);
+                                                                                P, ctx->opt.direction, k0, v0);
     }
     // pass A: by target block (stable), the result in (k0, v0) or (k1, v1)
     int w = radix_sort_pairs(k0, v0, k1, v1, m, bits_for(n), tmp, s, "summary_radix");

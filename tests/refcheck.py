@@ -39,13 +39,20 @@ def canonical(ids) -> np.ndarray:
     return np.array(out, dtype=np.int32)
 
 
-def brute_force(n, edges, vlabel, k, alive=None):
-    """Canonical ids of the k-bisimulation classes from the pairwise definition."""
+def brute_force(n, edges, vlabel, k, alive=None, direction="forward"):
+    """Canonical ids of the k-bisimulation classes from the pairwise definition.
+
+    direction: "forward" matches out-edges, "backward" in-edges (Section 2.5),
+    "both" matches the out-edges and, separately, the in-edges."""
     alive = [True] * n if alive is None else [bool(a) for a in alive]
     out = [[] for _ in range(n)]
     for s, d, l in edges:
         if alive[s] and alive[d]:
-            out[s].append((l, d))
+            # the edge's label carries its direction as seen from the vertex
+            if direction in ("forward", "both"):
+                out[s].append(((l, "out"), d))
+            if direction in ("backward", "both"):
+                out[d].append(((l, "in"), s))
     R = [[alive[u] and alive[v] and vlabel[u] == vlabel[v] for v in range(n)] for u in range(n)]
     history = [R]
     for _ in range(k):

@@ -166,6 +166,83 @@ def test_brute_force_random_multigraphs():
         _check_against_brute(n, edges, vl, rnd.randint(0, 5), alive=np.array(alive, np.uint8))
 
 
+# --------------------------------------------------------------------------- backward and forward-backward
+
+def _run_dir(n, edges, vl, k, direction, alive=None):
+    s, d, l = edges_to_arrays(edges) if edges else (np.zeros(0, np.int32),) * 3
+    P, r, _ = oracle.refine(n, s, d, l, np.array(vl, np.int32), k, alive=alive, direction=direction)
+    return P, r
+
+
+@pytest.mark.parametrize("direction", ["backward", "both"])
+def test_directions_exhaustive_n3_one_label(direction):
+    pairs = [(u, v) for u in range(3) for v in range(3)]
+    for mask in range(1 << len(pairs)):
+        edges = [(u, v, 0) for i, (u, v) in enumerate(pairs) if mask >> i & 1]
+        for vl in ([0, 0, 0], [0, 0, 1]):
+            bf = brute_force(3, edges, vl, 3, direction=direction)
+            for k in range(4):
+                assert _run_dir(3, edges, vl, k, direction)[0].tolist() == bf[k].tolist(), (edges, vl, k)
+
+
+@pytest.mark.parametrize("direction", ["backward", "both"])
+def test_directions_random_multigraphs(direction):
+    rnd = random.Random(2111 + len(direction))
+    for _ in range(150):
+        n = rnd.randint(1, 10)
+        edges = [(rnd.randrange(n), rnd.randrange(n), rnd.randrange(2)) for _ in range(rnd.randint(0, 3 * n))]
+        vl = [rnd.choice([-1, 0, 1]) for _ in range(n)]
+        alive = np.array([rnd.random() > 0.15 for _ in range(n)], np.uint8)
+        kmax = rnd.randint(0, 5)
+        bf = brute_force(n, edges, vl, kmax, alive=alive, direction=direction)
+        for k in range(kmax + 1):
+            assert _run_dir(n, edges, vl, k, direction, alive)[0].tolist() == bf[k].tolist()
+
+
+@pytest.mark.parametrize("m", [1, 4, 7])
+def test_directed_path_backward_and_both(m):
+    # backward: a vertex sees only its predecessors, so after k rounds the
+    # vertices at distance >= k from the source form one block (the mirror of
+    # the forward form); both: a vertex is told apart by min(distance to the
+    # source, k) and min(distance to the sink, k)
+    edges = [(i, i + 1, 0) for i in range(m)]
+    vl = [0] * (m + 1)
+    for k in range(m + 2):
+        P, _ = _run_dir(m + 1, edges, vl, k, "backward")
+        assert P.tolist() == [i if i < k else k for i in range(m + 1)]
+        P, _ = _run_dir(m + 1, edges, vl, k, "both")
+        key = [(min(i, k), min(m - i, k)) for i in range(m + 1)]
+        first = {}
+        assert P.tolist() == [first.setdefault(x, i) for i, x in enumerate(key)]
+    assert _run_dir(m + 1, edges, vl, oracle.FIXPOINT, "backward")[1] == m
+
+
+def test_backward_fixpoint_is_the_coarsest_stable_partition_of_the_reversed_graph():
+    rnd = random.Random(8)
+    for _ in range(80):
+        n = rnd.randint(1, 14)
+        edges = [(rnd.randrange(n), rnd.randrange(n), rnd.randrange(3)) for _ in range(rnd.randint(0, 3 * n))]
+        vl = [rnd.randrange(2) for _ in range(n)]
+        P, _ = _run_dir(n, edges, vl, oracle.FIXPOINT, "backward")
+        assert P.tolist() == coarsest_stable(n, [(d, s, l) for s, d, l in edges], vl).tolist()
+
+
+def test_label_filter_keeps_only_listed_labels():
+    # an out-star with leaf labels: filtering the only edge label that tells
+    # two hubs apart merges them
+    edges = [(0, 2, 5), (1, 3, 6)]
+    s, d, l = edges_to_arrays(edges)
+    vl = np.zeros(4, np.int32)
+    P, _, _ = oracle.refine(4, s, d, l, vl, 1)
+    assert P.tolist() == [0, 1, 2, 2]
+    P, _, _ = oracle.refine(4, s, d, l, vl, 1, label_filter=[5])
+    assert P.tolist() == [0, 1, 1, 1]               # vertex 1 lost its only edge: like a sink
+    P, _, _ = oracle.refine(4, s, d, l, vl, 1, label_filter=[])
+    assert P.tolist() == [0, 0, 0, 0]
+    P, _, _ = oracle.refine(4, s, d, l, vl, 1, label_filter=[5, 6, 7])
+    assert P.tolist() == [0, 1, 2, 2]
+
+
 # --------------------------------------------------------------------------- fixpoint
 
 def test_fixpoint_equals_coarsest_stable_partition():
