@@ -82,6 +82,10 @@ def parse_args():
                     help="profiler capture window only: run the 1k-op update batches of the serving section "
                          "alone and bracket K incremental batches (after eight) with cudaProfilerStart/Stop, "
                          "for ncu --profile-from-start off; prints the batches' latencies, not a bench line")
+    ap.add_argument("--literal-alg4", action="store_true",
+                    help="diagnostic only: on each of the five configurations, the partition of Algorithm 4 taken "
+                         "literally (no edge labels in its last round) against the definition's; prints one JSON "
+                         "line per configuration, not a bench line")
     ap.add_argument("--union-rounds", action="store_true",
                     help="batched workload: run the union through the single-graph round kernels instead of the "
                          "persistent per-graph kernel")
@@ -774,11 +778,57 @@ def profile_updates(args, local):
     print(json.dumps({"profile_updates": args.profile_updates, "batch_ms": lat}))
 
 
+def literal_alg4_diagnostic(args, local):
+    """Per configuration: blocks of P_k by the definition and by Algorithm 4
+    taken literally, and the vertices whose literal class spans several of the
+    definition's blocks (the literal algorithm merged them)."""
+    import torch
+    from paper_2111_12493_gb300 import bisim, graphgen
+    dev = torch.device("cuda", local)
+    sc = args.scale
+    cases = [
+        ("uniform 10k/50k, k=2", graphgen.uniform_graph(seed=1), 2),
+        ("power-law 10M/100M, k=4 (its fixpoint round)", workload_graph(sc), 4),
+        ("chains 1000x1000 + 2M random edges, k=4 (its fixpoint round)",
+         graphgen.chain_graph(n_paths=max(10, int(1000 * sc)), path_len=1000, extra=int(2_000_000 * sc), seed=3), 4),
+        ("4096 batched graphs as one union (graph id folded into the vertex label), k=3", None, 3),
+        ("power-law 5M/50M (update base graph), k=2",
+         graphgen.powerlaw_graph(n=max(1000, int(5_000_000 * sc)), m=max(10_000, int(50_000_000 * sc)),
+                                 exponent=2.1, dmax=min(1_000_000, int(50_000_000 * sc) // 10), n_elabels=1000,
+                                 n_vlabels=200, untyped_frac=0.1, seed=5), 2)]
+    for name, g, k in cases:
+        if g is None:
+            b = graphgen.batched_graphs(n_graphs=max(8, int(4096 * sc)), seed=4)
+            u = graphgen.batched_union(b)
+            g = dict(u, vlabel=(u["graph"].astype(np.int64) * 16 + u["vlabel"]).astype(np.int32))
+        t = [torch.from_numpy(np.ascontiguousarray(g[x])).to(dev) for x in ("src", "dst", "elabel", "vlabel")]
+        ctx = bisim.summarize_init_coo(g["n"], *t)
+        _, blocks = bisim.bisim_iterate(ctx, k, 0)
+        P = bisim.get_partition(ctx).cpu().numpy()
+        t0 = time.perf_counter()
+        lit, lblocks = bisim.bisim_literal_alg4(ctx, k)
+        dt = time.perf_counter() - t0
+        lit = lit.cpu().numpy()
+        bisim.summarize_destroy(ctx)
+        # literal classes that hold more than one of the definition's blocks
+        pairs = np.unique(np.stack([lit, P]).T, axis=0)
+        per_lit = np.bincount(pairs[:, 0], minlength=g["n"])
+        merged = per_lit[lit] > 1
+        print(json.dumps({"literal_alg4": name, "k": k, "n_vertices": int(g["n"]), "n_edges": int(len(g["src"])),
+                          "blocks_definition": int(blocks), "blocks_literal": int(lblocks),
+                          "definition_blocks_merged": int(blocks - lblocks),
+                          "vertices_in_merged_classes": int(merged.sum()),
+                          "fraction_of_vertices": float(merged.mean()), "literal_s": round(dt, 2)}), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_init()
     if args.profile_updates > 0:
         profile_updates(args, local)
+        return
+    if args.literal_alg4:
+        literal_alg4_diagnostic(args, local)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)

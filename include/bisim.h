@@ -307,6 +307,25 @@ bisim_status bisim_refine_round_noalloc(int32_t n_vertices, int64_t n_edges, con
                                         const int32_t* block_in, int32_t* block_out,
                                         int64_t* out_num_blocks, void* stream);
 
+/*
+ * bisim_literal_alg4 -- diagnostic: the partition Algorithm 4 (Section 3.3.1)
+ * computes when taken literally, with exact identifiers (no hash collisions).
+ * Algorithm 4 keeps two identifiers per vertex: id_s is refined like the
+ * definition of Section 2.5 in rounds 1 .. k-1; id_o has no own term, takes
+ * (edge label, neighbour's id_o) in its first round and only the neighbours'
+ * id_o after that; the final round combines the own id_s with the set of the
+ * neighbours' id_o and no edge labels. A vertex without out-edges keeps both
+ * identifiers. The definition's P_k (bisim_iterate) always refines this
+ * partition; where it is strictly finer, the literal algorithm merges classes
+ * that the definition separates. Writes canonical ids to block (int32[n],
+ * device or host) and the block count to *out_num_blocks (may be NULL).
+ * Leaves the context's own partition unchanged. Not for batched contexts
+ * (BISIM_ESTATE). Allocates about 2k temporary contexts on an auxiliary graph
+ * of 2n vertices; a diagnostic, not a fast path. Synchronises `stream`.
+ */
+bisim_status bisim_literal_alg4(bisim_ctx* ctx, int32_t k, int32_t* block, int64_t* out_num_blocks,
+                                void* stream);
+
 /* Counters of the context (see bisim_stats). Synchronises nothing. */
 bisim_status bisim_get_stats(const bisim_ctx* ctx, bisim_stats* out);
 

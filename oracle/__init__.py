@@ -173,6 +173,44 @@ def refine_round_threads(n, src, dst, elabel, P, threads=0, alive=None, graph=No
     return out
 
 
+def literal_alg4(n, src, dst, elabel, vlabel, k, alive=None):
+    """Algorithm 4 (Section 3.3.1) as printed, with exact identifiers.
+
+    Two identifiers per vertex start from the label partition. For k = 1 one
+    round gives id_s <- (own id_s, {(label, neighbour id_o)}). For k >= 2,
+    rounds 1 .. k-1 give id_s <- (own id_s, {(label, neighbour id_s)}) and
+    id_o <- {(label, neighbour id_o)} in round 1, {neighbour id_o} after it (no
+    own term); the final round gives id_s <- (own id_s, {neighbour id_o}). A
+    vertex that receives no message (no live out-edge) keeps its identifiers.
+    Identifiers are compared exactly (the paper assumes unique hashes), so each
+    is a partition; returns canonical ids (smallest member, -1 if dead).
+    Plain Python: tuples and frozensets in dicts.
+    """
+    live = [True] * n if alive is None else [bool(a) for a in np.asarray(alive).tolist()]
+    out = [[] for _ in range(n)]
+    for u, w, l in zip(np.asarray(src).tolist(), np.asarray(dst).tolist(), np.asarray(elabel).tolist()):
+        if live[u] and live[w]:
+            out[u].append((int(l), w))
+
+    def canon(key):
+        first = {}
+        return [first.setdefault(key(v), v) if live[v] else -1 for v in range(n)]
+
+    ids = ido = canon(lambda v: int(vlabel[v]))
+    if k == 0:
+        return np.array(ids, np.int32)
+    if k == 1:
+        return np.array(canon(lambda v: (ids[v], frozenset((l, ido[w]) for l, w in out[v]))), np.int32)
+    for i in range(1, k):
+        new_s = canon(lambda v: (ids[v], frozenset((l, ids[w]) for l, w in out[v])))
+        if i == 1:
+            new_o = canon(lambda v: ("msg", frozenset((l, ido[w]) for l, w in out[v])) if out[v] else ("keep", ido[v]))
+        else:
+            new_o = canon(lambda v: ("msg", frozenset(ido[w] for _, w in out[v])) if out[v] else ("keep", ido[v]))
+        ids, ido = new_s, new_o
+    return np.array(canon(lambda v: (ids[v], frozenset(ido[w] for _, w in out[v]))), np.int32)
+
+
 def summary_edges(src, dst, elabel, P, label_filter=None):
     """Edges of the summary graph of partition P (Section 2.6): one per distinct
     (P[u], l, P[w]) over the edges (u, w, l) whose endpoints are in a block,

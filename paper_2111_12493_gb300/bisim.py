@@ -79,6 +79,7 @@ def _load():
         "bisim_refine_round_noalloc": (ctypes.c_int, [i32, i64, p, p, p, p, p, ctypes.POINTER(i64), p]),
         "bisim_autotune": (ctypes.c_int, [p, i32, ctypes.POINTER(Options), p]),
         "get_block_sizes": (ctypes.c_int, [p, p, p]),
+        "bisim_literal_alg4": (ctypes.c_int, [p, i32, p, ctypes.POINTER(i64), p]),
         "get_summary_edges": (ctypes.c_int, [p, p, p, p, i64, ctypes.POINTER(i64), p]),
     }
     for name, (res, args) in sigs.items():
@@ -246,6 +247,17 @@ def get_summary_edges(ctx: Context, stream=None):
         if count.value <= cap:
             return tuple(o[:count.value] for o in outs)
         cap = count.value
+
+
+def bisim_literal_alg4(ctx: Context, k: int, out=None, stream=None):
+    """Diagnostic: the partition of Algorithm 4 taken literally (two identifier
+    tracks, no edge labels in the last round). Returns (partition, blocks)."""
+    if out is None:
+        out = torch.empty(ctx.n_vertices, dtype=torch.int32, device="cuda")
+    blocks = ctypes.c_int64()
+    _check(_lib.bisim_literal_alg4(ctx.ptr, k, _ptr(out, torch.int32, "out", ctx.n_vertices), ctypes.byref(blocks),
+                                   _stream(stream)), ctx.ptr)
+    return out, blocks.value
 
 
 def bisim_autotune(ctx: Context, rounds: int = 2, stream=None) -> dict:

@@ -401,6 +401,56 @@ def test_summary_skips_dead_vertices_and_every_edge_has_a_witness():
     assert sorted(np.flatnonzero(sizes).tolist()) == sorted(set(int(b) for b in P if b >= 0))
 
 
+# --------------------------------------------------------------------------- Algorithm 4 taken literally
+
+def test_literal_alg4_reproduces_the_worked_example():
+    # the worked example of Section 3.3.1 runs Algorithm 4 itself on the
+    # Figure 3 graph at k = 2 (tautology start): classes {v1}, {v2}, {v3, v4}
+    gf = parse_golden("fig3_worked_example.txt")
+    s, d, l = edges_to_arrays(gf["edges"])
+    for mode in ("T", "L"):
+        P = oracle.literal_alg4(gf["n"], s, d, l, np.array(gf["vlabel"][mode], np.int32), 2)
+        assert P.tolist() == gf["expect"][(mode, 2)].tolist()
+
+
+def test_literal_alg4_merges_what_the_definition_separates():
+    # v -a-> X, v -b-> Y and v' -a-> Y, v' -b-> X, where X and Y differ by
+    # their own out-label: the last round of Algorithm 4 drops the edge label,
+    # so it merges v and v' at k = 2; the definition keeps the pairing apart
+    edges = [(0, 2, 0), (0, 3, 1), (1, 3, 0), (1, 2, 1), (2, 4, 2), (3, 5, 3)]
+    s, d, l = edges_to_arrays(edges)
+    vl = np.zeros(6, np.int32)
+    lit = oracle.literal_alg4(6, s, d, l, vl, 2)
+    P, _, _ = oracle.refine(6, s, d, l, vl, 2)
+    assert lit[0] == lit[1] and P[0] != P[1]
+
+
+def test_literal_alg4_keeps_sinks_apart_by_their_identifier():
+    # two sinks with different labels reached over the same edge label: the
+    # sinks keep their id_o (no messages), so their predecessors stay apart
+    edges = [(0, 2, 0), (1, 3, 0)]
+    s, d, l = edges_to_arrays(edges)
+    vl = np.array([0, 0, 1, 2], np.int32)
+    lit = oracle.literal_alg4(4, s, d, l, vl, 2)
+    assert lit.tolist() == [0, 1, 2, 3]
+
+
+def test_literal_alg4_is_refined_by_the_definition():
+    rnd = random.Random(4)
+    for _ in range(200):
+        n = rnd.randint(1, 12)
+        edges = [(rnd.randrange(n), rnd.randrange(n), rnd.randrange(2)) for _ in range(rnd.randint(0, 3 * n))]
+        s, d, l = edges_to_arrays(edges) if edges else (np.zeros(0, np.int32),) * 3
+        vl = np.array([rnd.randrange(2) for _ in range(n)], np.int32)
+        alive = np.array([rnd.random() > 0.1 for _ in range(n)], np.uint8)
+        for k in range(0, 5):
+            lit = oracle.literal_alg4(n, s, d, l, vl, k, alive=alive)
+            P, _, _ = oracle.refine(n, s, d, l, vl, k, alive=alive)
+            if k <= 1:
+                assert lit.tolist() == P.tolist()      # one round: the same signature
+            assert _refines(P, lit)
+
+
 # --------------------------------------------------------------------------- CPU baselines
 
 @pytest.mark.parametrize("seed", range(4))
