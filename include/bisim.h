@@ -326,6 +326,35 @@ bisim_status bisim_refine_round_noalloc(int32_t n_vertices, int64_t n_edges, con
 bisim_status bisim_literal_alg4(bisim_ctx* ctx, int32_t k, int32_t* block, int64_t* out_num_blocks,
                                 void* stream);
 
+/*
+ * bisim_export_state -- the context's state as one self-contained byte blob:
+ * the options (direction, label filter, k_incremental, ...), vertex labels and
+ * live flags, the current partition, the graph as it stands after every
+ * update batch (as an out-CSR of the context's own edge list), and, once
+ * apply_updates has built it, the incremental state of Section 3.2 (per level
+ * the block of every vertex, the block records and the signature index that
+ * play the role of the vertex hash index of Section 3.2.1). Batches applied to
+ * an imported context continue exactly where the exported one stood; by
+ * Theorem 2 (Section 3.2.2) the partition then equals a batch run on the
+ * edited graph.
+ *   buf        host memory of `capacity` bytes, or NULL
+ *   out_bytes  the blob's size; the blob is written only when capacity >= it
+ *              (call with capacity 0 to size the buffer)
+ * Not for batched contexts (BISIM_ESTATE). The format is this library's own
+ * (versioned, host byte order). Synchronises `stream`.
+ */
+bisim_status bisim_export_state(bisim_ctx* ctx, void* buf, int64_t capacity, int64_t* out_bytes, void* stream);
+
+/*
+ * bisim_import_state -- a new context from a blob of bisim_export_state (host
+ * memory, `bytes` long). The graph, options, partition and incremental state
+ * are restored as exported, nothing is recomputed but the round layout and
+ * the row store of the graph. BISIM_EINVAL for a blob that is not one
+ * (magic, version, length or header inconsistent); nothing is allocated then.
+ * Synchronises `stream`.
+ */
+bisim_status bisim_import_state(bisim_ctx** out, const void* buf, int64_t bytes, void* stream);
+
 /* Counters of the context (see bisim_stats). Synchronises nothing. */
 bisim_status bisim_get_stats(const bisim_ctx* ctx, bisim_stats* out);
 

@@ -80,6 +80,8 @@ def _load():
         "bisim_autotune": (ctypes.c_int, [p, i32, ctypes.POINTER(Options), p]),
         "get_block_sizes": (ctypes.c_int, [p, p, p]),
         "bisim_literal_alg4": (ctypes.c_int, [p, i32, p, ctypes.POINTER(i64), p]),
+        "bisim_export_state": (ctypes.c_int, [p, p, i64, ctypes.POINTER(i64), p]),
+        "bisim_import_state": (ctypes.c_int, [pp, p, i64, p]),
         "get_summary_edges": (ctypes.c_int, [p, p, p, p, i64, ctypes.POINTER(i64), p]),
     }
     for name, (res, args) in sigs.items():
@@ -247,6 +249,24 @@ def get_summary_edges(ctx: Context, stream=None):
         if count.value <= cap:
             return tuple(o[:count.value] for o in outs)
         cap = count.value
+
+
+def bisim_export_state(ctx: Context, stream=None) -> bytes:
+    """The context's state (graph, options, partition, incremental levels) as bytes."""
+    size = ctypes.c_int64()
+    _check(_lib.bisim_export_state(ctx.ptr, None, 0, ctypes.byref(size), _stream(stream)), ctx.ptr)
+    buf = ctypes.create_string_buffer(size.value)
+    _check(_lib.bisim_export_state(ctx.ptr, buf, size.value, ctypes.byref(size), _stream(stream)), ctx.ptr)
+    return buf.raw
+
+
+def bisim_import_state(blob: bytes, stream=None) -> Context:
+    """A new context from bisim_export_state's bytes."""
+    out = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(_lib.bisim_import_state(ctypes.byref(out), buf, len(blob), _stream(stream)))
+    n = ctypes.cast(buf, ctypes.POINTER(ctypes.c_int32))[4]      # StateHeader.n follows magic, version, size
+    return Context(out, n)
 
 
 def bisim_literal_alg4(ctx: Context, k: int, out=None, stream=None):

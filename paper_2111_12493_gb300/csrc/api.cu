@@ -636,6 +636,209 @@ bisim_status apply_updates(bisim_ctx* ctx, const bisim_op* ops, int64_t n_ops, v
     return BISIM_OK;
 }
 
+// ----------------------------------------------------------------------------- state export / import
+
+namespace {
+
+// Fixed part of an exported state; the arrays follow it, each starting on an
+// 8-byte boundary, in the order of state_arrays().
+struct StateHeader {
+    char magic[8];                 // "BISIMST1"
+    uint32_t version;              // 1
+    uint32_t header_bytes;
+    int32_t n;
+    int32_t inc_k;                 // levels of incremental state, -1: none
+    int64_t m;                     // edges of the context's own edge list (after direction and filter)
+    int32_t k_incremental, hash_bits, small_max_degree, mid_max_degree, hub_chunk, flags, direction, nfilter;
+    int64_t mem_budget_bytes;
+    int64_t bcap;
+    uint64_t isize;
+    int64_t bnext[kMaxIncLevels + 1];
+    int64_t itomb[kMaxIncLevels + 1];
+    int32_t cur_k;
+    int32_t has_alive;
+    int64_t updates_applied;
+    int64_t num_blocks;
+    int32_t rounds, rounds_executed;
+};
+
+constexpr char kStateMagic[8] = {'B', 'I', 'S', 'I', 'M', 'S', 'T', '1'};
+
+struct StateArray {
+    void* dev;                     // device source (export) or destination (import); null: host-side item
+    size_t bytes;
+};
+
+size_t pad8(size_t b) { return (b + 7) & ~size_t(7); }
+
+// The arrays of a state in blob order: filter, vertex labels, alive flags,
+// current partition, CSR (row_ptr, col, labels), then per level block ids,
+// |S|, stale flags, block records (key, count, smallest member) and index
+// (key, block).
+std::vector<StateArray> state_arrays(const bisim_ctx* ctx, const StateHeader& h) {
+    const size_t n = static_cast<size_t>(h.n), m = static_cast<size_t>(h.m);
+    std::vector<StateArray> a;
+    a.push_back({ctx->dfilter, 4 * static_cast<size_t>(h.nfilter)});
+    a.push_back({ctx->vlabel, 4 * n});
+    a.push_back({ctx->alive, h.has_alive ? n : 0});
+    a.push_back({ctx->P[ctx->cur], 4 * n});
+    a.push_back({ctx->row_ptr, 8 * (n + 1)});
+    a.push_back({ctx->col, 4 * m});
+    a.push_back({ctx->elab, 4 * m});
+    for (int j = 0; j <= h.inc_k; ++j) {
+        a.push_back({ctx->lid[j], 4 * n});
+        a.push_back({ctx->lcnt[j], 4 * n});
+        a.push_back({ctx->lstale[j], n});
+        a.push_back({ctx->bkey[j], 8 * static_cast<size_t>(h.bcap)});
+        a.push_back({ctx->bcnt[j], 4 * static_cast<size_t>(h.bcap)});
+        a.push_back({ctx->bmin[j], 4 * static_cast<size_t>(h.bcap)});
+        a.push_back({ctx->ikey[j], 8 * h.isize});
+        a.push_back({ctx->ibid[j], 4 * h.isize});
+    }
+    return a;
+}
+
+size_t state_bytes(const std::vector<StateArray>& a) {
+    size_t b = pad8(sizeof(StateHeader));
+    for (const auto& x : a) b += pad8(x.bytes);
+    return b;
+}
+
+}  // namespace
+
+bisim_status bisim_export_state(bisim_ctx* ctx, void* buf, int64_t capacity, int64_t* out_bytes, void* stream) {
+    if (ctx == nullptr) return set_error(nullptr, BISIM_EINVAL, "ctx is NULL");
+    ctx->last_stream = stream;
+    if (out_bytes == nullptr || capacity < 0) return set_error(ctx, BISIM_EINVAL, "invalid size arguments");
+    if (ctx->gid != nullptr) return set_error(ctx, BISIM_ESTATE, "batched contexts have no exportable state");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bisim_status st;
+    // the CSR of the current graph (rebuilt from the row store when batches edited it)
+    if ((st = refresh_after_edit(ctx, s)) != BISIM_OK || (st = ensure_vertex_csr(ctx, s)) != BISIM_OK) return st;
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kStateMagic, 8);
+    h.version = 1;
+    h.header_bytes = sizeof(StateHeader);
+    h.n = ctx->n;
+    h.m = ctx->m;
+    h.inc_k = ctx->inc_k == ctx->opt.k_incremental && ctx->store_ready ? ctx->inc_k : -1;
+    h.k_incremental = ctx->opt.k_incremental;
+    h.hash_bits = ctx->opt.hash_bits;
+    h.small_max_degree = ctx->opt.small_max_degree;
+    h.mid_max_degree = ctx->opt.mid_max_degree;
+    h.hub_chunk = ctx->opt.hub_chunk;
+    h.flags = ctx->opt.flags;
+    h.direction = ctx->opt.direction;
+    h.nfilter = ctx->nfilter;
+    h.mem_budget_bytes = ctx->opt.mem_budget_bytes;
+    h.bcap = h.inc_k >= 0 ? ctx->bcap : 0;
+    h.isize = h.inc_k >= 0 ? ctx->isize : 0;
+    for (int j = 0; j <= kMaxIncLevels; ++j) {
+        h.bnext[j] = ctx->bnext[j];
+        h.itomb[j] = ctx->itomb[j];
+    }
+    h.cur_k = ctx->cur_k;
+    h.has_alive = ctx->alive != nullptr ? 1 : 0;
+    h.updates_applied = ctx->stats.updates_applied;
+    h.num_blocks = ctx->stats.num_blocks;
+    h.rounds = ctx->stats.rounds;
+    h.rounds_executed = ctx->stats.rounds_executed;
+    const std::vector<StateArray> arrays = state_arrays(ctx, h);
+    const size_t total = state_bytes(arrays);
+    *out_bytes = static_cast<int64_t>(total);
+    if (buf == nullptr || capacity < static_cast<int64_t>(total)) return BISIM_OK;
+    char* p = static_cast<char*>(buf);
+    std::memset(p, 0, pad8(sizeof(StateHeader)));
+    std::memcpy(p, &h, sizeof(h));
+    size_t off = pad8(sizeof(StateHeader));
+    cudaError_t e;
+    for (const auto& x : arrays) {
+        if (x.bytes > 0 && (e = cudaMemcpyAsync(p + off, x.dev, x.bytes, cudaMemcpyDefault, s)))
+            return cuda_error(ctx, e, "export state");
+        off += pad8(x.bytes);
+    }
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "export state");
+    return BISIM_OK;
+}
+
+bisim_status bisim_import_state(bisim_ctx** out, const void* buf, int64_t bytes, void* stream) {
+    if (out == nullptr) return set_error(nullptr, BISIM_EINVAL, "out pointer is NULL");
+    *out = nullptr;
+    if (buf == nullptr || bytes < static_cast<int64_t>(sizeof(StateHeader)))
+        return set_error(nullptr, BISIM_EINVAL, "state buffer too small");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1 || h.header_bytes != sizeof(StateHeader))
+        return set_error(nullptr, BISIM_EINVAL, "not an exported bisim state (magic or version)");
+    if (h.n < 0 || h.m < 0 || h.inc_k < -1 || h.inc_k > kMaxIncLevels || h.nfilter < 0 || h.bcap < 0 ||
+        (h.inc_k >= 0 && (h.bcap < 2 * static_cast<int64_t>(h.n) || h.isize == 0 || (h.isize & (h.isize - 1)))))
+        return set_error(nullptr, BISIM_EINVAL, "exported state header is inconsistent");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // sizes from the header alone, before anything is allocated
+    bisim_ctx probe;
+    probe.n = h.n;
+    const std::vector<StateArray> sizes = state_arrays(&probe, h);
+    if (static_cast<int64_t>(state_bytes(sizes)) != bytes)
+        return set_error(nullptr, BISIM_EINVAL, "exported state has the wrong length");
+    const char* p = static_cast<const char*>(buf);
+    std::vector<const char*> at;
+    size_t off = pad8(sizeof(StateHeader));
+    for (const auto& x : sizes) {
+        at.push_back(p + off);
+        off += pad8(x.bytes);
+    }
+    bisim_options o;
+    bisim_default_options(&o);
+    o.k_incremental = h.k_incremental;
+    o.hash_bits = h.hash_bits;
+    o.small_max_degree = h.small_max_degree;
+    o.mid_max_degree = h.mid_max_degree;
+    o.hub_chunk = h.hub_chunk;
+    o.flags = h.flags;
+    o.direction = h.direction;
+    o.n_label_filter = h.nfilter;
+    o.label_filter = reinterpret_cast<const int32_t*>(at[0]);
+    o.mem_budget_bytes = h.mem_budget_bytes;
+    bisim_ctx* ctx = nullptr;
+    bisim_status st = new_ctx(out, h.n, h.m, &o, s, &ctx);
+    if (st != BISIM_OK) return st;
+    // the exported edge list already has the direction and filter applied: built as given
+    const uint8_t* alive = h.has_alive ? reinterpret_cast<const uint8_t*>(at[2]) : nullptr;
+    if ((st = copy_vertex_arrays(ctx, reinterpret_cast<const int32_t*>(at[1]), alive, s)) == BISIM_OK &&
+        (st = build_from_csr(ctx, reinterpret_cast<const int64_t*>(at[4]), reinterpret_cast<const int32_t*>(at[5]),
+                             reinterpret_cast<const int32_t*>(at[6]), s)) == BISIM_OK &&
+        (st = finish_init(ctx, s)) == BISIM_OK && h.inc_k >= 0)
+        st = inc_alloc_levels(ctx, h.inc_k, h.bcap, h.isize, s);
+    cudaError_t e = cudaSuccess;
+    if (st == BISIM_OK) {
+        const std::vector<StateArray> dst = state_arrays(ctx, h);
+        for (size_t i = 7; i < dst.size() && !e; ++i)       // the levels
+            if (dst[i].bytes > 0) e = cudaMemcpyAsync(dst[i].dev, at[i], dst[i].bytes, cudaMemcpyHostToDevice, s);
+        if (!e && h.n > 0) e = cudaMemcpyAsync(ctx->P[ctx->cur], at[3], 4 * static_cast<size_t>(h.n), cudaMemcpyHostToDevice, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) st = cuda_error(ctx, e, "import state");
+    }
+    if (st != BISIM_OK) {
+        const std::string msg = ctx->err;
+        destroy_ctx(ctx);
+        return set_error(nullptr, st, msg);
+    }
+    for (int j = 0; j <= kMaxIncLevels; ++j) ctx->itomb[j] = h.itomb[j];
+    if (h.inc_k >= 0 && (st = inc_set_next_ids(ctx, h.bnext, s)) != BISIM_OK) {
+        const std::string msg = ctx->err;
+        destroy_ctx(ctx);
+        return set_error(nullptr, st, msg);
+    }
+    ctx->cur_k = h.cur_k;
+    ctx->stats.updates_applied = h.updates_applied;
+    ctx->stats.num_blocks = h.num_blocks;
+    ctx->stats.rounds = h.rounds;
+    ctx->stats.rounds_executed = h.rounds_executed;
+    *out = ctx;
+    return BISIM_OK;
+}
+
 bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream) {
     if (ctx == nullptr) return set_error(nullptr, BISIM_EINVAL, "ctx is NULL");
     ctx->last_stream = stream;

@@ -590,6 +590,10 @@ bisim_status csr_sources(bisim_ctx* ctx, const int64_t* row_ptr, int32_t n, int6
 // ----------------------------------------------------------------------------- incremental levels (inc.cu)
 
 bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s);
+// The row store and the levels' arrays of K levels, allocated and not filled (state import).
+bisim_status inc_alloc_levels(bisim_ctx* ctx, int K, int64_t bcap, uint64_t isize, cudaStream_t s);
+// Sets the next unused block id of every level (host and device counters).
+bisim_status inc_set_next_ids(bisim_ctx* ctx, const int64_t* bnext, cudaStream_t s);
 bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* rowchg, int64_t n_ops,
                         cudaStream_t s);
 void inc_release(bisim_ctx* ctx, cudaStream_t s);

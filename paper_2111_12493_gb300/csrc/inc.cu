@@ -1309,6 +1309,58 @@ void inc_release(bisim_ctx* ctx, cudaStream_t s) {
     ctx->inc_k = -1;
 }
 
+// The incremental state of K levels allocated but not computed: the row
+// store (from the CSR), the levels' arrays at the given record and index
+// sizes, and the per-batch scratch. bisim_import_state fills the levels from
+// an exported state.
+bisim_status inc_alloc_levels(bisim_ctx* ctx, int K, int64_t bcap, uint64_t isize, cudaStream_t s) {
+    if (K < 0 || K > kMaxIncLevels) return set_error(ctx, BISIM_EINVAL, "k_incremental out of range");
+    inc_release(ctx, s);
+    bisim_status st;
+    if ((st = store_build(ctx, s)) != BISIM_OK) return st;
+    if ((st = refresh_after_edit(ctx, s)) != BISIM_OK) return st;
+    if ((st = ensure_skey(ctx, s)) != BISIM_OK) return st;
+    const size_t n = static_cast<size_t>(std::max(ctx->n, 1));
+    ctx->bcap = bcap;
+    ctx->isize = isize;
+    cudaError_t e;
+    for (int j = 0; j <= K; ++j) {
+        if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->lid[j]), 4 * n, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->lcnt[j]), 4 * n, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bkey[j]), 8 * static_cast<size_t>(bcap), s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bcnt[j]), 4 * static_cast<size_t>(bcap), s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bmin[j]), 4 * static_cast<size_t>(bcap), s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ikey[j]), 8 * isize, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ibid[j]), 4 * isize, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->lstale[j]), n, s))) {
+            inc_release(ctx, s);
+            return cuda_error(ctx, e, "alloc incremental state");
+        }
+    }
+    ctx->inc_k = K;
+    ctx->inc_small_max = ctx->opt.small_max_degree;
+    Scratch* Sp = new Scratch();
+    if ((e = alloc_scratch(ctx, *Sp, s))) {
+        delete Sp;
+        inc_release(ctx, s);
+        return cuda_error(ctx, e, "alloc incremental scratch");
+    }
+    ctx->inc_ws = Sp;
+    return BISIM_OK;
+}
+
+// Next unused block id per level, on the host and in the device counters the
+// settle kernels draw new ids from (state import).
+bisim_status inc_set_next_ids(bisim_ctx* ctx, const int64_t* bnext, cudaStream_t s) {
+    if (ctx->inc_ws == nullptr) return set_error(ctx, BISIM_ESTATE, "no incremental state");
+    Scratch& S = *static_cast<Scratch*>(ctx->inc_ws);
+    for (int j = 0; j <= kMaxIncLevels; ++j) ctx->bnext[j] = bnext[j];
+    cudaError_t e = cudaMemcpyAsync(S.dbnext, ctx->bnext, sizeof(int64_t) * (kMaxIncLevels + 1),
+                                    cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaStreamSynchronize(s);          // the source is the context's host array
+    return e ? cuda_error(ctx, e, "restore block ids") : BISIM_OK;
+}
+
 // Full build of the incremental state: every live vertex is the frontier of
 // an empty state at every level.
 bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s) {
