@@ -864,6 +864,7 @@ bisim_status get_partition(bisim_ctx* ctx, int32_t* block, void* stream) {
 bisim_status bisim_get_stats(const bisim_ctx* ctx, bisim_stats* out) {
     if (ctx == nullptr || out == nullptr) return set_error(nullptr, BISIM_EINVAL, "NULL argument");
     *out = ctx->stats;
+    out->device_bytes = ctx->device_bytes;         // what the context holds now
     return BISIM_OK;
 }
 

@@ -885,6 +885,7 @@ struct HostStage {
 // Work buffers of the incremental path, kept between batches.
 struct Scratch {
     char* base = nullptr;
+    size_t bytes = 0;                  // device bytes of base (counted in the context's device_bytes)
     Work W{};
     int64_t* dbnext = nullptr;         // [kMaxIncLevels + 1] next unused block id per level
     unsigned long long* dacc = nullptr;   // [kMaxIncLevels + 1][4] per-level accumulators (k_settle)
@@ -921,6 +922,8 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     need(4 * n); need(16); need(3 * sizeof(RowTask) * n); need(16);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&S.base), bytes, s);
     if (e) return e;
+    S.bytes = bytes;
+    ctx->device_bytes += static_cast<int64_t>(bytes);
     if ((e = cudaHostAlloc(reinterpret_cast<void**>(&S.h), sizeof(HostStage), cudaHostAllocDefault))) {
         cudaFreeAsync(S.base, s);
         S.base = nullptr;
@@ -1289,6 +1292,7 @@ bisim_status write_output(bisim_ctx* ctx, cudaStream_t s) {
 void inc_release(bisim_ctx* ctx, cudaStream_t s) {
     const size_t n = static_cast<size_t>(std::max(ctx->n, 1));
     if (ctx->inc_ws != nullptr) {
+        ctx->device_bytes -= static_cast<int64_t>(static_cast<Scratch*>(ctx->inc_ws)->bytes);
         free_scratch(static_cast<Scratch*>(ctx->inc_ws), s);
         ctx->inc_ws = nullptr;
     }

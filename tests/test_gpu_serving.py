@@ -130,3 +130,78 @@ def test_memory_budget_serialises_large_requests(serving):
     want, _, _ = oracle.refine(G["n"], G["src"], G["dst"], G["elabel"], G["vlabel"], 2)
     for r in res:
         assert np.array_equal(r, want)
+
+
+@pytest.mark.parametrize("n,m,k", [(5_000, 20_000, 1), (50_000, 400_000, 3), (300_000, 600_000, 3),
+                                   (1_000_000, 10_000_000, 2)])
+def test_admission_estimate_covers_the_measured_footprint(serving, n, m, k):
+    # the scheduler admits a graph by estimate_bytes before its context
+    # exists: it must not underestimate what the context then holds, after
+    # the summarization and after the incremental state is primed
+    import torch
+    from paper_2111_12493_gb300 import bisim
+    g = (graphgen.uniform_graph(n=n, m=m, seed=23) if m <= 2 * n else
+         graphgen.powerlaw_graph(n=n, m=m, dmax=min(100_000, m // 10), n_elabels=200, n_vlabels=20, seed=24))
+    d = [torch.from_numpy(g[x]).cuda() for x in ("src", "dst", "elabel", "vlabel")]
+    ctx = bisim.summarize_init_coo(n, *d, options=bisim.default_options(k_incremental=k))
+    bisim.bisim_iterate(ctx, -1, 10)
+    after_iterate = bisim.bisim_get_stats(ctx)["device_bytes"]
+    bisim.apply_updates(ctx, torch.zeros((0, 4), dtype=torch.int32, device="cuda"))
+    primed = bisim.bisim_get_stats(ctx)["device_bytes"]
+    bisim.summarize_destroy(ctx)
+    est = serving.estimate_bytes(n, m, k)
+    assert est >= primed >= after_iterate > 0, (est, primed, after_iterate)
+    assert est <= 1.6 * primed + (64 << 20)           # and stays close enough to admit others
+
+
+def test_two_requests_overlap_on_the_device(serving):
+    # two independent summarizations on two slots: their device spans (CUDA
+    # events on each slot's stream) intersect, and together they finish in
+    # less time than one after the other
+    import threading
+    import torch
+    gs = [graphgen.powerlaw_graph(n=400_000, m=4_000_000, dmax=40_000, n_elabels=100, n_vlabels=20, seed=s)
+          for s in (25, 26)]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    reqs = [serving.Request("summarize", i, dict(n=g["n"], src=t(g["src"]), dst=t(g["dst"]), edge_label=t(g["elabel"]),
+                                                 vertex_label=t(g["vlabel"]), k=-1, cap=10, keep=False))
+            for i, g in enumerate(gs)]
+    ex = serving.GpuExecutor(slots=2)
+    for r in reqs:                                     # warm-up (round graphs, pools)
+        ex(r, 0)
+    torch.cuda.synchronize()
+
+    def timed(slot, r, out):
+        s = ex.streams[slot]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        ex(r, slot)
+        e1.record(s)
+        out[slot] = (e0, e1)
+
+    solo = []
+    for i, r in enumerate(reqs):
+        out = {}
+        timed(i, r, out)
+        torch.cuda.synchronize()
+        solo.append(out[i][0].elapsed_time(out[i][1]))
+    best = None
+    for _ in range(3):
+        out = {}
+        th = [threading.Thread(target=timed, args=(i, r, out)) for i, r in enumerate(reqs)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        torch.cuda.synchronize()
+        (a0, a1), (b0, b1) = out[0], out[1]
+        # spans relative to a0; overlap = min(ends) - max(starts)
+        sa, ea = 0.0, a0.elapsed_time(a1)
+        sb, eb = a0.elapsed_time(b0), a0.elapsed_time(b1)
+        together = max(ea, eb) - min(sa, sb)
+        overlap = min(ea, eb) - max(sa, sb)
+        if best is None or together < best[0]:
+            best = (together, overlap)
+    together, overlap = best
+    assert overlap > 0, (solo, together, overlap)
+    assert together < 0.95 * sum(solo), (solo, together)
