@@ -39,15 +39,34 @@ __global__ void k_validate_coo(const int32_t* __restrict__ src, const int32_t* _
     }
 }
 
-// Sort keys are the sources' positions in the layout (so the sorted edges are
-// its packed rows); values are the packed (label, target) words.
-__global__ void k_pack_coo(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                           const int32_t* __restrict__ elab, int64_t m, const int32_t* __restrict__ vpos,
-                           uint32_t* __restrict__ keys, uint64_t* __restrict__ vals) {
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        keys[e] = static_cast<uint32_t>(vpos[src[e]]);
-        vals[e] = (static_cast<uint64_t>(static_cast<uint32_t>(elab[e])) << 32) | static_cast<uint32_t>(dst[e]);
+// Every edge written into its source's packed row of the layout: the row of
+// position p is [prp[p], prp[p+1]); a per-row cursor hands out the slots, one
+// atomic per distinct source in a warp (the lanes of one source take
+// consecutive slots in lane order). Signatures are sets, so the order of the
+// edges inside a row is never read; it follows the order in which warps reach
+// the row's cursor. Edge lists grouped by source (the common case) write each
+// row in runs.
+__global__ void k_place_coo(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                            const int32_t* __restrict__ elab, int64_t m, const int32_t* __restrict__ vpos,
+                            const int64_t* __restrict__ prp, int32_t* __restrict__ cursor,
+                            unsigned long long* __restrict__ pe) {
+    const unsigned lane = threadIdx.x & 31u;
+    // trip count is uniform across the warp so the match below sees every lane
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t e0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; e0 < m; e0 += stride) {
+        const int64_t e = e0 + threadIdx.x;
+        int32_t pos = -1;
+        if (e < m) pos = vpos[src[e]];
+        const unsigned peers = __match_any_sync(0xffffffffu, pos);
+        const int leader = __ffs(peers) - 1;
+        int32_t base = 0;
+        if (pos >= 0 && lane == static_cast<unsigned>(leader)) base = atomicAdd(&cursor[pos], __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (pos >= 0) {
+            const int32_t r = base + __popc(peers & ((1u << lane) - 1u));
+            pe[prp[pos] + r] = (static_cast<unsigned long long>(static_cast<uint32_t>(elab[e])) << 32) |
+                               static_cast<uint32_t>(dst[e]);
+        }
     }
 }
 
@@ -76,40 +95,28 @@ __global__ void k_validate_csr(const int64_t* __restrict__ rp, const int32_t* __
     }
 }
 
-// Degree class of each live vertex (see kNumClasses); dead vertices get kClassDead.
-
-int bits_for(int64_t n) {
-    int b = 0;
-    while ((static_cast<int64_t>(1) << b) < n) ++b;
-    return b;
-}
-
 }  // namespace
 
 // COO -> the round layout directly: out-degrees, then the positions of the
-// layout (vertices grouped by degree class), then one stable LSD radix sort of
-// the edges keyed by their source's position. The sorted (label, target)
-// words are the layout's packed rows; the vertex-ordered CSR is rebuilt from
-// them only if an update or the list-mode path asks for it.
+// layout (vertices grouped by degree class) and their row offsets, then every
+// edge placed into its source's row (k_place_coo). The (label, target) words
+// are the layout's packed rows; the vertex-ordered CSR is rebuilt from them
+// only if an update or the list-mode path asks for it.
 bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* dst,
                             const int32_t* elab, cudaStream_t s) {
     const int32_t n = ctx->n;
     const int64_t m = ctx->m;
     const int64_t cap = std::max<int64_t>(m, 1);
     cudaError_t e;
-    const size_t tmp_words = std::max(radix_temp_words(m), scan_temp_words(n + 1));
-    const size_t bytes = sizeof(uint32_t) * 2 * cap + sizeof(int32_t) * (n + 1) + sizeof(int64_t) * tmp_words + 256 * 4;
-    char* scratch = nullptr;
-    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s))) return cuda_error(ctx, e, "alloc CSR scratch");
-    auto carve = [&](size_t b) { char* p = scratch; scratch += (b + 255) & ~size_t(255); return p; };
-    char* base = scratch;
-    uint32_t* k0 = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * cap));
-    uint32_t* k1 = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * cap));
-    int32_t* deg = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (n + 1)));
-    int64_t* tmp = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * tmp_words));
-    uint64_t *v0 = nullptr, *v1 = nullptr;
-    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&v0), sizeof(uint64_t) * cap, s)) ||
-        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&v1), sizeof(uint64_t) * cap, s))) {
+    // scratch: out-degrees, then the per-row cursors of the placement
+    const size_t nv = static_cast<size_t>(n) + 1;
+    const size_t bytes = 2 * ((sizeof(int32_t) * nv + 255) & ~size_t(255));
+    char* base = nullptr;
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, s))) return cuda_error(ctx, e, "alloc CSR scratch");
+    int32_t* deg = reinterpret_cast<int32_t*>(base);
+    int32_t* cursor = reinterpret_cast<int32_t*>(base + bytes / 2);
+    unsigned long long* rows = nullptr;
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&rows), sizeof(unsigned long long) * cap, s))) {
         cudaFreeAsync(base, s);
         return cuda_error(ctx, e, "alloc packed rows");
     }
@@ -133,20 +140,15 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
         cudaFreeAsync(base, s);
         return st;
     }
-    int which = 0;
     if (m > 0) {
-        {
-            // read src, dst, label and the source's position; write key + value
-            Launch L(site_pack, s, 0, m, 28.0 * m);
-            k_pack_coo<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(src, dst, elab, m, ctx->dvpos, k0,
-                                                                                    v0);
-        }
-        which = radix_sort_pairs(k0, v0, k1, v1, m, bits_for(n), tmp, s);
+        // read src, dst, label, the source's position and row offset; write the packed word
+        cudaMemsetAsync(cursor, 0, sizeof(int32_t) * nv, s);
+        Launch L(site_pack, s, 0, m, 24.0 * m);
+        k_place_coo<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(src, dst, elab, m, ctx->dvpos,
+                                                                                 ctx->dprp, cursor, rows);
     }
-    uint64_t* rows = which ? v1 : v0;
-    ctx_free(ctx, which ? v0 : v1, sizeof(uint64_t) * cap, s);
     ctx_free(ctx, ctx->dpe, sizeof(unsigned long long) * ctx->dpe_cap, s);
-    ctx->dpe = reinterpret_cast<unsigned long long*>(rows);
+    ctx->dpe = rows;
     ctx->dpe_cap = cap;
     cudaFreeAsync(base, s);
     if ((e = cudaGetLastError())) return cuda_error(ctx, e, "build layout");
