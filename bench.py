@@ -53,10 +53,11 @@ WORKLOAD = dict(n=10_000_000, m=100_000_000, exponent=2.1, dmax=1_000_000, n_ela
 # Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel from one ncu capture; None until captured for the current kernel.
 NCU_TRAFFIC_BYTES = {
-    # k_radix_scatter (one 8-bit pass of the CSR build over (u32 key, u64 value) pairs): 715 MB read +
-    # 639 MB written per launch on the 5M / 50M instance (ncu --set full, 10 launches); traffic grows with
-    # the items, so x2 for the 100M-edge launch. Algorithmic: 24 B per item, 2.4 GB per launch.
-    "radix_scatter": 2 * (715.0e6 + 639.4e6),
+    # k_place_coo (the CSR build's placement of every edge into its row): 408.1 MB read + 216.1 MB
+    # written for the 30M-edge instance of the generator (bench.py --scale 0.3, ncu --set full, one
+    # launch); traffic grows with the edges, so x(100/30) for the 100M-edge launch. Algorithmic: 24 B
+    # per edge (source, target, label, source position, row offset, packed word), 2.4 GB per launch.
+    "csr_place": (408.1e6 + 216.1e6) * 100.0 / 30.0,
 }
 # Per-round algorithmic bytes of a refinement round (the row entries and vertices it processed).
 ROUND_EDGE_BYTES = 12.0     # packed (label, target) word 8 + gathered block id 4
@@ -495,9 +496,9 @@ def run_ours(args, world, rank, local):
                     "share_of_kernel_time": round(top["total_ms"] / total_kernel_ms, 4)}
         if traffic is not None:
             roofline["traffic_vs_alg"] = round(traffic / roofline["alg_bytes_per_launch"], 3)
-            roofline["traffic_note"] = ("ncu DRAM bytes of one pass over 50M items x2 (traffic grows with the "
-                                        "items); every launch of this site is a pass over all edges, so the "
-                                        "per-launch figures describe the same launch")
+            roofline["traffic_note"] = ("ncu DRAM bytes of the 30M-edge launch scaled to 100M edges (traffic "
+                                        "grows with the edges); every launch of this site is one pass over all "
+                                        "edges, so the per-launch figures describe the same launch")
         kernels = sorted(({"name": p["name"], "launches": p["launches"], "ms": round(p["total_ms"], 3),
                            "share": round(p["total_ms"] / total_kernel_ms, 4),
                            "GB/s": round(p["alg_bytes"] / (p["total_ms"] / 1e3) / 1e9, 1) if p["total_ms"] else None}

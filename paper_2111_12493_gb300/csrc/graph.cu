@@ -124,7 +124,7 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
     cudaMemsetAsync(&ctx->dstate->error, 0, sizeof(unsigned), s);
     cudaMemsetAsync(deg, 0, sizeof(int32_t) * (n + 1), s);
     BISIM_SITE(site_val, "validate_edges");
-    BISIM_SITE(site_pack, "csr_pack");
+    BISIM_SITE(site_pack, "csr_place");
     if (m > 0)
         Launch(site_val, s, 0, m, 8.0 * m),
         k_validate_coo<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(src, dst, m, n, ctx->alive, deg,
