@@ -64,7 +64,7 @@ ROUND_EDGE_BYTES = 12.0     # packed (label, target) word 8 + gathered block id 
 ROUND_VERTEX_BYTES = 44.0   # row offset 4 + own block 4 + new block written 4 + two 16-byte table accesses
 SIG_SITES = ("dense_thread_sig_8", "dense_thread_sig_16", "dense_thread_sig_32", "dense_warp_sig",
              "dense_mid_512", "dense_mid_1024", "dense_mid_2048", "dense_mid_4096", "dense_mid_8192",
-             "hub_count", "dense_hub_finalize")
+             "hub_insert", "dense_hub_finalize")
 
 
 def parse_args():
@@ -310,7 +310,7 @@ def _round_work(bisim, ctx, k):
     bisim.bisim_iterate(ctx, k, 0)
     bisim.bisim_profile_enable(False)
     prof = {p["name"]: p for p in bisim.bisim_profile_read()}
-    listed = prof.get("dense_insert", {}).get("vertices", 0)
+    listed = prof.get("dense_verify", {}).get("vertices", 0)
     entries = sum(prof.get(n, {}).get("edges", 0) for n in SIG_SITES)
     return listed, entries
 

@@ -334,18 +334,8 @@ struct bisim_ctx {
     bisim::HubChunk* dchunks = nullptr;              // hub rows cut into chunks of at most 4096 edges
     int64_t n_dchunks = 0;
     int64_t n_dhub = 0;
-    int32_t* hshift = nullptr;                       // [n_dhub] log2 of the hub's value-bucket count
-    int64_t* hbbase = nullptr;                       // [n_dhub] first bucket of the hub
-    int32_t* bhub = nullptr;                         // [n_buckets] hub of the bucket
-    unsigned long long* bcount = nullptr;            // [n_buckets] values per bucket, this round
-    unsigned* bfill = nullptr;                       // [n_buckets] values placed so far, this round
-    int64_t* boff = nullptr;                         // [n_buckets + 1] bucket ranges in bvals
-    unsigned long long* bvals = nullptr;             // [hub edges] pair values grouped by bucket
-    unsigned long long* bmv = nullptr;               // [hub edges] pair values in row order
-    int64_t* bscan = nullptr;                        // scan scratch
-    int64_t n_buckets = 0;
+    unsigned long long* htab = nullptr;              // [2 * hub edges] per-hub open-addressing tables of pair values
     int64_t hub_edges = 0;
-    int64_t bscan_words = 0;
     bisim::HubAcc* dacc = nullptr;
     void* round_graph = nullptr;                     // cudaGraphExec_t of the device-side round loop
     void* capture_stream = nullptr;                  // cudaStream_t used only to capture it

@@ -58,14 +58,10 @@ __device__ __forceinline__ int ceil_log2(int64_t d) {
     return d <= 1 ? 0 : 64 - __clzll(static_cast<unsigned long long>(d - 1));
 }
 
-// Block-aggregated list appends and counts: one atomic per CTA rather than per warp, which
+// Block-aggregated list append: one atomic per CTA rather than per warp, which
 // matters when a whole grid adds to a single counter (tens of thousands of
 // warps on one address serialise in L2). Every thread of the CTA must call
-// them; `sh` holds kThreads / 32 + 1 words of shared memory.
-__device__ __forceinline__ void block_count(bool flag, unsigned long long* counter) {
-    const int c = __syncthreads_count(flag);
-    if (threadIdx.x == 0 && c) atomicAdd(counter, static_cast<unsigned long long>(c));
-}
+// it; `sh` holds kThreads / 32 + 1 words of shared memory.
 
 template <class T>
 __device__ __forceinline__ void block_push(bool flag, T value, T* list, unsigned* counter, unsigned* sh) {
@@ -86,6 +82,44 @@ __device__ __forceinline__ void block_push(bool flag, T value, T* list, unsigned
     __syncthreads();
     if (flag) list[sh[W] + sh[w] + __popc(b & lanemask_lt())] = value;
     __syncthreads();                                 // sh is free for the next call
+}
+
+// Exclusive scan of in[0..len) into out (which may be in) by one CTA of 1024
+// threads; every thread gets the total. Chunks of 1024 values: a warp scan,
+// a scan of the 32 warp sums, and a carry between chunks.
+__device__ int64_t cta_exclusive_scan(const int64_t* in, int64_t* out, int64_t len) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < len; b += 1024) {
+        const int64_t t = b + threadIdx.x;
+        const int64_t x = t < len ? in[t] : 0;
+        int64_t inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (static_cast<int>(lane_id()) >= o) inc += y;
+        }
+        if (lane_id() == 31) wsum[threadIdx.x >> 5] = inc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int64_t w = wsum[threadIdx.x];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (static_cast<int>(threadIdx.x) >= o) w += y;
+            }
+            wsum[threadIdx.x] = w;                       // inclusive over warps
+        }
+        __syncthreads();
+        const int64_t before = carry + (threadIdx.x >= 32 ? wsum[(threadIdx.x >> 5) - 1] : 0) + inc - x;
+        if (t < len) out[t] = before;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = before + x;
+        __syncthreads();
+    }
+    return carry;
 }
 
 // ----------------------------------------------------------------------------- layout kernels
@@ -541,189 +575,189 @@ __global__ void __launch_bounds__(T) k_dense_mid_sig(int cls, const DenseView D,
     }
 }
 
-// Hub rows are deduplicated by value buckets: pass 1 counts, per hub, the row's
-// pair values per bucket (the top bits of a salted mix of the value); a scan
-// turns the counts into bucket ranges; pass 2 scatters the values into their
-// buckets; pass 3 gives every bucket a CTA that deduplicates it in a
-// shared-memory set. No value leaves its bucket, so the hub's set size and sum
-// are the sums over its buckets. Every pass streams; nothing in global memory
-// is probed at random.
+// Hub rows (above the CTA classes) are cut into chunks over many CTAs. Every
+// hub has an open-addressing table in global memory with two slots per row
+// entry: the chunk of packed edges [b, e) owns slots [2b, 2e), counted from
+// the first hub edge, so the tables need no layout of their own and are never
+// more than half full. A round first clears the tables of the listed hubs
+// (k_hub_clear); then every chunk filters its pair values through a small
+// shared-memory set and inserts the values new to the chunk into its hub's
+// table (k_hub_insert). The inserter that finds a value's slot empty adds the
+// value to the hub's count and sum, so a value repeated within a chunk or
+// across chunks is counted once: count and sum are those of the hub's set.
 struct HubSets {
     int64_t first;                 // position of the first hub
     int64_t n_hub;
-    const int32_t* shift;          // log2 of the hub's bucket count
-    const int64_t* bbase;          // first bucket of each hub
-    const int32_t* bhub;           // hub of each bucket
-    unsigned long long* bcount;    // values per bucket (pass 1)
-    unsigned* bfill;               // values placed per bucket (pass 2)
-    int64_t* boff;                 // bucket ranges in bvals (scan of bcount)
-    unsigned long long* bvals;     // the bucketed pair values
-    unsigned long long* bmv;       // the hub edges' pair values in row order (pass 1 -> pass 2)
+    unsigned long long* tab;       // two slots per hub edge (0 = empty; the value 0 is acc[h].zero)
     int64_t e0;                    // first hub edge in the packed rows
     HubAcc* acc;
 };
 
+// No hub is listed this round (every hub is alone in its block): the hub
+// passes, whose resident grids stride over all chunks, return at once.
+__device__ __forceinline__ bool no_hub_listed(const DenseView& D) {
+    return D.aoff[kDHub + 1] == D.aoff[kDHub];
+}
+
+// Sub-ranges of a salted mix of the pair values, taken by the set comparison
+// of two long rows when one shared-memory set cannot hold a row.
 constexpr uint64_t kSaltBucket = 0x452821e638d01377ull;
-constexpr int kHubMaxBuckets = 2048;            // per hub
-constexpr int kHubBucketTarget = 1024;          // values per bucket aimed at
-constexpr int kHubSetSlots = 4096;              // shared-memory set of a bucket pass (32 KB)
-constexpr int kHubMaxSplits = 1 << 12;          // sub-ranges tried before a bucket is declared full
+constexpr int kHubMaxSplits = 1 << 12;          // sub-ranges tried before the comparison gives up
 
 __device__ __forceinline__ uint64_t bucket_mix(uint64_t mv) { return mix64(mv ^ kSaltBucket); }
 
-__device__ __forceinline__ uint32_t bucket_of(uint64_t mixed, int shift) {
-    return shift == 0 ? 0u : static_cast<uint32_t>(mixed >> (64 - shift));
-}
-
-// Sub-range `sub` of `splits` inside a bucket: the next bits of the mix after the bucket's.
+// Sub-range `sub` of `splits`: the top bits of the mix after its first `shift`.
 __device__ __forceinline__ uint32_t split_of(uint64_t mixed, int shift, uint32_t splits) {
     return splits <= 1 ? 0u : static_cast<uint32_t>((mixed << shift) >> (64 - __ffs(splits) + 1));
 }
 
-// Pass 1: per-chunk histogram of bucket ids, added into the hub's bucket
-// counts; the pair values are kept in row order for pass 2.
-__global__ void __launch_bounds__(kThreads) k_hub_count(const HubChunk* __restrict__ chunks, const DenseView D,
-                                                        const HubSets H) {
-    __shared__ unsigned hist[kHubMaxBuckets];
-    const HubChunk c = chunks[blockIdx.x];
-    if (alone_last_round(D, H.first + c.hub)) return;    // whole CTA: the hub needs no signature
-    if (D.work && threadIdx.x == 0) work_add(D, kWorkHub, c.begin == D.prp[H.first + c.hub] ? 1 : 0,
-                                             static_cast<unsigned long long>(c.end - c.begin));
-    const int shift = H.shift[c.hub];
-    const int nb = 1 << shift;
-    for (int b = threadIdx.x; b < nb; b += kThreads) hist[b] = 0u;
-    __syncthreads();
-    for (int64_t e = c.begin + threadIdx.x; e < c.end; e += kThreads) {
-        const uint64_t mv = packed_pair_value(__ldcs(D.pe + e), D.P);
-        H.bmv[e - H.e0] = mv;
-        atomicAdd(&hist[bucket_of(bucket_mix(mv), shift)], 1u);
-    }
-    __syncthreads();
-    const int64_t base = H.bbase[c.hub];
-    for (int b = threadIdx.x; b < nb; b += kThreads)
-        if (hist[b]) atomicAdd(&H.bcount[base + b], static_cast<unsigned long long>(hist[b]));
-}
-
-// Pass 2: the chunk's values go to their buckets. Each CTA reserves one range
-// per bucket it touches, so the writes of a bucket are contiguous.
-constexpr int kHubStage = kHubChunkMax;
-__global__ void __launch_bounds__(kThreads) k_hub_scatter(const HubChunk* __restrict__ chunks, const DenseView D,
-                                                          const HubSets H) {
-    extern __shared__ unsigned long long stage[];                  // kHubStage values
-    unsigned* where = reinterpret_cast<unsigned*>(stage + kHubStage);   // bucket << 16 | index in the CTA's range
-    __shared__ unsigned hist[kHubMaxBuckets];
-    __shared__ unsigned start[kHubMaxBuckets];
-    const HubChunk c = chunks[blockIdx.x];
-    if (alone_last_round(D, H.first + c.hub)) return;    // counted nothing in pass 1
-    const int shift = H.shift[c.hub];
-    const int nb = 1 << shift;
-    const int cnt = static_cast<int>(c.end - c.begin);
-    for (int b = threadIdx.x; b < nb; b += kThreads) hist[b] = 0u;
-    __syncthreads();
-    const unsigned long long* src = H.bmv + (c.begin - H.e0);
-    for (int j = threadIdx.x; j < cnt; j += kThreads) {
-        const uint64_t mv = __ldcs(src + j);
-        const uint32_t b = bucket_of(bucket_mix(mv), shift);
-        stage[j] = mv;
-        where[j] = (b << 16) | atomicAdd(&hist[b], 1u);
-    }
-    __syncthreads();
-    const int64_t base = H.bbase[c.hub];
-    for (int b = threadIdx.x; b < nb; b += kThreads)
-        start[b] = hist[b] ? atomicAdd(&H.bfill[base + b], hist[b]) : 0u;
-    __syncthreads();
-    for (int j = threadIdx.x; j < cnt; j += kThreads) {
-        const unsigned w = where[j];
-        const int64_t gb = base + (w >> 16);
-        H.bvals[H.boff[gb] + start[w >> 16] + (w & 0xffffu)] = stage[j];
+// Pass 1: the listed hubs' table slots are cleared, chunk by chunk (16 bytes
+// per edge, the two slots it owns).
+__global__ void __launch_bounds__(kThreads) k_hub_clear(const HubChunk* __restrict__ chunks, int64_t n_chunks,
+                                                        const DenseView D, const HubSets H) {
+    if (no_hub_listed(D)) return;
+    for (int64_t ci = blockIdx.x; ci < n_chunks; ci += gridDim.x) {
+        const HubChunk c = chunks[ci];
+        if (alone_last_round(D, H.first + c.hub)) continue;          // the same for the whole CTA
+        ulonglong2* t = reinterpret_cast<ulonglong2*>(H.tab + 2 * (c.begin - H.e0));
+        const int64_t cnt = c.end - c.begin;
+        for (int64_t j = threadIdx.x; j < cnt; j += kThreads) t[j] = make_ulonglong2(0ull, 0ull);
     }
 }
 
-// Pass 3: one CTA per bucket. The bucket's distinct values are counted and
-// summed through a shared-memory set; a bucket with more distinct values than
-// the set takes (kHubSetLimit) is redone in 2, 4, ... sub-ranges of the mix,
-// one set pass each.
-constexpr int kHubSetLimit = 3072;
-constexpr int kDedupUnroll = 4;
-constexpr size_t kHubScatterSmem = (sizeof(unsigned long long) + sizeof(unsigned)) * kHubStage;
-constexpr size_t kHubDedupSmem = sizeof(unsigned long long) * kHubSetSlots;
-__global__ void __launch_bounds__(kThreads) k_hub_dedup(const HubSets H, unsigned* err) {
-    extern __shared__ unsigned long long tab[];                    // kHubSetSlots
-    __shared__ unsigned zero, used, over;
+// Insert of a nonzero pair value into a hub's table of `size` slots (linear
+// probing from hub_slot, the value's high half scaled to the table). Slots
+// only go from empty to a value within a round, so a plain read that sees the
+// value is final and one that sees an empty slot is settled by the
+// compare-and-swap. `first` is the caller's read of the first slot (so that a
+// thread's reads for several values are in flight together). True for the
+// inserter that placed the value.
+__device__ __forceinline__ uint64_t hub_slot(unsigned long long mv, uint64_t size) {
+    return ((mv >> 32) * size) >> 32;
+}
+
+__device__ __forceinline__ bool hub_table_insert(unsigned long long* tab, uint64_t size, unsigned long long mv,
+                                                 unsigned long long first, unsigned* err) {
+    uint64_t at = hub_slot(mv, size);
+    for (uint64_t probe = 0; probe < size; ++probe) {
+        const unsigned long long cur = probe == 0 ? first : tab[at];
+        if (cur == mv) return false;
+        if (cur == 0ull) {
+            const unsigned long long prev = atomicCAS(&tab[at], 0ull, mv);
+            if (prev == 0ull) return true;
+            if (prev == mv) return false;
+        }
+        if (++at == size) at = 0;
+    }
+    atomicOr(err, kErrHubFull);                        // unreachable: the table has two slots per edge
+    return false;
+}
+
+// Pass 2: per chunk, its values go through a shared-memory set of
+// kHubLocalSlots slots (a filter only: once it holds kHubLocalLimit values,
+// the rest go to the table directly); the values new to the set, and those
+// that bypass it, are inserted into the hub's table, the first table reads of
+// a thread's kHubUnroll values in flight together. The CTA adds its new
+// values' count and sum to the hub's accumulator once per chunk. The filter
+// is small on purpose: eight CTAs per SM hide the table reads' latency, and
+// on the 10M-vertex power-law graph a 32 KB filter (six CTAs per SM) made the
+// pass 2.5 times slower than this 16 KB one, and no filter 15% slower.
+constexpr int kHubUnroll = 4;
+constexpr int kHubLocalSlots = 2048;                   // 16 KB
+constexpr int kHubLocalLimit = 512;                    // checked once per iteration of kThreads * kHubUnroll values
+static_assert(kHubLocalLimit + kThreads * kHubUnroll <= 3 * kHubLocalSlots / 4, "hub filter can fill up");
+constexpr size_t kHubInsertSmem = sizeof(unsigned long long) * kHubLocalSlots;
+__global__ void __launch_bounds__(kThreads) k_hub_insert(const HubChunk* __restrict__ chunks, int64_t n_chunks,
+                                                         const DenseView D, const HubSets H, unsigned* err) {
+    extern __shared__ unsigned long long set[];                    // kHubLocalSlots
+    __shared__ unsigned zero, used;
     __shared__ unsigned long long wsum[kThreads / 32];
     __shared__ unsigned wcnt[kThreads / 32];
-    volatile unsigned* overv = &over;
-    const int64_t gb = blockIdx.x;
-    const int h = H.bhub[gb];
-    const int shift = H.shift[h];
-    const int64_t lo = H.boff[gb], hi = H.boff[gb + 1];
-    if (lo == hi) return;                                // empty bucket (or a hub left out this round)
-    uint64_t sum = 0;
-    unsigned cnt = 0;
-    bool done = false;
-    for (uint32_t splits = 1; splits <= static_cast<uint32_t>(kHubMaxSplits) && !done; splits <<= 1) {
-        sum = 0;
-        cnt = 0;
-        bool o = false;
-        for (uint32_t sub = 0; sub < splits && !o; ++sub) {
-            for (int j = threadIdx.x; j < kHubSetSlots; j += kThreads) tab[j] = 0ull;
-            if (threadIdx.x == 0) {
-                zero = 0u;
-                used = 0u;
-                over = 0u;
+    if (no_hub_listed(D)) return;
+    for (int64_t ci = blockIdx.x; ci < n_chunks; ci += gridDim.x) {
+        const HubChunk c = chunks[ci];
+        const int64_t hp = H.first + c.hub;
+        if (alone_last_round(D, hp)) continue;                       // the same for the whole CTA
+        if (D.work && threadIdx.x == 0)
+            work_add(D, kWorkHub, c.begin == D.prp[hp] ? 1 : 0, static_cast<unsigned long long>(c.end - c.begin));
+        for (int j = threadIdx.x; j < kHubLocalSlots; j += kThreads) set[j] = 0ull;
+        if (threadIdx.x == 0) {
+            zero = 0u;
+            used = 0u;
+        }
+        const int64_t rb = D.prp[hp];
+        const uint64_t size = 2 * static_cast<uint64_t>(D.prp[hp + 1] - rb);
+        unsigned long long* tab = H.tab + 2 * (rb - H.e0);
+        HubAcc* acc = H.acc + c.hub;
+        __syncthreads();
+        uint64_t sum = 0;
+        unsigned cnt = 0;
+        for (int64_t b0 = c.begin; b0 < c.end; b0 += static_cast<int64_t>(kThreads) * kHubUnroll) {
+            // loads, then gathers, then the filter, then the first table reads of
+            // all the thread's values, before any value waits on its own chain
+            uint64_t mv[kHubUnroll];
+            bool send[kHubUnroll];
+#pragma unroll
+            for (int k = 0; k < kHubUnroll; ++k) {
+                const int64_t e = b0 + static_cast<int64_t>(k) * kThreads + threadIdx.x;
+                mv[k] = e < c.end ? __ldcs(D.pe + e) : 0ull;
             }
-            __syncthreads();
-            for (int64_t e0 = lo + threadIdx.x; e0 < hi; e0 += kThreads * kDedupUnroll) {
-                if (*overv) break;
-                uint64_t mv[kDedupUnroll];
 #pragma unroll
-                for (int k = 0; k < kDedupUnroll; ++k) {
-                    const int64_t e = e0 + static_cast<int64_t>(k) * kThreads;
-                    mv[k] = e < hi ? __ldcs(H.bvals + e) : 0ull;
-                }
+            for (int k = 0; k < kHubUnroll; ++k) {
+                send[k] = b0 + static_cast<int64_t>(k) * kThreads + threadIdx.x < c.end;
+                if (send[k]) mv[k] = packed_pair_value(mv[k], D.P);
+            }
+            const bool room = *reinterpret_cast<volatile unsigned*>(&used) < static_cast<unsigned>(kHubLocalLimit);
+            unsigned added = 0;
 #pragma unroll
-                for (int k = 0; k < kDedupUnroll; ++k) {
-                    if (e0 + static_cast<int64_t>(k) * kThreads >= hi) break;
-                    if (splits > 1 && split_of(bucket_mix(mv[k]), shift, splits) != sub) continue;
-                    if (smem_set_insert(tab, kHubSetSlots - 1, &zero, mv[k])) {
-                        sum += mv[k];
-                        ++cnt;
-                        if (mv[k] != 0ull && atomicAdd(&used, 1u) + 1u > static_cast<unsigned>(kHubSetLimit))
-                            *overv = 1u;
-                    }
+            for (int k = 0; k < kHubUnroll; ++k) {
+                if (!send[k]) continue;
+                if (mv[k] == 0ull) {
+                    send[k] = false;
+                    if (atomicExch(&acc->zero, 1u) == 0u) ++cnt;         // the value 0 adds nothing to the sum
+                } else if (room) {
+                    send[k] = smem_set_insert(set, kHubLocalSlots - 1, &zero, mv[k]);
+                    added += send[k] ? 1u : 0u;
                 }
             }
-            __syncthreads();
-            o = *overv != 0u;               // the same for every thread
-            __syncthreads();
-        }
-        done = !o;
-    }
-    if (!done) {
-        if (threadIdx.x == 0) atomicOr(err, kErrHubFull);
-        return;                             // uniform: every thread saw the same flags
-    }
+            // one shared add per warp for the filter's fill
 #pragma unroll
-    for (int o2 = 16; o2 > 0; o2 >>= 1) {
-        sum += __shfl_xor_sync(0xffffffffu, sum, o2);
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, o2);
-    }
-    if (lane_id() == 0) {
-        wsum[threadIdx.x >> 5] = sum;
-        wcnt[threadIdx.x >> 5] = cnt;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint64_t s2 = 0;
-        unsigned c2 = 0;
-        for (int w = 0; w < kThreads / 32; ++w) {
-            s2 += wsum[w];
-            c2 += wcnt[w];
+            for (int o = 16; o > 0; o >>= 1) added += __shfl_xor_sync(0xffffffffu, added, o);
+            if (lane_id() == 0 && added) atomicAdd(&used, added);
+            unsigned long long first[kHubUnroll];
+#pragma unroll
+            for (int k = 0; k < kHubUnroll; ++k) first[k] = send[k] ? tab[hub_slot(mv[k], size)] : 0ull;
+#pragma unroll
+            for (int k = 0; k < kHubUnroll; ++k) {
+                if (send[k] && hub_table_insert(tab, size, mv[k], first[k], err)) {
+                    sum += mv[k];
+                    ++cnt;
+                }
+            }
         }
-        if (c2) {
-            atomicAdd(&H.acc[h].sum, static_cast<unsigned long long>(s2));
-            atomicAdd(&H.acc[h].count, c2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         }
+        if (lane_id() == 0) {
+            wsum[threadIdx.x >> 5] = sum;
+            wcnt[threadIdx.x >> 5] = cnt;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t s2 = 0;
+            unsigned c2 = 0;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                s2 += wsum[w];
+                c2 += wcnt[w];
+            }
+            if (c2) {
+                atomicAdd(&acc->sum, static_cast<unsigned long long>(s2));
+                atomicAdd(&acc->count, c2);
+            }
+        }
+        __syncthreads();                               // the set and the sums are reused by the next chunk
     }
 }
 
@@ -732,6 +766,7 @@ __global__ void __launch_bounds__(kThreads) k_hub_dedup(const HubSets H, unsigne
 __global__ void k_dense_hub_finalize(const DenseView D, const HubSets H) {
     const int64_t h = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (h >= H.n_hub) return;
+    if (no_hub_listed(D)) return;
     const int64_t pos = H.first + h;
     if (alone_last_round(D, pos)) return;
     finish_sig(D, pos, D.P[D.vert[pos]], H.acc[h].count, H.acc[h].sum);
@@ -968,21 +1003,28 @@ __global__ void __launch_bounds__(kThreads) k_active_count(const DenseView D, co
     const int64_t tiles = (count + kActTile - 1) / kActTile;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int64_t e0 = t * kActTile + static_cast<int64_t>(threadIdx.x) * kActPer;
+        // every load of the eight entries is issued before the first store
+        // (the copy's stores would otherwise order the next entry's loads)
+        int32_t pos[kActPer], v[kActPer], pv[kActPer];
+        bool stay[kActPer];
+#pragma unroll
+        for (int k = 0; k < kActPer; ++k) pos[k] = e0 + k < count ? D.act[e0 + k] : -1;
+#pragma unroll
+        for (int k = 0; k < kActPer; ++k) {
+            stay[k] = pos[k] >= 0 && stays_listed(D, pos[k]);
+            v[k] = pos[k] >= 0 && !full ? D.vert[pos[k]] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < kActPer; ++k) pv[k] = v[k] >= 0 ? Pout[v[k]] : 0;
         unsigned keep = 0;
         int c = 0;
 #pragma unroll
         for (int k = 0; k < kActPer; ++k) {
-            if (e0 + k < count) {
-                const int32_t pos = D.act[e0 + k];
-                if (!full) {
-                    const int32_t v = D.vert[pos];
-                    Pin[v] = Pout[v];
-                }
-                if (stays_listed(D, pos)) {
-                    ++keep;
-                    while (c + 1 < kDClasses && pos >= cb.b[c + 1]) ++c;      // entries ascend: c only grows
-                    atomicAdd(&csum[c], 1u);
-                }
+            if (v[k] >= 0) Pin[v[k]] = pv[k];
+            if (stay[k]) {
+                ++keep;
+                while (c + 1 < kDClasses && pos[k] >= cb.b[c + 1]) ++c;      // entries ascend: c only grows
+                atomicAdd(&csum[c], 1u);
             }
         }
 #pragma unroll
@@ -1003,40 +1045,10 @@ __global__ void __launch_bounds__(kThreads) k_active_count(const DenseView D, co
 // Pass 2 (one CTA): exclusive scan of the tile counts; the new length goes to tcount[slot_total].
 __global__ void __launch_bounds__(1024) k_active_scan(const int64_t* __restrict__ aoff, int64_t* __restrict__ tcount,
                                                       int64_t slot_total, const int32_t* stop) {
-    __shared__ int64_t wsum[32];
-    __shared__ int64_t carry;
     if (stop != nullptr && *stop >= 2) return;
     const int64_t tiles = (aoff[kDClasses] + kActTile - 1) / kActTile;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int64_t b = 0; b < tiles; b += 1024) {
-        const int64_t t = b + threadIdx.x;
-        const int64_t x = t < tiles ? tcount[t] : 0;
-        int64_t inc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (static_cast<int>(lane_id()) >= o) inc += y;
-        }
-        if (lane_id() == 31) wsum[threadIdx.x >> 5] = inc;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            int64_t w = wsum[threadIdx.x];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
-                if (static_cast<int>(threadIdx.x) >= o) w += y;
-            }
-            wsum[threadIdx.x] = w;                       // inclusive over warps
-        }
-        __syncthreads();
-        const int64_t before = carry + (threadIdx.x >= 32 ? wsum[(threadIdx.x >> 5) - 1] : 0) + inc - x;
-        if (t < tiles) tcount[t] = before;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = before + x;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) tcount[slot_total] = carry;
+    const int64_t total = cta_exclusive_scan(tcount, tcount, tiles);
+    if (threadIdx.x == 0) tcount[slot_total] = total;
 }
 
 // Pass 3: every tile writes its survivors at its offset into the next list.
@@ -1267,8 +1279,7 @@ __global__ void __launch_bounds__(kThreads) k_table_clear_round(const LoopState*
 // ----------------------------------------------------------------------------- host helpers
 
 HubSets hub_sets(const bisim_ctx* ctx) {
-    return HubSets{ctx->dbegin[kDHub], ctx->n_dhub, ctx->hshift, ctx->hbbase, ctx->bhub, ctx->bcount,
-                   ctx->bfill, ctx->boff, ctx->bvals, ctx->bmv, ctx->dedge_begin[kDHub], ctx->dacc};
+    return HubSets{ctx->dbegin[kDHub], ctx->n_dhub, ctx->htab, ctx->dedge_begin[kDHub], ctx->dacc};
 }
 
 template <class K>
@@ -1338,11 +1349,9 @@ void set_attributes() {
         allow_smem(k_dense_mid_sig<2048, 512>, sizeof(unsigned long long) * 2 * 2048);
         allow_smem(k_dense_mid_sig<4096, 512>, sizeof(unsigned long long) * 2 * 4096);
         allow_smem(k_dense_mid_sig<8192, 512>, sizeof(unsigned long long) * 2 * 8192);
-        cudaFuncSetAttribute(k_hub_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kHubScatterSmem));
-        cudaFuncSetAttribute(k_hub_dedup, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kHubDedupSmem));
         allow_smem(k_dense_compare_cta, kCompareSmem);
+        persistent_grid(k_hub_clear, kThreads, 0, 1);
+        persistent_grid(k_hub_insert, kThreads, kHubInsertSmem, 1);
         persistent_grid(k_dense_thread_sig<8>, kThreads, 0, 1);
         persistent_grid(k_dense_thread_sig<16>, kThreads, 0, 1);
         persistent_grid(k_dense_thread_sig<32>, kThreads, 0, 1);
@@ -1477,8 +1486,6 @@ void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, const int32
         k_round_begin<<<1, 1, 0, s>>>(ctx->dstate, ctx->daoff, ctx->dbegin[kDClasses]);
     }
     if (ctx->n_dhub > 0) {
-        cudaMemsetAsync(ctx->bcount, 0, sizeof(unsigned long long) * (ctx->n_buckets + 1), s);   // + the scan's end
-        cudaMemsetAsync(ctx->bfill, 0, sizeof(unsigned) * ctx->n_buckets, s);
         cudaMemsetAsync(ctx->dacc, 0, sizeof(HubAcc) * ctx->n_dhub, s);
     }
     const int64_t* db = ctx->dbegin;
@@ -1489,9 +1496,8 @@ void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, const int32
     static const int site_mid[5] = {prof_site("dense_mid_512"), prof_site("dense_mid_1024"),
                                     prof_site("dense_mid_2048"), prof_site("dense_mid_4096"),
                                     prof_site("dense_mid_8192")};
-    BISIM_SITE(site_hc, "hub_count");
-    BISIM_SITE(site_hs, "hub_scatter");
-    BISIM_SITE(site_hd, "hub_dedup");
+    BISIM_SITE(site_hc, "hub_clear");
+    BISIM_SITE(site_hi, "hub_insert");
     BISIM_SITE(site_hf, "dense_hub_finalize");
     // classes 0..4 (degree <= 8), 5 (<= 16) and 6 (<= 32): one thread per vertex
     if (D.work) cudaMemsetAsync(D.work, 0, sizeof(unsigned long long) * kWorkWords, s);
@@ -1519,17 +1525,12 @@ void launch_round(bisim_ctx* ctx, cudaStream_t s, const TableRef& t, const int32
         if (ctx->n_dchunks > 0) {
             {
                 Launch L(site_hc, s, 0, 0, 0.0);
-                k_hub_count<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, 0, s>>>(ctx->dchunks, D, H);
+                k_hub_clear<<<persistent_grid(k_hub_clear, kThreads, 0, ctx->n_dchunks), kThreads, 0, s>>>(
+                    ctx->dchunks, ctx->n_dchunks, D, H);
             }
-            exclusive_scan_i64(reinterpret_cast<const int64_t*>(ctx->bcount), ctx->boff, ctx->n_buckets + 1,
-                               ctx->bscan, s);
-            {
-                Launch L(site_hs, s, 0, 0, 0.0);
-                k_hub_scatter<<<static_cast<unsigned>(ctx->n_dchunks), kThreads, kHubScatterSmem, s>>>(ctx->dchunks, D,
-                                                                                                     H);
-            }
-            Launch L(site_hd, s, 0, 0, 0.0);
-            k_hub_dedup<<<static_cast<unsigned>(ctx->n_buckets), kThreads, kHubDedupSmem, s>>>(H, err);
+            Launch L(site_hi, s, 0, 0, 0.0);
+            k_hub_insert<<<persistent_grid(k_hub_insert, kThreads, kHubInsertSmem, ctx->n_dchunks), kThreads,
+                           kHubInsertSmem, s>>>(ctx->dchunks, ctx->n_dchunks, D, H, err);
         }
         Launch L(site_hf, s, 0, 0, 0.0);
         k_dense_hub_finalize<<<grid_for(ctx->n_dhub, 128), 128, 0, s>>>(D, H);
@@ -1559,16 +1560,14 @@ void add_round_work(bisim_ctx* ctx, double listed) {
         prof_add_bytes(sites[g], kSigVertexBytes * rows[g] + kEdgeBytes * edges[g]);
         prof_add_work(sites[g], static_cast<int64_t>(rows[g]), static_cast<int64_t>(edges[g]));
     }
-    BISIM_SITE(site_hc, "hub_count");
-    BISIM_SITE(site_hs, "hub_scatter");
-    BISIM_SITE(site_hd, "hub_dedup");
+    BISIM_SITE(site_hi, "hub_insert");
     BISIM_SITE(site_hf, "dense_hub_finalize");
+    // the hub rows' algorithmic bytes are those of reading them; clearing the
+    // tables is overhead of this design (no bytes)
     const double he = edges[kWorkHub];
-    prof_add_bytes(site_hc, (kEdgeBytes + 8.0) * he);
-    prof_add_bytes(site_hs, 16.0 * he);
-    prof_add_bytes(site_hd, 8.0 * he);
+    prof_add_bytes(site_hi, kEdgeBytes * he);
     prof_add_bytes(site_hf, kSigVertexBytes * rows[kWorkHub]);
-    prof_add_work(site_hc, 0, static_cast<int64_t>(he));
+    prof_add_work(site_hi, 0, static_cast<int64_t>(he));
     prof_add_work(site_hf, static_cast<int64_t>(rows[kWorkHub]), 0);
     BISIM_SITE(site_in, "dense_insert");
     BISIM_SITE(site_v, "dense_verify");
@@ -1656,28 +1655,12 @@ bisim_status alloc_round_state(bisim_ctx* ctx, cudaStream_t s) {
 
 void free_hub_layout(bisim_ctx* ctx, cudaStream_t s) {
     ctx_free(ctx, ctx->dchunks, sizeof(HubChunk) * ctx->n_dchunks, s);
-    ctx_free(ctx, ctx->hshift, sizeof(int32_t) * ctx->n_dhub, s);
-    ctx_free(ctx, ctx->hbbase, sizeof(int64_t) * ctx->n_dhub, s);
-    ctx_free(ctx, ctx->bhub, sizeof(int32_t) * ctx->n_buckets, s);
-    ctx_free(ctx, ctx->bcount, sizeof(unsigned long long) * (ctx->n_buckets + 1), s);
-    ctx_free(ctx, ctx->bfill, sizeof(unsigned) * ctx->n_buckets, s);
-    ctx_free(ctx, ctx->boff, sizeof(int64_t) * (ctx->n_buckets + 1), s);
-    ctx_free(ctx, ctx->bvals, sizeof(unsigned long long) * ctx->hub_edges, s);
-    ctx_free(ctx, ctx->bmv, sizeof(unsigned long long) * ctx->hub_edges, s);
-    ctx_free(ctx, ctx->bscan, sizeof(int64_t) * ctx->bscan_words, s);
+    ctx_free(ctx, ctx->htab, 2 * sizeof(unsigned long long) * ctx->hub_edges, s);
     ctx_free(ctx, ctx->dacc, sizeof(HubAcc) * ctx->n_dhub, s);
     ctx->dchunks = nullptr;
-    ctx->hshift = nullptr;
-    ctx->hbbase = nullptr;
-    ctx->bhub = nullptr;
-    ctx->bcount = nullptr;
-    ctx->bfill = nullptr;
-    ctx->boff = nullptr;
-    ctx->bvals = nullptr;
-    ctx->bmv = nullptr;
-    ctx->bscan = nullptr;
+    ctx->htab = nullptr;
     ctx->dacc = nullptr;
-    ctx->n_dchunks = ctx->n_dhub = ctx->n_buckets = ctx->hub_edges = ctx->bscan_words = 0;
+    ctx->n_dchunks = ctx->n_dhub = ctx->hub_edges = 0;
 }
 
 // Copies the rows of the vertex-ordered CSR into the packed rows (all but hubs).
@@ -1776,43 +1759,21 @@ bisim_status dense_layout_hubs(bisim_ctx* ctx, bool pack_from_csr, cudaStream_t 
         cudaMemcpyAsync(rows.data(), ctx->dprp + begin[kDHub], sizeof(int64_t) * (nh + 1), cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "read hub rows");
         std::vector<HubChunk> chunks;
-        std::vector<int32_t> shift(nh), bhub;
-        std::vector<int64_t> bbase(nh);
         const int64_t csz = std::max(256, ctx->opt.hub_chunk);
-        for (int64_t h = 0; h < nh; ++h) {
-            const int64_t d = rows[h + 1] - rows[h];
-            int sh = 0;
-            while ((int64_t{1} << sh) * kHubBucketTarget < d && (1 << sh) < kHubMaxBuckets) ++sh;
-            shift[h] = sh;
-            bbase[h] = static_cast<int64_t>(bhub.size());
-            for (int b = 0; b < (1 << sh); ++b) bhub.push_back(static_cast<int32_t>(h));
+        for (int64_t h = 0; h < nh; ++h)
             for (int64_t b = rows[h]; b < rows[h + 1]; b += csz)
                 chunks.push_back(HubChunk{static_cast<int32_t>(h), -1, b, std::min(rows[h + 1], b + csz)});
-        }
-        const int64_t nbk = static_cast<int64_t>(bhub.size());
         ctx->n_dhub = nh;
         ctx->n_dchunks = static_cast<int64_t>(chunks.size());
-        ctx->n_buckets = nbk;
         ctx->hub_edges = std::max<int64_t>(rows[nh] - rows[0], 1);
-        ctx->bscan_words = static_cast<int64_t>(scan_temp_words(nbk + 1));
         if ((!chunks.empty() &&
              (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dchunks), sizeof(HubChunk) * chunks.size(), s))) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->hshift), sizeof(int32_t) * nh, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->hbbase), sizeof(int64_t) * nh, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bhub), sizeof(int32_t) * nbk, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bcount), sizeof(unsigned long long) * (nbk + 1), s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bfill), sizeof(unsigned) * nbk, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->boff), sizeof(int64_t) * (nbk + 1), s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bvals), sizeof(unsigned long long) * ctx->hub_edges, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bmv), sizeof(unsigned long long) * ctx->hub_edges, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bscan), sizeof(int64_t) * ctx->bscan_words, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->htab), 2 * sizeof(unsigned long long) * ctx->hub_edges,
+                           s)) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dacc), sizeof(HubAcc) * nh, s)))
-            return cuda_error(ctx, e, "alloc hub buckets");
+            return cuda_error(ctx, e, "alloc hub tables");
         if (!chunks.empty())
             cudaMemcpyAsync(ctx->dchunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(ctx->hshift, shift.data(), sizeof(int32_t) * nh, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(ctx->hbbase, bbase.data(), sizeof(int64_t) * nh, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(ctx->bhub, bhub.data(), sizeof(int32_t) * nbk, cudaMemcpyHostToDevice, s);
         if (pack_from_csr && !chunks.empty()) {
             // hub rows are copied chunk by chunk, like the rounds read them
             const int64_t edges = m - ctx->dedge_begin[kDHub];
