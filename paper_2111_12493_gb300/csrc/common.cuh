@@ -123,7 +123,7 @@ struct DevState {
     unsigned int deferred;          // vertices whose set comparison is left to k_verify_deferred
     unsigned int pairs;             // dense rounds: small pairs left to a warp comparison
     unsigned int listed;            // dense rounds: positions that need the table this round
-    unsigned int pad;
+    unsigned int unsorted;          // COO build: some edge's source is smaller than the one before it
 };
 
 __device__ __forceinline__ unsigned long long table_read(const TableRef& t, uint64_t pos) {

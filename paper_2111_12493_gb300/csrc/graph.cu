@@ -13,60 +13,113 @@ unsigned grid_for(int64_t n, int threads) {
     return static_cast<unsigned>(std::max<int64_t>(1, cdiv(n, threads)));
 }
 
-// Checks every edge and counts out-degrees (one atomic per distinct source in
-// a warp; edge lists are often grouped by source). Degrees of a list that fails
-// the check are never used.
-__global__ void k_validate_coo(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                               int64_t m, int32_t n, const uint8_t* __restrict__ alive,
-                               int32_t* __restrict__ deg, unsigned* err) {
-    // trip count is uniform across the warp so the match below sees every lane
+// Runs of equal keys among a warp's lanes (lane order): a lane heads a run
+// when its key differs from the previous lane's. Sources grouped in the edge
+// list give a few runs per warp; any order stays correct, with more runs.
+__device__ __forceinline__ unsigned run_heads(int32_t key, unsigned lane) {
+    const int32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+    return __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+}
+
+// Lanes in the run headed by `lane` (a head): up to the next head.
+__device__ __forceinline__ int run_length(unsigned heads, unsigned lane) {
+    const unsigned after = lane == 31 ? 0u : heads >> (lane + 1);
+    return after ? __ffs(after) : 32 - static_cast<int>(lane);
+}
+
+// The head of the run that holds `lane`.
+__device__ __forceinline__ int run_head(unsigned heads, unsigned lane) {
+    const unsigned upto = lane == 31 ? heads : heads & ((2u << lane) - 1u);
+    return 31 - __clz(upto);
+}
+
+// Checks every edge, and finds out whether the list is sorted by source. For
+// a sorted list each source's edges form one run [start, end) of the list:
+// the run's first edge records start[v] and adds -start to deg[v], its last
+// edge adds end, so deg[v] = end - start (in modular 32-bit arithmetic, exact
+// for any degree below 2^32) with two atomics per vertex on distinct
+// addresses. For an unsorted list these values are not used (k_count_coo
+// counts again). A list that fails the check is not used at all.
+__global__ void __launch_bounds__(256) k_validate_coo(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                                                      int64_t m, int32_t n, const uint8_t* __restrict__ alive,
+                                                      uint32_t* __restrict__ deg, int64_t* __restrict__ start,
+                                                      DevState* st) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t e0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; e0 < m; e0 += stride) {
-        const int64_t e = e0 + threadIdx.x;
-        int32_t s = -1;
-        if (e < m) {
-            s = src[e];
-            const int32_t d = dst[e];
-            bool ok = s >= 0 && s < n && d >= 0 && d < n;
-            if (ok && alive != nullptr) ok = alive[s] && alive[d];
-            if (!ok) {
-                atomicOr(err, kErrBadInput);
-                s = -1;
-            }
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t s = src[e];
+        const int32_t d = dst[e];
+        const int32_t prev = e > 0 ? src[e - 1] : -1;
+        const int32_t next = e + 1 < m ? src[e + 1] : -1;
+        bool ok = s >= 0 && s < n && d >= 0 && d < n;
+        if (ok && alive != nullptr) ok = alive[s] && alive[d];
+        if (!ok) {
+            atomicOr(&st->error, kErrBadInput);
+            continue;
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, s);
-        if (s >= 0 && (threadIdx.x & 31) == static_cast<unsigned>(__ffs(peers) - 1)) atomicAdd(&deg[s], __popc(peers));
+        if (prev > s) atomicOr(&st->unsorted, 1u);
+        if (prev != s) {
+            start[s] = e;
+            atomicAdd(&deg[s], 0u - static_cast<uint32_t>(e));
+        }
+        if (next != s) atomicAdd(&deg[s], static_cast<uint32_t>(e + 1));
     }
 }
 
-// Every edge written into its source's packed row of the layout: the row of
-// position p is [prp[p], prp[p+1]); a per-row cursor hands out the slots, one
-// atomic per distinct source in a warp (the lanes of one source take
-// consecutive slots in lane order). Signatures are sets, so the order of the
-// edges inside a row is never read; it follows the order in which warps reach
-// the row's cursor. Edge lists grouped by source (the common case) write each
-// row in runs.
-__global__ void k_place_coo(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                            const int32_t* __restrict__ elab, int64_t m, const int32_t* __restrict__ vpos,
-                            const int64_t* __restrict__ prp, int32_t* __restrict__ cursor,
-                            unsigned long long* __restrict__ pe) {
+// Out-degrees of an unsorted list: one atomic per run of equal sources in a
+// warp.
+__global__ void __launch_bounds__(256) k_count_coo(const int32_t* __restrict__ src, int64_t m,
+                                                   uint32_t* __restrict__ deg) {
     const unsigned lane = threadIdx.x & 31u;
-    // trip count is uniform across the warp so the match below sees every lane
+    // trip count is uniform across the warp so the shuffles see every lane
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t e0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; e0 < m; e0 += stride) {
         const int64_t e = e0 + threadIdx.x;
-        int32_t pos = -1;
-        if (e < m) pos = vpos[src[e]];
-        const unsigned peers = __match_any_sync(0xffffffffu, pos);
-        const int leader = __ffs(peers) - 1;
+        const int32_t s = e < m ? src[e] : -1;
+        const unsigned heads = run_heads(s, lane);
+        if (s >= 0 && ((heads >> lane) & 1u)) atomicAdd(&deg[s], static_cast<uint32_t>(run_length(heads, lane)));
+    }
+}
+
+__device__ __forceinline__ unsigned long long pack_word(int32_t label, int32_t target) {
+    return (static_cast<unsigned long long>(static_cast<uint32_t>(label)) << 32) | static_cast<uint32_t>(target);
+}
+
+// Every edge written into its source's packed row of the layout: the row of
+// position p is [prp[p], prp[p+1]). A sorted list places edge e at offset
+// e - start[v] of its row: no atomics, and the row keeps the list's order.
+__global__ void __launch_bounds__(256) k_place_sorted(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                                                      const int32_t* __restrict__ elab, int64_t m,
+                                                      const int32_t* __restrict__ vpos, const int64_t* __restrict__ prp,
+                                                      const int64_t* __restrict__ start,
+                                                      unsigned long long* __restrict__ pe) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t v = src[e];
+        pe[prp[vpos[v]] + (e - start[v])] = pack_word(elab[e], dst[e]);
+    }
+}
+
+// The same for an unsorted list: a per-row cursor hands out the slots, one
+// atomic per run of equal sources in a warp (the run's lanes take consecutive
+// slots in lane order). Signatures are sets, so the order of the edges inside
+// a row is never read; it follows the order in which warps reach the row's
+// cursor.
+__global__ void __launch_bounds__(256) k_place_coo(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                                                   const int32_t* __restrict__ elab, int64_t m,
+                                                   const int32_t* __restrict__ vpos, const int64_t* __restrict__ prp,
+                                                   int32_t* __restrict__ cursor, unsigned long long* __restrict__ pe) {
+    const unsigned lane = threadIdx.x & 31u;
+    // trip count is uniform across the warp so the shuffles see every lane
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t e0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; e0 < m; e0 += stride) {
+        const int64_t e = e0 + threadIdx.x;
+        const int32_t pos = e < m ? vpos[src[e]] : -1;
+        const unsigned heads = run_heads(pos, lane);
         int32_t base = 0;
-        if (pos >= 0 && lane == static_cast<unsigned>(leader)) base = atomicAdd(&cursor[pos], __popc(peers));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (pos >= 0) {
-            const int32_t r = base + __popc(peers & ((1u << lane) - 1u));
-            pe[prp[pos] + r] = (static_cast<unsigned long long>(static_cast<uint32_t>(elab[e])) << 32) |
-                               static_cast<uint32_t>(dst[e]);
-        }
+        if (pos >= 0 && ((heads >> lane) & 1u)) base = atomicAdd(&cursor[pos], run_length(heads, lane));
+        const int h = run_head(heads, lane);
+        base = __shfl_sync(0xffffffffu, base, h);
+        if (pos >= 0) pe[prp[pos] + base + (static_cast<int>(lane) - h)] = pack_word(elab[e], dst[e]);
     }
 }
 
@@ -108,13 +161,16 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
     const int64_t m = ctx->m;
     const int64_t cap = std::max<int64_t>(m, 1);
     cudaError_t e;
-    // scratch: out-degrees, then the per-row cursors of the placement
+    // scratch: out-degrees, then the runs' first edges (sorted list) or the
+    // per-row cursors (unsorted list)
     const size_t nv = static_cast<size_t>(n) + 1;
-    const size_t bytes = 2 * ((sizeof(int32_t) * nv + 255) & ~size_t(255));
+    const size_t deg_bytes = (sizeof(uint32_t) * nv + 255) & ~size_t(255);
+    const size_t bytes = deg_bytes + sizeof(int64_t) * nv;
     char* base = nullptr;
     if ((e = cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, s))) return cuda_error(ctx, e, "alloc CSR scratch");
-    int32_t* deg = reinterpret_cast<int32_t*>(base);
-    int32_t* cursor = reinterpret_cast<int32_t*>(base + bytes / 2);
+    uint32_t* deg = reinterpret_cast<uint32_t*>(base);
+    int64_t* start = reinterpret_cast<int64_t*>(base + deg_bytes);
+    int32_t* cursor = reinterpret_cast<int32_t*>(start);
     unsigned long long* rows = nullptr;
     if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&rows), sizeof(unsigned long long) * cap, s))) {
         cudaFreeAsync(base, s);
@@ -122,30 +178,41 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
     }
 
     cudaMemsetAsync(&ctx->dstate->error, 0, sizeof(unsigned), s);
-    cudaMemsetAsync(deg, 0, sizeof(int32_t) * (n + 1), s);
+    cudaMemsetAsync(&ctx->dstate->unsorted, 0, sizeof(unsigned), s);
+    cudaMemsetAsync(deg, 0, sizeof(uint32_t) * nv, s);
     BISIM_SITE(site_val, "validate_edges");
+    BISIM_SITE(site_cnt, "count_edges");
     BISIM_SITE(site_pack, "csr_place");
+    const unsigned grid = grid_for(std::min<int64_t>(m, 1 << 22), 256);
     if (m > 0)
         Launch(site_val, s, 0, m, 8.0 * m),
-        k_validate_coo<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(src, dst, m, n, ctx->alive, deg,
-                                                                                   &ctx->dstate->error);
+        k_validate_coo<<<grid, 256, 0, s>>>(src, dst, m, n, ctx->alive, deg, start, ctx->dstate);
     cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); return cuda_error(ctx, e, "validate edges"); }
     if (ctx->hstate->error & kErrBadInput) {
         cudaFreeAsync(base, s);
         return set_error(ctx, BISIM_EINVAL, "edge endpoint out of range [0, n) or on a dead vertex");
     }
-    bisim_status st = dense_layout_positions(ctx, deg, s);
+    const bool sorted = ctx->hstate->unsorted == 0;
+    if (!sorted && m > 0) {
+        cudaMemsetAsync(deg, 0, sizeof(uint32_t) * nv, s);
+        Launch(site_cnt, s, 0, m, 4.0 * m),
+        k_count_coo<<<grid, 256, 0, s>>>(src, m, deg);
+    }
+    bisim_status st = dense_layout_positions(ctx, reinterpret_cast<const int32_t*>(deg), s);
     if (st != BISIM_OK) {
         cudaFreeAsync(base, s);
         return st;
     }
     if (m > 0) {
         // read src, dst, label, the source's position and row offset; write the packed word
-        cudaMemsetAsync(cursor, 0, sizeof(int32_t) * nv, s);
         Launch L(site_pack, s, 0, m, 24.0 * m);
-        k_place_coo<<<grid_for(std::min<int64_t>(m, 1 << 22), 256), 256, 0, s>>>(src, dst, elab, m, ctx->dvpos,
-                                                                                 ctx->dprp, cursor, rows);
+        if (sorted) {
+            k_place_sorted<<<grid, 256, 0, s>>>(src, dst, elab, m, ctx->dvpos, ctx->dprp, start, rows);
+        } else {
+            cudaMemsetAsync(cursor, 0, sizeof(int32_t) * nv, s);
+            k_place_coo<<<grid, 256, 0, s>>>(src, dst, elab, m, ctx->dvpos, ctx->dprp, cursor, rows);
+        }
     }
     ctx_free(ctx, ctx->dpe, sizeof(unsigned long long) * ctx->dpe_cap, s);
     ctx->dpe = rows;

@@ -76,6 +76,26 @@ def test_powerlaw_scaled_spans_every_bucket(B):
     assert stats["n_hub"] > 0 and stats["n_mid"] > 0 and stats["n_small"] > 0
 
 
+@pytest.mark.parametrize("order", ["sorted", "shuffled", "descending", "one_swap"])
+def test_edge_list_order_does_not_matter(B, order):
+    # a list sorted by source takes the run-based placement, any other the
+    # cursor-based one; both give the oracle's partition
+    g = graphgen.powerlaw_graph(n=100_000, m=1_000_000, dmax=100_000, seed=12)
+    assert np.all(g["src"][1:] >= g["src"][:-1])
+    m = g["src"].size
+    if order == "shuffled":
+        perm = np.random.default_rng(13).permutation(m)
+    elif order == "descending":
+        perm = np.argsort(-g["src"].astype(np.int64), kind="stable")
+    elif order == "one_swap":
+        perm = np.arange(m)
+        perm[[m // 2, m // 2 + 1000]] = perm[[m // 2 + 1000, m // 2]]
+    else:
+        perm = np.arange(m)
+    h = dict(g, src=g["src"][perm], dst=g["dst"][perm], elabel=g["elabel"][perm])
+    check(B, h, [1, oracle.FIXPOINT], cap=10)
+
+
 def test_chain_scaled_fixpoint(B):
     g = graphgen.chain_graph(n_paths=100, path_len=200, extra=4_000, seed=3)
     check(B, g, [5, oracle.FIXPOINT])
