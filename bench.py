@@ -50,14 +50,20 @@ METRIC = "k-bisim edge-iterations/sec (1 GB300, bit-exact); update-batch p50/p99
 UNIT = "edge-iterations/s"
 WORKLOAD = dict(n=10_000_000, m=100_000_000, exponent=2.1, dmax=1_000_000, n_elabels=1000, n_vlabels=200,
                 untyped=0.1, k="fixpoint", cap=10, seed=2)
-# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel from one ncu capture; None until captured for the current kernel.
-NCU_TRAFFIC_BYTES = {
-    # k_place_coo (the CSR build's placement of every edge into its row): 408.1 MB read + 216.1 MB
-    # written for the 30M-edge instance of the generator (bench.py --scale 0.3, ncu --set full, one
-    # launch); traffic grows with the edges, so x(100/30) for the 100M-edge launch. Algorithmic: 24 B
-    # per edge (source, target, label, source position, row offset, packed word), 2.4 GB per launch.
-    "csr_place": (408.1e6 + 216.1e6) * 100.0 / 30.0,
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work of the
+# kernels that can be the dominant one, each from one ncu --set full capture of one launch
+# on the generator's 3M-vertex / 30M-edge instance (bench.py --scale 0.3, inputs larger
+# than L2); a launch's traffic is this times the units it processed. Entries are removed
+# when their kernel changes.
+NCU_TRAFFIC_PER_UNIT = {
+    # k_place_sorted: 420.1 MB read + 205.7 MB written for 30M edges (algorithmic 24 B per edge)
+    "csr_place": ((420.07e6 + 205.74e6) / 30e6, "edges"),
+    # k_dense_verify, round 1 (all 3M positions listed): 214.7 MB read + 18.3 MB written
+    # (algorithmic 20 B per listed vertex); later rounds list scattered positions, whose
+    # sectors serve fewer bytes, so this is a lower bound for them
+    "dense_verify": ((214.7e6 + 18.3e6) / 3e6, "vertices"),
+    # k_dense_insert, round 1: 145.1 MB read + 30.0 MB written (algorithmic 24 B per vertex)
+    "dense_insert": ((145.1e6 + 30.0e6) / 3e6, "vertices"),
 }
 # Per-round algorithmic bytes of a refinement round (the row entries and vertices it processed).
 ROUND_EDGE_BYTES = 12.0     # packed (label, target) word 8 + gathered block id 4
@@ -487,8 +493,11 @@ def run_ours(args, world, rank, local):
     kernels = None
     if top and top["total_ms"] > 0:
         achieved = top["alg_bytes"] / (top["total_ms"] / 1e3) / 1e9
-        # the captured traffic is for the headline launch size only
-        traffic = NCU_TRAFFIC_BYTES.get(top["name"]) if (W.name == "powerlaw" and args.scale == 1.0) else None
+        per_unit = NCU_TRAFFIC_PER_UNIT.get(top["name"]) if W.name == "powerlaw" else None
+        traffic = None
+        if per_unit is not None:
+            units = top.get(per_unit[1], 0) / max(1, top["launches"])
+            traffic = per_unit[0] * units if units > 0 else None
         roofline = {"bound": "hbm", "kernel": top["name"], "achieved": round(achieved, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
                     "traffic": traffic, "alg_bytes_per_launch": top["alg_bytes"] / max(1, top["launches"]),
@@ -496,9 +505,9 @@ def run_ours(args, world, rank, local):
                     "share_of_kernel_time": round(top["total_ms"] / total_kernel_ms, 4)}
         if traffic is not None:
             roofline["traffic_vs_alg"] = round(traffic / roofline["alg_bytes_per_launch"], 3)
-            roofline["traffic_note"] = ("ncu DRAM bytes of the 30M-edge launch scaled to 100M edges (traffic "
-                                        "grows with the edges); every launch of this site is one pass over all "
-                                        "edges, so the per-launch figures describe the same launch")
+            roofline["traffic_note"] = (f"ncu DRAM bytes per {per_unit[1][:-1]} of one launch on the 30M-edge "
+                                        f"instance ({per_unit[0]:.1f} B) x the {per_unit[1]} an average launch "
+                                        f"processed here")
         kernels = sorted(({"name": p["name"], "launches": p["launches"], "ms": round(p["total_ms"], 3),
                            "share": round(p["total_ms"] / total_kernel_ms, 4),
                            "GB/s": round(p["alg_bytes"] / (p["total_ms"] / 1e3) / 1e9, 1) if p["total_ms"] else None}
