@@ -96,6 +96,9 @@ def parse_args():
     ap.add_argument("--union-rounds", action="store_true",
                     help="batched workload: run the union through the single-graph round kernels instead of the "
                          "persistent per-graph kernel")
+    ap.add_argument("--batch-split", type=int, default=None, metavar="V",
+                    help="batched workload: graphs of at most V vertices go to the persistent kernel (default: "
+                         "the library's, or the autotuner's choice)")
     ap.add_argument("--workload", default="powerlaw", choices=["powerlaw", "chain", "paths", "batched"],
                     help="powerlaw: 10M/100M to the fixpoint (the headline); chain: 1000 paths of 1000 "
                          "+ 2M random edges to the fixpoint; paths: 1000 paths of 1000 with one vertex and one "
@@ -172,7 +175,9 @@ class Workload:
                              f"labels; k=3",
                  "n_graphs": int(g["n_graphs"]), "n_vertices": self.n, "n_edges": self.m, "k": 3,
                  "round_path": "union through the single-graph round kernels" if self.union_rounds else
-                           "one persistent kernel, a CTA per graph from a largest-first queue",
+                           "graphs up to batch_split vertices: one persistent kernel, a CTA per graph from a "
+                           "largest-first queue; larger graphs: the union's round kernels on the same GPU at "
+                           "the same time",
                  "l2": "inputs larger than L2"}
         if extra:
             d.update(extra)
@@ -384,7 +389,10 @@ def run_ours(args, world, rank, local):
         tuned = bisim.bisim_autotune(ctx, rounds=2)
         bisim.summarize_destroy(ctx)
         W.options = bisim.default_options(**{k: tuned[k] for k in ("small_max_degree", "mid_max_degree",
-                                                                   "hub_chunk")})
+                                                                   "hub_chunk", "batch_split")})
+    if W.batched and args.batch_split is not None:
+        W.options = W.options or bisim.default_options()
+        W.options.batch_split = args.batch_split
 
     if W.batched and args.union_rounds:
         W.options = W.options or bisim.default_options()
@@ -535,7 +543,10 @@ def run_ours(args, world, rank, local):
                                                    f"{int(rounds)} is the result, the round after it confirms "
                                                    f"the fixpoint and is counted because it runs",
                                 "autotuned": None if tuned is None else
-                                {k: tuned[k] for k in ("small_max_degree", "mid_max_degree", "hub_chunk")}}),
+                                {k: tuned[k] for k in ("small_max_degree", "mid_max_degree", "hub_chunk")
+                                 + (("batch_split",) if W.batched else ())},
+                                **({"batch_split": int(W.options.batch_split) if W.options else None}
+                                   if W.batched else {})}),
             "iterate_only": {"value": iterate_only, "unit": UNIT, "rounds_executed": int(it_exec),
                              "note": "bisim_iterate alone on a resident context (round graph already captured)"},
             "profiled_steps": {"ms_per_step": profiled_ms / args.steps,

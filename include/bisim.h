@@ -76,11 +76,12 @@ enum { BISIM_FLAG_FULL_RECOMPUTE = 2 };
 enum { BISIM_FLAG_EAGER = 4 };
 
 /* BISIM_FLAG_UNION_ROUNDS: batched contexts run the rounds of the disjoint
- * union through the single-graph round kernels instead of the persistent
- * per-graph kernel (same partition; kept to compare the two). By default
- * bisim_iterate on a batched context is one launch of a persistent kernel
- * whose CTAs take the graphs from a work queue, largest first, and run each
- * graph's rounds, renumbering and collision levels to the end. */
+ * union through the single-graph round kernels for every graph, whatever
+ * batch_split says (same partition). Otherwise bisim_iterate on a batched
+ * context launches a persistent kernel whose CTAs take the graphs of at most
+ * batch_split vertices from a work queue, largest first, and run each graph's
+ * rounds, renumbering and collision levels to the end, while the larger graphs
+ * go through the union's round kernels at the same time. */
 enum { BISIM_FLAG_UNION_ROUNDS = 8 };
 
 /* Direction of the edges that make up a vertex's signature (Section 2.5:
@@ -114,8 +115,9 @@ typedef struct {
     int32_t mid_max_degree;    /* out-degree <= this: one warp (up to 256) or one CTA per vertex,
                                   pair values deduplicated in a shared-memory set (default 8192,
                                   max 8192); above it: hub path, the row cut into chunks over many
-                                  CTAs, its pair values bucketed by a mix of their bits and each
-                                  bucket deduplicated by one CTA in shared memory */
+                                  CTAs, which insert their pair values into a per-hub table in
+                                  device memory (two slots per row entry) behind a small
+                                  shared-memory filter */
     int32_t hub_chunk;         /* edges per CTA on the hub path (default 4096, 256..4096) */
     int32_t flags;             /* BISIM_FLAG_* bits (default 0) */
     int64_t mem_budget_bytes;  /* refuse (BISIM_ENOMEM) contexts whose device footprint would
@@ -126,6 +128,13 @@ typedef struct {
                                   2.4.2); update operations on other labels are ignored.
                                   0 (default): every edge */
     const int32_t* label_filter;  /* host or device memory, read while the context is created */
+    int32_t batch_split;       /* batched contexts: graphs of at most this many vertices are refined
+                                  by the persistent kernel, larger ones by the union's round kernels
+                                  on the caller's stream while the persistent kernel runs beside
+                                  them on a stream of its own (0, the default: every graph through
+                                  the round kernels, the fastest split measured on the 4096-graph
+                                  workload; INT32_MAX: every graph through the persistent kernel;
+                                  bisim_autotune picks it per context). Same partitions either way. */
 } bisim_options;
 
 typedef struct {
@@ -181,12 +190,14 @@ bisim_status summarize_init_coo(bisim_ctx** out, int32_t n_vertices, int64_t n_e
  * of each graph, stored graph after graph; edge_label int32[total edges];
  * vertex_label int32[total vertices]. No block ever crosses two graphs, and
  * get_partition returns graph-local canonical ids. The result for every graph
- * equals refining that graph alone. bisim_iterate on such a context is one
- * launch of a persistent kernel: its CTAs take the graphs from a device queue
- * (largest first) and each runs one graph's rounds, renumbering and collision
- * levels to the end; out_rounds is then the largest fixpoint round over the
- * graphs (k for a fixed k) and out_num_blocks the sum of their block counts,
- * as for the union refined as one graph. The per-graph table regions need
+ * equals refining that graph alone. bisim_iterate on such a context launches
+ * a persistent kernel whose CTAs take the graphs of at most
+ * opt->batch_split vertices from a device queue (largest first), each
+ * running one graph's rounds, renumbering and collision levels to the end,
+ * while the larger graphs go through the union's round kernels on the
+ * caller's stream; out_rounds is the largest fixpoint round over the graphs
+ * (k for a fixed k) and out_num_blocks the sum of their block counts, as for
+ * the union refined as one graph. The per-graph table regions need
  * fewer than 2^32 slots in total, else the union's round kernels run instead
  * (as with BISIM_FLAG_UNION_ROUNDS). apply_updates is not supported on
  * batched contexts (BISIM_ESTATE).
@@ -264,13 +275,16 @@ bisim_status get_summary_edges(bisim_ctx* ctx, int32_t* src_block, int32_t* labe
  * bisim_autotune -- choose the degree-class thresholds of the round layout
  * of the single-graph round kernels (mid_max_degree: rows above it take the
  * hub path; small_max_degree: rows up to it take one thread each) and the hub
- * chunk size for this context's graph (the persistent batched kernel's tiers
- * are fixed) by timing `rounds` refinement rounds (1..64) under each candidate value, one
- * setting at a time, on `stream`. The chosen values stay in the context (and
- * are written to *out when out is not NULL) and take effect from the next
- * bisim_iterate or apply_updates. Results never depend on these settings.
- * Leaves the context's partition undefined until the next bisim_iterate.
- * Synchronises `stream`.
+ * chunk size for this context's graph by timing `rounds` refinement rounds
+ * (1..64) under each candidate value, one setting at a time, on `stream`; on
+ * a batched context then batch_split (which graphs the persistent kernel
+ * takes and which the round kernels beside it), each candidate timed as a
+ * whole bisim_iterate of `rounds` rounds. The persistent kernel's own tiers
+ * are fixed. The chosen values stay in the context (and are written to *out
+ * when out is not NULL) and take effect from the next bisim_iterate or
+ * apply_updates. Results never depend on these settings. Leaves the
+ * context's partition undefined until the next bisim_iterate. Synchronises
+ * `stream`.
  */
 bisim_status bisim_autotune(bisim_ctx* ctx, int32_t rounds, bisim_options* out, void* stream);
 

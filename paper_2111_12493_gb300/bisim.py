@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("small_max_degree", ctypes.c_int32), ("mid_max_degree", ctypes.c_int32),
                 ("hub_chunk", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("mem_budget_bytes", ctypes.c_int64), ("direction", ctypes.c_int32),
-                ("n_label_filter", ctypes.c_int32), ("label_filter", ctypes.c_void_p)]
+                ("n_label_filter", ctypes.c_int32), ("label_filter", ctypes.c_void_p),
+                ("batch_split", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

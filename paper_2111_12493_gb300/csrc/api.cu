@@ -99,6 +99,7 @@ void free_temps(std::vector<void*>& temps, cudaStream_t s) {
 void destroy_ctx(bisim_ctx* ctx) {
     if (ctx == nullptr) return;
     dense_release(ctx);
+    segment_release(ctx);
     // free in the order of the stream the context last worked on, and wait for
     // it: the pool then hands the memory straight to the next context, which a
     // free still pending on the device would make it map afresh
@@ -121,6 +122,7 @@ bisim_options resolve_options(const bisim_options* in) {
     if (o.hub_chunk <= 0) o.hub_chunk = 4096;
     o.hub_chunk = std::min(std::max(o.hub_chunk, 256), kHubChunkMax);
     if (o.k_incremental < 0) o.k_incremental = 0;
+    if (o.batch_split < 0) o.batch_split = 0;
     return o;
 }
 
@@ -283,14 +285,12 @@ bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s) {
     return BISIM_OK;
 }
 
-// Resets to P_0 and refines: k rounds, or to the fixpoint (k = BISIM_FIXPOINT)
-// with at most `cap` rounds. Equal block counts in two consecutive rounds prove
-// the fixpoint, since every round refines the previous partition.
-bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
-                        int32_t* out_executed, int64_t* out_blocks, bool allow_graph) {
-    // batched contexts: every graph's rounds in one persistent launch
-    if (segment_usable(ctx)) return segment_rounds(ctx, k, cap, s, out_rounds, out_executed, out_blocks);
-    cudaError_t e;
+// Resets to P_0 and lists the live positions for the dense rounds: all of
+// them, or (keep_graph given, batched contexts) only those of the graphs with
+// keep_graph[g] != 0; *out_prev is then the block count of P_0 as the rounds
+// count it (see dense_keep_graphs).
+bisim_status dense_rounds_begin(bisim_ctx* ctx, cudaStream_t s, const uint8_t* keep_graph, int64_t* out_prev,
+                                int64_t* out_dropped) {
     bisim_status pst = dense_prepare(ctx, s);
     if (pst != BISIM_OK) return pst;
     if (ctx->opt.mem_budget_bytes > 0 && ctx->device_bytes > ctx->opt.mem_budget_bytes)
@@ -298,7 +298,19 @@ bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, 
     if (ctx->n > 0) cudaMemcpyAsync(ctx->P[0], ctx->P0, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToDevice, s);
     dense_start(ctx, s);
     ctx->cur = 0;
-    int64_t prev = ctx->last_blocks;   // |P_0|
+    *out_prev = ctx->last_blocks;   // |P_0|
+    *out_dropped = 0;
+    if (keep_graph != nullptr) return dense_keep_graphs(ctx, s, keep_graph, out_prev, out_dropped);
+    return BISIM_OK;
+}
+
+// Refines from the state dense_rounds_begin left: k rounds, or to the fixpoint
+// (k = BISIM_FIXPOINT) with at most `cap` rounds. Equal block counts in two
+// consecutive rounds prove the fixpoint, since every round refines the
+// previous partition.
+bisim_status dense_rounds_run(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int64_t prev,
+                              int32_t* out_rounds, int32_t* out_executed, int64_t* out_blocks, bool allow_graph) {
+    cudaError_t e;
     const bool fixpoint = k == BISIM_FIXPOINT;
     const int32_t limit = fixpoint ? cap : k;
     int32_t rounds = limit, executed = 0;
@@ -341,6 +353,22 @@ bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, 
     }
     unpin_partition(ctx, s);
     if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "refinement rounds");
+    *out_rounds = rounds;
+    *out_executed = executed;
+    *out_blocks = prev;
+    return BISIM_OK;
+}
+
+// Resets to P_0 and refines (see dense_rounds_run); batched contexts go to
+// segment_rounds.
+bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
+                        int32_t* out_executed, int64_t* out_blocks, bool allow_graph) {
+    if (segment_usable(ctx)) return segment_rounds(ctx, k, cap, s, out_rounds, out_executed, out_blocks);
+    int64_t prev = 0, dropped = 0;
+    bisim_status st = dense_rounds_begin(ctx, s, nullptr, &prev, &dropped);
+    if (st != BISIM_OK) return st;
+    int32_t rounds = 0, executed = 0;
+    if ((st = dense_rounds_run(ctx, k, cap, s, prev, &rounds, &executed, &prev, allow_graph)) != BISIM_OK) return st;
     ctx->cur_k = rounds;
     ctx->stats.rounds = rounds;
     ctx->stats.rounds_executed = executed;
@@ -366,6 +394,7 @@ void bisim_default_options(bisim_options* opt) {
     opt->mid_max_degree = kMidMaxN;
     opt->hub_chunk = 4096;
     opt->mem_budget_bytes = 0;
+    opt->batch_split = 0;
 }
 
 bisim_status summarize_init(bisim_ctx** out, int32_t n_vertices, int64_t n_edges, const int64_t* row_ptr,

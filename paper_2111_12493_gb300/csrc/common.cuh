@@ -344,7 +344,15 @@ struct bisim_ctx {
     int64_t round_graph_launches = 0;                // kernels in one captured round
 
     // batched contexts: the persistent per-graph kernel (segment.cu)
-    int32_t* seg_order = nullptr;                    // [n_graphs] work queue, largest graph first
+    int32_t* seg_order = nullptr;                    // [n_graphs] work queue of the persistent kernel, largest graph first
+    std::vector<int64_t> seg_vcount;                 // host: vertices per graph
+    std::vector<int32_t> seg_sorted;                 // host: graphs, largest first (by edges, then vertices)
+    int32_t seg_split = -1;                          // batch_split the queue and seg_big were built for
+    int32_t seg_n_small = 0;                         // graphs in the persistent kernel's queue
+    uint8_t* seg_big = nullptr;                      // [n_graphs] the graph runs through the union's round kernels
+    bisim::Slot* seg_table = nullptr;                // the persistent kernel's table regions while the union runs beside it
+    void* seg_stream = nullptr;                      // cudaStream_t of the persistent kernel beside the union
+    void* seg_events[2] = {nullptr, nullptr};        // fork and join of the two streams
     int64_t* seg_e0 = nullptr;                       // [n] first entry of the vertex's row in dpe
     int32_t* seg_deg = nullptr;                      // [n] its length
     int64_t seg_rows_version = -1;                   // layout_version the two arrays were taken from
@@ -497,6 +505,14 @@ bisim_status apply_ops_to_store(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
 // layout for every call, like the full recompute of an update batch, pass false).
 bisim_status run_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
                         int32_t* out_executed, int64_t* out_blocks, bool allow_graph = true);
+// The two halves of the dense path of run_rounds: reset to P_0 and list the
+// positions (only those of the graphs with keep_graph[g] != 0 when given),
+// then refine from there; out_prev / prev is |P_0| as the rounds count it,
+// out_dropped the live vertices left out (counted as blocks by the rounds).
+bisim_status dense_rounds_begin(bisim_ctx* ctx, cudaStream_t s, const uint8_t* keep_graph, int64_t* out_prev,
+                                int64_t* out_dropped);
+bisim_status dense_rounds_run(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int64_t prev,
+                              int32_t* out_rounds, int32_t* out_executed, int64_t* out_blocks, bool allow_graph);
 bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- dense rounds (dense.cu)
@@ -505,6 +521,13 @@ bisim_status refresh_after_edit(bisim_ctx* ctx, cudaStream_t s);
 bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s);
 // The layout's positions, classes and row offsets from the out-degrees (deg[n]).
 bisim_status dense_layout_positions(bisim_ctx* ctx, const int32_t* deg, cudaStream_t s);
+// Batched contexts: drops from the active list the positions of the graphs
+// with keep_graph[g] == 0 (marked alone, so no round kernel touches them) and
+// turns *prev from |P_0| into the count the rounds see: P_0's blocks of the
+// kept graphs plus the dropped live vertices (k_round_begin counts every
+// unlisted live vertex as a block).
+bisim_status dense_keep_graphs(bisim_ctx* ctx, cudaStream_t s, const uint8_t* keep_graph, int64_t* prev,
+                               int64_t* dropped);
 // The hub part of the layout, after the packed rows exist (or, with
 // pack_from_csr, copying the hub rows from the vertex-ordered CSR); marks the
 // layout ready.
@@ -520,6 +543,7 @@ bisim_status segment_init(bisim_ctx* ctx, const int64_t* voff_host, const int64_
                           cudaStream_t s);
 // Whether bisim_iterate runs the persistent per-graph kernel for this context.
 bool segment_usable(const bisim_ctx* ctx);
+void segment_release(bisim_ctx* ctx);
 // All rounds of every graph of a batched context in one launch; the partition ends in P[0].
 bisim_status segment_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t s, int32_t* out_rounds,
                             int32_t* out_executed, int64_t* out_blocks);

@@ -1106,6 +1106,34 @@ __global__ void __launch_bounds__(kThreads) k_active_finish(const int32_t* __res
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < len; i += stride) act[i] = next[i];
 }
 
+// Batched contexts: the positions of the graphs left out are marked alone in
+// their block (the next compaction drops them from the list, and no round
+// kernel touches them); DevState.blocks counts them and DevState.aux those
+// that are their own P_0 block id (P_0's blocks among them).
+__global__ void k_keep_graphs(const int32_t* __restrict__ vert, const int32_t* __restrict__ gid,
+                              const uint8_t* __restrict__ keep, const int32_t* __restrict__ P0, int64_t n_live,
+                              uint8_t* __restrict__ own, uint8_t* __restrict__ joined, DevState* st) {
+    unsigned long long dropped = 0, blocks0 = 0;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_live; p += stride) {
+        const int32_t v = vert[p];
+        if (keep[gid[v]]) continue;
+        own[p] = 1;
+        joined[p] = 0;
+        ++dropped;
+        if (P0[v] == v) ++blocks0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dropped += __shfl_xor_sync(0xffffffffu, dropped, o);
+        blocks0 += __shfl_xor_sync(0xffffffffu, blocks0, o);
+    }
+    if (lane_id() == 0 && dropped) {
+        atomicAdd(&st->blocks, dropped);
+        atomicAdd(&st->aux, blocks0);
+    }
+}
+
 // Start of a run of rounds: every live position is listed.
 __global__ void k_active_init(int32_t* __restrict__ act, int64_t n_live, int64_t* __restrict__ aoff,
                               unsigned long long* __restrict__ ccount, const ClassBounds cb) {
@@ -1444,7 +1472,8 @@ ClassBounds class_bounds(const bisim_ctx* ctx) {
 // End of a round: P_{i+1} of the listed vertices into the input buffer and the
 // list compacted to the vertices still not alone (see k_active_count). `stop`
 // is the captured loop's decision, or null for host-driven rounds.
-void launch_round_end(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const int32_t* stop) {
+void launch_round_end(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const int32_t* stop,
+                      const int32_t* Pfrom = nullptr) {
     BISIM_SITE(site, "active_compact");
     const int64_t n_live = ctx->dbegin[kDClasses];
     if (n_live <= 0) return;
@@ -1454,7 +1483,7 @@ void launch_round_end(bisim_ctx* ctx, cudaStream_t s, const DenseView& D, const 
     // then the list and flags again, and 8 per survivor (written, copied)
     Launch L(site, s, 0, 0, 0.0);
     unsigned long long* ccount = class_counts(ctx);
-    k_active_count<<<grid, kThreads, 0, s>>>(D, ctx->P[1], ctx->P[0], ctx->n, n_live, ctx->dtile, ccount,
+    k_active_count<<<grid, kThreads, 0, s>>>(D, Pfrom ? Pfrom : ctx->P[1], ctx->P[0], ctx->n, n_live, ctx->dtile, ccount,
                                              class_bounds(ctx), stop);
     k_active_scan<<<1, 1024, 0, s>>>(ctx->daoff, ctx->dtile, slot_total, stop);
     k_active_scatter<<<grid, kThreads, 0, s>>>(D, ctx->dtile, ctx->dact2, stop);
@@ -1904,6 +1933,27 @@ void dense_mark_dead(bisim_ctx* ctx, cudaStream_t s) {
     BISIM_SITE(site, "dense_dead");
     Launch L(site, s, ctx->n - n_live, 0, 12.0 * (ctx->n - n_live));
     k_dense_dead<<<grid_for(ctx->n - n_live, 256), 256, 0, s>>>(ctx->dvert, n_live, ctx->n, ctx->P[0], ctx->P[1]);
+}
+
+bisim_status dense_keep_graphs(bisim_ctx* ctx, cudaStream_t s, const uint8_t* keep_graph, int64_t* prev,
+                               int64_t* dropped) {
+    const int64_t n_live = ctx->dbegin[kDClasses];
+    if (n_live <= 0 || ctx->gid == nullptr) return BISIM_OK;
+    cudaMemsetAsync(ctx->dstate, 0, sizeof(DevState), s);
+    BISIM_SITE(site, "active_init");
+    {
+        Launch L(site, s, n_live, 0, 13.0 * n_live);
+        k_keep_graphs<<<static_cast<unsigned>(std::min<int64_t>(kPersistGrid, cdiv(n_live, kThreads))), kThreads, 0,
+                        s>>>(ctx->dvert, ctx->gid, keep_graph, ctx->P0, n_live, ctx->downs, ctx->djoined, ctx->dstate);
+    }
+    // the list keeps the other positions; both partition buffers hold P_0 there
+    launch_round_end(ctx, s, dense_view(ctx), nullptr, ctx->P[0]);
+    cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "list the kept graphs");
+    *dropped = static_cast<int64_t>(ctx->hstate->blocks);
+    *prev = *prev - static_cast<int64_t>(ctx->hstate->aux) + *dropped;
+    return BISIM_OK;
 }
 
 bisim_status dense_round(bisim_ctx* ctx, cudaStream_t s, int64_t* out_blocks) {

@@ -595,7 +595,7 @@ __global__ void k_seg_rows(const int32_t* __restrict__ vpos, const int64_t* __re
     deg[v] = static_cast<int32_t>(prp[p + 1] - a);
 }
 
-int seg_grid(int32_t G) {
+int seg_grid(int32_t G, bool beside_union) {
     static int per_sm = -1, sms = 0;
     if (per_sm < 0) {
         int dev = 0;
@@ -607,7 +607,7 @@ int seg_grid(int32_t G) {
         per_sm = std::max(b, 1);
         cudaGetLastError();
     }
-    return static_cast<int>(std::min<int64_t>(G, static_cast<int64_t>(per_sm) * std::max(sms, 1)));
+    return static_cast<int>(std::min<int64_t>(G, static_cast<int64_t>(beside_union ? 1 : per_sm) * std::max(sms, 1)));
 }
 
 }  // namespace
@@ -623,11 +623,37 @@ bisim_status segment_init(bisim_ctx* ctx, const int64_t* voff_host, const int64_
         if (ea != eb) return ea > eb;
         return voff_host[a + 1] - voff_host[a] > voff_host[b + 1] - voff_host[b];
     });
+    ctx->seg_sorted = order;
+    ctx->seg_vcount.resize(n_graphs);
+    for (int32_t g = 0; g < n_graphs; ++g) ctx->seg_vcount[g] = voff_host[g + 1] - voff_host[g];
     cudaError_t e;
-    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->seg_order), sizeof(int32_t) * n_graphs, s)))
+    if ((e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->seg_order), sizeof(int32_t) * n_graphs, s)) ||
+        (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->seg_big), std::max<size_t>(n_graphs, 1), s)))
         return cuda_error(ctx, e, "alloc graph queue");
-    cudaMemcpyAsync(ctx->seg_order, order.data(), sizeof(int32_t) * n_graphs, cudaMemcpyHostToDevice, s);
-    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "upload graph queue");
+    ctx->seg_split = -1;
+    return BISIM_OK;
+}
+
+// The persistent kernel's queue for a split: the graphs of at most `split`
+// vertices, largest first; seg_big flags the others, which the union's round
+// kernels refine beside it.
+bisim_status segment_queue(bisim_ctx* ctx, int32_t split, cudaStream_t s) {
+    if (ctx->seg_split == split) return BISIM_OK;
+    const int32_t G = ctx->n_graphs;
+    std::vector<int32_t> queue;
+    std::vector<uint8_t> big(G, 0);
+    queue.reserve(G);
+    for (int32_t g : ctx->seg_sorted) {
+        if (ctx->seg_vcount[g] <= split) queue.push_back(g);
+        else big[g] = 1;
+    }
+    ctx->seg_n_small = static_cast<int32_t>(queue.size());
+    if (!queue.empty())
+        cudaMemcpyAsync(ctx->seg_order, queue.data(), sizeof(int32_t) * queue.size(), cudaMemcpyHostToDevice, s);
+    if (G > 0) cudaMemcpyAsync(ctx->seg_big, big.data(), G, cudaMemcpyHostToDevice, s);
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "upload graph queue");   // the host vectors die here
+    ctx->seg_split = split;
     return BISIM_OK;
 }
 
@@ -668,14 +694,61 @@ bisim_status segment_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t
                                                                          ctx->seg_deg);
         ctx->seg_rows_version = ctx->layout_version;
     }
+    bisim_status st;
+    if ((st = segment_queue(ctx, ctx->opt.batch_split, s)) != BISIM_OK) return st;
+    const int32_t n_small = ctx->seg_n_small;
+    const bool any_big = n_small < ctx->n_graphs;
+    if (any_big && (n_small == 0 || limit <= 0)) {
+        // every graph above the split: the union's round kernels alone
+        int64_t prev = 0, dropped = 0, blocks = 0;
+        int32_t rounds = 0, executed = 0;
+        if ((st = dense_rounds_begin(ctx, s, nullptr, &prev, &dropped)) != BISIM_OK ||
+            (st = dense_rounds_run(ctx, k, cap, s, prev, &rounds, &executed, &blocks, true)) != BISIM_OK)
+            return st;
+        ctx->cur_k = rounds;
+        ctx->stats.rounds = rounds;
+        ctx->stats.rounds_executed = executed;
+        ctx->stats.num_blocks = blocks;
+        *out_rounds = rounds;
+        *out_executed = executed;
+        *out_blocks = blocks;
+        return BISIM_OK;
+    }
+    // graphs above the split (if any) go through the union's round kernels on
+    // the caller's stream while the persistent kernel takes the others on a
+    // second stream: the two touch disjoint vertices and table regions (the
+    // persistent kernel's in a table of its own, since the union's rounds
+    // clear theirs whole)
+    const bool hybrid = any_big;
+    int64_t prev_u = 0, dropped = 0;
+    cudaStream_t ks = s;
+    if (hybrid) {
+        if ((st = dense_rounds_begin(ctx, s, ctx->seg_big, &prev_u, &dropped)) != BISIM_OK) return st;
+        if (ctx->seg_table == nullptr &&
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->seg_table), sizeof(Slot) * ctx->n_rslots, s)))
+            return cuda_error(ctx, e, "alloc the persistent kernel's table");
+        if (ctx->seg_stream == nullptr &&
+            ((e = cudaStreamCreateWithFlags(reinterpret_cast<cudaStream_t*>(&ctx->seg_stream), cudaStreamNonBlocking)) ||
+             (e = cudaEventCreateWithFlags(reinterpret_cast<cudaEvent_t*>(&ctx->seg_events[0]), cudaEventDisableTiming)) ||
+             (e = cudaEventCreateWithFlags(reinterpret_cast<cudaEvent_t*>(&ctx->seg_events[1]), cudaEventDisableTiming))))
+            return cuda_error(ctx, e, "create the persistent kernel's stream");
+        ctx->stats.device_bytes = ctx->device_bytes;
+        if (ctx->opt.mem_budget_bytes > 0 && ctx->device_bytes > ctx->opt.mem_budget_bytes)
+            return set_error(ctx, BISIM_ENOMEM, "context exceeds the memory budget");
+        ks = static_cast<cudaStream_t>(ctx->seg_stream);
+    }
     SegState* dst = static_cast<SegState*>(ctx->seg_state);
     SegState* hst = static_cast<SegState*>(ctx->seg_host);
     cudaMemsetAsync(dst, 0, sizeof(SegState), s);
-    if (limit > 0 && n > 0) {
+    if (hybrid) {
+        cudaEventRecord(static_cast<cudaEvent_t>(ctx->seg_events[0]), s);
+        cudaStreamWaitEvent(ks, static_cast<cudaEvent_t>(ctx->seg_events[0]), 0);
+    }
+    if (limit > 0 && n > 0 && n_small > 0) {
         SegArgs A;
         A.voff = ctx->voff;
         A.order = ctx->seg_order;
-        A.G = ctx->n_graphs;
+        A.G = n_small;
         A.re0 = ctx->seg_e0;
         A.rdeg = ctx->seg_deg;
         A.pe = ctx->dpe;
@@ -688,7 +761,7 @@ bisim_status segment_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t
         A.own = ctx->seg_own;
         A.joined = ctx->seg_joined;
         for (int i = 0; i < 4; ++i) A.list[i] = ctx->seg_lists + static_cast<int64_t>(i) * n;
-        A.slots = ctx->rtable;
+        A.slots = hybrid ? ctx->seg_table : ctx->rtable;
         A.rbase = ctx->rbase;
         A.rmask = ctx->rmask;
         const int hb = ctx->opt.hash_bits;
@@ -701,15 +774,26 @@ bisim_status segment_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t
         // (label, target: 8 B) and its partition gather (4 B) per edge, and per
         // vertex its row offsets, partition reads and writes, hash, size, slot
         // and flags (about 40 B); rounds after the first skip settled vertices,
-        // so this is an upper bound
-        Launch L(site, s, n, ctx->m, static_cast<double>(limit) * (12.0 * ctx->m + 40.0 * n));
-        k_segments<<<seg_grid(ctx->n_graphs), kSegThreads, kSegSmem, s>>>(A);
+        // so this is an upper bound (none is counted when the union's kernels,
+        // timed under their own sites, take part of the batch)
+        Launch L(site, ks, n, ctx->m, hybrid ? 0.0 : static_cast<double>(limit) * (12.0 * ctx->m + 40.0 * n));
+        // beside the union's kernels the persistent kernel keeps one CTA per SM
+        k_segments<<<seg_grid(n_small, hybrid), kSegThreads, kSegSmem, ks>>>(A);
         if ((e = cudaGetLastError())) return cuda_error(ctx, e, "launch batched rounds");
-    } else if (n > 0) {
+    } else if (n > 0 && !hybrid) {
         cudaMemcpyAsync(ctx->P[0], ctx->P0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+    }
+    int32_t rounds_u = 0, executed_u = 0;
+    int64_t blocks_u = 0;
+    bisim_status st_u = BISIM_OK;
+    if (hybrid) {
+        cudaEventRecord(static_cast<cudaEvent_t>(ctx->seg_events[1]), ks);
+        st_u = dense_rounds_run(ctx, k, cap, s, prev_u, &rounds_u, &executed_u, &blocks_u, true);
+        cudaStreamWaitEvent(s, static_cast<cudaEvent_t>(ctx->seg_events[1]), 0);   // also when the union failed
     }
     cudaMemcpyAsync(hst, dst, sizeof(SegState), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "batched rounds");
+    if (st_u != BISIM_OK) return st_u;
     if (hst->error & kErrHubFull) return set_error(ctx, BISIM_ETIMEOUT, "row set passes reached their split limit");
     if (hst->error) return set_error(ctx, BISIM_ETIMEOUT, "signature table probe limit reached");
     int32_t rounds = limit, executed = 0;
@@ -721,6 +805,12 @@ bisim_status segment_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t
         rounds = fixpoint ? hst->rounds : limit;
         executed = hst->executed;
         blocks = static_cast<int64_t>(hst->blocks);
+        if (hybrid) {
+            // the union's count holds the dropped live vertices as blocks
+            rounds = fixpoint ? std::max(rounds, rounds_u) : limit;
+            executed = std::max(executed, executed_u);
+            blocks += blocks_u - dropped;
+        }
     }
     ctx->cur = 0;
     ctx->cur_k = rounds;
@@ -732,6 +822,15 @@ bisim_status segment_rounds(bisim_ctx* ctx, int32_t k, int32_t cap, cudaStream_t
     *out_executed = executed;
     *out_blocks = blocks;
     return BISIM_OK;
+}
+
+void segment_release(bisim_ctx* ctx) {
+    if (ctx->seg_stream) cudaStreamDestroy(static_cast<cudaStream_t>(ctx->seg_stream));
+    for (void*& ev : ctx->seg_events) {
+        if (ev) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
+        ev = nullptr;
+    }
+    ctx->seg_stream = nullptr;
 }
 
 }  // namespace bisim

@@ -9,8 +9,13 @@
 //   hub_chunk         edges per CTA on the hub path       (1024, 2048, 4096)
 // Each candidate rebuilds the layout, runs one warm-up round and then times
 // `rounds` rounds from P_0 with CUDA events on the caller's stream; the fastest
-// value stays before the next setting is tuned.
+// value stays before the next setting is tuned. Batched contexts then tune
+// batch_split (graphs up to it go to the persistent kernel, larger ones to the
+// union's round kernels beside it) over (0, 2048, 8192, 32768, INT32_MAX), each
+// candidate timed as a whole bisim_iterate of `rounds` rounds after a warm-up
+// one.
 #include <cfloat>
+#include <climits>
 
 #include "common.cuh"
 #include "prof.cuh"
@@ -34,6 +39,29 @@ bisim_status time_rounds(bisim_ctx* ctx, cudaStream_t s, int32_t rounds, float* 
         ctx->cur = 0;
         cudaEventRecord(a, s);
         for (int32_t r = 0; r < (pass == 0 ? 1 : rounds) && st == BISIM_OK; ++r) st = dense_round(ctx, s, &blocks);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(&ms, a, b);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *out_ms = ms;
+    return st;
+}
+
+// One whole run of `rounds` rounds (batched contexts: both kernels), after a
+// warm-up run.
+bisim_status time_iterate(bisim_ctx* ctx, cudaStream_t s, int32_t rounds, float* out_ms) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float ms = 0.f;
+    bisim_status st = BISIM_OK;
+    for (int pass = 0; pass < 2 && st == BISIM_OK; ++pass) {
+        int32_t r = 0, x = 0;
+        int64_t blocks = 0;
+        cudaEventRecord(a, s);
+        st = run_rounds(ctx, rounds, 0, s, &r, &x, &blocks);
         cudaEventRecord(b, s);
         cudaEventSynchronize(b);
         cudaEventElapsedTime(&ms, a, b);
@@ -89,6 +117,24 @@ extern "C" bisim_status bisim_autotune(bisim_ctx* ctx, int32_t rounds, bisim_opt
         // the next bisim_iterate builds the layout with the chosen settings (the
         // incremental path buckets its frontiers with them on every batch)
         ctx->dense_ready = false;
+        if (segment_usable(ctx)) {
+            const int32_t keep = ctx->opt.batch_split;
+            int32_t best = keep;
+            float best_ms = FLT_MAX;
+            for (int32_t c : {0, 2048, 8192, 32768, INT_MAX}) {
+                ctx->opt.batch_split = c;
+                float ms = 0.f;
+                if ((st = time_iterate(ctx, s, rounds, &ms)) != BISIM_OK) {
+                    ctx->opt.batch_split = keep;
+                    return st;
+                }
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+            ctx->opt.batch_split = best;
+        }
     }
     if (out) *out = ctx->opt;
     return BISIM_OK;

@@ -43,15 +43,26 @@ def test_default_options_without_gpu():
         pytest.skip(str(e))
     lib = ctypes.CDLL(path)
 
+    # the whole bisim_options of include/bisim.h: the call writes every field
     class Options(ctypes.Structure):
         _fields_ = [("k_incremental", ctypes.c_int32), ("hash_bits", ctypes.c_int32),
                     ("small_max_degree", ctypes.c_int32), ("mid_max_degree", ctypes.c_int32),
                     ("hub_chunk", ctypes.c_int32), ("flags", ctypes.c_int32),
-                    ("mem_budget_bytes", ctypes.c_int64)]
+                    ("mem_budget_bytes", ctypes.c_int64), ("direction", ctypes.c_int32),
+                    ("n_label_filter", ctypes.c_int32), ("label_filter", ctypes.c_void_p),
+                    ("batch_split", ctypes.c_int32)]
 
-    o = Options()
-    lib.bisim_default_options(ctypes.byref(o))
+    class Guarded(ctypes.Structure):
+        _fields_ = [("o", Options), ("guard", ctypes.c_uint8 * 64)]
+
+    g = Guarded()
+    ctypes.memset(g.guard, 0xA5, 64)
+    lib.bisim_default_options(ctypes.byref(g.o))
+    o = g.o
     assert (o.k_incremental, o.hash_bits, o.small_max_degree, o.mid_max_degree) == (2, 64, 32, 8192)
+    assert (o.hub_chunk, o.flags, o.mem_budget_bytes, o.direction, o.n_label_filter) == (4096, 0, 0, 0, 0)
+    assert not o.label_filter and o.batch_split >= 0
+    assert bytes(g.guard) == b"\xa5" * 64, "bisim_default_options wrote past the struct this test declares"
     lib.bisim_last_error.restype = ctypes.c_char_p
     assert lib.bisim_last_error(None) is not None
 

@@ -1,12 +1,13 @@
-"""Batched contexts: the persistent per-graph kernel against the oracle.
+"""Batched contexts: the persistent per-graph kernel, the union's round
+kernels and splits between the two, against the oracle.
 
-bisim_iterate on a batched context runs one launch of a persistent kernel whose
-CTAs take whole graphs from a queue. Every graph's partition must equal its
-solo run in the oracle (graph-local canonical ids), and the round count and
-block count must be those of the disjoint union refined together: the largest
-fixpoint round over the graphs, and the sum of their block counts. The same
-batches also run through the union's single-graph kernels
-(BISIM_FLAG_UNION_ROUNDS), which must give the same answers.
+With batch_split = INT32_MAX bisim_iterate on a batched context is one launch
+of a persistent kernel whose CTAs take whole graphs from a queue; with 0 (the
+default) the union's single-graph round kernels refine every graph; in
+between the two run side by side. Every graph's partition must equal its solo
+run in the oracle (graph-local canonical ids), and the round count and block
+count must be those of the disjoint union refined together: the largest
+fixpoint round over the graphs, and the sum of their block counts.
 """
 
 import numpy as np
@@ -16,6 +17,8 @@ import oracle
 from paper_2111_12493_gb300 import graphgen
 
 pytestmark = pytest.mark.gpu
+
+INT32_MAX = 2**31 - 1
 
 
 @pytest.fixture(scope="module")
@@ -81,7 +84,8 @@ def _concat(graphs):
 def test_persistent_kernel_matches_solo_runs(B, k):
     b = graphgen.batched_graphs(n_graphs=64, nmin=2, nmax=6000, seed=14)
     want, wr, wb = oracle_batched(b, k, cap=12)
-    for name, opt in (("persistent", None), ("union", B.default_options(flags=B.FLAG_UNION_ROUNDS))):
+    for name, opt in (("persistent", B.default_options(batch_split=INT32_MAX)),
+                      ("union", B.default_options(flags=B.FLAG_UNION_ROUNDS))):
         P, rounds, blocks, _ = run_batched(B, b, k, cap=12, options=opt)
         _same(P, want, f"{name} k={k}")
         assert rounds == wr, (name, rounds, wr)
@@ -92,7 +96,8 @@ def test_persistent_kernel_matches_solo_runs(B, k):
 def test_persistent_kernel_resolves_hash_collisions(B, bits):
     b = graphgen.batched_graphs(n_graphs=12, nmin=20, nmax=600 if bits == 1 else 3000, seed=15 + bits)
     want, wr, wb = oracle_batched(b, oracle.FIXPOINT, cap=8)
-    P, rounds, blocks, stats = run_batched(B, b, oracle.FIXPOINT, cap=8, options=B.default_options(hash_bits=bits))
+    P, rounds, blocks, stats = run_batched(B, b, oracle.FIXPOINT, cap=8,
+                                           options=B.default_options(hash_bits=bits, batch_split=INT32_MAX))
     _same(P, want, f"hash_bits={bits}")
     assert (rounds, blocks) == (wr, wb)
     assert stats["collision_levels"] > 0
@@ -137,23 +142,25 @@ def test_persistent_kernel_long_rows_and_row_copies(B):
               (g2["n"], g2["src"], g2["dst"], g2["elabel"], g2["vlabel"]),
               (5, [], [], [], [0, 1, 0, 1, 2]), (1, [0], [0], [3], [4])]
     b = _concat(graphs)
+    persistent = B.default_options(batch_split=INT32_MAX)
     for k in (1, 2, oracle.FIXPOINT):
         want, wr, wb = oracle_batched(b, k, cap=10)
-        P, rounds, blocks, _ = run_batched(B, b, k, cap=10)
+        P, rounds, blocks, _ = run_batched(B, b, k, cap=10, options=persistent)
         _same(P, want, f"k={k}")
         assert (rounds, blocks) == (wr, wb)
     # the two long rows, and every group of copies, share a block after one round
-    P, _, _, _ = run_batched(B, b, 1)
+    P, _, _, _ = run_batched(B, b, 1, options=persistent)
     v0 = int(b["vertex_offsets"][1])
     for lo, hi in ((0, 2), (2, 5), (5, 12), (12, 30), (30, 60), (60, 62)):
         assert len(set(P[v0 + lo:v0 + hi].tolist())) == 1, (lo, hi)
 
 
 def test_batched_iterate_is_one_launch(B):
-    """The default batched path is a single kernel launch per bisim_iterate."""
+    """With every graph in the persistent kernel, bisim_iterate is a single kernel launch."""
     b = graphgen.batched_graphs(n_graphs=20, nmin=10, nmax=2000, seed=17)
     counts = {}
-    for name, opt in (("persistent", None), ("union", B.default_options(flags=B.FLAG_UNION_ROUNDS))):
+    for name, opt in (("persistent", B.default_options(batch_split=INT32_MAX)),
+                      ("union", B.default_options(flags=B.FLAG_UNION_ROUNDS))):
         ctx = B.summarize_init_batched(*(_dev(b[key]) for key in ("vertex_offsets", "edge_offsets", "src_local",
                                                                   "dst_local", "elabel", "vlabel")), options=opt)
         B.bisim_iterate(ctx, 3, 0)
@@ -168,12 +175,83 @@ def test_persistent_kernel_repeated_calls(B):
     """A context iterated again (the queue and the table regions are reused)."""
     b = graphgen.batched_graphs(n_graphs=40, nmin=10, nmax=4000, seed=16)
     ctx = B.summarize_init_batched(*(_dev(b[key]) for key in
-                                     ("vertex_offsets", "edge_offsets", "src_local", "dst_local", "elabel", "vlabel")))
+                                     ("vertex_offsets", "edge_offsets", "src_local", "dst_local", "elabel", "vlabel")),
+                                   options=B.default_options(batch_split=INT32_MAX))
     try:
         for k in (3, 1, oracle.FIXPOINT, 3):
             rounds, blocks = B.bisim_iterate(ctx, k, 12)
             want, wr, wb = oracle_batched(b, k, cap=12)
             _same(B.get_partition(ctx).cpu().numpy(), want, f"k={k}")
             assert (rounds, blocks) == (wr, wb)
+    finally:
+        B.summarize_destroy(ctx)
+
+
+
+@pytest.mark.parametrize("split", [0, 500, 2500, INT32_MAX])
+@pytest.mark.parametrize("k", [1, 3, oracle.FIXPOINT])
+def test_split_between_the_two_kernels_matches_solo_runs(B, split, k):
+    """Graphs above batch_split go through the union's round kernels while the
+    persistent kernel takes the others on a second stream; every split gives
+    each graph its solo result and the union's round and block counts."""
+    b = graphgen.batched_graphs(n_graphs=48, nmin=2, nmax=6000, seed=19)
+    want, wr, wb = oracle_batched(b, k, cap=12)
+    P, rounds, blocks, _ = run_batched(B, b, k, cap=12, options=B.default_options(batch_split=split))
+    _same(P, want, f"split={split} k={k}")
+    assert (rounds, blocks) == (wr, wb)
+
+
+def test_split_with_hash_collisions(B):
+    b = graphgen.batched_graphs(n_graphs=16, nmin=20, nmax=3000, seed=20)
+    want, wr, wb = oracle_batched(b, oracle.FIXPOINT, cap=8)
+    P, rounds, blocks, stats = run_batched(B, b, oracle.FIXPOINT, cap=8,
+                                           options=B.default_options(hash_bits=8, batch_split=1000))
+    _same(P, want, "hash_bits=8 split=1000")
+    assert (rounds, blocks) == (wr, wb)
+    assert stats["collision_levels"] > 0
+
+
+@pytest.mark.parametrize("which_still", ["small", "large", "none"])
+def test_split_round_counts_when_one_side_is_at_its_fixpoint(B, which_still):
+    """The fixpoint round of the batch is the larger of the two sides', also
+    when one side's graphs are already stable at P_0 (edgeless graphs)."""
+    chain = lambda n: (n, np.arange(n - 1), np.arange(1, n), np.zeros(n - 1, np.int32), np.zeros(n, np.int32))
+    edgeless = lambda n: (n, [], [], [], np.arange(n) % 3)
+    small = chain(40) if which_still == "small" else edgeless(40)
+    large = chain(3000) if which_still == "large" else edgeless(3000)
+    b = _concat([small, large, edgeless(7)])
+    for k in (oracle.FIXPOINT, 2):
+        want, wr, wb = oracle_batched(b, k, cap=5000)
+        P, rounds, blocks, _ = run_batched(B, b, k, cap=5000, options=B.default_options(batch_split=1000))
+        _same(P, want, f"{which_still} k={k}")
+        assert (rounds, blocks) == (wr, wb), (which_still, k, rounds, wr, blocks, wb)
+
+
+def test_split_context_iterated_again(B):
+    b = graphgen.batched_graphs(n_graphs=30, nmin=10, nmax=5000, seed=21)
+    ctx = B.summarize_init_batched(*(_dev(b[key]) for key in
+                                     ("vertex_offsets", "edge_offsets", "src_local", "dst_local", "elabel", "vlabel")),
+                                   options=B.default_options(batch_split=1500))
+    try:
+        for k in (3, oracle.FIXPOINT, 1, 3):
+            rounds, blocks = B.bisim_iterate(ctx, k, 12)
+            want, wr, wb = oracle_batched(b, k, cap=12)
+            _same(B.get_partition(ctx).cpu().numpy(), want, f"k={k}")
+            assert (rounds, blocks) == (wr, wb)
+    finally:
+        B.summarize_destroy(ctx)
+
+
+def test_autotune_picks_a_listed_split_and_keeps_results(B):
+    b = graphgen.batched_graphs(n_graphs=40, nmin=10, nmax=20_000, seed=22)
+    want, wr, wb = oracle_batched(b, 3)
+    ctx = B.summarize_init_batched(*(_dev(b[key]) for key in
+                                     ("vertex_offsets", "edge_offsets", "src_local", "dst_local", "elabel", "vlabel")))
+    try:
+        tuned = B.bisim_autotune(ctx, rounds=2)
+        assert tuned["batch_split"] in (0, 2048, 8192, 32768, INT32_MAX)
+        rounds, blocks = B.bisim_iterate(ctx, 3, 0)
+        _same(B.get_partition(ctx).cpu().numpy(), want, f"tuned split {tuned['batch_split']}")
+        assert (rounds, blocks) == (wr, wb)
     finally:
         B.summarize_destroy(ctx)

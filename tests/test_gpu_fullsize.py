@@ -135,13 +135,21 @@ def test_chain_full_fixpoint(B):
 
 
 def test_batched_4096_sampled_graphs(B):
+    """The 4096-graph workload through the union's round kernels (the default),
+    a split between them and the persistent kernel, and the persistent kernel
+    alone: identical partitions, sampled graphs equal to their oracle runs."""
     b = graphgen.batched_graphs(seed=4)
     vo, eo = b["vertex_offsets"], b["edge_offsets"]
-    ctx = B.summarize_init_batched(_dev(vo), _dev(eo), _dev(b["src_local"]), _dev(b["dst_local"]),
-                                   _dev(b["elabel"]), _dev(b["vlabel"]))
-    B.bisim_iterate(ctx, 3, 0)
-    got = B.get_partition(ctx).cpu().numpy()
-    B.summarize_destroy(ctx)
+    d = [_dev(vo), _dev(eo), _dev(b["src_local"]), _dev(b["dst_local"]), _dev(b["elabel"]), _dev(b["vlabel"])]
+    runs = {}
+    for split in (0, 16384, 2**31 - 1):
+        ctx = B.summarize_init_batched(*d, options=B.default_options(batch_split=split))
+        runs[split] = B.bisim_iterate(ctx, 3, 0), B.get_partition(ctx).cpu().numpy()
+        B.summarize_destroy(ctx)
+    got = runs[0][1]
+    for split, (rb, P) in runs.items():
+        assert rb == runs[0][0], split
+        _same(P, got, f"batch_split={split}")
     sizes = np.diff(vo)
     rng = np.random.default_rng(44)
     pick = sorted(set(rng.choice(b["n_graphs"], 48, replace=False).tolist()) |
