@@ -289,6 +289,16 @@ bisim_status get_summary_edges(bisim_ctx* ctx, int32_t* src_block, int32_t* labe
 bisim_status bisim_autotune(bisim_ctx* ctx, int32_t rounds, bisim_options* out, void* stream);
 
 /*
+ * bisim_retune -- set a context's tuning options without timing anything:
+ * small_max_degree, mid_max_degree, hub_chunk and batch_split are taken from
+ * *opt (clamped as at creation); every other field of *opt is ignored. For
+ * settings that bisim_autotune chose earlier on a graph of the same shape.
+ * Results never depend on them; the round layout is rebuilt by the next
+ * bisim_iterate or apply_updates. BISIM_EINVAL for a NULL ctx or opt.
+ */
+bisim_status bisim_retune(bisim_ctx* ctx, const bisim_options* opt);
+
+/*
  * bisim_refine_round_noalloc -- one refinement round (block_in -> block_out)
  * that allocates no memory at all. The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory, such as a

@@ -385,6 +385,18 @@ using namespace bisim;
 
 extern "C" {
 
+bisim_status bisim_retune(bisim_ctx* ctx, const bisim_options* opt) {
+    if (ctx == nullptr) return set_error(nullptr, BISIM_EINVAL, "ctx is NULL");
+    if (opt == nullptr) return set_error(ctx, BISIM_EINVAL, "opt is NULL");
+    const bisim_options o = resolve_options(opt);
+    ctx->opt.small_max_degree = o.small_max_degree;
+    ctx->opt.mid_max_degree = o.mid_max_degree;
+    ctx->opt.hub_chunk = o.hub_chunk;
+    ctx->opt.batch_split = o.batch_split;
+    ctx->dense_ready = false;        // the next run rebuilds the layout with them
+    return BISIM_OK;
+}
+
 void bisim_default_options(bisim_options* opt) {
     if (opt == nullptr) return;
     std::memset(opt, 0, sizeof(*opt));
