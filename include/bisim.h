@@ -293,10 +293,12 @@ bisim_status bisim_autotune(bisim_ctx* ctx, int32_t rounds, bisim_options* out, 
  * small_max_degree, mid_max_degree, hub_chunk and batch_split are taken from
  * *opt (clamped as at creation); every other field of *opt is ignored. For
  * settings that bisim_autotune chose earlier on a graph of the same shape.
- * Results never depend on them; the round layout is rebuilt by the next
- * bisim_iterate or apply_updates. BISIM_EINVAL for a NULL ctx or opt.
+ * Results never depend on them; the round layout is rebuilt with them by the
+ * next bisim_iterate or apply_updates (the vertex-ordered CSR it is rebuilt
+ * from is made on `stream` first when the context has none). BISIM_EINVAL for
+ * a NULL ctx or opt. Synchronises `stream`.
  */
-bisim_status bisim_retune(bisim_ctx* ctx, const bisim_options* opt);
+bisim_status bisim_retune(bisim_ctx* ctx, const bisim_options* opt, void* stream);
 
 /*
  * bisim_refine_round_noalloc -- one refinement round (block_in -> block_out)

@@ -79,7 +79,7 @@ def _load():
         "bisim_launch_count": (i64, []),
         "bisim_refine_round_noalloc": (ctypes.c_int, [i32, i64, p, p, p, p, p, ctypes.POINTER(i64), p]),
         "bisim_autotune": (ctypes.c_int, [p, i32, ctypes.POINTER(Options), p]),
-        "bisim_retune": (ctypes.c_int, [p, ctypes.POINTER(Options)]),
+        "bisim_retune": (ctypes.c_int, [p, ctypes.POINTER(Options), p]),
         "get_block_sizes": (ctypes.c_int, [p, p, p]),
         "bisim_literal_alg4": (ctypes.c_int, [p, i32, p, ctypes.POINTER(i64), p]),
         "bisim_export_state": (ctypes.c_int, [p, p, i64, ctypes.POINTER(i64), p]),
@@ -296,14 +296,14 @@ def bisim_autotune(ctx: Context, rounds: int = 2, stream=None) -> dict:
 TUNING_FIELDS = ("small_max_degree", "mid_max_degree", "hub_chunk", "batch_split")
 
 
-def bisim_retune(ctx: Context, **settings) -> None:
+def bisim_retune(ctx: Context, stream=None, **settings) -> None:
     """Set the context's tuning options (TUNING_FIELDS) without timing; the
     layout is rebuilt by the next bisim_iterate or apply_updates."""
     unknown = set(settings) - set(TUNING_FIELDS)
     if unknown:
         raise ValueError(f"not tuning options: {sorted(unknown)}")
     o = default_options(**settings)
-    _check(_lib.bisim_retune(ctx.ptr, ctypes.byref(o)), ctx.ptr)
+    _check(_lib.bisim_retune(ctx.ptr, ctypes.byref(o), _stream(stream)), ctx.ptr)
 
 
 def bisim_get_stats(ctx: Context) -> dict:

@@ -385,9 +385,19 @@ using namespace bisim;
 
 extern "C" {
 
-bisim_status bisim_retune(bisim_ctx* ctx, const bisim_options* opt) {
+bisim_status bisim_retune(bisim_ctx* ctx, const bisim_options* opt, void* stream) {
     if (ctx == nullptr) return set_error(nullptr, BISIM_EINVAL, "ctx is NULL");
     if (opt == nullptr) return set_error(ctx, BISIM_EINVAL, "opt is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ctx->last_stream = stream;
+    bisim_status st;
+    // the new layout is built from the vertex-ordered CSR: make it from the
+    // current layout while that one is still valid
+    if ((st = refresh_after_edit(ctx, s)) != BISIM_OK || (st = dense_prepare(ctx, s)) != BISIM_OK ||
+        (st = ensure_vertex_csr(ctx, s)) != BISIM_OK)
+        return st;
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "retune");
     const bisim_options o = resolve_options(opt);
     ctx->opt.small_max_degree = o.small_max_degree;
     ctx->opt.mid_max_degree = o.mid_max_degree;

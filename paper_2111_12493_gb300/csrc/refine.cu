@@ -17,6 +17,7 @@
 // every level resolves at least one group per colliding hash and the loop ends
 // with the exact partition.
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <tuple>
 
@@ -423,6 +424,67 @@ __global__ void k_resolve_insert(const int32_t* __restrict__ list, int64_t count
     slot[v] = table_insert(t, h, v, err);
 }
 
+// P_0's table insert with each CTA tile's vertices combined first: a
+// shared-memory map from the level-0 hash to the tile's smallest vertex with
+// it, so that each distinct hash of the tile goes into the global table once
+// (the few hundred labels of ten million vertices otherwise send every vertex
+// to the same few slots, and their reads and atomics queue there). The table
+// then keeps the smallest vertex per hash as before, and every vertex gets its
+// hash's slot. A hash the map cannot place within kP0Probes slots goes into
+// the table from its vertex alone.
+constexpr int kP0Per = 8;
+constexpr int kP0Tile = 256 * kP0Per;
+constexpr int kP0Slots = 1024;
+constexpr int kP0Probes = 16;
+constexpr unsigned long long kP0Empty = ~0ull;
+__global__ void __launch_bounds__(256) k_p0_insert(int32_t n, const uint8_t* __restrict__ alive, LabelMode M,
+                                                   uint32_t* __restrict__ slot, TableRef t, unsigned* err) {
+    __shared__ unsigned long long key[kP0Slots];
+    __shared__ int32_t vmin[kP0Slots];
+    __shared__ uint32_t gslot[kP0Slots];
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * kP0Tile; base < n;
+         base += static_cast<int64_t>(gridDim.x) * kP0Tile) {
+        for (int i = threadIdx.x; i < kP0Slots; i += blockDim.x) {
+            key[i] = kP0Empty;
+            vmin[i] = INT_MAX;
+        }
+        __syncthreads();
+        uint64_t h[kP0Per];
+        int where[kP0Per];                      // map entry; -1: straight to the table; -2: nothing (dead, past n)
+#pragma unroll
+        for (int k = 0; k < kP0Per; ++k) {
+            const int64_t v = base + static_cast<int64_t>(k) * blockDim.x + threadIdx.x;
+            where[k] = -2;
+            h[k] = 0;
+            if (v >= n || (alive != nullptr && !alive[v])) continue;
+            h[k] = level_hash(M.hash0(static_cast<int32_t>(v)), 0u, t.hmask);
+            where[k] = -1;
+            if (h[k] == kP0Empty) continue;
+            uint32_t pos = static_cast<uint32_t>(h[k]) & (kP0Slots - 1);
+            for (int probe = 0; probe < kP0Probes; ++probe) {
+                const unsigned long long prev = atomicCAS(&key[pos], kP0Empty, h[k]);
+                if (prev == kP0Empty || prev == h[k]) {
+                    atomicMin(&vmin[pos], static_cast<int32_t>(v));
+                    where[k] = static_cast<int>(pos);
+                    break;
+                }
+                pos = (pos + 1) & (kP0Slots - 1);
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kP0Slots; i += blockDim.x)
+            if (key[i] != kP0Empty) gslot[i] = table_insert(t, key[i], vmin[i], err);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kP0Per; ++k) {
+            const int64_t v = base + static_cast<int64_t>(k) * blockDim.x + threadIdx.x;
+            if (where[k] >= 0) slot[v] = gslot[where[k]];
+            else if (where[k] == -1) slot[v] = table_insert(t, h[k], static_cast<int32_t>(v), err);
+        }
+        __syncthreads();                          // the map is cleared for the next tile
+    }
+}
+
 // Confirm each vertex against its slot's smallest vertex. Equal: that vertex is
 // its block id. Different: queue it for the next level.
 template <class Mode>
@@ -739,8 +801,8 @@ bisim_status compute_p0(bisim_ctx* ctx, cudaStream_t s) {
     if (ctx->n > 0) {
         BISIM_SITE(site, "label_insert");
         Launch L(site, s, ctx->n, 0, 20.0 * ctx->n);   // label 4 B + one 16-byte table slot
-        k_resolve_insert<LabelMode><<<grid_for(ctx->n, 256), 256, 0, s>>>(nullptr, ctx->n, ctx->alive, M, 0u,
-                                                                          ctx->slot, t, &ctx->dstate->error);
+        k_p0_insert<<<static_cast<unsigned>(std::min<int64_t>(cdiv(ctx->n, kP0Tile), 152 * 8)), 256, 0, s>>>(
+            ctx->n, ctx->alive, M, ctx->slot, t, &ctx->dstate->error);
     }
     int64_t blocks = 0;
     bisim_status st = resolve(ctx, M, ctx->P0, nullptr, 0, s, &blocks);

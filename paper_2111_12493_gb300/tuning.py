@@ -93,7 +93,7 @@ def autotune_cached(ctx, cache: TuneCache, options=None, rounds: int = 2, stream
     key = shape_key(bisim.bisim_get_stats(ctx), {f: getattr(opts, f) for f, _ in opts._fields_}, _device_name())
     hit = cache.lookup(key)
     if hit is not None:
-        bisim.bisim_retune(ctx, **hit)
+        bisim.bisim_retune(ctx, stream=stream, **hit)
         return hit, True
     tuned = bisim.bisim_autotune(ctx, rounds=rounds, stream=stream)
     settings = {k: int(tuned[k]) for k in bisim.TUNING_FIELDS}

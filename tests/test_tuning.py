@@ -56,7 +56,7 @@ def test_known_shape_skips_the_tuner(tmp_path, monkeypatch):
 
     monkeypatch.setattr(bisim, "bisim_get_stats", lambda ctx: stats)
     monkeypatch.setattr(bisim, "bisim_autotune", fake_autotune)
-    monkeypatch.setattr(bisim, "bisim_retune", lambda ctx, **kw: calls["retune"].append(kw))
+    monkeypatch.setattr(bisim, "bisim_retune", lambda ctx, stream=None, **kw: calls["retune"].append(kw))
     monkeypatch.setattr(tuning, "_device_name", lambda: "GPU A")
     cache = tuning.TuneCache(str(tmp_path / "t.json"))
     got, hit = tuning.autotune_cached(object(), cache)
