@@ -96,6 +96,38 @@ def test_edge_list_order_does_not_matter(B, order):
     check(B, h, [1, oracle.FIXPOINT], cap=10)
 
 
+def test_big_hubs_with_few_and_many_distinct_values(B):
+    """Hub rows of 100k entries with a few distinct pairs and of 250k with
+    about 200k distinct pairs (the hub path's per-hub tables near their
+    design load), and a pair of equal 40k-entry rows in different orders,
+    against the oracle."""
+    rng = np.random.default_rng(91)
+    n = 60_000
+    src, dst, lab = [], [], []
+    # a 100k-entry hub with few distinct pairs (labels 0..3, targets of 3 vertex labels)
+    src.append(np.zeros(100_000, np.int64)); dst.append(rng.integers(1000, n, 100_000))
+    lab.append(rng.integers(0, 4, 100_000))
+    # a 250k-entry hub with about 200k distinct pairs: the set overflows
+    src.append(np.ones(250_000, np.int64)); dst.append(rng.integers(1000, n, 250_000))
+    lab.append(rng.integers(0, 4000, 250_000))
+    # two equal 40k-entry rows (sources 2 and 3), in different orders
+    t = rng.integers(1000, n, 40_000); l = rng.integers(0, 50, 40_000)
+    for u in (2, 3):
+        p = rng.permutation(t.size)
+        src.append(np.full(t.size, u)); dst.append(t[p]); lab.append(l[p])
+    rest = rng.integers(4, n, 200_000)
+    src.append(rest); dst.append(rng.integers(0, n, rest.size)); lab.append(rng.integers(0, 8, rest.size))
+    vlabel = rng.integers(0, 3, n).astype(np.int32)
+    vlabel[1000:] = rng.integers(0, 60, n - 1000)
+    vlabel[3] = vlabel[2]
+    g = dict(n=n, src=np.concatenate(src).astype(np.int32), dst=np.concatenate(dst).astype(np.int32),
+             elabel=np.concatenate(lab).astype(np.int32), vlabel=vlabel)
+    stats = check(B, g, [1, 2, oracle.FIXPOINT], cap=6)
+    assert stats["n_hub"] >= 4
+    P, _, _, _ = gpu_partition(B, g, 1)
+    assert P[2] == P[3] == 2
+
+
 def test_chain_scaled_fixpoint(B):
     g = graphgen.chain_graph(n_paths=100, path_len=200, extra=4_000, seed=3)
     check(B, g, [5, oracle.FIXPOINT])
