@@ -323,8 +323,7 @@ bisim_status bisim_retune(bisim_ctx* ctx, const bisim_options* opt, void* stream
  * touch nothing. All scratch lives in one fixed array of about 10.5 MB inside
  * the library, which every GPU that loads the library holds until the process
  * exits. The first call on a device looks up that array's device address
- * (once per device); make that first call before any stream capture. Every
- * call shares the array and clears what it needs at its start, so calls that
+ * (once per device). Every call shares the array and clears what it needs at its start, so calls that
  * overlap on the GPU -- from two threads or two streams at once -- race and
  * must be serialised by the caller. Synchronises `stream`.
  */

@@ -100,6 +100,12 @@ void destroy_ctx(bisim_ctx* ctx) {
     if (ctx == nullptr) return;
     dense_release(ctx);
     segment_release(ctx);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(static_cast<cudaStream_t>(ctx->copy_stream));
+        cudaStreamDestroy(static_cast<cudaStream_t>(ctx->copy_stream));
+    }
+    for (void* ev : ctx->copy_events)
+        if (ev) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
     // free in the order of the stream the context last worked on, and wait for
     // it: the pool then hands the memory straight to the next context, which a
     // free still pending on the device would make it map afresh
@@ -188,6 +194,36 @@ bisim_status copy_vertex_arrays(bisim_ctx* ctx, const int32_t* vlabel, const uin
         if (ctx->n > 0) cudaMemcpyAsync(ctx->alive, alive, ctx->n, cudaMemcpyDefault, s);
     }
     if ((e = cudaGetLastError())) return cuda_error(ctx, e, "copy vertex arrays");
+    return BISIM_OK;
+}
+
+// Device buffers for a host COO list (temps[0..2]: sources, targets, labels)
+// and their copies on the context's copy stream, each followed by its event
+// (copy_events[1..3]); copy_events[0] orders the copies after the buffers'
+// allocation on `s`.
+bisim_status coo_arrive(bisim_ctx* ctx, const int32_t* src, const int32_t* dst, const int32_t* lab, size_t bytes,
+                        cudaStream_t s, std::vector<void*>& temps) {
+    cudaError_t e;
+    if (ctx->copy_stream == nullptr) {
+        if ((e = cudaStreamCreateWithFlags(reinterpret_cast<cudaStream_t*>(&ctx->copy_stream), cudaStreamNonBlocking)))
+            return cuda_error(ctx, e, "create copy stream");
+        for (void*& ev : ctx->copy_events)
+            if ((e = cudaEventCreateWithFlags(reinterpret_cast<cudaEvent_t*>(&ev), cudaEventDisableTiming)))
+                return cuda_error(ctx, e, "create copy events");
+    }
+    cudaStream_t cs = static_cast<cudaStream_t>(ctx->copy_stream);
+    const int32_t* host[3] = {src, dst, lab};
+    for (int i = 0; i < 3; ++i) {
+        void* d = nullptr;
+        if ((e = cudaMallocAsync(&d, bytes, s))) return cuda_error(ctx, e, "alloc edge arrays");
+        temps.push_back(d);
+    }
+    cudaEventRecord(static_cast<cudaEvent_t>(ctx->copy_events[0]), s);
+    cudaStreamWaitEvent(cs, static_cast<cudaEvent_t>(ctx->copy_events[0]), 0);
+    for (int i = 0; i < 3; ++i) {
+        if ((e = cudaMemcpyAsync(temps[i], host[i], bytes, cudaMemcpyDefault, cs))) return cuda_error(ctx, e, "copy edge arrays");
+        cudaEventRecord(static_cast<cudaEvent_t>(ctx->copy_events[1 + i]), cs);
+    }
     return BISIM_OK;
 }
 
@@ -479,6 +515,35 @@ bisim_status summarize_init_coo(bisim_ctx** out, int32_t n_vertices, int64_t n_e
     const void *ds = nullptr, *dd = nullptr, *dl = nullptr;
     cudaError_t e;
     const size_t eb = sizeof(int32_t) * static_cast<size_t>(n_edges);
+    if (n_edges > 0 && edge_view_identity(ctx) && !device_accessible(src) && !device_accessible(dst) &&
+        !device_accessible(edge_label)) {
+        // a host list: copied in on a stream of its own, sources first, while
+        // P_0 and then the sources' part of the build run on `stream`
+        if ((st = copy_vertex_arrays(ctx, vertex_label, alive, s)) == BISIM_OK) st = coo_arrive(ctx, src, dst, edge_label, eb, s, temps);
+        if (st == BISIM_OK) st = finish_init(ctx, s);
+        if (st == BISIM_OK) {
+            const CooArrival arr{static_cast<cudaEvent_t>(ctx->copy_events[1]),
+                                 static_cast<cudaEvent_t>(ctx->copy_events[2]),
+                                 static_cast<cudaEvent_t>(ctx->copy_events[3])};
+            st = build_from_coo(ctx, static_cast<const int32_t*>(temps[0]), static_cast<const int32_t*>(temps[1]),
+                                static_cast<const int32_t*>(temps[2]), s, &arr);
+        }
+        // no copy may still write a buffer that is freed (a failed build can
+        // return before it waited for the last of them)
+        if (st != BISIM_OK && ctx->copy_stream) cudaStreamSynchronize(static_cast<cudaStream_t>(ctx->copy_stream));
+        free_temps(temps, s);
+        if (st == BISIM_OK) {
+            ctx->stats.device_bytes = ctx->device_bytes;
+            if ((e = cudaStreamSynchronize(s))) st = cuda_error(ctx, e, "build from a host list");
+        }
+        if (st == BISIM_OK) {
+            *out = ctx;
+            return BISIM_OK;
+        }
+        std::string msg = ctx->err;
+        destroy_ctx(ctx);
+        return set_error(nullptr, st, msg);
+    }
     if ((st = copy_vertex_arrays(ctx, vertex_label, alive, s)) == BISIM_OK) {
         if ((e = stage(src, eb, s, &ds, temps)) || (e = stage(dst, eb, s, &dd, temps)) ||
             (e = stage(edge_label, eb, s, &dl, temps)))

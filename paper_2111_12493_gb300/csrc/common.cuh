@@ -339,6 +339,8 @@ struct bisim_ctx {
     bisim::HubAcc* dacc = nullptr;
     void* round_graph = nullptr;                     // cudaGraphExec_t of the device-side round loop
     void* capture_stream = nullptr;                  // cudaStream_t used only to capture it
+    void* copy_stream = nullptr;                     // cudaStream_t bringing a host COO list in beside the build
+    void* copy_events[4] = {nullptr, nullptr, nullptr, nullptr};   // buffers ready; sources, targets, labels copied
     void* dloop = nullptr;                           // loop state on the device
     void* hloop = nullptr;                           // its pinned host mirror
     int64_t round_graph_launches = 0;                // kernels in one captured round
@@ -455,8 +457,14 @@ int radix_sort_pairs(uint32_t* k0, uint64_t* v0, uint32_t* k1, uint64_t* v1, int
 
 // ----------------------------------------------------------------------------- graph build (graph.cu)
 
+// Events of a COO list being copied in on another stream (sources, targets,
+// labels, in that order): build_from_coo waits for each array just before its
+// first use.
+struct CooArrival {
+    cudaEvent_t src, dst, lab;
+};
 bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* dst,
-                            const int32_t* elab, cudaStream_t s);
+                            const int32_t* elab, cudaStream_t s, const CooArrival* arrival = nullptr);
 bisim_status build_from_csr(bisim_ctx* ctx, const int64_t* row_ptr, const int32_t* col,
                             const int32_t* elab, cudaStream_t s);
 

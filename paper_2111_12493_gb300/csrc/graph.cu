@@ -33,7 +33,8 @@ __device__ __forceinline__ int run_head(unsigned heads, unsigned lane) {
     return 31 - __clz(upto);
 }
 
-// Checks every edge, and finds out whether the list is sorted by source. For
+// Checks every edge (or, with dst null, every source; k_validate_dst then
+// checks the targets), and finds out whether the list is sorted by source. For
 // a sorted list each source's edges form one run [start, end) of the list:
 // the run's first edge records start[v] and adds -start to deg[v], its last
 // edge adds end, so deg[v] = end - start (in modular 32-bit arithmetic, exact
@@ -47,11 +48,11 @@ __global__ void __launch_bounds__(256) k_validate_coo(const int32_t* __restrict_
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
         const int32_t s = src[e];
-        const int32_t d = dst[e];
+        const int32_t d = dst != nullptr ? dst[e] : 0;
         const int32_t prev = e > 0 ? src[e - 1] : -1;
         const int32_t next = e + 1 < m ? src[e + 1] : -1;
         bool ok = s >= 0 && s < n && d >= 0 && d < n;
-        if (ok && alive != nullptr) ok = alive[s] && alive[d];
+        if (ok && alive != nullptr) ok = alive[s] && (dst == nullptr || alive[d]);
         if (!ok) {
             atomicOr(&st->error, kErrBadInput);
             continue;
@@ -62,6 +63,16 @@ __global__ void __launch_bounds__(256) k_validate_coo(const int32_t* __restrict_
             atomicAdd(&deg[s], 0u - static_cast<uint32_t>(e));
         }
         if (next != s) atomicAdd(&deg[s], static_cast<uint32_t>(e + 1));
+    }
+}
+
+// The targets' check of a list whose sources k_validate_coo checked alone.
+__global__ void __launch_bounds__(256) k_validate_dst(const int32_t* __restrict__ dst, int64_t m, int32_t n,
+                                                      const uint8_t* __restrict__ alive, DevState* st) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t d = dst[e];
+        if (d < 0 || d >= n || (alive != nullptr && !alive[d])) atomicOr(&st->error, kErrBadInput);
     }
 }
 
@@ -156,7 +167,7 @@ __global__ void k_validate_csr(const int64_t* __restrict__ rp, const int32_t* __
 // are the layout's packed rows; the vertex-ordered CSR is rebuilt from them
 // only if an update or the list-mode path asks for it.
 bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* dst,
-                            const int32_t* elab, cudaStream_t s) {
+                            const int32_t* elab, cudaStream_t s, const CooArrival* arrival) {
     const int32_t n = ctx->n;
     const int64_t m = ctx->m;
     const int64_t cap = std::max<int64_t>(m, 1);
@@ -184,9 +195,12 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
     BISIM_SITE(site_cnt, "count_edges");
     BISIM_SITE(site_pack, "csr_place");
     const unsigned grid = grid_for(std::min<int64_t>(m, 1 << 22), 256);
+    // arriving arrays: the sources are checked and counted while the targets
+    // and labels are still being copied in
+    if (arrival != nullptr) cudaStreamWaitEvent(s, arrival->src, 0);
     if (m > 0)
-        Launch(site_val, s, 0, m, 8.0 * m),
-        k_validate_coo<<<grid, 256, 0, s>>>(src, dst, m, n, ctx->alive, deg, start, ctx->dstate);
+        Launch(site_val, s, 0, m, arrival ? 4.0 * m : 8.0 * m),
+        k_validate_coo<<<grid, 256, 0, s>>>(src, arrival ? nullptr : dst, m, n, ctx->alive, deg, start, ctx->dstate);
     cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s))) { cudaFreeAsync(base, s); return cuda_error(ctx, e, "validate edges"); }
     if (ctx->hstate->error & kErrBadInput) {
@@ -204,6 +218,14 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
         cudaFreeAsync(base, s);
         return st;
     }
+    if (arrival != nullptr && m > 0) {
+        cudaStreamWaitEvent(s, arrival->dst, 0);
+        {
+            Launch L(site_val, s, 0, m, 4.0 * m);
+            k_validate_dst<<<grid, 256, 0, s>>>(dst, m, n, ctx->alive, ctx->dstate);
+        }
+        cudaStreamWaitEvent(s, arrival->lab, 0);
+    }
     if (m > 0) {
         // read src, dst, label, the source's position and row offset; write the packed word
         Launch L(site_pack, s, 0, m, 24.0 * m);
@@ -219,6 +241,13 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
     ctx->dpe_cap = cap;
     cudaFreeAsync(base, s);
     if ((e = cudaGetLastError())) return cuda_error(ctx, e, "build layout");
+    if (arrival != nullptr && m > 0) {
+        // the targets' check ran after the layout was made: read it now
+        cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "validate edge targets");
+        if (ctx->hstate->error & kErrBadInput)
+            return set_error(ctx, BISIM_EINVAL, "edge endpoint out of range [0, n) or on a dead vertex");
+    }
     return dense_layout_hubs(ctx, false, s);
 }
 

@@ -283,6 +283,35 @@ def test_host_memory_inputs_and_outputs(B):
     B.summarize_destroy(ctx)
 
 
+def test_host_lists_are_checked_while_they_arrive(B):
+    """A host COO list is copied in beside the build (sources first): a bad
+    source is caught before the layout, a bad target after it, and both give
+    BISIM_EINVAL; an unsorted and a sorted power-law list, pinned, refine to
+    the oracle's partition."""
+    import torch
+    g = graphgen.powerlaw_graph(n=50_000, m=500_000, dmax=40_000, seed=14)
+    want, _, _ = oracle.refine(g["n"], g["src"], g["dst"], g["elabel"], g["vlabel"], 3)
+    perm = np.random.default_rng(15).permutation(g["src"].size)
+    for order in (np.arange(g["src"].size), perm):
+        h = {k: torch.from_numpy(np.ascontiguousarray(g[k][order] if k != "vlabel" else g[k])).pin_memory()
+             for k in ("src", "dst", "elabel", "vlabel")}
+        ctx = B.summarize_init_coo(g["n"], h["src"], h["dst"], h["elabel"], h["vlabel"])
+        B.bisim_iterate(ctx, 3)
+        assert np.array_equal(B.get_partition(ctx).cpu().numpy(), want)
+        B.summarize_destroy(ctx)
+    for which in ("src", "dst"):
+        bad = {k: torch.from_numpy(g[k].copy()).pin_memory() for k in ("src", "dst", "elabel", "vlabel")}
+        bad[which][g["src"].size // 2] = g["n"] + 5
+        with pytest.raises(B.BisimError) as ei:
+            B.summarize_init_coo(g["n"], bad["src"], bad["dst"], bad["elabel"], bad["vlabel"])
+        assert ei.value.status == 1, which
+    # the library is still usable afterwards
+    ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]))
+    B.bisim_iterate(ctx, 3)
+    assert np.array_equal(B.get_partition(ctx).cpu().numpy(), want)
+    B.summarize_destroy(ctx)
+
+
 @pytest.mark.parametrize("bits", [64, 8])
 def test_device_round_loop_matches_eager_rounds(B, bits):
     # default: the round loop runs as one captured graph (while node on the
