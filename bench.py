@@ -513,7 +513,8 @@ def run_ours(args, world, rank, local):
                     "share_of_kernel_time": round(top["total_ms"] / total_kernel_ms, 4)}
         if traffic is not None:
             roofline["traffic_vs_alg"] = round(traffic / roofline["alg_bytes_per_launch"], 3)
-            roofline["traffic_note"] = (f"ncu DRAM bytes per {per_unit[1][:-1]} of one launch on the 30M-edge "
+            unit1 = {"vertices": "listed vertex", "edges": "edge"}[per_unit[1]]
+            roofline["traffic_note"] = (f"ncu DRAM bytes per {unit1} of one launch on the 30M-edge "
                                         f"instance ({per_unit[0]:.1f} B) x the {per_unit[1]} an average launch "
                                         f"processed here")
         kernels = sorted(({"name": p["name"], "launches": p["launches"], "ms": round(p["total_ms"], 3),
