@@ -149,6 +149,10 @@ typedef struct {
     int64_t n_small, n_mid, n_hub;  /* vertices per degree bucket */
     int64_t updates_applied;   /* operations applied by apply_updates so far */
     int64_t last_frontier;     /* vertices recomputed by the last apply_updates */
+    int64_t state_builds;      /* full builds of the incremental state: the first one, and one
+                                  whenever a level's block ids or index slots could run out in
+                                  the next batch (ids of blocks left without members are reused,
+                                  so this happens only when the index fills with tombstones) */
 } bisim_stats;
 
 /* Fills `opt` with the defaults listed above. */

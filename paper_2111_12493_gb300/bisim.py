@@ -48,7 +48,7 @@ class Stats(ctypes.Structure):
                 ("num_blocks", ctypes.c_int64), ("collision_levels", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("n_small", ctypes.c_int64), ("n_mid", ctypes.c_int64),
                 ("n_hub", ctypes.c_int64), ("updates_applied", ctypes.c_int64),
-                ("last_frontier", ctypes.c_int64)]
+                ("last_frontier", ctypes.c_int64), ("state_builds", ctypes.c_int64)]
 
 
 class KernelProfile(ctypes.Structure):

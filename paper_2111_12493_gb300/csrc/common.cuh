@@ -412,7 +412,10 @@ struct bisim_ctx {
     int32_t* bmin[bisim::kMaxIncLevels + 1] = {};
     unsigned long long* ikey[bisim::kMaxIncLevels + 1] = {};
     int32_t* ibid[bisim::kMaxIncLevels + 1] = {};
-    int64_t bnext[bisim::kMaxIncLevels + 1] = {};   // next unused block id
+    int32_t* lfree[bisim::kMaxIncLevels + 1] = {};  // [bcap] block ids freed by earlier batches, reused first
+    int64_t bnext[bisim::kMaxIncLevels + 1] = {};   // next never-used block id
+    int64_t nfree[bisim::kMaxIncLevels + 1] = {};   // ids in lfree after the last batch
+    long long* lfreec = nullptr;   // device [kMaxIncLevels + 1][3]: ids in lfree, taken, freed (in the scratch)
     int64_t itomb[bisim::kMaxIncLevels + 1] = {};   // tombstones in the index
     void* inc_ws = nullptr;        // per-batch work buffers of the incremental path (kept between batches)
     int64_t bcap = 0;              // block records per level

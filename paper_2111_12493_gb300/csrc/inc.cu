@@ -65,6 +65,8 @@ struct Level {
     unsigned long long* ikey;     // index slots: key (0 empty, 1 tombstone)
     int32_t* ibid;                // index slots: block id
     uint64_t imask;
+    int32_t* free;                // block ids freed by earlier batches
+    long long* fc;                // [3]: ids in `free` when the level starts, taken, freed this level
 };
 
 // Per-batch scratch shared by the levels.
@@ -97,7 +99,7 @@ struct Work {
 };
 
 constexpr unsigned kChkGroup = 1u, kChkProbe = 2u, kChkMin = 4u, kChkCompare = 8u, kChkAssign = 16u,
-                   kChkOutput = 32u, kChkSettle = 64u;
+                   kChkOutput = 32u, kChkSettle = 64u, kChkPurge = 128u;
 
 // ----------------------------------------------------------------------------- frontier
 
@@ -606,6 +608,22 @@ __global__ void __launch_bounds__(kCmpThreads) k_compare(const unsigned long lon
     }
 }
 
+// A block id for a group that needs a new one: first the ids freed by earlier
+// batches (k_retire frees the ids of blocks left without members; the level's
+// list holds fc[0] of them while the level runs, and fc[1] counts those
+// taken), then never-used ones. An id freed by a batch is reused only from the
+// next batch on: no vertex, and after the batch no block signature of the
+// level above, still names it (every vertex that had an out-edge into one of
+// its members was in that level's frontier).
+__device__ __forceinline__ long long take_block_id(const Level& L, int64_t* bnext) {
+    if (L.fc != nullptr) {
+        const long long avail = L.fc[0];
+        const long long p = static_cast<long long>(atomicAdd(reinterpret_cast<unsigned long long*>(&L.fc[1]), 1ull));
+        if (p < avail) return L.free[avail - 1 - p];
+    }
+    return static_cast<long long>(atomicAdd(reinterpret_cast<unsigned long long*>(bnext), 1ull));
+}
+
 // 4. groups without a live match: keep the old id if the membership is that
 // of one old block, else take a fresh id. Also (re)keys the index.
 // acc[0] index tombstones made, acc[1] rebuild flags, acc[2] tombstones reused
@@ -644,7 +662,7 @@ __global__ void k_settle(const int32_t* __restrict__ FL, int64_t fl, Level L, Wo
             return;
         }
     } else {
-        const long long nb = atomicAdd(reinterpret_cast<unsigned long long*>(bnext), 1ull);
+        const long long nb = take_block_id(L, bnext);
         if (nb >= bcap) {
             atomicOr(reinterpret_cast<unsigned*>(&counters[1]), 1u);   // out of block ids: rebuild
             W.decision[g] = kNew;
@@ -697,7 +715,7 @@ __global__ void k_settle_single(const int32_t* __restrict__ FX, int64_t fx, Leve
         L.bmin[o] = INT_MAX;
         return;
     }
-    const long long nb = atomicAdd(reinterpret_cast<unsigned long long*>(bnext), 1ull);
+    const long long nb = take_block_id(L, bnext);
     if (nb >= bcap) {
         atomicOr(reinterpret_cast<unsigned*>(&counters[1]), 1u);   // out of block ids: rebuild
         W.decision[v] = kNew;
@@ -749,7 +767,9 @@ __global__ void k_assign(const int32_t* __restrict__ F, int64_t f, const uint8_t
     }
 }
 
-// blocks left without members lose their index entry; per-block flags reset
+// blocks left without members lose their index entry and free their id (for
+// the next batch's new blocks, after the free list's unused part); per-block
+// flags reset
 __global__ void k_retire(const int32_t* __restrict__ tlist, int64_t nt, Level L, Work W,
                          unsigned long long* __restrict__ counters) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -760,6 +780,11 @@ __global__ void k_retire(const int32_t* __restrict__ tlist, int64_t nt, Level L,
     W.dirty[b] = 0u;
     W.cntF[b] = 0u;
     if (L.bcnt[b] != 0) return;
+    if (L.fc != nullptr) {
+        const long long left = L.fc[0] - min(L.fc[0], L.fc[1]);
+        const long long at = static_cast<long long>(atomicAdd(reinterpret_cast<unsigned long long*>(&L.fc[2]), 1ull));
+        L.free[left + at] = b;
+    }
     const unsigned long long key = L.bkey[b];
     uint64_t pos = key & L.imask;
     for (uint64_t probe = 0; probe <= L.imask; ++probe) {
@@ -857,12 +882,56 @@ __global__ void k_output(int32_t n, const uint8_t* __restrict__ alive, const int
     P[v] = alive[v] ? bmin[b] : -1;
 }
 
+// End of a batch: each level's free list becomes its unused part followed by
+// the ids freed in the batch (one thread per level).
+__global__ void k_free_commit(long long* __restrict__ fc, int levels) {
+    const int j = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
+    if (j >= levels) return;
+    long long* c = fc + 3 * j;
+    c[0] = c[0] - min(c[0], c[1]) + c[2];
+    c[1] = 0;
+    c[2] = 0;
+}
+
+// Index without tombstones: emptied (by a memset), then every block with
+// members and a key enters again. Those are the index's live entries (a block
+// keyed by k_settle keeps one entry under its bkey until it is re-keyed or
+// retired; a block made by k_settle_single has key 0 and none), so matching
+// sees the same candidates as before.
+__global__ void k_index_refill(const int32_t* __restrict__ bcnt, const unsigned long long* __restrict__ bkey,
+                               int64_t used, unsigned long long* __restrict__ ikey, int32_t* __restrict__ ibid,
+                               uint64_t imask, unsigned* __restrict__ err) {
+    for (int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; b < used;
+         b += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const unsigned long long key = bkey[b];
+        if (bcnt[b] <= 0 || key <= kIdxTomb) continue;
+        uint64_t pos = key & imask;
+        bool placed = false;
+        for (uint64_t probe = 0; probe <= imask && !placed; ++probe) {
+            if (ikey[pos] == kIdxEmpty && atomicCAS(&ikey[pos], kIdxEmpty, key) == kIdxEmpty) {
+                ibid[pos] = static_cast<int32_t>(b);
+                placed = true;
+            }
+            pos = (pos + 1) & imask;
+        }
+        if (!placed) atomicOr(err, kChkPurge);
+    }
+}
+
+// Free list of an imported level: every id below the next never-used one
+// whose block has no members.
+__global__ void k_free_collect(const int32_t* __restrict__ bcnt, int64_t used, int32_t* __restrict__ free,
+                               long long* __restrict__ fc) {
+    for (int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; b < used;
+         b += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        if (bcnt[b] == 0) free[atomicAdd(reinterpret_cast<unsigned long long*>(&fc[0]), 1ull)] = static_cast<int32_t>(b);
+}
+
 // ----------------------------------------------------------------------------- host side
 
 Level level_view(const bisim_ctx* ctx, int j) {
     return Level{ctx->lstale[j], ctx->lid[j], ctx->lcnt[j], ctx->bkey[j], ctx->bcnt[j], ctx->bmin[j], ctx->ikey[j],
-                 ctx->ibid[j],
-                 ctx->isize - 1};
+                 ctx->ibid[j], ctx->isize - 1, ctx->lfree[j], ctx->lfreec ? ctx->lfreec + 3 * j : nullptr};
 }
 
 constexpr int kHubPrefetch = 2048;     // hub records read back with the level's counts
@@ -879,6 +948,7 @@ struct HostStage {
     unsigned long long ncand;
     int64_t bnext[kMaxIncLevels + 1];
     unsigned long long acc[kMaxIncLevels + 1][4];
+    long long fc[kMaxIncLevels + 1][3];
     HubInfo hubs[kHubPrefetch];
 };
 
@@ -889,6 +959,7 @@ struct Scratch {
     Work W{};
     int64_t* dbnext = nullptr;         // [kMaxIncLevels + 1] next unused block id per level
     unsigned long long* dacc = nullptr;   // [kMaxIncLevels + 1][4] per-level accumulators (k_settle)
+    long long* dfree = nullptr;        // [kMaxIncLevels + 1][3] free-list counters (Level::fc)
     int32_t* blist = nullptr;          // [n] live frontier grouped by class
     int64_t* dbegin = nullptr;         // [kNumClasses + 1]
     unsigned long long* ccount = nullptr;   // [kNumClasses] vertices per class
@@ -916,7 +987,7 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     size_t lslots = 64;
     while (lslots < 2 * n) lslots <<= 1;
     need(8 * lslots);
-    need(8 * L); need(32 * L); need(32);
+    need(8 * L); need(32 * L); need(24 * L); need(32);
     need(4 * n); need(8 * (kNumClasses + 1)); need(8 * kNumClasses); need(8 * kNumClasses); need(8 * kNumClasses);
     need(sizeof(HubInfo) * std::max<size_t>(n, kHubPrefetch)); need(16);
     need(4 * n); need(16); need(3 * sizeof(RowTask) * n); need(16);
@@ -958,6 +1029,8 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     S.ltab = reinterpret_cast<unsigned long long*>(carve(8 * lslots));
     S.dbnext = reinterpret_cast<int64_t*>(carve(8 * L));
     S.dacc = reinterpret_cast<unsigned long long*>(carve(32 * L));
+    S.dfree = reinterpret_cast<long long*>(carve(24 * L));
+    ctx->lfreec = S.dfree;
     W.err = reinterpret_cast<unsigned*>(carve(32));
     W.n = ctx->n;
     W.bcap = ctx->bcap;
@@ -975,6 +1048,7 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     cudaMemsetAsync(W.err, 0, 32, s);
     cudaMemsetAsync(S.dbnext, 0, 8 * L, s);
     cudaMemsetAsync(S.dacc, 0, 32 * L, s);
+    cudaMemsetAsync(S.dfree, 0, 24 * L, s);                 // free lists start empty
     // per-block flags start (and are kept) at zero
     cudaMemsetAsync(W.cntF, 0, 4 * bc, s);
     cudaMemsetAsync(W.touched, 0, 4 * bc, s);
@@ -1249,6 +1323,8 @@ bisim_status inc_finish(bisim_ctx* ctx, Scratch& S, bool* rebuild, cudaStream_t 
     cudaMemcpyAsync(S.h->acc, S.dacc, 32 * L, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&S.h->err, S.W.err, 4, cudaMemcpyDeviceToHost, s);
     cudaMemsetAsync(S.dacc, 0, 32 * L, s);
+    k_free_commit<<<1, 32, 0, s>>>(S.dfree, L);
+    cudaMemcpyAsync(S.h->fc, S.dfree, 24 * L, cudaMemcpyDeviceToHost, s);
     cudaError_t e;
     if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "incremental update");
     if (S.h->err) {
@@ -1261,6 +1337,7 @@ bisim_status inc_finish(bisim_ctx* ctx, Scratch& S, bool* rebuild, cudaStream_t 
         ctx->itomb[j] += static_cast<int64_t>(S.h->acc[j][0]) - static_cast<int64_t>(S.h->acc[j][2]);
         if (S.h->acc[j][1]) *rebuild = true;
         ctx->bnext[j] = std::min<int64_t>(S.h->bnext[j], ctx->bcap);
+        ctx->nfree[j] = S.h->fc[j][0];
     }
     if (!*rebuild && ctx->n > 0 && ctx->hstate->error)
         return set_error(ctx, BISIM_EINVAL, "incremental state inconsistent at output");
@@ -1305,11 +1382,14 @@ void inc_release(bisim_ctx* ctx, cudaStream_t s) {
         ctx_free(ctx, ctx->ikey[j], 8 * ctx->isize, s);
         ctx_free(ctx, ctx->ibid[j], 4 * ctx->isize, s);
         ctx_free(ctx, ctx->lstale[j], n, s);
+        ctx_free(ctx, ctx->lfree[j], 4 * static_cast<size_t>(ctx->bcap), s);
         ctx->lstale[j] = nullptr;
+        ctx->lfree[j] = nullptr;
         ctx->lid[j] = ctx->lcnt[j] = ctx->bcnt[j] = ctx->bmin[j] = ctx->ibid[j] = nullptr;
         ctx->bkey[j] = ctx->ikey[j] = nullptr;
-        ctx->bnext[j] = ctx->itomb[j] = 0;
+        ctx->bnext[j] = ctx->itomb[j] = ctx->nfree[j] = 0;
     }
+    ctx->lfreec = nullptr;                                 // lives in the scratch
     ctx->inc_k = -1;
 }
 
@@ -1336,7 +1416,8 @@ bisim_status inc_alloc_levels(bisim_ctx* ctx, int K, int64_t bcap, uint64_t isiz
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bmin[j]), 4 * static_cast<size_t>(bcap), s)) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ikey[j]), 8 * isize, s)) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ibid[j]), 4 * isize, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->lstale[j]), n, s))) {
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->lstale[j]), n, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->lfree[j]), 4 * static_cast<size_t>(bcap), s))) {
             inc_release(ctx, s);
             return cuda_error(ctx, e, "alloc incremental state");
         }
@@ -1354,15 +1435,24 @@ bisim_status inc_alloc_levels(bisim_ctx* ctx, int K, int64_t bcap, uint64_t isiz
 }
 
 // Next unused block id per level, on the host and in the device counters the
-// settle kernels draw new ids from (state import).
+// settle kernels draw new ids from, and the free lists: the ids below it whose
+// blocks have no members (state import; called once the block records are in).
 bisim_status inc_set_next_ids(bisim_ctx* ctx, const int64_t* bnext, cudaStream_t s) {
     if (ctx->inc_ws == nullptr) return set_error(ctx, BISIM_ESTATE, "no incremental state");
     Scratch& S = *static_cast<Scratch*>(ctx->inc_ws);
-    for (int j = 0; j <= kMaxIncLevels; ++j) ctx->bnext[j] = bnext[j];
-    cudaError_t e = cudaMemcpyAsync(S.dbnext, ctx->bnext, sizeof(int64_t) * (kMaxIncLevels + 1),
-                                    cudaMemcpyHostToDevice, s);
+    constexpr int L = kMaxIncLevels + 1;
+    for (int j = 0; j < L; ++j) ctx->bnext[j] = std::max<int64_t>(0, std::min<int64_t>(bnext[j], ctx->bcap));
+    cudaError_t e = cudaMemcpyAsync(S.dbnext, ctx->bnext, sizeof(int64_t) * L, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(S.dfree, 0, 24 * L, s);
+    for (int j = 0; !e && j <= ctx->inc_k; ++j)
+        if (ctx->bnext[j] > 0)
+            k_free_collect<<<grid_for(ctx->bnext[j], 256), 256, 0, s>>>(ctx->bcnt[j], ctx->bnext[j], ctx->lfree[j],
+                                                                       S.dfree + 3 * j);
+    if (!e) e = cudaMemcpyAsync(S.h->fc, S.dfree, 24 * L, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);          // the source is the context's host array
-    return e ? cuda_error(ctx, e, "restore block ids") : BISIM_OK;
+    if (e) return cuda_error(ctx, e, "restore block ids");
+    for (int j = 0; j < L; ++j) ctx->nfree[j] = S.h->fc[j][0];
+    return BISIM_OK;
 }
 
 // Full build of the incremental state: every live vertex is the frontier of
@@ -1390,7 +1480,8 @@ bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s) {
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->bmin[j]), 4 * static_cast<size_t>(ctx->bcap), s)) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ikey[j]), 8 * is, s)) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->ibid[j]), 4 * is, s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->lstale[j]), n, s)))
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->lstale[j]), n, s)) ||
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->lfree[j]), 4 * static_cast<size_t>(ctx->bcap), s)))
             return cuda_error(ctx, e, "alloc incremental state");
         cudaMemsetAsync(ctx->lstale[j], 0, n, s);
         cudaMemsetAsync(ctx->lid[j], 0xff, 4 * n, s);        // -1: no block yet
@@ -1423,6 +1514,7 @@ bisim_status inc_build(bisim_ctx* ctx, cudaStream_t s) {
         return st;
     }
     ctx->stats.last_frontier = fl;
+    ctx->stats.state_builds += 1;
     return BISIM_OK;
 }
 
@@ -1474,12 +1566,41 @@ bisim_status inc_update(bisim_ctx* ctx, const uint8_t* vchanged, const uint8_t* 
         inc_release(ctx, s);      // the state may be half-updated: the next batch rebuilds it
         return st;
     }
-    // out of block ids or index slots: start over from the current graph
+    // out of block ids or index slots: start over from the current graph. The
+    // next batch takes at most n ids, the free ones first; the index holds the
+    // live blocks' keys and the tombstones. An index that is full mostly of
+    // tombstones is refilled in place instead.
     bool full = rebuild;
-    for (int j = 0; j <= K; ++j)
-        if (ctx->bnext[j] + n >= ctx->bcap || static_cast<uint64_t>(ctx->bnext[j] + ctx->itomb[j]) * 10 > ctx->isize * 7)
+    bool refilled = false;
+    for (int j = 0; j <= K && !full; ++j) {
+        const int64_t in_use = ctx->bnext[j] - ctx->nfree[j];
+        if (ctx->bnext[j] + std::max<int64_t>(0, n - ctx->nfree[j]) >= ctx->bcap ||
+            static_cast<uint64_t>(in_use) * 2 > ctx->isize) {
             full = true;
+        } else if (static_cast<uint64_t>(in_use + ctx->itomb[j]) * 10 > ctx->isize * 7) {
+            BISIM_SITE(site, "inc_index_refill");
+            Launch Lk(site, s, in_use, 0, 12.0 * ctx->bnext[j] + 8.0 * ctx->isize);
+            cudaMemsetAsync(ctx->ikey[j], 0, 8 * ctx->isize, s);
+            k_index_refill<<<grid_for(ctx->bnext[j], 256), 256, 0, s>>>(ctx->bcnt[j], ctx->bkey[j], ctx->bnext[j],
+                                                                       ctx->ikey[j], ctx->ibid[j], ctx->isize - 1,
+                                                                       S.W.err);
+            ctx->itomb[j] = 0;
+            refilled = true;
+        }
+    }
     if (full) return inc_build(ctx, s);
+    if (refilled) {
+        cudaMemcpyAsync(&S.h->err, S.W.err, 4, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e) {
+            inc_release(ctx, s);
+            return cuda_error(ctx, e, "index refill");
+        }
+        if (S.h->err) {
+            inc_release(ctx, s);
+            return set_error(ctx, BISIM_EINVAL, "incremental index refill failed its self-check");
+        }
+    }
     ctx->stats.last_frontier = total;
     return BISIM_OK;
 }

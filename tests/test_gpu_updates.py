@@ -342,3 +342,59 @@ def test_updates_from_an_empty_edge_set(B, n):
         B.apply_updates(ctx, _dev(ops))
         check_partition(B, ctx, state, 2)
     B.summarize_destroy(ctx)
+
+
+def _churn_batch(rng, n, last_added, size, label_base):
+    """Removes the previous batch's edges and adds `size` new ones, each with a
+    label of its own: every source leaves its (large) block for a block of its
+    own at every level above 0, and returns to the large block a batch later,
+    leaving that block without members."""
+    ops = [(1, u, w, l) for u, w, l in last_added]
+    srcs = rng.choice(n, size=size, replace=False)
+    added = [(int(u), int(rng.integers(n)), label_base + i) for i, u in enumerate(srcs)]
+    ops += [(0, u, w, l) for u, w, l in added]
+    return np.array(ops, dtype=np.int32).reshape(-1, 4), added
+
+
+def test_block_ids_are_reused_and_the_state_is_built_once(B):
+    """A long stream whose batches keep making and emptying blocks. Block ids
+    are never renamed, so a level would run out of them after about
+    bcap - n = n + 1024 new blocks if the ids of emptied blocks were not
+    reused; here every batch makes about 1.5k new blocks per level (about 18k
+    per level over the run, for n = 4000) and the state must still be built
+    only once, with every partition equal to the oracle's. The index's
+    tombstones are cleared in place along the way. A copy exported half way
+    and imported (its free lists rebuilt from the block sizes) continues in
+    step, without a build of its own."""
+    rng = np.random.default_rng(2024)
+    n = 4000
+    src = np.arange(n, dtype=np.int32)
+    dst = rng.integers(0, n, n).astype(np.int32)
+    elabel = np.zeros(n, np.int32)
+    vlabel = rng.integers(0, 2, n).astype(np.int32)
+    state = dict(n=n, alive=np.ones(n, np.uint8), vlabel=vlabel, src=src, dst=dst, elabel=elabel)
+    ctx = B.summarize_init_coo(n, _dev(src), _dev(dst), _dev(elabel), _dev(vlabel),
+                               options=B.default_options(k_incremental=2))
+    B.apply_updates(ctx, _dev(np.zeros((0, 4), np.int32)))
+    B.bisim_profile_reset()
+    B.bisim_profile_enable(True)
+    try:
+        added, copy = [], None
+        for step in range(12):
+            ops, added = _churn_batch(rng, n, added, 1500, 1000 + 10_000 * step)
+            state = _apply_big(state, ops)
+            B.apply_updates(ctx, _dev(ops))
+            if copy is not None:
+                B.apply_updates(copy, _dev(ops))
+                assert np.array_equal(B.get_partition(copy).cpu().numpy(), B.get_partition(ctx).cpu().numpy())
+            check_partition(B, ctx, state, 2)
+            if step == 5:
+                copy = B.bisim_import_state(B.bisim_export_state(ctx))
+        refills = sum(p["launches"] for p in B.bisim_profile_read() if p["name"] == "inc_index_refill")
+    finally:
+        B.bisim_profile_enable(False)
+    assert B.bisim_get_stats(ctx)["state_builds"] == 1
+    assert B.bisim_get_stats(copy)["state_builds"] == 0
+    assert refills >= 1
+    B.summarize_destroy(ctx)
+    B.summarize_destroy(copy)
