@@ -81,7 +81,7 @@ struct Work {
     int64_t* resume;              // [n] next index slot to probe
     uint32_t* cntF;               // [bcap] frontier members per old block
     uint32_t* touched;            // [bcap]
-    uint32_t* dirty;              // [bcap]
+    uint32_t* dirty;              // [bcap / 32] bit per block: its smallest member left
     int32_t* tlist;               // [bcap]
     int32_t* dlist;               // [bcap]
     int32_t* cand;                // [n] representatives with a candidate block
@@ -357,7 +357,9 @@ __global__ void k_remove(const int32_t* __restrict__ F, Level L, Work W) {
         atomicSub(&L.bcnt[b], 1);
         atomicAdd(&W.cntF[b], 1u);
         if (atomicExch(&W.touched[b], 1u) == 0u) W.tlist[atomicAdd(&W.counters[0], 1ull)] = b;
-        if (L.bmin[b] == v && atomicExch(&W.dirty[b], 1u) == 0u) W.dlist[atomicAdd(&W.counters[1], 1ull)] = b;
+        const unsigned bit = 1u << (b & 31);
+        if (L.bmin[b] == v && (atomicOr(&W.dirty[b >> 5], bit) & bit) == 0u)
+            W.dlist[atomicAdd(&W.counters[1], 1ull)] = b;
     }
 }
 
@@ -369,50 +371,32 @@ __global__ void k_dirty_reset(const int32_t* __restrict__ dlist, Level L, Work W
 }
 
 // smallest remaining member of every block whose minimum left (nothing to do
-// when no minimum left)
-// The dirty blocks (usually a few hundred) are first loaded into a
-// shared-memory set, so the pass over all vertices reads only lid, alive and
-// inF and looks blocks up on chip; with more dirty blocks than the set holds
-// it reads W.dirty instead.
-constexpr int kRescanSlots = 4096;
+// when no minimum left). One pass over all vertices, four per thread: the block
+// ids are read in 16-byte words and looked up in the dirty bitmap (one bit per
+// block, small enough to stay in L2); only members of dirty blocks read their
+// live and frontier flags.
 __global__ void __launch_bounds__(256) k_rescan(int32_t n, const uint8_t* __restrict__ alive, Level L, Work W) {
-    __shared__ int32_t set[kRescanSlots];
     const int64_t nd = dev_count(&W.counters[1]);
     if (nd == 0) return;
-    const bool on_chip = nd <= kRescanSlots / 2;
-    if (on_chip) {
-        for (int k = threadIdx.x; k < kRescanSlots; k += blockDim.x) set[k] = -1;
-        __syncthreads();
-        for (int64_t i = threadIdx.x; i < nd; i += blockDim.x) {
-            const int32_t b = W.dlist[i];
-            uint32_t pos = static_cast<uint32_t>(mix64(static_cast<uint64_t>(b))) & (kRescanSlots - 1);
-            for (int probe = 0; probe < kRescanSlots; ++probe) {
-                const int32_t prev = atomicCAS(&set[pos], -1, b);
-                if (prev == -1 || prev == b) break;
-                pos = (pos + 1) & (kRescanSlots - 1);
-            }
-        }
-        __syncthreads();
+    const uint32_t* __restrict__ bits = W.dirty;
+    auto visit = [&](int32_t u, int32_t b) {
+        if (b < 0 || b >= W.bcap || ((__ldg(&bits[b >> 5]) >> (b & 31)) & 1u) == 0u) return;
+        if (!alive[u] || W.inF[u]) return;
+        atomicMin(&L.bmin[b], u);
+    };
+    const int64_t quads = n / 4;
+    const int4* lid4 = reinterpret_cast<const int4*>(L.lid);
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < quads;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int4 b = lid4[q];
+        const int32_t u = static_cast<int32_t>(4 * q);
+        visit(u, b.x);
+        visit(u + 1, b.y);
+        visit(u + 2, b.z);
+        visit(u + 3, b.w);
     }
-    for (int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; u < n;
-         u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int32_t b = L.lid[u];
-        if (b < 0 || !alive[u] || W.inF[u]) continue;
-        bool dirty;
-        if (on_chip) {
-            dirty = false;
-            uint32_t pos = static_cast<uint32_t>(mix64(static_cast<uint64_t>(b))) & (kRescanSlots - 1);
-            for (int probe = 0; probe < kRescanSlots; ++probe) {
-                const int32_t cur = set[pos];
-                if (cur == b) { dirty = true; break; }
-                if (cur == -1) break;
-                pos = (pos + 1) & (kRescanSlots - 1);
-            }
-        } else {
-            dirty = W.dirty[b] != 0u;
-        }
-        if (dirty) atomicMin(&L.bmin[b], static_cast<int32_t>(u));
-    }
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t < n - 4 * quads) visit(static_cast<int32_t>(4 * quads + t), L.lid[4 * quads + t]);
 }
 
 // group statistics of the live frontier
@@ -777,7 +761,8 @@ __global__ void k_retire(const int32_t* __restrict__ tlist, int64_t nt, Level L,
     const int32_t b = tlist[i];
     // (counters: the level's accumulators, as for k_settle)
     W.touched[b] = 0u;
-    W.dirty[b] = 0u;
+    const unsigned bit = 1u << (b & 31);
+    if (W.dirty[b >> 5] & bit) atomicAnd(&W.dirty[b >> 5], ~bit);
     W.cntF[b] = 0u;
     if (L.bcnt[b] != 0) return;
     if (L.fc != nullptr) {
@@ -978,11 +963,12 @@ struct Scratch {
 cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     const size_t n = static_cast<size_t>(std::max(ctx->n, 1));
     const size_t bc = static_cast<size_t>(ctx->bcap);
+    const size_t dw = (bc + 31) / 32;                      // dirty bitmap words
     constexpr size_t L = kMaxIncLevels + 1;
     size_t bytes = 0;
     auto need = [&](size_t b) { bytes += (b + 255) & ~size_t(255); };
     need(4 * n); need(4 * n); need(8 * n); need(4 * n); need(4 * n); need(4 * n); need(4 * n); need(8 * n);
-    need(4 * bc); need(4 * bc); need(4 * bc); need(4 * bc); need(4 * bc);
+    need(4 * bc); need(4 * bc); need(4 * dw); need(4 * bc); need(4 * bc);
     need(4 * n); need(4 * n); need(8 * 16); need(4 * n); need(4 * n); need(n); need(n); need(n); need(n); need(4 * n);
     size_t lslots = 64;
     while (lslots < 2 * n) lslots <<= 1;
@@ -1013,7 +999,7 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     W.resume = reinterpret_cast<int64_t*>(carve(8 * n));
     W.cntF = reinterpret_cast<uint32_t*>(carve(4 * bc));
     W.touched = reinterpret_cast<uint32_t*>(carve(4 * bc));
-    W.dirty = reinterpret_cast<uint32_t*>(carve(4 * bc));
+    W.dirty = reinterpret_cast<uint32_t*>(carve(4 * dw));
     W.tlist = reinterpret_cast<int32_t*>(carve(4 * bc));
     W.dlist = reinterpret_cast<int32_t*>(carve(4 * bc));
     W.cand = reinterpret_cast<int32_t*>(carve(4 * n));
@@ -1052,7 +1038,7 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     // per-block flags start (and are kept) at zero
     cudaMemsetAsync(W.cntF, 0, 4 * bc, s);
     cudaMemsetAsync(W.touched, 0, 4 * bc, s);
-    cudaMemsetAsync(W.dirty, 0, 4 * bc, s);
+    cudaMemsetAsync(W.dirty, 0, 4 * dw, s);
     cudaMemsetAsync(W.changed, 0, n, s);
     cudaMemsetAsync(W.inF, 0, n, s);                       // pool memory is recycled: start clean
     cudaMemsetAsync(W.recomp, 0, n, s);
@@ -1194,11 +1180,19 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t* frontier, cu
     const int32_t n = ctx->n;
     cudaError_t e;
     bisim_status st;
-    BISIM_SITE(site, "inc_level");
+    BISIM_SITE(site_remove, "inc_remove");
+    BISIM_SITE(site_single, "inc_single");
+    BISIM_SITE(site_label, "inc_label");
+    BISIM_SITE(site_group, "inc_group");
+    BISIM_SITE(site_probe, "inc_probe");
+    BISIM_SITE(site_compare, "inc_compare");
+    BISIM_SITE(site_settle, "inc_settle");
+    BISIM_SITE(site_assign, "inc_assign");
+    BISIM_SITE(site_retire, "inc_retire");
     // 1. frontier vertices leave their old blocks (sizes read on the device)
     cudaMemsetAsync(W.counters, 0, 8 * 6, s);
     {
-        Launch Lk(site, s, 0, 0, 0.0);
+        Launch Lk(site_remove, s, 0, 0, 0.0);
         k_remove<<<kDevGrid, 256, 0, s>>>(W.F, L, W);
         k_dirty_reset<<<kDevGrid, 256, 0, s>>>(W.dlist, L, W);
         k_rescan<<<kDevGrid, 256, 0, s>>>(n, ctx->alive, L, W);
@@ -1214,7 +1208,7 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t* frontier, cu
     unsigned long long* acc = S.dacc + 4 * j;
     if (fx > 0) {
         // alone one level down: no signature, see k_settle_single
-        Launch Lk(site, s, fx, 0, 16.0 * fx);
+        Launch Lk(site_single, s, fx, 0, 16.0 * fx);
         k_settle_single<<<grid_for(fx, 256), 256, 0, s>>>(S.FX, fx, L, W, S.dbnext + j, ctx->bcap, acc);
     }
     // 2. exact groups within the live frontier
@@ -1223,7 +1217,7 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t* frontier, cu
         if (j == 0) {
             uint64_t slots = 64;
             while (slots < 2 * static_cast<uint64_t>(fl)) slots <<= 1;
-            Launch Lk(site, s, fl, 0, 40.0 * fl);
+            Launch Lk(site_label, s, fl, 0, 40.0 * fl);
             cudaMemsetAsync(S.ltab, 0xff, sizeof(unsigned long long) * slots, s);
             k_label_insert<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, ctx->vlabel, S.ltab, slots - 1, W.err);
             k_label_read<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, ctx->vlabel, S.ltab, slots - 1, W.grp, W.err);
@@ -1238,7 +1232,7 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t* frontier, cu
                 return st;
             }
         }
-        Launch Lk(site, s, fl, 0, 24.0 * fl);
+        Launch Lk(site_group, s, fl, 0, 24.0 * fl);
         k_group_init<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, W);
         k_group_stats<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, W);
     }
@@ -1247,7 +1241,7 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t* frontier, cu
     // still leaves candidates (different signatures under one hash)
     const uint64_t hmask = ctx->opt.hash_bits >= 64 ? ~0ull : ((1ull << ctx->opt.hash_bits) - 1);
     if (fl > 0) {
-        Launch Lk(site, s, fl, 0, 32.0 * fl);
+        Launch Lk(site_probe, s, fl, 0, 32.0 * fl);
         cudaMemsetAsync(&W.counters[2], 0, 8, s);
         k_probe<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, L, W, j, ctx->vlabel, hmask);
     }
@@ -1265,7 +1259,7 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t* frontier, cu
             attr = true;
         }
         {
-            Launch Lk(site, s, 0, 0, 0.0);
+            Launch Lk(site_compare, s, 0, 0, 0.0);
             k_compare<kCmpSmallSlots><<<kCmpGrid, kCmpThreads, sizeof(unsigned long long) * kCmpSmallSlots, s>>>(
                 &W.counters[2], L, Lp, W, ctx->xro, ctx->xlen, ctx->xpe, ctx->cnt, ctx->skey, B.hub_list, B.n_hub,
                 B.toff, B.tmask, B.tab, B.acc, 0, kCmpSmallSlots / 2);
@@ -1289,17 +1283,17 @@ bisim_status level_pass(bisim_ctx* ctx, int j, Scratch& S, int64_t* frontier, cu
     if (LB.hubmem) cudaFreeAsync(LB.hubmem, s);
     // 4. keep or create ids; 5. assign; retire empty blocks
     if (fl > 0) {
-        Launch Lk(site, s, fl, 0, 24.0 * fl);
+        Launch Lk(site_settle, s, fl, 0, 24.0 * fl);
         k_settle<<<grid_for(fl, 256), 256, 0, s>>>(W.FL, fl, L, W, S.dbnext + j, ctx->bcap, acc);
     }
     if (f > 0) {
-        Launch Lk(site, s, f, 0, 24.0 * f);
+        Launch Lk(site_assign, s, f, 0, 24.0 * f);
         k_assign<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, ctx->alive, L, W, ctx->cnt, j, S.clist, S.chcount,
                                                  j < ctx->inc_k ? ctx->lstale[j + 1] : nullptr);
         k_set_flags<<<grid_for(f, 256), 256, 0, s>>>(W.F, f, W.inF, 0);
     }
     if (ntouched > 0) {
-        Launch Lk(site, s, ntouched, 0, 16.0 * ntouched);
+        Launch Lk(site_retire, s, ntouched, 0, 16.0 * ntouched);
         k_retire<<<grid_for(ntouched, 256), 256, 0, s>>>(W.tlist, ntouched, L, W, acc);
     }
     return BISIM_OK;
