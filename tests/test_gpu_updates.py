@@ -398,3 +398,32 @@ def test_block_ids_are_reused_and_the_state_is_built_once(B):
     assert refills >= 1
     B.summarize_destroy(ctx)
     B.summarize_destroy(copy)
+
+
+def test_long_mixed_stream_reuses_block_ids(B):
+    """150 batches of edge adds and deletes, vertex deletions, revivals and
+    relabels on a 600-vertex graph at k = 3. The level-3 partitions alone
+    show about 3.4k new member sets over the run, against 2n + 1024 = 2224
+    ids per level of which about 1.6k are spare after the build, so without
+    reuse the state would be rebuilt on the way; every partition must equal
+    the oracle's and the state be built once."""
+    rng = np.random.default_rng(606)
+    g = graphgen.uniform_graph(n=600, m=1800, n_elabels=3, n_vlabels=4, seed=66)
+    state = dict(n=g["n"], alive=np.ones(g["n"], np.uint8), vlabel=g["vlabel"].copy(), src=g["src"],
+                 dst=g["dst"], elabel=g["elabel"])
+    ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]),
+                               options=B.default_options(k_incremental=3))
+    applied = 0
+    for step in range(150):
+        ops = random_batch(rng, state, int(rng.integers(100, 400)), n_elabels=3, n_vlabels=4)
+        try:
+            state2 = oracle.apply_ops(state, ops)
+        except oracle.UpdateRejected:
+            continue
+        B.apply_updates(ctx, _dev(ops))
+        state = state2
+        applied += 1
+        check_partition(B, ctx, state, 3)
+    assert applied >= 100
+    assert B.bisim_get_stats(ctx)["state_builds"] == 1
+    B.summarize_destroy(ctx)
