@@ -179,8 +179,13 @@ bisim_status summarize_init(bisim_ctx** out, int32_t n_vertices, int64_t n_edges
 
 /*
  * summarize_init_coo -- as summarize_init, from an edge list: src/dst int32[m]
- * in [0, n), edge_label int32[m]. The out-CSR is built on the device by a
- * stable LSD radix sort on src.
+ * in [0, n), edge_label int32[m], in any order (a list sorted by src is
+ * detected and placed without atomics). The rows are built on the device,
+ * keeping each source's edges in list order. When all three edge arrays are in
+ * host memory they are copied in on a stream of the context's own while P_0
+ * and the sources' part of the build run on `stream`; such copies of
+ * different contexts (calls from several host threads) take turns, one
+ * context's edge arrays at a time over the host link.
  */
 bisim_status summarize_init_coo(bisim_ctx** out, int32_t n_vertices, int64_t n_edges,
                                 const int32_t* src, const int32_t* dst,

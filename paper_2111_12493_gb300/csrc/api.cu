@@ -1,6 +1,8 @@
 // C-ABI entry points (declared in include/bisim.h): argument checks, input
 // staging, context lifetime, and the round loop of bisim_iterate.
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -196,6 +198,53 @@ bisim_status copy_vertex_arrays(bisim_ctx* ctx, const int32_t* vlabel, const uin
     if ((e = cudaGetLastError())) return cuda_error(ctx, e, "copy vertex arrays");
     return BISIM_OK;
 }
+
+// Host graphs of different contexts are copied in one after the other: the
+// host link bounds such a copy, and two at once would only share it and
+// finish both late, while one after the other lets the first context build
+// and refine while the second copies. A context holds the lane from before
+// its first copy until its build has seen the last one arrive. A wait gives
+// up after a minute (the lane then only loses its ordering), so a context
+// that never lets go cannot block the others for good.
+struct UploadLane {
+    std::mutex mu;
+    std::condition_variable cv;
+    bool busy = false;
+};
+
+UploadLane& upload_lane() {
+    static UploadLane* lane = new UploadLane();      // never freed: no destructor runs while a thread waits
+    return *lane;
+}
+
+void lane_take() {
+    UploadLane& L = upload_lane();
+    std::unique_lock<std::mutex> lk(L.mu);
+    L.cv.wait_for(lk, std::chrono::seconds(60), [&] { return !L.busy; });
+    L.busy = true;
+}
+
+void lane_hand_on() {
+    UploadLane& L = upload_lane();
+    {
+        std::lock_guard<std::mutex> lk(L.mu);
+        L.busy = false;
+    }
+    L.cv.notify_one();
+}
+
+struct LaneTurn {
+    bool held = false;
+    void take() {
+        lane_take();
+        held = true;
+    }
+    void give() {
+        if (held) lane_hand_on();
+        held = false;
+    }
+    ~LaneTurn() { give(); }
+};
 
 // Device buffers for a host COO list (temps[0..2]: sources, targets, labels)
 // and their copies on the context's copy stream, each followed by its event
@@ -518,7 +567,10 @@ bisim_status summarize_init_coo(bisim_ctx** out, int32_t n_vertices, int64_t n_e
     if (n_edges > 0 && edge_view_identity(ctx) && !device_accessible(src) && !device_accessible(dst) &&
         !device_accessible(edge_label)) {
         // a host list: copied in on a stream of its own, sources first, while
-        // P_0 and then the sources' part of the build run on `stream`
+        // P_0 and then the sources' part of the build run on `stream`; the
+        // upload lane is held until the build has seen the last array arrive
+        LaneTurn turn;
+        turn.take();
         if ((st = copy_vertex_arrays(ctx, vertex_label, alive, s)) == BISIM_OK) st = coo_arrive(ctx, src, dst, edge_label, eb, s, temps);
         if (st == BISIM_OK) st = finish_init(ctx, s);
         if (st == BISIM_OK) {
@@ -528,6 +580,7 @@ bisim_status summarize_init_coo(bisim_ctx** out, int32_t n_vertices, int64_t n_e
             st = build_from_coo(ctx, static_cast<const int32_t*>(temps[0]), static_cast<const int32_t*>(temps[1]),
                                 static_cast<const int32_t*>(temps[2]), s, &arr);
         }
+        turn.give();
         // no copy may still write a buffer that is freed (a failed build can
         // return before it waited for the last of them)
         if (st != BISIM_OK && ctx->copy_stream) cudaStreamSynchronize(static_cast<cudaStream_t>(ctx->copy_stream));

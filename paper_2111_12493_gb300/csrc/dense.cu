@@ -24,8 +24,10 @@
 // levels; the smallest vertex of each level's group is final, so the loop ends
 // with the exact partition.
 #include <algorithm>
+#include <condition_variable>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -772,6 +774,29 @@ __global__ void k_dense_hub_finalize(const DenseView D, const HubSets H) {
     finish_sig(D, pos, D.P[D.vert[pos]], H.acc[h].count, H.acc[h].sum);
 }
 
+
+// Hub chunks from the hub rows' offsets rows[0..nh] (device): hub h's row
+// [rows[h], rows[h+1]) in chunks of csz entries, hubs in order. One CTA of
+// 1024 threads; off[nh] is scratch for the chunk counts and their offsets.
+__global__ void __launch_bounds__(1024) k_hub_chunks(const int64_t* __restrict__ rows, int64_t nh, int64_t csz,
+                                                     int64_t* __restrict__ off, HubChunk* __restrict__ out) {
+    for (int64_t h = threadIdx.x; h < nh; h += blockDim.x) off[h] = (rows[h + 1] - rows[h] + csz - 1) / csz;
+    __syncthreads();
+    cta_exclusive_scan(off, off, nh);
+    __syncthreads();
+    for (int64_t h = threadIdx.x; h < nh; h += blockDim.x) {
+        const int64_t rb = rows[h], re = rows[h + 1];
+        int64_t c = off[h];
+        for (int64_t b = rb; b < re; b += csz, ++c) {
+            HubChunk k;
+            k.hub = static_cast<int32_t>(h);
+            k.vertex = -1;
+            k.begin = b;
+            k.end = b + csz < re ? b + csz : re;
+            out[c] = k;
+        }
+    }
+}
 
 // Start of a round: the status word, with the vertices that are not listed
 // (alone in their block of P_i, hence alone in P_{i+1}) already counted as
@@ -1785,34 +1810,35 @@ bisim_status dense_layout_hubs(bisim_ctx* ctx, bool pack_from_csr, cudaStream_t 
     const int64_t nh = begin[kDHub + 1] - begin[kDHub];
     BISIM_SITE(site_p, "dense_pack");
     if (nh > 0) {
+        // the chunks are laid out on the device from the rows' offsets (read
+        // back only to size them): a host-to-device copy here would wait behind
+        // any upload of another context in flight on the copy engine
         std::vector<int64_t> rows(nh + 1);
         cudaMemcpyAsync(rows.data(), ctx->dprp + begin[kDHub], sizeof(int64_t) * (nh + 1), cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "read hub rows");
-        std::vector<HubChunk> chunks;
         const int64_t csz = std::max(256, ctx->opt.hub_chunk);
-        for (int64_t h = 0; h < nh; ++h)
-            for (int64_t b = rows[h]; b < rows[h + 1]; b += csz)
-                chunks.push_back(HubChunk{static_cast<int32_t>(h), -1, b, std::min(rows[h + 1], b + csz)});
+        int64_t n_chunks = 0;
+        for (int64_t h = 0; h < nh; ++h) n_chunks += (rows[h + 1] - rows[h] + csz - 1) / csz;
         ctx->n_dhub = nh;
-        ctx->n_dchunks = static_cast<int64_t>(chunks.size());
+        ctx->n_dchunks = n_chunks;
         ctx->hub_edges = std::max<int64_t>(rows[nh] - rows[0], 1);
-        if ((!chunks.empty() &&
-             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dchunks), sizeof(HubChunk) * chunks.size(), s))) ||
+        int64_t* off = nullptr;
+        if ((n_chunks > 0 &&
+             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dchunks), sizeof(HubChunk) * n_chunks, s))) ||
             (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->htab), 2 * sizeof(unsigned long long) * ctx->hub_edges,
                            s)) ||
-            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dacc), sizeof(HubAcc) * nh, s)))
+            (e = ctx_alloc(ctx, reinterpret_cast<void**>(&ctx->dacc), sizeof(HubAcc) * nh, s)) ||
+            (e = cudaMallocAsync(reinterpret_cast<void**>(&off), sizeof(int64_t) * nh, s)))
             return cuda_error(ctx, e, "alloc hub tables");
-        if (!chunks.empty())
-            cudaMemcpyAsync(ctx->dchunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice, s);
-        if (pack_from_csr && !chunks.empty()) {
+        k_hub_chunks<<<1, 1024, 0, s>>>(ctx->dprp + begin[kDHub], nh, csz, off, ctx->dchunks);
+        cudaFreeAsync(off, s);
+        if (pack_from_csr && n_chunks > 0) {
             // hub rows are copied chunk by chunk, like the rounds read them
             const int64_t edges = m - ctx->dedge_begin[kDHub];
             Launch L(site_p, s, nh, edges, 16.0 * edges);
-            k_dense_pack_chunks<<<static_cast<unsigned>(chunks.size()), 256, 0, s>>>(
+            k_dense_pack_chunks<<<static_cast<unsigned>(n_chunks), 256, 0, s>>>(
                 ctx->dchunks, ctx->dvert, begin[kDHub], ctx->dprp, ctx->row_ptr, ctx->col, ctx->elab, ctx->dpe);
         }
-        // the host vectors die here: finish the uploads first
-        if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "upload hub layout");
     }
     if ((e = cudaGetLastError())) return cuda_error(ctx, e, "build dense layout");
     ctx->dense_ready = true;
@@ -1821,12 +1847,56 @@ bisim_status dense_layout_hubs(bisim_ctx* ctx, bool pack_from_csr, cudaStream_t 
     return BISIM_OK;
 }
 
+// Executable round graphs are destroyed on a thread of their own: the call
+// waits for copies in flight on other streams (a 1.2 GB upload of another
+// context held it for the upload's whole length), and neither the context
+// that drops its graph nor its caller has a reason to wait for them. The
+// state is never freed, so the idle thread outlives nothing it uses.
+struct GraphReaper {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<std::pair<int, cudaGraphExec_t>> queue;
+    bool started = false;
+};
+
+GraphReaper& graph_reaper() {
+    static GraphReaper* r = new GraphReaper();
+    return *r;
+}
+
+void reap_graphs() {
+    GraphReaper& R = graph_reaper();
+    for (;;) {
+        std::pair<int, cudaGraphExec_t> job;
+        {
+            std::unique_lock<std::mutex> lk(R.mu);
+            R.cv.wait(lk, [&] { return !R.queue.empty(); });
+            job = R.queue.back();
+            R.queue.pop_back();
+        }
+        cudaSetDevice(job.first);
+        cudaGraphExecDestroy(job.second);
+    }
+}
+
+void drop_round_graph(bisim_ctx* ctx) {
+    if (ctx->round_graph == nullptr) return;
+    GraphReaper& R = graph_reaper();
+    {
+        std::lock_guard<std::mutex> lk(R.mu);
+        if (!R.started) {
+            std::thread(reap_graphs).detach();
+            R.started = true;
+        }
+        R.queue.push_back({ctx->device, static_cast<cudaGraphExec_t>(ctx->round_graph)});
+    }
+    R.cv.notify_one();
+    ctx->round_graph = nullptr;
+}
+
 bisim_status dense_prepare(bisim_ctx* ctx, cudaStream_t s) {
     if (ctx->dense_ready) return BISIM_OK;
-    if (ctx->round_graph) {                    // captured for the previous layout
-        cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->round_graph));
-        ctx->round_graph = nullptr;
-    }
+    drop_round_graph(ctx);                     // captured for the previous layout
     bisim_status st;
     if ((st = ensure_vertex_csr(ctx, s)) != BISIM_OK) return st;
     const int32_t n = ctx->n;
@@ -2096,7 +2166,7 @@ bisim_status dense_graph_rounds(bisim_ctx* ctx, cudaStream_t s, int32_t limit, b
 }
 
 void dense_release(bisim_ctx* ctx) {
-    if (ctx->round_graph) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->round_graph));
+    drop_round_graph(ctx);
     if (ctx->capture_stream) cudaStreamDestroy(static_cast<cudaStream_t>(ctx->capture_stream));
     pinned_give(ctx->hloop);
     ctx->round_graph = nullptr;

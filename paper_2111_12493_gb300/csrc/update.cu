@@ -572,15 +572,21 @@ struct PurgeTarget {
     }
 };
 
-// A deleted vertex's out-row empties; a revived vertex's in-row starts afresh
-// (its former sources were purged).
+// A deleted vertex's out-row empties, and its out-edges count as changed: a
+// vertex deleted and added again in one batch with its old label is live
+// before and after and keeps its label, so only this flag puts it into the
+// frontiers above level 0. A revived vertex's in-row starts afresh (its former
+// sources were purged).
 __global__ void k_vertex_rows(VertexOps V, const uint8_t* __restrict__ killed, const uint8_t* __restrict__ revived,
-                              StoreView S) {
+                              StoreView S, uint8_t* __restrict__ rowchg) {
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < V.nv;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         if (i + 1 < V.nv && V.key[i + 1] == V.key[i]) continue;
         const int32_t x = static_cast<int32_t>(V.key[i]);
-        if (killed[x]) S.xlen[x] = 0;
+        if (killed[x]) {
+            S.xlen[x] = 0;
+            rowchg[x] = 1;
+        }
         if (revived[x]) S.ylen[x] = 0;
     }
 }
@@ -1112,7 +1118,7 @@ bisim_status apply_ops_to_store(bisim_ctx* ctx, const bisim_op* d_ops, int64_t n
         k_vertex_tasks<<<grid_for(nv, 256), 256, 0, s>>>(B.V, killed, revived, S, LA, nullptr);
         run_tiers(LA, VertexSources{ctx->ype, killed, revived, rowchg, S, LP}, s);
         run_tiers(LP, PurgeTarget{ctx->xpe}, s);
-        k_vertex_rows<<<grid_for(nv, 256), 256, 0, s>>>(B.V, killed, revived, S);
+        k_vertex_rows<<<grid_for(nv, 256), 256, 0, s>>>(B.V, killed, revived, S, rowchg);
         if (pmem) cudaFreeAsync(pmem, s);
     }
     // added copies: rows that cannot take them move first

@@ -19,11 +19,10 @@ Request kinds:
   release(graph_id)
       drop a resident graph and return its memory to the budget.
 
-Summarize requests whose graph is in host memory take turns for the upload:
-the host link, not the GPU, bounds such a request's build, and two uploads at
-once would only split the link, so one request's upload and build run while
-the others refine, download or wait (an "upload lane"). Requests with device
-inputs build without waiting.
+Summarize requests whose graph is in host memory are uploaded one after the
+other by the library (summarize_init_coo queues the edge arrays of one
+context at a time on the host link), so one request's upload overlaps the
+others' builds and rounds instead of sharing the link with them.
 
 The scheduling logic (admission by slots and memory, per-graph ordering) is
 independent of the GPU: `Scheduler` takes an executor callable, which the
@@ -33,7 +32,6 @@ tests replace by a CPU stand-in.
 from __future__ import annotations
 
 import collections
-import contextlib
 import threading
 import time
 from concurrent.futures import Future
@@ -219,7 +217,6 @@ class GpuExecutor:
         torch.cuda.set_device(device)
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
         self.contexts: dict = {}
-        self.upload_lane = threading.Lock()
 
     def __call__(self, req: Request, slot: int):
         torch, B = self.torch, self.bisim
@@ -232,10 +229,8 @@ class GpuExecutor:
                 if old is not None:
                     B.summarize_destroy(old)
                 opt = B.default_options(k_incremental=p.get("k_incremental", 2))
-                from_host = not p["src"].is_cuda
-                with self.upload_lane if from_host else contextlib.nullcontext():
-                    ctx = B.summarize_init_coo(p["n"], p["src"], p["dst"], p["edge_label"], p["vertex_label"],
-                                               options=opt, stream=stream)
+                ctx = B.summarize_init_coo(p["n"], p["src"], p["dst"], p["edge_label"], p["vertex_label"],
+                                           options=opt, stream=stream)
                 rounds, blocks = B.bisim_iterate(ctx, p.get("k", B.FIXPOINT), p.get("cap", 10), stream=stream)
                 out = B.get_partition(ctx, stream=stream)
                 footprint = 0

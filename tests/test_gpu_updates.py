@@ -269,6 +269,28 @@ def test_batch_that_outgrows_the_row_store(B):
     B.summarize_destroy(ctx)
 
 
+@pytest.mark.parametrize("k", [1, 2])
+def test_vertex_deleted_and_added_again_with_its_label(B, k):
+    """A vertex deleted and added again in one batch with the label it had is
+    live before and after and keeps its label, yet its out-edges are gone:
+    its signatures above level 0 must be recomputed."""
+    n = 7
+    src = np.array([0, 0, 2, 5], np.int32)
+    dst = np.array([1, 3, 3, 6], np.int32)
+    lab = np.array([1, 2, 1, 1], np.int32)
+    vl = np.zeros(n, np.int32)
+    state = dict(n=n, alive=np.ones(n, np.uint8), vlabel=vl.copy(), src=src, dst=dst, elabel=lab)
+    ctx = B.summarize_init_coo(n, _dev(src), _dev(dst), _dev(lab), _dev(vl), options=B.default_options(k_incremental=k))
+    B.apply_updates(ctx, _dev(np.zeros((0, 4), np.int32)))
+    for ops in ([[3, 0, 0, 0], [2, 0, 0, 0]], [[0, 0, 1, 1]], [[3, 2, 0, 0], [2, 2, 0, 0], [0, 4, 2, 1]],
+                [[0, 0, 3, 2], [3, 0, 0, 0], [2, 0, 0, 0]]):
+        ops = np.array(ops, np.int32)
+        state = oracle.apply_ops(state, ops)
+        B.apply_updates(ctx, _dev(ops))
+        check_partition(B, ctx, state, k)
+    B.summarize_destroy(ctx)
+
+
 def test_revived_vertices_do_not_keep_old_in_edges(B):
     """A vertex deleted in one batch and added again in a later one comes back
     without the edges it had (edges into it stayed in their source rows while
