@@ -449,3 +449,30 @@ def test_long_mixed_stream_reuses_block_ids(B):
     assert applied >= 100
     assert B.bisim_get_stats(ctx)["state_builds"] == 1
     B.summarize_destroy(ctx)
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_long_mixed_streams_on_power_law_graphs(B, seed):
+    """Eighty batches of mixed operations on a power-law graph with hubs
+    (out-degrees up to 600, so hub rows take the long-row and hub paths),
+    k = 2, every partition equal to the oracle's."""
+    rng = np.random.default_rng(seed)
+    g = graphgen.powerlaw_graph(n=1500, m=9000, dmax=600, n_elabels=4, n_vlabels=3, seed=700 + seed)
+    state = dict(n=g["n"], alive=np.ones(g["n"], np.uint8), vlabel=g["vlabel"].copy(), src=g["src"],
+                 dst=g["dst"], elabel=g["elabel"])
+    ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]),
+                               options=B.default_options(k_incremental=2, mid_max_degree=256))
+    applied = 0
+    for step in range(80):
+        ops = random_batch(rng, state, int(rng.integers(20, 300)), n_elabels=4, n_vlabels=3)
+        try:
+            state2 = oracle.apply_ops(state, ops)
+        except oracle.UpdateRejected:
+            continue
+        B.apply_updates(ctx, _dev(ops))
+        state = state2
+        applied += 1
+        check_partition(B, ctx, state, 2)
+    assert applied >= 50
+    assert B.bisim_get_stats(ctx)["state_builds"] == 1
+    B.summarize_destroy(ctx)
