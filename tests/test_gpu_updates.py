@@ -476,3 +476,32 @@ def test_long_mixed_streams_on_power_law_graphs(B, seed):
     assert applied >= 50
     assert B.bisim_get_stats(ctx)["state_builds"] == 1
     B.summarize_destroy(ctx)
+
+
+@pytest.mark.parametrize("direction,mode,keep", [(1, "backward", None), (2, "both", [1, 3])])
+def test_long_streams_in_other_directions_and_with_a_label_filter(B, direction, mode, keep):
+    """Forty batches of mixed operations with backward or forward-backward
+    signatures, with and without a label filter, k = 3: every partition equal
+    to the oracle's under the same parameterization (Section 2.4.2)."""
+    rng = np.random.default_rng(44 + direction)
+    g = graphgen.uniform_graph(n=500, m=1500, n_elabels=4, n_vlabels=3, seed=45)
+    state = dict(n=g["n"], alive=np.ones(g["n"], np.uint8), vlabel=g["vlabel"].copy(), src=g["src"],
+                 dst=g["dst"], elabel=g["elabel"])
+    opts = dict(direction=direction)
+    if keep is not None:
+        opts["label_filter"] = keep
+    ctx = B.summarize_init_coo(g["n"], _dev(g["src"]), _dev(g["dst"]), _dev(g["elabel"]), _dev(g["vlabel"]),
+                               options=B.default_options(k_incremental=3, **opts))
+    for step in range(40):
+        ops = random_batch(rng, state, int(rng.integers(1, 250)), n_elabels=4, n_vlabels=3)
+        try:
+            state2 = oracle.apply_ops(state, ops)
+        except oracle.UpdateRejected:
+            continue
+        B.apply_updates(ctx, _dev(ops))
+        state = state2
+        got = B.get_partition(ctx).cpu().numpy()
+        want, _, _ = oracle.refine(state["n"], state["src"], state["dst"], state["elabel"], state["vlabel"], 3,
+                                   alive=state["alive"], direction=mode, label_filter=keep)
+        assert np.array_equal(got, want), step
+    B.summarize_destroy(ctx)
