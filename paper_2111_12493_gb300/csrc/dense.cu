@@ -24,7 +24,9 @@
 // levels; the smallest vertex of each level's group is final, so the loop ends
 // with the exact partition.
 #include <algorithm>
+#include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <thread>
@@ -1851,12 +1853,16 @@ bisim_status dense_layout_hubs(bisim_ctx* ctx, bool pack_from_csr, cudaStream_t 
 // waits for copies in flight on other streams (a 1.2 GB upload of another
 // context held it for the upload's whole length), and neither the context
 // that drops its graph nor its caller has a reason to wait for them. The
-// state is never freed, so the idle thread outlives nothing it uses.
+// state is never freed, so the idle thread outlives nothing it uses; at
+// process exit a handler waits (at most ten seconds) until the queue is
+// empty, so that no destroy runs while the CUDA runtime shuts down.
 struct GraphReaper {
     std::mutex mu;
-    std::condition_variable cv;
+    std::condition_variable cv;       // work queued
+    std::condition_variable idle;     // queue empty and no destroy running
     std::vector<std::pair<int, cudaGraphExec_t>> queue;
     bool started = false;
+    bool busy = false;
 };
 
 GraphReaper& graph_reaper() {
@@ -1873,10 +1879,22 @@ void reap_graphs() {
             R.cv.wait(lk, [&] { return !R.queue.empty(); });
             job = R.queue.back();
             R.queue.pop_back();
+            R.busy = true;
         }
         cudaSetDevice(job.first);
         cudaGraphExecDestroy(job.second);
+        {
+            std::lock_guard<std::mutex> lk(R.mu);
+            R.busy = false;
+        }
+        R.idle.notify_all();
     }
+}
+
+void drain_graph_reaper() {
+    GraphReaper& R = graph_reaper();
+    std::unique_lock<std::mutex> lk(R.mu);
+    R.idle.wait_for(lk, std::chrono::seconds(10), [&] { return R.queue.empty() && !R.busy; });
 }
 
 void drop_round_graph(bisim_ctx* ctx) {
@@ -1886,6 +1904,7 @@ void drop_round_graph(bisim_ctx* ctx) {
         std::lock_guard<std::mutex> lk(R.mu);
         if (!R.started) {
             std::thread(reap_graphs).detach();
+            std::atexit(drain_graph_reaper);
             R.started = true;
         }
         R.queue.push_back({ctx->device, static_cast<cudaGraphExec_t>(ctx->round_graph)});
