@@ -203,9 +203,9 @@ bisim_status copy_vertex_arrays(bisim_ctx* ctx, const int32_t* vlabel, const uin
 // host link bounds such a copy, and two at once would only share it and
 // finish both late, while one after the other lets the first context build
 // and refine while the second copies. A context holds the lane from before
-// its first copy until its build has seen the last one arrive. A wait gives
-// up after a minute (the lane then only loses its ordering), so a context
-// that never lets go cannot block the others for good.
+// its first copy until the last one has arrived. A wait gives up after a
+// minute (the lane then only loses its ordering), so a context that never
+// lets go cannot block the others for good.
 struct UploadLane {
     std::mutex mu;
     std::condition_variable cv;
@@ -568,15 +568,18 @@ bisim_status summarize_init_coo(bisim_ctx** out, int32_t n_vertices, int64_t n_e
         !device_accessible(edge_label)) {
         // a host list: copied in on a stream of its own, sources first, while
         // P_0 and then the sources' part of the build run on `stream`; the
-        // upload lane is held until the build has seen the last array arrive
+        // upload lane is held until the last array has arrived
         LaneTurn turn;
         turn.take();
         if ((st = copy_vertex_arrays(ctx, vertex_label, alive, s)) == BISIM_OK) st = coo_arrive(ctx, src, dst, edge_label, eb, s, temps);
         if (st == BISIM_OK) st = finish_init(ctx, s);
         if (st == BISIM_OK) {
-            const CooArrival arr{static_cast<cudaEvent_t>(ctx->copy_events[1]),
-                                 static_cast<cudaEvent_t>(ctx->copy_events[2]),
-                                 static_cast<cudaEvent_t>(ctx->copy_events[3])};
+            CooArrival arr;
+            arr.src = static_cast<cudaEvent_t>(ctx->copy_events[1]);
+            arr.dst = static_cast<cudaEvent_t>(ctx->copy_events[2]);
+            arr.lab = static_cast<cudaEvent_t>(ctx->copy_events[3]);
+            arr.arrived = [](void* t) { static_cast<LaneTurn*>(t)->give(); };
+            arr.arrived_arg = &turn;
             st = build_from_coo(ctx, static_cast<const int32_t*>(temps[0]), static_cast<const int32_t*>(temps[1]),
                                 static_cast<const int32_t*>(temps[2]), s, &arr);
         }

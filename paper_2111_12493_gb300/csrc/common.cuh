@@ -465,6 +465,10 @@ int radix_sort_pairs(uint32_t* k0, uint64_t* v0, uint32_t* k1, uint64_t* v1, int
 // first use.
 struct CooArrival {
     cudaEvent_t src, dst, lab;
+    // called (when set) as soon as the last array has arrived, before the
+    // rows are placed
+    void (*arrived)(void*) = nullptr;
+    void* arrived_arg = nullptr;
 };
 bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* dst,
                             const int32_t* elab, cudaStream_t s, const CooArrival* arrival = nullptr);

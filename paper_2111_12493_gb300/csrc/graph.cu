@@ -225,6 +225,14 @@ bisim_status build_from_coo(bisim_ctx* ctx, const int32_t* src, const int32_t* d
             k_validate_dst<<<grid, 256, 0, s>>>(dst, m, n, ctx->alive, ctx->dstate);
         }
         cudaStreamWaitEvent(s, arrival->lab, 0);
+        if (arrival->arrived != nullptr) {
+            // the host link is free again: let the next upload start
+            if ((e = cudaEventSynchronize(arrival->lab))) {
+                cudaFreeAsync(base, s);
+                return cuda_error(ctx, e, "edge labels copy");
+            }
+            arrival->arrived(arrival->arrived_arg);
+        }
     }
     if (m > 0) {
         // read src, dst, label, the source's position and row offset; write the packed word
