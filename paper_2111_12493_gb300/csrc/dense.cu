@@ -1005,6 +1005,12 @@ struct ClassBounds {
     int64_t b[kDClasses + 1];
 };
 
+// First packed edge of every class: prp at the classes' first positions.
+__global__ void k_class_edge_begin(const int64_t* __restrict__ prp, const ClassBounds cb, int64_t* __restrict__ out) {
+    const int c = static_cast<int>(threadIdx.x);
+    if (c <= kDClasses) out[c] = prp[cb.b[c]];
+}
+
 __device__ __forceinline__ bool stays_listed(const DenseView& D, int64_t pos) {
     return !alone_last_round(D, pos);
 }
@@ -1798,8 +1804,9 @@ bisim_status dense_layout_positions(bisim_ctx* ctx, const int32_t* deg, cudaStre
         k_dense_degrees<<<grid_for(n_live + 1, 256), 256, 0, s>>>(ctx->dvert, n_live, deg, pdeg);
     }
     exclusive_scan_i64(pdeg, ctx->dprp, n_live + 1, tmp, s);
-    for (int c = 0; c <= kDClasses; ++c)
-        cudaMemcpyAsync(&ctx->dedge_begin[c], ctx->dprp + begin[c], sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    // the classes' first edges in one read-back (dbeg is free again)
+    k_class_edge_begin<<<1, 32, 0, s>>>(ctx->dprp, class_bounds(ctx), dbeg);
+    cudaMemcpyAsync(ctx->dedge_begin, dbeg, sizeof(int64_t) * (kDClasses + 1), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(base, s);
     if ((e = cudaStreamSynchronize(s))) return cuda_error(ctx, e, "row offsets");
     return BISIM_OK;

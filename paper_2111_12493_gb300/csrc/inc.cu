@@ -920,6 +920,7 @@ Level level_view(const bisim_ctx* ctx, int j) {
 }
 
 constexpr int kHubPrefetch = 2048;     // hub records read back with the level's counts
+constexpr size_t kHubStageBytes = size_t{1} << 20;   // pinned stage of a frontier's hub layout
 constexpr int64_t kThreadClassOps = 20000;   // batches above this use thread-per-vertex classes
 
 // Host copies of everything a level pass reads back, in pinned memory so that
@@ -956,6 +957,7 @@ struct Scratch {
     unsigned long long* chcount = nullptr;
     TierLists tiers{};                 // in-row tasks, [n] per tier
     HostStage* h = nullptr;            // pinned
+    char* hub_stage = nullptr;         // pinned: a frontier's hub chunks, offsets, masks and ids (kHubStageBytes)
     int32_t* FX = nullptr;             // [n] live frontier vertices alone in their block one level down
     unsigned long long* ltab = nullptr;   // level-0 label table, a power of two >= 2n slots
 };
@@ -982,6 +984,13 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
     S.bytes = bytes;
     ctx->device_bytes += static_cast<int64_t>(bytes);
     if ((e = cudaHostAlloc(reinterpret_cast<void**>(&S.h), sizeof(HostStage), cudaHostAllocDefault))) {
+        cudaFreeAsync(S.base, s);
+        S.base = nullptr;
+        return e;
+    }
+    if ((e = cudaHostAlloc(reinterpret_cast<void**>(&S.hub_stage), kHubStageBytes, cudaHostAllocDefault))) {
+        cudaFreeHost(S.h);
+        S.h = nullptr;
         cudaFreeAsync(S.base, s);
         S.base = nullptr;
         return e;
@@ -1047,10 +1056,9 @@ cudaError_t alloc_scratch(bisim_ctx* ctx, Scratch& S, cudaStream_t s) {
 
 void free_scratch(Scratch* S, cudaStream_t s) {
     if (S->base) cudaFreeAsync(S->base, s);
-    if (S->h) {
-        cudaStreamSynchronize(s);                          // no copy into the stage is left in flight
-        cudaFreeHost(S->h);
-    }
+    if (S->h || S->hub_stage) cudaStreamSynchronize(s);   // no copy into or out of a stage is left in flight
+    if (S->h) cudaFreeHost(S->h);
+    if (S->hub_stage) cudaFreeHost(S->hub_stage);
     delete S;
 }
 
@@ -1113,24 +1121,38 @@ bisim_status finish_buckets(bisim_ctx* ctx, Scratch& S, ListBuckets& out, cudaSt
         for (int64_t b = rb; b < re; b += csz)
             chunks.push_back(HubChunk{static_cast<int32_t>(h), hubs[h].v, b, std::min(re, b + csz)});
     }
-    const size_t bytes = sizeof(HubChunk) * chunks.size() + 256 + sizeof(int64_t) * B.n_hub + 256 +
-                         sizeof(uint32_t) * B.n_hub + 256 + sizeof(unsigned long long) * words + 256 +
-                         sizeof(HubAcc) * B.n_hub + 256 + sizeof(int32_t) * B.n_hub + 256;
+    // the host-made part (chunks, table offsets, masks, hub ids) first, so that
+    // one copy from the pinned stage moves it when it fits there
+    auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t head = r256(sizeof(HubChunk) * chunks.size()) + r256(sizeof(int64_t) * B.n_hub) +
+                        r256(sizeof(uint32_t) * B.n_hub) + r256(sizeof(int32_t) * B.n_hub);
+    const size_t bytes = head + r256(sizeof(unsigned long long) * words) + r256(sizeof(HubAcc) * B.n_hub);
     char* p = nullptr;
     if ((e = cudaMallocAsync(reinterpret_cast<void**>(&p), bytes, s))) return cuda_error(ctx, e, "alloc frontier hubs");
     out.hubmem = p;
-    auto carve = [&](size_t b) { char* q = p; p += (b + 255) & ~size_t(255); return q; };
+    char* const dbase = p;
+    auto carve = [&](size_t b) { char* q = p; p += r256(b); return q; };
     HubChunk* dchunks = reinterpret_cast<HubChunk*>(carve(sizeof(HubChunk) * chunks.size()));
     int64_t* dtoff = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * B.n_hub));
     uint32_t* dtmask = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * B.n_hub));
+    int32_t* dids = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * B.n_hub));
     unsigned long long* dtab = reinterpret_cast<unsigned long long*>(carve(sizeof(unsigned long long) * words));
     HubAcc* dacc = reinterpret_cast<HubAcc*>(carve(sizeof(HubAcc) * B.n_hub));
-    int32_t* dids = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * B.n_hub));
-    // pageable sources: each copy has taken its data when the call returns
-    cudaMemcpyAsync(dchunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(dtoff, toff.data(), sizeof(int64_t) * B.n_hub, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(dtmask, tmask.data(), sizeof(uint32_t) * B.n_hub, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(dids, ids.data(), sizeof(int32_t) * B.n_hub, cudaMemcpyHostToDevice, s);
+    if (head <= kHubStageBytes) {
+        // the stage's last copy has finished: the level synchronised since
+        char* h = S.hub_stage;
+        std::memcpy(h + (reinterpret_cast<char*>(dchunks) - dbase), chunks.data(), sizeof(HubChunk) * chunks.size());
+        std::memcpy(h + (reinterpret_cast<char*>(dtoff) - dbase), toff.data(), sizeof(int64_t) * B.n_hub);
+        std::memcpy(h + (reinterpret_cast<char*>(dtmask) - dbase), tmask.data(), sizeof(uint32_t) * B.n_hub);
+        std::memcpy(h + (reinterpret_cast<char*>(dids) - dbase), ids.data(), sizeof(int32_t) * B.n_hub);
+        cudaMemcpyAsync(dbase, h, head, cudaMemcpyHostToDevice, s);
+    } else {
+        // pageable sources: each copy has taken its data when the call returns
+        cudaMemcpyAsync(dchunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(dtoff, toff.data(), sizeof(int64_t) * B.n_hub, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(dtmask, tmask.data(), sizeof(uint32_t) * B.n_hub, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(dids, ids.data(), sizeof(int32_t) * B.n_hub, cudaMemcpyHostToDevice, s);
+    }
     B.hub_list = dids;
     B.chunks = dchunks;
     B.n_chunks = static_cast<int64_t>(chunks.size());
