@@ -584,6 +584,21 @@ def test_apply_ops_sequential_semantics():
     assert sorted(zip(out["src"].tolist(), out["dst"].tolist(), out["elabel"].tolist())) == [(2, 3, 7)]
 
 
+def test_vertex_deleted_and_added_with_its_label_has_no_edges_left():
+    # a vertex deleted and added again in one batch with the label it had
+    # comes back without its edges: with every label equal and no edge left,
+    # every vertex is in one block at k = 1 (before the batch, vertex 0's
+    # out-edge set it apart)
+    st = dict(n=4, alive=np.ones(4, np.uint8), vlabel=np.zeros(4, np.int32),
+              src=np.array([0], np.int32), dst=np.array([1], np.int32), elabel=np.array([1], np.int32))
+    before, _, _ = oracle.refine(4, st["src"], st["dst"], st["elabel"], st["vlabel"], 1)
+    assert before.tolist() == [0, 1, 1, 1]
+    out = oracle.apply_ops(st, np.array([[oracle.OP_VERTEX_DEL, 0, 0, 0], [oracle.OP_VERTEX_ADD, 0, 0, 0]], np.int32))
+    assert len(out["src"]) == 0 and out["alive"].tolist() == [1, 1, 1, 1] and out["vlabel"].tolist() == [0, 0, 0, 0]
+    after, _, _ = oracle.refine(4, out["src"], out["dst"], out["elabel"], out["vlabel"], 1, alive=out["alive"])
+    assert after.tolist() == [0, 0, 0, 0]
+
+
 def test_apply_ops_rejects_whole_batch():
     st = dict(n=3, alive=np.array([1, 1, 0], np.uint8), vlabel=np.zeros(3, np.int32),
               src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32), elabel=np.zeros(0, np.int32))
