@@ -90,3 +90,52 @@ def test_calls_fail_loudly_without_a_gpu():
     with pytest.raises(RuntimeError):
         bisim.summarize_init_coo(2, torch.zeros(0, dtype=torch.int32), torch.zeros(0, dtype=torch.int32),
                                  torch.zeros(0, dtype=torch.int32), torch.zeros(2, dtype=torch.int32))
+
+
+def _header_struct(name):
+    """Fields of `typedef struct { ... } name;` in the header as (field, kind)
+    pairs, kind one of i32, i64, f64, ptr, char[N]."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        arr = re.fullmatch(r"char (\w+)\[(\d+)\]", decl)
+        if arr:
+            fields.append((arr.group(1), f"char[{arr.group(2)}]"))
+            continue
+        typ, names = re.fullmatch(r"((?:const )?\w+\s*\*?)\s*(.+)", decl).groups()
+        kind = "ptr" if "*" in typ else {"int32_t": "i32", "int64_t": "i64", "double": "f64"}[typ.strip()]
+        fields.extend((n.strip(), kind) for n in names.split(","))
+    return fields
+
+
+def _ctypes_kind(t):
+    import ctypes as C
+    if t is C.c_int32:
+        return "i32"
+    if t is C.c_int64:
+        return "i64"
+    if t is C.c_double:
+        return "f64"
+    if t is C.c_void_p:
+        return "ptr"
+    if issubclass(t, C.Array) and t._type_ is C.c_char:
+        return f"char[{t._length_}]"
+    raise AssertionError(t)
+
+
+@pytest.mark.parametrize("cname,pyname", [("bisim_options", "Options"), ("bisim_stats", "Stats"),
+                                          ("bisim_kernel_profile", "KernelProfile")])
+def test_binding_structs_mirror_the_header(cname, pyname):
+    # the ctypes mirrors of the binding must match the header field by field,
+    # or calls would read and write past them
+    try:
+        from paper_2111_12493_gb300 import bisim
+    except (OSError, RuntimeError) as e:  # library not built here
+        pytest.skip(str(e))
+    py = [(f, _ctypes_kind(t)) for f, t in getattr(bisim, pyname)._fields_]
+    assert py == _header_struct(cname)
