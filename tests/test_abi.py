@@ -139,3 +139,9 @@ def test_binding_structs_mirror_the_header(cname, pyname):
         pytest.skip(str(e))
     py = [(f, _ctypes_kind(t)) for f, t in getattr(bisim, pyname)._fields_]
     assert py == _header_struct(cname)
+
+
+def test_update_rows_match_the_op_struct():
+    # apply_updates takes [n_ops, 4] int32 rows (kind, src, dst, label): bisim_op
+    # must be exactly those four 32-bit fields, in that order
+    assert _header_struct("bisim_op") == [("kind", "i32"), ("src", "i32"), ("dst", "i32"), ("label", "i32")]
